@@ -1,0 +1,87 @@
+"""Seeded synthetic inputs for the FFS island GA (tests, smoke check and bench).
+
+This module holds no arithmetic of the method: it only draws instances and
+random job orders with numpy's PCG64 generator, so both the CUDA path and
+the CPU oracle can be fed identical inputs.  The GA's own randomness
+(Philox4x32-10) is not here; each side implements it on its own.
+
+Instance shapes follow the workloads the library is measured on (the paper's
+own 300x4x2 instances, Section 5 and Table 1, are unpublished; these stand
+in for them):
+
+  tiny         20 jobs x 5 stages, 3 machines per stage, p ~ U[1,99]; 8x8 torus
+  dual_100x10  100 jobs x 10 stages, M_s ~ U[2,5]; 64x64 torus + pseudo 4096
+  scale_500x20 500 jobs x 20 stages, M_s ~ U[5,10]; 4 x 128x128 torus +
+               4 pseudo islands of 16384 (131072 chromosomes)
+  batch_256    256 instances, n ~ U[20,500], S ~ U[5,20], M_s ~ U[2,10];
+               32x32 torus each
+  paper_300x4  the paper's shape: 300 jobs x 4 stages x 2 machines,
+               p ~ U[1,5] (Section 5, Table 1), for context runs
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class InstanceSpec:
+    n: int
+    S: int
+    M: np.ndarray   # int32 [S]
+    p: np.ndarray   # int32 [n][S]
+
+
+def make_instance(n: int, S: int, m_lo: int, m_hi: int, p_lo: int = 1, p_hi: int = 99,
+                  seed: int = 1) -> InstanceSpec:
+    """M_s ~ U{m_lo..m_hi}, p[j][s] ~ U{p_lo..p_hi}, drawn in that order."""
+    rng = np.random.default_rng(seed)
+    M = rng.integers(m_lo, m_hi + 1, size=S, dtype=np.int64).astype(np.int32)
+    p = rng.integers(p_lo, p_hi + 1, size=(n, S), dtype=np.int64).astype(np.int32)
+    return InstanceSpec(n, S, M, p)
+
+
+def make_batch(count: int = 256, seed: int = 1, n_range=(20, 500), s_range=(5, 20),
+               m_range=(2, 10), p_range=(1, 99)) -> list[InstanceSpec]:
+    """Uneven instances: n, S, then M_s and p per instance, one stream."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        S = int(rng.integers(s_range[0], s_range[1] + 1))
+        M = rng.integers(m_range[0], m_range[1] + 1, size=S, dtype=np.int64).astype(np.int32)
+        p = rng.integers(p_range[0], p_range[1] + 1, size=(n, S), dtype=np.int64).astype(np.int32)
+        out.append(InstanceSpec(n, S, M, p))
+    return out
+
+
+def random_population(n: int, N: int, ld: int | None = None, seed: int = 0) -> np.ndarray:
+    """N random job orders of n jobs as int16 rows of length ld (padding = 0)."""
+    ld = ld if ld is not None else ((n + 7) // 8) * 8
+    rng = np.random.default_rng(seed)
+    pop = np.zeros((N, ld), dtype=np.int16)
+    keys = rng.random((N, n))
+    pop[:, :n] = np.argsort(keys, axis=1).astype(np.int16)
+    return pop
+
+
+WORKLOADS = {
+    "tiny": dict(n=20, S=5, m=(3, 3), seed=1, n_cellular=1, rows=8, cols=8,
+                 n_pseudo=0, pseudo_size=0, generations=100),
+    "dual_100x10": dict(n=100, S=10, m=(2, 5), seed=1, n_cellular=1, rows=64, cols=64,
+                        n_pseudo=1, pseudo_size=4096, generations=1000,
+                        migration="ring", gap=50, mig_num=2, mig_den=100),
+    "scale_500x20": dict(n=500, S=20, m=(5, 10), seed=1, n_cellular=4, rows=128, cols=128,
+                         n_pseudo=4, pseudo_size=16384, generations=200,
+                         migration="ring", gap=1, mig_num=2, mig_den=100),
+    "paper_300x4": dict(n=300, S=4, m=(2, 2), p=(1, 5), seed=1, n_cellular=1, rows=16, cols=16,
+                        n_pseudo=1, pseudo_size=256, generations=2000,
+                        migration="penetration", gap=500),
+}
+
+
+def workload_instance(name: str) -> InstanceSpec:
+    w = WORKLOADS[name]
+    p = w.get("p", (1, 99))
+    return make_instance(w["n"], w["S"], w["m"][0], w["m"][1], p[0], p[1], seed=w["seed"])

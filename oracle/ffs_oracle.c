@@ -1,0 +1,543 @@
+/*
+ * ffs_oracle.c -- plain, slow, single-threaded CPU oracle for the flexible
+ * flow shop (FFS) island GA hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent statement of what
+ * the GPU library must compute.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline arm may load it.  It shares no code, header, table
+ * or constant generator with the CUDA library; every function below is
+ * written from its definition, in the order the method states it, with no
+ * blocking, fusion or reordering.
+ *
+ * Sources (Luo & El Baz, "A Dual Heterogeneous Island Genetic Algorithm for
+ * Solving Large Size Flexible Flow Shop Scheduling Problems on Hybrid
+ * multi-core CPU and GPU Platforms", arXiv:1903.10722):
+ *   - Section 3: the FFS problem (jobs pass all stages in order, each
+ *     operation on exactly one of M_s identical machines, no preemption).
+ *   - Section 4.1: the two islands (cellular GA on a 2D grid, pseudo GA with
+ *     complementary parents whose children replace them).
+ *   - Section 4.2: the cellular step (recombine two neighbours, mutate,
+ *     replace the cell if better).
+ *   - Section 4.3, Eq. (1)-(2): the penetration migration policy.
+ *   - Section 5: parameter values (pc 1.00 / pm 0.05 cellular, pc 0.75
+ *     pseudo, theta 1.00).
+ * The schedule decoder (stage-wise list scheduling) and the operators (order
+ * crossover, swap mutation, binary tournament on a von Neumann torus) are not
+ * spelled out in the paper; the readings used here are listed in the header
+ * comment of each function and in the design notes of the repository.
+ *
+ * Philox4x32-10 follows Salmon, Moraes, Dror and Shaw, "Parallel Random
+ * Numbers: As Easy as 1, 2, 3", SC 2011 (Section 4, the Philox S-box).
+ *
+ * Parity status: the decoder, the operators, Philox and the migration
+ * formulas are pinned by tests (hand-worked Gantt charts, closed forms,
+ * brute force, library cross-checks).  The GA loop as a whole (the sequence
+ * of generations) has no published trajectory: "parity unpinned" beyond
+ * those component pins.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al. 2011)                                  */
+/* ------------------------------------------------------------------ */
+
+/* One call = ten rounds.  Each round multiplies the even words of the
+ * counter by the two Philox multipliers, and builds the new counter from the
+ * high halves xor'ed with the odd words and the round key; the key is bumped
+ * by the two Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                       uint32_t out[4])
+{
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += weyl0;
+            k1 += weyl1;
+        }
+        uint64_t prod0 = (uint64_t)mult0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)mult1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Purpose codes of the counter's fourth word (top 8 bits). */
+enum { ORC_PURPOSE_INIT = 1, ORC_PURPOSE_CELLULAR = 2, ORC_PURPOSE_PSEUDO = 3,
+       ORC_PURPOSE_SURROGATE = 4 };
+
+/* Draw number d of the stream keyed by (seed, island, generation, cell):
+ * counter = (d / 4, cell, generation, island | purpose << 24),
+ * key = (low, high) 32-bit halves of the seed, result word = d mod 4. */
+uint32_t orc_draw(uint64_t seed, uint32_t purpose, uint32_t island,
+                  uint32_t generation, uint32_t cell, uint32_t d)
+{
+    uint32_t ctr[4] = { d / 4u, cell, generation, (island & 0xFFFFFFu) | (purpose << 24) };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[d % 4u];
+}
+
+/* Integer in [0, k): the high word of x * k (no rejection step). */
+uint32_t orc_uniform(uint32_t x, uint32_t k)
+{
+    return (uint32_t)(((uint64_t)x * (uint64_t)k) >> 32);
+}
+
+/* Bernoulli event with probability threshold / 2^32 (threshold in [0, 2^32]). */
+int orc_bernoulli(uint32_t x, uint64_t threshold)
+{
+    return (uint64_t)x < threshold;
+}
+
+/* ------------------------------------------------------------------ */
+/* Schedule decoder: stage-wise list scheduling                        */
+/* ------------------------------------------------------------------ */
+
+/* Stage 1 takes the jobs in chromosome order.  Every later stage takes them
+ * in ascending (completion time at the previous stage, job index) order.
+ * Each job goes to the machine that is free earliest, the lowest machine
+ * index on ties, and starts at max(machine free time, release from the
+ * previous stage).  Stage-1 release time is 0.  Returns C_max.
+ *
+ * p is [n][S] row-major (job-major).  If gantt is not NULL it receives
+ * n*S records of 5 int64 (stage, job, machine, start, end) in dispatch
+ * order, stage by stage. */
+typedef struct { int64_t c; int32_t j; } orc_pair;
+
+static int orc_pair_cmp(const void *a, const void *b)
+{
+    const orc_pair *x = (const orc_pair *)a, *y = (const orc_pair *)b;
+    if (x->c < y->c) return -1;
+    if (x->c > y->c) return 1;
+    if (x->j < y->j) return -1;
+    if (x->j > y->j) return 1;
+    return 0;
+}
+
+int64_t orc_decode(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                   const int16_t *perm, int64_t *gantt)
+{
+    int64_t *c_prev = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *c_cur = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    orc_pair *pairs = (orc_pair *)malloc((size_t)n * sizeof(orc_pair));
+    int64_t rec = 0;
+    for (int32_t s = 0; s < S; ++s) {
+        if (s == 0) {
+            for (int32_t k = 0; k < n; ++k) order[k] = perm[k];
+        } else {
+            for (int32_t j = 0; j < n; ++j) { pairs[j].c = c_prev[j]; pairs[j].j = j; }
+            qsort(pairs, (size_t)n, sizeof(orc_pair), orc_pair_cmp);
+            for (int32_t k = 0; k < n; ++k) order[k] = pairs[k].j;
+        }
+        int32_t ms = M[s];
+        int64_t *free_at = (int64_t *)calloc((size_t)ms, sizeof(int64_t));
+        for (int32_t k = 0; k < n; ++k) {
+            int32_t j = order[k];
+            int32_t best = 0;
+            for (int32_t m = 1; m < ms; ++m)
+                if (free_at[m] < free_at[best]) best = m;
+            int64_t ready = (s == 0) ? 0 : c_prev[j];
+            int64_t start = free_at[best] > ready ? free_at[best] : ready;
+            int64_t end = start + (int64_t)p[(int64_t)j * S + s];
+            c_cur[j] = end;
+            free_at[best] = end;
+            if (gantt) {
+                gantt[rec * 5 + 0] = s;
+                gantt[rec * 5 + 1] = j;
+                gantt[rec * 5 + 2] = best;
+                gantt[rec * 5 + 3] = start;
+                gantt[rec * 5 + 4] = end;
+                ++rec;
+            }
+        }
+        free(free_at);
+        int64_t *t = c_prev; c_prev = c_cur; c_cur = t;
+    }
+    int64_t cmax = 0;
+    for (int32_t j = 0; j < n; ++j) if (c_prev[j] > cmax) cmax = c_prev[j];
+    free(c_prev); free(c_cur); free(order); free(pairs);
+    return cmax;
+}
+
+/* Makespan of every row of a population [N][ld] (int16 genes). */
+void orc_eval_population(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                         const int16_t *pop, int64_t N, int64_t ld, int64_t *out)
+{
+    for (int64_t i = 0; i < N; ++i)
+        out[i] = orc_decode(n, S, M, p, pop + i * ld, NULL);
+}
+
+/* Brute force over all n! orders (n <= 10): returns the minimum makespan and
+ * writes the maximum to *worst.  Uses the lexicographic next-permutation walk. */
+int64_t orc_bruteforce(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                       int64_t *worst, int16_t *best_perm)
+{
+    int16_t perm[16];
+    for (int32_t i = 0; i < n; ++i) perm[i] = (int16_t)i;
+    int64_t best = -1, wst = -1;
+    for (;;) {
+        int64_t c = orc_decode(n, S, M, p, perm, NULL);
+        if (best < 0 || c < best) {
+            best = c;
+            if (best_perm) memcpy(best_perm, perm, (size_t)n * sizeof(int16_t));
+        }
+        if (c > wst) wst = c;
+        int32_t i = n - 2;
+        while (i >= 0 && perm[i] >= perm[i + 1]) --i;
+        if (i < 0) break;
+        int32_t k = n - 1;
+        while (perm[k] <= perm[i]) --k;
+        int16_t t = perm[i]; perm[i] = perm[k]; perm[k] = t;
+        for (int32_t a = i + 1, b = n - 1; a < b; ++a, --b) {
+            t = perm[a]; perm[a] = perm[b]; perm[b] = t;
+        }
+    }
+    if (worst) *worst = wst;
+    return best;
+}
+
+/* ------------------------------------------------------------------ */
+/* Genetic operators                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Random initial chromosome (Section 4.1, "random initialization"): the
+ * Fisher-Yates shuffle of the identity, i = n-1 down to 1, swapping a[i] with
+ * a[uniform(i+1)], where the swap at position i uses draw number n-1-i. */
+void orc_init_chromosome(uint64_t seed, uint32_t island, uint32_t cell, int32_t n,
+                         int16_t *out)
+{
+    for (int32_t i = 0; i < n; ++i) out[i] = (int16_t)i;
+    for (int32_t i = n - 1; i >= 1; --i) {
+        uint32_t x = orc_draw(seed, ORC_PURPOSE_INIT, island, 0u, cell, (uint32_t)(n - 1 - i));
+        int32_t j = (int32_t)orc_uniform(x, (uint32_t)(i + 1));
+        int16_t t = out[i]; out[i] = out[j]; out[j] = t;
+    }
+}
+
+/* Order crossover (Davis's OX): the child keeps p1's genes at positions
+ * l..r (inclusive); the remaining positions, visited from r+1 onward and
+ * wrapping to 0, receive the genes of p2 in the order met when scanning p2
+ * from position r+1 onward (wrapping), skipping genes already in the child. */
+void orc_order_crossover(int32_t n, const int16_t *p1, const int16_t *p2,
+                         int32_t l, int32_t r, int16_t *child)
+{
+    unsigned char *taken = (unsigned char *)calloc((size_t)n, 1);
+    for (int32_t k = l; k <= r; ++k) {
+        child[k] = p1[k];
+        taken[p1[k]] = 1;
+    }
+    int32_t pos = (r + 1) % n;
+    for (int32_t t = 0; t < n; ++t) {
+        int16_t g = p2[(r + 1 + t) % n];
+        if (taken[g]) continue;
+        child[pos] = g;
+        taken[g] = 1;
+        pos = (pos + 1) % n;
+    }
+    free(taken);
+}
+
+/* The five cells of the von Neumann neighbourhood of cell c on an R x Q torus:
+ * slot 0 = the cell itself, 1 = north (row - 1), 2 = south (row + 1),
+ * 3 = west (column - 1), 4 = east (column + 1), rows and columns mod R, Q. */
+void orc_neighbours(int32_t rows, int32_t cols, int32_t c, int32_t out[5])
+{
+    int32_t r = c / cols, q = c % cols;
+    out[0] = c;
+    out[1] = ((r - 1 + rows) % rows) * cols + q;
+    out[2] = ((r + 1) % rows) * cols + q;
+    out[3] = r * cols + (q - 1 + cols) % cols;
+    out[4] = r * cols + (q + 1) % cols;
+}
+
+/* GA parameters as plain numbers (the oracle's own representation). */
+typedef struct {
+    uint64_t seed;
+    uint64_t cell_pc;      /* crossover threshold, Bernoulli fires iff x < pc */
+    uint64_t cell_pm;      /* mutation threshold (one swap per child) */
+    uint64_t pseudo_pc;    /* pseudo crossover threshold */
+    int32_t cell_replace_le;   /* 0: replace iff child < cell; 1: iff child <= cell */
+    int32_t pseudo_always;     /* 0: pair keeps the 2 best of {c1,c2,a,b}; 1: children replace parents */
+} orc_params;
+
+/* One child of the cellular island for cell c (Section 4.2), given its ten
+ * draws x[0..9]: two binary tournaments over the five neighbourhood slots
+ * (draws 0,1 and 2,3; the lower makespan wins, the first-drawn on ties),
+ * crossover with probability pc (draw 4; cut points from draws 5 and 6,
+ * l = min, r = max), otherwise the child is a copy of the first parent;
+ * then with probability pm (draw 7) one swap of the positions given by draws
+ * 8 and 9.  The parents' makespans are those of the previous generation. */
+void orc_cellular_child(int32_t n, int32_t rows, int32_t cols, int32_t c,
+                        const uint32_t x[10], const orc_params *prm,
+                        const int16_t *pop, int64_t ld, const int64_t *ms,
+                        int16_t *child, int32_t *parents_out)
+{
+    int32_t nb[5];
+    orc_neighbours(rows, cols, c, nb);
+    int32_t a1 = nb[orc_uniform(x[0], 5u)], b1 = nb[orc_uniform(x[1], 5u)];
+    int32_t par1 = (ms[b1] < ms[a1]) ? b1 : a1;
+    int32_t a2 = nb[orc_uniform(x[2], 5u)], b2 = nb[orc_uniform(x[3], 5u)];
+    int32_t par2 = (ms[b2] < ms[a2]) ? b2 : a2;
+    if (parents_out) { parents_out[0] = par1; parents_out[1] = par2; }
+    if (orc_bernoulli(x[4], prm->cell_pc)) {
+        int32_t u = (int32_t)orc_uniform(x[5], (uint32_t)n);
+        int32_t v = (int32_t)orc_uniform(x[6], (uint32_t)n);
+        int32_t l = u < v ? u : v, r = u < v ? v : u;
+        orc_order_crossover(n, pop + (int64_t)par1 * ld, pop + (int64_t)par2 * ld, l, r, child);
+    } else {
+        memcpy(child, pop + (int64_t)par1 * ld, (size_t)n * sizeof(int16_t));
+    }
+    if (orc_bernoulli(x[7], prm->cell_pm)) {
+        int32_t i = (int32_t)orc_uniform(x[8], (uint32_t)n);
+        int32_t j = (int32_t)orc_uniform(x[9], (uint32_t)n);
+        int16_t t = child[i]; child[i] = child[j]; child[j] = t;
+    }
+}
+
+/* One synchronous generation of a cellular island (Section 4.1-4.2): every
+ * cell reads the previous generation (pop_in, ms_in) and writes the next
+ * (pop_out, ms_out); the child replaces the cell iff its makespan is lower
+ * (or not higher, with cell_replace_le).  Returns the number of children
+ * decoded. */
+int64_t orc_cellular_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                                const orc_params *prm, uint32_t island, uint32_t generation,
+                                int32_t rows, int32_t cols, int64_t ld,
+                                const int16_t *pop_in, const int64_t *ms_in,
+                                int16_t *pop_out, int64_t *ms_out)
+{
+    int32_t cells = rows * cols;
+    int16_t *child = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    for (int32_t c = 0; c < cells; ++c) {
+        uint32_t x[10];
+        for (uint32_t d = 0; d < 10u; ++d)
+            x[d] = orc_draw(prm->seed, ORC_PURPOSE_CELLULAR, island, generation, (uint32_t)c, d);
+        orc_cellular_child(n, rows, cols, c, x, prm, pop_in, ld, ms_in, child, NULL);
+        int64_t mc = orc_decode(n, S, M, p, child, NULL);
+        int better = prm->cell_replace_le ? (mc <= ms_in[c]) : (mc < ms_in[c]);
+        int16_t *dst = pop_out + (int64_t)c * ld;
+        if (better) {
+            memcpy(dst, child, (size_t)n * sizeof(int16_t));
+            ms_out[c] = mc;
+        } else {
+            memcpy(dst, pop_in + (int64_t)c * ld, (size_t)n * sizeof(int16_t));
+            ms_out[c] = ms_in[c];
+        }
+    }
+    free(child);
+    return cells;
+}
+
+/* Complementary parents of the pseudo island (Section 4.1): a pair is a
+ * random chromosome a and its complement, read for a job-order chromosome as
+ * the reversed order b[i] = a[n-1-i].  Pair k occupies slots 2k and 2k+1 and
+ * a is drawn with cell index 2k. */
+void orc_init_pseudo_pair(uint64_t seed, uint32_t island, int32_t k, int32_t n,
+                          int16_t *a, int16_t *b)
+{
+    orc_init_chromosome(seed, island, (uint32_t)(2 * k), n, a);
+    for (int32_t i = 0; i < n; ++i) b[i] = a[n - 1 - i];
+}
+
+/* The two best members of a pseudo family given in role order
+ * (c1, c2, a, b): ranked by (makespan, role), lowest first. */
+void orc_family_best2(const int64_t fms[4], int32_t out[2])
+{
+    int32_t first = 0;
+    for (int32_t t = 1; t < 4; ++t) if (fms[t] < fms[first]) first = t;
+    int32_t second = -1;
+    for (int32_t t = 0; t < 4; ++t) {
+        if (t == first) continue;
+        if (second < 0 || fms[t] < fms[second]) second = t;
+    }
+    out[0] = first;
+    out[1] = second;
+}
+
+/* One generation of a pseudo island (Section 4.1-4.2): pair k (slots 2k,
+ * 2k+1) crosses with probability pc (draw 0; cuts from draws 1 and 2):
+ * c1 = OX(a, b), c2 = OX(b, a) on the same cuts.  With pseudo_always the
+ * children replace the parents; otherwise the pair keeps the two best of
+ * (c1, c2, a, b) ranked by (makespan, that role order), best in slot 2k.
+ * Without crossover the pair is copied unchanged.  Returns the number of
+ * children decoded. */
+int64_t orc_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                              const orc_params *prm, uint32_t island, uint32_t generation,
+                              int32_t size, int64_t ld,
+                              const int16_t *pop_in, const int64_t *ms_in,
+                              int16_t *pop_out, int64_t *ms_out)
+{
+    int16_t *c1 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int16_t *c2 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int64_t decoded = 0;
+    for (int32_t k = 0; k < size / 2; ++k) {
+        const int16_t *a = pop_in + (int64_t)(2 * k) * ld;
+        const int16_t *b = pop_in + (int64_t)(2 * k + 1) * ld;
+        int16_t *oa = pop_out + (int64_t)(2 * k) * ld;
+        int16_t *ob = pop_out + (int64_t)(2 * k + 1) * ld;
+        uint32_t x0 = orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation, (uint32_t)k, 0u);
+        if (!orc_bernoulli(x0, prm->pseudo_pc)) {
+            memcpy(oa, a, (size_t)n * sizeof(int16_t));
+            memcpy(ob, b, (size_t)n * sizeof(int16_t));
+            ms_out[2 * k] = ms_in[2 * k];
+            ms_out[2 * k + 1] = ms_in[2 * k + 1];
+            continue;
+        }
+        uint32_t x1 = orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation, (uint32_t)k, 1u);
+        uint32_t x2 = orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation, (uint32_t)k, 2u);
+        int32_t u = (int32_t)orc_uniform(x1, (uint32_t)n);
+        int32_t v = (int32_t)orc_uniform(x2, (uint32_t)n);
+        int32_t l = u < v ? u : v, r = u < v ? v : u;
+        orc_order_crossover(n, a, b, l, r, c1);
+        orc_order_crossover(n, b, a, l, r, c2);
+        int64_t m1 = orc_decode(n, S, M, p, c1, NULL);
+        int64_t m2 = orc_decode(n, S, M, p, c2, NULL);
+        decoded += 2;
+        if (prm->pseudo_always) {
+            memcpy(oa, c1, (size_t)n * sizeof(int16_t));
+            memcpy(ob, c2, (size_t)n * sizeof(int16_t));
+            ms_out[2 * k] = m1;
+            ms_out[2 * k + 1] = m2;
+            continue;
+        }
+        /* the family in role order c1, c2, a, b */
+        const int16_t *fam[4] = { c1, c2, a, b };
+        int64_t fms[4] = { m1, m2, ms_in[2 * k], ms_in[2 * k + 1] };
+        int32_t pick[2];
+        orc_family_best2(fms, pick);
+        int32_t first = pick[0], second = pick[1];
+        /* pop_in and pop_out are distinct buffers (synchronous generations) */
+        memcpy(oa, fam[first], (size_t)n * sizeof(int16_t));
+        memcpy(ob, fam[second], (size_t)n * sizeof(int16_t));
+        ms_out[2 * k] = fms[first];
+        ms_out[2 * k + 1] = fms[second];
+    }
+    free(c1); free(c2);
+    return decoded;
+}
+
+/* ------------------------------------------------------------------ */
+/* Migration                                                            */
+/* ------------------------------------------------------------------ */
+
+typedef struct { int64_t ms; int32_t idx; } orc_rank;
+
+static int orc_rank_cmp(const void *a, const void *b)
+{
+    const orc_rank *x = (const orc_rank *)a, *y = (const orc_rank *)b;
+    if (x->ms < y->ms) return -1;
+    if (x->ms > y->ms) return 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+/* Cell indices of an island sorted by (makespan, cell index) ascending:
+ * the reading of the paper's sort of each island before migration
+ * (Section 4.2-4.3): rank 0 is the best individual, rank N-1 the worst. */
+void orc_rank_island(int32_t N, const int64_t *ms, int32_t *order)
+{
+    orc_rank *r = (orc_rank *)malloc((size_t)N * sizeof(orc_rank));
+    for (int32_t i = 0; i < N; ++i) { r[i].ms = ms[i]; r[i].idx = i; }
+    qsort(r, (size_t)N, sizeof(orc_rank), orc_rank_cmp);
+    for (int32_t i = 0; i < N; ++i) order[i] = r[i].idx;
+    free(r);
+}
+
+/* Ring migration: island i sends copies of its best k rows to island
+ * (i+1) mod I, where the t-th best immigrant overwrites the destination's
+ * rank N-1-t row (the worst first).  k = max(1, floor(num * min(N_i, N_dst)
+ * / den)).  All ranks and rows are taken from a snapshot before any write.
+ * pops[i] is [N_i][ld], ms[i] is [N_i]. */
+void orc_migrate_ring(int32_t I, const int32_t *sizes, int64_t ld, int32_t n,
+                      int16_t **pops, int64_t **ms, int64_t num, int64_t den)
+{
+    int32_t **order = (int32_t **)malloc((size_t)I * sizeof(int32_t *));
+    int16_t **snap = (int16_t **)malloc((size_t)I * sizeof(int16_t *));
+    int64_t **snap_ms = (int64_t **)malloc((size_t)I * sizeof(int64_t *));
+    int32_t *kk = (int32_t *)malloc((size_t)I * sizeof(int32_t));
+    for (int32_t i = 0; i < I; ++i) {
+        order[i] = (int32_t *)malloc((size_t)sizes[i] * sizeof(int32_t));
+        orc_rank_island(sizes[i], ms[i], order[i]);
+    }
+    for (int32_t i = 0; i < I; ++i) {
+        int32_t dst = (i + 1) % I;
+        int32_t nmin = sizes[i] < sizes[dst] ? sizes[i] : sizes[dst];
+        int64_t k = (num * (int64_t)nmin) / den;
+        if (k < 1) k = 1;
+        kk[i] = (int32_t)k;
+        snap[i] = (int16_t *)malloc((size_t)k * (size_t)n * sizeof(int16_t));
+        snap_ms[i] = (int64_t *)malloc((size_t)k * sizeof(int64_t));
+        for (int32_t t = 0; t < k; ++t) {
+            int32_t src = order[i][t];
+            memcpy(snap[i] + (int64_t)t * n, pops[i] + (int64_t)src * ld, (size_t)n * sizeof(int16_t));
+            snap_ms[i][t] = ms[i][src];
+        }
+    }
+    for (int32_t i = 0; i < I; ++i) {
+        int32_t dst = (i + 1) % I;
+        for (int32_t t = 0; t < kk[i]; ++t) {
+            int32_t cell = order[dst][sizes[dst] - 1 - t];
+            memcpy(pops[dst] + (int64_t)cell * ld, snap[i] + (int64_t)t * n, (size_t)n * sizeof(int16_t));
+            ms[dst][cell] = snap_ms[i][t];
+        }
+    }
+    for (int32_t i = 0; i < I; ++i) { free(order[i]); free(snap[i]); free(snap_ms[i]); }
+    free(order); free(snap); free(snap_ms); free(kk);
+}
+
+/* Penetration migration between two islands A and B (Section 4.3,
+ * Eq. (1)-(2)), read for makespans (lower is better): with best makespans
+ * cA, cB, nothing moves if cA == cB.  Otherwise lo = min, hi = max,
+ * beta = lo / hi and the move happens iff 1 - beta < theta, i.e.
+ * (hi - lo) * theta_den < theta_num * hi; then alpha = 1 - beta and
+ * floor(alpha * N) = floor((hi - lo) * N / hi) of the best rows of the
+ * lower-makespan island overwrite as many of the worst rows of the other
+ * (t-th best onto rank N-1-t), N = min(N_A, N_B).
+ * Returns the signed count: > 0 for A -> B, < 0 for B -> A, 0 for none. */
+int64_t orc_penetration_count(int64_t cA, int64_t cB, int32_t N,
+                              int64_t theta_num, int64_t theta_den)
+{
+    if (cA == cB) return 0;
+    int64_t lo = cA < cB ? cA : cB, hi = cA < cB ? cB : cA;
+    if (!((hi - lo) * theta_den < theta_num * hi)) return 0;
+    int64_t count = ((hi - lo) * (int64_t)N) / hi;
+    return cA < cB ? count : -count;
+}
+
+int64_t orc_migrate_penetration(int32_t NA, int32_t NB, int64_t ld, int32_t n,
+                                int16_t *popA, int64_t *msA, int16_t *popB, int64_t *msB,
+                                int64_t theta_num, int64_t theta_den)
+{
+    int32_t *oa = (int32_t *)malloc((size_t)NA * sizeof(int32_t));
+    int32_t *ob = (int32_t *)malloc((size_t)NB * sizeof(int32_t));
+    orc_rank_island(NA, msA, oa);
+    orc_rank_island(NB, msB, ob);
+    int32_t N = NA < NB ? NA : NB;
+    int64_t cnt = orc_penetration_count(msA[oa[0]], msB[ob[0]], N, theta_num, theta_den);
+    int64_t k = cnt < 0 ? -cnt : cnt;
+    int16_t *spop = cnt > 0 ? popA : popB;
+    int64_t *sms = cnt > 0 ? msA : msB;
+    int32_t *sord = cnt > 0 ? oa : ob;
+    int16_t *dpop = cnt > 0 ? popB : popA;
+    int64_t *dms = cnt > 0 ? msB : msA;
+    int32_t *dord = cnt > 0 ? ob : oa;
+    int32_t dN = cnt > 0 ? NB : NA;
+    for (int64_t t = 0; t < k; ++t) {
+        int32_t src = sord[t], dst = dord[dN - 1 - t];
+        memcpy(dpop + (int64_t)dst * ld, spop + (int64_t)src * ld, (size_t)n * sizeof(int16_t));
+        dms[dst] = sms[src];
+    }
+    free(oa); free(ob);
+    return cnt;
+}
