@@ -1,0 +1,359 @@
+"""Benchmark: exact FFS makespan evaluations per second of the dual-island GA
+on one GB300 (one JSON line on stdout).
+
+Workload (default ``scale_500x20``): 500 jobs x 20 stages, machines per stage
+uniform in [5, 10], processing times uniform in [1, 99] (instance seed 1);
+4 cellular islands on 128 x 128 tori + 4 pseudo islands of 16384 rows
+(131072 chromosomes of 500 int16 genes), GA seed 7.  A step is one
+generation of every island (fused cellular kernels, pseudo breed / decode /
+replace) followed by a ring migration of 2% (ranking + row copies), replayed
+from the library's CUDA graph.  ``value`` = exact makespan evaluations
+(children decoded) per second, counted by the library.
+
+Other keys: ``roofline`` for the dominant kernel (the fused cellular
+generation, integer-ALU bound; algorithmic ops per launch / its CUDA-event
+duration vs. SMs x 128 lanes x max SM clock), ``e2e`` (the same step with the
+populations uploaded from and downloaded to pinned host memory every step),
+``cpu_baseline`` (the CPU oracle on a bounded sample), ``clocks`` (nvidia-smi
+sampled during the timed region).
+
+``--impl reference`` times the CPU oracle on this workload instead.  N > 1
+(torchrun) runs independent replicas, one per GPU (the islands of one run
+are not sharded across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_SM_MHZ = 2070.0
+LANES_PER_SM = 128
+
+
+def ops_per_eval(n: int, M) -> int:
+    """Algorithmic integer ops of one decode: per stage n * ((M_s - 1) + 3)
+    (argmin compares, max, add, store) plus n * ceil(log2 M_{s-1}) for the
+    merge into stage s >= 2's order."""
+    import math
+    Me = [min(int(m), n) for m in M]
+    ops = sum(n * ((m - 1) + 3) for m in Me)
+    ops += sum(n * math.ceil(math.log2(Me[s - 1])) if Me[s - 1] > 1 else 0 for s in range(1, len(Me)))
+    return ops
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def _peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {}, "fallback"
+
+
+def cpu_oracle_rate(workload: str, budget_s: float = 12.0):
+    """Single-thread CPU oracle: cellular generations on a 16 x 16 torus of the
+    same instance until ~budget_s; returns (evals/s, sample description)."""
+    import numpy as np
+
+    import oracle as orc
+    from ffs_workloads import WORKLOADS, workload_instance
+    w = WORKLOADS[workload]
+    spec = workload_instance(workload)
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    prm = orc.Params(seed=7)
+    rows = cols = 16
+    ld = (spec.n + 7) // 8 * 8
+    pop = np.zeros((rows * cols, ld), dtype=np.int16)
+    for c in range(rows * cols):
+        pop[c, :spec.n] = orc.init_chromosome(7, 0, c, spec.n)
+    ms = orc.eval_population(o, pop)
+    t0 = time.perf_counter()
+    evals = gens = 0
+    while time.perf_counter() - t0 < budget_s:
+        gens += 1
+        pop, ms, d = orc.cellular_generation(o, prm, 0, gens, rows, cols, pop, ms)
+        evals += d
+    dt = time.perf_counter() - t0
+    sample = (f"{gens} cellular generations of a 16x16 torus ({evals} exact decodes) on the "
+              f"{spec.n}x{spec.S} instance, single thread, {dt:.1f} s")
+    del w
+    return evals / dt, sample
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from ffs_workloads import WORKLOADS
+    per_step = []
+    total_evals = 0
+    budget = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        rate, sample = cpu_oracle_rate(args.workload, budget_s=budget)
+        if i >= args.warmup:
+            per_step.append(rate)
+    value = statistics.mean(per_step)
+    line = {
+        "impl": "reference", "metric": "exact FFS makespan evals/sec", "value": value, "unit": "evals/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": budget * 1000.0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": _config(args.workload, ws),
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    del WORKLOADS
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(workload: str, ws: int) -> dict:
+    from ffs_workloads import WORKLOADS
+    w = WORKLOADS[workload]
+    cfg = {"workload": workload, "n_jobs": w["n"], "n_stages": w["S"], "machines_per_stage": list(w["m"]),
+           "cellular_islands": w["n_cellular"], "torus": [w["rows"], w["cols"]],
+           "pseudo_islands": w["n_pseudo"], "pseudo_size": w["pseudo_size"],
+           "chromosomes": w["n_cellular"] * w["rows"] * w["cols"] + w["n_pseudo"] * w["pseudo_size"],
+           "migration": f"{w.get('migration', 'none')} {w.get('mig_num', 0)}/{w.get('mig_den', 1)} every "
+                        f"{w.get('gap', 0)} generation(s)",
+           "ga_seed": 7, "instance_seed": w["seed"], "parallelism": f"replicas x{ws}",
+           "l2": "inputs larger than L2 (populations 2 x 131072 x 504 x 2 B = 264 MB)"}
+    return cfg
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    from ffs_workloads import WORKLOADS, workload_instance
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+    ffs.load()
+    w = WORKLOADS[args.workload]
+    spec = workload_instance(args.workload)
+    inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p)
+    prm = ffs.ffs_params_default()
+    prm.seed = 7
+    prm.migration_mode = ffs.FFS_MIG_RING if w.get("migration", "ring") == "ring" else ffs.FFS_MIG_PENETRATION
+    prm.migration_gap = int(w.get("gap", 1))
+    prm.ring_num, prm.ring_den = w.get("mig_num", 2), w.get("mig_den", 100)
+    stream = torch.cuda.current_stream()
+    isl = ffs.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
+    torch.cuda.synchronize()
+
+    # ---- warm-up (also builds the CUDA graph) ----
+    ffs.ffs_island_step(isl, -1, args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K generations replayed from the graph ----
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    d0 = ffs.ffs_islands_decoded(isl)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ffs.ffs_island_step(isl, -1, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+
+    # ---- dominant kernel: the fused cellular generation, timed alone on the same stream ----
+    cells = w["rows"] * w["cols"]
+    ld = isl.ld
+    pin = torch.empty((cells, ld), dtype=torch.int16, device="cuda")
+    pout = torch.empty_like(pin)
+    msin = torch.empty(cells, dtype=torch.int32, device="cuda")
+    msout = torch.empty_like(msin)
+    ffs.ffs_islands_get(isl, 0, pin, ld, msin)
+    kernel_ms = []
+    for r in range(max(3, min(args.steps, 6))):
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        ffs.ffs_cellular_step(inst, prm, 0, 10_000 + r, w["rows"], w["cols"], ld, pin, msin, pout, msout)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        kernel_ms.append(k0.elapsed_time(k1))
+    clock_info = clocks.stop()
+    d1 = ffs.ffs_islands_decoded(isl)
+    evals = d1 - d0
+
+    # ---- e2e: the same steps with populations from / to pinned host memory ----
+    host_pops = [torch.empty((n_i, spec.n), dtype=torch.int16).pin_memory() for n_i in isl.sizes]
+    host_ms = [torch.empty(n_i, dtype=torch.int32).pin_memory() for n_i in isl.sizes]
+    for i in range(isl.n_islands):
+        ffs.ffs_islands_get(isl, i, host_pops[i], spec.n, host_ms[i])
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = sum(p.numel() * 2 for p in host_pops)
+    d2h = h2d + sum(m.numel() * 4 for m in host_ms)
+    e_d0 = ffs.ffs_islands_decoded(isl)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i in range(isl.n_islands):
+            ffs.ffs_islands_set(isl, i, host_pops[i], spec.n, None)
+        ffs.ffs_island_step(isl, -1, 1)
+        for i in range(isl.n_islands):
+            ffs.ffs_islands_get(isl, i, host_pops[i], spec.n, host_ms[i])
+        torch.cuda.synchronize()
+    e2e_time = time.perf_counter() - t0
+    e2e_evals = ffs.ffs_islands_decoded(isl) - e_d0
+
+    # ---- reduce over ranks (max time) ----
+    value_time = elapsed
+    if dist:
+        t = torch.tensor([elapsed, e2e_time], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value_time, e2e_time = float(t[0]), float(t[1])
+    total_evals = evals * ws
+    value = total_evals / value_time
+
+    peaks, peak_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MHZ))
+    num_sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
+    ops_eval = ops_per_eval(spec.n, spec.M)
+    kern_s = statistics.mean(kernel_ms) / 1000.0
+    achieved = cells * ops_eval / kern_s
+
+    line = {
+        "metric": "exact FFS makespan evals/sec", "value": value, "unit": "evals/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value_time / args.steps * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded instance and Philox GA)",
+        "config": _config(args.workload, ws),
+        "e2e": {"value": e2e_evals * ws / e2e_time, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * launches_per_generation(w),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "k_cellular (fused tournament + OX + swap + decode + replace)",
+                     "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": cells * ops_eval,
+                     "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"},
+        "clocks": clock_info,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, sample = cpu_oracle_rate(args.workload)
+        line["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    isl.close()
+    inst.close()
+    return 0
+
+
+def launches_per_generation(w) -> int:
+    """Kernels of one generation: one fused kernel per cellular island, three
+    per pseudo island (breed, decode, replace), one advance, and when
+    migrating the ranking plus the copy kernel."""
+    n = w["n_cellular"] + 3 * w["n_pseudo"] + 1
+    if w.get("gap", 0) == 1 and w["n_cellular"] + w["n_pseudo"] > 1:
+        n += 2
+    return n
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="scale_500x20")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

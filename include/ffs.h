@@ -1,0 +1,244 @@
+/*
+ * ffs.h -- C ABI of the GB300 library for the flexible flow shop (FFS) dual
+ * island genetic algorithm of Luo & El Baz, "A Dual Heterogeneous Island
+ * Genetic Algorithm for Solving Large Size Flexible Flow Shop Scheduling
+ * Problems on Hybrid multi-core CPU and GPU Platforms" (arXiv:1903.10722).
+ *
+ * Every step of the hot path runs in this library's own CUDA kernels for
+ * sm_103a.  Conventions shared by all calls:
+ *   - Every call returns an ffs_status; FFS_OK is 0.  No call exits, aborts
+ *     or traps; on failure ffs_last_error() (per host thread) says why.
+ *   - Handles (ffs_instance, ffs_islands) are opaque, owned by the library
+ *     and released by their *_destroy call.
+ *   - Host arrays given to *_create calls are copied; the caller keeps them.
+ *   - "device" pointers must be CUDA device (or managed) memory of the
+ *     current device; the call only enqueues work on `stream` and returns
+ *     without waiting (stream-ordered, asynchronous) unless it says it
+ *     synchronises.  `stream` is a cudaStream_t (NULL = legacy default).
+ *   - Chromosomes are job orders: a row of n int16 genes, a permutation of
+ *     0..n-1, rows `ld` genes apart (ld >= n, ld a multiple of 8, row base
+ *     16-byte aligned).
+ *   - Makespans are int32.  A row holding a gene outside [0, n) gets
+ *     makespan -1 (it is not decoded).
+ */
+#ifndef FFS_H
+#define FFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FFS_OK = 0,
+    FFS_EINVAL = 1,        /* invalid argument (sizes, NULL, alignment, ranges) */
+    FFS_ENOMEM = 2,        /* device or host allocation failed */
+    FFS_ECUDA = 3,         /* a CUDA runtime call failed */
+    FFS_EOVERFLOW = 4,     /* the instance's times do not fit the 32-bit keys */
+    FFS_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    FFS_EDEVICE = 6,       /* a kernel reported an error word */
+    FFS_EUNSUPPORTED = 7   /* valid input beyond this build's limits */
+} ffs_status;
+
+typedef struct ffs_instance ffs_instance;
+typedef struct ffs_islands ffs_islands;
+typedef void *ffs_stream;   /* cudaStream_t */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *ffs_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Problem instance (Section 3): n jobs each pass stages 0..S-1 in order;
+ * stage s has M_s identical parallel machines; job j takes proc_time[j][s]
+ * time units at stage s on whichever machine it is given; no preemption.
+ *
+ * machines_per_stage: host int32[S], each >= 1.
+ * proc_time: host int32[n][S] row-major (job-major), each >= 1.
+ * Limits: 1 <= n <= 32767 (int16 genes), 1 <= S <= 64, min(M_s, n) <= 32,
+ * and sum of all proc_time below 2^(30 - ceil(log2(n + 1))) (the decoder's
+ * 32-bit (time, job) keys); otherwise FFS_EINVAL / FFS_EUNSUPPORTED /
+ * FFS_EOVERFLOW.  Copies the tables to the current device.  Synchronous.
+ * ---------------------------------------------------------------------- */
+int ffs_instance_create(int32_t n_jobs, int32_t n_stages, const int32_t *machines_per_stage,
+                        const int32_t *proc_time, ffs_instance **out);
+int ffs_instance_destroy(ffs_instance *inst);
+
+/* ------------------------------------------------------------------------
+ * Batched makespan evaluation (the decoder).  Each row is decoded by
+ * stage-wise list scheduling: stage 0 takes the jobs in row order; every
+ * later stage takes them in ascending (completion time at the previous
+ * stage, job index) order; each job goes to the machine that is free
+ * earliest (lowest index on ties) and starts at max(machine free time, its
+ * completion at the previous stage).  makespan[i] = the last completion at
+ * the last stage.  (Section 3 states the problem; the paper names only the
+ * objective, this decoding rule is the library's reading.)
+ *
+ * pop: device int16[N][ld]; makespan: device int32[N].  N >= 0 (N = 0 is a
+ * no-op).  Asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+int ffs_population_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
+                        int32_t *makespan, ffs_stream stream);
+
+/* Same, with an explicit launch shape: decode_chunk = jobs per round
+ * (multiple of 8; >= n means one round per stage) and block_threads
+ * (multiple of 32, <= 512); 0 lets the library choose.  Results do not
+ * depend on the shape. */
+int ffs_population_eval_tuned(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
+                              int32_t *makespan, int32_t decode_chunk, int32_t block_threads,
+                              ffs_stream stream);
+
+/* Same, with host (pageable or pinned) pop and makespan: copies pop in,
+ * decodes and copies the makespans out on `stream`, then synchronises the
+ * stream.  Uses a library-owned device buffer grown on demand. */
+int ffs_population_eval_host(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
+                             int32_t *makespan, ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Counter-based randomness: Philox4x32-10 (Salmon et al., SC 2011).  Draw
+ * d of the stream (seed, purpose, island, generation, cell) is word d mod 4
+ * of Philox applied to the counter (d / 4, cell, generation,
+ * island | purpose << 24) under the key (low, high halves of seed).
+ * Purposes: 1 initial population, 2 cellular generation, 3 pseudo
+ * generation, 4 surrogate candidates.
+ * out: device uint32[n_cells][n_draws], row c holding cell cell0 + c.
+ * ---------------------------------------------------------------------- */
+#define FFS_PURPOSE_INIT 1
+#define FFS_PURPOSE_CELLULAR 2
+#define FFS_PURPOSE_PSEUDO 3
+#define FFS_PURPOSE_SURROGATE 4
+int ffs_philox_draws(uint64_t seed, uint32_t purpose, uint32_t island, uint32_t generation,
+                     uint32_t cell0, int32_t n_cells, int32_t n_draws, uint32_t *out,
+                     ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * GA parameters.  Probabilities are thresholds t in [0, 2^32]: an event
+ * fires iff its draw x < t (t = floor(p * 2^32)).  Defaults (Section 5):
+ * cellular crossover 1.00 and mutation 0.05, pseudo crossover 0.75,
+ * penetration threshold theta = 1, ring migration of 2% every 50
+ * generations.
+ * ---------------------------------------------------------------------- */
+#define FFS_MIG_NONE 0
+#define FFS_MIG_RING 1
+#define FFS_MIG_PENETRATION 2
+
+typedef struct {
+    uint64_t seed;            /* Philox key */
+    uint64_t cell_pc;         /* cellular crossover threshold */
+    uint64_t cell_pm;         /* cellular mutation threshold (one swap per child) */
+    uint64_t pseudo_pc;       /* pseudo crossover threshold */
+    int32_t cell_replace_le;  /* 0: child replaces cell iff strictly better; 1: iff not worse */
+    int32_t pseudo_always;    /* 0: pair keeps the 2 best of {c1, c2, a, b}; 1: children replace parents */
+    int32_t migration_mode;   /* FFS_MIG_* used by ffs_island_step every migration_gap generations */
+    int32_t migration_gap;    /* 0 = never inside ffs_island_step */
+    int64_t ring_num, ring_den;    /* ring: k = max(1, floor(ring_num * N / ring_den)), k <= N/2 */
+    int64_t theta_num, theta_den;  /* penetration threshold theta = num / den, in [0, 1] */
+    int32_t decode_chunk;     /* decoder chunk (jobs per round, multiple of 8); 0 = library choice */
+    int32_t block_threads;    /* threads per block for the decoder; 0 = library choice */
+} ffs_params;
+
+/* Fill *p with the defaults above (seed 7). */
+void ffs_params_default(ffs_params *p);
+
+/* ------------------------------------------------------------------------
+ * Stateless generation steps on caller buffers (all device pointers).
+ *
+ * ffs_population_init: random initial rows (Section 4.1).  kind 0
+ * (cellular): row c is the Fisher-Yates shuffle of the identity using
+ * draws (seed, purpose 1, island, generation 0, cell c): for i = n-1 .. 1
+ * swap genes i and uniform(i+1) with draw n-1-i, where uniform(k) of draw
+ * x = (x * k) >> 32.  kind 1 (pseudo, N even): rows 2k, 2k+1 are a and its
+ * complement, read as the reversed order, a drawn with cell 2k.  Padding
+ * genes n..ld-1 are set to 0.  Makespans are not computed.
+ *
+ * ffs_cellular_step: one synchronous generation of a cellular island on an
+ * rows x cols torus (Sections 4.1-4.2): every cell draws ten numbers
+ * (purpose 2): two binary tournaments over its von Neumann neighbourhood
+ * [itself, north, south, west, east] (draws 0-1 and 2-3; lower makespan
+ * wins, the first drawn on ties), order crossover of the two winners with
+ * probability cell_pc (draw 4, cut points from draws 5-6) or else a copy of
+ * the first winner, one swap mutation with probability cell_pm (draw 7,
+ * positions from draws 8-9), decoding, and replacement of the cell iff the
+ * child is better.  Reads pop_in/ms_in, writes pop_out/ms_out (distinct
+ * buffers of rows*cols rows).
+ *
+ * ffs_pseudo_step: one generation of a pseudo island of `size` rows (even)
+ * (Sections 4.1-4.2): pair k = rows (2k, 2k+1) crosses with probability
+ * pseudo_pc (draw 0, purpose 3; cut points from draws 1-2): c1 = OX(a, b),
+ * c2 = OX(b, a); the pair keeps the two best of (c1, c2, a, b) ranked by
+ * (makespan, that order), best first, or with pseudo_always the children.
+ * Pairs that do not cross are copied.  scratch: device memory of
+ * ffs_pseudo_scratch_bytes(size, ld) bytes, 256-byte aligned, owned by the
+ * caller; its contents on entry do not matter.
+ * ---------------------------------------------------------------------- */
+int ffs_population_init(const ffs_instance *inst, uint64_t seed, uint32_t island, int32_t kind,
+                        int64_t N, int32_t ld, int16_t *pop, ffs_stream stream);
+int ffs_cellular_step(const ffs_instance *inst, const ffs_params *prm, uint32_t island,
+                      uint32_t generation, int32_t rows, int32_t cols, int32_t ld,
+                      const int16_t *pop_in, const int32_t *ms_in, int16_t *pop_out,
+                      int32_t *ms_out, ffs_stream stream);
+int64_t ffs_pseudo_scratch_bytes(int32_t size, int32_t ld);
+int ffs_pseudo_step(const ffs_instance *inst, const ffs_params *prm, uint32_t island,
+                    uint32_t generation, int32_t size, int32_t ld, const int16_t *pop_in,
+                    const int32_t *ms_in, int16_t *pop_out, int32_t *ms_out, void *scratch,
+                    ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Islands: the dual-island GA state on the device (Section 4.1, Fig. 2).
+ * Islands are kept in ring order [cellular 0, pseudo 0, cellular 1,
+ * pseudo 1, ...]; island i uses Philox island id i.  Each cellular island is
+ * a rows x cols torus, each pseudo island has pseudo_size rows (even).
+ * ffs_islands_create allocates library-owned device memory, initialises
+ * every island (ffs_population_init) and decodes it; generation = 0.
+ * ---------------------------------------------------------------------- */
+int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t n_cellular,
+                       int32_t rows, int32_t cols, int32_t n_pseudo, int32_t pseudo_size,
+                       ffs_stream stream, ffs_islands **out);
+int ffs_islands_destroy(ffs_islands *isl);
+
+/* Number of islands, row stride, generation count; sizes (may be NULL)
+ * receives n_islands int32 and kinds (may be NULL) 0 = cellular, 1 = pseudo. */
+int ffs_islands_info(const ffs_islands *isl, int32_t *n_islands, int32_t *ld,
+                     int64_t *generation, int32_t *sizes, int32_t *kinds);
+
+/* Run n_generations synchronous generations of every island (island = -1)
+ * or of one island; generation numbers continue from the handle's count.
+ * After each generation g with migration_gap > 0 and g % migration_gap == 0,
+ * runs ffs_migrate(migration_mode) (only when all islands are stepped).
+ * The generation loop is replayed from a CUDA graph.  Asynchronous. */
+int ffs_island_step(ffs_islands *isl, int32_t island, int32_t n_generations, ffs_stream stream);
+
+/* Migration (Section 4.3).  Islands are ranked by (makespan, row index).
+ * FFS_MIG_RING: island i sends copies of its k best rows to island
+ * (i+1) mod I, the t-th best overwriting the destination's t-th worst,
+ * k = max(1, floor(ring_num * min(N_i, N_dst) / ring_den)), all ranks
+ * taken before any write.
+ * FFS_MIG_PENETRATION (Eq. (1)-(2), for makespans): for each pair
+ * (cellular q, pseudo q) with best makespans cA != cB, lo = min, hi = max:
+ * if (hi - lo) * theta_den < theta_num * hi, the lower island's
+ * floor((hi - lo) * N / hi) best rows overwrite the other's worst
+ * (N = min of the two sizes).  Asynchronous. */
+int ffs_migrate(ffs_islands *isl, int32_t mode, ffs_stream stream);
+
+/* Copy island `island`'s current rows (into pop, row stride ld_out >= n)
+ * and makespans out, or in (ffs_islands_set).  Pointers may be host or
+ * device memory (copies use cudaMemcpyDefault); either may be NULL to skip.
+ * Asynchronous on `stream` (pageable host memory makes the copy
+ * synchronous with respect to the host, as CUDA does). */
+int ffs_islands_get(const ffs_islands *isl, int32_t island, int16_t *pop, int32_t ld_out,
+                    int32_t *makespan, ffs_stream stream);
+int ffs_islands_set(ffs_islands *isl, int32_t island, const int16_t *pop, int32_t ld_in,
+                    const int32_t *makespan, ffs_stream stream);
+
+/* Best makespan over all islands and where it is (lowest island, then
+ * lowest row on ties).  Synchronises `stream`.  Outputs are host pointers. */
+int ffs_islands_best(const ffs_islands *isl, int32_t *best_makespan, int32_t *best_island,
+                     int32_t *best_row, ffs_stream stream);
+
+/* Number of exact decodes (children evaluated) since creation; synchronises. */
+int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFS_H */

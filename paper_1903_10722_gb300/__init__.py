@@ -1,0 +1,301 @@
+"""GB300 (sm_103a) library for the dual heterogeneous island GA on the
+flexible flow shop (Luo & El Baz, arXiv:1903.10722).
+
+This package is a thin ctypes binding over the C ABI declared in
+``include/ffs.h``; every function keeps the C name and only marshals
+arguments (tensor pointers, the current torch CUDA stream, host arrays).
+All computation happens in the CUDA kernels of ``libffs_gb300.so``.  There is
+no CPU fallback: if the library cannot be loaded, every call raises.
+
+Device memory and streams come from PyTorch: pass CUDA tensors (int16 rows
+of ``ld`` genes, int32 makespans) and calls run on the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import _build
+
+_lib = None
+
+FFS_OK, FFS_EINVAL, FFS_ENOMEM, FFS_ECUDA, FFS_EOVERFLOW, FFS_ETIMEOUT, FFS_EDEVICE, FFS_EUNSUPPORTED = range(8)
+FFS_PURPOSE_INIT, FFS_PURPOSE_CELLULAR, FFS_PURPOSE_PSEUDO, FFS_PURPOSE_SURROGATE = 1, 2, 3, 4
+FFS_MIG_NONE, FFS_MIG_RING, FFS_MIG_PENETRATION = 0, 1, 2
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+
+
+class FFSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ffs status {status}: {msg}")
+        self.status = status
+
+
+class ffs_params(ctypes.Structure):
+    _fields_ = [
+        ("seed", _u64), ("cell_pc", _u64), ("cell_pm", _u64), ("pseudo_pc", _u64),
+        ("cell_replace_le", _i32), ("pseudo_always", _i32),
+        ("migration_mode", _i32), ("migration_gap", _i32),
+        ("ring_num", _i64), ("ring_den", _i64), ("theta_num", _i64), ("theta_den", _i64),
+        ("decode_chunk", _i32), ("block_threads", _i32),
+    ]
+
+
+# (name, restype, argtypes) of every exported call; the names follow include/ffs.h
+_SIGS = [
+    ("ffs_last_error", ctypes.c_char_p, []),
+    ("ffs_instance_create", _i32, [_i32, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
+    ("ffs_instance_destroy", _i32, [_vp]),
+    ("ffs_population_eval", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    ("ffs_population_eval_tuned", _i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i32, _vp]),
+    ("ffs_population_eval_host", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    ("ffs_philox_draws", _i32, [_u64, _u32, _u32, _u32, _u32, _i32, _i32, _vp, _vp]),
+    ("ffs_params_default", None, [ctypes.POINTER(ffs_params)]),
+    ("ffs_population_init", _i32, [_vp, _u64, _u32, _i32, _i64, _i32, _vp, _vp]),
+    ("ffs_cellular_step", _i32, [_vp, ctypes.POINTER(ffs_params), _u32, _u32, _i32, _i32, _i32,
+                                 _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_pseudo_scratch_bytes", _i64, [_i32, _i32]),
+    ("ffs_pseudo_step", _i32, [_vp, ctypes.POINTER(ffs_params), _u32, _u32, _i32, _i32,
+                               _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_islands_create", _i32, [_vp, ctypes.POINTER(ffs_params), _i32, _i32, _i32, _i32, _i32,
+                                  _vp, ctypes.POINTER(_vp)]),
+    ("ffs_islands_destroy", _i32, [_vp]),
+    ("ffs_islands_info", _i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_island_step", _i32, [_vp, _i32, _i32, _vp]),
+    ("ffs_migrate", _i32, [_vp, _i32, _vp]),
+    ("ffs_islands_get", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
+    ("ffs_islands_set", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
+    ("ffs_islands_best", _i32, [_vp, _vp, _vp, _vp, _vp]),
+    ("ffs_islands_decoded", _i32, [_vp, _vp, _vp]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libffs_gb300.so (building it with nvcc if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise FFSError(FFS_EUNSUPPORTED, f"CUDA library not built: {path}")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_names() -> list[str]:
+    return [s[0] for s in _SIGS]
+
+
+def _check(rc: int):
+    if rc != FFS_OK:
+        raise FFSError(rc, load().ffs_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor, numpy array or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def ffs_params_default() -> ffs_params:
+    p = ffs_params()
+    load().ffs_params_default(ctypes.byref(p))
+    return p
+
+
+def threshold(prob: float) -> int:
+    """Bernoulli threshold floor(prob * 2^32) of a probability."""
+    return int(prob * 4294967296.0) if prob < 1.0 else 4294967296
+
+
+# ---------------------------------------------------------------------------
+# Instances
+# ---------------------------------------------------------------------------
+class Instance:
+    """Owner of an ffs_instance handle (Section 3 problem tables)."""
+
+    def __init__(self, n: int, S: int, M, p):
+        import numpy as np
+        self.n, self.S = int(n), int(S)
+        self.M = np.ascontiguousarray(M, dtype=np.int32)
+        self.p = np.ascontiguousarray(p, dtype=np.int32).reshape(self.n, self.S)
+        h = _vp()
+        _check(load().ffs_instance_create(self.n, self.S, self.M.ctypes.data, self.p.ctypes.data,
+                                          ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def ld(self) -> int:
+        return (self.n + 7) // 8 * 8
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ffs_instance_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ffs_instance_create(n, S, M, p) -> Instance:
+    return Instance(n, S, M, p)
+
+
+def ffs_population_eval(inst: Instance, pop, N: int, ld: int, makespan, stream=None):
+    _check(load().ffs_population_eval(inst.handle, _ptr(pop), N, ld, _ptr(makespan), _stream(stream)))
+
+
+def ffs_population_eval_tuned(inst: Instance, pop, N, ld, makespan, decode_chunk=0, block_threads=0,
+                              stream=None):
+    _check(load().ffs_population_eval_tuned(inst.handle, _ptr(pop), N, ld, _ptr(makespan),
+                                            decode_chunk, block_threads, _stream(stream)))
+
+
+def ffs_population_eval_host(inst: Instance, pop, N, ld, makespan, stream=None):
+    _check(load().ffs_population_eval_host(inst.handle, _ptr(pop), N, ld, _ptr(makespan), _stream(stream)))
+
+
+def ffs_philox_draws(seed, purpose, island, generation, cell0, n_cells, n_draws, out, stream=None):
+    _check(load().ffs_philox_draws(seed, purpose, island, generation, cell0, n_cells, n_draws, _ptr(out),
+                                   _stream(stream)))
+
+
+def ffs_population_init(inst: Instance, seed, island, kind, N, ld, pop, stream=None):
+    _check(load().ffs_population_init(inst.handle, seed, island, kind, N, ld, _ptr(pop), _stream(stream)))
+
+
+def ffs_cellular_step(inst: Instance, prm: ffs_params, island, generation, rows, cols, ld,
+                      pop_in, ms_in, pop_out, ms_out, stream=None):
+    _check(load().ffs_cellular_step(inst.handle, ctypes.byref(prm), island, generation, rows, cols, ld,
+                                    _ptr(pop_in), _ptr(ms_in), _ptr(pop_out), _ptr(ms_out), _stream(stream)))
+
+
+def ffs_pseudo_scratch_bytes(size: int, ld: int) -> int:
+    return int(load().ffs_pseudo_scratch_bytes(size, ld))
+
+
+def ffs_pseudo_step(inst: Instance, prm: ffs_params, island, generation, size, ld, pop_in, ms_in,
+                    pop_out, ms_out, scratch, stream=None):
+    _check(load().ffs_pseudo_step(inst.handle, ctypes.byref(prm), island, generation, size, ld,
+                                  _ptr(pop_in), _ptr(ms_in), _ptr(pop_out), _ptr(ms_out), _ptr(scratch),
+                                  _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Islands
+# ---------------------------------------------------------------------------
+class Islands:
+    """Owner of an ffs_islands handle (ring order [cell 0, pseudo 0, cell 1, ...])."""
+
+    def __init__(self, inst: Instance, prm: ffs_params, n_cellular: int, rows: int, cols: int,
+                 n_pseudo: int, pseudo_size: int, stream=None):
+        self.inst = inst
+        h = _vp()
+        _check(load().ffs_islands_create(inst.handle, ctypes.byref(prm), n_cellular, rows, cols, n_pseudo,
+                                         pseudo_size, _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        n = _i32()
+        ld = _i32()
+        gen = _i64()
+        _check(load().ffs_islands_info(h, ctypes.byref(n), ctypes.byref(ld), ctypes.byref(gen), None, None))
+        self.n_islands, self.ld = n.value, ld.value
+        sizes = (_i32 * self.n_islands)()
+        kinds = (_i32 * self.n_islands)()
+        _check(load().ffs_islands_info(h, None, None, None, sizes, kinds))
+        self.sizes = list(sizes)
+        self.kinds = ["cellular" if k == 0 else "pseudo" for k in kinds]
+
+    def generation(self) -> int:
+        g = _i64()
+        _check(load().ffs_islands_info(self.handle, None, None, ctypes.byref(g), None, None))
+        return g.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ffs_islands_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ffs_islands_create(inst, prm, n_cellular, rows, cols, n_pseudo, pseudo_size, stream=None) -> Islands:
+    return Islands(inst, prm, n_cellular, rows, cols, n_pseudo, pseudo_size, stream)
+
+
+def ffs_island_step(isl: Islands, island: int, n_generations: int, stream=None):
+    _check(load().ffs_island_step(isl.handle, island, n_generations, _stream(stream)))
+
+
+def ffs_migrate(isl: Islands, mode: int, stream=None):
+    _check(load().ffs_migrate(isl.handle, mode, _stream(stream)))
+
+
+def ffs_islands_get(isl: Islands, island: int, pop, ld_out: int, makespan, stream=None):
+    _check(load().ffs_islands_get(isl.handle, island, _ptr(pop), ld_out, _ptr(makespan), _stream(stream)))
+
+
+def ffs_islands_set(isl: Islands, island: int, pop, ld_in: int, makespan, stream=None):
+    _check(load().ffs_islands_set(isl.handle, island, _ptr(pop), ld_in, _ptr(makespan), _stream(stream)))
+
+
+def ffs_islands_best(isl: Islands, stream=None):
+    m, i, r = _i32(), _i32(), _i32()
+    _check(load().ffs_islands_best(isl.handle, ctypes.byref(m), ctypes.byref(i), ctypes.byref(r),
+                                   _stream(stream)))
+    return m.value, i.value, r.value
+
+
+def ffs_islands_decoded(isl: Islands, stream=None) -> int:
+    c = _i64()
+    _check(load().ffs_islands_decoded(isl.handle, ctypes.byref(c), _stream(stream)))
+    return c.value
+
+
+def island_tensors(isl: Islands, island: int):
+    """(pop int16 [N][n], makespans int32 [N]) of one island, as CUDA tensors."""
+    import torch
+    N = isl.sizes[island]
+    pop = torch.empty((N, isl.inst.n), dtype=torch.int16, device="cuda")
+    ms = torch.empty(N, dtype=torch.int32, device="cuda")
+    ffs_islands_get(isl, island, pop, isl.inst.n, ms)
+    return pop, ms

@@ -1,0 +1,425 @@
+// ffs_capi.cu -- C ABI entry points: errors, instances, the batched decoder,
+// Philox draws and population initialisation.
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+#include "ffs_internal.cuh"
+
+namespace fgpu {
+
+static thread_local std::string g_err;
+
+int set_error(int status, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return status;
+}
+
+void clear_error() { g_err.clear(); }
+
+int validate_rows(const void *p, int ld, int n)
+{
+    if (ld < n || (ld & 7) != 0)
+        return set_error(FFS_EINVAL, "ld = %d must be >= n = %d and a multiple of 8", ld, n);
+    if (((uintptr_t)p & 15u) != 0) return set_error(FFS_EINVAL, "population base must be 16-byte aligned");
+    return FFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched decoder kernel.  One thread per chromosome; a warp's 32 lanes
+// decode 32 rows in lock step (same instance, same control flow).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__restrict__ tab_g,
+                                              const int32_t *__restrict__ stage_g,
+                                              const int16_t *__restrict__ pop, int64_t N, int ld,
+                                              int32_t *__restrict__ out, const int32_t *count_dev,
+                                              unsigned long long *decoded)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int T = blockDim.x;
+    const SmemMap map = smem_map(L.n, L.S, T);
+    if (count_dev) N = *count_dev;
+    stage_table(smem + map.tab, tab_g, L.S * (L.n + 1));
+    int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
+    for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    __syncthreads();
+    DecodeLayout Ls = L;
+    Ls.M = st;
+    Ls.heap_off = st + L.S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
+    uint32_t *region = smem + map.region + threadIdx.x;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0 && N > 0) atomicAdd(decoded, (unsigned long long)N);
+    for (int64_t base = (int64_t)blockIdx.x * T + warp * 32; base < N; base += (int64_t)gridDim.x * T) {
+        const int64_t c = base + lane;
+        const int64_t cc = c < N ? c : N - 1;
+        const int32_t ms = decode_chromosome(Ls, pop + cc * ld, region, T, smem + map.tab, wst);
+        if (c < N) out[c] = ms;
+    }
+}
+
+static std::mutex g_plan_mutex;
+
+static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words,
+                                Plan *out);
+
+int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words, Plan *out)
+{
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    for (const auto &e : inst->plan_cache) {
+        if (e.first.kernel == kernel && e.first.B_req == B_req && e.first.T_req == T_req &&
+            e.first.min_words == min_words) {
+            *out = e.second;
+            return FFS_OK;
+        }
+    }
+    int rc = plan_decode_uncached(inst, kernel, B_req, T_req, min_words, out);
+    if (rc == FFS_OK) inst->plan_cache.push_back({ffs_instance::PlanKey{kernel, B_req, T_req, min_words}, *out});
+    return rc;
+}
+
+static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words,
+                                Plan *out)
+{
+    const int n = inst->n, S = inst->S;
+    const size_t smem_cap = 232448;  // 227 KB per block on sm_100-class parts
+    int bestT = 0, bestB = 0, bestBlocks = 0;
+    size_t bestSmem = 0;
+    long bestScore = -1;
+    const int single_B = round_up(n, 8);
+    int Bs[8];
+    int nb = 0;
+    if (B_req > 0) {
+        if (B_req % 8) return set_error(FFS_EINVAL, "decode_chunk %d is not a multiple of 8", B_req);
+        Bs[nb++] = B_req >= n ? single_B : B_req;
+    } else {
+        Bs[nb++] = single_B;
+        for (int b : {8, 16, 32, 64, 128})
+            if (b < n) Bs[nb++] = b;
+    }
+    int Ts[5];
+    int nt = 0;
+    if (T_req > 0) {
+        if (T_req % 32 || T_req > 512) return set_error(FFS_EINVAL, "block_threads %d must be a multiple of 32, <= 512", T_req);
+        Ts[nt++] = T_req;
+    } else {
+        for (int t : {64, 128, 256, 512}) Ts[nt++] = t;
+    }
+    for (int bi = 0; bi < nb; ++bi) {
+        const int B = Bs[bi];
+        const bool single = B >= n;
+        int tw = (single ? 0 : inst->heap_words) + B;
+        if (tw < min_words) tw = min_words;
+        for (int ti = 0; ti < nt; ++ti) {
+            const int T = Ts[ti];
+            const SmemMap m = smem_map(n, S, T);
+            const size_t smem = (size_t)(m.region + tw * T) * 4u;
+            if (smem > smem_cap) continue;
+            int blocks = 0;
+            if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                continue;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, T, smem) != cudaSuccess) continue;
+            if (blocks <= 0) continue;
+            // resident threads, saturating at 1024, then fewer rounds (larger B), then fewer blocks
+            long resident = (long)blocks * T;
+            long sat = resident > 1024 ? 1024 : resident;
+            long rounds_penalty = single ? 0 : (long)(16 * 64 / B);
+            long score = sat * 64 - rounds_penalty * 8 + (T == 128 ? 1 : 0);
+            if (score > bestScore) {
+                bestScore = score;
+                bestT = T; bestB = B; bestBlocks = blocks; bestSmem = smem;
+            }
+        }
+    }
+    (void)cudaGetLastError();
+    if (bestScore < 0)
+        return set_error(FFS_EUNSUPPORTED, "no decoder launch shape fits shared memory (n=%d, S=%d)", n, S);
+    Plan p;
+    p.T = bestT;
+    p.smem = bestSmem;
+    p.blocks_per_sm = bestBlocks;
+    DecodeLayout &L = p.L;
+    memset(&L, 0, sizeof(L));
+    L.n = n; L.S = S; L.SH = inst->SH;
+    L.single = bestB >= n ? 1 : 0;
+    L.B = L.single ? single_B : bestB;
+    L.heap_words = L.single ? 0 : inst->heap_words;
+    int tw = L.heap_words + L.B;
+    L.thread_words = tw < min_words ? min_words : tw;
+    p.smem_words_fixed = smem_map(n, S, bestT).region;
+    *out = p;
+    return FFS_OK;
+}
+
+int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
+                const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
+                cudaStream_t st)
+{
+    Plan p;
+    int rc = plan_decode(inst, (const void *)k_eval, B_req, T_req, 0, &p);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    const int grid = grid_for(inst, p, N);
+    k_eval<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, pop, N, ld, out, count_dev, decoded);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Philox draws and initial populations.
+// ---------------------------------------------------------------------------
+__global__ void k_philox(uint64_t seed, uint32_t purpose, uint32_t island, uint32_t generation,
+                         uint32_t cell0, int n_cells, int n_draws, uint32_t *out)
+{
+    const int64_t total_blocks = (int64_t)n_cells * ((n_draws + 3) / 4);
+    const int per = (n_draws + 3) / 4;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total_blocks;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / per), b = (int)(t % per);
+        const U4 v = draw_block(seed, purpose, island, generation, cell0 + (uint32_t)c, (uint32_t)b);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int d = b * 4 + k;
+            if (d < n_draws) out[(int64_t)c * n_draws + d] = w[k];
+        }
+    }
+}
+
+// One thread per chromosome (cellular) or per pair (pseudo): Fisher-Yates in
+// the row itself (global memory, the thread's own row).
+__global__ void k_init(uint64_t seed, uint32_t island, int kind, int64_t N, int n, int ld, int16_t *pop)
+{
+    const int64_t units = kind == 0 ? N : N / 2;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = kind == 0 ? u : 2 * u;
+        int16_t *a = pop + r * ld;
+        for (int i = 0; i < ld; ++i) a[i] = (int16_t)(i < n ? i : 0);
+        U4 blk{0, 0, 0, 0};
+        for (int i = n - 1; i >= 1; --i) {
+            const int d = n - 1 - i;
+            if ((d & 3) == 0) blk = draw_block(seed, kPurposeInit, island, 0u, (uint32_t)r, (uint32_t)(d >> 2));
+            const uint32_t x = (d & 3) == 0 ? blk.x : (d & 3) == 1 ? blk.y : (d & 3) == 2 ? blk.z : blk.w;
+            const int j = (int)uniform_below(x, (uint32_t)(i + 1));
+            const int16_t t = a[i];
+            a[i] = a[j];
+            a[j] = t;
+        }
+        if (kind == 1) {
+            int16_t *b = a + ld;
+            for (int i = 0; i < ld; ++i) b[i] = i < n ? a[n - 1 - i] : (int16_t)0;
+        }
+    }
+}
+
+int launch_init(const ffs_instance *inst, uint64_t seed, uint32_t island, int kind, int64_t N, int ld,
+                int16_t *pop, cudaStream_t st)
+{
+    const int64_t units = kind == 0 ? N : N / 2;
+    if (units <= 0) return FFS_OK;
+    int64_t g = (units + 127) / 128;
+    if (g > 65535) g = 65535;
+    k_init<<<(int)g, 128, 0, st>>>(seed, island, kind, N, inst->n, ld, pop);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+}  // namespace fgpu
+
+using namespace fgpu;
+
+extern "C" {
+
+const char *ffs_last_error(void) { return g_err.c_str(); }
+
+void ffs_params_default(ffs_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->seed = 7;
+    p->cell_pc = 4294967296ull;            // 1.00
+    p->cell_pm = 214748364ull;             // floor(0.05 * 2^32)
+    p->pseudo_pc = 3221225472ull;          // 0.75
+    p->cell_replace_le = 0;
+    p->pseudo_always = 0;
+    p->migration_mode = FFS_MIG_RING;
+    p->migration_gap = 50;
+    p->ring_num = 2;
+    p->ring_den = 100;
+    p->theta_num = 1;
+    p->theta_den = 1;
+}
+
+int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p, ffs_instance **out)
+{
+    clear_error();
+    if (!out || !M || !p) return set_error(FFS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1 || n > 32767) return set_error(FFS_EINVAL, "n_jobs = %d outside [1, 32767]", n);
+    if (S < 1 || S > kMaxStages) return set_error(FFS_EINVAL, "n_stages = %d outside [1, %d]", S, kMaxStages);
+    int64_t total = 0;
+    for (int s = 0; s < S; ++s) {
+        if (M[s] < 1) return set_error(FFS_EINVAL, "machines_per_stage[%d] = %d < 1", s, M[s]);
+        if ((M[s] < n ? M[s] : n) > kMaxM)
+            return set_error(FFS_EUNSUPPORTED, "stage %d: %d machines (> %d) for %d jobs", s, M[s], kMaxM, n);
+    }
+    for (int64_t i = 0; i < (int64_t)n * S; ++i) {
+        if (p[i] < 1) return set_error(FFS_EINVAL, "proc_time[%lld][%lld] = %d < 1",
+                                       (long long)(i / S), (long long)(i % S), p[i]);
+        total += p[i];
+    }
+    int bits = 0;
+    while ((1 << bits) <= n) ++bits;            // ids 1..n fit in `bits`
+    const int SH = bits + 2;
+    if (total >= (int64_t(1) << (32 - SH)))
+        return set_error(FFS_EOVERFLOW, "total processing time %lld needs more than %d bits of key",
+                         (long long)total, 32 - SH);
+    ffs_instance *I = new ffs_instance();
+    I->n = n; I->S = S; I->SH = SH; I->total_p = total;
+    cudaGetDevice(&I->device);
+    cudaDeviceGetAttribute(&I->num_sms, cudaDevAttrMultiProcessorCount, I->device);
+    I->M_eff.resize(S);
+    I->heap_off.resize(S);
+    int off = 0;
+    for (int s = 0; s < S; ++s) {
+        I->M_eff[s] = M[s] < n ? M[s] : n;
+        I->heap_off[s] = off;
+        off += I->M_eff[s];
+    }
+    I->heap_words = off;
+    I->tab_words = S * (n + 1);
+    std::vector<uint32_t> tab((size_t)I->tab_words, 0u);
+    for (int s = 0; s < S; ++s)
+        for (int j = 0; j < n; ++j) tab[(size_t)s * (n + 1) + j + 1] = (uint32_t)p[(size_t)j * S + s] << SH;
+    std::vector<int32_t> stage(2 * S);
+    for (int s = 0; s < S; ++s) { stage[s] = I->M_eff[s]; stage[S + s] = I->heap_off[s]; }
+    // padded so the 16-byte staging loads never read past the allocation
+    const size_t tab_bytes = (size_t)round_up(I->tab_words, 4) * 4;
+    if (cudaMalloc(&I->d_tab, tab_bytes) != cudaSuccess || cudaMalloc(&I->d_stage, 8 * S) != cudaSuccess) {
+        cudaFree(I->d_tab);
+        delete I;
+        (void)cudaGetLastError();
+        return set_error(FFS_ENOMEM, "device allocation of the instance tables failed");
+    }
+    cudaMemset(I->d_tab, 0, tab_bytes);
+    if (cudaMemcpy(I->d_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(I->d_stage, stage.data(), stage.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(I->d_tab);
+        cudaFree(I->d_stage);
+        delete I;
+        return set_error(FFS_ECUDA, "copy of the instance tables failed");
+    }
+    *out = I;
+    return FFS_OK;
+}
+
+int ffs_instance_destroy(ffs_instance *I)
+{
+    if (!I) return FFS_OK;
+    cudaFree(I->d_tab);
+    cudaFree(I->d_stage);
+    cudaFree(I->d_host_pop);
+    cudaFree(I->d_host_ms);
+    delete I;
+    return FFS_OK;
+}
+
+int ffs_population_eval(const ffs_instance *I, const int16_t *pop, int64_t N, int32_t ld, int32_t *ms,
+                        ffs_stream stream)
+{
+    clear_error();
+    if (!I) return set_error(FFS_EINVAL, "NULL instance");
+    if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
+    if (N == 0) return FFS_OK;
+    if (!pop || !ms) return set_error(FFS_EINVAL, "NULL population or output");
+    int rc = validate_rows(pop, ld, I->n);
+    if (rc) return rc;
+    return launch_eval(I, pop, N, ld, ms, nullptr, 0, 0, nullptr, (cudaStream_t)stream);
+}
+
+int ffs_population_eval_tuned(const ffs_instance *I, const int16_t *pop, int64_t N, int32_t ld, int32_t *ms,
+                              int32_t decode_chunk, int32_t block_threads, ffs_stream stream)
+{
+    clear_error();
+    if (!I) return set_error(FFS_EINVAL, "NULL instance");
+    if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
+    if (decode_chunk < 0 || block_threads < 0) return set_error(FFS_EINVAL, "negative launch shape");
+    if (N == 0) return FFS_OK;
+    if (!pop || !ms) return set_error(FFS_EINVAL, "NULL population or output");
+    int rc = validate_rows(pop, ld, I->n);
+    if (rc) return rc;
+    return launch_eval(I, pop, N, ld, ms, nullptr, decode_chunk, block_threads, nullptr, (cudaStream_t)stream);
+}
+
+int ffs_population_eval_host(const ffs_instance *I_, const int16_t *pop, int64_t N, int32_t ld,
+                             int32_t *ms, ffs_stream stream)
+{
+    clear_error();
+    ffs_instance *I = const_cast<ffs_instance *>(I_);
+    if (!I) return set_error(FFS_EINVAL, "NULL instance");
+    if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
+    if (N == 0) return FFS_OK;
+    if (!pop || !ms) return set_error(FFS_EINVAL, "NULL population or output");
+    if (ld < I->n || (ld & 7)) return set_error(FFS_EINVAL, "ld = %d must be >= n and a multiple of 8", ld);
+    const size_t need = (size_t)N * ld * 2;
+    if (need > I->host_cap) {
+        cudaFree(I->d_host_pop);
+        cudaFree(I->d_host_ms);
+        I->d_host_pop = nullptr;
+        I->d_host_ms = nullptr;
+        I->host_cap = 0;
+        if (cudaMalloc(&I->d_host_pop, need) != cudaSuccess ||
+            cudaMalloc(&I->d_host_ms, (size_t)N * 4) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return set_error(FFS_ENOMEM, "device staging buffer of %zu bytes", need);
+        }
+        I->host_cap = need;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    FFS_CUDA_TRY(cudaMemcpyAsync(I->d_host_pop, pop, need, cudaMemcpyHostToDevice, st));
+    int rc = launch_eval(I, I->d_host_pop, N, ld, I->d_host_ms, nullptr, 0, 0, nullptr, st);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaMemcpyAsync(ms, I->d_host_ms, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
+int ffs_philox_draws(uint64_t seed, uint32_t purpose, uint32_t island, uint32_t generation, uint32_t cell0,
+                     int32_t n_cells, int32_t n_draws, uint32_t *out, ffs_stream stream)
+{
+    clear_error();
+    if (n_cells < 0 || n_draws < 0) return set_error(FFS_EINVAL, "negative size");
+    if (n_cells == 0 || n_draws == 0) return FFS_OK;
+    if (!out) return set_error(FFS_EINVAL, "NULL output");
+    if (purpose > 255) return set_error(FFS_EINVAL, "purpose %u > 255", purpose);
+    const int64_t blocks = (int64_t)n_cells * ((n_draws + 3) / 4);
+    int64_t g = (blocks + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_philox<<<(int)g, 256, 0, (cudaStream_t)stream>>>(seed, purpose, island, generation, cell0, n_cells,
+                                                        n_draws, out);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int ffs_population_init(const ffs_instance *I, uint64_t seed, uint32_t island, int32_t kind, int64_t N,
+                        int32_t ld, int16_t *pop, ffs_stream stream)
+{
+    clear_error();
+    if (!I) return set_error(FFS_EINVAL, "NULL instance");
+    if (kind != 0 && kind != 1) return set_error(FFS_EINVAL, "kind %d is not 0 (cellular) or 1 (pseudo)", kind);
+    if (N < 0 || (kind == 1 && (N & 1))) return set_error(FFS_EINVAL, "bad N = %lld", (long long)N);
+    if (N == 0) return FFS_OK;
+    if (!pop) return set_error(FFS_EINVAL, "NULL population");
+    int rc = validate_rows(pop, ld, I->n);
+    if (rc) return rc;
+    return launch_init(I, seed, island, kind, N, ld, pop, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,814 @@
+// ffs_ga.cu -- GA generations on the GPU: the fused cellular generation, the
+// pseudo island (complementary pairs), migration, and the islands handle
+// that replays one generation of every island from a CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ffs_internal.cuh"
+
+namespace fgpu {
+
+// ---------------------------------------------------------------------------
+// Order crossover into `child` (global row): the child keeps p1[l..r]; the
+// other positions, from r+1 onward cyclically, take p2's genes met from
+// position r+1 onward cyclically, skipping genes already placed.  `bits` is
+// this thread's interleaved shared bitmask of ceil(n/32) words.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void order_crossover(int n, const int16_t *p1, const int16_t *p2, int l, int r,
+                                                int16_t *child, uint32_t *bits, int T)
+{
+    const int words = (n + 31) >> 5;
+    for (int k = 0; k < words; ++k) bits[k * T] = 0u;
+    for (int k = l; k <= r; ++k) {
+        const int g = p1[k];
+        child[k] = (int16_t)g;
+        if ((unsigned)g < (unsigned)n) bits[(g >> 5) * T] |= 1u << (g & 31);
+    }
+    int pos = (r + 1 == n) ? 0 : r + 1;
+    int idx = pos;
+    for (int t = 0; t < n; ++t) {
+        const int g = p2[idx];
+        idx = (idx + 1 == n) ? 0 : idx + 1;
+        const bool taken = (unsigned)g < (unsigned)n ? ((bits[(g >> 5) * T] >> (g & 31)) & 1u) : false;
+        if (!taken) {
+            child[pos] = (int16_t)g;
+            pos = (pos + 1 == n) ? 0 : pos + 1;
+        }
+    }
+}
+
+__device__ __forceinline__ void copy_row(int16_t *dst, const int16_t *src, int ld)
+{
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    for (int k = 0; k < (ld >> 3); ++k) d[k] = s[k];
+}
+
+// ---------------------------------------------------------------------------
+// One generation of a cellular island, fused: draws, two binary tournaments
+// over the von Neumann neighbourhood (previous generation's makespans),
+// order crossover, swap mutation, decoding and replace-if-better.  One
+// thread per cell; the child is built in the cell's output row.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t *__restrict__ tab_g,
+                                                  const int32_t *__restrict__ stage_g, GaScalars g,
+                                                  IslandRef ref, int rows, int cols, int ld,
+                                                  unsigned long long *decoded)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int T = blockDim.x;
+    const SmemMap map = smem_map(L.n, L.S, T);
+    stage_table(smem + map.tab, tab_g, L.S * (L.n + 1));
+    int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
+    for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    __syncthreads();
+    DecodeLayout Ls = L;
+    Ls.M = st;
+    Ls.heap_off = st + L.S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
+    uint32_t *region = smem + map.region + threadIdx.x;
+
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(ref, pin, msin, pout, msout, gen);
+    const int n = L.n;
+    const int cells = rows * cols;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, (unsigned long long)cells);
+
+    for (int base = blockIdx.x * T + warp * 32; base < cells; base += gridDim.x * T) {
+        const int c = base + lane;
+        const bool valid = c < cells;
+        const int16_t *drow;
+        if (valid) {
+            const U4 b0 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 0u);
+            const U4 b1 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 1u);
+            const U4 b2 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 2u);
+            const int r = c / cols, q = c - r * cols;
+            const int nb[5] = {c, ((r + rows - 1) % rows) * cols + q, ((r + 1) % rows) * cols + q,
+                               r * cols + (q + cols - 1) % cols, r * cols + (q + 1) % cols};
+            int a = nb[uniform_below(b0.x, 5u)], b = nb[uniform_below(b0.y, 5u)];
+            const int par1 = (msin[b] < msin[a]) ? b : a;
+            a = nb[uniform_below(b0.z, 5u)];
+            b = nb[uniform_below(b0.w, 5u)];
+            const int par2 = (msin[b] < msin[a]) ? b : a;
+            int16_t *child = pout + (int64_t)c * ld;
+            if (fires(b1.x, g.cell_pc)) {
+                const int u = (int)uniform_below(b1.y, (uint32_t)n), v = (int)uniform_below(b1.z, (uint32_t)n);
+                order_crossover(n, pin + (int64_t)par1 * ld, pin + (int64_t)par2 * ld, min(u, v), max(u, v),
+                                child, region, T);
+            } else {
+                copy_row(child, pin + (int64_t)par1 * ld, ld);
+            }
+            if (fires(b1.w, g.cell_pm)) {
+                const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
+                const int16_t t = child[i];
+                child[i] = child[j];
+                child[j] = t;
+            }
+            drow = child;
+        } else {
+            drow = pin + (int64_t)(cells - 1) * ld;
+        }
+        const int32_t ms = decode_chromosome(Ls, drow, region, T, smem + map.tab, wst);
+        if (valid) {
+            const int32_t old = msin[c];
+            const bool better = ms >= 0 && (g.replace_le ? (uint32_t)ms <= (uint32_t)old
+                                                          : (uint32_t)ms < (uint32_t)old);
+            if (better) {
+                msout[c] = ms;
+            } else {
+                copy_row(pout + (int64_t)c * ld, pin + (int64_t)c * ld, ld);
+                msout[c] = old;
+            }
+        }
+    }
+}
+
+int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int rows, int cols,
+                    int ld, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
+{
+    Plan p;
+    const int min_words = (inst->n + 31) / 32;
+    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, min_words, &p);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    const int grid = grid_for(inst, p, (int64_t)rows * cols);
+    k_cellular<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, ref, rows, cols, ld, decoded);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pseudo island.  Scratch layout (each part 256-byte aligned):
+//   children int16[size][ld] | child_ms int32[size] | pair_slot int32[size/2] | count int32
+// ---------------------------------------------------------------------------
+static inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t pseudo_scratch_bytes(int size, int ld)
+{
+    return (int64_t)(a256((size_t)size * ld * 2) + a256((size_t)size * 4) + a256((size_t)(size / 2 + 1) * 4) + 256);
+}
+
+struct PseudoScratch {
+    int16_t *children;
+    int32_t *child_ms;
+    int32_t *pair_slot;
+    int32_t *count;
+};
+
+static PseudoScratch carve(void *base, int size, int ld)
+{
+    char *p = static_cast<char *>(base);
+    PseudoScratch s;
+    s.children = reinterpret_cast<int16_t *>(p);
+    p += a256((size_t)size * ld * 2);
+    s.child_ms = reinterpret_cast<int32_t *>(p);
+    p += a256((size_t)size * 4);
+    s.pair_slot = reinterpret_cast<int32_t *>(p);
+    p += a256((size_t)(size / 2 + 1) * 4);
+    s.count = reinterpret_cast<int32_t *>(p);
+    return s;
+}
+
+// Thread per pair: crossover decision and the two children, written to
+// compacted child slots so the decoder runs only on real children.
+__global__ void k_pseudo_breed(GaScalars g, IslandRef ref, int size, int n, int ld, PseudoScratch s)
+{
+    extern __shared__ uint32_t bits_smem[];
+    const int T = blockDim.x;
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(ref, pin, msin, pout, msout, gen);
+    const int pairs = size / 2;
+    const int k = blockIdx.x * T + threadIdx.x;
+    bool cross = false;
+    U4 d{0, 0, 0, 0};
+    if (k < pairs) {
+        d = draw_block(g.seed, kPurposePseudo, ref.island, gen, (uint32_t)k, 0u);
+        cross = fires(d.x, g.pseudo_pc);
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, cross);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(s.count, 2 * __popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (k >= pairs) return;
+    if (!cross) {
+        s.pair_slot[k] = -1;
+        return;
+    }
+    const int slot = base + 2 * __popc(mask & ((1u << lane) - 1u));
+    s.pair_slot[k] = slot;
+    const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
+    const int l = min(u, v), r = max(u, v);
+    const int16_t *a = pin + (int64_t)(2 * k) * ld;
+    const int16_t *b = a + ld;
+    uint32_t *bits = bits_smem + threadIdx.x;
+    order_crossover(n, a, b, l, r, s.children + (int64_t)slot * ld, bits, T);
+    order_crossover(n, b, a, l, r, s.children + (int64_t)(slot + 1) * ld, bits, T);
+}
+
+// Thread per pair: the pair keeps the two best of (c1, c2, a, b), or the
+// children, or itself when it did not cross.
+__global__ void k_pseudo_replace(GaScalars g, IslandRef ref, int size, int ld, PseudoScratch s)
+{
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(ref, pin, msin, pout, msout, gen);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= size / 2) return;
+    const int16_t *a = pin + (int64_t)(2 * k) * ld;
+    const int16_t *b = a + ld;
+    const int slot = s.pair_slot[k];
+    const int16_t *src[2];
+    int32_t m[2];
+    if (slot < 0) {
+        src[0] = a; src[1] = b;
+        m[0] = msin[2 * k]; m[1] = msin[2 * k + 1];
+    } else {
+        const int16_t *fam[4] = {s.children + (int64_t)slot * ld, s.children + (int64_t)(slot + 1) * ld, a, b};
+        const int32_t fm[4] = {s.child_ms[slot], s.child_ms[slot + 1], msin[2 * k], msin[2 * k + 1]};
+        int first = 0, second = 1;
+        if (!g.pseudo_always) {
+            for (int t = 1; t < 4; ++t)
+                if ((uint32_t)fm[t] < (uint32_t)fm[first]) first = t;
+            second = -1;
+            for (int t = 0; t < 4; ++t) {
+                if (t == first) continue;
+                if (second < 0 || (uint32_t)fm[t] < (uint32_t)fm[second]) second = t;
+            }
+        }
+        src[0] = fam[first]; src[1] = fam[second];
+        m[0] = fm[first]; m[1] = fm[second];
+    }
+    copy_row(pout + (int64_t)(2 * k) * ld, src[0], ld);
+    copy_row(pout + (int64_t)(2 * k + 1) * ld, src[1], ld);
+    msout[2 * k] = m[0];
+    msout[2 * k + 1] = m[1];
+}
+
+int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int size, int ld,
+                  void *scratch, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
+{
+    const int pairs = size / 2;
+    if (pairs <= 0) return FFS_OK;
+    PseudoScratch s = carve(scratch, size, ld);
+    FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, sizeof(int32_t), st));
+    const int words = (inst->n + 31) / 32;
+    int T = 128;
+    while (T > 32 && (size_t)T * words * 4 > 160 * 1024) T >>= 1;
+    const size_t smem = (size_t)T * words * 4;
+    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, ref, size, inst->n, ld, s);
+    FFS_CUDA_TRY(cudaGetLastError());
+    int rc = launch_eval(inst, s.children, size, ld, s.child_ms, s.count, B_req, T_req, decoded, st);
+    if (rc) return rc;
+    k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, ref, size, ld, s);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Migration.  Islands are ranked by (makespan, row) with a bitonic sort in
+// shared memory (one block per island), then rows are copied warp by warp.
+// ---------------------------------------------------------------------------
+struct IslandDesc {
+    int16_t *pop[2];
+    int32_t *ms[2];
+    int32_t *order;    // [N] rows sorted by (makespan, row)
+    int32_t N;
+    int32_t kind;
+    int32_t k_ring;    // rows sent to the next island by ring migration
+    int32_t ring_off;  // prefix sum of k_ring
+};
+
+constexpr int kMaxMigrationRows = 16384;
+
+// Migration runs iff gate is NULL, or the completed generation count
+// gate[0] is a positive multiple of gap.
+__device__ __forceinline__ bool migration_due(const int32_t *gate, int gap)
+{
+    if (!gate) return true;
+    const int g = gate[0];
+    return gap > 0 && g > 0 && (g % gap) == 0;
+}
+
+__global__ void __launch_bounds__(1024) k_rank(const IslandDesc *desc, const int32_t *cur, const int32_t *gate,
+                                               int gap)
+{
+    if (!migration_due(gate, gap)) return;
+    extern __shared__ unsigned long long keys[];
+    const IslandDesc d = desc[blockIdx.x];
+    const int32_t *ms = d.ms[cur[blockIdx.x]];
+    int npad = 1;
+    while (npad < d.N) npad <<= 1;
+    for (int t = threadIdx.x; t < npad; t += blockDim.x)
+        keys[t] = t < d.N ? ((unsigned long long)(uint32_t)ms[t] << 32) | (uint32_t)t : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= npad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < npad; t += blockDim.x) {
+                const int o = t ^ j;
+                if (o > t) {
+                    const unsigned long long x = keys[t], y = keys[o];
+                    const bool up = (t & k) == 0;
+                    if ((x > y) == up) { keys[t] = y; keys[o] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < d.N; t += blockDim.x) d.order[t] = (int32_t)(keys[t] & 0xFFFFFFFFu);
+}
+
+// One warp per migrated row: island i's t-th best onto island (i+1)'s t-th worst.
+__global__ void k_ring_copy(const IslandDesc *desc, int I, const int32_t *cur, int ld, int total_rows,
+                            const int32_t *gate, int gap)
+{
+    if (!migration_due(gate, gap)) return;
+    const int lane = threadIdx.x & 31;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total_rows; w += (gridDim.x * blockDim.x) >> 5) {
+        int i = 0;
+        while (i + 1 < I && desc[i + 1].ring_off <= w) ++i;
+        const int t = w - desc[i].ring_off;
+        const int j = (i + 1) % I;
+        const IslandDesc &s = desc[i], &dd = desc[j];
+        const int src = s.order[t], dst = dd.order[dd.N - 1 - t];
+        const int4 *from = reinterpret_cast<const int4 *>(s.pop[cur[i]] + (int64_t)src * ld);
+        int4 *to = reinterpret_cast<int4 *>(dd.pop[cur[j]] + (int64_t)dst * ld);
+        for (int k = lane; k < (ld >> 3); k += 32) to[k] = from[k];
+        if (lane == 0) dd.ms[cur[j]][dst] = s.ms[cur[i]][src];
+    }
+}
+
+// Penetration (Eq. (1)-(2) for makespans): one thread per pair (2q, 2q+1)
+// decides the signed count; then one warp per candidate row copies.
+__global__ void k_penetration(const IslandDesc *desc, int pairs, const int32_t *cur, long long theta_num,
+                              long long theta_den, int32_t *counts, const int32_t *gate, int gap)
+{
+    if (!migration_due(gate, gap)) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= pairs) return;
+    const IslandDesc &A = desc[2 * q], &B = desc[2 * q + 1];
+    const long long cA = (uint32_t)A.ms[cur[2 * q]][A.order[0]];
+    const long long cB = (uint32_t)B.ms[cur[2 * q + 1]][B.order[0]];
+    long long cnt = 0;
+    if (cA != cB) {
+        const long long lo = cA < cB ? cA : cB, hi = cA < cB ? cB : cA;
+        const long long N = A.N < B.N ? A.N : B.N;
+        if ((hi - lo) * theta_den < theta_num * hi) cnt = ((hi - lo) * N) / hi;
+        if (cA > cB) cnt = -cnt;
+    }
+    counts[q] = (int32_t)cnt;
+}
+
+__global__ void k_penetration_copy(const IslandDesc *desc, int pairs, const int32_t *cur, int ld,
+                                   const int32_t *counts, int rows_per_pair, const int32_t *gate, int gap)
+{
+    if (!migration_due(gate, gap)) return;
+    const int lane = threadIdx.x & 31;
+    const int total = pairs * rows_per_pair;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += (gridDim.x * blockDim.x) >> 5) {
+        const int q = w / rows_per_pair, t = w - q * rows_per_pair;
+        const int c = counts[q];
+        const int k = c < 0 ? -c : c;
+        if (t >= k) continue;
+        const int si = c > 0 ? 2 * q : 2 * q + 1, di = c > 0 ? 2 * q + 1 : 2 * q;
+        const IslandDesc &s = desc[si], &dd = desc[di];
+        const int src = s.order[t], dst = dd.order[dd.N - 1 - t];
+        const int4 *from = reinterpret_cast<const int4 *>(s.pop[cur[si]] + (int64_t)src * ld);
+        int4 *to = reinterpret_cast<int4 *>(dd.pop[cur[di]] + (int64_t)dst * ld);
+        for (int kk = lane; kk < (ld >> 3); kk += 32) to[kk] = from[kk];
+        if (lane == 0) dd.ms[cur[di]][dst] = s.ms[cur[si]][src];
+    }
+}
+
+// Advance the generation counter and flip the buffers of islands [i0, i1).
+__global__ void k_advance(int32_t *cur, int32_t *gen, int i0, int i1)
+{
+    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < i1) {
+        cur[i] ^= 1;
+        gen[i] += 1;
+    }
+}
+
+}  // namespace fgpu
+
+using namespace fgpu;
+
+struct ffs_islands {
+    const ffs_instance *inst = nullptr;
+    ffs_params prm{};
+    int I = 0, ld = 0, rows = 0, cols = 0;
+    std::vector<int> kind, size;
+    std::vector<int> host_cur;
+    std::vector<long long> host_gen;
+    std::vector<IslandDesc> desc;
+    IslandDesc *d_desc = nullptr;
+    int32_t *d_cur = nullptr, *d_gen = nullptr, *d_counts = nullptr;
+    void *d_scratch = nullptr;        // pseudo scratch (shared by the pseudo islands)
+    unsigned long long *d_decoded = nullptr;
+    int ring_rows = 0, max_N = 0, min_pair_rows = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_all = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace fgpu {
+
+static int island_generation_launch(ffs_islands *S, int i, cudaStream_t st)
+{
+    const GaScalars g = scalars_of(&S->prm);
+    IslandRef r;
+    memset(&r, 0, sizeof(r));
+    r.pop[0] = S->desc[i].pop[0];
+    r.pop[1] = S->desc[i].pop[1];
+    r.ms[0] = S->desc[i].ms[0];
+    r.ms[1] = S->desc[i].ms[1];
+    r.dev_cur = S->d_cur + i;
+    r.dev_gen = S->d_gen + i;
+    r.island = (uint32_t)i;
+    if (S->kind[i] == 0)
+        return launch_cellular(S->inst, g, r, S->rows, S->cols, S->ld, S->prm.decode_chunk, S->prm.block_threads,
+                               S->d_decoded, st);
+    return launch_pseudo(S->inst, g, r, S->size[i], S->ld, S->d_scratch, S->prm.decode_chunk,
+                         S->prm.block_threads, S->d_decoded, st);
+}
+
+static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
+{
+    if (mode == FFS_MIG_NONE || S->I < 2) return FFS_OK;
+    if (S->max_N > kMaxMigrationRows)
+        return set_error(FFS_EUNSUPPORTED, "migration ranks islands of at most %d rows", kMaxMigrationRows);
+    const int32_t *gate = gated ? S->d_gen : nullptr;
+    const int gap = S->prm.migration_gap;
+    int npad = 1;
+    while (npad < S->max_N) npad <<= 1;
+    const size_t smem = (size_t)npad * 8;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rank<<<S->I, 1024, smem, st>>>(S->d_desc, S->d_cur, gate, gap);
+    FFS_CUDA_TRY(cudaGetLastError());
+    if (mode == FFS_MIG_RING) {
+        const int warps = S->ring_rows;
+        int blocks = (warps * 32 + 255) / 256;
+        if (blocks > 1024) blocks = 1024;
+        k_ring_copy<<<blocks, 256, 0, st>>>(S->d_desc, S->I, S->d_cur, S->ld, S->ring_rows, gate, gap);
+        FFS_CUDA_TRY(cudaGetLastError());
+    } else {
+        const int pairs = S->I / 2;
+        k_penetration<<<1, 64, 0, st>>>(S->d_desc, pairs, S->d_cur, S->prm.theta_num, S->prm.theta_den,
+                                       S->d_counts, gate, gap);
+        FFS_CUDA_TRY(cudaGetLastError());
+        int blocks = (pairs * S->min_pair_rows * 32 + 255) / 256;
+        if (blocks > 2048) blocks = 2048;
+        if (blocks < 1) blocks = 1;
+        k_penetration_copy<<<blocks, 256, 0, st>>>(S->d_desc, pairs, S->d_cur, S->ld, S->d_counts,
+                                                  S->min_pair_rows, gate, gap);
+        FFS_CUDA_TRY(cudaGetLastError());
+    }
+    return FFS_OK;
+}
+
+static int generation_all(ffs_islands *S, cudaStream_t st)
+{
+    for (int i = 0; i < S->I; ++i) {
+        int rc = island_generation_launch(S, i, st);
+        if (rc) return rc;
+    }
+    // flip to the new generation first: migration works on it
+    k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
+    FFS_CUDA_TRY(cudaGetLastError());
+    if (S->prm.migration_gap > 0) {
+        int rc = migrate_launch(S, S->prm.migration_mode, true, st);
+        if (rc) return rc;
+    }
+    return FFS_OK;
+}
+
+}  // namespace fgpu
+
+extern "C" {
+
+int ffs_cellular_step(const ffs_instance *I, const ffs_params *prm, uint32_t island, uint32_t generation,
+                      int32_t rows, int32_t cols, int32_t ld, const int16_t *pop_in, const int32_t *ms_in,
+                      int16_t *pop_out, int32_t *ms_out, ffs_stream stream)
+{
+    clear_error();
+    if (!I || !prm || !pop_in || !ms_in || !pop_out || !ms_out) return set_error(FFS_EINVAL, "NULL argument");
+    if (rows < 1 || cols < 1 || (int64_t)rows * cols > (1 << 30)) return set_error(FFS_EINVAL, "bad torus %dx%d", rows, cols);
+    if (pop_in == pop_out) return set_error(FFS_EINVAL, "pop_in and pop_out must differ");
+    int rc = validate_rows(pop_in, ld, I->n);
+    if (rc) return rc;
+    if ((rc = validate_rows(pop_out, ld, I->n))) return rc;
+    IslandRef r;
+    memset(&r, 0, sizeof(r));
+    r.pop_in = pop_in; r.ms_in = ms_in; r.pop_out = pop_out; r.ms_out = ms_out;
+    r.generation = generation;
+    r.island = island;
+    return launch_cellular(I, scalars_of(prm), r, rows, cols, ld, prm->decode_chunk, prm->block_threads, nullptr,
+                           (cudaStream_t)stream);
+}
+
+int64_t ffs_pseudo_scratch_bytes(int32_t size, int32_t ld)
+{
+    if (size < 0 || ld < 0) return -1;
+    return pseudo_scratch_bytes(size, ld);
+}
+
+int ffs_pseudo_step(const ffs_instance *I, const ffs_params *prm, uint32_t island, uint32_t generation,
+                    int32_t size, int32_t ld, const int16_t *pop_in, const int32_t *ms_in, int16_t *pop_out,
+                    int32_t *ms_out, void *scratch, ffs_stream stream)
+{
+    clear_error();
+    if (!I || !prm || !pop_in || !ms_in || !pop_out || !ms_out || !scratch)
+        return set_error(FFS_EINVAL, "NULL argument");
+    if (size < 2 || (size & 1)) return set_error(FFS_EINVAL, "pseudo island size %d must be even and >= 2", size);
+    if (pop_in == pop_out) return set_error(FFS_EINVAL, "pop_in and pop_out must differ");
+    if (((uintptr_t)scratch & 255u) != 0) return set_error(FFS_EINVAL, "scratch must be 256-byte aligned");
+    int rc = validate_rows(pop_in, ld, I->n);
+    if (rc) return rc;
+    if ((rc = validate_rows(pop_out, ld, I->n))) return rc;
+    IslandRef r;
+    memset(&r, 0, sizeof(r));
+    r.pop_in = pop_in; r.ms_in = ms_in; r.pop_out = pop_out; r.ms_out = ms_out;
+    r.generation = generation;
+    r.island = island;
+    return launch_pseudo(I, scalars_of(prm), r, size, ld, scratch, prm->decode_chunk, prm->block_threads, nullptr,
+                         (cudaStream_t)stream);
+}
+
+static void islands_free(ffs_islands *S)
+{
+    if (!S) return;
+    if (S->graph_all) cudaGraphExecDestroy(S->graph_all);
+    if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
+    for (void *p : S->allocs) cudaFree(p);
+    delete S;
+}
+
+int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t n_cellular, int32_t rows,
+                       int32_t cols, int32_t n_pseudo, int32_t pseudo_size, ffs_stream stream, ffs_islands **out)
+{
+    clear_error();
+    if (!inst || !prm || !out) return set_error(FFS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n_cellular < 0 || n_pseudo < 0 || n_cellular + n_pseudo < 1 || n_cellular + n_pseudo > 4096)
+        return set_error(FFS_EINVAL, "island counts %d + %d", n_cellular, n_pseudo);
+    if (n_cellular > 0 && (rows < 1 || cols < 1 || (int64_t)rows * cols > kMaxMigrationRows * 64))
+        return set_error(FFS_EINVAL, "bad torus %dx%d", rows, cols);
+    if (n_pseudo > 0 && (pseudo_size < 2 || (pseudo_size & 1)))
+        return set_error(FFS_EINVAL, "pseudo island size %d must be even and >= 2", pseudo_size);
+    if (prm->migration_mode < FFS_MIG_NONE || prm->migration_mode > FFS_MIG_PENETRATION)
+        return set_error(FFS_EINVAL, "migration_mode %d", prm->migration_mode);
+    if (prm->ring_den <= 0 || prm->ring_num < 0 || prm->theta_den <= 0 || prm->theta_num < 0 ||
+        prm->theta_num > prm->theta_den)
+        return set_error(FFS_EINVAL, "migration fractions must be num >= 0, den > 0, theta <= 1");
+    if (prm->migration_gap < 0) return set_error(FFS_EINVAL, "migration_gap %d < 0", prm->migration_gap);
+    ffs_islands *S = new ffs_islands();
+    S->inst = inst;
+    S->prm = *prm;
+    S->rows = rows;
+    S->cols = cols;
+    S->ld = round_up(inst->n, 8);
+    for (int q = 0; q < std::max(n_cellular, n_pseudo); ++q) {
+        if (q < n_cellular) { S->kind.push_back(0); S->size.push_back(rows * cols); }
+        if (q < n_pseudo) { S->kind.push_back(1); S->size.push_back(pseudo_size); }
+    }
+    S->I = (int)S->kind.size();
+    S->host_cur.assign(S->I, 0);
+    S->host_gen.assign(S->I, 0);
+    S->desc.resize(S->I);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+        S->allocs.push_back(p);
+        return p;
+    };
+    int ring_off = 0, max_pseudo = 0;
+    for (int i = 0; i < S->I; ++i) {
+        const int N = S->size[i];
+        S->max_N = std::max(S->max_N, N);
+        IslandDesc &d = S->desc[i];
+        memset(&d, 0, sizeof(d));
+        d.N = N;
+        d.kind = S->kind[i];
+        for (int b = 0; b < 2; ++b) {
+            d.pop[b] = (int16_t *)alloc((size_t)N * S->ld * 2);
+            d.ms[b] = (int32_t *)alloc((size_t)N * 4);
+        }
+        d.order = (int32_t *)alloc((size_t)N * 4);
+        if (!d.pop[0] || !d.pop[1] || !d.ms[0] || !d.ms[1] || !d.order) {
+            islands_free(S);
+            return set_error(FFS_ENOMEM, "island %d buffers", i);
+        }
+        if (S->kind[i] == 1) max_pseudo = std::max(max_pseudo, N);
+    }
+    if (S->I > 1 && prm->migration_mode != FFS_MIG_NONE && S->max_N > kMaxMigrationRows) {
+        islands_free(S);
+        return set_error(FFS_EUNSUPPORTED, "migration ranks islands of at most %d rows", kMaxMigrationRows);
+    }
+    for (int i = 0; i < S->I; ++i) {
+        const int j = (i + 1) % S->I;
+        const int nmin = std::min(S->size[i], S->size[j]);
+        long long k = (long long)(prm->ring_num * (long long)nmin / prm->ring_den);
+        if (k < 1) k = 1;
+        if (2 * k > nmin) {
+            islands_free(S);
+            return set_error(FFS_EINVAL, "ring migration of %lld rows exceeds half of %d", k, nmin);
+        }
+        S->desc[i].k_ring = (int)k;
+        S->desc[i].ring_off = ring_off;
+        ring_off += (int)k;
+    }
+    S->ring_rows = ring_off;
+    S->min_pair_rows = 0;
+    for (int q = 0; q + 1 < S->I; q += 2) S->min_pair_rows = std::max(S->min_pair_rows, std::min(S->size[q], S->size[q + 1]));
+    S->d_desc = (IslandDesc *)alloc(sizeof(IslandDesc) * S->I);
+    S->d_cur = (int32_t *)alloc(4 * S->I);
+    S->d_gen = (int32_t *)alloc(4 * S->I);
+    S->d_counts = (int32_t *)alloc(4 * (S->I / 2 + 1));
+    S->d_decoded = (unsigned long long *)alloc(8);
+    if (max_pseudo > 0) S->d_scratch = alloc((size_t)pseudo_scratch_bytes(max_pseudo, S->ld));
+    if (!S->d_desc || !S->d_cur || !S->d_gen || !S->d_counts || !S->d_decoded || (max_pseudo > 0 && !S->d_scratch)) {
+        islands_free(S);
+        return set_error(FFS_ENOMEM, "island state");
+    }
+    int rc = FFS_OK;
+    if (cudaMemcpyAsync(S->d_desc, S->desc.data(), sizeof(IslandDesc) * S->I, cudaMemcpyHostToDevice, st) ||
+        cudaMemsetAsync(S->d_cur, 0, 4 * S->I, st) || cudaMemsetAsync(S->d_gen, 0, 4 * S->I, st) ||
+        cudaMemsetAsync(S->d_decoded, 0, 8, st))
+        rc = set_error(FFS_ECUDA, "island state initialisation");
+    for (int i = 0; i < S->I && !rc; ++i) {
+        rc = launch_init(inst, prm->seed, (uint32_t)i, S->kind[i], S->size[i], S->ld, S->desc[i].pop[0], st);
+        if (!rc)
+            rc = launch_eval(inst, S->desc[i].pop[0], S->size[i], S->ld, S->desc[i].ms[0], nullptr, prm->decode_chunk,
+                             prm->block_threads, nullptr, st);
+    }
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = set_error(FFS_ECUDA, "initialisation failed");
+    if (rc) {
+        islands_free(S);
+        return rc;
+    }
+    *out = S;
+    return FFS_OK;
+}
+
+int ffs_islands_destroy(ffs_islands *S)
+{
+    islands_free(S);
+    return FFS_OK;
+}
+
+int ffs_islands_info(const ffs_islands *S, int32_t *n_islands, int32_t *ld, int64_t *generation, int32_t *sizes,
+                     int32_t *kinds)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (n_islands) *n_islands = S->I;
+    if (ld) *ld = S->ld;
+    if (generation) *generation = S->host_gen.empty() ? 0 : S->host_gen[0];
+    for (int i = 0; i < S->I; ++i) {
+        if (sizes) sizes[i] = S->size[i];
+        if (kinds) kinds[i] = S->kind[i];
+    }
+    return FFS_OK;
+}
+
+int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (island < -1 || island >= S->I) return set_error(FFS_EINVAL, "island %d outside [-1, %d)", island, S->I);
+    if (n_generations < 0) return set_error(FFS_EINVAL, "n_generations %d < 0", n_generations);
+    if (n_generations == 0) return FFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (island >= 0) {
+        for (int g = 0; g < n_generations; ++g) {
+            int rc = island_generation_launch(S, island, st);
+            if (rc) return rc;
+            k_advance<<<1, 32, 0, st>>>(S->d_cur, S->d_gen, island, island + 1);
+            FFS_CUDA_TRY(cudaGetLastError());
+            S->host_cur[island] ^= 1;
+            S->host_gen[island] += 1;
+        }
+        return FFS_OK;
+    }
+    for (int i = 1; i < S->I; ++i)
+        if (S->host_gen[i] != S->host_gen[0])
+            return set_error(FFS_EINVAL, "islands were stepped separately; generation counts differ");
+    if (!S->graph_all) {
+        if (!S->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        FFS_CUDA_TRY(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeRelaxed));
+        int rc = generation_all(S, S->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(S->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return set_error(FFS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&S->graph_all, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            S->graph_all = nullptr;
+            return set_error(FFS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int g = 0; g < n_generations; ++g) {
+        FFS_CUDA_TRY(cudaGraphLaunch(S->graph_all, st));
+        for (int i = 0; i < S->I; ++i) {
+            S->host_cur[i] ^= 1;
+            S->host_gen[i] += 1;
+        }
+    }
+    return FFS_OK;
+}
+
+int ffs_migrate(ffs_islands *S, int32_t mode, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (mode < FFS_MIG_NONE || mode > FFS_MIG_PENETRATION) return set_error(FFS_EINVAL, "mode %d", mode);
+    return migrate_launch(S, mode, false, (cudaStream_t)stream);
+}
+
+int ffs_islands_get(const ffs_islands *S, int32_t island, int16_t *pop, int32_t ld_out, int32_t *ms, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (island < 0 || island >= S->I) return set_error(FFS_EINVAL, "island %d", island);
+    const int c = S->host_cur[island], N = S->size[island], n = S->inst->n;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pop) {
+        if (ld_out < n) return set_error(FFS_EINVAL, "ld_out %d < n %d", ld_out, n);
+        FFS_CUDA_TRY(cudaMemcpy2DAsync(pop, (size_t)ld_out * 2, S->desc[island].pop[c], (size_t)S->ld * 2,
+                                       (size_t)n * 2, N, cudaMemcpyDefault, st));
+    }
+    if (ms) FFS_CUDA_TRY(cudaMemcpyAsync(ms, S->desc[island].ms[c], (size_t)N * 4, cudaMemcpyDefault, st));
+    return FFS_OK;
+}
+
+int ffs_islands_set(ffs_islands *S, int32_t island, const int16_t *pop, int32_t ld_in, const int32_t *ms,
+                    ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (island < 0 || island >= S->I) return set_error(FFS_EINVAL, "island %d", island);
+    const int c = S->host_cur[island], N = S->size[island], n = S->inst->n;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pop) {
+        if (ld_in < n) return set_error(FFS_EINVAL, "ld_in %d < n %d", ld_in, n);
+        FFS_CUDA_TRY(cudaMemcpy2DAsync(S->desc[island].pop[c], (size_t)S->ld * 2, pop, (size_t)ld_in * 2,
+                                       (size_t)n * 2, N, cudaMemcpyDefault, st));
+    }
+    if (ms) FFS_CUDA_TRY(cudaMemcpyAsync(S->desc[island].ms[c], ms, (size_t)N * 4, cudaMemcpyDefault, st));
+    return FFS_OK;
+}
+
+int ffs_islands_best(const ffs_islands *S, int32_t *best_ms, int32_t *best_island, int32_t *best_row,
+                     ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t bm = -1, bi = -1, br = -1;
+    std::vector<int32_t> h;
+    for (int i = 0; i < S->I; ++i) {
+        h.resize(S->size[i]);
+        FFS_CUDA_TRY(cudaMemcpyAsync(h.data(), S->desc[i].ms[S->host_cur[i]], h.size() * 4, cudaMemcpyDeviceToHost, st));
+        FFS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int r = 0; r < S->size[i]; ++r)
+            if (h[r] >= 0 && (bm < 0 || h[r] < bm)) { bm = h[r]; bi = i; br = r; }
+    }
+    if (best_ms) *best_ms = bm;
+    if (best_island) *best_island = bi;
+    if (best_row) *best_row = br;
+    return FFS_OK;
+}
+
+int ffs_islands_decoded(const ffs_islands *S, int64_t *count, ffs_stream stream)
+{
+    clear_error();
+    if (!S || !count) return set_error(FFS_EINVAL, "NULL argument");
+    unsigned long long v = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&v, S->d_decoded, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    FFS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *count = (int64_t)v;
+    return FFS_OK;
+}
+
+}  // extern "C"

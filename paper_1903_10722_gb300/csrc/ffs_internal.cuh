@@ -1,0 +1,161 @@
+// ffs_internal.cuh -- host-side internals shared by the library's .cu files.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ffs.h"
+#include "ffs_device.cuh"
+
+namespace fgpu {
+
+// Thread-local error message; returns the status for one-line returns.
+int set_error(int status, const char *fmt, ...);
+void clear_error();
+
+#define FFS_CUDA_TRY(expr)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return ::fgpu::set_error(FFS_ECUDA, "%s failed: %s (%s:%d)", #expr,                \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);             \
+    } while (0)
+
+// Launch plan of a decoding kernel.
+struct Plan {
+    DecodeLayout L;
+    int T = 0;            // threads per block
+    size_t smem = 0;      // dynamic shared bytes
+    int blocks_per_sm = 0;
+    int smem_words_fixed = 0;  // table + stage descriptors + warp state
+};
+
+// Shared-memory word offsets inside a decoding block.
+struct SmemMap {
+    int tab;       // processing-time table
+    int stage;     // [2S]: M_s, heap offset
+    int warp;      // warp state, (T/32) * S * 2 words
+    int region;    // per-thread interleaved region
+};
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+__host__ __device__ inline SmemMap smem_map(int n, int S, int T)
+{
+    SmemMap m;
+    m.tab = 0;
+    m.stage = round_up(S * (n + 1), 4);
+    m.warp = m.stage + round_up(2 * S, 4);
+    m.region = m.warp + round_up((T / 32) * S * 2, 4);
+    return m;
+}
+
+}  // namespace fgpu
+
+struct ffs_instance {
+    int n = 0, S = 0, SH = 0, device = 0;
+    int64_t total_p = 0;
+    std::vector<int32_t> M_eff;      // min(M_s, n)
+    std::vector<int32_t> heap_off;   // prefix sums of M_eff
+    int heap_words = 0;
+    uint32_t *d_tab = nullptr;       // [S][n+1] pre-shifted times
+    int32_t *d_stage = nullptr;      // [2S]: M_eff, heap_off
+    int tab_words = 0;
+    int num_sms = 0;
+    // launch plans already chosen: (kernel, chunk request, threads request, extra words)
+    struct PlanKey { const void *kernel; int B_req, T_req, min_words; };
+    mutable std::vector<std::pair<PlanKey, fgpu::Plan>> plan_cache;
+    // buffers of ffs_population_eval_host
+    int16_t *d_host_pop = nullptr;
+    int32_t *d_host_ms = nullptr;
+    size_t host_cap = 0;
+};
+
+namespace fgpu {
+
+// Choose (B, T) for a decoding kernel, honouring requests (0 = choose).
+// min_words: per-thread words the kernel needs besides decoding (e.g. the
+// crossover bitmask).  kernel: for the occupancy query.
+int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words,
+                Plan *out);
+
+// Grid size for N items (persistent, grid-stride).
+inline int grid_for(const ffs_instance *inst, const Plan &p, int64_t N)
+{
+    int64_t need = (N + p.T - 1) / p.T;
+    int64_t cap = (int64_t)inst->num_sms * (p.blocks_per_sm > 0 ? p.blocks_per_sm : 1);
+    int64_t g = need < cap ? need : cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// Kernel-side view of where a GA step reads and writes.
+struct IslandRef {
+    const int16_t *pop_in;
+    const int32_t *ms_in;
+    int16_t *pop_out;
+    int32_t *ms_out;
+    int16_t *pop[2];
+    int32_t *ms[2];
+    const int32_t *dev_cur;   // non-null: in = [cur], out = [cur ^ 1]
+    const int32_t *dev_gen;   // non-null: generation = *dev_gen + 1
+    uint32_t generation;
+    uint32_t island;
+};
+
+__device__ __forceinline__ void resolve(const IslandRef &r, const int16_t *&pin, const int32_t *&min_,
+                                        int16_t *&pout, int32_t *&mout, uint32_t &gen)
+{
+    if (r.dev_cur) {
+        const int c = *r.dev_cur;
+        pin = r.pop[c];
+        min_ = r.ms[c];
+        pout = r.pop[c ^ 1];
+        mout = r.ms[c ^ 1];
+        gen = (uint32_t)(*r.dev_gen) + 1u;
+    } else {
+        pin = r.pop_in;
+        min_ = r.ms_in;
+        pout = r.pop_out;
+        mout = r.ms_out;
+        gen = r.generation;
+    }
+}
+
+struct GaScalars {
+    uint64_t seed, cell_pc, cell_pm, pseudo_pc;
+    int32_t replace_le, pseudo_always;
+};
+
+inline GaScalars scalars_of(const ffs_params *p)
+{
+    GaScalars g;
+    g.seed = p->seed;
+    g.cell_pc = p->cell_pc;
+    g.cell_pm = p->cell_pm;
+    g.pseudo_pc = p->pseudo_pc;
+    g.replace_le = p->cell_replace_le;
+    g.pseudo_always = p->pseudo_always;
+    return g;
+}
+
+// Launchers (defined in the .cu files).
+int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
+                const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
+                cudaStream_t st);
+int launch_init(const ffs_instance *inst, uint64_t seed, uint32_t island, int kind, int64_t N, int ld,
+                int16_t *pop, cudaStream_t st);
+int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int rows,
+                    int cols, int ld, int B_req, int T_req, unsigned long long *decoded,
+                    cudaStream_t st);
+int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int size,
+                  int ld, void *scratch, int B_req, int T_req, unsigned long long *decoded,
+                  cudaStream_t st);
+int64_t pseudo_scratch_bytes(int size, int ld);
+
+int validate_rows(const void *p, int ld, int n);
+
+}  // namespace fgpu

@@ -22,3 +22,23 @@ def golden():
         with open(os.path.join(GOLDEN, name)) as f:
             return json.load(f)
     return load
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA binding, loaded (and built if needed) for a GPU test."""
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    assert torch.cuda.is_available(), "GPU test without a CUDA device"
+    ffs.load()
+    return ffs
+
+
+def dev(a, dtype=None):
+    import numpy as np
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
