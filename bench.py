@@ -313,7 +313,8 @@ def run_ours(args):
                      "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
                      "kernel": "k_cellular (fused tournament + OX + swap + decode + replace)",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": cells * ops_eval,
-                     "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"},
+                     "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
+                     "launch_shape": ffs.ffs_decode_plan(inst, 1)},
         "clocks": clock_info,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -342,7 +343,7 @@ def launches_per_generation(w) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="scale_500x20")

@@ -88,6 +88,14 @@ int ffs_population_eval_tuned(const ffs_instance *inst, const int16_t *pop, int6
                               int32_t *makespan, int32_t decode_chunk, int32_t block_threads,
                               ffs_stream stream);
 
+/* The launch shape the library uses for a decoding kernel (kernel 0: the
+ * batched decoder, 1: the fused cellular generation) given requested
+ * decode_chunk / block_threads (0 = choose): jobs per round, threads per
+ * block, resident blocks per SM and dynamic shared bytes per block.  Host
+ * pointers; any may be NULL.  Synchronous, launches nothing. */
+int ffs_decode_plan(const ffs_instance *inst, int32_t kernel, int32_t decode_chunk, int32_t block_threads,
+                    int32_t *chunk_out, int32_t *threads_out, int32_t *blocks_per_sm, int64_t *smem_bytes);
+
 /* Same, with host (pageable or pinned) pop and makespan: copies pop in,
  * decodes and copies the makespans out on `stream`, then synchronises the
  * stream.  Uses a library-owned device buffer grown on demand. */

@@ -157,6 +157,8 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
     return FFS_OK;
 }
 
+const void *eval_kernel() { return (const void *)k_eval; }
+
 int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
                 const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
                 cudaStream_t st)
@@ -356,6 +358,23 @@ int ffs_population_eval_tuned(const ffs_instance *I, const int16_t *pop, int64_t
     int rc = validate_rows(pop, ld, I->n);
     if (rc) return rc;
     return launch_eval(I, pop, N, ld, ms, nullptr, decode_chunk, block_threads, nullptr, (cudaStream_t)stream);
+}
+
+int ffs_decode_plan(const ffs_instance *I, int32_t kernel, int32_t decode_chunk, int32_t block_threads,
+                    int32_t *chunk_out, int32_t *threads_out, int32_t *blocks_per_sm, int64_t *smem_bytes)
+{
+    clear_error();
+    if (!I) return set_error(FFS_EINVAL, "NULL instance");
+    if (kernel != 0 && kernel != 1) return set_error(FFS_EINVAL, "kernel %d is not 0 or 1", kernel);
+    Plan p;
+    int rc = plan_decode(I, kernel == 0 ? eval_kernel() : cellular_kernel(), decode_chunk, block_threads,
+                         kernel == 0 ? 0 : (I->n + 31) / 32, &p);
+    if (rc) return rc;
+    if (chunk_out) *chunk_out = p.L.B;
+    if (threads_out) *threads_out = p.T;
+    if (blocks_per_sm) *blocks_per_sm = p.blocks_per_sm;
+    if (smem_bytes) *smem_bytes = (int64_t)p.smem;
+    return FFS_OK;
 }
 
 int ffs_population_eval_host(const ffs_instance *I_, const int16_t *pop, int64_t N, int32_t ld,

@@ -53,7 +53,8 @@ __device__ __forceinline__ void copy_row(int16_t *dst, const int16_t *src, int l
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t *__restrict__ tab_g,
                                                   const int32_t *__restrict__ stage_g, GaScalars g,
-                                                  IslandRef ref, int rows, int cols, int ld,
+                                                  const __grid_constant__ IslandBatch batch, int rows,
+                                                  int cols, int ld,
                                                   unsigned long long *decoded)
 {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -70,19 +71,23 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
     uint32_t *region = smem + map.region + threadIdx.x;
 
-    const int16_t *pin;
-    const int32_t *msin;
-    int16_t *pout;
-    int32_t *msout;
-    uint32_t gen;
-    resolve(ref, pin, msin, pout, msout, gen);
     const int n = L.n;
     const int cells = rows * cols;
-    if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, (unsigned long long)cells);
+    const int total = cells * batch.count;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, (unsigned long long)total);
 
-    for (int base = blockIdx.x * T + warp * 32; base < cells; base += gridDim.x * T) {
-        const int c = base + lane;
-        const bool valid = c < cells;
+    for (int base = blockIdx.x * T + warp * 32; base < total; base += gridDim.x * T) {
+        const int gc = base + lane;
+        const bool valid = gc < total;
+        const int bi = (valid ? gc : total - 1) / cells;
+        const int c = (valid ? gc : total - 1) - bi * cells;
+        const IslandRef &ref = batch.ref[bi];
+        const int16_t *pin;
+        const int32_t *msin;
+        int16_t *pout;
+        int32_t *msout;
+        uint32_t gen;
+        resolve(ref, pin, msin, pout, msout, gen);
         const int16_t *drow;
         if (valid) {
             const U4 b0 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 0u);
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
             }
             drow = child;
         } else {
-            drow = pin + (int64_t)(cells - 1) * ld;
+            drow = pin + (int64_t)c * ld;   // decoded for lock step only; nothing is written
         }
         const int32_t ms = decode_chromosome(Ls, drow, region, T, smem + map.tab, wst);
         if (valid) {
@@ -129,7 +134,9 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     }
 }
 
-int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int rows, int cols,
+const void *cellular_kernel() { return (const void *)k_cellular; }
+
+int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
                     int ld, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
     Plan p;
@@ -137,8 +144,8 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandRe
     int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, min_words, &p);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
-    const int grid = grid_for(inst, p, (int64_t)rows * cols);
-    k_cellular<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, ref, rows, cols, ld, decoded);
+    const int grid = grid_for(inst, p, (int64_t)rows * cols * batch.count);
+    k_cellular<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, batch, rows, cols, ld, decoded);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -149,9 +156,10 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandRe
 // ---------------------------------------------------------------------------
 static inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int64_t pseudo_scratch_bytes(int size, int ld)
+int64_t pseudo_scratch_bytes(int size, int ld, int islands)
 {
-    return (int64_t)(a256((size_t)size * ld * 2) + a256((size_t)size * 4) + a256((size_t)(size / 2 + 1) * 4) + 256);
+    const size_t rows = (size_t)size * islands;
+    return (int64_t)(a256(rows * ld * 2) + a256(rows * 4) + a256((rows / 2 + 1) * 4) + 256);
 }
 
 struct PseudoScratch {
@@ -161,37 +169,43 @@ struct PseudoScratch {
     int32_t *count;
 };
 
-static PseudoScratch carve(void *base, int size, int ld)
+static PseudoScratch carve(void *base, int size, int ld, int islands)
 {
+    const size_t rows = (size_t)size * islands;
     char *p = static_cast<char *>(base);
     PseudoScratch s;
     s.children = reinterpret_cast<int16_t *>(p);
-    p += a256((size_t)size * ld * 2);
+    p += a256(rows * ld * 2);
     s.child_ms = reinterpret_cast<int32_t *>(p);
-    p += a256((size_t)size * 4);
+    p += a256(rows * 4);
     s.pair_slot = reinterpret_cast<int32_t *>(p);
-    p += a256((size_t)(size / 2 + 1) * 4);
+    p += a256((rows / 2 + 1) * 4);
     s.count = reinterpret_cast<int32_t *>(p);
     return s;
 }
 
 // Thread per pair: crossover decision and the two children, written to
 // compacted child slots so the decoder runs only on real children.
-__global__ void k_pseudo_breed(GaScalars g, IslandRef ref, int size, int n, int ld, PseudoScratch s)
+__global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n, int ld,
+                               PseudoScratch s)
 {
     extern __shared__ uint32_t bits_smem[];
     const int T = blockDim.x;
+    const int pairs = size / 2;
+    const int total = pairs * batch.count;
+    const int gp = blockIdx.x * T + threadIdx.x;
+    const int bi = (gp < total ? gp : total - 1) / pairs;
+    const int k = (gp < total ? gp : total - 1) - bi * pairs;
+    const IslandRef &ref = batch.ref[bi];
     const int16_t *pin;
     const int32_t *msin;
     int16_t *pout;
     int32_t *msout;
     uint32_t gen;
     resolve(ref, pin, msin, pout, msout, gen);
-    const int pairs = size / 2;
-    const int k = blockIdx.x * T + threadIdx.x;
     bool cross = false;
     U4 d{0, 0, 0, 0};
-    if (k < pairs) {
+    if (gp < total) {
         d = draw_block(g.seed, kPurposePseudo, ref.island, gen, (uint32_t)k, 0u);
         cross = fires(d.x, g.pseudo_pc);
     }
@@ -200,13 +214,13 @@ __global__ void k_pseudo_breed(GaScalars g, IslandRef ref, int size, int n, int 
     int base = 0;
     if (lane == 0 && mask) base = atomicAdd(s.count, 2 * __popc(mask));
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (k >= pairs) return;
+    if (gp >= total) return;
     if (!cross) {
-        s.pair_slot[k] = -1;
+        s.pair_slot[gp] = -1;
         return;
     }
     const int slot = base + 2 * __popc(mask & ((1u << lane) - 1u));
-    s.pair_slot[k] = slot;
+    s.pair_slot[gp] = slot;
     const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
     const int l = min(u, v), r = max(u, v);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
@@ -218,19 +232,22 @@ __global__ void k_pseudo_breed(GaScalars g, IslandRef ref, int size, int n, int 
 
 // Thread per pair: the pair keeps the two best of (c1, c2, a, b), or the
 // children, or itself when it did not cross.
-__global__ void k_pseudo_replace(GaScalars g, IslandRef ref, int size, int ld, PseudoScratch s)
+__global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int ld,
+                                 PseudoScratch s)
 {
+    const int pairs = size / 2;
+    const int gp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gp >= pairs * batch.count) return;
+    const int bi = gp / pairs, k = gp - bi * pairs;
     const int16_t *pin;
     const int32_t *msin;
     int16_t *pout;
     int32_t *msout;
     uint32_t gen;
-    resolve(ref, pin, msin, pout, msout, gen);
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= size / 2) return;
+    resolve(batch.ref[bi], pin, msin, pout, msout, gen);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
     const int16_t *b = a + ld;
-    const int slot = s.pair_slot[k];
+    const int slot = s.pair_slot[gp];
     const int16_t *src[2];
     int32_t m[2];
     if (slot < 0) {
@@ -258,12 +275,12 @@ __global__ void k_pseudo_replace(GaScalars g, IslandRef ref, int size, int ld, P
     msout[2 * k + 1] = m[1];
 }
 
-int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int size, int ld,
+int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size, int ld,
                   void *scratch, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
-    const int pairs = size / 2;
+    const int pairs = size / 2 * batch.count;
     if (pairs <= 0) return FFS_OK;
-    PseudoScratch s = carve(scratch, size, ld);
+    PseudoScratch s = carve(scratch, size, ld, batch.count);
     FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, sizeof(int32_t), st));
     const int words = (inst->n + 31) / 32;
     int T = 128;
@@ -271,11 +288,11 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandRef 
     const size_t smem = (size_t)T * words * 4;
     if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, ref, size, inst->n, ld, s);
+    k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, batch, size, inst->n, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
-    int rc = launch_eval(inst, s.children, size, ld, s.child_ms, s.count, B_req, T_req, decoded, st);
+    int rc = launch_eval(inst, s.children, 2 * (int64_t)pairs, ld, s.child_ms, s.count, B_req, T_req, decoded, st);
     if (rc) return rc;
-    k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, ref, size, ld, s);
+    k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, batch, size, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -429,9 +446,8 @@ struct ffs_islands {
 
 namespace fgpu {
 
-static int island_generation_launch(ffs_islands *S, int i, cudaStream_t st)
+static IslandRef device_ref(const ffs_islands *S, int i)
 {
-    const GaScalars g = scalars_of(&S->prm);
     IslandRef r;
     memset(&r, 0, sizeof(r));
     r.pop[0] = S->desc[i].pop[0];
@@ -441,11 +457,33 @@ static int island_generation_launch(ffs_islands *S, int i, cudaStream_t st)
     r.dev_cur = S->d_cur + i;
     r.dev_gen = S->d_gen + i;
     r.island = (uint32_t)i;
-    if (S->kind[i] == 0)
-        return launch_cellular(S->inst, g, r, S->rows, S->cols, S->ld, S->prm.decode_chunk, S->prm.block_threads,
-                               S->d_decoded, st);
-    return launch_pseudo(S->inst, g, r, S->size[i], S->ld, S->d_scratch, S->prm.decode_chunk,
-                         S->prm.block_threads, S->d_decoded, st);
+    return r;
+}
+
+// One generation of the islands in `ids` (all of one kind): cellular islands
+// in launches of up to kMaxBatch, pseudo islands likewise, one decode of all
+// their children per launch.
+static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids, cudaStream_t st)
+{
+    const GaScalars g = scalars_of(&S->prm);
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<int> sel;
+        for (int i : ids)
+            if (S->kind[i] == kind) sel.push_back(i);
+        for (size_t b0 = 0; b0 < sel.size(); b0 += kMaxBatch) {
+            IslandBatch batch;
+            memset(&batch, 0, sizeof(batch));
+            batch.count = (int)std::min(sel.size() - b0, (size_t)kMaxBatch);
+            for (int t = 0; t < batch.count; ++t) batch.ref[t] = device_ref(S, sel[b0 + t]);
+            int rc = kind == 0
+                         ? launch_cellular(S->inst, g, batch, S->rows, S->cols, S->ld, S->prm.decode_chunk,
+                                           S->prm.block_threads, S->d_decoded, st)
+                         : launch_pseudo(S->inst, g, batch, S->size[sel[b0]], S->ld, S->d_scratch,
+                                         S->prm.decode_chunk, S->prm.block_threads, S->d_decoded, st);
+            if (rc) return rc;
+        }
+    }
+    return FFS_OK;
 }
 
 static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
@@ -484,10 +522,10 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
 
 static int generation_all(ffs_islands *S, cudaStream_t st)
 {
-    for (int i = 0; i < S->I; ++i) {
-        int rc = island_generation_launch(S, i, st);
-        if (rc) return rc;
-    }
+    std::vector<int> all(S->I);
+    for (int i = 0; i < S->I; ++i) all[i] = i;
+    int rc0 = islands_generation_launch(S, all, st);
+    if (rc0) return rc0;
     // flip to the new generation first: migration works on it
     k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
     FFS_CUDA_TRY(cudaGetLastError());
@@ -513,12 +551,14 @@ int ffs_cellular_step(const ffs_instance *I, const ffs_params *prm, uint32_t isl
     int rc = validate_rows(pop_in, ld, I->n);
     if (rc) return rc;
     if ((rc = validate_rows(pop_out, ld, I->n))) return rc;
-    IslandRef r;
-    memset(&r, 0, sizeof(r));
+    IslandBatch b;
+    memset(&b, 0, sizeof(b));
+    b.count = 1;
+    IslandRef &r = b.ref[0];
     r.pop_in = pop_in; r.ms_in = ms_in; r.pop_out = pop_out; r.ms_out = ms_out;
     r.generation = generation;
     r.island = island;
-    return launch_cellular(I, scalars_of(prm), r, rows, cols, ld, prm->decode_chunk, prm->block_threads, nullptr,
+    return launch_cellular(I, scalars_of(prm), b, rows, cols, ld, prm->decode_chunk, prm->block_threads, nullptr,
                            (cudaStream_t)stream);
 }
 
@@ -541,12 +581,14 @@ int ffs_pseudo_step(const ffs_instance *I, const ffs_params *prm, uint32_t islan
     int rc = validate_rows(pop_in, ld, I->n);
     if (rc) return rc;
     if ((rc = validate_rows(pop_out, ld, I->n))) return rc;
-    IslandRef r;
-    memset(&r, 0, sizeof(r));
+    IslandBatch b;
+    memset(&b, 0, sizeof(b));
+    b.count = 1;
+    IslandRef &r = b.ref[0];
     r.pop_in = pop_in; r.ms_in = ms_in; r.pop_out = pop_out; r.ms_out = ms_out;
     r.generation = generation;
     r.island = island;
-    return launch_pseudo(I, scalars_of(prm), r, size, ld, scratch, prm->decode_chunk, prm->block_threads, nullptr,
+    return launch_pseudo(I, scalars_of(prm), b, size, ld, scratch, prm->decode_chunk, prm->block_threads, nullptr,
                          (cudaStream_t)stream);
 }
 
@@ -642,7 +684,10 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
     S->d_gen = (int32_t *)alloc(4 * S->I);
     S->d_counts = (int32_t *)alloc(4 * (S->I / 2 + 1));
     S->d_decoded = (unsigned long long *)alloc(8);
-    if (max_pseudo > 0) S->d_scratch = alloc((size_t)pseudo_scratch_bytes(max_pseudo, S->ld));
+    int n_pseudo_islands = 0;
+    for (int i = 0; i < S->I; ++i) n_pseudo_islands += S->kind[i] == 1;
+    if (max_pseudo > 0)
+        S->d_scratch = alloc((size_t)pseudo_scratch_bytes(max_pseudo, S->ld, std::min(n_pseudo_islands, kMaxBatch)));
     if (!S->d_desc || !S->d_cur || !S->d_gen || !S->d_counts || !S->d_decoded || (max_pseudo > 0 && !S->d_scratch)) {
         islands_free(S);
         return set_error(FFS_ENOMEM, "island state");
@@ -698,7 +743,7 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
     cudaStream_t st = (cudaStream_t)stream;
     if (island >= 0) {
         for (int g = 0; g < n_generations; ++g) {
-            int rc = island_generation_launch(S, island, st);
+            int rc = islands_generation_launch(S, std::vector<int>{island}, st);
             if (rc) return rc;
             k_advance<<<1, 32, 0, st>>>(S->d_cur, S->d_gen, island, island + 1);
             FFS_CUDA_TRY(cudaGetLastError());

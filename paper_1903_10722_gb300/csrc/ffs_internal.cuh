@@ -125,6 +125,14 @@ __device__ __forceinline__ void resolve(const IslandRef &r, const int16_t *&pin,
     }
 }
 
+// Up to kMaxBatch islands of one kind stepped by one launch (same instance,
+// same size); lanes of a warp may belong to different islands.
+constexpr int kMaxBatch = 16;
+struct IslandBatch {
+    IslandRef ref[kMaxBatch];
+    int count;
+};
+
 struct GaScalars {
     uint64_t seed, cell_pc, cell_pm, pseudo_pc;
     int32_t replace_le, pseudo_always;
@@ -148,13 +156,16 @@ int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld,
                 cudaStream_t st);
 int launch_init(const ffs_instance *inst, uint64_t seed, uint32_t island, int kind, int64_t N, int ld,
                 int16_t *pop, cudaStream_t st);
-int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int rows,
+int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows,
                     int cols, int ld, int B_req, int T_req, unsigned long long *decoded,
                     cudaStream_t st);
-int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandRef &ref, int size,
+int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
                   int ld, void *scratch, int B_req, int T_req, unsigned long long *decoded,
                   cudaStream_t st);
-int64_t pseudo_scratch_bytes(int size, int ld);
+// scratch for `islands` pseudo islands of `size` rows each
+int64_t pseudo_scratch_bytes(int size, int ld, int islands = 1);
+const void *cellular_kernel();
+const void *eval_kernel();
 
 int validate_rows(const void *p, int ld, int n);
 

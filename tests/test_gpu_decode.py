@@ -49,12 +49,20 @@ def test_eval_matches_oracle(gpu, shape):
         shapes.append((0, threads))
     if n > 8:
         shapes.append((8, 64))
+    ran = 0
     for chunk, threads in shapes:
         out.fill_(-7)
-        gpu.ffs_population_eval_tuned(g, d, N, pop.shape[1], out, chunk, threads)
+        try:
+            gpu.ffs_population_eval_tuned(g, d, N, pop.shape[1], out, chunk, threads)
+        except gpu.FFSError as e:
+            # a forced shape may not fit shared memory; the library's own choice always does
+            assert e.status == gpu.FFS_EUNSUPPORTED and (chunk, threads) != (0, 0), (chunk, threads)
+            continue
         torch.cuda.synchronize()
         got = out.cpu().numpy().astype(np.int64)
         assert np.array_equal(got, want), (chunk, threads, np.flatnonzero(got != want)[:5])
+        ran += 1
+    assert ran >= len(shapes) // 2
 
 
 def test_eval_full_scale_sampled(gpu):
