@@ -192,6 +192,31 @@ int ffs_pseudo_step(const ffs_instance *inst, const ffs_params *prm, uint32_t is
                     ffs_stream stream);
 
 /* ------------------------------------------------------------------------
+ * ffs_pseudo_step without caller scratch.  The paper has no counterpart:
+ * this is for callers that cannot allocate device memory (code running where
+ * cudaMalloc is not allowed or must not block, or inside a framework that
+ * owns every allocation).  It is ffs_pseudo_step with its scratch in a fixed
+ * array of FFS_NOALLOC_SCRATCH_BYTES compiled into the library (a
+ * file-scope __device__ array: each GPU that loads the library holds it
+ * until the process exits).  The caller still passes inputs and outputs.
+ *   - Sizes whose scratch (ffs_pseudo_scratch_bytes(size, ld)) exceeds the
+ *     array are rejected with FFS_EUNSUPPORTED, e.g. size 4096 with ld 480
+ *     fits, size 16384 with ld 504 does not.
+ *   - It calls no cudaMalloc / cudaFree and no allocating library routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the slot counter is cleared on the stream at the start of each
+ *     call.  Calls that overlap on the GPU (different streams, or
+ *     concurrent graph branches) race on the array and give wrong results.
+ * ---------------------------------------------------------------------- */
+#define FFS_NOALLOC_SCRATCH_BYTES (4u << 20)
+int ffs_pseudo_step_noalloc(const ffs_instance *inst, const ffs_params *prm, uint32_t island,
+                            uint32_t generation, int32_t size, int32_t ld, const int16_t *pop_in,
+                            const int32_t *ms_in, int16_t *pop_out, int32_t *ms_out, ffs_stream stream);
+
+/* ------------------------------------------------------------------------
  * Islands: the dual-island GA state on the device (Section 4.1, Fig. 2).
  * Islands are kept in ring order [cellular 0, pseudo 0, cellular 1,
  * pseudo 1, ...]; island i uses Philox island id i.  Each cellular island is

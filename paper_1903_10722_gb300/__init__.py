@@ -64,6 +64,8 @@ _SIGS = [
     ("ffs_pseudo_scratch_bytes", _i64, [_i32, _i32]),
     ("ffs_pseudo_step", _i32, [_vp, ctypes.POINTER(ffs_params), _u32, _u32, _i32, _i32,
                                _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_pseudo_step_noalloc", _i32, [_vp, ctypes.POINTER(ffs_params), _u32, _u32, _i32, _i32,
+                                       _vp, _vp, _vp, _vp, _vp]),
     ("ffs_islands_create", _i32, [_vp, ctypes.POINTER(ffs_params), _i32, _i32, _i32, _i32, _i32,
                                   _vp, ctypes.POINTER(_vp)]),
     ("ffs_islands_destroy", _i32, [_vp]),
@@ -225,6 +227,17 @@ def ffs_pseudo_step(inst: Instance, prm: ffs_params, island, generation, size, l
     _check(load().ffs_pseudo_step(inst.handle, ctypes.byref(prm), island, generation, size, ld,
                                   _ptr(pop_in), _ptr(ms_in), _ptr(pop_out), _ptr(ms_out), _ptr(scratch),
                                   _stream(stream)))
+
+
+FFS_NOALLOC_SCRATCH_BYTES = 4 << 20
+
+
+def ffs_pseudo_step_noalloc(inst: Instance, prm: ffs_params, island, generation, size, ld, pop_in, ms_in,
+                            pop_out, ms_out, stream=None):
+    """ffs_pseudo_step with the library's fixed scratch array (no allocation)."""
+    _check(load().ffs_pseudo_step_noalloc(inst.handle, ctypes.byref(prm), island, generation, size, ld,
+                                          _ptr(pop_in), _ptr(ms_in), _ptr(pop_out), _ptr(ms_out),
+                                          _stream(stream)))
 
 
 # ---------------------------------------------------------------------------
