@@ -66,26 +66,26 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
 
 static std::mutex g_plan_mutex;
 
-static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words,
-                                Plan *out);
+static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req,
+                                int bits_per_warp, Plan *out);
 
-int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words, Plan *out)
+int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp, Plan *out)
 {
     std::lock_guard<std::mutex> lock(g_plan_mutex);
     for (const auto &e : inst->plan_cache) {
         if (e.first.kernel == kernel && e.first.B_req == B_req && e.first.T_req == T_req &&
-            e.first.min_words == min_words) {
+            e.first.bits_per_warp == bits_per_warp) {
             *out = e.second;
             return FFS_OK;
         }
     }
-    int rc = plan_decode_uncached(inst, kernel, B_req, T_req, min_words, out);
-    if (rc == FFS_OK) inst->plan_cache.push_back({ffs_instance::PlanKey{kernel, B_req, T_req, min_words}, *out});
+    int rc = plan_decode_uncached(inst, kernel, B_req, T_req, bits_per_warp, out);
+    if (rc == FFS_OK) inst->plan_cache.push_back({ffs_instance::PlanKey{kernel, B_req, T_req, bits_per_warp}, *out});
     return rc;
 }
 
-static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words,
-                                Plan *out)
+static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req,
+                                int bits_per_warp, Plan *out)
 {
     const int n = inst->n, S = inst->S;
     const size_t smem_cap = 232448;  // 227 KB per block on sm_100-class parts
@@ -114,11 +114,10 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
     for (int bi = 0; bi < nb; ++bi) {
         const int B = Bs[bi];
         const bool single = B >= n;
-        int tw = (single ? 0 : inst->heap_words) + B;
-        if (tw < min_words) tw = min_words;
+        const int tw = (single ? 0 : inst->heap_words) + B + 1;   // +1: prefetch slot
         for (int ti = 0; ti < nt; ++ti) {
             const int T = Ts[ti];
-            const SmemMap m = smem_map(n, S, T);
+            const SmemMap m = smem_map(n, S, T, bits_per_warp);
             const size_t smem = (size_t)(m.region + tw * T) * 4u;
             if (smem > smem_cap) continue;
             int blocks = 0;
@@ -150,9 +149,8 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
     L.single = bestB >= n ? 1 : 0;
     L.B = L.single ? single_B : bestB;
     L.heap_words = L.single ? 0 : inst->heap_words;
-    int tw = L.heap_words + L.B;
-    L.thread_words = tw < min_words ? min_words : tw;
-    p.smem_words_fixed = smem_map(n, S, bestT).region;
+    L.thread_words = L.heap_words + L.B + 1;
+    p.smem_words_fixed = smem_map(n, S, bestT, bits_per_warp).region;
     *out = p;
     return FFS_OK;
 }

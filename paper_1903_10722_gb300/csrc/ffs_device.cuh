@@ -88,16 +88,14 @@ __device__ __forceinline__ uint32_t lds_u32(const uint32_t *row, uint32_t byte_o
     return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(row) + byte_off);
 }
 
-// One dispatch: f[] sorted ascending, pops f[0], inserts the completion key.
+// One dispatch: f[] sorted ascending, pops f[0], inserts the completion key
+// of the job `in` whose pre-shifted processing time at this stage is pp.
 template <int M>
-__device__ __forceinline__ uint32_t dispatch(uint32_t (&f)[M], uint32_t in, const uint32_t *prow,
-                                             uint32_t lowmask)
+__device__ __forceinline__ uint32_t dispatch_pp(uint32_t (&f)[M], uint32_t in, uint32_t pp, uint32_t lowmask)
 {
     const uint32_t f0 = f[0];
-    const uint32_t idoff = in & lowmask;
-    const uint32_t pp = lds_u32(prow, idoff);
     // start = max(machine free, release); keep the incoming job id.
-    const uint32_t u = (f0 & ~lowmask) | idoff;
+    const uint32_t u = (f0 & ~lowmask) | (in & lowmask);
     const uint32_t x = max(u, in) + pp;
     if constexpr (M == 1) {
         f[0] = x;
@@ -111,6 +109,13 @@ __device__ __forceinline__ uint32_t dispatch(uint32_t (&f)[M], uint32_t in, cons
         f[M - 1] = max(f[M - 1], x);
     }
     return f0;
+}
+
+template <int M>
+__device__ __forceinline__ uint32_t dispatch(uint32_t (&f)[M], uint32_t in, const uint32_t *prow,
+                                             uint32_t lowmask)
+{
+    return dispatch_pp<M>(f, in, lds_u32(prow, in & lowmask), lowmask);
 }
 
 // Per-warp round bookkeeping lives in shared memory (identical in all lanes).
@@ -142,11 +147,14 @@ __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__re
     skip = skip < 0 ? 0 : (skip > cnt ? cnt : skip);
     int w = 0;
     if constexpr (FIRST) {
-        // genes arrive 8 per 16-byte load; cnt is a multiple of 8 except at the tail
+        // genes arrive 8 per 16-byte load, one load ahead; cnt is a multiple of 8
+        // except at the tail (rows are padded to 8 genes, so the load stays in the row)
         const int4 *g4 = reinterpret_cast<const int4 *>(genes);
         const uint32_t n = (uint32_t)L.n;
+        int4 vnext = g4[0];
         for (int i0 = 0; i0 < cnt; i0 += 8) {
-            const int4 v = g4[i0 >> 3];
+            const int4 v = vnext;
+            if (i0 + 8 < cnt) vnext = g4[(i0 >> 3) + 1];
             const uint32_t words[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
 #pragma unroll
             for (int h = 0; h < 8; ++h) {
@@ -163,12 +171,28 @@ __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__re
             }
         }
     } else {
+        // The next key and its processing time are loaded one step ahead: the
+        // store of step i goes to slot i - skip <= i, never to slot i + 1.
+        // Slot cnt may be read (the region has one spare word per thread).
+        const uint32_t idmask = lowmask & ~3u;
+        uint32_t in = buf[0];
+        uint32_t pp = lds_u32(prow, in & idmask);
         int i = 0;
-        for (; i < skip; ++i) (void)dispatch<M>(f, buf[i * T], prow, lowmask);
+        for (; i < skip; ++i) {
+            const uint32_t in_n = buf[(i + 1) * T];
+            const uint32_t pp_n = lds_u32(prow, in_n & idmask);
+            (void)dispatch_pp<M>(f, in, pp, lowmask);
+            in = in_n;
+            pp = pp_n;
+        }
 #pragma unroll 4
         for (; i < cnt; ++i) {
-            const uint32_t popped = dispatch<M>(f, buf[i * T], prow, lowmask);
+            const uint32_t in_n = buf[(i + 1) * T];
+            const uint32_t pp_n = lds_u32(prow, in_n & idmask);
+            const uint32_t popped = dispatch_pp<M>(f, in, pp, lowmask);
             if constexpr (EMIT) buf[(i - skip) * T] = popped;
+            in = in_n;
+            pp = pp_n;
         }
         if constexpr (EMIT) w = cnt - skip;
     }
@@ -228,6 +252,9 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     const int n = L.n, S = L.S;
     const uint32_t lowmask = (1u << L.SH) - 1u;
     uint32_t *buf = region + L.heap_words * T;
+    // Every buffer slot holds a valid key (or 0) before the one-ahead reads
+    // can touch it: clear the buffer and its spare slot.
+    for (int w = 0; w <= L.B; ++w) buf[w * T] = 0u;
     bool bad = false;
     uint32_t last_key = 0;
     const int lane = threadIdx.x & 31;
@@ -237,9 +264,10 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     // Every round moves stage 0 forward by B jobs or some stage's flush by
     // up to B keys; this bound is never reached by a correct schedule.
     const int max_rounds = (n + L.B - 1) / L.B + S * (kMaxM / 8 + 2) + 2;
+    int s_lo = 0;   // stages before s_lo have dispatched and emitted everything
     for (int round = 0; round < max_rounds; ++round) {
         int avail = 0;  // keys in buf for the next stage
-        for (int s = 0; s < S; ++s) {
+        for (int s = s_lo; s < S; ++s) {
             const int M = L.M[s];
             const int d0 = wst[s].dispatched;
             const int cnt = (s == 0) ? min(L.B, n - d0) : avail;
@@ -278,6 +306,10 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
             if (lane == 0) { wst[s].dispatched = d1; wst[s].flushed = flushed; }
             __syncwarp();
             avail = w;
+            const bool done = d1 == n && (last || flushed == M);
+            if (done && s == s_lo) ++s_lo;
+            // nothing reaches later stages this round unless this one is finished
+            if (avail == 0 && !done) break;
         }
         if (wst[S - 1].dispatched >= n) break;
     }

@@ -10,39 +10,92 @@
 namespace fgpu {
 
 // ---------------------------------------------------------------------------
-// Order crossover into `child` (global row): the child keeps p1[l..r]; the
-// other positions, from r+1 onward cyclically, take p2's genes met from
-// position r+1 onward cyclically, skipping genes already placed.  `bits` is
-// this thread's interleaved shared bitmask of ceil(n/32) words.
+// Warp-cooperative child construction.  Each lane of the warp supplies one
+// child to build (parents, cut points, whether crossover fires, output row);
+// the warp builds them one after the other with all 32 lanes on the genes,
+// so rows are read and written in coalesced 64-byte runs.
+//
+// Order crossover: the child keeps p1[l..r]; the other positions, from r+1
+// onward cyclically, take p2's genes met from position r+1 onward
+// cyclically, skipping genes already placed.  Without crossover the child
+// copies p1.  `bits` is a warp-private shared bitmask of ceil(n/32) words.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void order_crossover(int n, const int16_t *p1, const int16_t *p2, int l, int r,
-                                                int16_t *child, uint32_t *bits, int T)
+struct ChildJob {
+    const int16_t *p1;
+    const int16_t *p2;
+    int16_t *child;
+    int l, r;
+    bool cross;
+    bool active;
+};
+
+__device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, int ld, uint32_t *bits)
 {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int words = (n + 31) >> 5;
-    for (int k = 0; k < words; ++k) bits[k * T] = 0u;
-    for (int k = l; k <= r; ++k) {
-        const int g = p1[k];
-        child[k] = (int16_t)g;
-        if ((unsigned)g < (unsigned)n) bits[(g >> 5) * T] |= 1u << (g & 31);
-    }
-    int pos = (r + 1 == n) ? 0 : r + 1;
-    int idx = pos;
-    for (int t = 0; t < n; ++t) {
-        const int g = p2[idx];
-        idx = (idx + 1 == n) ? 0 : idx + 1;
-        const bool taken = (unsigned)g < (unsigned)n ? ((bits[(g >> 5) * T] >> (g & 31)) & 1u) : false;
-        if (!taken) {
-            child[pos] = (int16_t)g;
-            pos = (pos + 1 == n) ? 0 : pos + 1;
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, me.active);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const int16_t *p1 = (const int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.p1, j);
+        const int16_t *p2 = (const int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.p2, j);
+        int16_t *child = (int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.child, j);
+        const int l = __shfl_sync(0xFFFFFFFFu, me.l, j);
+        const int r = __shfl_sync(0xFFFFFFFFu, me.r, j);
+        const bool cross = __shfl_sync(0xFFFFFFFFu, (int)me.cross, j) != 0;
+        if (!cross) {
+            const int4 *s4 = reinterpret_cast<const int4 *>(p1);
+            int4 *d4 = reinterpret_cast<int4 *>(child);
+            for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
+            __syncwarp();
+            continue;
         }
+        for (int w = lane; w < words; w += 32) bits[w] = 0u;
+        __syncwarp();
+        for (int k = l + lane; k <= r; k += 32) {
+            const int g = p1[k];
+            child[k] = (int16_t)g;
+            if ((unsigned)g < (unsigned)n) atomicOr(&bits[g >> 5], 1u << (g & 31));
+        }
+        __syncwarp();
+        const int start = (r + 1 == n) ? 0 : r + 1;
+        int placed = 0;
+        for (int t0 = 0; t0 < n; t0 += 32) {
+            const int t = t0 + lane;
+            int idx = start + t;
+            if (idx >= n) idx -= n;
+            int g = 0;
+            bool take = false;
+            if (t < n) {
+                g = p2[idx];
+                take = !((unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u));
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) {
+                int pos = start + placed + __popc(m & lt);
+                if (pos >= n) pos -= n;
+                child[pos] = (int16_t)g;
+            }
+            placed += __popc(m);
+        }
+        __syncwarp();
     }
 }
 
-__device__ __forceinline__ void copy_row(int16_t *dst, const int16_t *src, int ld)
+// Warp-cooperative row copies: lane j's (src, dst) pair when `active`.
+__device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, int16_t *dst, int ld)
 {
-    const int4 *s = reinterpret_cast<const int4 *>(src);
-    int4 *d = reinterpret_cast<int4 *>(dst);
-    for (int k = 0; k < (ld >> 3); ++k) d[k] = s[k];
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, active);
+    while (todo) {
+        const int j = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const int4 *s4 = (const int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)src, j);
+        int4 *d4 = (int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)dst, j);
+        for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -59,7 +112,8 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int T = blockDim.x;
-    const SmemMap map = smem_map(L.n, L.S, T);
+    const int bits_per_warp = (L.n + 31) >> 5;
+    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
     stage_table(smem + map.tab, tab_g, L.S * (L.n + 1));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
@@ -69,6 +123,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     Ls.heap_off = st + L.S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
+    uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
     uint32_t *region = smem + map.region + threadIdx.x;
 
     const int n = L.n;
@@ -88,49 +143,59 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
         int32_t *msout;
         uint32_t gen;
         resolve(ref, pin, msin, pout, msout, gen);
-        const int16_t *drow;
+        ChildJob job;
+        job.active = valid;
+        job.child = pout + (int64_t)c * ld;
+        job.p1 = job.p2 = pin;
+        job.l = job.r = 0;
+        job.cross = false;
+        U4 b2{0, 0, 0, 0};
+        bool mutate = false;
         if (valid) {
             const U4 b0 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 0u);
             const U4 b1 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 1u);
-            const U4 b2 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 2u);
+            b2 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 2u);
             const int r = c / cols, q = c - r * cols;
-            const int nb[5] = {c, ((r + rows - 1) % rows) * cols + q, ((r + 1) % rows) * cols + q,
-                               r * cols + (q + cols - 1) % cols, r * cols + (q + 1) % cols};
-            int a = nb[uniform_below(b0.x, 5u)], b = nb[uniform_below(b0.y, 5u)];
+            const int up = ((r + rows - 1) % rows) * cols + q, down = ((r + 1) % rows) * cols + q;
+            const int west = r * cols + (q + cols - 1) % cols, east = r * cols + (q + 1) % cols;
+            auto slot = [&](uint32_t x) {
+                const uint32_t k = uniform_below(x, 5u);
+                return k == 0 ? c : k == 1 ? up : k == 2 ? down : k == 3 ? west : east;
+            };
+            int a = slot(b0.x), b = slot(b0.y);
             const int par1 = (msin[b] < msin[a]) ? b : a;
-            a = nb[uniform_below(b0.z, 5u)];
-            b = nb[uniform_below(b0.w, 5u)];
+            a = slot(b0.z);
+            b = slot(b0.w);
             const int par2 = (msin[b] < msin[a]) ? b : a;
-            int16_t *child = pout + (int64_t)c * ld;
-            if (fires(b1.x, g.cell_pc)) {
-                const int u = (int)uniform_below(b1.y, (uint32_t)n), v = (int)uniform_below(b1.z, (uint32_t)n);
-                order_crossover(n, pin + (int64_t)par1 * ld, pin + (int64_t)par2 * ld, min(u, v), max(u, v),
-                                child, region, T);
-            } else {
-                copy_row(child, pin + (int64_t)par1 * ld, ld);
-            }
-            if (fires(b1.w, g.cell_pm)) {
-                const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
-                const int16_t t = child[i];
-                child[i] = child[j];
-                child[j] = t;
-            }
-            drow = child;
-        } else {
-            drow = pin + (int64_t)c * ld;   // decoded for lock step only; nothing is written
+            job.p1 = pin + (int64_t)par1 * ld;
+            job.p2 = pin + (int64_t)par2 * ld;
+            job.cross = fires(b1.x, g.cell_pc);
+            const int u = (int)uniform_below(b1.y, (uint32_t)n), v = (int)uniform_below(b1.z, (uint32_t)n);
+            job.l = min(u, v);
+            job.r = max(u, v);
+            mutate = fires(b1.w, g.cell_pm);
         }
+        warp_build_children(job, n, ld, wbits);
+        if (mutate) {
+            int16_t *child = job.child;
+            const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
+            const int16_t t = child[i];
+            child[i] = child[j];
+            child[j] = t;
+        }
+        __syncwarp();
+        // lanes past the end decode a row of their island in lock step; nothing is written
+        const int16_t *drow = valid ? job.child : pin + (int64_t)c * ld;
         const int32_t ms = decode_chromosome(Ls, drow, region, T, smem + map.tab, wst);
+        bool keep_old = false;
         if (valid) {
             const int32_t old = msin[c];
             const bool better = ms >= 0 && (g.replace_le ? (uint32_t)ms <= (uint32_t)old
                                                           : (uint32_t)ms < (uint32_t)old);
-            if (better) {
-                msout[c] = ms;
-            } else {
-                copy_row(pout + (int64_t)c * ld, pin + (int64_t)c * ld, ld);
-                msout[c] = old;
-            }
+            msout[c] = better ? ms : old;
+            keep_old = !better;
         }
+        warp_copy_rows(keep_old, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
     }
 }
 
@@ -140,8 +205,8 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBa
                     int ld, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
     Plan p;
-    const int min_words = (inst->n + 31) / 32;
-    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, min_words, &p);
+    const int bits_per_warp = (inst->n + 31) / 32;
+    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, (int64_t)rows * cols * batch.count);
@@ -184,8 +249,8 @@ static PseudoScratch carve(void *base, int size, int ld, int islands)
     return s;
 }
 
-// Thread per pair: crossover decision and the two children, written to
-// compacted child slots so the decoder runs only on real children.
+// Thread per pair: crossover decision, compacted child slots; the warp then
+// builds the two children of each crossing pair cooperatively.
 __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n, int ld,
                                PseudoScratch s)
 {
@@ -214,20 +279,25 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     int base = 0;
     if (lane == 0 && mask) base = atomicAdd(s.count, 2 * __popc(mask));
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (gp >= total) return;
-    if (!cross) {
-        s.pair_slot[gp] = -1;
-        return;
-    }
     const int slot = base + 2 * __popc(mask & ((1u << lane) - 1u));
-    s.pair_slot[gp] = slot;
+    if (gp < total) s.pair_slot[gp] = cross ? slot : -1;
     const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
-    const int l = min(u, v), r = max(u, v);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
     const int16_t *b = a + ld;
-    uint32_t *bits = bits_smem + threadIdx.x;
-    order_crossover(n, a, b, l, r, s.children + (int64_t)slot * ld, bits, T);
-    order_crossover(n, b, a, l, r, s.children + (int64_t)(slot + 1) * ld, bits, T);
+    uint32_t *bits = bits_smem + (threadIdx.x >> 5) * ((n + 31) >> 5);
+    ChildJob job;
+    job.active = cross;
+    job.cross = true;
+    job.l = min(u, v);
+    job.r = max(u, v);
+    job.p1 = a;
+    job.p2 = b;
+    job.child = s.children + (int64_t)slot * ld;
+    warp_build_children(job, n, ld, bits);
+    job.p1 = b;
+    job.p2 = a;
+    job.child = s.children + (int64_t)(slot + 1) * ld;
+    warp_build_children(job, n, ld, bits);
 }
 
 // Thread per pair: the pair keeps the two best of (c1, c2, a, b), or the
@@ -236,9 +306,11 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
                                  PseudoScratch s)
 {
     const int pairs = size / 2;
+    const int total = pairs * batch.count;
     const int gp = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gp >= pairs * batch.count) return;
-    const int bi = gp / pairs, k = gp - bi * pairs;
+    const bool valid = gp < total;
+    const int gq = valid ? gp : total - 1;
+    const int bi = gq / pairs, k = gq - bi * pairs;
     const int16_t *pin;
     const int32_t *msin;
     int16_t *pout;
@@ -247,14 +319,14 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
     resolve(batch.ref[bi], pin, msin, pout, msout, gen);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
     const int16_t *b = a + ld;
-    const int slot = s.pair_slot[gp];
+    const int slot = s.pair_slot[gq];
     const int16_t *src[2];
     int32_t m[2];
     if (slot < 0) {
         src[0] = a; src[1] = b;
         m[0] = msin[2 * k]; m[1] = msin[2 * k + 1];
     } else {
-        const int16_t *fam[4] = {s.children + (int64_t)slot * ld, s.children + (int64_t)(slot + 1) * ld, a, b};
+        const int16_t *c1 = s.children + (int64_t)slot * ld, *c2 = c1 + ld;
         const int32_t fm[4] = {s.child_ms[slot], s.child_ms[slot + 1], msin[2 * k], msin[2 * k + 1]};
         int first = 0, second = 1;
         if (!g.pseudo_always) {
@@ -266,13 +338,18 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
                 if (second < 0 || (uint32_t)fm[t] < (uint32_t)fm[second]) second = t;
             }
         }
-        src[0] = fam[first]; src[1] = fam[second];
-        m[0] = fm[first]; m[1] = fm[second];
+        auto pick = [&](int t) { return t == 0 ? c1 : t == 1 ? c2 : t == 2 ? a : b; };
+        src[0] = pick(first);
+        src[1] = pick(second);
+        m[0] = fm[first];
+        m[1] = fm[second];
     }
-    copy_row(pout + (int64_t)(2 * k) * ld, src[0], ld);
-    copy_row(pout + (int64_t)(2 * k + 1) * ld, src[1], ld);
-    msout[2 * k] = m[0];
-    msout[2 * k + 1] = m[1];
+    if (valid) {
+        msout[2 * k] = m[0];
+        msout[2 * k + 1] = m[1];
+    }
+    warp_copy_rows(valid, src[0], pout + (int64_t)(2 * k) * ld, ld);
+    warp_copy_rows(valid, src[1], pout + (int64_t)(2 * k + 1) * ld, ld);
 }
 
 int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size, int ld,
@@ -283,9 +360,8 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
     PseudoScratch s = carve(scratch, size, ld, batch.count);
     FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, sizeof(int32_t), st));
     const int words = (inst->n + 31) / 32;
-    int T = 128;
-    while (T > 32 && (size_t)T * words * 4 > 160 * 1024) T >>= 1;
-    const size_t smem = (size_t)T * words * 4;
+    const int T = 128;
+    const size_t smem = (size_t)(T / 32) * words * 4;
     if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, batch, size, inst->n, ld, s);

@@ -39,18 +39,20 @@ struct SmemMap {
     int tab;       // processing-time table
     int stage;     // [2S]: M_s, heap offset
     int warp;      // warp state, (T/32) * S * 2 words
+    int bits;      // per-warp crossover bitmask, (T/32) * bits_per_warp words
     int region;    // per-thread interleaved region
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-__host__ __device__ inline SmemMap smem_map(int n, int S, int T)
+__host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_warp = 0)
 {
     SmemMap m;
     m.tab = 0;
     m.stage = round_up(S * (n + 1), 4);
     m.warp = m.stage + round_up(2 * S, 4);
-    m.region = m.warp + round_up((T / 32) * S * 2, 4);
+    m.bits = m.warp + round_up((T / 32) * S * 2, 4);
+    m.region = m.bits + round_up((T / 32) * bits_per_warp, 4);
     return m;
 }
 
@@ -67,7 +69,7 @@ struct ffs_instance {
     int tab_words = 0;
     int num_sms = 0;
     // launch plans already chosen: (kernel, chunk request, threads request, extra words)
-    struct PlanKey { const void *kernel; int B_req, T_req, min_words; };
+    struct PlanKey { const void *kernel; int B_req, T_req, bits_per_warp; };
     mutable std::vector<std::pair<PlanKey, fgpu::Plan>> plan_cache;
     // buffers of ffs_population_eval_host
     int16_t *d_host_pop = nullptr;
@@ -78,9 +80,9 @@ struct ffs_instance {
 namespace fgpu {
 
 // Choose (B, T) for a decoding kernel, honouring requests (0 = choose).
-// min_words: per-thread words the kernel needs besides decoding (e.g. the
-// crossover bitmask).  kernel: for the occupancy query.
-int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int min_words,
+// bits_per_warp: shared words per warp the kernel needs besides decoding
+// (the crossover bitmask).  kernel: for the occupancy query.
+int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp,
                 Plan *out);
 
 // Grid size for N items (persistent, grid-stride).
