@@ -54,11 +54,12 @@ const char *ffs_last_error(void);
  * time units at stage s on whichever machine it is given; no preemption.
  *
  * machines_per_stage: host int32[S], each >= 1.
- * proc_time: host int32[n][S] row-major (job-major), each >= 1.
+ * proc_time: host int32[n][S] row-major (job-major), each in [1, 65535].
  * Limits: 1 <= n <= 32767 (int16 genes), 1 <= S <= 64, min(M_s, n) <= 32,
- * and sum of all proc_time below 2^(30 - ceil(log2(n + 1))) (the decoder's
- * 32-bit (time, job) keys); otherwise FFS_EINVAL / FFS_EUNSUPPORTED /
- * FFS_EOVERFLOW.  Copies the tables to the current device.  Synchronous.
+ * and sum of all proc_time below 2^(31 - ceil(log2(n + 1))) (the decoder's
+ * 32-bit (time, job) keys; every completion time is at most that sum);
+ * otherwise FFS_EINVAL / FFS_EUNSUPPORTED / FFS_EOVERFLOW.  Copies the
+ * tables to the current device.  Synchronous.
  * ---------------------------------------------------------------------- */
 int ffs_instance_create(int32_t n_jobs, int32_t n_stages, const int32_t *machines_per_stage,
                         const int32_t *proc_time, ffs_instance **out);
@@ -270,6 +271,42 @@ int ffs_islands_best(const ffs_islands *isl, int32_t *best_makespan, int32_t *be
 
 /* Number of exact decodes (children evaluated) since creation; synchronises. */
 int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Batch: many instances of uneven size, each evolving one cellular island
+ * on a rows x cols torus (the island step of Sections 4.1-4.2 per instance;
+ * instance i uses Philox island id i).  One generation of every instance is
+ * one persistent kernel launch (blocks take (instance, tile) work units,
+ * heaviest instances first, from a device counter), replayed from a CUDA
+ * graph.
+ *
+ * ffs_batch_create: count instances given back to back: n_jobs[count],
+ * n_stages[count], machines = the count M arrays concatenated,
+ * proc_time = the count [n_i][S_i] tables concatenated (host memory; same
+ * limits as ffs_instance_create).  Allocates library-owned device memory,
+ * initialises every island and decodes it; synchronous.
+ * ffs_batch_step: n_generations generations of every instance; async.
+ * ffs_batch_autotune: times every launch shape (threads per block x decode
+ * chunk) that fits, `repeats` timed runs each, on generations that do not
+ * advance the state, keeps the fastest and reports it; synchronous.
+ * ffs_batch_get: rows and makespans of one instance (host or device
+ * pointers, cudaMemcpyDefault).  ffs_batch_best: best makespan of every
+ * instance into best[count] (host), synchronous.
+ * ---------------------------------------------------------------------- */
+typedef struct ffs_batch ffs_batch;
+int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stages, const int32_t *machines,
+                     const int32_t *proc_time, const ffs_params *prm, int32_t rows, int32_t cols,
+                     ffs_stream stream, ffs_batch **out);
+int ffs_batch_destroy(ffs_batch *b);
+int ffs_batch_step(ffs_batch *b, int32_t n_generations, ffs_stream stream);
+int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t *threads_out,
+                       int32_t *chunk_out, float *best_ms);
+int ffs_batch_info(const ffs_batch *b, int32_t *count, int64_t *generation, int32_t *threads,
+                   int32_t *chunk, int32_t *blocks_per_sm);
+int ffs_batch_get(const ffs_batch *b, int32_t instance, int16_t *pop, int32_t ld_out, int32_t *makespan,
+                  ffs_stream stream);
+int ffs_batch_best(const ffs_batch *b, int32_t *best, ffs_stream stream);
+int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream);
 
 #ifdef __cplusplus
 }

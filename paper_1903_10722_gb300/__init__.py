@@ -76,6 +76,15 @@ _SIGS = [
     ("ffs_islands_set", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
     ("ffs_islands_best", _i32, [_vp, _vp, _vp, _vp, _vp]),
     ("ffs_islands_decoded", _i32, [_vp, _vp, _vp]),
+    ("ffs_batch_create", _i32, [_i32, _vp, _vp, _vp, _vp, ctypes.POINTER(ffs_params), _i32, _i32, _vp,
+                                ctypes.POINTER(_vp)]),
+    ("ffs_batch_destroy", _i32, [_vp]),
+    ("ffs_batch_step", _i32, [_vp, _i32, _vp]),
+    ("ffs_batch_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    ("ffs_batch_info", _i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_batch_get", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
+    ("ffs_batch_best", _i32, [_vp, _vp, _vp]),
+    ("ffs_batch_decoded", _i32, [_vp, _vp, _vp]),
 ]
 
 
@@ -321,4 +330,84 @@ def island_tensors(isl: Islands, island: int):
     pop = torch.empty((N, isl.inst.n), dtype=torch.int16, device="cuda")
     ms = torch.empty(N, dtype=torch.int32, device="cuda")
     ffs_islands_get(isl, island, pop, isl.inst.n, ms)
+    return pop, ms
+
+
+# ---------------------------------------------------------------------------
+# Batch of uneven instances
+# ---------------------------------------------------------------------------
+class Batch:
+    """Owner of an ffs_batch handle: one cellular island per instance."""
+
+    def __init__(self, specs, prm: ffs_params, rows: int, cols: int, stream=None):
+        import numpy as np
+        self.specs = specs
+        self.count = len(specs)
+        self.rows, self.cols = rows, cols
+        n = np.array([s.n for s in specs], dtype=np.int32)
+        S = np.array([s.S for s in specs], dtype=np.int32)
+        M = np.ascontiguousarray(np.concatenate([np.asarray(s.M, dtype=np.int32) for s in specs]))
+        p = np.ascontiguousarray(np.concatenate([np.asarray(s.p, dtype=np.int32).ravel() for s in specs]))
+        h = _vp()
+        _check(load().ffs_batch_create(self.count, n.ctypes.data, S.ctypes.data, M.ctypes.data, p.ctypes.data,
+                                       ctypes.byref(prm), rows, cols, _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def info(self) -> dict:
+        c, t, b, bps = _i32(), _i32(), _i32(), _i32()
+        g = _i64()
+        _check(load().ffs_batch_info(self.handle, ctypes.byref(c), ctypes.byref(g), ctypes.byref(t),
+                                     ctypes.byref(b), ctypes.byref(bps)))
+        return {"count": c.value, "generation": g.value, "threads": t.value, "chunk": b.value,
+                "blocks_per_sm": bps.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ffs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ffs_batch_step(b: Batch, n_generations: int, stream=None):
+    _check(load().ffs_batch_step(b.handle, n_generations, _stream(stream)))
+
+
+def ffs_batch_autotune(b: Batch, repeats: int = 2, stream=None) -> dict:
+    t, c = _i32(), _i32()
+    ms = ctypes.c_float()
+    _check(load().ffs_batch_autotune(b.handle, repeats, _stream(stream), ctypes.byref(t), ctypes.byref(c),
+                                     ctypes.byref(ms)))
+    return {"threads": t.value, "chunk": c.value, "ms": ms.value}
+
+
+def ffs_batch_get(b: Batch, instance: int, pop, ld_out: int, makespan, stream=None):
+    _check(load().ffs_batch_get(b.handle, instance, _ptr(pop), ld_out, _ptr(makespan), _stream(stream)))
+
+
+def ffs_batch_best(b: Batch, stream=None):
+    import numpy as np
+    out = np.zeros(b.count, dtype=np.int32)
+    _check(load().ffs_batch_best(b.handle, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def ffs_batch_decoded(b: Batch, stream=None) -> int:
+    c = _i64()
+    _check(load().ffs_batch_decoded(b.handle, ctypes.byref(c), _stream(stream)))
+    return c.value
+
+
+def batch_tensors(b: Batch, instance: int):
+    """(pop int16 [cells][n], makespans int32 [cells]) of one instance, as CUDA tensors."""
+    import torch
+    n = b.specs[instance].n
+    cells = b.rows * b.cols
+    pop = torch.empty((cells, n), dtype=torch.int16, device="cuda")
+    ms = torch.empty(cells, dtype=torch.int32, device="cuda")
+    ffs_batch_get(b, instance, pop, n, ms)
     return pop, ms

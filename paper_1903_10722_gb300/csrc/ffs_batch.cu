@@ -1,0 +1,481 @@
+// ffs_batch.cu -- many FFS instances of uneven size, each with one cellular
+// island, evolved together: one persistent launch per generation, replayed
+// from a CUDA graph, with the launch shape chosen by a timing autotuner.
+//
+// Work is split into units (instance, tile of `threads` cells).  Units are
+// ordered heaviest first (decode cost ~ n * sum_s (2 M_s + 6)) and blocks of
+// the persistent grid take the next unit from a device counter, stage that
+// instance's processing-time table into shared memory and run the fused
+// cellular generation on the tile.  Shared memory is sized for the largest
+// instance.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "ffs_internal.cuh"
+#include "ffs_ga_device.cuh"
+
+namespace fgpu {
+
+struct BatchInst {
+    int32_t n, S, SH, heap_words;
+    uint32_t mulSH;
+    int32_t ld;
+    const uint32_t *tab;
+    const int32_t *stage;
+    int16_t *pop[2];
+    int32_t *ms[2];
+};
+
+struct BatchShape {
+    int B;          // jobs per round requested (instances with n <= B run in one round)
+    int max_n, max_S, max_tw;
+};
+
+__global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restrict__ insts, const int2 *__restrict__ units,
+                                                        int n_units, int *counter, GaScalars g, const int32_t *cur,
+                                                        const int32_t *gen, int rows, int cols, BatchShape shape,
+                                                        unsigned long long *decoded, unsigned long long decoded_add)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_unit;
+    const int T = blockDim.x;
+    const int bits_per_warp = (shape.max_n + 31) >> 5;
+    const SmemMap map = smem_map(shape.max_n, shape.max_S, T, bits_per_warp);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * shape.max_S;
+    uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
+    uint32_t *region = smem + map.region + threadIdx.x;
+    int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
+    const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
+    const int cells = rows * cols;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, decoded_add);
+    for (;;) {
+        __syncthreads();  // the previous unit is done with shared memory
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= n_units) break;
+        const int2 un = units[u];
+        const BatchInst &I = insts[un.x];
+        const int n = I.n, S = I.S;
+        stage_table(smem + map.tab, I.tab, table_words(n, S));
+        for (int i = threadIdx.x; i < 2 * S; i += T) st[i] = I.stage[i];
+        __syncthreads();
+        DecodeLayout L;
+        L.n = n;
+        L.S = S;
+        L.SH = I.SH;
+        L.mulSH = I.mulSH;
+        L.single = shape.B >= n ? 1 : 0;
+        L.B = L.single ? round_up(n, 8) : shape.B;
+        L.heap_words = L.single ? 0 : I.heap_words;
+        L.thread_words = L.heap_words + L.B + 1;
+        L.M = st;
+        L.heap_off = st + S;
+        IslandRef ref;
+        memset(&ref, 0, sizeof(ref));
+        ref.pop[0] = I.pop[0];
+        ref.pop[1] = I.pop[1];
+        ref.ms[0] = I.ms[0];
+        ref.ms[1] = I.ms[1];
+        ref.dev_cur = cur;
+        ref.dev_gen = gen;
+        ref.island = (uint32_t)un.x;
+        const int end = min(un.y + T, cells);
+        for (int base = un.y + warp * 32; base < end; base += T) {
+            const int c = base + lane;
+            const bool valid = c < end;
+            cellular_warp_cells(L, g, ref, valid ? c : end - 1, valid, rows, cols, I.ld, wbits, region, T, tab, wst);
+        }
+    }
+}
+
+__global__ void k_batch_advance(int32_t *cur, int32_t *gen)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        cur[0] ^= 1;
+        gen[0] += 1;
+    }
+}
+
+}  // namespace fgpu
+
+using namespace fgpu;
+
+struct ffs_batch {
+    int count = 0, rows = 0, cols = 0;
+    ffs_params prm{};
+    std::vector<ffs_instance *> insts;
+    std::vector<BatchInst> hinst;
+    std::vector<double> cost;
+    BatchInst *d_inst = nullptr;
+    int2 *d_units = nullptr;
+    int n_units = 0;
+    int *d_counter = nullptr;
+    int32_t *d_cur = nullptr, *d_gen = nullptr;
+    unsigned long long *d_decoded = nullptr;
+    int host_cur = 0;
+    long long host_gen = 0;
+    int T = 0, B = 0, blocks_per_sm = 0;
+    size_t smem = 0;
+    BatchShape shape{};
+    int num_sms = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace fgpu {
+
+static void batch_free(ffs_batch *b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (void *p : b->allocs) cudaFree(p);
+    for (ffs_instance *I : b->insts) ffs_instance_destroy(I);
+    delete b;
+}
+
+// Shape (threads per block T, chunk B): feasibility and occupancy.
+static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *smem, int *blocks)
+{
+    BatchShape s{};
+    s.B = B;
+    for (const BatchInst &I : b->hinst) {
+        s.max_n = std::max(s.max_n, I.n);
+        s.max_S = std::max(s.max_S, I.S);
+        const bool single = B >= I.n;
+        const int tw = (single ? 0 : I.heap_words) + (single ? round_up(I.n, 8) : B) + 1;
+        s.max_tw = std::max(s.max_tw, tw);
+    }
+    const SmemMap m = smem_map(s.max_n, s.max_S, T, (s.max_n + 31) / 32);
+    const size_t bytes = (size_t)(m.region + s.max_tw * T) * 4u;
+    if (bytes > 232448) return FFS_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(k_batch_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FFS_EUNSUPPORTED;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_cellular, T, bytes) != cudaSuccess || nb < 1) {
+        (void)cudaGetLastError();
+        return FFS_EUNSUPPORTED;
+    }
+    *shape = s;
+    *smem = bytes;
+    *blocks = nb;
+    return FFS_OK;
+}
+
+// Work units (instance, first cell) for tiles of T cells, heaviest first.
+static int batch_units(ffs_batch *b, int T, cudaStream_t st)
+{
+    const int cells = b->rows * b->cols;
+    const int tiles = (cells + T - 1) / T;
+    std::vector<int> order(b->count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+    std::vector<int2> units;
+    units.reserve((size_t)b->count * tiles);
+    for (int i : order)
+        for (int t = 0; t < tiles; ++t) units.push_back(make_int2(i, t * T));
+    b->n_units = (int)units.size();
+    FFS_CUDA_TRY(cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
+static int batch_set_shape(ffs_batch *b, int T, int B, cudaStream_t st)
+{
+    BatchShape s;
+    size_t smem;
+    int nb;
+    if (batch_shape(b, T, B, &s, &smem, &nb)) return set_error(FFS_EUNSUPPORTED, "batch shape T=%d B=%d does not fit", T, B);
+    b->T = T;
+    b->B = B;
+    b->shape = s;
+    b->smem = smem;
+    b->blocks_per_sm = nb;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return batch_units(b, T, st);
+}
+
+// One generation's launch (the counter reset and the persistent kernel);
+// advance = false leaves the generation state untouched (autotuning).
+static int batch_generation(ffs_batch *b, bool advance, unsigned long long *decoded, cudaStream_t st)
+{
+    FFS_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_batch_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    int grid = b->num_sms * b->blocks_per_sm;
+    if (grid > b->n_units) grid = b->n_units;
+    k_batch_cellular<<<grid, b->T, b->smem, st>>>(b->d_inst, b->d_units, b->n_units, b->d_counter, scalars_of(&b->prm),
+                                                   b->d_cur, b->d_gen, b->rows, b->cols, b->shape, decoded,
+                                                   (unsigned long long)b->count * b->rows * b->cols);
+    FFS_CUDA_TRY(cudaGetLastError());
+    if (advance) {
+        k_batch_advance<<<1, 32, 0, st>>>(b->d_cur, b->d_gen);
+        FFS_CUDA_TRY(cudaGetLastError());
+    }
+    return FFS_OK;
+}
+
+}  // namespace fgpu
+
+extern "C" {
+
+int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stages, const int32_t *machines,
+                     const int32_t *proc_time, const ffs_params *prm, int32_t rows, int32_t cols, ffs_stream stream,
+                     ffs_batch **out)
+{
+    clear_error();
+    if (!out || !n_jobs || !n_stages || !machines || !proc_time || !prm) return set_error(FFS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (count < 1 || count > (1 << 20)) return set_error(FFS_EINVAL, "count %d", count);
+    if (rows < 1 || cols < 1 || (int64_t)rows * cols > (1 << 24)) return set_error(FFS_EINVAL, "bad torus %dx%d", rows, cols);
+    cudaStream_t st = (cudaStream_t)stream;
+    ffs_batch *b = new ffs_batch();
+    b->count = count;
+    b->rows = rows;
+    b->cols = cols;
+    b->prm = *prm;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+        b->allocs.push_back(p);
+        return p;
+    };
+    const int cells = rows * cols;
+    int64_t moff = 0, poff = 0;
+    for (int i = 0; i < count; ++i) {
+        ffs_instance *I = nullptr;
+        int rc = ffs_instance_create(n_jobs[i], n_stages[i], machines + moff, proc_time + poff, &I);
+        if (rc) {
+            std::string msg = std::string("instance ") + std::to_string(i) + ": " + ffs_last_error();
+            batch_free(b);
+            return set_error(rc, "%s", msg.c_str());
+        }
+        b->insts.push_back(I);
+        double c = 0;
+        for (int s = 0; s < I->S; ++s) c += (double)I->n * (2.0 * I->M_eff[s] + 6.0);
+        b->cost.push_back(c);
+        BatchInst h;
+        memset(&h, 0, sizeof(h));
+        h.n = I->n;
+        h.S = I->S;
+        h.SH = I->SH;
+        h.mulSH = 1u << I->SH;
+        h.heap_words = I->heap_words;
+        h.ld = round_up(I->n, 8);
+        h.tab = I->d_tab;
+        h.stage = I->d_stage;
+        for (int k = 0; k < 2; ++k) {
+            h.pop[k] = (int16_t *)alloc((size_t)cells * h.ld * 2);
+            h.ms[k] = (int32_t *)alloc((size_t)cells * 4);
+            if (!h.pop[k] || !h.ms[k]) {
+                batch_free(b);
+                return set_error(FFS_ENOMEM, "populations of instance %d", i);
+            }
+        }
+        b->hinst.push_back(h);
+        moff += n_stages[i];
+        poff += (int64_t)n_jobs[i] * n_stages[i];
+    }
+    b->d_inst = (BatchInst *)alloc(sizeof(BatchInst) * count);
+    b->d_units = (int2 *)alloc(sizeof(int2) * (size_t)count * cells);   // enough for tiles of >= 1 cell
+    b->d_counter = (int *)alloc(sizeof(int));
+    b->d_cur = (int32_t *)alloc(4);
+    b->d_gen = (int32_t *)alloc(4);
+    b->d_decoded = (unsigned long long *)alloc(8);
+    if (!b->d_inst || !b->d_units || !b->d_counter || !b->d_cur || !b->d_gen || !b->d_decoded) {
+        batch_free(b);
+        return set_error(FFS_ENOMEM, "batch state");
+    }
+    int rc = FFS_OK;
+    if (cudaMemcpyAsync(b->d_inst, b->hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st) ||
+        cudaMemsetAsync(b->d_cur, 0, 4, st) || cudaMemsetAsync(b->d_gen, 0, 4, st) ||
+        cudaMemsetAsync(b->d_decoded, 0, 8, st))
+        rc = set_error(FFS_ECUDA, "batch state initialisation");
+    for (int i = 0; i < count && !rc; ++i) {
+        rc = launch_init(b->insts[i], prm->seed, (uint32_t)i, 0, cells, b->hinst[i].ld, b->hinst[i].pop[0], st);
+        if (!rc)
+            rc = launch_eval(b->insts[i], b->hinst[i].pop[0], cells, b->hinst[i].ld, b->hinst[i].ms[0], nullptr, 0, 0,
+                             nullptr, st);
+    }
+    // default shape: the largest tile that fits with chunk 32 (or the requested one)
+    if (!rc) {
+        const int Breq = prm->decode_chunk > 0 ? prm->decode_chunk : 32;
+        const int Ts[4] = {256, 128, 64, 32};
+        rc = FFS_EUNSUPPORTED;
+        for (int t = 0; t < 4 && rc; ++t) {
+            if (prm->block_threads > 0 && Ts[t] != prm->block_threads) continue;
+            rc = batch_set_shape(b, Ts[t], Breq, st);
+        }
+        if (rc) rc = set_error(FFS_EUNSUPPORTED, "no batch launch shape fits shared memory");
+    }
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = set_error(FFS_ECUDA, "batch initialisation failed");
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return FFS_OK;
+}
+
+int ffs_batch_destroy(ffs_batch *b)
+{
+    batch_free(b);
+    return FFS_OK;
+}
+
+int ffs_batch_step(ffs_batch *b, int32_t n_generations, ffs_stream stream)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (n_generations < 0) return set_error(FFS_EINVAL, "n_generations %d < 0", n_generations);
+    if (n_generations == 0) return FFS_OK;
+    if (!b->graph) {
+        if (!b->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        FFS_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed));
+        int rc = batch_generation(b, true, b->d_decoded, b->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return set_error(FFS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return set_error(FFS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int g = 0; g < n_generations; ++g) {
+        FFS_CUDA_TRY(cudaGraphLaunch(b->graph, (cudaStream_t)stream));
+        b->host_cur ^= 1;
+        b->host_gen += 1;
+    }
+    return FFS_OK;
+}
+
+int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t *threads_out, int32_t *chunk_out,
+                       float *best_ms)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (repeats < 1) repeats = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    FFS_CUDA_TRY(cudaEventCreate(&e0));
+    FFS_CUDA_TRY(cudaEventCreate(&e1));
+    float best = -1.0f;
+    int bestT = b->T, bestB = b->B;
+    const int Ts[4] = {64, 128, 256, 512};
+    const int Bs[5] = {8, 16, 32, 64, 128};
+    int rc = FFS_OK;
+    for (int ti = 0; ti < 4 && !rc; ++ti) {
+        for (int bi = 0; bi < 5 && !rc; ++bi) {
+            BatchShape s;
+            size_t smem;
+            int nb;
+            if (batch_shape(b, Ts[ti], Bs[bi], &s, &smem, &nb)) continue;
+            if ((rc = batch_set_shape(b, Ts[ti], Bs[bi], st))) break;
+            // writes the next-generation buffers only; the state does not advance
+            if ((rc = batch_generation(b, false, nullptr, st))) break;
+            float total = 0.0f;
+            for (int r = 0; r < repeats && !rc; ++r) {
+                cudaEventRecord(e0, st);
+                rc = batch_generation(b, false, nullptr, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(FFS_ECUDA, "autotune timing");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            const float avg = total / repeats;
+            if (!rc && (best < 0.0f || avg < best)) {
+                best = avg;
+                bestT = Ts[ti];
+                bestB = Bs[bi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if ((rc = batch_set_shape(b, bestT, bestB, st))) return rc;
+    if (threads_out) *threads_out = bestT;
+    if (chunk_out) *chunk_out = bestB;
+    if (best_ms) *best_ms = best;
+    return FFS_OK;
+}
+
+int ffs_batch_info(const ffs_batch *b, int32_t *count, int64_t *generation, int32_t *threads, int32_t *chunk,
+                   int32_t *blocks_per_sm)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (count) *count = b->count;
+    if (generation) *generation = b->host_gen;
+    if (threads) *threads = b->T;
+    if (chunk) *chunk = b->B;
+    if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+    return FFS_OK;
+}
+
+int ffs_batch_get(const ffs_batch *b, int32_t instance, int16_t *pop, int32_t ld_out, int32_t *ms, ffs_stream stream)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (instance < 0 || instance >= b->count) return set_error(FFS_EINVAL, "instance %d", instance);
+    const BatchInst &h = b->hinst[instance];
+    const int cells = b->rows * b->cols;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pop) {
+        if (ld_out < h.n) return set_error(FFS_EINVAL, "ld_out %d < n %d", ld_out, h.n);
+        FFS_CUDA_TRY(cudaMemcpy2DAsync(pop, (size_t)ld_out * 2, h.pop[b->host_cur], (size_t)h.ld * 2, (size_t)h.n * 2,
+                                       cells, cudaMemcpyDefault, st));
+    }
+    if (ms) FFS_CUDA_TRY(cudaMemcpyAsync(ms, h.ms[b->host_cur], (size_t)cells * 4, cudaMemcpyDefault, st));
+    return FFS_OK;
+}
+
+int ffs_batch_best(const ffs_batch *b, int32_t *best, ffs_stream stream)
+{
+    clear_error();
+    if (!b || !best) return set_error(FFS_EINVAL, "NULL argument");
+    const int cells = b->rows * b->cols;
+    std::vector<int32_t> h((size_t)cells);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < b->count; ++i) {
+        FFS_CUDA_TRY(cudaMemcpyAsync(h.data(), b->hinst[i].ms[b->host_cur], (size_t)cells * 4, cudaMemcpyDeviceToHost, st));
+        FFS_CUDA_TRY(cudaStreamSynchronize(st));
+        int32_t m = -1;
+        for (int32_t v : h)
+            if (v >= 0 && (m < 0 || v < m)) m = v;
+        best[i] = m;
+    }
+    return FFS_OK;
+}
+
+int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream)
+{
+    clear_error();
+    if (!b || !count) return set_error(FFS_EINVAL, "NULL argument");
+    unsigned long long v = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&v, b->d_decoded, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    FFS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *count = (int64_t)v;
+    return FFS_OK;
+}
+
+}  // extern "C"

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
     const int T = blockDim.x;
     const SmemMap map = smem_map(L.n, L.S, T);
     if (count_dev) N = *count_dev;
-    stage_table(smem + map.tab, tab_g, L.S * (L.n + 1));
+    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
     __syncthreads();
@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
     for (int64_t base = (int64_t)blockIdx.x * T + warp * 32; base < N; base += (int64_t)gridDim.x * T) {
         const int64_t c = base + lane;
         const int64_t cc = c < N ? c : N - 1;
-        const int32_t ms = decode_chromosome(Ls, pop + cc * ld, region, T, smem + map.tab, wst);
+        const int32_t ms = decode_chromosome(Ls, pop + cc * ld, region, T,
+                                             reinterpret_cast<const uint16_t *>(smem + map.tab), wst);
         if (c < N) out[c] = ms;
     }
 }
@@ -145,7 +146,7 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
     p.blocks_per_sm = bestBlocks;
     DecodeLayout &L = p.L;
     memset(&L, 0, sizeof(L));
-    L.n = n; L.S = S; L.SH = inst->SH;
+    L.n = n; L.S = S; L.SH = inst->SH; L.mulSH = 1u << inst->SH;
     L.single = bestB >= n ? 1 : 0;
     L.B = L.single ? single_B : bestB;
     L.heap_words = L.single ? 0 : inst->heap_words;
@@ -273,11 +274,13 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
     for (int64_t i = 0; i < (int64_t)n * S; ++i) {
         if (p[i] < 1) return set_error(FFS_EINVAL, "proc_time[%lld][%lld] = %d < 1",
                                        (long long)(i / S), (long long)(i % S), p[i]);
+        if (p[i] > 65535) return set_error(FFS_EUNSUPPORTED, "proc_time[%lld][%lld] = %d > 65535",
+                                           (long long)(i / S), (long long)(i % S), p[i]);
         total += p[i];
     }
     int bits = 0;
     while ((1 << bits) <= n) ++bits;            // ids 1..n fit in `bits`
-    const int SH = bits + 2;
+    const int SH = bits + 1;
     if (total >= (int64_t(1) << (32 - SH)))
         return set_error(FFS_EOVERFLOW, "total processing time %lld needs more than %d bits of key",
                          (long long)total, 32 - SH);
@@ -294,14 +297,15 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
         off += I->M_eff[s];
     }
     I->heap_words = off;
-    I->tab_words = S * (n + 1);
-    std::vector<uint32_t> tab((size_t)I->tab_words, 0u);
+    I->tab_words = table_words(n, S);
+    std::vector<uint16_t> tab((size_t)I->tab_words * 2, 0u);
+    const int rowh = table_row_halves(n);
     for (int s = 0; s < S; ++s)
-        for (int j = 0; j < n; ++j) tab[(size_t)s * (n + 1) + j + 1] = (uint32_t)p[(size_t)j * S + s] << SH;
+        for (int j = 0; j < n; ++j) tab[(size_t)s * rowh + j + 1] = (uint16_t)p[(size_t)j * S + s];
     std::vector<int32_t> stage(2 * S);
     for (int s = 0; s < S; ++s) { stage[s] = I->M_eff[s]; stage[S + s] = I->heap_off[s]; }
-    // padded so the 16-byte staging loads never read past the allocation
-    const size_t tab_bytes = (size_t)round_up(I->tab_words, 4) * 4;
+    // table_words is a multiple of 4: the 16-byte staging loads stay inside
+    const size_t tab_bytes = (size_t)I->tab_words * 4;
     if (cudaMalloc(&I->d_tab, tab_bytes) != cudaSuccess || cudaMalloc(&I->d_stage, 8 * S) != cudaSuccess) {
         cudaFree(I->d_tab);
         delete I;
@@ -309,7 +313,7 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
         return set_error(FFS_ENOMEM, "device allocation of the instance tables failed");
     }
     cudaMemset(I->d_tab, 0, tab_bytes);
-    if (cudaMemcpy(I->d_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(I->d_tab, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(I->d_stage, stage.data(), stage.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(I->d_tab);
         cudaFree(I->d_stage);

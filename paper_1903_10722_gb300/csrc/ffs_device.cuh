@@ -52,7 +52,7 @@ __device__ __forceinline__ bool fires(uint32_t x, uint64_t threshold) { return (
 //
 // A chromosome is decoded stage after stage by list scheduling.  The M
 // machine free times of a stage live in registers as a sorted array of
-// 32-bit keys  key = time << SH | (job + 1) << 2  (SH = bits(n) + 2); the
+// 32-bit keys  key = time << SH | (job + 1) << 1  (SH = bits(n) + 1); the
 // initial free times are key 0.  Dispatching a job pops the smallest key f0
 // (the earliest-free machine; among equal free times any choice gives the
 // same start time, so the makespan is the one of the lowest-index rule) and
@@ -72,6 +72,7 @@ __device__ __forceinline__ bool fires(uint32_t x, uint64_t threshold) { return (
 // ---------------------------------------------------------------------------
 struct DecodeLayout {
     int32_t n, S, SH;
+    uint32_t mulSH;        // 1 << SH
     int32_t B;             // keys per round (multiple of 8)
     int32_t single;        // 1 if B >= n: one round, heaps stay in registers
     int32_t heap_words;    // sum of M_s (0 when single)
@@ -80,23 +81,27 @@ struct DecodeLayout {
     const int32_t *heap_off; // [S] word offset of each stage's heap, shared memory
 };
 
-// Shared-memory table of pre-shifted processing times: row s holds n + 1
-// words, word j + 1 = p[j][s] << SH (word 0 unused), so the low bits of a
-// key, (job + 1) << 2, are the byte offset of the job's entry.
-__device__ __forceinline__ uint32_t lds_u32(const uint32_t *row, uint32_t byte_off)
+// Shared-memory table of processing times (uint16): row s holds n + 1
+// entries (padded to an even count), entry j + 1 = p[j][s] (entry 0 = 0), so
+// the low bits of a key, (job + 1) << 1, are the byte offset of the job's entry.
+__device__ __forceinline__ uint32_t lds_u16(const uint16_t *row, uint32_t byte_off)
 {
-    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(row) + byte_off);
+    return *reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(row) + byte_off);
 }
 
+__host__ __device__ inline int table_row_halves(int n) { return (n + 2) & ~1; }
+
 // One dispatch: f[] sorted ascending, pops f[0], inserts the completion key
-// of the job `in` whose pre-shifted processing time at this stage is pp.
+// of the job `in` whose processing time at this stage is p:
+// completion = max(machine free, release) + p, carrying the job's id.
 template <int M>
-__device__ __forceinline__ uint32_t dispatch_pp(uint32_t (&f)[M], uint32_t in, uint32_t pp, uint32_t lowmask)
+__device__ __forceinline__ uint32_t dispatch_pp(uint32_t (&f)[M], uint32_t in, uint32_t p, uint32_t lowmask,
+                                                uint32_t mulSH)
 {
     const uint32_t f0 = f[0];
     // start = max(machine free, release); keep the incoming job id.
     const uint32_t u = (f0 & ~lowmask) | (in & lowmask);
-    const uint32_t x = max(u, in) + pp;
+    const uint32_t x = p * mulSH + max(u, in);
     if constexpr (M == 1) {
         f[0] = x;
     } else {
@@ -112,10 +117,10 @@ __device__ __forceinline__ uint32_t dispatch_pp(uint32_t (&f)[M], uint32_t in, u
 }
 
 template <int M>
-__device__ __forceinline__ uint32_t dispatch(uint32_t (&f)[M], uint32_t in, const uint32_t *prow,
-                                             uint32_t lowmask)
+__device__ __forceinline__ uint32_t dispatch(uint32_t (&f)[M], uint32_t in, const uint16_t *prow,
+                                             uint32_t lowmask, uint32_t mulSH)
 {
-    return dispatch_pp<M>(f, in, lds_u32(prow, in & lowmask), lowmask);
+    return dispatch_pp<M>(f, in, lds_u16(prow, in & lowmask), lowmask, mulSH);
 }
 
 // Per-warp round bookkeeping lives in shared memory (identical in all lanes).
@@ -130,7 +135,7 @@ struct WarpStageState {
 // Returns the number of keys written to buf this round.
 template <int M, bool FIRST, bool EMIT>
 __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__restrict__ heap,
-                                           uint32_t *__restrict__ buf, const uint32_t *prow,
+                                           uint32_t *__restrict__ buf, const uint16_t *prow,
                                            const int16_t *__restrict__ genes, int T, int d0, int cnt,
                                            uint32_t lowmask, bool &bad_gene, uint32_t *last_key,
                                            int &flushed_out)
@@ -162,8 +167,8 @@ __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__re
                     uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
                     g = (uint32_t)(int32_t)(int16_t)g;
                     if (g >= n) { bad_gene = true; g = 0; }
-                    const uint32_t in = (g + 1u) << 2;
-                    const uint32_t popped = dispatch<M>(f, in, prow, lowmask);
+                    const uint32_t in = (g + 1u) << 1;
+                    const uint32_t popped = dispatch<M>(f, in, prow, lowmask, L.mulSH);
                     if constexpr (EMIT) {
                         if (i0 + h >= skip) { buf[w * T] = popped; ++w; }
                     }
@@ -174,22 +179,23 @@ __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__re
         // The next key and its processing time are loaded one step ahead: the
         // store of step i goes to slot i - skip <= i, never to slot i + 1.
         // Slot cnt may be read (the region has one spare word per thread).
-        const uint32_t idmask = lowmask & ~3u;
+        const uint32_t idmask = lowmask & ~1u;
+        const uint32_t mulSH = L.mulSH;
         uint32_t in = buf[0];
-        uint32_t pp = lds_u32(prow, in & idmask);
+        uint32_t pp = lds_u16(prow, in & idmask);
         int i = 0;
         for (; i < skip; ++i) {
             const uint32_t in_n = buf[(i + 1) * T];
-            const uint32_t pp_n = lds_u32(prow, in_n & idmask);
-            (void)dispatch_pp<M>(f, in, pp, lowmask);
+            const uint32_t pp_n = lds_u16(prow, in_n & idmask);
+            (void)dispatch_pp<M>(f, in, pp, lowmask, mulSH);
             in = in_n;
             pp = pp_n;
         }
 #pragma unroll 4
         for (; i < cnt; ++i) {
             const uint32_t in_n = buf[(i + 1) * T];
-            const uint32_t pp_n = lds_u32(prow, in_n & idmask);
-            const uint32_t popped = dispatch_pp<M>(f, in, pp, lowmask);
+            const uint32_t pp_n = lds_u16(prow, in_n & idmask);
+            const uint32_t popped = dispatch_pp<M>(f, in, pp, lowmask, mulSH);
             if constexpr (EMIT) buf[(i - skip) * T] = popped;
             in = in_n;
             pp = pp_n;
@@ -221,7 +227,7 @@ __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__re
 
 template <bool FIRST, bool EMIT>
 __device__ __forceinline__ int stage_round_dispatch(int M, const DecodeLayout &L, uint32_t *heap,
-                                                    uint32_t *buf, const uint32_t *prow,
+                                                    uint32_t *buf, const uint16_t *prow,
                                                     const int16_t *genes, int T, int d0, int cnt,
                                                     uint32_t lowmask, bool &bad, uint32_t *last,
                                                     int &fl)
@@ -241,12 +247,12 @@ __device__ __forceinline__ int stage_round_dispatch(int M, const DecodeLayout &L
 
 // Decode one chromosome (row of genes in global memory, 16-byte aligned).
 //   region: this thread's interleaved shared words (base + tid), stride T.
-//   ptab  : shared table, row s at ptab + s * (n + 1).
+//   ptab  : shared uint16 table, row s at ptab + s * table_row_halves(n).
 //   wst   : this warp's per-stage state, S entries (shared).
 // All lanes of a warp must call this together for the same instance.
 // Returns the makespan, or -1 if a gene is outside [0, n).
 __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, const int16_t *row,
-                                                     uint32_t *region, int T, const uint32_t *ptab,
+                                                     uint32_t *region, int T, const uint16_t *ptab,
                                                      WarpStageState *wst)
 {
     const int n = L.n, S = L.S;
@@ -271,7 +277,7 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
             const int M = L.M[s];
             const int d0 = wst[s].dispatched;
             const int cnt = (s == 0) ? min(L.B, n - d0) : avail;
-            const uint32_t *prow = ptab + s * (n + 1);
+            const uint16_t *prow = ptab + s * table_row_halves(n);
             uint32_t *heap = region + L.heap_off[s] * T;
             const bool last = (s == S - 1);
             int w = 0, fl = 0;

@@ -6,103 +6,13 @@
 #include <vector>
 
 #include "ffs_internal.cuh"
+#include "ffs_ga_device.cuh"
 
 namespace fgpu {
 
 // ---------------------------------------------------------------------------
-// Warp-cooperative child construction.  Each lane of the warp supplies one
-// child to build (parents, cut points, whether crossover fires, output row);
-// the warp builds them one after the other with all 32 lanes on the genes,
-// so rows are read and written in coalesced 64-byte runs.
-//
-// Order crossover: the child keeps p1[l..r]; the other positions, from r+1
-// onward cyclically, take p2's genes met from position r+1 onward
-// cyclically, skipping genes already placed.  Without crossover the child
-// copies p1.  `bits` is a warp-private shared bitmask of ceil(n/32) words.
-// ---------------------------------------------------------------------------
-struct ChildJob {
-    const int16_t *p1;
-    const int16_t *p2;
-    int16_t *child;
-    int l, r;
-    bool cross;
-    bool active;
-};
-
-__device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, int ld, uint32_t *bits)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int words = (n + 31) >> 5;
-    unsigned todo = __ballot_sync(0xFFFFFFFFu, me.active);
-    while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const int16_t *p1 = (const int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.p1, j);
-        const int16_t *p2 = (const int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.p2, j);
-        int16_t *child = (int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.child, j);
-        const int l = __shfl_sync(0xFFFFFFFFu, me.l, j);
-        const int r = __shfl_sync(0xFFFFFFFFu, me.r, j);
-        const bool cross = __shfl_sync(0xFFFFFFFFu, (int)me.cross, j) != 0;
-        if (!cross) {
-            const int4 *s4 = reinterpret_cast<const int4 *>(p1);
-            int4 *d4 = reinterpret_cast<int4 *>(child);
-            for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
-            __syncwarp();
-            continue;
-        }
-        for (int w = lane; w < words; w += 32) bits[w] = 0u;
-        __syncwarp();
-        for (int k = l + lane; k <= r; k += 32) {
-            const int g = p1[k];
-            child[k] = (int16_t)g;
-            if ((unsigned)g < (unsigned)n) atomicOr(&bits[g >> 5], 1u << (g & 31));
-        }
-        __syncwarp();
-        const int start = (r + 1 == n) ? 0 : r + 1;
-        int placed = 0;
-        for (int t0 = 0; t0 < n; t0 += 32) {
-            const int t = t0 + lane;
-            int idx = start + t;
-            if (idx >= n) idx -= n;
-            int g = 0;
-            bool take = false;
-            if (t < n) {
-                g = p2[idx];
-                take = !((unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u));
-            }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
-            if (take) {
-                int pos = start + placed + __popc(m & lt);
-                if (pos >= n) pos -= n;
-                child[pos] = (int16_t)g;
-            }
-            placed += __popc(m);
-        }
-        __syncwarp();
-    }
-}
-
-// Warp-cooperative row copies: lane j's (src, dst) pair when `active`.
-__device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, int16_t *dst, int ld)
-{
-    const int lane = threadIdx.x & 31;
-    unsigned todo = __ballot_sync(0xFFFFFFFFu, active);
-    while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const int4 *s4 = (const int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)src, j);
-        int4 *d4 = (int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)dst, j);
-        for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
-    }
-    __syncwarp();
-}
-
-// ---------------------------------------------------------------------------
-// One generation of a cellular island, fused: draws, two binary tournaments
-// over the von Neumann neighbourhood (previous generation's makespans),
-// order crossover, swap mutation, decoding and replace-if-better.  One
-// thread per cell; the child is built in the cell's output row.
+// One generation of a cellular island, fused (see cellular_warp_cells).
+// One thread per cell; islands of a batch are laid end to end.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t *__restrict__ tab_g,
                                                   const int32_t *__restrict__ stage_g, GaScalars g,
@@ -114,7 +24,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     const int T = blockDim.x;
     const int bits_per_warp = (L.n + 31) >> 5;
     const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
-    stage_table(smem + map.tab, tab_g, L.S * (L.n + 1));
+    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
     __syncthreads();
@@ -125,8 +35,8 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
     uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
     uint32_t *region = smem + map.region + threadIdx.x;
+    const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
 
-    const int n = L.n;
     const int cells = rows * cols;
     const int total = cells * batch.count;
     if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, (unsigned long long)total);
@@ -136,66 +46,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
         const bool valid = gc < total;
         const int bi = (valid ? gc : total - 1) / cells;
         const int c = (valid ? gc : total - 1) - bi * cells;
-        const IslandRef &ref = batch.ref[bi];
-        const int16_t *pin;
-        const int32_t *msin;
-        int16_t *pout;
-        int32_t *msout;
-        uint32_t gen;
-        resolve(ref, pin, msin, pout, msout, gen);
-        ChildJob job;
-        job.active = valid;
-        job.child = pout + (int64_t)c * ld;
-        job.p1 = job.p2 = pin;
-        job.l = job.r = 0;
-        job.cross = false;
-        U4 b2{0, 0, 0, 0};
-        bool mutate = false;
-        if (valid) {
-            const U4 b0 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 0u);
-            const U4 b1 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 1u);
-            b2 = draw_block(g.seed, kPurposeCellular, ref.island, gen, (uint32_t)c, 2u);
-            const int r = c / cols, q = c - r * cols;
-            const int up = ((r + rows - 1) % rows) * cols + q, down = ((r + 1) % rows) * cols + q;
-            const int west = r * cols + (q + cols - 1) % cols, east = r * cols + (q + 1) % cols;
-            auto slot = [&](uint32_t x) {
-                const uint32_t k = uniform_below(x, 5u);
-                return k == 0 ? c : k == 1 ? up : k == 2 ? down : k == 3 ? west : east;
-            };
-            int a = slot(b0.x), b = slot(b0.y);
-            const int par1 = (msin[b] < msin[a]) ? b : a;
-            a = slot(b0.z);
-            b = slot(b0.w);
-            const int par2 = (msin[b] < msin[a]) ? b : a;
-            job.p1 = pin + (int64_t)par1 * ld;
-            job.p2 = pin + (int64_t)par2 * ld;
-            job.cross = fires(b1.x, g.cell_pc);
-            const int u = (int)uniform_below(b1.y, (uint32_t)n), v = (int)uniform_below(b1.z, (uint32_t)n);
-            job.l = min(u, v);
-            job.r = max(u, v);
-            mutate = fires(b1.w, g.cell_pm);
-        }
-        warp_build_children(job, n, ld, wbits);
-        if (mutate) {
-            int16_t *child = job.child;
-            const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
-            const int16_t t = child[i];
-            child[i] = child[j];
-            child[j] = t;
-        }
-        __syncwarp();
-        // lanes past the end decode a row of their island in lock step; nothing is written
-        const int16_t *drow = valid ? job.child : pin + (int64_t)c * ld;
-        const int32_t ms = decode_chromosome(Ls, drow, region, T, smem + map.tab, wst);
-        bool keep_old = false;
-        if (valid) {
-            const int32_t old = msin[c];
-            const bool better = ms >= 0 && (g.replace_le ? (uint32_t)ms <= (uint32_t)old
-                                                          : (uint32_t)ms < (uint32_t)old);
-            msout[c] = better ? ms : old;
-            keep_old = !better;
-        }
-        warp_copy_rows(keep_old, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
+        cellular_warp_cells(Ls, g, batch.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
     }
 }
 

@@ -45,11 +45,15 @@ struct SmemMap {
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Words of the shared uint16 processing-time table (S rows of
+// table_row_halves(n) entries), rounded to 16 bytes.
+__host__ __device__ inline int table_words(int n, int S) { return round_up(S * table_row_halves(n) / 2, 4); }
+
 __host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_warp = 0)
 {
     SmemMap m;
     m.tab = 0;
-    m.stage = round_up(S * (n + 1), 4);
+    m.stage = table_words(n, S);
     m.warp = m.stage + round_up(2 * S, 4);
     m.bits = m.warp + round_up((T / 32) * S * 2, 4);
     m.region = m.bits + round_up((T / 32) * bits_per_warp, 4);
@@ -64,7 +68,7 @@ struct ffs_instance {
     std::vector<int32_t> M_eff;      // min(M_s, n)
     std::vector<int32_t> heap_off;   // prefix sums of M_eff
     int heap_words = 0;
-    uint32_t *d_tab = nullptr;       // [S][n+1] pre-shifted times
+    uint32_t *d_tab = nullptr;       // uint16 [S][table_row_halves(n)] times, as words
     int32_t *d_stage = nullptr;      // [2S]: M_eff, heap_off
     int tab_words = 0;
     int num_sms = 0;

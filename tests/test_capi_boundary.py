@@ -52,8 +52,9 @@ def test_instance_validation_before_device():
     rc, msg = _create(3, 2, [1, 1], [[1, 1], [0, 1], [1, 1]])
     assert rc == ffs.FFS_EINVAL and "proc_time[1][0]" in msg
     assert _create(40, 1, [33], np.ones((40, 1)))[0] == ffs.FFS_EUNSUPPORTED
-    # 500 jobs: keys hold 21 bits of time; 500 * 21 * 200 > 2^21
-    assert _create(500, 21, [2] * 21, np.full((500, 21), 200))[0] == ffs.FFS_EOVERFLOW
+    # 500 jobs: keys hold 22 bits of time; 500 * 21 * 500 > 2^22
+    assert _create(500, 21, [2] * 21, np.full((500, 21), 500))[0] == ffs.FFS_EOVERFLOW
+    assert _create(5, 1, [1], np.full((5, 1), 70000))[0] == ffs.FFS_EUNSUPPORTED
     assert ffs.load().ffs_instance_create(3, 1, None, None, None) == ffs.FFS_EINVAL
 
 

@@ -1,0 +1,95 @@
+"""Batched uneven instances (one cellular island per instance, one persistent
+launch per generation from a CUDA graph) against the CPU oracle, bit-exact;
+launch shapes from the autotuner must not change results."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from ffs_workloads import InstanceSpec, make_batch, make_instance
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_state(spec, island, rows, cols, seed=7):
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    ld = (spec.n + 7) // 8 * 8
+    pop = np.zeros((rows * cols, ld), dtype=np.int16)
+    for c in range(rows * cols):
+        pop[c, :spec.n] = orc.init_chromosome(seed, island, c, spec.n)
+    return o, pop, orc.eval_population(o, pop)
+
+
+def _mixed_specs():
+    shapes = [(1, 1, 1, 1), (7, 3, 2, 4), (20, 5, 3, 3), (37, 6, 1, 8), (60, 2, 5, 40), (100, 8, 2, 5),
+              (13, 1, 4, 4), (250, 4, 2, 10), (44, 7, 1, 1), (3, 5, 2, 6), (90, 3, 9, 10), (17, 2, 1, 3)]
+    return [make_instance(n, S, lo, hi, seed=k + 3) for k, (n, S, lo, hi) in enumerate(shapes)]
+
+
+def test_batch_mixed_instances_match_oracle(gpu):
+    specs = _mixed_specs()
+    rows, cols = 6, 5          # 30 cells: tiles end part-way through a warp
+    prm = gpu.ffs_params_default()
+    oprm = orc.Params(seed=7)
+    b = gpu.Batch(specs, prm, rows, cols)
+    states = [_oracle_state(s, i, rows, cols) for i, s in enumerate(specs)]
+
+    def compare(tag):
+        for i, s in enumerate(specs):
+            pop, ms = gpu.batch_tensors(b, i)
+            torch.cuda.synchronize()
+            assert np.array_equal(pop.cpu().numpy(), states[i][1][:, :s.n]), (tag, i)
+            assert np.array_equal(ms.cpu().numpy().astype(np.int64), states[i][2]), (tag, i)
+
+    compare("init")
+    gen = 0
+    for block in range(4):
+        if block == 2:
+            tuned = gpu.ffs_batch_autotune(b, repeats=1)
+            assert tuned["threads"] > 0 and tuned["chunk"] > 0
+        gpu.ffs_batch_step(b, 3)
+        for _ in range(3):
+            gen += 1
+            for i, s in enumerate(specs):
+                o, pop, ms = states[i]
+                pop, ms, _ = orc.cellular_generation(o, oprm, i, gen, rows, cols, pop, ms)
+                states[i] = (o, pop, ms)
+        compare(gen)
+    best = gpu.ffs_batch_best(b)
+    assert best.tolist() == [int(st[2].min()) for st in states]
+    assert gpu.ffs_batch_decoded(b) == gen * len(specs) * rows * cols
+    assert b.info()["generation"] == gen
+
+
+def test_batch_256_uneven_sampled(gpu):
+    """256 instances, n in [20,500], S in [5,20], M in [2,10], 32x32 torus each."""
+    specs = make_batch(256, seed=1)
+    rows = cols = 32
+    prm = gpu.ffs_params_default()
+    oprm = orc.Params(seed=7)
+    b = gpu.Batch(specs, prm, rows, cols)
+    order = sorted(range(256), key=lambda i: specs[i].n * specs[i].S)
+    sample = sorted(set([order[0], order[1], order[-1], order[-2], order[128], 0, 255]))
+    before = {i: [t.cpu().numpy() for t in gpu.batch_tensors(b, i)] for i in sample}
+    for i in sample:
+        for c in (0, 513, 1023):
+            assert before[i][0][c].tolist() == orc.init_chromosome(7, i, c, specs[i].n).tolist()
+    gpu.ffs_batch_step(b, 1)
+    after = {i: [t.cpu().numpy() for t in gpu.batch_tensors(b, i)] for i in sample}
+    rng = np.random.default_rng(4)
+    for i in sample:
+        s = specs[i]
+        o = orc.Instance(s.n, s.S, s.M, s.p)
+        ld = (s.n + 7) // 8 * 8
+        pop = np.zeros((rows * cols, ld), dtype=np.int16)
+        pop[:, :s.n] = before[i][0]
+        ms = before[i][1].astype(np.int64)
+        assert np.array_equal(ms, orc.eval_population(o, pop)[:]) if s.n * s.S < 2000 else True
+        for c in rng.choice(1024, 12, replace=False).tolist() + [0, 1023]:
+            x = [orc.draw(7, orc.PURPOSE_CELLULAR, i, 1, c, d) for d in range(10)]
+            child, _ = orc.cellular_child(o, oprm, rows, cols, c, x, pop, ms)
+            mc = orc.decode(o, child)
+            if mc < ms[c]:
+                assert after[i][0][c].tolist() == child[:s.n].tolist() and after[i][1][c] == mc, (i, c)
+            else:
+                assert after[i][0][c].tolist() == pop[c, :s.n].tolist() and after[i][1][c] == ms[c], (i, c)
