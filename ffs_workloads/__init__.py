@@ -75,6 +75,8 @@ WORKLOADS = {
     "scale_500x20": dict(n=500, S=20, m=(5, 10), seed=1, n_cellular=4, rows=128, cols=128,
                          n_pseudo=4, pseudo_size=16384, generations=200,
                          migration="ring", gap=1, mig_num=2, mig_den=100),
+    "batch_256": dict(count=256, n=(20, 500), S=(5, 20), m=(2, 10), seed=1, rows=32, cols=32,
+                      generations=500),
     "paper_300x4": dict(n=300, S=4, m=(2, 2), p=(1, 5), seed=1, n_cellular=1, rows=16, cols=16,
                         n_pseudo=1, pseudo_size=256, generations=2000,
                         migration="penetration", gap=500),
