@@ -21,7 +21,7 @@ def _oracle_state(spec, island, rows, cols, seed=7):
 
 
 def _mixed_specs():
-    shapes = [(1, 1, 1, 1), (7, 3, 2, 4), (20, 5, 3, 3), (37, 6, 1, 8), (60, 2, 5, 40), (100, 8, 2, 5),
+    shapes = [(1, 1, 1, 1), (7, 3, 2, 4), (20, 5, 3, 3), (37, 6, 1, 8), (60, 2, 5, 32), (100, 8, 2, 5),
               (13, 1, 4, 4), (250, 4, 2, 10), (44, 7, 1, 1), (3, 5, 2, 6), (90, 3, 9, 10), (17, 2, 1, 3)]
     return [make_instance(n, S, lo, hi, seed=k + 3) for k, (n, S, lo, hi) in enumerate(shapes)]
 
