@@ -308,6 +308,47 @@ int ffs_batch_get(const ffs_batch *b, int32_t instance, int16_t *pop, int32_t ld
 int ffs_batch_best(const ffs_batch *b, int32_t *best, ffs_stream stream);
 int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Surrogate network (the paper has no surrogate: this is the library's
+ * learned pre-screen of oversampled offspring, whose exact makespans still
+ * come only from the decoder).
+ *
+ * ffs_gemm_bf16: D[M][N] (FP32, row stride ldd, 16-byte aligned) =
+ * A[M][K] * B[N][K]^T with A, B BF16 (uint16 bit patterns), K-major rows
+ * (strides lda, ldb in elements, multiples of 8, 16-byte aligned bases);
+ * N a multiple of 64; rows of A past M and columns past K read as zero.
+ * Runs on the 5th-generation tensor cores (TMA -> shared memory ->
+ * tcgen05.mma -> tensor memory).  err: device int32 that a kernel sets to a
+ * non-zero code if one of its bounded waits gave up.  Asynchronous.
+ *
+ * ffs_mlp: y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 with BF16 weights and
+ * activations and FP32 accumulation.  in_dim <= 4096; h1, h2 multiples of
+ * 64 in [64, 1024]; batches up to max_batch (a multiple of 128).
+ *   set_params/get take host FP32 arrays W1[h1][in_dim], b1[h1],
+ *   W2[h2][h1], b2[h2], w3[h2], b3 (get with grads = 1 returns the last
+ *   training step's gradients); both synchronise the device.
+ *   forward: x device BF16 [B][ldx] (ldx >= in_dim, multiple of 8), y
+ *   device FP32 [B].  train_step: one Adam step (beta 0.9/0.999, eps 1e-8)
+ *   on the mean squared error to target (device FP32 [B]); B a multiple of
+ *   128; loss (device FP32, may be NULL) receives the batch MSE.
+ *   ffs_mlp_check synchronises and returns FFS_ETIMEOUT if a tensor-core
+ *   wait gave up since the last check.
+ * ---------------------------------------------------------------------- */
+typedef struct ffs_mlp ffs_mlp;
+int ffs_gemm_bf16(const uint16_t *A, int32_t lda, const uint16_t *B, int32_t ldb, float *D, int32_t ldd,
+                  int32_t M, int32_t N, int32_t K, int32_t *err, ffs_stream stream);
+int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ffs_mlp **out);
+int ffs_mlp_destroy(ffs_mlp *mlp);
+int ffs_mlp_input_width(const ffs_mlp *mlp);
+int ffs_mlp_set_params(ffs_mlp *mlp, const float *W1, const float *b1, const float *W2, const float *b2,
+                       const float *w3, float b3);
+int ffs_mlp_get(const ffs_mlp *mlp, int32_t grads, float *W1, float *b1, float *W2, float *b2, float *w3,
+                float *b3);
+int ffs_mlp_forward(ffs_mlp *mlp, const uint16_t *x, int32_t ldx, int32_t B, float *y, ffs_stream stream);
+int ffs_mlp_train_step(ffs_mlp *mlp, const uint16_t *x, int32_t ldx, const float *target, int32_t B, float lr,
+                       float *loss, ffs_stream stream);
+int ffs_mlp_check(ffs_mlp *mlp, ffs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,90 @@
+"""Surrogate network oracle -- TEST INFRASTRUCTURE ONLY (plain numpy, float64).
+
+The network maps a chromosome's feature vector x (in_dim values) to a
+predicted normalised makespan: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2),
+y = w3 . h2 + b3, trained on the mean squared error with Adam (Kingma & Ba,
+"Adam: A Method for Stochastic Optimization", 2015).
+
+`rounded=True` reproduces where the GPU path stores BF16 values: the input,
+W1, W2 and both hidden activations are rounded to BF16 (round to nearest
+even), everything else is exact (float64 here; FP32 accumulation on the GPU).
+The gradients are those of that function with the hidden activations'
+rounding treated as identity (straight-through), plus BF16 rounding of the
+backpropagated hidden-layer signals, which is where the GPU rounds them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round float32 values to the nearest BF16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    out = u.astype(np.uint32).view(np.float32).astype(np.float64)
+    nan = np.isnan(f)
+    out[nan] = np.nan
+    return out
+
+
+def init_params(in_dim: int, h1: int, h2: int, seed: int = 0) -> dict:
+    """He-style uniform initialisation, drawn with numpy (an input, not the method)."""
+    rng = np.random.default_rng(seed)
+
+    def u(shape, fan_in):
+        lim = np.sqrt(6.0 / fan_in)
+        return rng.uniform(-lim, lim, size=shape).astype(np.float32)
+    return {"W1": u((h1, in_dim), in_dim), "b1": np.zeros(h1, np.float32),
+            "W2": u((h2, h1), h1), "b2": np.zeros(h2, np.float32),
+            "w3": u((h2,), h2) * 0.1, "b3": np.float32(0.0)}
+
+
+def forward(params: dict, X, rounded: bool = True):
+    X = np.asarray(X, dtype=np.float64)
+    r = bf16_round if rounded else (lambda a: np.asarray(a, dtype=np.float64))
+    Xr = r(X)
+    W1, W2 = r(params["W1"]), r(params["W2"])
+    Z1 = Xr @ W1.T + np.asarray(params["b1"], np.float64)
+    H1 = r(np.maximum(Z1, 0.0))
+    Z2 = H1 @ W2.T + np.asarray(params["b2"], np.float64)
+    H2 = r(np.maximum(Z2, 0.0))
+    y = H2 @ np.asarray(params["w3"], np.float64) + float(params["b3"])
+    return y, {"X": Xr, "W1": W1, "W2": W2, "H1": H1, "H2": H2, "Z1": Z1, "Z2": Z2}
+
+
+def loss_and_grads(params: dict, X, t, rounded: bool = True):
+    """MSE loss and its gradients with respect to every parameter."""
+    y, c = forward(params, X, rounded)
+    t = np.asarray(t, dtype=np.float64)
+    B = len(t)
+    e = y - t
+    loss = float(np.mean(e * e))
+    dy = 2.0 * e / B
+    r = bf16_round if rounded else (lambda a: np.asarray(a, dtype=np.float64))
+    w3 = np.asarray(params["w3"], np.float64)
+    gw3 = c["H2"].T @ dy
+    gb3 = dy.sum()
+    dZ2 = r(np.outer(dy, w3) * (c["H2"] > 0))
+    gW2 = dZ2.T @ c["H1"]
+    gb2 = dZ2.sum(axis=0)
+    dH1 = dZ2 @ c["W2"]
+    dZ1 = dH1 * (c["H1"] > 0)
+    gW1 = r(dZ1).T @ c["X"]
+    gb1 = dZ1.sum(axis=0)
+    return loss, {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2, "w3": gw3, "b3": gb3}
+
+
+def adam_step(params: dict, grads: dict, state: dict, lr: float, b1: float = 0.9, b2: float = 0.999,
+              eps: float = 1e-8) -> dict:
+    """One Adam update (in float64); state holds m, v and t."""
+    t = state.get("t", 0) + 1
+    out = {}
+    for k, g in grads.items():
+        m = b1 * state.get(("m", k), 0.0) + (1 - b1) * np.asarray(g, np.float64)
+        v = b2 * state.get(("v", k), 0.0) + (1 - b2) * np.asarray(g, np.float64) ** 2
+        state[("m", k)], state[("v", k)] = m, v
+        out[k] = np.asarray(params[k], np.float64) - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+    state["t"] = t
+    return out

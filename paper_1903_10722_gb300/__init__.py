@@ -85,6 +85,15 @@ _SIGS = [
     ("ffs_batch_get", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
     ("ffs_batch_best", _i32, [_vp, _vp, _vp]),
     ("ffs_batch_decoded", _i32, [_vp, _vp, _vp]),
+    ("ffs_gemm_bf16", _i32, [_vp, _i32, _vp, _i32, _vp, _i32, _i32, _i32, _i32, _vp, _vp]),
+    ("ffs_mlp_create", _i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
+    ("ffs_mlp_destroy", _i32, [_vp]),
+    ("ffs_mlp_input_width", _i32, [_vp]),
+    ("ffs_mlp_set_params", _i32, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_float]),
+    ("ffs_mlp_get", _i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_mlp_forward", _i32, [_vp, _vp, _i32, _i32, _vp, _vp]),
+    ("ffs_mlp_train_step", _i32, [_vp, _vp, _i32, _vp, _i32, ctypes.c_float, _vp, _vp]),
+    ("ffs_mlp_check", _i32, [_vp, _vp]),
 ]
 
 
@@ -411,3 +420,61 @@ def batch_tensors(b: Batch, instance: int):
     ms = torch.empty(cells, dtype=torch.int32, device="cuda")
     ffs_batch_get(b, instance, pop, n, ms)
     return pop, ms
+
+
+# ---------------------------------------------------------------------------
+# Surrogate network (tensor-core GEMM and MLP)
+# ---------------------------------------------------------------------------
+def ffs_gemm_bf16(A, lda: int, B, ldb: int, D, ldd: int, M: int, N: int, K: int, err, stream=None):
+    """D = A B^T on the tensor cores (A, B bf16 tensors, D fp32, err int32 device scalar)."""
+    _check(load().ffs_gemm_bf16(_ptr(A), lda, _ptr(B), ldb, _ptr(D), ldd, M, N, K, _ptr(err), _stream(stream)))
+
+
+class MLP:
+    """Owner of an ffs_mlp handle."""
+
+    def __init__(self, in_dim: int, h1: int, h2: int, max_batch: int):
+        h = _vp()
+        _check(load().ffs_mlp_create(in_dim, h1, h2, max_batch, ctypes.byref(h)))
+        self.handle = h
+        self.in_dim, self.h1, self.h2, self.max_batch = in_dim, h1, h2, max_batch
+        self.width = int(load().ffs_mlp_input_width(h))
+
+    def set_params(self, p: dict):
+        import numpy as np
+        arrs = [np.ascontiguousarray(p[k], dtype=np.float32) for k in ("W1", "b1", "W2", "b2", "w3")]
+        _check(load().ffs_mlp_set_params(self.handle, *[a.ctypes.data for a in arrs], float(p["b3"])))
+
+    def get(self, grads: bool = False) -> dict:
+        import numpy as np
+        out = {"W1": np.zeros((self.h1, self.in_dim), np.float32), "b1": np.zeros(self.h1, np.float32),
+               "W2": np.zeros((self.h2, self.h1), np.float32), "b2": np.zeros(self.h2, np.float32),
+               "w3": np.zeros(self.h2, np.float32)}
+        b3 = ctypes.c_float()
+        _check(load().ffs_mlp_get(self.handle, int(grads), *[out[k].ctypes.data for k in ("W1", "b1", "W2", "b2", "w3")],
+                                  ctypes.byref(b3)))
+        out["b3"] = np.float32(b3.value)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ffs_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ffs_mlp_forward(m: MLP, x, ldx: int, B: int, y, stream=None):
+    _check(load().ffs_mlp_forward(m.handle, _ptr(x), ldx, B, _ptr(y), _stream(stream)))
+
+
+def ffs_mlp_train_step(m: MLP, x, ldx: int, target, B: int, lr: float, loss=None, stream=None):
+    _check(load().ffs_mlp_train_step(m.handle, _ptr(x), ldx, _ptr(target), B, lr, _ptr(loss), _stream(stream)))
+
+
+def ffs_mlp_check(m: MLP, stream=None):
+    _check(load().ffs_mlp_check(m.handle, _stream(stream)))

@@ -1,0 +1,615 @@
+// ffs_mlp.cu -- the surrogate network: a BF16 GEMM on the 5th-generation
+// tensor cores (TMA -> shared memory -> tcgen05.mma -> TMEM -> registers)
+// and the small MLP built on it (in -> h1 -> h2 -> 1, ReLU, BF16 weights and
+// activations, FP32 accumulation), trained online with Adam on MSE.
+//
+// Every GEMM here is D[M][N] = A[M][K] * B[N][K]^T with both operands
+// K-major (rows of K contiguous BF16); the backward pass transposes its
+// operands into that layout with small CUDA-core kernels.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ffs_internal.cuh"
+#include "ffs_tc.cuh"
+
+namespace fgpu {
+
+constexpr int kGemmStages = 4;
+constexpr int kBM = 128, kBK = 64;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
+
+struct GemmEpi {
+    float *D;                 // mode 0: FP32 output [M][ldd]
+    __nv_bfloat16 *Db;        // mode 1: BF16 relu(acc + bias) [M][ldd]
+    const float *bias;        // mode 1: [N]
+    int ldd;
+    int M_valid;
+    int mode;
+    int *err;                 // set to a non-zero code if a wait timed out
+};
+
+template <int BN>
+struct GemmSmem {
+    static constexpr uint32_t A_BYTES = kBM * kBK * 2;
+    static constexpr uint32_t B_BYTES = BN * kBK * 2;
+    static constexpr uint32_t TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr size_t BYTES = 1024 + kGemmStages * (A_BYTES + B_BYTES) + 256;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
+                                                       const __grid_constant__ CUtensorMap tmB, int K, GemmEpi epi)
+{
+    using SM = GemmSmem<BN>;
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ int s_fail;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + kGemmStages * SM::A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kGemmStages * SM::B_BYTES);
+    uint64_t *empty = full + kGemmStages;
+    uint64_t *done = empty + kGemmStages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int KC = K / kBK;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGemmStages; ++s) {
+            tc::mbar_init(full + s, 1);
+            tc::mbar_init(empty + s, 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_fence_init();
+        s_fail = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, SM::TCOLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kc = 0; kc < KC; ++kc) {
+            const int s = kc % kGemmStages;
+            if (kc >= kGemmStages && !tc::mbar_wait(empty + s, ((kc / kGemmStages) - 1) & 1, kWaitLimitNs)) {
+                s_fail = 1;
+                break;
+            }
+            tc::mbar_expect_tx(full + s, SM::A_BYTES + SM::B_BYTES);
+            tc::tma_load_2d(sA + s * SM::A_BYTES, &tmA, kc * kBK, m0, full + s);
+            tc::tma_load_2d(sB + s * SM::B_BYTES, &tmB, kc * kBK, n0, full + s);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: 4 MMAs of K = 16 per 64-wide chunk
+        const uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+        for (int kc = 0; kc < KC; ++kc) {
+            const int s = kc % kGemmStages;
+            if (!tc::mbar_wait(full + s, (kc / kGemmStages) & 1, kWaitLimitNs)) {
+                s_fail = 2;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(sA + s * SM::A_BYTES), b0 = tc::smem_u32(sB + s * SM::B_BYTES);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+                tc::mma_bf16(tmem, tc::sdesc_k_sw128(a0 + 32u * k), tc::sdesc_k_sw128(b0 + 32u * k), idesc,
+                             kc > 0 || k > 0);
+            tc::mma_commit(empty + s);
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+    const bool ok = tc::mbar_wait(done, 0, kWaitLimitNs);
+    if (!ok) s_fail = 3;
+    tc::fence_after_sync();
+
+    // epilogue: warp w owns accumulator rows 32w .. 32w+31 (its TMEM lanes)
+    const int row = m0 + warp * 32 + lane;
+    const bool write = ok && row < epi.M_valid;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        if (!write) continue;
+        if (epi.mode == 0) {
+            float4 *dst = reinterpret_cast<float4 *>(epi.D + (size_t)row * epi.ldd + n0 + c);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+            uint32_t packed[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float x0 = fmaxf(v[2 * q] + epi.bias[n0 + c + 2 * q], 0.0f);
+                const float x1 = fmaxf(v[2 * q + 1] + epi.bias[n0 + c + 2 * q + 1], 0.0f);
+                const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                packed[q] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(epi.Db + (size_t)row * epi.ldd + n0 + c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, SM::TCOLS);
+    if (threadIdx.x == 0 && s_fail) atomicExch(epi.err, s_fail);
+}
+
+// ---------------------------------------------------------------------------
+// Host: tensor maps and the GEMM launcher.
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// BF16 matrix [rows][ld] with `cols` valid columns, tiles of box_rows x 64.
+static int make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld, int box_rows)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(FFS_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    if (((uintptr_t)ptr & 15u) || (ld % 8)) return set_error(FFS_EINVAL, "GEMM operand must be 16-byte aligned, ld % 8 == 0");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FFS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FFS_OK;
+}
+
+template <int BN>
+static int launch_gemm_bn(const CUtensorMap &ta, const CUtensorMap &tb, int Mtiles, int N, int K, const GemmEpi &epi,
+                          cudaStream_t st)
+{
+    const size_t smem = GemmSmem<BN>::BYTES;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(Mtiles, N / BN);
+    k_gemm_bf16<BN><<<grid, 128, smem, st>>>(ta, tb, K, epi);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// D = A[M][K] * B[N][K]^T.  A rows beyond M read as zero (TMA fill); K is
+// rounded up to 64 with zero columns beyond Kvalid; N a multiple of 64.
+int gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int Kvalid, GemmEpi epi, cudaStream_t st)
+{
+    if (M < 1 || N < 64 || N % 64 || Kvalid < 1) return set_error(FFS_EINVAL, "GEMM shape M=%d N=%d K=%d", M, N, Kvalid);
+    const int K = round_up(Kvalid, kBK);
+    const int BN = (N % 256 == 0) ? 256 : (N % 192 == 0) ? 192 : (N % 128 == 0) ? 128 : 64;
+    CUtensorMap ta, tb;
+    int rc = make_map(&ta, A, M, Kvalid, lda, kBM);
+    if (rc) return rc;
+    if ((rc = make_map(&tb, B, N, Kvalid, ldb, BN))) return rc;
+    epi.M_valid = M;
+    const int Mtiles = (M + kBM - 1) / kBM;
+    switch (BN) {
+    case 256: return launch_gemm_bn<256>(ta, tb, Mtiles, N, K, epi, st);
+    case 192: return launch_gemm_bn<192>(ta, tb, Mtiles, N, K, epi, st);
+    case 128: return launch_gemm_bn<128>(ta, tb, Mtiles, N, K, epi, st);
+    default: return launch_gemm_bn<64>(ta, tb, Mtiles, N, K, epi, st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core kernels of the MLP (elementwise, reductions, transposes, Adam).
+// ---------------------------------------------------------------------------
+__global__ void k_f32_to_bf16_padded(const float *src, int rows, int cols, int ld_src, __nv_bfloat16 *dst, int ld_dst)
+{
+    const int r = blockIdx.y;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ld_dst; c += gridDim.x * blockDim.x)
+        dst[(size_t)r * ld_dst + c] = __float2bfloat16_rn(c < cols ? src[(size_t)r * ld_src + c] : 0.0f);
+}
+
+// dst[c][r] = src[r][c] for a BF16 [rows][cols] matrix (32 x 32 tiles).
+__global__ void k_transpose_bf16(const __nv_bfloat16 *src, int rows, int cols, int lds, __nv_bfloat16 *dst, int ldd)
+{
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * lds + c] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[(size_t)c * ldd + r] = tile[threadIdx.x][i];
+    }
+}
+
+// y[b] = H2[b] . w3 + b3 (warp per row)
+__global__ void k_out_layer(const __nv_bfloat16 *H2, int B, int h2, const float *w3, const float *b3, float *y)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= B) return;
+    float acc = 0.0f;
+    for (int j = lane; j < h2; j += 32) acc += __bfloat162float(H2[(size_t)warp * h2 + j]) * w3[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0) y[warp] = acc + b3[0];
+}
+
+// dy = 2 (y - t) / B; loss accumulates mean squared error.
+__global__ void k_loss(const float *y, const float *t, int B, float *dy, float *loss)
+{
+    float acc = 0.0f;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const float e = y[b] - t[b];
+        dy[b] = 2.0f * e / (float)B;
+        acc += e * e;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc / (float)B);
+}
+
+// dZ2[b][j] = dy[b] w3[j] [H2[b][j] > 0]; written as BF16 row-major and transposed.
+__global__ void k_dz2(const float *dy, const __nv_bfloat16 *H2, const float *w3, int B, int h2, __nv_bfloat16 *dZ2,
+                      __nv_bfloat16 *dZ2T)
+{
+    const size_t total = (size_t)B * h2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / h2), j = (int)(i % h2);
+        const float g = __bfloat162float(H2[i]) > 0.0f ? dy[b] * w3[j] : 0.0f;
+        const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+        dZ2[i] = gb;
+        dZ2T[(size_t)j * B + b] = gb;
+    }
+}
+
+// dZ1T[j][b] = dH1[b][j] [H1[b][j] > 0] as BF16.
+__global__ void k_dz1T(const float *dH1, const __nv_bfloat16 *H1, int B, int h1, __nv_bfloat16 *dZ1T, float *dZ1)
+{
+    const size_t total = (size_t)B * h1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / h1), j = (int)(i % h1);
+        const float g = __bfloat162float(H1[i]) > 0.0f ? dH1[i] : 0.0f;
+        dZ1[i] = g;
+        dZ1T[(size_t)j * B + b] = __float2bfloat16_rn(g);
+    }
+}
+
+// out[j] = sum_b X[b][j] (* w[b] if w): column sums of a [B][C] matrix.
+template <typename T>
+__global__ void k_colsum(const T *X, const float *w, int B, int C, float *out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= C) return;
+    float acc = 0.0f;
+    for (int b = 0; b < B; ++b) {
+        float x;
+        if constexpr (sizeof(T) == 2) x = __bfloat162float(X[(size_t)b * C + j]);
+        else x = (float)X[(size_t)b * C + j];
+        acc += w ? x * w[b] : x;
+    }
+    out[j] = acc;
+}
+
+__global__ void k_sum(const float *x, int n, float *out)
+{
+    float acc = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += x[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    __shared__ float part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        out[0] = s;
+    }
+}
+
+// Adam (Kingma & Ba 2015) on n parameters; step t >= 1.
+__global__ void k_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+}  // namespace fgpu
+
+using namespace fgpu;
+
+struct ffs_mlp {
+    int in_dim = 0, K1 = 0, h1 = 0, h2 = 0, max_batch = 0;
+    long long adam_t = 0;
+    // parameters (FP32 masters): W1 [h1][K1] (columns >= in_dim stay 0), b1, W2 [h2][h1], b2, w3 [h2], b3 [1]
+    float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *w3 = nullptr, *b3 = nullptr;
+    float *gW1 = nullptr, *gb1 = nullptr, *gW2 = nullptr, *gb2 = nullptr, *gw3 = nullptr, *gb3 = nullptr;
+    float *m = nullptr, *v = nullptr;      // Adam moments over the concatenated parameters
+    float *params = nullptr, *grads = nullptr;
+    size_t n_params = 0;
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2Tb = nullptr;
+    // activations / scratch for max_batch rows
+    __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *H1T = nullptr, *XT = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
+                  *dZ1T = nullptr;
+    float *y = nullptr, *dy = nullptr, *dH1 = nullptr, *dZ1 = nullptr;
+    int *err = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace fgpu {
+
+static void mlp_free(ffs_mlp *M)
+{
+    if (!M) return;
+    for (void *p : M->allocs) cudaFree(p);
+    delete M;
+}
+
+static int refresh_bf16(ffs_mlp *M, cudaStream_t st)
+{
+    k_f32_to_bf16_padded<<<dim3(4, M->h1), 128, 0, st>>>(M->W1, M->h1, M->K1, M->K1, M->W1b, M->K1);
+    k_f32_to_bf16_padded<<<dim3(4, M->h2), 128, 0, st>>>(M->W2, M->h2, M->h1, M->h1, M->W2b, M->h1);
+    k_transpose_bf16<<<dim3((M->h1 + 31) / 32, (M->h2 + 31) / 32), dim3(32, 8), 0, st>>>(M->W2b, M->h2, M->h1, M->h1,
+                                                                                        M->W2Tb, M->h2);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+static int mlp_forward(ffs_mlp *M, const void *x, int ldx, int B, float *y, cudaStream_t st)
+{
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    e.err = M->err;
+    e.mode = 1;
+    e.Db = M->H1;
+    e.bias = M->b1;
+    e.ldd = M->h1;
+    int rc = gemm_bf16(x, ldx, M->W1b, M->K1, B, M->h1, M->in_dim, e, st);
+    if (rc) return rc;
+    e.Db = M->H2;
+    e.bias = M->b2;
+    e.ldd = M->h2;
+    if ((rc = gemm_bf16(M->H1, M->h1, M->W2b, M->h1, B, M->h2, M->h1, e, st))) return rc;
+    k_out_layer<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, M->h2, M->w3, M->b3, y);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+}  // namespace fgpu
+
+extern "C" {
+
+int ffs_gemm_bf16(const uint16_t *A, int32_t lda, const uint16_t *B, int32_t ldb, float *D, int32_t ldd, int32_t M,
+                  int32_t N, int32_t K, int32_t *err, ffs_stream stream)
+{
+    clear_error();
+    if (!A || !B || !D || !err) return set_error(FFS_EINVAL, "NULL argument");
+    if (ldd % 4 || ((uintptr_t)D & 15u)) return set_error(FFS_EINVAL, "D must be 16-byte aligned with ldd % 4 == 0");
+    if (lda < K || ldb < K || ldd < N) return set_error(FFS_EINVAL, "leading dimensions too small");
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    e.D = D;
+    e.ldd = ldd;
+    e.mode = 0;
+    e.err = err;
+    return gemm_bf16(A, lda, B, ldb, M, N, K, e, (cudaStream_t)stream);
+}
+
+int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ffs_mlp **out)
+{
+    clear_error();
+    if (!out) return set_error(FFS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (in_dim < 1 || in_dim > 4096) return set_error(FFS_EINVAL, "in_dim %d", in_dim);
+    if (h1 < 64 || h1 % 64 || h1 > 1024 || h2 < 64 || h2 % 64 || h2 > 1024)
+        return set_error(FFS_EINVAL, "hidden sizes must be multiples of 64 in [64, 1024]");
+    if (max_batch < 128 || max_batch % 128) return set_error(FFS_EINVAL, "max_batch %d must be a multiple of 128", max_batch);
+    ffs_mlp *M = new ffs_mlp();
+    M->in_dim = in_dim;
+    M->K1 = round_up(in_dim, 64);
+    M->h1 = h1;
+    M->h2 = h2;
+    M->max_batch = max_batch;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+        M->allocs.push_back(p);
+        return p;
+    };
+    const size_t nW1 = (size_t)h1 * M->K1, nW2 = (size_t)h2 * h1;
+    M->n_params = nW1 + h1 + nW2 + h2 + h2 + 1;
+    M->params = (float *)alloc(M->n_params * 4);
+    M->grads = (float *)alloc(M->n_params * 4);
+    M->m = (float *)alloc(M->n_params * 4);
+    M->v = (float *)alloc(M->n_params * 4);
+    const size_t Bm = (size_t)max_batch;
+    M->W1b = (__nv_bfloat16 *)alloc(nW1 * 2);
+    M->W2b = (__nv_bfloat16 *)alloc(nW2 * 2);
+    M->W2Tb = (__nv_bfloat16 *)alloc(nW2 * 2);
+    M->H1 = (__nv_bfloat16 *)alloc(Bm * h1 * 2);
+    M->H2 = (__nv_bfloat16 *)alloc(Bm * h2 * 2);
+    M->H1T = (__nv_bfloat16 *)alloc(Bm * h1 * 2);
+    M->XT = (__nv_bfloat16 *)alloc(Bm * M->K1 * 2);
+    M->dZ2 = (__nv_bfloat16 *)alloc(Bm * h2 * 2);
+    M->dZ2T = (__nv_bfloat16 *)alloc(Bm * h2 * 2);
+    M->dZ1T = (__nv_bfloat16 *)alloc(Bm * h1 * 2);
+    M->y = (float *)alloc(Bm * 4);
+    M->dy = (float *)alloc(Bm * 4);
+    M->dH1 = (float *)alloc(Bm * h1 * 4);
+    M->dZ1 = (float *)alloc(Bm * h1 * 4);
+    M->err = (int *)alloc(4);
+    for (void *p : M->allocs)
+        if (!p) {
+            mlp_free(M);
+            return set_error(FFS_ENOMEM, "MLP buffers");
+        }
+    float *p = M->params, *g = M->grads;
+    M->W1 = p; M->gW1 = g; p += nW1; g += nW1;
+    M->b1 = p; M->gb1 = g; p += h1; g += h1;
+    M->W2 = p; M->gW2 = g; p += nW2; g += nW2;
+    M->b2 = p; M->gb2 = g; p += h2; g += h2;
+    M->w3 = p; M->gw3 = g; p += h2; g += h2;
+    M->b3 = p; M->gb3 = g;
+    if (cudaMemset(M->params, 0, M->n_params * 4) || cudaMemset(M->m, 0, M->n_params * 4) ||
+        cudaMemset(M->v, 0, M->n_params * 4) || cudaMemset(M->grads, 0, M->n_params * 4) || cudaMemset(M->err, 0, 4) ||
+        refresh_bf16(M, 0) || cudaDeviceSynchronize()) {
+        mlp_free(M);
+        return set_error(FFS_ECUDA, "MLP initialisation");
+    }
+    *out = M;
+    return FFS_OK;
+}
+
+int ffs_mlp_destroy(ffs_mlp *M)
+{
+    mlp_free(M);
+    return FFS_OK;
+}
+
+int ffs_mlp_input_width(const ffs_mlp *M) { return M ? M->K1 : -1; }
+
+int ffs_mlp_set_params(ffs_mlp *M, const float *W1, const float *b1, const float *W2, const float *b2, const float *w3,
+                       float b3)
+{
+    clear_error();
+    if (!M || !W1 || !b1 || !W2 || !b2 || !w3) return set_error(FFS_EINVAL, "NULL argument");
+    std::vector<float> w1p((size_t)M->h1 * M->K1, 0.0f);
+    for (int o = 0; o < M->h1; ++o)
+        for (int i = 0; i < M->in_dim; ++i) w1p[(size_t)o * M->K1 + i] = W1[(size_t)o * M->in_dim + i];
+    FFS_CUDA_TRY(cudaMemcpy(M->W1, w1p.data(), w1p.size() * 4, cudaMemcpyHostToDevice));
+    FFS_CUDA_TRY(cudaMemcpy(M->b1, b1, (size_t)M->h1 * 4, cudaMemcpyHostToDevice));
+    FFS_CUDA_TRY(cudaMemcpy(M->W2, W2, (size_t)M->h2 * M->h1 * 4, cudaMemcpyHostToDevice));
+    FFS_CUDA_TRY(cudaMemcpy(M->b2, b2, (size_t)M->h2 * 4, cudaMemcpyHostToDevice));
+    FFS_CUDA_TRY(cudaMemcpy(M->w3, w3, (size_t)M->h2 * 4, cudaMemcpyHostToDevice));
+    FFS_CUDA_TRY(cudaMemcpy(M->b3, &b3, 4, cudaMemcpyHostToDevice));
+    FFS_CUDA_TRY(cudaMemset(M->m, 0, M->n_params * 4));
+    FFS_CUDA_TRY(cudaMemset(M->v, 0, M->n_params * 4));
+    M->adam_t = 0;
+    int rc = refresh_bf16(M, 0);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaDeviceSynchronize());
+    return FFS_OK;
+}
+
+// Host copies of the parameters (grads = 0) or of the last step's gradients (grads = 1).
+int ffs_mlp_get(const ffs_mlp *M, int32_t grads, float *W1, float *b1, float *W2, float *b2, float *w3, float *b3)
+{
+    clear_error();
+    if (!M) return set_error(FFS_EINVAL, "NULL MLP");
+    FFS_CUDA_TRY(cudaDeviceSynchronize());
+    const float *src = grads ? M->grads : M->params;
+    std::vector<float> all(M->n_params);
+    FFS_CUDA_TRY(cudaMemcpy(all.data(), src, all.size() * 4, cudaMemcpyDeviceToHost));
+    size_t off = 0;
+    if (W1)
+        for (int o = 0; o < M->h1; ++o)
+            for (int i = 0; i < M->in_dim; ++i) W1[(size_t)o * M->in_dim + i] = all[off + (size_t)o * M->K1 + i];
+    off += (size_t)M->h1 * M->K1;
+    if (b1) memcpy(b1, &all[off], (size_t)M->h1 * 4);
+    off += M->h1;
+    if (W2) memcpy(W2, &all[off], (size_t)M->h2 * M->h1 * 4);
+    off += (size_t)M->h2 * M->h1;
+    if (b2) memcpy(b2, &all[off], (size_t)M->h2 * 4);
+    off += M->h2;
+    if (w3) memcpy(w3, &all[off], (size_t)M->h2 * 4);
+    off += M->h2;
+    if (b3) *b3 = all[off];
+    return FFS_OK;
+}
+
+int ffs_mlp_forward(ffs_mlp *M, const uint16_t *x, int32_t ldx, int32_t B, float *y, ffs_stream stream)
+{
+    clear_error();
+    if (!M || !x || !y) return set_error(FFS_EINVAL, "NULL argument");
+    if (B < 1 || B > M->max_batch) return set_error(FFS_EINVAL, "batch %d outside [1, %d]", B, M->max_batch);
+    if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
+    return mlp_forward(M, x, ldx, B, y, (cudaStream_t)stream);
+}
+
+int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *target, int32_t B, float lr,
+                       float *loss, ffs_stream stream)
+{
+    clear_error();
+    if (!M || !x || !target) return set_error(FFS_EINVAL, "NULL argument");
+    if (B < 128 || B % 128 || B > M->max_batch)
+        return set_error(FFS_EINVAL, "training batch %d must be a multiple of 128 and <= %d", B, M->max_batch);
+    if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = mlp_forward(M, x, ldx, B, M->y, st);
+    if (rc) return rc;
+    const int h1 = M->h1, h2 = M->h2, K1 = M->K1;
+    if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, st));
+    k_loss<<<(B + 255) / 256, 256, 0, st>>>(M->y, target, B, M->dy, loss);
+    // output layer gradients
+    k_colsum<__nv_bfloat16><<<(h2 + 127) / 128, 128, 0, st>>>(M->H2, M->dy, B, h2, M->gw3);
+    k_sum<<<1, 256, 0, st>>>(M->dy, B, M->gb3);
+    k_dz2<<<512, 256, 0, st>>>(M->dy, M->H2, M->w3, B, h2, M->dZ2, M->dZ2T);
+    k_colsum<__nv_bfloat16><<<(h2 + 127) / 128, 128, 0, st>>>(M->dZ2, nullptr, B, h2, M->gb2);
+    // gW2 = dZ2^T H1: A = dZ2T [h2][B], B = H1T [h1][B]
+    k_transpose_bf16<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(M->H1, B, h1, h1, M->H1T, B);
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    e.err = M->err;
+    e.mode = 0;
+    e.D = M->gW2;
+    e.ldd = h1;
+    if ((rc = gemm_bf16(M->dZ2T, B, M->H1T, B, h2, h1, B, e, st))) return rc;
+    // dH1 = dZ2 W2: A = dZ2 [B][h2], B = W2T [h1][h2]
+    e.D = M->dH1;
+    e.ldd = h1;
+    if ((rc = gemm_bf16(M->dZ2, h2, M->W2Tb, h2, B, h1, h2, e, st))) return rc;
+    k_dz1T<<<512, 256, 0, st>>>(M->dH1, M->H1, B, h1, M->dZ1T, M->dZ1);
+    k_colsum<float><<<(h1 + 127) / 128, 128, 0, st>>>(M->dZ1, nullptr, B, h1, M->gb1);
+    // gW1 = dZ1^T X: A = dZ1T [h1][B], B = XT [K1][B]
+    k_transpose_bf16<<<dim3((K1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
+        reinterpret_cast<const __nv_bfloat16 *>(x), B, M->in_dim, ldx, M->XT, B);
+    if (K1 > M->in_dim) FFS_CUDA_TRY(cudaMemsetAsync(M->XT + (size_t)M->in_dim * B, 0, (size_t)(K1 - M->in_dim) * B * 2, st));
+    e.D = M->gW1;
+    e.ldd = K1;
+    if ((rc = gemm_bf16(M->dZ1T, B, M->XT, B, h1, K1, B, e, st))) return rc;
+    // Adam
+    M->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)M->adam_t), c2 = 1.0f - powf(b2, (float)M->adam_t);
+    k_adam<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, b1, b2, 1e-8f, c1, c2);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return refresh_bf16(M, st);
+}
+
+// Non-zero if a tensor-core kernel of this MLP timed out waiting (then cleared).
+int ffs_mlp_check(ffs_mlp *M, ffs_stream stream)
+{
+    clear_error();
+    if (!M) return set_error(FFS_EINVAL, "NULL MLP");
+    int h = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&h, M->err, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    FFS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h) {
+        cudaMemsetAsync(M->err, 0, 4, (cudaStream_t)stream);
+        return set_error(FFS_ETIMEOUT, "tensor-core GEMM wait timed out (code %d)", h);
+    }
+    return FFS_OK;
+}
+
+}  // extern "C"
