@@ -74,10 +74,13 @@ def test_mlp_gradients_match_oracle_and_training_reduces_loss(gpu):
     B = 512
     X = _features(rng, B, in_dim)
     t = (X[:, :50].sum(axis=1) / 25.0 - 1.0).astype(np.float32)
-    Xd = _bf16(X)
+    ldx = m.width
+    Xp = np.zeros((B, ldx), np.float32)
+    Xp[:, :in_dim] = X
+    Xd = _bf16(Xp)
     td = torch.from_numpy(t).cuda()
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    gpu.ffs_mlp_train_step(m, Xd, in_dim, td, B, 0.0, loss)
+    gpu.ffs_mlp_train_step(m, Xd, ldx, td, B, 0.0, loss)
     gpu.ffs_mlp_check(m)
     g = m.get(grads=True)
     oloss, og = omlp.loss_and_grads(p, X, t, rounded=True)
@@ -89,6 +92,6 @@ def test_mlp_gradients_match_oracle_and_training_reduces_loss(gpu):
     assert abs(float(g["b3"]) - float(og["b3"])) <= 1e-3 * (abs(float(og["b3"])) + 1e-3)
     first = float(loss.item())
     for _ in range(150):
-        gpu.ffs_mlp_train_step(m, Xd, in_dim, td, B, 1e-3, loss)
+        gpu.ffs_mlp_train_step(m, Xd, ldx, td, B, 1e-3, loss)
     gpu.ffs_mlp_check(m)
     assert float(loss.item()) < 0.2 * first
