@@ -109,13 +109,14 @@ int ffs_population_eval_host(const ffs_instance *inst, const int16_t *pop, int64
  * of Philox applied to the counter (d / 4, cell, generation,
  * island | purpose << 24) under the key (low, high halves of seed).
  * Purposes: 1 initial population, 2 cellular generation, 3 pseudo
- * generation, 4 surrogate candidates.
+ * generation, 15 surrogate training batches, 16 + k surrogate candidate k.
  * out: device uint32[n_cells][n_draws], row c holding cell cell0 + c.
  * ---------------------------------------------------------------------- */
 #define FFS_PURPOSE_INIT 1
 #define FFS_PURPOSE_CELLULAR 2
 #define FFS_PURPOSE_PSEUDO 3
-#define FFS_PURPOSE_SURROGATE 4
+#define FFS_PURPOSE_TRAIN_SAMPLE 15
+#define FFS_PURPOSE_SURROGATE 16   /* + candidate index */
 int ffs_philox_draws(uint64_t seed, uint32_t purpose, uint32_t island, uint32_t generation,
                      uint32_t cell0, int32_t n_cells, int32_t n_draws, uint32_t *out,
                      ffs_stream stream);
@@ -348,6 +349,40 @@ int ffs_mlp_forward(ffs_mlp *mlp, const uint16_t *x, int32_t ldx, int32_t B, flo
 int ffs_mlp_train_step(ffs_mlp *mlp, const uint16_t *x, int32_t ldx, const float *target, int32_t B, float lr,
                        float *loss, ffs_stream stream);
 int ffs_mlp_check(ffs_mlp *mlp, ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Surrogate-screened cellular islands.  After ffs_islands_attach_surrogate,
+ * every generation of every cellular island: each cell makes `candidates`
+ * children (candidate k exactly like the cellular child of
+ * ffs_cellular_step, with Philox purpose 16 + k); the network scores them
+ * (features: x[j] = position of job j / (n - 1) for j < n, zero up to
+ * in_dim - 40, then 40 instance-summary values); only the lowest-scored
+ * candidate (lowest k on ties) is decoded exactly and replaces the cell iff
+ * better.  During the first warmup_generations every score is 0 (so
+ * candidate 0 is taken).  Every exact (child, makespan) pair goes to a
+ * device ring buffer; every train_every generations, train_steps Adam steps
+ * on batches of train_batch pairs drawn from it (Philox purpose 15) fit the
+ * network to makespan / LB - 1.  Pseudo islands are not screened.  The
+ * network must have in_dim >= n + 40 and max_batch >= cellular cells x
+ * candidates; it is used, not owned.  Generations then run as direct launches
+ * (no graph).  ffs_islands_surrogate_last copies the last generation's
+ * scores [cells x candidates] and picks [cells] (cellular islands in ring
+ * order), the last training loss, and reports the pairs produced so far.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t candidates;          /* children per cell, 1..16 (8) */
+    int32_t train_every;         /* generations between training rounds (1; 0 = never) */
+    int32_t train_steps;         /* Adam steps per round (4) */
+    int32_t train_batch;         /* pairs per step, multiple of 128 (1024) */
+    int32_t ring_capacity;       /* pairs kept (131072) */
+    int32_t warmup_generations;  /* generations scored 0 while the ring fills (5) */
+    float lr;                    /* Adam learning rate (1e-3) */
+} ffs_surrogate_params;
+void ffs_surrogate_params_default(ffs_surrogate_params *p);
+int ffs_islands_attach_surrogate(ffs_islands *isl, ffs_mlp *mlp, const ffs_surrogate_params *sp,
+                                 ffs_stream stream);
+int ffs_islands_surrogate_last(const ffs_islands *isl, float *scores, int32_t *chosen, float *loss,
+                               int64_t *pairs, ffs_stream stream);
 
 #ifdef __cplusplus
 }

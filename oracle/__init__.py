@@ -36,7 +36,7 @@ _lib = None
 PURPOSE_INIT = 1
 PURPOSE_CELLULAR = 2
 PURPOSE_PSEUDO = 3
-PURPOSE_SURROGATE = 4
+PURPOSE_SURROGATE = 16   # + candidate index
 
 _i16p = ctypes.POINTER(ctypes.c_int16)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -112,6 +112,10 @@ def _load():
         lib.orc_pseudo_generation.argtypes = gen_args + [ctypes.c_int32, ctypes.c_int64,
                                                          _i16p, _i64p, _i16p, _i64p]
         lib.orc_pseudo_generation.restype = ctypes.c_int64
+        lib.orc_screened_cellular_generation.argtypes = gen_args + [
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _i16p, _i64p, _i16p, _i64p,
+            ctypes.POINTER(ctypes.c_float), ctypes.c_int32, _i32p, _i16p]
+        lib.orc_screened_cellular_generation.restype = ctypes.c_int64
         lib.orc_family_best2.argtypes = [_i64p, _i32p]
         lib.orc_family_best2.restype = None
         lib.orc_init_pseudo_pair.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
@@ -301,6 +305,29 @@ def cellular_generation(inst: Instance, prm: Params, island: int, generation: in
                                     _ptr(ms, ctypes.c_int64), _ptr(out, ctypes.c_int16),
                                     _ptr(out_ms, ctypes.c_int64))
     return out, out_ms, int(k)
+
+
+def screened_cellular_generation(inst: Instance, prm: Params, island: int, generation: int, rows: int,
+                                 cols: int, pop: np.ndarray, ms: np.ndarray, scores: np.ndarray, K: int):
+    """One surrogate-screened cellular generation given the candidates' scores;
+    returns (new pop, new makespans, chosen candidate per cell, candidates [cells*K][n])."""
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    ms = np.ascontiguousarray(ms, dtype=np.int64)
+    sc = np.ascontiguousarray(scores, dtype=np.float32)
+    out = np.zeros_like(pop)
+    out_ms = np.zeros_like(ms)
+    cells = rows * cols
+    chosen = np.zeros(cells, dtype=np.int32)
+    cands = np.zeros((cells * K, inst.n), dtype=np.int16)
+    cp = prm._c()
+    lib.orc_screened_cellular_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
+                                         ctypes.byref(cp), island, generation, rows, cols, pop.shape[1],
+                                         _ptr(pop, ctypes.c_int16), _ptr(ms, ctypes.c_int64),
+                                         _ptr(out, ctypes.c_int16), _ptr(out_ms, ctypes.c_int64),
+                                         _ptr(sc, ctypes.c_float), K, _ptr(chosen, ctypes.c_int32),
+                                         _ptr(cands, ctypes.c_int16))
+    return out, out_ms, chosen, cands
 
 
 def family_best2(fms) -> list:

@@ -74,7 +74,7 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 
 /* Purpose codes of the counter's fourth word (top 8 bits). */
 enum { ORC_PURPOSE_INIT = 1, ORC_PURPOSE_CELLULAR = 2, ORC_PURPOSE_PSEUDO = 3,
-       ORC_PURPOSE_SURROGATE = 4 };
+       ORC_PURPOSE_SURROGATE = 16 /* + candidate index */ };
 
 /* Draw number d of the stream keyed by (seed, island, generation, cell):
  * counter = (d / 4, cell, generation, island | purpose << 24),
@@ -540,4 +540,57 @@ int64_t orc_migrate_penetration(int32_t NA, int32_t NB, int64_t ld, int32_t n,
     }
     free(oa); free(ob);
     return cnt;
+}
+
+/* ------------------------------------------------------------------ */
+/* Surrogate-screened cellular generation                              */
+/* ------------------------------------------------------------------ */
+
+/* Each cell makes K candidate children, candidate k exactly as the cellular
+ * child (tournaments, crossover, mutation) but with the draws of purpose
+ * ORC_PURPOSE_SURROGATE + k.  The candidate with the lowest given score
+ * (scores[c * K + k]; the lowest k on ties) is decoded exactly and replaces
+ * the cell iff its makespan is lower (or not higher, with cell_replace_le).
+ * The scores are an input (the network's predictions), so this checks the
+ * screening around them.  chosen[c] receives the picked k.  Returns the
+ * number of exact decodes. */
+int64_t orc_screened_cellular_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                                         const orc_params *prm, uint32_t island, uint32_t generation,
+                                         int32_t rows, int32_t cols, int64_t ld,
+                                         const int16_t *pop_in, const int64_t *ms_in,
+                                         int16_t *pop_out, int64_t *ms_out,
+                                         const float *scores, int32_t K, int32_t *chosen,
+                                         int16_t *candidates /* [cells*K][n], may be NULL */)
+{
+    int32_t cells = rows * cols;
+    int16_t *child = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int16_t *best = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    for (int32_t c = 0; c < cells; ++c) {
+        int32_t pick = 0;
+        for (int32_t k = 0; k < K; ++k) {
+            uint32_t x[10];
+            for (uint32_t d = 0; d < 10u; ++d)
+                x[d] = orc_draw(prm->seed, ORC_PURPOSE_SURROGATE + (uint32_t)k, island, generation, (uint32_t)c, d);
+            orc_cellular_child(n, rows, cols, c, x, prm, pop_in, ld, ms_in, child, NULL);
+            if (candidates) memcpy(candidates + ((int64_t)c * K + k) * n, child, (size_t)n * sizeof(int16_t));
+            if (k == 0 || scores[(int64_t)c * K + k] < scores[(int64_t)c * K + pick]) {
+                pick = k;
+                memcpy(best, child, (size_t)n * sizeof(int16_t));
+            }
+        }
+        if (chosen) chosen[c] = pick;
+        int64_t mc = orc_decode(n, S, M, p, best, NULL);
+        int better = prm->cell_replace_le ? (mc <= ms_in[c]) : (mc < ms_in[c]);
+        int16_t *dst = pop_out + (int64_t)c * ld;
+        if (better) {
+            memcpy(dst, best, (size_t)n * sizeof(int16_t));
+            ms_out[c] = mc;
+        } else {
+            memcpy(dst, pop_in + (int64_t)c * ld, (size_t)n * sizeof(int16_t));
+            ms_out[c] = ms_in[c];
+        }
+    }
+    free(child);
+    free(best);
+    return cells;
 }

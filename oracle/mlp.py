@@ -88,3 +88,34 @@ def adam_step(params: dict, grads: dict, state: dict, lr: float, b1: float = 0.9
         out[k] = np.asarray(params[k], np.float64) - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
     state["t"] = t
     return out
+
+
+def instance_features(n: int, S: int, M, p, width: int = 40) -> np.ndarray:
+    """The network's instance summary: per stage s < 12 the triple
+    (M_s / 10, mean_j p[j][s] / 99, load_s / (M_s * LB)), then n / 500,
+    S / 20, LB / sum p, zero-padded to `width` (float32)."""
+    p = np.asarray(p, dtype=np.float64).reshape(n, S)
+    M = np.asarray(M, dtype=np.float64)
+    loads = p.sum(axis=0)
+    lb = max(p.sum(axis=1).max(), max(np.ceil(loads[s] / M[s]) for s in range(S)))
+    f = np.zeros(width, dtype=np.float64)
+    k = 0
+    for s in range(min(S, 12)):
+        f[k:k + 3] = (M[s] / 10.0, loads[s] / n / 99.0, loads[s] / (M[s] * lb))
+        k += 3
+    f[36:39] = (n / 500.0, S / 20.0, lb / p.sum())
+    return f.astype(np.float32)
+
+
+def features(rows: np.ndarray, n: int, P: int, inst_feat: np.ndarray) -> np.ndarray:
+    """Network input of job orders: x[j] = position of job j / (n - 1) for j < n
+    (0 when n = 1), zero for n <= j < P, then the instance features; rounded
+    to BF16 as the GPU stores them."""
+    rows = np.asarray(rows)
+    X = np.zeros((rows.shape[0], P + len(inst_feat)), dtype=np.float32)
+    denom = np.float32(max(n - 1, 1))
+    pos = (np.arange(n, dtype=np.float32) / denom).astype(np.float32)
+    for r in range(rows.shape[0]):
+        X[r, rows[r, :n].astype(np.int64)] = pos
+    X[:, P:] = inst_feat
+    return bf16_round(X)

@@ -21,7 +21,7 @@ from . import _build
 _lib = None
 
 FFS_OK, FFS_EINVAL, FFS_ENOMEM, FFS_ECUDA, FFS_EOVERFLOW, FFS_ETIMEOUT, FFS_EDEVICE, FFS_EUNSUPPORTED = range(8)
-FFS_PURPOSE_INIT, FFS_PURPOSE_CELLULAR, FFS_PURPOSE_PSEUDO, FFS_PURPOSE_SURROGATE = 1, 2, 3, 4
+FFS_PURPOSE_INIT, FFS_PURPOSE_CELLULAR, FFS_PURPOSE_PSEUDO, FFS_PURPOSE_SURROGATE = 1, 2, 3, 16
 FFS_MIG_NONE, FFS_MIG_RING, FFS_MIG_PENETRATION = 0, 1, 2
 
 _vp = ctypes.c_void_p
@@ -94,6 +94,9 @@ _SIGS = [
     ("ffs_mlp_forward", _i32, [_vp, _vp, _i32, _i32, _vp, _vp]),
     ("ffs_mlp_train_step", _i32, [_vp, _vp, _i32, _vp, _i32, ctypes.c_float, _vp, _vp]),
     ("ffs_mlp_check", _i32, [_vp, _vp]),
+    ("ffs_surrogate_params_default", None, [_vp]),
+    ("ffs_islands_attach_surrogate", _i32, [_vp, _vp, _vp, _vp]),
+    ("ffs_islands_surrogate_last", _i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
 ]
 
 
@@ -478,3 +481,26 @@ def ffs_mlp_train_step(m: MLP, x, ldx: int, target, B: int, lr: float, loss=None
 
 def ffs_mlp_check(m: MLP, stream=None):
     _check(load().ffs_mlp_check(m.handle, _stream(stream)))
+
+
+class ffs_surrogate_params(ctypes.Structure):
+    _fields_ = [("candidates", _i32), ("train_every", _i32), ("train_steps", _i32), ("train_batch", _i32),
+                ("ring_capacity", _i32), ("warmup_generations", _i32), ("lr", ctypes.c_float)]
+
+
+def ffs_surrogate_params_default() -> ffs_surrogate_params:
+    p = ffs_surrogate_params()
+    load().ffs_surrogate_params_default(ctypes.byref(p))
+    return p
+
+
+def ffs_islands_attach_surrogate(isl: Islands, m: MLP, sp: ffs_surrogate_params, stream=None):
+    _check(load().ffs_islands_attach_surrogate(isl.handle, m.handle, ctypes.byref(sp), _stream(stream)))
+    isl.surrogate = m
+
+
+def ffs_islands_surrogate_last(isl: Islands, scores=None, chosen=None, loss=None, stream=None) -> int:
+    pairs = _i64()
+    _check(load().ffs_islands_surrogate_last(isl.handle, _ptr(scores), _ptr(chosen), _ptr(loss), ctypes.byref(pairs),
+                                             _stream(stream)))
+    return pairs.value

@@ -288,6 +288,8 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
     I->n = n; I->S = S; I->SH = SH; I->total_p = total;
     cudaGetDevice(&I->device);
     cudaDeviceGetAttribute(&I->num_sms, cudaDevAttrMultiProcessorCount, I->device);
+    I->host_M.assign(M, M + S);
+    I->host_p.assign(p, p + (size_t)n * S);
     I->M_eff.resize(S);
     I->heap_off.resize(S);
     int off = 0;

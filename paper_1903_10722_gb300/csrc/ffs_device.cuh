@@ -11,9 +11,11 @@ namespace fgpu {
 constexpr int kMaxM = 32;        // machines per stage after clamping to n
 constexpr int kMaxStages = 64;
 
-// Purpose codes of the Philox counter's fourth word (bits 24..31).
+// Purpose codes of the Philox counter's fourth word (bits 24..31):
+// surrogate candidate k of a cell uses kPurposeSurrogateBase + k (k < 16),
+// the surrogate's training-batch sampling kPurposeTrainSample.
 constexpr uint32_t kPurposeInit = 1, kPurposeCellular = 2, kPurposePseudo = 3,
-                   kPurposeSurrogate = 4;
+                   kPurposeTrainSample = 15, kPurposeSurrogateBase = 16;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two

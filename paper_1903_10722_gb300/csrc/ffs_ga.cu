@@ -2,6 +2,7 @@
 // pseudo island (complementary pairs), migration, and the islands handle
 // that replays one generation of every island from a CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -353,7 +354,30 @@ __global__ void k_advance(int32_t *cur, int32_t *gen, int i0, int i1)
 
 using namespace fgpu;
 
+// Surrogate screening state attached to an islands handle.
+struct SurrogateState {
+    ffs_mlp *mlp = nullptr;
+    ffs_surrogate_params sp{};
+    int P = 0, ldx = 0, nfeat = 40;
+    int cells_total = 0;           // cells of all cellular islands
+    int16_t *cand = nullptr;       // [cells_total * K][ld]
+    void *X = nullptr;             // BF16 [cells_total * K][ldx]
+    float *scores = nullptr;       // [cells_total * K]
+    int32_t *chosen = nullptr;     // [cells_total]
+    int16_t *ring_rows = nullptr;  // [ring_cap][ld]
+    int32_t *ring_ms = nullptr;
+    long long ring_cap = 0, ring_count = 0;
+    float *inst_feat = nullptr;    // [nfeat]
+    float inv_lb = 0.0f;
+    int16_t *train_rows = nullptr; // [train_batch][ld]
+    void *train_X = nullptr;       // BF16 [train_batch][ldx]
+    float *train_t = nullptr, *loss = nullptr;
+    long long train_rounds = 0;
+    std::vector<int> cell_islands;
+};
+
 struct ffs_islands {
+    SurrogateState *sur = nullptr;
     const ffs_instance *inst = nullptr;
     ffs_params prm{};
     int I = 0, ld = 0, rows = 0, cols = 0;
@@ -387,9 +411,12 @@ static IslandRef device_ref(const ffs_islands *S, int i)
     return r;
 }
 
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, cudaStream_t st);
+
 // One generation of the islands in `ids` (all of one kind): cellular islands
 // in launches of up to kMaxBatch, pseudo islands likewise, one decode of all
-// their children per launch.
+// their children per launch.  With a surrogate attached, the cellular
+// islands take the screened path.
 static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids, cudaStream_t st)
 {
     const GaScalars g = scalars_of(&S->prm);
@@ -397,6 +424,11 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
         std::vector<int> sel;
         for (int i : ids)
             if (S->kind[i] == kind) sel.push_back(i);
+        if (kind == 0 && S->sur && !sel.empty()) {
+            int rc = screened_cellular_launch(S, sel, st);
+            if (rc) return rc;
+            continue;
+        }
         for (size_t b0 = 0; b0 < sel.size(); b0 += kMaxBatch) {
             IslandBatch batch;
             memset(&batch, 0, sizeof(batch));
@@ -444,6 +476,68 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
                                                   S->min_pair_rows, gate, gap);
         FFS_CUDA_TRY(cudaGetLastError());
     }
+    return FFS_OK;
+}
+
+// Screened generation of the cellular islands in `sel`: candidates, network
+// scores (all zero during the warm-up generations: candidate 0 is taken),
+// best-scored candidate decoded exactly, ring buffer append.
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, cudaStream_t st)
+{
+    SurrogateState *R = S->sur;
+    const GaScalars g = scalars_of(&S->prm);
+    const int K = R->sp.candidates, cells = S->rows * S->cols;
+    int offset = 0;   // cells before this batch among the cellular islands
+    for (size_t b0 = 0; b0 < sel.size(); b0 += kMaxBatch) {
+        IslandBatch batch;
+        memset(&batch, 0, sizeof(batch));
+        batch.count = (int)std::min(sel.size() - b0, (size_t)kMaxBatch);
+        for (int t = 0; t < batch.count; ++t) batch.ref[t] = device_ref(S, sel[b0 + t]);
+        const int ncells = batch.count * cells;
+        int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
+        float *scores = R->scores + (int64_t)offset * K;
+        int rc = launch_sur_candidates(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, st);
+        if (rc) return rc;
+        const bool warm = S->host_gen[sel[b0]] + 1 > R->sp.warmup_generations;
+        if (warm) {
+            void *X = static_cast<char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
+            if ((rc = launch_sur_features(cand, (int64_t)ncells * K, S->inst->n, S->ld, R->P, R->inst_feat, R->nfeat, X,
+                                          R->ldx, st)))
+                return rc;
+            if ((rc = ffs_mlp_forward(R->mlp, static_cast<const uint16_t *>(X), R->ldx, ncells * K, scores, st)))
+                return rc;
+        } else if ((rc = launch_fill_f32(scores, (int64_t)ncells * K, 0.0f, st))) {
+            return rc;
+        }
+        if ((rc = launch_sur_select(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, scores, R->chosen + offset,
+                                    R->ring_rows, R->ring_ms, R->ring_cap, R->ring_count, S->prm.decode_chunk,
+                                    S->prm.block_threads, S->d_decoded, st)))
+            return rc;
+        R->ring_count += ncells;
+        offset += ncells;
+    }
+    return FFS_OK;
+}
+
+// Online training of the surrogate on pairs from the ring buffer.
+static int surrogate_train(ffs_islands *S, cudaStream_t st)
+{
+    SurrogateState *R = S->sur;
+    const long long valid = std::min(R->ring_count, R->ring_cap);
+    if (valid < R->sp.train_batch) return FFS_OK;
+    for (int s = 0; s < R->sp.train_steps; ++s) {
+        const uint32_t draw_gen = (uint32_t)(R->train_rounds * R->sp.train_steps + s);
+        int rc = launch_sur_gather(R->ring_rows, R->ring_ms, valid, S->ld, S->prm.seed, draw_gen, R->sp.train_batch,
+                                   R->train_rows, R->train_t, R->inv_lb, st);
+        if (rc) return rc;
+        if ((rc = launch_sur_features(R->train_rows, R->sp.train_batch, S->inst->n, S->ld, R->P, R->inst_feat,
+                                      R->nfeat, R->train_X, R->ldx, st)))
+            return rc;
+        if ((rc = ffs_mlp_train_step(R->mlp, static_cast<const uint16_t *>(R->train_X), R->ldx, R->train_t,
+                                     R->sp.train_batch, R->sp.lr, R->loss, st)))
+            return rc;
+    }
+    R->train_rounds += 1;
     return FFS_OK;
 }
 
@@ -522,6 +616,7 @@ int ffs_pseudo_step(const ffs_instance *I, const ffs_params *prm, uint32_t islan
 static void islands_free(ffs_islands *S)
 {
     if (!S) return;
+    delete S->sur;
     if (S->graph_all) cudaGraphExecDestroy(S->graph_all);
     if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void *p : S->allocs) cudaFree(p);
@@ -639,6 +734,128 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
     return FFS_OK;
 }
 
+void ffs_surrogate_params_default(ffs_surrogate_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->candidates = 8;
+    p->train_every = 1;
+    p->train_steps = 4;
+    p->train_batch = 1024;
+    p->ring_capacity = 1 << 17;
+    p->warmup_generations = 5;
+    p->lr = 1e-3f;
+}
+
+int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surrogate_params *sp, ffs_stream stream)
+{
+    clear_error();
+    if (!S || !mlp || !sp) return set_error(FFS_EINVAL, "NULL argument");
+    if (S->sur) return set_error(FFS_EINVAL, "a surrogate is already attached");
+    if (sp->candidates < 1 || sp->candidates > 16) return set_error(FFS_EINVAL, "candidates %d outside [1, 16]", sp->candidates);
+    if (sp->train_batch < 128 || sp->train_batch % 128) return set_error(FFS_EINVAL, "train_batch must be a multiple of 128");
+    if (sp->train_steps < 0 || sp->train_every < 0 || sp->warmup_generations < 0)
+        return set_error(FFS_EINVAL, "negative training schedule");
+    const int n = S->inst->n, nfeat = 40;
+    const int in_dim = mlp_in_dim(mlp);
+    if (in_dim < n + nfeat) return set_error(FFS_EINVAL, "network input %d < n + %d", in_dim, nfeat);
+    std::vector<int> cell_islands;
+    for (int i = 0; i < S->I; ++i)
+        if (S->kind[i] == 0) cell_islands.push_back(i);
+    if (cell_islands.empty()) return set_error(FFS_EINVAL, "no cellular island to screen");
+    const int cells_total = (int)cell_islands.size() * S->rows * S->cols;
+    const int K = sp->candidates;
+    if ((long long)cells_total * K > mlp_max_batch(mlp))
+        return set_error(FFS_EINVAL, "network max_batch %d < %lld candidates per generation", mlp_max_batch(mlp),
+                         (long long)cells_total * K);
+    if (sp->train_batch > mlp_max_batch(mlp)) return set_error(FFS_EINVAL, "train_batch above the network's max_batch");
+    if (sp->ring_capacity < cells_total || sp->ring_capacity < sp->train_batch)
+        return set_error(FFS_EINVAL, "ring_capacity must hold one generation's pairs and a training batch");
+    SurrogateState *R = new SurrogateState();
+    R->mlp = mlp;
+    R->sp = *sp;
+    R->P = in_dim - nfeat;
+    R->ldx = ffs_mlp_input_width(mlp);
+    R->nfeat = nfeat;
+    R->cells_total = cells_total;
+    R->cell_islands = cell_islands;
+    R->ring_cap = sp->ring_capacity;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+        S->allocs.push_back(p);
+        return p;
+    };
+    const size_t ncand = (size_t)cells_total * K;
+    R->cand = (int16_t *)alloc(ncand * S->ld * 2);
+    R->X = alloc(ncand * R->ldx * 2);
+    R->scores = (float *)alloc(ncand * 4);
+    R->chosen = (int32_t *)alloc((size_t)cells_total * 4);
+    R->ring_rows = (int16_t *)alloc((size_t)R->ring_cap * S->ld * 2);
+    R->ring_ms = (int32_t *)alloc((size_t)R->ring_cap * 4);
+    R->inst_feat = (float *)alloc(nfeat * 4);
+    R->train_rows = (int16_t *)alloc((size_t)sp->train_batch * S->ld * 2);
+    R->train_X = alloc((size_t)sp->train_batch * R->ldx * 2);
+    R->train_t = (float *)alloc((size_t)sp->train_batch * 4);
+    R->loss = (float *)alloc(4);
+    if (!R->cand || !R->X || !R->scores || !R->chosen || !R->ring_rows || !R->ring_ms || !R->inst_feat ||
+        !R->train_rows || !R->train_X || !R->train_t || !R->loss) {
+        delete R;
+        return set_error(FFS_ENOMEM, "surrogate buffers");
+    }
+    // instance summary features (host): per stage s < 12 (M_s/10, mean p/99, load/(M_s LB)), n/500, S/20, LB/sum p
+    const ffs_instance *I = S->inst;
+    std::vector<double> load(I->S, 0.0), job(I->n, 0.0);
+    for (int j = 0; j < I->n; ++j)
+        for (int s = 0; s < I->S; ++s) {
+            const double p = I->host_p[(size_t)j * I->S + s];
+            load[s] += p;
+            job[j] += p;
+        }
+    double lb = 0.0, total = 0.0;
+    for (int j = 0; j < I->n; ++j) lb = std::max(lb, job[j]);
+    for (int s = 0; s < I->S; ++s) {
+        lb = std::max(lb, std::ceil(load[s] / I->host_M[s]));
+        total += load[s];
+    }
+    std::vector<float> f(nfeat, 0.0f);
+    for (int s = 0; s < std::min(I->S, 12); ++s) {
+        f[3 * s] = (float)(I->host_M[s] / 10.0);
+        f[3 * s + 1] = (float)(load[s] / I->n / 99.0);
+        f[3 * s + 2] = (float)(load[s] / (I->host_M[s] * lb));
+    }
+    f[36] = (float)(I->n / 500.0);
+    f[37] = (float)(I->S / 20.0);
+    f[38] = (float)(lb / total);
+    R->inv_lb = (float)(1.0 / lb);
+    if (cudaMemcpy(R->inst_feat, f.data(), nfeat * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete R;
+        return set_error(FFS_ECUDA, "surrogate features upload");
+    }
+    (void)stream;
+    S->sur = R;
+    if (S->graph_all) {
+        cudaGraphExecDestroy(S->graph_all);
+        S->graph_all = nullptr;
+    }
+    return FFS_OK;
+}
+
+int ffs_islands_surrogate_last(const ffs_islands *S, float *scores, int32_t *chosen, float *loss, int64_t *pairs,
+                               ffs_stream stream)
+{
+    clear_error();
+    if (!S || !S->sur) return set_error(FFS_EINVAL, "no surrogate attached");
+    const SurrogateState *R = S->sur;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (scores)
+        FFS_CUDA_TRY(cudaMemcpyAsync(scores, R->scores, (size_t)R->cells_total * R->sp.candidates * 4, cudaMemcpyDefault, st));
+    if (chosen) FFS_CUDA_TRY(cudaMemcpyAsync(chosen, R->chosen, (size_t)R->cells_total * 4, cudaMemcpyDefault, st));
+    if (loss) FFS_CUDA_TRY(cudaMemcpyAsync(loss, R->loss, 4, cudaMemcpyDefault, st));
+    if (pairs) *pairs = R->ring_count;
+    return FFS_OK;
+}
+
 int ffs_islands_destroy(ffs_islands *S)
 {
     islands_free(S);
@@ -682,6 +899,21 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
     for (int i = 1; i < S->I; ++i)
         if (S->host_gen[i] != S->host_gen[0])
             return set_error(FFS_EINVAL, "islands were stepped separately; generation counts differ");
+    if (S->sur) {
+        // screened generations: direct launches (the training steps depend on host counters)
+        for (int g = 0; g < n_generations; ++g) {
+            int rc = generation_all(S, st);
+            if (rc) return rc;
+            for (int i = 0; i < S->I; ++i) {
+                S->host_cur[i] ^= 1;
+                S->host_gen[i] += 1;
+            }
+            if (S->sur->sp.train_every > 0 && S->host_gen[0] % S->sur->sp.train_every == 0) {
+                if ((rc = surrogate_train(S, st))) return rc;
+            }
+        }
+        return FFS_OK;
+    }
     if (!S->graph_all) {
         if (!S->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;

@@ -65,6 +65,8 @@ __host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_wa
 struct ffs_instance {
     int n = 0, S = 0, SH = 0, device = 0;
     int64_t total_p = 0;
+    std::vector<int32_t> host_M;     // machines per stage as given
+    std::vector<int32_t> host_p;     // [n][S] processing times as given
     std::vector<int32_t> M_eff;      // min(M_s, n)
     std::vector<int32_t> heap_off;   // prefix sums of M_eff
     int heap_words = 0;
@@ -174,5 +176,20 @@ const void *cellular_kernel();
 const void *eval_kernel();
 
 int validate_rows(const void *p, int ld, int n);
+
+// Surrogate screening (ffs_surrogate.cu).
+int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
+                          int ld, int K, int16_t *cand, cudaStream_t st);
+int launch_sur_features(const int16_t *rows, int64_t nrows, int n, int ld, int P, const float *inst_feat, int nfeat,
+                        void *X, int ldx, cudaStream_t st);
+int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
+                      int ld, int K, const int16_t *cand, const float *scores, int32_t *chosen, int16_t *ring_rows,
+                      int32_t *ring_ms, long long ring_cap, long long ring_base, int B_req, int T_req,
+                      unsigned long long *decoded, cudaStream_t st);
+int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long valid, int ld, uint64_t seed,
+                      uint32_t draw_gen, int B, int16_t *out_rows, float *targets, float inv_lb, cudaStream_t st);
+int launch_fill_f32(float *p, int64_t n, float v, cudaStream_t st);
+int mlp_in_dim(const ffs_mlp *m);
+int mlp_max_batch(const ffs_mlp *m);
 
 }  // namespace fgpu

@@ -359,6 +359,9 @@ struct ffs_mlp {
 
 namespace fgpu {
 
+int mlp_in_dim(const ffs_mlp *m) { return m->in_dim; }
+int mlp_max_batch(const ffs_mlp *m) { return m->max_batch; }
+
 static void mlp_free(ffs_mlp *M)
 {
     if (!M) return;

@@ -1,0 +1,90 @@
+"""Surrogate-screened cellular generations against the oracle: given the
+network's scores (dumped from the GPU), the oracle's screened generation must
+reproduce the populations and the picks bit-exactly; the scores themselves
+must match the float64 network oracle on the oracle's own candidate features."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from ffs_workloads import make_instance
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_every, seed=7):
+    spec = make_instance(n, S, mlo, mhi, seed=n + S)
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    prm = gpu.ffs_params_default()
+    prm.seed = seed
+    prm.migration_mode, prm.migration_gap = 0, 0
+    isl = gpu.Islands(g, prm, 1, rows, cols, n_pseudo, psize)
+    params = omlp.init_params(540, 512, 256, seed=11)
+    params["b1"] = np.random.default_rng(1).normal(0, 0.05, 512).astype(np.float32)
+    net = gpu.MLP(540, 512, 256, max(1024, ((rows * cols * K + 127) // 128) * 128))
+    net.set_params(params)
+    sp = gpu.ffs_surrogate_params_default()
+    sp.candidates, sp.warmup_generations, sp.train_every = K, warmup, train_every
+    sp.train_batch, sp.train_steps = 256, 2
+    sp.ring_capacity = max(4096, rows * cols * 4)
+    gpu.ffs_islands_attach_surrogate(isl, net, sp)
+    ga = orc.IslandGA(o, orc.Params(seed=seed), 1, rows, cols, n_pseudo, psize)
+    return spec, o, g, isl, ga, params
+
+
+def _compare(gpu, isl, ga, n, tag):
+    for i in range(isl.n_islands):
+        pop, ms = gpu.island_tensors(isl, i)
+        torch.cuda.synchronize()
+        assert np.array_equal(pop.cpu().numpy(), ga.pops[i][:, :n]), (tag, i)
+        assert np.array_equal(ms.cpu().numpy().astype(np.int64), ga.mss[i]), (tag, i)
+
+
+@pytest.mark.parametrize("warmup", [0, 2])
+def test_screened_generations_match_oracle_given_scores(gpu, warmup):
+    rows, cols, K = 8, 8, 8
+    spec, o, g, isl, ga, params = _setup(gpu, 20, 5, 3, 3, rows, cols, 1, 32, K, warmup, 0)
+    inst_feat = omlp.instance_features(spec.n, spec.S, spec.M, spec.p)
+    cells = rows * cols
+    for gen in range(1, 5):
+        gpu.ffs_island_step(isl, -1, 1)
+        scores = np.zeros(cells * K, np.float32)
+        chosen = np.zeros(cells, np.int32)
+        gpu.ffs_islands_surrogate_last(isl, scores, chosen)
+        torch.cuda.synchronize()
+        pop, ms, want_chosen, cands = orc.screened_cellular_generation(
+            o, ga.prm, 0, gen, rows, cols, ga.pops[0], ga.mss[0], scores, K)
+        assert chosen.tolist() == want_chosen.tolist(), gen
+        ga.pops[0], ga.mss[0] = pop, ms
+        ga.pops[1], ga.mss[1], d = orc.pseudo_generation(o, ga.prm, 1, gen, ga.pops[1], ga.mss[1])
+        _compare(gpu, isl, ga, spec.n, gen)
+        if gen <= warmup:
+            assert not scores.any()
+        else:
+            X = omlp.features(cands, spec.n, 500, inst_feat)
+            want, _ = omlp.forward(params, X, rounded=True)
+            scale = np.mean(np.abs(want)) + 1e-3
+            assert np.max(np.abs(scores - want)) <= 2e-2 * scale, gen
+
+
+def test_screened_training_runs_and_keeps_parity(gpu):
+    rows, cols, K = 16, 16, 8
+    spec, o, g, isl, ga, params = _setup(gpu, 60, 6, 2, 4, rows, cols, 0, 0, K, 1, 1)
+    cells = rows * cols
+    losses = []
+    for gen in range(1, 13):
+        gpu.ffs_island_step(isl, -1, 1)
+        scores = np.zeros(cells * K, np.float32)
+        loss = np.zeros(1, np.float32)
+        pairs = gpu.ffs_islands_surrogate_last(isl, scores, None, loss)
+        torch.cuda.synchronize()
+        pop, ms, _, _ = orc.screened_cellular_generation(o, ga.prm, 0, gen, rows, cols, ga.pops[0], ga.mss[0],
+                                                         scores, K)
+        ga.pops[0], ga.mss[0] = pop, ms
+        _compare(gpu, isl, ga, spec.n, gen)
+        assert pairs == gen * cells
+        if pairs >= 256:
+            losses.append(float(loss[0]))
+    assert all(np.isfinite(losses)) and losses[-1] < losses[0]
