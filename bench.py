@@ -405,6 +405,83 @@ def run_batch(args):
     return 0
 
 
+def _spearman(a, b) -> float:
+    import numpy as np
+    ra = np.argsort(np.argsort(a, kind="stable"), kind="stable").astype(np.float64)
+    rb = np.argsort(np.argsort(b, kind="stable"), kind="stable").astype(np.float64)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    return float((ra * rb).sum() / np.sqrt((ra * ra).sum() * (rb * rb).sum()))
+
+
+def run_surrogate(args):
+    """Plain vs surrogate-screened dual-island GA on the 100 x 10 instance
+    family (64x64 cellular + 4096 pseudo): best makespan against wall-clock.
+    The screened GA scores 8 candidates per cell with the 540-512-256-1 BF16
+    network (tcgen05 GEMMs) and decodes only the best-scored one; the network
+    trains online on the exact pairs.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    from ffs_workloads import WORKLOADS, workload_instance
+    from oracle import mlp as omlp   # parameter initialisation (numpy) only
+
+    torch.cuda.set_device(0)
+    w = WORKLOADS["dual_100x10"]
+    spec = workload_instance("dual_100x10")
+    inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p)
+    gens = args.steps
+    every = max(1, gens // 40)
+    curves, extra = {}, {}
+    for mode in ("plain", "screened"):
+        prm = ffs.ffs_params_default()
+        prm.migration_mode, prm.migration_gap = ffs.FFS_MIG_RING, w["gap"]
+        isl = ffs.Islands(inst, prm, 1, w["rows"], w["cols"], 1, w["pseudo_size"])
+        net = None
+        if mode == "screened":
+            net = ffs.MLP(540, 512, 256, w["rows"] * w["cols"] * 8)
+            net.set_params(omlp.init_params(540, 512, 256, seed=3))
+            sp = ffs.ffs_surrogate_params_default()
+            ffs.ffs_islands_attach_surrogate(isl, net, sp)
+        torch.cuda.synchronize()
+        curve = [(0.0, ffs.ffs_islands_best(isl)[0], 0)]
+        t_total = 0.0
+        done = 0
+        while done < gens:
+            k = min(every, gens - done)
+            t0 = time.perf_counter()
+            ffs.ffs_island_step(isl, -1, k)
+            torch.cuda.synchronize()
+            t_total += time.perf_counter() - t0
+            done += k
+            curve.append((t_total, ffs.ffs_islands_best(isl)[0], done))
+        curves[mode] = curve
+        if mode == "screened":
+            cells, K = w["rows"] * w["cols"], 8
+            scores = np.zeros(cells * K, np.float32)
+            cands = np.zeros((cells * K, spec.n), np.int16)
+            loss = np.zeros(1, np.float32)
+            pairs = ffs.ffs_islands_surrogate_last(isl, scores, None, loss, cands, spec.n)
+            exact = np.zeros(cells * K, np.int32)
+            ffs.ffs_population_eval_host(inst, np.ascontiguousarray(np.pad(cands, ((0, 0), (0, inst.ld - spec.n)))),
+                                         cells * K, inst.ld, exact)
+            extra = {"spearman_last_generation_candidates": _spearman(scores, exact), "train_loss": float(loss[0]),
+                     "exact_pairs": pairs}
+        isl.close()
+    plain_t, plain_best = curves["plain"][-1][0], curves["plain"][-1][1]
+    reach = next((t for t, b, _ in curves["screened"] if b <= plain_best), None)
+    scr_t, scr_best = curves["screened"][-1][0], curves["screened"][-1][1]
+    line = {
+        "metric": "best makespan vs wall-clock, plain vs surrogate-screened GA", "workload": "dual_100x10",
+        "generations": gens, "plain": {"best": plain_best, "seconds": plain_t, "curve": curves["plain"]},
+        "screened": {"best": scr_best, "seconds": scr_t, "curve": curves["screened"]},
+        "time_to_plain_best_ratio": (reach / plain_t) if reach is not None else None, **extra,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def launches_per_generation(w) -> int:
     """Kernels of one generation: one fused kernel per cellular island, three
     per pseudo island (breed, decode, replace), one advance, and when
@@ -430,6 +507,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch_256":
         return run_batch(args)
+    if args.workload == "surrogate_100x10":
+        return run_surrogate(args)
     return run_ours(args)
 
 

@@ -367,7 +367,9 @@ int ffs_mlp_check(ffs_mlp *mlp, ffs_stream stream);
  * candidates; it is used, not owned.  Generations then run as direct launches
  * (no graph).  ffs_islands_surrogate_last copies the last generation's
  * scores [cells x candidates] and picks [cells] (cellular islands in ring
- * order), the last training loss, and reports the pairs produced so far.
+ * order), the last training loss, the last generation's candidate rows
+ * (candidates [cells x candidates][ld_out], may be NULL), and reports the
+ * pairs produced so far.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int32_t candidates;          /* children per cell, 1..16 (8) */
@@ -382,7 +384,7 @@ void ffs_surrogate_params_default(ffs_surrogate_params *p);
 int ffs_islands_attach_surrogate(ffs_islands *isl, ffs_mlp *mlp, const ffs_surrogate_params *sp,
                                  ffs_stream stream);
 int ffs_islands_surrogate_last(const ffs_islands *isl, float *scores, int32_t *chosen, float *loss,
-                               int64_t *pairs, ffs_stream stream);
+                               int64_t *pairs, int16_t *candidates, int32_t ld_out, ffs_stream stream);
 
 #ifdef __cplusplus
 }

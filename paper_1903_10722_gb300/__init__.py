@@ -96,7 +96,7 @@ _SIGS = [
     ("ffs_mlp_check", _i32, [_vp, _vp]),
     ("ffs_surrogate_params_default", None, [_vp]),
     ("ffs_islands_attach_surrogate", _i32, [_vp, _vp, _vp, _vp]),
-    ("ffs_islands_surrogate_last", _i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_islands_surrogate_last", _i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
 ]
 
 
@@ -499,8 +499,9 @@ def ffs_islands_attach_surrogate(isl: Islands, m: MLP, sp: ffs_surrogate_params,
     isl.surrogate = m
 
 
-def ffs_islands_surrogate_last(isl: Islands, scores=None, chosen=None, loss=None, stream=None) -> int:
+def ffs_islands_surrogate_last(isl: Islands, scores=None, chosen=None, loss=None, candidates=None, ld_out: int = 0,
+                               stream=None) -> int:
     pairs = _i64()
     _check(load().ffs_islands_surrogate_last(isl.handle, _ptr(scores), _ptr(chosen), _ptr(loss), ctypes.byref(pairs),
-                                             _stream(stream)))
+                                             _ptr(candidates), ld_out, _stream(stream)))
     return pairs.value

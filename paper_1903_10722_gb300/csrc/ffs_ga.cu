@@ -842,7 +842,7 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
 }
 
 int ffs_islands_surrogate_last(const ffs_islands *S, float *scores, int32_t *chosen, float *loss, int64_t *pairs,
-                               ffs_stream stream)
+                               int16_t *candidates, int32_t ld_out, ffs_stream stream)
 {
     clear_error();
     if (!S || !S->sur) return set_error(FFS_EINVAL, "no surrogate attached");
@@ -852,6 +852,11 @@ int ffs_islands_surrogate_last(const ffs_islands *S, float *scores, int32_t *cho
         FFS_CUDA_TRY(cudaMemcpyAsync(scores, R->scores, (size_t)R->cells_total * R->sp.candidates * 4, cudaMemcpyDefault, st));
     if (chosen) FFS_CUDA_TRY(cudaMemcpyAsync(chosen, R->chosen, (size_t)R->cells_total * 4, cudaMemcpyDefault, st));
     if (loss) FFS_CUDA_TRY(cudaMemcpyAsync(loss, R->loss, 4, cudaMemcpyDefault, st));
+    if (candidates) {
+        if (ld_out < S->inst->n) return set_error(FFS_EINVAL, "ld_out %d < n %d", ld_out, S->inst->n);
+        FFS_CUDA_TRY(cudaMemcpy2DAsync(candidates, (size_t)ld_out * 2, R->cand, (size_t)S->ld * 2, (size_t)S->inst->n * 2,
+                                       (size_t)R->cells_total * R->sp.candidates, cudaMemcpyDefault, st));
+    }
     if (pairs) *pairs = R->ring_count;
     return FFS_OK;
 }
