@@ -157,7 +157,7 @@ def run_reference(args):
     from ffs_workloads import WORKLOADS
     per_step = []
     total_evals = 0
-    budget = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    budget = max(0.5, min(20.0, 100.0 / max(1, args.steps + args.warmup)))   # whole run ~100 s
     for i in range(args.warmup + args.steps):
         rate, sample = cpu_oracle_rate(args.workload, budget_s=budget)
         if i >= args.warmup:
