@@ -88,3 +88,31 @@ def test_screened_training_runs_and_keeps_parity(gpu):
         if pairs >= 256:
             losses.append(float(loss[0]))
     assert all(np.isfinite(losses)) and losses[-1] < losses[0]
+
+
+def test_trained_screen_beats_plain_ga_at_equal_exact_decodes(gpu):
+    """100 x 10 instance family (64x64 cellular + pseudo 4096, ring 2% every 50):
+    after 100 generations -- the same number of exact decodes per cell -- the
+    screened GA with the online-trained network holds a lower best makespan
+    than the plain GA (seeded run; the wall-clock comparison is reported by
+    bench.py --workload surrogate_100x10)."""
+    from ffs_workloads import WORKLOADS, workload_instance
+    w = WORKLOADS["dual_100x10"]
+    spec = workload_instance("dual_100x10")
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    best = {}
+    for mode in ("plain", "screened"):
+        prm = gpu.ffs_params_default()
+        prm.migration_mode, prm.migration_gap = gpu.FFS_MIG_RING, w["gap"]
+        isl = gpu.Islands(inst, prm, 1, w["rows"], w["cols"], 1, w["pseudo_size"])
+        if mode == "screened":
+            net = gpu.MLP(540, 512, 256, w["rows"] * w["cols"] * 8)
+            net.set_params(omlp.init_params(540, 512, 256, seed=3))
+            gpu.ffs_islands_attach_surrogate(isl, net, gpu.ffs_surrogate_params_default())
+        gpu.ffs_island_step(isl, -1, 100)
+        best[mode] = gpu.ffs_islands_best(isl)[0]
+        decoded = gpu.ffs_islands_decoded(isl)
+        best[mode + "_decoded"] = decoded
+        isl.close()
+    print("best makespan after 100 generations:", best)
+    assert best["screened"] < best["plain"]
