@@ -386,6 +386,31 @@ int ffs_islands_attach_surrogate(ffs_islands *isl, ffs_mlp *mlp, const ffs_surro
 int ffs_islands_surrogate_last(const ffs_islands *isl, float *scores, int32_t *chosen, float *loss,
                                int64_t *pairs, int16_t *candidates, int32_t ld_out, ffs_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Measurement and self-tests (no counterpart in the paper).
+ * ffs_measure_int_rate: lane operations per second of one 32-bit integer
+ * operation kind (0 min/max, 1 three-input logic, 2 add, 3 multiply-add)
+ * with 8 independent chains per thread at full occupancy; best of 3 runs;
+ * synchronous.
+ * ffs_selftest_wait_timeout: a kernel waits on an mbarrier that nothing
+ * completes, with the same bounded wait the tensor-core kernels use
+ * (limit_ns <= 2 s); returns FFS_ETIMEOUT with *status = 1 when the wait gave
+ * up as it must, FFS_OK with *status = 0 if the phase completed.
+ * ---------------------------------------------------------------------- */
+int ffs_measure_int_rate(int32_t kind, double *lane_ops_per_s, float *ms, ffs_stream stream);
+int ffs_selftest_wait_timeout(int64_t limit_ns, int32_t *status, ffs_stream stream);
+
+/* Checkpoint support: set the generation count of every island (the
+ * populations come back with ffs_islands_set); the next generation then
+ * draws the same Philox streams as an uninterrupted run.  Synchronous. */
+int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
+
+/* Time the fused cellular kernel (and the decoder used by the pseudo
+ * islands) at every launch shape that fits, on generations that do not
+ * advance the state, keep the fastest for both and report it; synchronous. */
+int ffs_islands_autotune(ffs_islands *isl, int32_t repeats, ffs_stream stream, int32_t *threads_out,
+                         int32_t *chunk_out, float *best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,10 @@ _SIGS = [
     ("ffs_surrogate_params_default", None, [_vp]),
     ("ffs_islands_attach_surrogate", _i32, [_vp, _vp, _vp, _vp]),
     ("ffs_islands_surrogate_last", _i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
+    ("ffs_measure_int_rate", _i32, [_i32, _vp, _vp, _vp]),
+    ("ffs_selftest_wait_timeout", _i32, [_i64, _vp, _vp]),
+    ("ffs_islands_set_generation", _i32, [_vp, _i64]),
+    ("ffs_islands_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
 ]
 
 
@@ -505,3 +509,29 @@ def ffs_islands_surrogate_last(isl: Islands, scores=None, chosen=None, loss=None
     _check(load().ffs_islands_surrogate_last(isl.handle, _ptr(scores), _ptr(chosen), _ptr(loss), ctypes.byref(pairs),
                                              _ptr(candidates), ld_out, _stream(stream)))
     return pairs.value
+
+
+def ffs_measure_int_rate(kind: int, stream=None) -> dict:
+    rate = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(load().ffs_measure_int_rate(kind, ctypes.byref(rate), ctypes.byref(ms), _stream(stream)))
+    return {"lane_ops_per_s": rate.value, "ms": ms.value}
+
+
+def ffs_selftest_wait_timeout(limit_ns: int, stream=None):
+    """(status code of the call, device status word)."""
+    st = _i32()
+    rc = load().ffs_selftest_wait_timeout(limit_ns, ctypes.byref(st), _stream(stream))
+    return rc, st.value
+
+
+def ffs_islands_set_generation(isl: Islands, generation: int):
+    _check(load().ffs_islands_set_generation(isl.handle, generation))
+
+
+def ffs_islands_autotune(isl: Islands, repeats: int = 2, stream=None) -> dict:
+    t, c = _i32(), _i32()
+    ms = ctypes.c_float()
+    _check(load().ffs_islands_autotune(isl.handle, repeats, _stream(stream), ctypes.byref(t), ctypes.byref(c),
+                                       ctypes.byref(ms)))
+    return {"threads": t.value, "chunk": c.value, "ms": ms.value}

@@ -861,6 +861,85 @@ int ffs_islands_surrogate_last(const ffs_islands *S, float *scores, int32_t *cho
     return FFS_OK;
 }
 
+int ffs_islands_set_generation(ffs_islands *S, int64_t generation)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (generation < 0 || generation > 0x7FFFFFFF) return set_error(FFS_EINVAL, "generation %lld", (long long)generation);
+    std::vector<int32_t> gen(S->I, (int32_t)generation);
+    FFS_CUDA_TRY(cudaMemcpy(S->d_gen, gen.data(), 4 * S->I, cudaMemcpyHostToDevice));
+    for (int i = 0; i < S->I; ++i) S->host_gen[i] = generation;
+    return FFS_OK;
+}
+
+int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int32_t *threads_out, int32_t *chunk_out,
+                         float *best_ms)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (S->sur) return set_error(FFS_EINVAL, "autotune before attaching a surrogate (its ring would record the timing runs)");
+    if (repeats < 1) repeats = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> all(S->I);
+    for (int i = 0; i < S->I; ++i) all[i] = i;
+    cudaEvent_t e0, e1;
+    FFS_CUDA_TRY(cudaEventCreate(&e0));
+    FFS_CUDA_TRY(cudaEventCreate(&e1));
+    const ffs_params saved = S->prm;
+    unsigned long long *saved_counter = S->d_decoded;
+    S->d_decoded = nullptr;   // the timing runs are not counted
+    float best = -1.0f;
+    int bestT = 0, bestB = 0;
+    int rc = FFS_OK;
+    const int Ts[4] = {64, 128, 256, 512};
+    const int Bs[6] = {8, 16, 32, 64, 128, 0};
+    for (int ti = 0; ti < 4 && !rc; ++ti) {
+        for (int bi = 0; bi < 6 && !rc; ++bi) {
+            const int B = Bs[bi] == 0 ? round_up(S->inst->n, 8) : Bs[bi];
+            if (Bs[bi] != 0 && B >= S->inst->n) continue;
+            Plan p;
+            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], (S->inst->n + 31) / 32, &p)) continue;
+            S->prm.decode_chunk = B;
+            S->prm.block_threads = Ts[ti];
+            // one untimed run, then the timed ones; they only rewrite the next-generation buffers
+            if ((rc = islands_generation_launch(S, all, st))) break;
+            float total = 0.0f;
+            for (int r = 0; r < repeats && !rc; ++r) {
+                cudaEventRecord(e0, st);
+                rc = islands_generation_launch(S, all, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(FFS_ECUDA, "autotune timing");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            const float avg = total / repeats;
+            if (!rc && (best < 0.0f || avg < best)) {
+                best = avg;
+                bestT = Ts[ti];
+                bestB = B;
+            }
+        }
+    }
+    (void)cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    S->d_decoded = saved_counter;
+    S->prm = saved;
+    if (rc) return rc;
+    if (best < 0.0f) return set_error(FFS_EUNSUPPORTED, "no launch shape could be timed");
+    S->prm.decode_chunk = bestB;
+    S->prm.block_threads = bestT;
+    if (S->graph_all) {
+        cudaGraphExecDestroy(S->graph_all);
+        S->graph_all = nullptr;
+    }
+    if (threads_out) *threads_out = bestT;
+    if (chunk_out) *chunk_out = bestB;
+    if (best_ms) *best_ms = best;
+    return FFS_OK;
+}
+
 int ffs_islands_destroy(ffs_islands *S)
 {
     islands_free(S);
