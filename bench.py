@@ -217,6 +217,9 @@ def run_ours(args):
     prm.ring_num, prm.ring_den = w.get("mig_num", 2), w.get("mig_den", 100)
     stream = torch.cuda.current_stream()
     isl = ffs.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
+    tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=2)
+    if tuned:
+        prm.decode_chunk, prm.block_threads = tuned["chunk"], tuned["threads"]
     torch.cuda.synchronize()
 
     # ---- warm-up (also builds the CUDA graph) ----
@@ -258,6 +261,8 @@ def run_ours(args):
     clock_info = clocks.stop()
     d1 = ffs.ffs_islands_decoded(isl)
     evals = d1 - d0
+    int_rates = {name: ffs.ffs_measure_int_rate(k)["lane_ops_per_s"] / 1e12
+                 for k, name in enumerate(("min_max", "lop3", "iadd3", "imad"))}
 
     # ---- e2e: the same steps with populations from / to pinned host memory ----
     host_pops = [torch.empty((n_i, spec.n), dtype=torch.int16).pin_memory() for n_i in isl.sizes]
@@ -314,7 +319,9 @@ def run_ours(args):
                      "kernel": "k_cellular (fused tournament + OX + swap + decode + replace)",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": cells * ops_eval,
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                     "launch_shape": ffs.ffs_decode_plan(inst, 1)},
+                     "launch_shape": ffs.ffs_decode_plan(inst, 1, prm.decode_chunk, prm.block_threads),
+                     "autotuned": tuned,
+                     "measured_int_rate_tops": int_rates},
         "clocks": clock_info,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -351,7 +358,7 @@ def run_batch(args):
     specs = make_batch(w["count"], seed=w["seed"])
     prm = ffs.ffs_params_default()
     b = ffs.Batch(specs, prm, w["rows"], w["cols"])
-    tuned = ffs.ffs_batch_autotune(b, repeats=2)
+    tuned = b.info() if args.no_autotune else ffs.ffs_batch_autotune(b, repeats=2)
     stream = torch.cuda.current_stream()
     ffs.ffs_batch_step(b, args.warmup)
     torch.cuda.synchronize()
@@ -500,6 +507,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="scale_500x20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
