@@ -405,6 +405,13 @@ int ffs_selftest_wait_timeout(int64_t limit_ns, int32_t *status, ffs_stream stre
  * draws the same Philox streams as an uninterrupted run.  Synchronous. */
 int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
 
+/* Launch one generation's kernels of one island kind (0: the fused
+ * cellular launch of all cellular islands, 1: the pseudo islands' breed,
+ * decode and replace) exactly as ffs_island_step does, without advancing
+ * the state: only the next-generation buffers are rewritten (for timing and
+ * profiling).  Not with a surrogate attached.  Asynchronous. */
+int ffs_islands_dry_run(ffs_islands *isl, int32_t kind, ffs_stream stream);
+
 /* Time the fused cellular kernel (and the decoder used by the pseudo
  * islands) at every launch shape that fits, on generations that do not
  * advance the state, keep the fastest for both and report it; synchronous. */

@@ -101,6 +101,7 @@ _SIGS = [
     ("ffs_selftest_wait_timeout", _i32, [_i64, _vp, _vp]),
     ("ffs_islands_set_generation", _i32, [_vp, _i64]),
     ("ffs_islands_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    ("ffs_islands_dry_run", _i32, [_vp, _i32, _vp]),
 ]
 
 
@@ -535,3 +536,7 @@ def ffs_islands_autotune(isl: Islands, repeats: int = 2, stream=None) -> dict:
     _check(load().ffs_islands_autotune(isl.handle, repeats, _stream(stream), ctypes.byref(t), ctypes.byref(c),
                                        ctypes.byref(ms)))
     return {"threads": t.value, "chunk": c.value, "ms": ms.value}
+
+
+def ffs_islands_dry_run(isl: Islands, kind: int, stream=None):
+    _check(load().ffs_islands_dry_run(isl.handle, kind, _stream(stream)))

@@ -872,6 +872,22 @@ int ffs_islands_set_generation(ffs_islands *S, int64_t generation)
     return FFS_OK;
 }
 
+int ffs_islands_dry_run(ffs_islands *S, int32_t kind, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (S->sur) return set_error(FFS_EINVAL, "not with a surrogate attached");
+    if (kind != 0 && kind != 1) return set_error(FFS_EINVAL, "kind %d", kind);
+    std::vector<int> ids;
+    for (int i = 0; i < S->I; ++i)
+        if (S->kind[i] == kind) ids.push_back(i);
+    unsigned long long *saved = S->d_decoded;
+    S->d_decoded = nullptr;
+    const int rc = islands_generation_launch(S, ids, (cudaStream_t)stream);
+    S->d_decoded = saved;
+    return rc;
+}
+
 int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int32_t *threads_out, int32_t *chunk_out,
                          float *best_ms)
 {
