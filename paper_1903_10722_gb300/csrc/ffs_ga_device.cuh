@@ -59,23 +59,31 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
         __syncwarp();
         const int start = (r + 1 == n) ? 0 : r + 1;
         int placed = 0;
-        for (int t0 = 0; t0 < n; t0 += 32) {
-            const int t = t0 + lane;
-            int idx = start + t;
-            if (idx >= n) idx -= n;
-            int g = 0;
-            bool take = false;
-            if (t < n) {
-                g = p2[idx];
-                take = !((unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u));
+        // p2 in groups of 8 x 32 genes: the 8 loads of a group are issued
+        // before the ballots that place them
+        for (int t0 = 0; t0 < n; t0 += 256) {
+            int gv[8];
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
+                const int t = t0 + 32 * c8 + lane;
+                int idx = start + t;
+                if (idx >= n) idx -= n;
+                gv[c8] = t < n ? (int)p2[idx] : 0;
             }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
-            if (take) {
-                int pos = start + placed + __popc(m & lt);
-                if (pos >= n) pos -= n;
-                child[pos] = (int16_t)g;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
+                const int t = t0 + 32 * c8 + lane;
+                if (t0 + 32 * c8 >= n) break;
+                const int g = gv[c8];
+                const bool take = t < n && !((unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u));
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+                if (take) {
+                    int pos = start + placed + __popc(m & lt);
+                    if (pos >= n) pos -= n;
+                    child[pos] = (int16_t)g;
+                }
+                placed += __popc(m);
             }
-            placed += __popc(m);
         }
         __syncwarp();
     }

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(512) k_int_rate(int iters, uint32_t seed, uint
             for (int j = 0; j < 8; ++j) {
                 if constexpr (KIND == 0) a[j] = (u & 1) ? min(a[j], b) : max(a[j], c);
                 else if constexpr (KIND == 1) a[j] = (a[j] ^ b) & (c | a[j]);
-                else if constexpr (KIND == 2) a[j] = a[j] + b + c;
+                else if constexpr (KIND == 2) a[j] = a[j] + a[(j + 1) & 7] + c;
                 else a[j] = a[j] * b + c;
             }
         }
