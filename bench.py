@@ -219,7 +219,9 @@ def run_ours(args):
     isl = ffs.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
     tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=2)
     if tuned:
-        prm.decode_chunk, prm.block_threads = tuned["chunk"], tuned["threads"]
+        used = ffs.ffs_islands_params(isl)
+        prm.decode_chunk, prm.block_threads, prm.decode_variant = used.decode_chunk, used.block_threads, used.decode_variant
+        tuned["variant"] = used.decode_variant
     torch.cuda.synchronize()
 
     # ---- warm-up (also builds the CUDA graph) ----

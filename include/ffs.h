@@ -82,12 +82,13 @@ int ffs_population_eval(const ffs_instance *inst, const int16_t *pop, int64_t N,
                         int32_t *makespan, ffs_stream stream);
 
 /* Same, with an explicit launch shape: decode_chunk = jobs per round
- * (multiple of 8; >= n means one round per stage) and block_threads
- * (multiple of 32, <= 512); 0 lets the library choose.  Results do not
- * depend on the shape. */
+ * (multiple of 8; >= n means one round per stage), block_threads
+ * (multiple of 32, <= 512) and variant (0 library choice, 1 one stage at a
+ * time, 2 stages in interleaved pairs); 0 lets the library choose.  Results
+ * do not depend on the shape or variant. */
 int ffs_population_eval_tuned(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
                               int32_t *makespan, int32_t decode_chunk, int32_t block_threads,
-                              ffs_stream stream);
+                              int32_t variant, ffs_stream stream);
 
 /* The launch shape the library uses for a decoding kernel (kernel 0: the
  * batched decoder, 1: the fused cellular generation) given requested
@@ -145,6 +146,7 @@ typedef struct {
     int64_t theta_num, theta_den;  /* penetration threshold theta = num / den, in [0, 1] */
     int32_t decode_chunk;     /* decoder chunk (jobs per round, multiple of 8); 0 = library choice */
     int32_t block_threads;    /* threads per block for the decoder; 0 = library choice */
+    int32_t decode_variant;   /* 0 = library choice, 1 = one stage at a time, 2 = stages in interleaved pairs */
 } ffs_params;
 
 /* Fill *p with the defaults above (seed 7). */
@@ -288,8 +290,9 @@ int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream strea
  * initialises every island and decodes it; synchronous.
  * ffs_batch_step: n_generations generations of every instance; async.
  * ffs_batch_autotune: times every launch shape (threads per block x decode
- * chunk) that fits, `repeats` timed runs each, on generations that do not
- * advance the state, keeps the fastest and reports it; synchronous.
+ * chunk x decoder variant) that fits, `repeats` timed runs each, on
+ * generations that do not advance the state, keeps the fastest and reports
+ * it; synchronous.
  * ffs_batch_get: rows and makespans of one instance (host or device
  * pointers, cudaMemcpyDefault).  ffs_batch_best: best makespan of every
  * instance into best[count] (host), synchronous.
@@ -303,7 +306,7 @@ int ffs_batch_step(ffs_batch *b, int32_t n_generations, ffs_stream stream);
 int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t *threads_out,
                        int32_t *chunk_out, float *best_ms);
 int ffs_batch_info(const ffs_batch *b, int32_t *count, int64_t *generation, int32_t *threads,
-                   int32_t *chunk, int32_t *blocks_per_sm);
+                   int32_t *chunk, int32_t *blocks_per_sm, int32_t *variant);
 int ffs_batch_get(const ffs_batch *b, int32_t instance, int16_t *pop, int32_t ld_out, int32_t *makespan,
                   ffs_stream stream);
 int ffs_batch_best(const ffs_batch *b, int32_t *best, ffs_stream stream);
@@ -411,10 +414,12 @@ int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
  * the state: only the next-generation buffers are rewritten (for timing and
  * profiling).  Not with a surrogate attached.  Asynchronous. */
 int ffs_islands_dry_run(ffs_islands *isl, int32_t kind, ffs_stream stream);
+int ffs_islands_params(const ffs_islands *isl, ffs_params *out);
 
 /* Time the fused cellular kernel (and the decoder used by the pseudo
- * islands) at every launch shape that fits, on generations that do not
- * advance the state, keep the fastest for both and report it; synchronous. */
+ * islands) at every launch shape and decoder variant that fits, on
+ * generations that do not advance the state, keep the fastest for both and
+ * report it (ffs_islands_params returns the parameters in use); synchronous. */
 int ffs_islands_autotune(ffs_islands *isl, int32_t repeats, ffs_stream stream, int32_t *threads_out,
                          int32_t *chunk_out, float *best_ms);
 

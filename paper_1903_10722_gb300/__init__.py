@@ -43,7 +43,7 @@ class ffs_params(ctypes.Structure):
         ("cell_replace_le", _i32), ("pseudo_always", _i32),
         ("migration_mode", _i32), ("migration_gap", _i32),
         ("ring_num", _i64), ("ring_den", _i64), ("theta_num", _i64), ("theta_den", _i64),
-        ("decode_chunk", _i32), ("block_threads", _i32),
+        ("decode_chunk", _i32), ("block_threads", _i32), ("decode_variant", _i32),
     ]
 
 
@@ -53,7 +53,7 @@ _SIGS = [
     ("ffs_instance_create", _i32, [_i32, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
     ("ffs_instance_destroy", _i32, [_vp]),
     ("ffs_population_eval", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
-    ("ffs_population_eval_tuned", _i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i32, _vp]),
+    ("ffs_population_eval_tuned", _i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i32, _i32, _vp]),
     ("ffs_population_eval_host", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ffs_decode_plan", _i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     ("ffs_philox_draws", _i32, [_u64, _u32, _u32, _u32, _u32, _i32, _i32, _vp, _vp]),
@@ -81,7 +81,7 @@ _SIGS = [
     ("ffs_batch_destroy", _i32, [_vp]),
     ("ffs_batch_step", _i32, [_vp, _i32, _vp]),
     ("ffs_batch_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
-    ("ffs_batch_info", _i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_batch_info", _i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("ffs_batch_get", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
     ("ffs_batch_best", _i32, [_vp, _vp, _vp]),
     ("ffs_batch_decoded", _i32, [_vp, _vp, _vp]),
@@ -102,6 +102,7 @@ _SIGS = [
     ("ffs_islands_set_generation", _i32, [_vp, _i64]),
     ("ffs_islands_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     ("ffs_islands_dry_run", _i32, [_vp, _i32, _vp]),
+    ("ffs_islands_params", _i32, [_vp, ctypes.POINTER(ffs_params)]),
 ]
 
 
@@ -210,10 +211,10 @@ def ffs_population_eval(inst: Instance, pop, N: int, ld: int, makespan, stream=N
     _check(load().ffs_population_eval(inst.handle, _ptr(pop), N, ld, _ptr(makespan), _stream(stream)))
 
 
-def ffs_population_eval_tuned(inst: Instance, pop, N, ld, makespan, decode_chunk=0, block_threads=0,
+def ffs_population_eval_tuned(inst: Instance, pop, N, ld, makespan, decode_chunk=0, block_threads=0, variant=0,
                               stream=None):
     _check(load().ffs_population_eval_tuned(inst.handle, _ptr(pop), N, ld, _ptr(makespan),
-                                            decode_chunk, block_threads, _stream(stream)))
+                                            decode_chunk, block_threads, variant, _stream(stream)))
 
 
 def ffs_decode_plan(inst: Instance, kernel: int = 0, decode_chunk: int = 0, block_threads: int = 0) -> dict:
@@ -371,12 +372,12 @@ class Batch:
         self.handle = h
 
     def info(self) -> dict:
-        c, t, b, bps = _i32(), _i32(), _i32(), _i32()
+        c, t, b, bps, v = _i32(), _i32(), _i32(), _i32(), _i32()
         g = _i64()
         _check(load().ffs_batch_info(self.handle, ctypes.byref(c), ctypes.byref(g), ctypes.byref(t),
-                                     ctypes.byref(b), ctypes.byref(bps)))
+                                     ctypes.byref(b), ctypes.byref(bps), ctypes.byref(v)))
         return {"count": c.value, "generation": g.value, "threads": t.value, "chunk": b.value,
-                "blocks_per_sm": bps.value}
+                "blocks_per_sm": bps.value, "variant": v.value}
 
     def close(self):
         if getattr(self, "handle", None):
@@ -540,3 +541,9 @@ def ffs_islands_autotune(isl: Islands, repeats: int = 2, stream=None) -> dict:
 
 def ffs_islands_dry_run(isl: Islands, kind: int, stream=None):
     _check(load().ffs_islands_dry_run(isl.handle, kind, _stream(stream)))
+
+
+def ffs_islands_params(isl: Islands) -> ffs_params:
+    p = ffs_params()
+    _check(load().ffs_islands_params(isl.handle, ctypes.byref(p)))
+    return p

@@ -31,6 +31,7 @@ struct BatchInst {
 struct BatchShape {
     int B;          // jobs per round requested (instances with n <= B run in one round)
     int max_n, max_S, max_tw;
+    int pairs;      // decoder variant: stages in interleaved pairs
 };
 
 __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restrict__ insts, const int2 *__restrict__ units,
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
         L.B = L.single ? round_up(n, 8) : shape.B;
         L.heap_words = L.single ? 0 : I.heap_words;
         L.thread_words = L.heap_words + L.B + 1;
+        L.pairs = shape.pairs;
         L.M = st;
         L.heap_off = st + S;
         IslandRef ref;
@@ -144,6 +146,7 @@ static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *sm
 {
     BatchShape s{};
     s.B = B;
+    s.pairs = pairs_of(b->prm.decode_variant);
     for (const BatchInst &I : b->hinst) {
         s.max_n = std::max(s.max_n, I.n);
         s.max_S = std::max(s.max_S, I.S);
@@ -378,15 +381,17 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
     FFS_CUDA_TRY(cudaEventCreate(&e0));
     FFS_CUDA_TRY(cudaEventCreate(&e1));
     float best = -1.0f;
-    int bestT = b->T, bestB = b->B;
+    int bestT = b->T, bestB = b->B, bestV = b->prm.decode_variant;
     const int Ts[4] = {64, 128, 256, 512};
     const int Bs[5] = {8, 16, 32, 64, 128};
     int rc = FFS_OK;
+    for (int vi = 1; vi <= 2 && !rc; ++vi)
     for (int ti = 0; ti < 4 && !rc; ++ti) {
         for (int bi = 0; bi < 5 && !rc; ++bi) {
             BatchShape s;
             size_t smem;
             int nb;
+            b->prm.decode_variant = vi;
             if (batch_shape(b, Ts[ti], Bs[bi], &s, &smem, &nb)) continue;
             if ((rc = batch_set_shape(b, Ts[ti], Bs[bi], st))) break;
             // writes the next-generation buffers only; the state does not advance
@@ -406,12 +411,14 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
                 best = avg;
                 bestT = Ts[ti];
                 bestB = Bs[bi];
+                bestV = vi;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    b->prm.decode_variant = bestV;
     if ((rc = batch_set_shape(b, bestT, bestB, st))) return rc;
     if (threads_out) *threads_out = bestT;
     if (chunk_out) *chunk_out = bestB;
@@ -420,10 +427,11 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
 }
 
 int ffs_batch_info(const ffs_batch *b, int32_t *count, int64_t *generation, int32_t *threads, int32_t *chunk,
-                   int32_t *blocks_per_sm)
+                   int32_t *blocks_per_sm, int32_t *variant)
 {
     clear_error();
     if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (variant) *variant = b->shape.pairs ? 2 : 1;
     if (count) *count = b->count;
     if (generation) *generation = b->host_gen;
     if (threads) *threads = b->T;

@@ -70,18 +70,22 @@ static std::mutex g_plan_mutex;
 static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req,
                                 int bits_per_warp, Plan *out);
 
-int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp, Plan *out)
+int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp, Plan *out,
+                int variant)
 {
     std::lock_guard<std::mutex> lock(g_plan_mutex);
     for (const auto &e : inst->plan_cache) {
         if (e.first.kernel == kernel && e.first.B_req == B_req && e.first.T_req == T_req &&
-            e.first.bits_per_warp == bits_per_warp) {
+            e.first.bits_per_warp == bits_per_warp && e.first.variant == variant) {
             *out = e.second;
             return FFS_OK;
         }
     }
     int rc = plan_decode_uncached(inst, kernel, B_req, T_req, bits_per_warp, out);
-    if (rc == FFS_OK) inst->plan_cache.push_back({ffs_instance::PlanKey{kernel, B_req, T_req, bits_per_warp}, *out});
+    if (rc == FFS_OK) {
+        out->L.pairs = pairs_of(variant);
+        inst->plan_cache.push_back({ffs_instance::PlanKey{kernel, B_req, T_req, bits_per_warp, variant}, *out});
+    }
     return rc;
 }
 
@@ -160,10 +164,10 @@ const void *eval_kernel() { return (const void *)k_eval; }
 
 int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
                 const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
-                cudaStream_t st)
+                cudaStream_t st, int variant)
 {
     Plan p;
-    int rc = plan_decode(inst, (const void *)k_eval, B_req, T_req, 0, &p);
+    int rc = plan_decode(inst, (const void *)k_eval, B_req, T_req, 0, &p, variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, N);
@@ -351,17 +355,19 @@ int ffs_population_eval(const ffs_instance *I, const int16_t *pop, int64_t N, in
 }
 
 int ffs_population_eval_tuned(const ffs_instance *I, const int16_t *pop, int64_t N, int32_t ld, int32_t *ms,
-                              int32_t decode_chunk, int32_t block_threads, ffs_stream stream)
+                              int32_t decode_chunk, int32_t block_threads, int32_t variant, ffs_stream stream)
 {
     clear_error();
     if (!I) return set_error(FFS_EINVAL, "NULL instance");
     if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
     if (decode_chunk < 0 || block_threads < 0) return set_error(FFS_EINVAL, "negative launch shape");
+    if (variant < 0 || variant > 2) return set_error(FFS_EINVAL, "decoder variant %d", variant);
     if (N == 0) return FFS_OK;
     if (!pop || !ms) return set_error(FFS_EINVAL, "NULL population or output");
     int rc = validate_rows(pop, ld, I->n);
     if (rc) return rc;
-    return launch_eval(I, pop, N, ld, ms, nullptr, decode_chunk, block_threads, nullptr, (cudaStream_t)stream);
+    return launch_eval(I, pop, N, ld, ms, nullptr, decode_chunk, block_threads, nullptr, (cudaStream_t)stream,
+                       variant);
 }
 
 int ffs_decode_plan(const ffs_instance *I, int32_t kernel, int32_t decode_chunk, int32_t block_threads,

@@ -79,6 +79,7 @@ struct DecodeLayout {
     int32_t single;        // 1 if B >= n: one round, heaps stay in registers
     int32_t heap_words;    // sum of M_s (0 when single)
     int32_t thread_words;  // words per thread in the interleaved region
+    int32_t pairs;         // 1: stages run two at a time, interleaved (see pair_round)
     const int32_t *M;        // [S] machines per stage (clamped to n), shared memory
     const int32_t *heap_off; // [S] word offset of each stage's heap, shared memory
 };
@@ -135,22 +136,36 @@ struct WarpStageState {
 //   FIRST: inputs are the chromosome's genes (global int16), else buf.
 //   EMIT : write popped keys to buf (every stage but the last).
 // Returns the number of keys written to buf this round.
+// Scalars of a round passed by value to the per-round functions, which are
+// kept out of line (one call per stage and round, not per job): each is a
+// small function for the compiler, instead of every instantiation inlined
+// into one giant kernel.
+struct RoundIn {
+    int n, B, single;
+    uint32_t mulSH, lowmask;
+};
+
+struct StageOut {
+    int w;              // keys written to buf
+    int flushed;        // heap keys flushed from registers this round
+    uint32_t last_key;  // last stage: the largest key of its heap
+    int bad;            // a gene outside [0, n) was read
+};
+
+// The heap holds Mr <= M real entries; slots from Mr up hold maximal keys,
+// which never pop and never move (used when M is the 32-slot catch-all).
 template <int M, bool FIRST, bool EMIT>
-__device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__restrict__ heap,
-                                           uint32_t *__restrict__ buf, const uint16_t *prow,
-                                           const int16_t *__restrict__ genes, int T, int d0, int cnt,
-                                           uint32_t lowmask, bool &bad_gene, uint32_t *last_key,
-                                           int &flushed_out)
+__device__ __noinline__ StageOut stage_round(RoundIn L, uint32_t *__restrict__ heap, uint32_t *__restrict__ buf,
+                                             const uint16_t *prow, const int16_t *__restrict__ genes, int T, int d0,
+                                             int cnt, int Mr)
 {
+    const uint32_t lowmask = L.lowmask;
+    bool bad_gene = false;
+    StageOut out{0, 0, 0u, 0};
     uint32_t f[M];
-    if (d0 > 0 && !L.single) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) f[m] = heap[m * T];
-    } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) f[m] = 0u;
-    }
-    int skip = M - d0;
+    for (int m = 0; m < M; ++m) f[m] = m < Mr ? ((d0 > 0 && !L.single) ? heap[m * T] : 0u) : 0xFFFFFFFFu;
+    int skip = Mr - d0;
     skip = skip < 0 ? 0 : (skip > cnt ? cnt : skip);
     int w = 0;
     if constexpr (FIRST) {
@@ -205,26 +220,34 @@ __device__ __forceinline__ int stage_round(const DecodeLayout &L, uint32_t *__re
         if constexpr (EMIT) w = cnt - skip;
     }
     const int d1 = d0 + cnt;
-    flushed_out = 0;
     if constexpr (EMIT) {
-        if (d1 == L.n && L.B - w >= M) {
+        if (d1 == L.n && L.B - w >= Mr) {
             // stage complete and the whole heap fits in this round: flush from registers
 #pragma unroll
-            for (int m = 0; m < M; ++m) buf[(w + m) * T] = f[m];
-            w += M;
-            flushed_out = M;
+            for (int m = 0; m < M; ++m)
+                if (m < Mr) buf[(w + m) * T] = f[m];
+            w += Mr;
+            out.flushed = Mr;
         } else if (!L.single) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) heap[m * T] = f[m];
+            for (int m = 0; m < M; ++m)
+                if (m < Mr) heap[m * T] = f[m];
         }
     } else {
         if (!L.single) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) heap[m * T] = f[m];
+            for (int m = 0; m < M; ++m)
+                if (m < Mr) heap[m * T] = f[m];
         }
-        *last_key = f[M - 1];
+        uint32_t lk = f[0];
+#pragma unroll
+        for (int m = 1; m < M; ++m)
+            if (m == Mr - 1) lk = f[m];
+        out.last_key = lk;
     }
-    return w;
+    out.w = w;
+    out.bad = bad_gene ? 1 : 0;
+    return out;
 }
 
 template <bool FIRST, bool EMIT>
@@ -234,17 +257,211 @@ __device__ __forceinline__ int stage_round_dispatch(int M, const DecodeLayout &L
                                                     uint32_t lowmask, bool &bad, uint32_t *last,
                                                     int &fl)
 {
+    const RoundIn R{L.n, L.B, L.single, L.mulSH, lowmask};
+    StageOut o{0, 0, 0u, 0};
 #define FFS_CASE(MM) \
-    case MM: return stage_round<MM, FIRST, EMIT>(L, heap, buf, prow, genes, T, d0, cnt, lowmask, bad, last, fl);
+    case MM: o = stage_round<MM, FIRST, EMIT>(R, heap, buf, prow, genes, T, d0, cnt, M); break;
     switch (M) {
         FFS_CASE(1) FFS_CASE(2) FFS_CASE(3) FFS_CASE(4) FFS_CASE(5) FFS_CASE(6) FFS_CASE(7)
         FFS_CASE(8) FFS_CASE(9) FFS_CASE(10) FFS_CASE(11) FFS_CASE(12) FFS_CASE(13) FFS_CASE(14)
-        FFS_CASE(15) FFS_CASE(16) FFS_CASE(17) FFS_CASE(18) FFS_CASE(19) FFS_CASE(20)
-        FFS_CASE(21) FFS_CASE(22) FFS_CASE(23) FFS_CASE(24) FFS_CASE(25) FFS_CASE(26)
-        FFS_CASE(27) FFS_CASE(28) FFS_CASE(29) FFS_CASE(30) FFS_CASE(31) FFS_CASE(32)
-        default: return 0;
+        FFS_CASE(15) FFS_CASE(16)
+        default: o = stage_round<kMaxM, FIRST, EMIT>(R, heap, buf, prow, genes, T, d0, cnt, M); break;
     }
 #undef FFS_CASE
+    if (o.bad) bad = true;
+    fl = o.flushed;
+    if (!EMIT) *last = o.last_key;
+    return o.w;
+}
+
+// ---------------------------------------------------------------------------
+// Two stages a, b = a + 1 in one loop.  Stage a's pop at step i (its f[0]
+// when the step starts) is stage b's input at the same step, so the two
+// dispatch chains of a step are independent: twice the instruction-level
+// parallelism per chromosome, and the key stream between a and b stays in
+// registers.  Both heaps are held at the larger size M; the smaller one is
+// padded with maximal keys, which never pop and never move.
+//   Phase 1: a's first Ma dispatches pop initial keys (nothing reaches b).
+//   Phase 2: b's first Mb dispatches pop initial keys (nothing emitted).
+//   Phase 3: b's pops go to the buffer (in place: slot w <= slot i).
+// When a has dispatched all n jobs its heap flows into b, and when b has,
+// b's heap flows to the buffer, at most as many keys as the buffer holds
+// this round (the rest in later rounds, from the saved heaps).
+// ---------------------------------------------------------------------------
+struct PairOut {
+    int w, da1, fa1, db1, fb1;
+    uint32_t last_key;
+};
+
+template <int M, bool EMIT_B>
+__device__ __noinline__ PairOut pair_round(RoundIn L, uint32_t *__restrict__ heap_a, uint32_t *__restrict__ heap_b,
+                                           uint32_t *__restrict__ buf, const uint16_t *prow_a, const uint16_t *prow_b,
+                                           int T, int Ma, int Mb, int da0, int fa0, int db0, int fb0, int cnt)
+{
+    const uint32_t lowmask = L.lowmask;
+    const uint32_t idmask = lowmask & ~1u, mulSH = L.mulSH;
+    int da1, fa1, db1, fb1;
+    uint32_t last_key_out = 0u;
+    const bool chunked = !L.single;
+    const int n = L.n;
+    uint32_t fa[M], fb[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        fa[m] = m < Ma ? ((chunked && da0 > 0) ? heap_a[m * T] : 0u) : 0xFFFFFFFFu;
+        fb[m] = m < Mb ? ((chunked && db0 > 0) ? heap_b[m * T] : 0u) : 0xFFFFFFFFu;
+    }
+    int w = 0, db = db0, i = 0;
+    int skip_a = Ma - da0;
+    skip_a = skip_a < 0 ? 0 : (skip_a > cnt ? cnt : skip_a);
+    uint32_t in_a = buf[0];
+    uint32_t pp_a = lds_u16(prow_a, in_a & idmask);
+    for (; i < skip_a; ++i) {
+        const uint32_t in_n = buf[(i + 1) * T];
+        const uint32_t pp_n = lds_u16(prow_a, in_n & idmask);
+        (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
+        in_a = in_n;
+        pp_a = pp_n;
+    }
+    uint32_t e = fa[0];
+    uint32_t pp_e = lds_u16(prow_b, e & idmask);
+    int end2 = i + (Mb - db > 0 ? Mb - db : 0);
+    end2 = end2 > cnt ? cnt : end2;
+    for (; i < end2; ++i) {
+        const uint32_t in_n = buf[(i + 1) * T];
+        const uint32_t pp_n = lds_u16(prow_a, in_n & idmask);
+        (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
+        (void)dispatch_pp<M>(fb, e, pp_e, lowmask, mulSH);
+        ++db;
+        e = fa[0];
+        pp_e = lds_u16(prow_b, e & idmask);
+        in_a = in_n;
+        pp_a = pp_n;
+    }
+#pragma unroll 2
+    for (; i < cnt; ++i) {
+        const uint32_t in_n = buf[(i + 1) * T];
+        const uint32_t pp_n = lds_u16(prow_a, in_n & idmask);
+        (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
+        const uint32_t pb = dispatch_pp<M>(fb, e, pp_e, lowmask, mulSH);
+        ++db;
+        if constexpr (EMIT_B) buf[(w++) * T] = pb;
+        e = fa[0];
+        pp_e = lds_u16(prow_b, e & idmask);
+        in_a = in_n;
+        pp_a = pp_n;
+    }
+    da1 = da0 + cnt;
+    fa1 = fa0;
+    if (chunked) {
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < Ma) heap_a[m * T] = fa[m];
+    }
+    if (da1 == n && fa0 < Ma) {
+        // a is complete: its remaining keys, in order, are b's last inputs
+        if (!chunked) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                if (m < Ma) {
+                    const uint32_t k = fa[m];
+                    const uint32_t pb = dispatch_pp<M>(fb, k, lds_u16(prow_b, k & idmask), lowmask, mulSH);
+                    if (EMIT_B && db >= Mb) buf[(w++) * T] = pb;
+                    ++db;
+                }
+            }
+            fa1 = Ma;
+        } else {
+            int take = Ma - fa0;
+            if (EMIT_B && take > L.B - w) take = L.B - w;
+            for (int t = 0; t < take; ++t) {
+                const uint32_t k = heap_a[(fa0 + t) * T];
+                const uint32_t pb = dispatch_pp<M>(fb, k, lds_u16(prow_b, k & idmask), lowmask, mulSH);
+                if (EMIT_B && db >= Mb) buf[(w++) * T] = pb;
+                ++db;
+            }
+            fa1 = fa0 + take;
+        }
+    }
+    db1 = db;
+    fb1 = fb0;
+    if (chunked) {
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < Mb) heap_b[m * T] = fb[m];
+    }
+    if constexpr (EMIT_B) {
+        if (db1 == n && fb0 < Mb) {
+            if (!chunked) {
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    if (m < Mb) buf[(w++) * T] = fb[m];
+                fb1 = Mb;
+            } else {
+                int take = Mb - fb0;
+                if (take > L.B - w) take = L.B - w;
+                for (int t = 0; t < take; ++t) buf[(w + t) * T] = heap_b[(fb0 + t) * T];
+                w += take;
+                fb1 = fb0 + take;
+            }
+        }
+    } else {
+        uint32_t lk = fb[0];
+#pragma unroll
+        for (int m = 1; m < M; ++m)
+            if (m == Mb - 1) lk = fb[m];
+        last_key_out = lk;
+    }
+    return PairOut{w, da1, fa1, db1, fb1, last_key_out};
+}
+
+template <bool EMIT_B>
+__device__ __forceinline__ int pair_round_dispatch(int Mp, const DecodeLayout &L, uint32_t *heap_a, uint32_t *heap_b,
+                                                   uint32_t *buf, const uint16_t *prow_a, const uint16_t *prow_b,
+                                                   int T, int Ma, int Mb, int da0, int fa0, int db0, int fb0, int cnt,
+                                                   uint32_t lowmask, uint32_t *last_key, int &da1, int &fa1, int &db1,
+                                                   int &fb1)
+{
+    const RoundIn R{L.n, L.B, L.single, L.mulSH, lowmask};
+    PairOut o{0, da0, fa0, db0, fb0, 0u};
+#define FFS_PCASE(MM)                                                                                        \
+    case MM:                                                                                                 \
+        o = pair_round<MM, EMIT_B>(R, heap_a, heap_b, buf, prow_a, prow_b, T, Ma, Mb, da0, fa0, db0, fb0, cnt); \
+        break;
+    switch (Mp) {
+        FFS_PCASE(1) FFS_PCASE(2) FFS_PCASE(3) FFS_PCASE(4) FFS_PCASE(5) FFS_PCASE(6) FFS_PCASE(7)
+        FFS_PCASE(8) FFS_PCASE(9) FFS_PCASE(10) FFS_PCASE(11) FFS_PCASE(12) FFS_PCASE(13) FFS_PCASE(14)
+        FFS_PCASE(15) FFS_PCASE(16) FFS_PCASE(kMaxM)
+        default:
+            o = pair_round<kMaxM, EMIT_B>(R, heap_a, heap_b, buf, prow_a, prow_b, T, Ma, Mb, da0, fa0, db0, fb0, cnt);
+            break;
+    }
+#undef FFS_PCASE
+    da1 = o.da1;
+    fa1 = o.fa1;
+    db1 = o.db1;
+    fb1 = o.fb1;
+    if (!EMIT_B) *last_key = o.last_key;
+    return o.w;
+}
+
+// Stage-0 input keys of the genes [0, cnt) of a chunk, written to buf.
+__device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uint32_t n, uint32_t *buf, int T,
+                                              bool &bad)
+{
+    const int4 *g4 = reinterpret_cast<const int4 *>(genes);
+    for (int i0 = 0; i0 < cnt; i0 += 8) {
+        const int4 v = g4[i0 >> 3];
+        const uint32_t words[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            if (i0 + h < cnt) {
+                uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
+                g = (uint32_t)(int32_t)(int16_t)g;
+                if (g >= n) { bad = true; g = 0; }
+                buf[(i0 + h) * T] = (g + 1u) << 1;
+            }
+        }
+    }
 }
 
 // Decode one chromosome (row of genes in global memory, 16-byte aligned).
@@ -272,6 +489,73 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     // Every round moves stage 0 forward by B jobs or some stage's flush by
     // up to B keys; this bound is never reached by a correct schedule.
     const int max_rounds = (n + L.B - 1) / L.B + S * (kMaxM / 8 + 2) + 2;
+    if (L.pairs) {
+        int s_lo = 0;   // pairs before s_lo (even) are finished
+        for (int round = 0; round < max_rounds; ++round) {
+            int avail = 0;
+            for (int s = s_lo; s < S; s += 2) {
+                const bool lastpair = s + 2 >= S;
+                if (s + 1 == S) {
+                    // odd stage count: the last stage alone
+                    const int M = L.M[s];
+                    const int d0 = wst[s].dispatched;
+                    const int cnt = (s == 0) ? min(L.B, n - d0) : avail;
+                    int fl = 0;
+                    if (cnt > 0) {
+                        if (s == 0)
+                            (void)stage_round_dispatch<true, false>(M, L, region + L.heap_off[s] * T, buf,
+                                                                    ptab + s * table_row_halves(n), row + d0, T, d0,
+                                                                    cnt, lowmask, bad, &last_key, fl);
+                        else
+                            (void)stage_round_dispatch<false, false>(M, L, region + L.heap_off[s] * T, buf,
+                                                                     ptab + s * table_row_halves(n), nullptr, T, d0,
+                                                                     cnt, lowmask, bad, &last_key, fl);
+                    }
+                    __syncwarp();
+                    if (lane == 0) wst[s].dispatched = d0 + cnt;
+                    __syncwarp();
+                    break;
+                }
+                const int a = s, b = s + 1;
+                const int Ma = L.M[a], Mb = L.M[b];
+                const int da0 = wst[a].dispatched, fa0 = wst[a].flushed;
+                const int db0 = wst[b].dispatched, fb0 = wst[b].flushed;
+                const int cnt = (a == 0) ? min(L.B, n - da0) : avail;
+                const bool emit_b = !lastpair || (b != S - 1);
+                int w = 0, da1 = da0, fa1 = fa0, db1 = db0, fb1 = fb0;
+                const bool work = cnt > 0 || (da0 == n && fa0 < Ma) || (emit_b && db0 == n && fb0 < Mb);
+                if (work) {
+                    if (a == 0 && cnt > 0) genes_to_keys(row + da0, cnt, (uint32_t)n, buf, T, bad);
+                    const int Mp = Ma > Mb ? Ma : Mb;
+                    const uint16_t *pa = ptab + a * table_row_halves(n), *pb = ptab + b * table_row_halves(n);
+                    uint32_t *ha = region + L.heap_off[a] * T, *hb = region + L.heap_off[b] * T;
+                    if (emit_b)
+                        w = pair_round_dispatch<true>(Mp, L, ha, hb, buf, pa, pb, T, Ma, Mb, da0, fa0, db0, fb0, cnt,
+                                                      lowmask, &last_key, da1, fa1, db1, fb1);
+                    else
+                        w = pair_round_dispatch<false>(Mp, L, ha, hb, buf, pa, pb, T, Ma, Mb, da0, fa0, db0, fb0, cnt,
+                                                       lowmask, &last_key, da1, fa1, db1, fb1);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    wst[a].dispatched = da1;
+                    wst[a].flushed = fa1;
+                    wst[b].dispatched = db1;
+                    wst[b].flushed = fb1;
+                }
+                __syncwarp();
+                avail = w;
+                const bool done = da1 == n && fa1 == Ma && db1 == n && (!emit_b || fb1 == Mb);
+                if (done && s == s_lo) s_lo += 2;
+                if (avail == 0 && !done) break;
+            }
+            if (wst[S - 1].dispatched >= n) break;
+        }
+        __syncwarp();
+        if (bad) return -1;
+        if (!L.single) last_key = region[(L.heap_off[S - 1] + L.M[S - 1] - 1) * T];
+        return (int32_t)(last_key >> L.SH);
+    }
     int s_lo = 0;   // stages before s_lo have dispatched and emitted everything
     for (int round = 0; round < max_rounds; ++round) {
         int avail = 0;  // keys in buf for the next stage

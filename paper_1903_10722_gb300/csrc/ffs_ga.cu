@@ -58,7 +58,7 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBa
 {
     Plan p;
     const int bits_per_warp = (inst->n + 31) / 32;
-    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p);
+    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p, g.variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, (int64_t)rows * cols * batch.count);
@@ -218,7 +218,8 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, batch, size, inst->n, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
-    int rc = launch_eval(inst, s.children, 2 * (int64_t)pairs, ld, s.child_ms, s.count, B_req, T_req, decoded, st);
+    int rc = launch_eval(inst, s.children, 2 * (int64_t)pairs, ld, s.child_ms, s.count, B_req, T_req, decoded, st,
+                         g.variant);
     if (rc) return rc;
     k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, batch, size, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
@@ -905,18 +906,20 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
     unsigned long long *saved_counter = S->d_decoded;
     S->d_decoded = nullptr;   // the timing runs are not counted
     float best = -1.0f;
-    int bestT = 0, bestB = 0;
+    int bestT = 0, bestB = 0, bestV = 1;
     int rc = FFS_OK;
     const int Ts[4] = {64, 128, 256, 512};
     const int Bs[6] = {8, 16, 32, 64, 128, 0};
+    for (int vi = 1; vi <= 2 && !rc; ++vi)
     for (int ti = 0; ti < 4 && !rc; ++ti) {
         for (int bi = 0; bi < 6 && !rc; ++bi) {
             const int B = Bs[bi] == 0 ? round_up(S->inst->n, 8) : Bs[bi];
             if (Bs[bi] != 0 && B >= S->inst->n) continue;
             Plan p;
-            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], (S->inst->n + 31) / 32, &p)) continue;
+            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], (S->inst->n + 31) / 32, &p, vi)) continue;
             S->prm.decode_chunk = B;
             S->prm.block_threads = Ts[ti];
+            S->prm.decode_variant = vi;
             // one untimed run, then the timed ones; they only rewrite the next-generation buffers
             if ((rc = islands_generation_launch(S, all, st))) break;
             float total = 0.0f;
@@ -934,6 +937,7 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
                 best = avg;
                 bestT = Ts[ti];
                 bestB = B;
+                bestV = vi;
             }
         }
     }
@@ -946,6 +950,7 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
     if (best < 0.0f) return set_error(FFS_EUNSUPPORTED, "no launch shape could be timed");
     S->prm.decode_chunk = bestB;
     S->prm.block_threads = bestT;
+    S->prm.decode_variant = bestV;
     if (S->graph_all) {
         cudaGraphExecDestroy(S->graph_all);
         S->graph_all = nullptr;
@@ -953,6 +958,14 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
     if (threads_out) *threads_out = bestT;
     if (chunk_out) *chunk_out = bestB;
     if (best_ms) *best_ms = best;
+    return FFS_OK;
+}
+
+int ffs_islands_params(const ffs_islands *S, ffs_params *out)
+{
+    clear_error();
+    if (!S || !out) return set_error(FFS_EINVAL, "NULL argument");
+    *out = S->prm;
     return FFS_OK;
 }
 

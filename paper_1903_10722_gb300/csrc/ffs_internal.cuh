@@ -75,7 +75,7 @@ struct ffs_instance {
     int tab_words = 0;
     int num_sms = 0;
     // launch plans already chosen: (kernel, chunk request, threads request, extra words)
-    struct PlanKey { const void *kernel; int B_req, T_req, bits_per_warp; };
+    struct PlanKey { const void *kernel; int B_req, T_req, bits_per_warp, variant; };
     mutable std::vector<std::pair<PlanKey, fgpu::Plan>> plan_cache;
     // buffers of ffs_population_eval_host
     int16_t *d_host_pop = nullptr;
@@ -88,8 +88,10 @@ namespace fgpu {
 // Choose (B, T) for a decoding kernel, honouring requests (0 = choose).
 // bits_per_warp: shared words per warp the kernel needs besides decoding
 // (the crossover bitmask).  kernel: for the occupancy query.
+// variant: 0 = library choice, 1 = one stage at a time, 2 = stages in interleaved pairs.
 int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp,
-                Plan *out);
+                Plan *out, int variant = 0);
+inline int pairs_of(int variant) { return variant == 1 ? 0 : 1; }
 
 // Grid size for N items (persistent, grid-stride).
 inline int grid_for(const ffs_instance *inst, const Plan &p, int64_t N)
@@ -144,6 +146,7 @@ struct IslandBatch {
 struct GaScalars {
     uint64_t seed, cell_pc, cell_pm, pseudo_pc;
     int32_t replace_le, pseudo_always;
+    int32_t variant;   // decoder variant (plan_decode)
 };
 
 inline GaScalars scalars_of(const ffs_params *p)
@@ -155,13 +158,14 @@ inline GaScalars scalars_of(const ffs_params *p)
     g.pseudo_pc = p->pseudo_pc;
     g.replace_le = p->cell_replace_le;
     g.pseudo_always = p->pseudo_always;
+    g.variant = p->decode_variant;
     return g;
 }
 
 // Launchers (defined in the .cu files).
 int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
                 const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
-                cudaStream_t st);
+                cudaStream_t st, int variant = 0);
 int launch_init(const ffs_instance *inst, uint64_t seed, uint32_t island, int kind, int64_t N, int ld,
                 int16_t *pop, cudaStream_t st);
 int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows,

@@ -206,7 +206,7 @@ int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const Island
                       unsigned long long *decoded, cudaStream_t st)
 {
     Plan p;
-    int rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_req, 0, &p);
+    int rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_req, 0, &p, g.variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, (int64_t)rows * cols * batch.count);

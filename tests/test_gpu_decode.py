@@ -50,17 +50,18 @@ def test_eval_matches_oracle(gpu, shape):
     if n > 8:
         shapes.append((8, 64))
     ran = 0
-    for chunk, threads in shapes:
+    shapes = [(c, t, v) for (c, t) in shapes for v in (1, 2)]
+    for chunk, threads, variant in shapes:
         out.fill_(-7)
         try:
-            gpu.ffs_population_eval_tuned(g, d, N, pop.shape[1], out, chunk, threads)
+            gpu.ffs_population_eval_tuned(g, d, N, pop.shape[1], out, chunk, threads, variant)
         except gpu.FFSError as e:
             # a forced shape may not fit shared memory; the library's own choice always does
-            assert e.status == gpu.FFS_EUNSUPPORTED and (chunk, threads) != (0, 0), (chunk, threads)
+            assert e.status == gpu.FFS_EUNSUPPORTED and (chunk, threads) != (0, 0), (chunk, threads, variant)
             continue
         torch.cuda.synchronize()
         got = out.cpu().numpy().astype(np.int64)
-        assert np.array_equal(got, want), (chunk, threads, np.flatnonzero(got != want)[:5])
+        assert np.array_equal(got, want), (chunk, threads, variant, np.flatnonzero(got != want)[:5])
         ran += 1
     assert ran >= len(shapes) // 2
 
@@ -102,7 +103,7 @@ def test_eval_padding_invalid_genes_and_empty(gpu):
     with pytest.raises(gpu.FFSError):
         gpu.ffs_population_eval(g, dev(pop), 20, 12, out)   # ld not a multiple of 8
     with pytest.raises(gpu.FFSError):
-        gpu.ffs_population_eval_tuned(g, dev(pop), 20, ld, out, 12, 0)  # chunk not a multiple of 8
+        gpu.ffs_population_eval_tuned(g, dev(pop), 20, ld, out, 12, 0, 0)  # chunk not a multiple of 8
 
 
 def test_eval_golden_examples(gpu, golden):

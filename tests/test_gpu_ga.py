@@ -18,8 +18,9 @@ def _pair(spec, ffs):
 
 
 def _params(ffs, seed=7, cell_pc=1.0, cell_pm=0.05, pseudo_pc=0.75, le=False, always=False,
-            mode=1, gap=50, ring=(2, 100), theta=(1, 1)):
+            mode=1, gap=50, ring=(2, 100), theta=(1, 1), decode_variant=0):
     p = ffs.ffs_params_default()
+    p.decode_variant = decode_variant
     p.seed = seed
     p.cell_pc, p.cell_pm, p.pseudo_pc = ffs.threshold(cell_pc), ffs.threshold(cell_pm), ffs.threshold(pseudo_pc)
     p.cell_replace_le, p.pseudo_always = int(le), int(always)
@@ -62,7 +63,8 @@ def test_population_init_matches_oracle(gpu):
 
 
 @pytest.mark.parametrize("variant", [dict(), dict(cell_pc=0.6, cell_pm=1.0), dict(le=True, cell_pm=0.3),
-                                     dict(cell_pc=0.0, cell_pm=0.0)])
+                                     dict(cell_pc=0.0, cell_pm=0.0), dict(decode_variant=1),
+                                     dict(decode_variant=2, cell_pm=0.5)])
 def test_cellular_generations_match_oracle(gpu, variant):
     spec = make_instance(20, 5, 3, 3, seed=1)
     o, g = _pair(spec, gpu)
@@ -83,13 +85,13 @@ def test_cellular_generations_match_oracle(gpu, variant):
         a, b, ma, mb = b, a, mb, ma
 
 
-@pytest.mark.parametrize("always", [False, True])
-@pytest.mark.parametrize("shape", [(20, 5, 3, 3, 64), (100, 10, 2, 5, 512), (33, 4, 1, 6, 130)])
-def test_pseudo_generations_match_oracle(gpu, always, shape):
+@pytest.mark.parametrize("always,dvar", [(False, 0), (True, 0), (False, 1)])
+@pytest.mark.parametrize("shape", [(20, 5, 3, 3, 64), (100, 10, 2, 5, 512), (33, 4, 1, 6, 130), (45, 7, 1, 20, 96)])
+def test_pseudo_generations_match_oracle(gpu, always, dvar, shape):
     n, S, mlo, mhi, size = shape
     spec = make_instance(n, S, mlo, mhi, seed=n + S)
     o, g = _pair(spec, gpu)
-    prm, oprm = _params(gpu, seed=5, always=always)
+    prm, oprm = _params(gpu, seed=5, always=always, decode_variant=dvar)
     ld = (n + 7) // 8 * 8
     pop = np.zeros((size, ld), dtype=np.int16)
     for k in range(size // 2):
