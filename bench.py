@@ -487,6 +487,59 @@ def run_surrogate(args):
     return 0
 
 
+def run_decode(args):
+    """The batched decoder alone: makespans of 131072 random job orders of the
+    500 x 20 instance per step (ffs_population_eval_tuned), for each decoder
+    variant at its best launch shape; one JSON line."""
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    from ffs_workloads import random_population, workload_instance
+
+    torch.cuda.set_device(0)
+    spec = workload_instance("scale_500x20")
+    inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p)
+    N = 131072
+    pop = torch.from_numpy(random_population(spec.n, N, seed=11)).cuda()
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ops = N * ops_per_eval(spec.n, spec.M)
+    peaks, peak_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MHZ))
+    num_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
+    results = {}
+    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 64) for t in (64, 128, 256)]
+    for variant in (1, 2):
+        best = None
+        for chunk, threads in shapes:
+            try:
+                ffs.ffs_population_eval_tuned(inst, pop, N, inst.ld, out, chunk, threads, variant)
+            except ffs.FFSError:
+                continue
+            ts = []
+            for _ in range(max(3, args.warmup)):
+                ffs.ffs_population_eval_tuned(inst, pop, N, inst.ld, out, chunk, threads, variant)
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ffs.ffs_population_eval_tuned(inst, pop, N, inst.ld, out, chunk, threads, variant)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            if best is None or ms < best["ms"]:
+                best = {"chunk": chunk, "threads": threads, "ms": ms}
+        best["evals_per_s"] = N / (best["ms"] / 1000.0)
+        best["frac"] = ops / (best["ms"] / 1000.0) / peak_ops
+        results[{1: "single_stage", 2: "stage_pairs"}[variant]] = best
+    line = {"metric": "exact FFS makespan evals/sec (decoder alone)", "workload": "decode_500x20",
+            "chromosomes": N, "ops_per_eval": ops_per_eval(spec.n, spec.M), "peak_tops": peak_ops / 1e12,
+            "peak_basis": peak_kind, "variants": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def launches_per_generation(w) -> int:
     """Kernels of one generation: one fused kernel per cellular island, three
     per pseudo island (breed, decode, replace), one advance, and when
@@ -515,6 +568,8 @@ def main():
         return run_batch(args)
     if args.workload == "surrogate_100x10":
         return run_surrogate(args)
+    if args.workload == "decode_500x20":
+        return run_decode(args)
     return run_ours(args)
 
 
