@@ -257,8 +257,10 @@ int ffs_island_step(ffs_islands *isl, int32_t island, int32_t n_generations, ffs
  * (N = min of the two sizes).  Asynchronous. */
 int ffs_migrate(ffs_islands *isl, int32_t mode, ffs_stream stream);
 
-/* Copy island `island`'s current rows (into pop, row stride ld_out >= n)
- * and makespans out, or in (ffs_islands_set).  Pointers may be host or
+/* Copy island `island`'s current rows (into pop, row stride ld_out >= n;
+ * ld_out equal to the handle's row stride, ffs_islands_info's ld, makes it
+ * one contiguous copy that includes the padding genes) and makespans out,
+ * or in (ffs_islands_set).  Pointers may be host or
  * device memory (copies use cudaMemcpyDefault); either may be NULL to skip.
  * Asynchronous on `stream` (pageable host memory makes the copy
  * synchronous with respect to the host, as CUDA does). */
@@ -408,11 +410,13 @@ int ffs_selftest_wait_timeout(int64_t limit_ns, int32_t *status, ffs_stream stre
  * draws the same Philox streams as an uninterrupted run.  Synchronous. */
 int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
 
-/* Launch one generation's kernels of one island kind (0: the fused
- * cellular launch of all cellular islands, 1: the pseudo islands' breed,
- * decode and replace) exactly as ffs_island_step does, without advancing
- * the state: only the next-generation buffers are rewritten (for timing and
- * profiling).  Not with a surrogate attached.  Asynchronous. */
+/* Launch one generation's kernels (kind 0: the cellular islands alone,
+ * 1: the pseudo islands alone, 2: all islands -- pseudo breed, the fused
+ * decode launch of all cellular cells and pseudo children, pseudo replace --
+ * exactly as ffs_island_step does, migration and generation advance
+ * excepted), without advancing the state: only the next-generation buffers
+ * are rewritten (for timing and profiling).  Not with a surrogate attached.
+ * Asynchronous. */
 int ffs_islands_dry_run(ffs_islands *isl, int32_t kind, ffs_stream stream);
 int ffs_islands_params(const ffs_islands *isl, ffs_params *out);
 

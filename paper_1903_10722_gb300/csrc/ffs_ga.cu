@@ -83,7 +83,8 @@ struct PseudoScratch {
     int16_t *children;
     int32_t *child_ms;
     int32_t *pair_slot;
-    int32_t *count;
+    int32_t *count;   // children this generation
+    int32_t *work;    // next warp work unit of the fused decode launch (count + 1)
 };
 
 static PseudoScratch carve(void *base, int size, int ld, int islands)
@@ -98,6 +99,7 @@ static PseudoScratch carve(void *base, int size, int ld, int islands)
     s.pair_slot = reinterpret_cast<int32_t *>(p);
     p += a256((rows / 2 + 1) * 4);
     s.count = reinterpret_cast<int32_t *>(p);
+    s.work = s.count + 1;
     return s;
 }
 
@@ -204,13 +206,28 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
     warp_copy_rows(valid, src[1], pout + (int64_t)(2 * k + 1) * ld, ld);
 }
 
+static int launch_pseudo_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
+                               int ld, const PseudoScratch &s, cudaStream_t st)
+{
+    const int pairs = size / 2 * batch.count;
+    FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));   // count and work
+    const int words = (inst->n + 31) / 32;
+    const int T = 128;
+    const size_t smem = (size_t)(T / 32) * words * 4;
+    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, batch, size, inst->n, ld, s);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
 int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size, int ld,
                   void *scratch, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
     const int pairs = size / 2 * batch.count;
     if (pairs <= 0) return FFS_OK;
     PseudoScratch s = carve(scratch, size, ld, batch.count);
-    FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, sizeof(int32_t), st));
+    FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));
     const int words = (inst->n + 31) / 32;
     const int T = 128;
     const size_t smem = (size_t)(T / 32) * words * 4;
@@ -222,6 +239,85 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
                          g.variant);
     if (rc) return rc;
     k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, batch, size, ld, s);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One launch for the decoding work of a generation: the fused cellular
+// cells of all cellular islands and the pseudo islands' compacted children.
+// Warps take 32-unit work items from a device counter (cellular items first,
+// they carry the crossover too), so the two kinds share one launch and its
+// last wave instead of each leaving a partly idle wave.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint32_t *__restrict__ tab_g,
+                                                     const int32_t *__restrict__ stage_g, GaScalars g,
+                                                     const __grid_constant__ IslandBatch cb, int rows, int cols, int ld,
+                                                     PseudoScratch ps, unsigned long long *decoded)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int T = blockDim.x;
+    const int bits_per_warp = (L.n + 31) >> 5;
+    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
+    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
+    int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
+    for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    __syncthreads();
+    DecodeLayout Ls = L;
+    Ls.M = st;
+    Ls.heap_off = st + L.S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
+    uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
+    uint32_t *region = smem + map.region + threadIdx.x;
+    const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
+    const int cells = rows * cols;
+    const int C = cells * cb.count, C32 = (C + 31) & ~31;
+    const int P = *ps.count;
+    const int witems = C32 / 32 + (P + 31) / 32;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, (unsigned long long)(C + P));
+    for (;;) {
+        int wu = 0;
+        if (lane == 0) wu = atomicAdd(ps.work, 1);
+        wu = __shfl_sync(0xFFFFFFFFu, wu, 0);
+        if (wu >= witems) break;
+        const int u0 = wu * 32;
+        if (u0 < C32) {
+            const int gc = u0 + lane;
+            const bool valid = gc < C;
+            const int gq = valid ? gc : C - 1;
+            const int bi = gq / cells, c = gq - bi * cells;
+            cellular_warp_cells(Ls, g, cb.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
+        } else {
+            const int k = u0 - C32 + lane;
+            const bool valid = k < P;
+            const int kk = valid ? k : P - 1;
+            const int32_t ms = decode_chromosome(Ls, ps.children + (int64_t)kk * ld, region, T, tab, wst);
+            if (valid) ps.child_ms[k] = ms;
+        }
+    }
+}
+
+// A whole generation of the cellular batch `cb` and the pseudo batch `pb`
+// (same torus for cb, same size for pb): pseudo breed, the fused decode
+// launch, pseudo replace.
+static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const IslandBatch &cb, int rows, int cols,
+                             const IslandBatch &pb, int psize, int ld, void *scratch, int B_req, int T_req,
+                             unsigned long long *decoded, cudaStream_t st)
+{
+    PseudoScratch s = carve(scratch, psize, ld, pb.count);
+    int rc = launch_pseudo_breed(inst, g, pb, psize, ld, s, st);
+    if (rc) return rc;
+    Plan p;
+    const int bits_per_warp = (inst->n + 31) / 32;
+    if ((rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_req, bits_per_warp, &p, g.variant))) return rc;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_step_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    const int64_t units = (int64_t)rows * cols * cb.count + (int64_t)psize * pb.count;
+    const int grid = grid_for(inst, p, units);
+    k_step_decode<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, cb, rows, cols, ld, s, decoded);
+    FFS_CUDA_TRY(cudaGetLastError());
+    const int pairs = psize / 2 * pb.count;
+    k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, pb, psize, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -421,6 +517,22 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
 static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids, cudaStream_t st)
 {
     const GaScalars g = scalars_of(&S->prm);
+    if (!S->sur) {
+        // both kinds present and each fits one batch: one fused decode launch
+        std::vector<int> cel, pse;
+        for (int i : ids) (S->kind[i] == 0 ? cel : pse).push_back(i);
+        if (!cel.empty() && !pse.empty() && (int)cel.size() <= kMaxBatch && (int)pse.size() <= kMaxBatch) {
+            IslandBatch cb, pb;
+            memset(&cb, 0, sizeof(cb));
+            memset(&pb, 0, sizeof(pb));
+            cb.count = (int)cel.size();
+            pb.count = (int)pse.size();
+            for (int t = 0; t < cb.count; ++t) cb.ref[t] = device_ref(S, cel[t]);
+            for (int t = 0; t < pb.count; ++t) pb.ref[t] = device_ref(S, pse[t]);
+            return launch_step_fused(S->inst, g, cb, S->rows, S->cols, pb, S->size[pse[0]], S->ld, S->d_scratch,
+                                     S->prm.decode_chunk, S->prm.block_threads, S->d_decoded, st);
+        }
+    }
     for (int kind = 0; kind < 2; ++kind) {
         std::vector<int> sel;
         for (int i : ids)
@@ -878,10 +990,10 @@ int ffs_islands_dry_run(ffs_islands *S, int32_t kind, ffs_stream stream)
     clear_error();
     if (!S) return set_error(FFS_EINVAL, "NULL islands");
     if (S->sur) return set_error(FFS_EINVAL, "not with a surrogate attached");
-    if (kind != 0 && kind != 1) return set_error(FFS_EINVAL, "kind %d", kind);
+    if (kind < 0 || kind > 2) return set_error(FFS_EINVAL, "kind %d", kind);
     std::vector<int> ids;
     for (int i = 0; i < S->I; ++i)
-        if (S->kind[i] == kind) ids.push_back(i);
+        if (kind == 2 || S->kind[i] == kind) ids.push_back(i);
     unsigned long long *saved = S->d_decoded;
     S->d_decoded = nullptr;
     const int rc = islands_generation_launch(S, ids, (cudaStream_t)stream);
@@ -1072,8 +1184,11 @@ int ffs_islands_get(const ffs_islands *S, int32_t island, int16_t *pop, int32_t 
     cudaStream_t st = (cudaStream_t)stream;
     if (pop) {
         if (ld_out < n) return set_error(FFS_EINVAL, "ld_out %d < n %d", ld_out, n);
-        FFS_CUDA_TRY(cudaMemcpy2DAsync(pop, (size_t)ld_out * 2, S->desc[island].pop[c], (size_t)S->ld * 2,
-                                       (size_t)n * 2, N, cudaMemcpyDefault, st));
+        if (ld_out == S->ld)   // same row stride: one contiguous copy (padding genes included)
+            FFS_CUDA_TRY(cudaMemcpyAsync(pop, S->desc[island].pop[c], (size_t)N * S->ld * 2, cudaMemcpyDefault, st));
+        else
+            FFS_CUDA_TRY(cudaMemcpy2DAsync(pop, (size_t)ld_out * 2, S->desc[island].pop[c], (size_t)S->ld * 2,
+                                           (size_t)n * 2, N, cudaMemcpyDefault, st));
     }
     if (ms) FFS_CUDA_TRY(cudaMemcpyAsync(ms, S->desc[island].ms[c], (size_t)N * 4, cudaMemcpyDefault, st));
     return FFS_OK;
@@ -1089,8 +1204,11 @@ int ffs_islands_set(ffs_islands *S, int32_t island, const int16_t *pop, int32_t 
     cudaStream_t st = (cudaStream_t)stream;
     if (pop) {
         if (ld_in < n) return set_error(FFS_EINVAL, "ld_in %d < n %d", ld_in, n);
-        FFS_CUDA_TRY(cudaMemcpy2DAsync(S->desc[island].pop[c], (size_t)S->ld * 2, pop, (size_t)ld_in * 2,
-                                       (size_t)n * 2, N, cudaMemcpyDefault, st));
+        if (ld_in == S->ld)   // same row stride: one contiguous copy (padding genes included)
+            FFS_CUDA_TRY(cudaMemcpyAsync(S->desc[island].pop[c], pop, (size_t)N * S->ld * 2, cudaMemcpyDefault, st));
+        else
+            FFS_CUDA_TRY(cudaMemcpy2DAsync(S->desc[island].pop[c], (size_t)S->ld * 2, pop, (size_t)ld_in * 2,
+                                           (size_t)n * 2, N, cudaMemcpyDefault, st));
     }
     if (ms) FFS_CUDA_TRY(cudaMemcpyAsync(S->desc[island].ms[c], ms, (size_t)N * 4, cudaMemcpyDefault, st));
     return FFS_OK;
