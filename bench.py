@@ -259,8 +259,9 @@ def run_ours(args):
     clock_info = clocks.stop()
     d1 = ffs.ffs_islands_decoded(isl)
     evals = d1 - d0
-    int_rates = {name: ffs.ffs_measure_int_rate(k)["lane_ops_per_s"] / 1e12
-                 for k, name in enumerate(("min_max", "lop3", "iadd3", "imad"))}
+    int_rates = {name: round(ffs.ffs_measure_int_rate(k)["lane_ops_per_s"] / 1e12, 2)
+                 for k, name in enumerate(("min_max", "lop3", "iadd3", "imad", "fmnmx", "vminmax_u16x2",
+                                           "min3_max3", "add_max", "min_max+imad", "min_max+fmnmx"))}
 
     # ---- e2e: the same steps with populations from / to pinned host memory ----
     # host rows with the library's row stride: each copy is one contiguous transfer
@@ -320,7 +321,8 @@ def run_ours(args):
                                "all pseudo children: decode), timed with its pseudo breed and replace launches",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": decodes_per_launch * ops_eval,
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                     "launch_shape": ffs.ffs_decode_plan(inst, 1, prm.decode_chunk, prm.block_threads),
+                     "launch_shape": ffs.ffs_decode_plan(inst, 2, prm.decode_chunk, prm.block_threads,
+                                                         prm.decode_variant),
                      "autotuned": tuned,
                      "measured_int_rate_tops": int_rates},
         "clocks": clock_info,
@@ -512,8 +514,9 @@ def run_decode(args):
     num_sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
     results = {}
-    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 64) for t in (64, 128, 256)]
-    for variant in (1, 2):
+    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 64) for t in (64, 128, 256, 512)]
+    names = {1: "single_stage", 2: "stage_pairs", 3: "single_stage_tmem", 4: "stage_pairs_tmem"}
+    for variant in (1, 2, 3, 4):
         best = None
         for chunk, threads in shapes:
             try:
@@ -532,10 +535,11 @@ def run_decode(args):
                 ts.append(e0.elapsed_time(e1))
             ms = statistics.median(ts)
             if best is None or ms < best["ms"]:
-                best = {"chunk": chunk, "threads": threads, "ms": ms}
+                best = {"chunk": chunk, "threads": threads, "ms": ms,
+                        "plan": ffs.ffs_decode_plan(inst, 0, chunk, threads, variant)}
         best["evals_per_s"] = N / (best["ms"] / 1000.0)
         best["frac"] = ops / (best["ms"] / 1000.0) / peak_ops
-        results[{1: "single_stage", 2: "stage_pairs"}[variant]] = best
+        results[names[variant]] = best
     line = {"metric": "exact FFS makespan evals/sec (decoder alone)", "workload": "decode_500x20",
             "chromosomes": N, "ops_per_eval": ops_per_eval(spec.n, spec.M), "peak_tops": peak_ops / 1e12,
             "peak_basis": peak_kind, "variants": results}

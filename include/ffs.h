@@ -83,20 +83,28 @@ int ffs_population_eval(const ffs_instance *inst, const int16_t *pop, int64_t N,
 
 /* Same, with an explicit launch shape: decode_chunk = jobs per round
  * (multiple of 8; >= n means one round per stage), block_threads
- * (multiple of 32, <= 512) and variant (0 library choice, 1 one stage at a
- * time, 2 stages in interleaved pairs); 0 lets the library choose.  Results
- * do not depend on the shape or variant. */
+ * (multiple of 32, <= 512) and variant (0 library choice: stage pairs, the
+ * heaps saved between rounds in tensor memory where that fits more threads
+ * per SM; 1 one stage at a time, 2 stages in interleaved pairs, both with
+ * the saved heaps in shared memory; 3 / 4 as 1 / 2 with the saved heaps in
+ * tensor memory whenever the shape allows it, i.e. chunked decoding and a
+ * block size that is a multiple of 128; FFS_EINVAL outside 0..4); 0 lets the
+ * library choose.  Results do not depend on the shape or variant. */
 int ffs_population_eval_tuned(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
                               int32_t *makespan, int32_t decode_chunk, int32_t block_threads,
                               int32_t variant, ffs_stream stream);
 
 /* The launch shape the library uses for a decoding kernel (kernel 0: the
- * batched decoder, 1: the fused cellular generation) given requested
- * decode_chunk / block_threads (0 = choose): jobs per round, threads per
- * block, resident blocks per SM and dynamic shared bytes per block.  Host
- * pointers; any may be NULL.  Synchronous, launches nothing. */
+ * batched decoder, 1: the fused cellular generation, 2: the fused decode
+ * launch of a dual-island generation) given requested decode_chunk /
+ * block_threads (0 = choose) and decoder variant (as in
+ * ffs_population_eval_tuned): jobs per round, threads per block, resident
+ * blocks per SM, dynamic shared bytes per block and the tensor-memory
+ * columns each block allocates for saved heaps (0: none).  Host pointers;
+ * any may be NULL.  Synchronous, launches nothing. */
 int ffs_decode_plan(const ffs_instance *inst, int32_t kernel, int32_t decode_chunk, int32_t block_threads,
-                    int32_t *chunk_out, int32_t *threads_out, int32_t *blocks_per_sm, int64_t *smem_bytes);
+                    int32_t variant, int32_t *chunk, int32_t *threads, int32_t *blocks_per_sm,
+                    int64_t *smem_bytes, int32_t *tmem_cols);
 
 /* Same, with host (pageable or pinned) pop and makespan: copies pop in,
  * decodes and copies the makespans out on `stream`, then synchronises the
@@ -146,7 +154,9 @@ typedef struct {
     int64_t theta_num, theta_den;  /* penetration threshold theta = num / den, in [0, 1] */
     int32_t decode_chunk;     /* decoder chunk (jobs per round, multiple of 8); 0 = library choice */
     int32_t block_threads;    /* threads per block for the decoder; 0 = library choice */
-    int32_t decode_variant;   /* 0 = library choice, 1 = one stage at a time, 2 = stages in interleaved pairs */
+    int32_t decode_variant;   /* as in ffs_population_eval_tuned: 0 = library choice, 1 = one stage at a
+                                 time, 2 = stages in interleaved pairs, 3 / 4 = as 1 / 2 with saved heaps
+                                 in tensor memory (batches: 3 / 4 decode as 1 / 2) */
 } ffs_params;
 
 /* Fill *p with the defaults above (seed 7). */
@@ -393,10 +403,13 @@ int ffs_islands_surrogate_last(const ffs_islands *isl, float *scores, int32_t *c
 
 /* ------------------------------------------------------------------------
  * Measurement and self-tests (no counterpart in the paper).
- * ffs_measure_int_rate: lane operations per second of one 32-bit integer
- * operation kind (0 min/max, 1 three-input logic, 2 add, 3 multiply-add)
- * with 8 independent chains per thread at full occupancy; best of 3 runs;
- * synchronous.
+ * ffs_measure_int_rate: lane operations per second of one 32-bit
+ * operation kind with 8 independent chains per thread at full occupancy;
+ * best of 3 runs; synchronous.  kind: 0 min/max, 1 three-input logic,
+ * 2 add, 3 multiply-add, 4 fp32 min/max on finite non-negative bit
+ * patterns, 5 packed 16-bit min/max, 6 three-input min/max, 7 add-then-max,
+ * 8 min/max and multiply-add alternating, 9 integer and fp32 min/max
+ * alternating; FFS_EINVAL outside 0..9.
  * ffs_selftest_wait_timeout: a kernel waits on an mbarrier that nothing
  * completes, with the same bounded wait the tensor-core kernels use
  * (limit_ns <= 2 s); returns FFS_ETIMEOUT with *status = 1 when the wait gave

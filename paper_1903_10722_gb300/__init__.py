@@ -55,7 +55,7 @@ _SIGS = [
     ("ffs_population_eval", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ffs_population_eval_tuned", _i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i32, _i32, _vp]),
     ("ffs_population_eval_host", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
-    ("ffs_decode_plan", _i32, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    ("ffs_decode_plan", _i32, [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     ("ffs_philox_draws", _i32, [_u64, _u32, _u32, _u32, _u32, _i32, _i32, _vp, _vp]),
     ("ffs_params_default", None, [ctypes.POINTER(ffs_params)]),
     ("ffs_population_init", _i32, [_vp, _u64, _u32, _i32, _i64, _i32, _vp, _vp]),
@@ -217,13 +217,16 @@ def ffs_population_eval_tuned(inst: Instance, pop, N, ld, makespan, decode_chunk
                                             decode_chunk, block_threads, variant, _stream(stream)))
 
 
-def ffs_decode_plan(inst: Instance, kernel: int = 0, decode_chunk: int = 0, block_threads: int = 0) -> dict:
-    """Launch shape of the decoder (kernel 0) or the fused cellular kernel (1)."""
-    B, T, bps = _i32(), _i32(), _i32()
+def ffs_decode_plan(inst: Instance, kernel: int = 0, decode_chunk: int = 0, block_threads: int = 0,
+                    variant: int = 0) -> dict:
+    """Launch shape of the decoder (kernel 0), the fused cellular kernel (1) or
+    the fused decode launch of a dual-island generation (2)."""
+    B, T, bps, tm = _i32(), _i32(), _i32(), _i32()
     sm = _i64()
-    _check(load().ffs_decode_plan(inst.handle, kernel, decode_chunk, block_threads, ctypes.byref(B),
-                                  ctypes.byref(T), ctypes.byref(bps), ctypes.byref(sm)))
-    return {"chunk": B.value, "threads": T.value, "blocks_per_sm": bps.value, "smem_bytes": sm.value}
+    _check(load().ffs_decode_plan(inst.handle, kernel, decode_chunk, block_threads, variant, ctypes.byref(B),
+                                  ctypes.byref(T), ctypes.byref(bps), ctypes.byref(sm), ctypes.byref(tm)))
+    return {"chunk": B.value, "threads": T.value, "blocks_per_sm": bps.value, "smem_bytes": sm.value,
+            "tmem_cols": tm.value}
 
 
 def ffs_population_eval_host(inst: Instance, pop, N, ld, makespan, stream=None):

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_unit;
+    __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const int bits_per_warp = (shape.max_n + 31) >> 5;
     const SmemMap map = smem_map(shape.max_n, shape.max_S, T, bits_per_warp);
@@ -63,19 +64,27 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
         const int n = I.n, S = I.S;
         stage_table(smem + map.tab, I.tab, table_words(n, S));
         for (int i = threadIdx.x; i < 2 * S; i += T) st[i] = I.stage[i];
+        if (threadIdx.x == 0) {
+            DecodeLayout &L = s_L;
+            L.n = n;
+            L.S = S;
+            L.SH = I.SH;
+            L.mulSH = I.mulSH;
+            L.single = shape.B >= n ? 1 : 0;
+            L.B = L.single ? round_up(n, 8) : shape.B;
+            L.heap_words = L.single ? 0 : I.heap_words;
+            L.thread_words = L.heap_words + L.B + 2;
+            L.pairs = shape.pairs;
+            L.tmem_cols = 0;   // saved heaps in shared memory
+            L.tmem_group_cols = 0;
+            L.tmem_stages = 0;
+            L.tmem_split = 0;
+            L.tmem_addr = 0;
+            L.M = st;
+            L.heap_off = st + S;
+        }
         __syncthreads();
-        DecodeLayout L;
-        L.n = n;
-        L.S = S;
-        L.SH = I.SH;
-        L.mulSH = I.mulSH;
-        L.single = shape.B >= n ? 1 : 0;
-        L.B = L.single ? round_up(n, 8) : shape.B;
-        L.heap_words = L.single ? 0 : I.heap_words;
-        L.thread_words = L.heap_words + L.B + 1;
-        L.pairs = shape.pairs;
-        L.M = st;
-        L.heap_off = st + S;
+        const DecodeLayout &L = s_L;
         IslandRef ref;
         memset(&ref, 0, sizeof(ref));
         ref.pop[0] = I.pop[0];
@@ -151,7 +160,7 @@ static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *sm
         s.max_n = std::max(s.max_n, I.n);
         s.max_S = std::max(s.max_S, I.S);
         const bool single = B >= I.n;
-        const int tw = (single ? 0 : I.heap_words) + (single ? round_up(I.n, 8) : B) + 1;
+        const int tw = (single ? 0 : I.heap_words) + (single ? round_up(I.n, 8) : B) + 2;
         s.max_tw = std::max(s.max_tw, tw);
     }
     const SmemMap m = smem_map(s.max_n, s.max_S, T, (s.max_n + 31) / 32);

@@ -42,16 +42,21 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
                                               unsigned long long *decoded)
 {
     extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const SmemMap map = smem_map(L.n, L.S, T);
     if (count_dev) N = *count_dev;
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    if (threadIdx.x == 0) {
+        s_L = L;
+        s_L.M = st;
+        s_L.heap_off = st + L.S;
+    }
     __syncthreads();
-    DecodeLayout Ls = L;
-    Ls.M = st;
-    Ls.heap_off = st + L.S;
+    DecodeLayout &Ls = s_L;
+    decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
     uint32_t *region = smem + map.region + threadIdx.x;
@@ -63,12 +68,13 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
                                              reinterpret_cast<const uint16_t *>(smem + map.tab), wst);
         if (c < N) out[c] = ms;
     }
+    decode_tmem_end(Ls);
 }
 
 static std::mutex g_plan_mutex;
 
 static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req,
-                                int bits_per_warp, Plan *out);
+                                int bits_per_warp, int tmem_pref, Plan *out);
 
 int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp, Plan *out,
                 int variant)
@@ -81,7 +87,7 @@ int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_r
             return FFS_OK;
         }
     }
-    int rc = plan_decode_uncached(inst, kernel, B_req, T_req, bits_per_warp, out);
+    int rc = plan_decode_uncached(inst, kernel, B_req, T_req, bits_per_warp, tmem_of(variant), out);
     if (rc == FFS_OK) {
         out->L.pairs = pairs_of(variant);
         inst->plan_cache.push_back({ffs_instance::PlanKey{kernel, B_req, T_req, bits_per_warp, variant}, *out});
@@ -89,14 +95,32 @@ int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_r
     return rc;
 }
 
+// Resident blocks per SM of `kernel` at this shape, or 0.
+static int occupancy(const void *kernel, int T, size_t smem)
+{
+    int blocks = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, T, smem) != cudaSuccess) return 0;
+    return blocks;
+}
+
+// Candidate shapes: chunk B x block size T, saved heaps in shared memory
+// only, or (chunked decoding, T a multiple of 128) a prefix of the stages'
+// heaps in TMEM with `tb` blocks per SM sharing its 512 columns.  Each TMEM
+// shape pads its shared memory, if needed, so that no more than tb blocks
+// are resident (a further block would wait in its TMEM allocation).  Score:
+// resident threads (saturating at 1024), then fewer rounds, then TMEM or not
+// as tmem_pref says (0: never, 1: only if it gains on the above, 2: preferred).
 static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, int B_req, int T_req,
-                                int bits_per_warp, Plan *out)
+                                int bits_per_warp, int tmem_pref, Plan *out)
 {
     const int n = inst->n, S = inst->S;
     const size_t smem_cap = 232448;  // 227 KB per block on sm_100-class parts
-    int bestT = 0, bestB = 0, bestBlocks = 0;
-    size_t bestSmem = 0;
-    long bestScore = -1;
+    struct Cand {
+        int T = 0, B = 0, blocks = 0, tmem_blocks = 0, group_cols = 0, tstages = 0, split = 0;
+        size_t smem = 0;
+        long score = -1;
+    } best;
     const int single_B = round_up(n, 8);
     int Bs[8];
     int nb = 0;
@@ -116,46 +140,78 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
     } else {
         for (int t : {64, 128, 256, 512}) Ts[nt++] = t;
     }
+    auto consider = [&](const Cand &c, bool single) {
+        const long resident = (long)c.blocks * c.T;
+        const long sat = resident > 1024 ? 1024 : resident;
+        const long rounds_penalty = single ? 0 : (long)(16 * 64 / c.B);
+        Cand k = c;
+        k.score = sat * 64 - rounds_penalty * 8 + (c.T == 128 ? 1 : 0) +
+                  (c.tmem_blocks ? (tmem_pref == 2 ? 2 : -2) : 0);
+        if (k.score > best.score) best = k;
+    };
     for (int bi = 0; bi < nb; ++bi) {
         const int B = Bs[bi];
         const bool single = B >= n;
-        const int tw = (single ? 0 : inst->heap_words) + B + 1;   // +1: prefetch slot
         for (int ti = 0; ti < nt; ++ti) {
             const int T = Ts[ti];
             const SmemMap m = smem_map(n, S, T, bits_per_warp);
-            const size_t smem = (size_t)(m.region + tw * T) * 4u;
-            if (smem > smem_cap) continue;
-            int blocks = 0;
-            if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-                continue;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, T, smem) != cudaSuccess) continue;
-            if (blocks <= 0) continue;
-            // resident threads, saturating at 1024, then fewer rounds (larger B), then fewer blocks
-            long resident = (long)blocks * T;
-            long sat = resident > 1024 ? 1024 : resident;
-            long rounds_penalty = single ? 0 : (long)(16 * 64 / B);
-            long score = sat * 64 - rounds_penalty * 8 + (T == 128 ? 1 : 0);
-            if (score > bestScore) {
-                bestScore = score;
-                bestT = T; bestB = B; bestBlocks = blocks; bestSmem = smem;
+            {
+                const int tw = (single ? 0 : inst->heap_words) + B + 2;   // +2: read-ahead slots
+                Cand c;
+                c.T = T;
+                c.B = B;
+                c.smem = (size_t)(m.region + tw * T) * 4u;
+                if (c.smem <= smem_cap && (c.blocks = occupancy(kernel, T, c.smem)) > 0) consider(c, single);
+            }
+            if (tmem_pref == 0 || single || T % 128 != 0) continue;
+            for (int tb : {1, 2, 4}) {
+                const int groups = T / 128;                 // warps per lane quarter
+                const int cols_block = 512 / tb;
+                const int gcols = cols_block / groups;
+                int split = 0, ns = 0;
+                while (ns < S && split + inst->M_eff[ns] <= gcols) split += inst->M_eff[ns++];
+                if (ns == 0) continue;
+                Cand c;
+                c.T = T;
+                c.B = B;
+                c.tmem_blocks = tb;
+                c.group_cols = gcols;
+                c.tstages = ns;
+                c.split = split;
+                const int tw = inst->heap_words - split + B + 2;
+                c.smem = (size_t)(m.region + tw * T) * 4u;
+                if (c.smem > smem_cap) continue;
+                c.blocks = occupancy(kernel, T, c.smem);
+                while (c.blocks > tb && c.smem + 4096 <= smem_cap) {
+                    c.smem += 4096;
+                    c.blocks = occupancy(kernel, T, c.smem);
+                }
+                if (c.blocks != tb) continue;
+                consider(c, false);
             }
         }
     }
     (void)cudaGetLastError();
-    if (bestScore < 0)
+    if (best.score < 0)
         return set_error(FFS_EUNSUPPORTED, "no decoder launch shape fits shared memory (n=%d, S=%d)", n, S);
     Plan p;
-    p.T = bestT;
-    p.smem = bestSmem;
-    p.blocks_per_sm = bestBlocks;
+    p.T = best.T;
+    p.smem = best.smem;
+    p.blocks_per_sm = best.blocks;
     DecodeLayout &L = p.L;
     memset(&L, 0, sizeof(L));
     L.n = n; L.S = S; L.SH = inst->SH; L.mulSH = 1u << inst->SH;
-    L.single = bestB >= n ? 1 : 0;
-    L.B = L.single ? single_B : bestB;
-    L.heap_words = L.single ? 0 : inst->heap_words;
-    L.thread_words = L.heap_words + L.B + 1;
-    p.smem_words_fixed = smem_map(n, S, bestT, bits_per_warp).region;
+    L.single = best.B >= n ? 1 : 0;
+    L.B = L.single ? single_B : best.B;
+    L.heap_words = L.single ? 0 : inst->heap_words - best.split;
+    L.thread_words = L.heap_words + L.B + 2;
+    if (best.tmem_blocks) {
+        L.tmem_cols = (uint32_t)(512 / best.tmem_blocks);
+        L.tmem_group_cols = best.group_cols;
+        L.tmem_stages = best.tstages;
+        L.tmem_split = best.split;
+    }
+    p.smem_words_fixed = smem_map(n, S, best.T, bits_per_warp).region;
     *out = p;
     return FFS_OK;
 }
@@ -361,7 +417,7 @@ int ffs_population_eval_tuned(const ffs_instance *I, const int16_t *pop, int64_t
     if (!I) return set_error(FFS_EINVAL, "NULL instance");
     if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
     if (decode_chunk < 0 || block_threads < 0) return set_error(FFS_EINVAL, "negative launch shape");
-    if (variant < 0 || variant > 2) return set_error(FFS_EINVAL, "decoder variant %d", variant);
+    if (variant < 0 || variant > kMaxVariant) return set_error(FFS_EINVAL, "decoder variant %d", variant);
     if (N == 0) return FFS_OK;
     if (!pop || !ms) return set_error(FFS_EINVAL, "NULL population or output");
     int rc = validate_rows(pop, ld, I->n);
@@ -371,19 +427,22 @@ int ffs_population_eval_tuned(const ffs_instance *I, const int16_t *pop, int64_t
 }
 
 int ffs_decode_plan(const ffs_instance *I, int32_t kernel, int32_t decode_chunk, int32_t block_threads,
-                    int32_t *chunk_out, int32_t *threads_out, int32_t *blocks_per_sm, int64_t *smem_bytes)
+                    int32_t variant, int32_t *chunk_out, int32_t *threads_out, int32_t *blocks_per_sm,
+                    int64_t *smem_bytes, int32_t *tmem_cols)
 {
     clear_error();
     if (!I) return set_error(FFS_EINVAL, "NULL instance");
-    if (kernel != 0 && kernel != 1) return set_error(FFS_EINVAL, "kernel %d is not 0 or 1", kernel);
+    if (kernel < 0 || kernel > 2) return set_error(FFS_EINVAL, "kernel %d is not 0, 1 or 2", kernel);
+    if (variant < 0 || variant > kMaxVariant) return set_error(FFS_EINVAL, "decoder variant %d", variant);
     Plan p;
-    int rc = plan_decode(I, kernel == 0 ? eval_kernel() : cellular_kernel(), decode_chunk, block_threads,
-                         kernel == 0 ? 0 : (I->n + 31) / 32, &p);
+    const void *k = kernel == 0 ? eval_kernel() : kernel == 1 ? cellular_kernel() : step_decode_kernel();
+    int rc = plan_decode(I, k, decode_chunk, block_threads, kernel == 0 ? 0 : (I->n + 31) / 32, &p, variant);
     if (rc) return rc;
     if (chunk_out) *chunk_out = p.L.B;
     if (threads_out) *threads_out = p.T;
     if (blocks_per_sm) *blocks_per_sm = p.blocks_per_sm;
     if (smem_bytes) *smem_bytes = (int64_t)p.smem;
+    if (tmem_cols) *tmem_cols = (int32_t)p.L.tmem_cols;
     return FFS_OK;
 }
 

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ffs_tc.cuh"
+
 namespace fgpu {
 
 constexpr int kMaxM = 32;        // machines per stage after clamping to n
@@ -68,30 +70,168 @@ __device__ __forceinline__ bool fires(uint32_t x, uint64_t threshold) { return (
 //
 // To bound shared memory for long chromosomes, the jobs flow through the
 // stages in rounds of at most B keys: a stage consumes what the previous
-// stage emitted this round; its heap is saved in shared memory between
-// rounds.  Per-thread shared words: sum_s M_s (heaps, skipped when B >= n)
-// + B (buffer), thread-interleaved (word w of thread t at w * T + t).
+// stage emitted this round; its heap is saved between rounds.  Per-thread
+// shared words: the saved heaps (skipped when B >= n) + B (buffer) + 2
+// (read-ahead slots), thread-interleaved (word w of thread t at w * T + t).
+//
+// Saved heaps in tensor memory: the decoder does no MMA, so the SM's 256 KB
+// of TMEM (128 lanes x 512 columns of 32 bits) is free storage.  A warp may
+// only touch the 32 lanes of its quarter (warp index mod 4), one lane per
+// thread, so the warps of a quarter split the block's columns: warp w owns
+// columns [(w / 4) * tmem_group_cols, +tmem_group_cols) of lanes 32 (w mod 4)
+// .. +31.  The heaps of the first tmem_stages stages (tmem_split words)
+// live there, the others in shared memory, which then holds fewer words per
+// thread and more threads per SM.
 // ---------------------------------------------------------------------------
 struct DecodeLayout {
     int32_t n, S, SH;
     uint32_t mulSH;        // 1 << SH
     int32_t B;             // keys per round (multiple of 8)
     int32_t single;        // 1 if B >= n: one round, heaps stay in registers
-    int32_t heap_words;    // sum of M_s (0 when single)
+    int32_t heap_words;    // saved-heap words in shared memory (0 when single)
     int32_t thread_words;  // words per thread in the interleaved region
     int32_t pairs;         // 1: stages run two at a time, interleaved (see pair_round)
+    uint32_t tmem_cols;    // TMEM columns the block allocates (0: no TMEM)
+    int32_t tmem_group_cols;  // columns per warp of a lane quarter
+    int32_t tmem_stages;   // stages [0, tmem_stages) keep their heaps in TMEM
+    int32_t tmem_split;    // their heap words (= heap_off[tmem_stages])
+    uint32_t tmem_addr;    // the block's TMEM base address, written by the allocation
     const int32_t *M;        // [S] machines per stage (clamped to n), shared memory
-    const int32_t *heap_off; // [S] word offset of each stage's heap, shared memory
+    const int32_t *heap_off; // [S] word offset of each stage's heap (prefix sums of M), shared memory
 };
+
+// ---------------------------------------------------------------------------
+// Shared-memory access by 32-bit shared-window address.  The per-round
+// functions below are out of line (one call per stage and round); passing
+// them 32-bit shared addresses instead of generic pointers keeps their
+// arguments few (all in registers) and their loads and stores in the shared
+// space.  One thread's words are T apart (stride = 4T bytes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lds32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lds16(uint32_t a)
+{
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+
+// A stage's saved heap as one word: bit 31 set -> TMEM address of the
+// thread's first heap word (consecutive columns of its lane; TMEM addresses
+// never use bit 31), else the shared address of its first word (stride 4T).
+constexpr uint32_t kHeapInTmem = 0x80000000u;
+
+__device__ __forceinline__ uint32_t heap_handle(const DecodeLayout &L, uint32_t region_sa, int T, int s)
+{
+    const int off = L.heap_off[s];
+    if (s < L.tmem_stages) {
+        const int warp = threadIdx.x >> 5;
+        return kHeapInTmem | (L.tmem_addr + ((uint32_t)((warp & 3) * 32) << 16) +
+                              (uint32_t)((warp >> 2) * L.tmem_group_cols + off));
+    }
+    return region_sa + (uint32_t)((off - L.tmem_split) * T) * 4u;
+}
+
+// Saved heap -> f[0, Mr) (the other slots keep their values).  TMEM loads
+// are issued together and waited for once, after the thread's earlier TMEM
+// stores have completed.
+template <int M>
+__device__ __forceinline__ void heap_load(uint32_t h, uint32_t (&f)[M], int Mr, uint32_t stride)
+{
+    if (h & kHeapInTmem) {
+        const uint32_t ta = h & ~kHeapInTmem;
+        tc::tmem_wait_st();
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < Mr) f[m] = tc::tmem_ld1(ta + (uint32_t)m);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int m = 0; m < M; ++m) tc::reg_fence(f[m]);
+    } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < Mr) f[m] = lds32(h + (uint32_t)m * stride);
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void heap_store(uint32_t h, const uint32_t (&f)[M], int Mr, uint32_t stride)
+{
+    if (h & kHeapInTmem) {
+        const uint32_t ta = h & ~kHeapInTmem;
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < Mr) tc::tmem_st1(ta + (uint32_t)m, f[m]);
+    } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < Mr) sts32(h + (uint32_t)m * stride, f[m]);
+    }
+}
+
+// One word of a saved heap.
+__device__ __forceinline__ uint32_t heap_read1(uint32_t h, int idx, uint32_t stride)
+{
+    if (h & kHeapInTmem) {
+        tc::tmem_wait_st();
+        uint32_t v = tc::tmem_ld1((h & ~kHeapInTmem) + (uint32_t)idx);
+        tc::tmem_wait_ld();
+        tc::reg_fence(v);
+        return v;
+    }
+    return lds32(h + (uint32_t)idx * stride);
+}
+
+// f[idx] for a warp-uniform runtime idx, without indexing the register array.
+template <int M>
+__device__ __forceinline__ uint32_t pick_key(const uint32_t (&f)[M], int idx)
+{
+    uint32_t k = f[0];
+#pragma unroll
+    for (int m = 1; m < M; ++m) k = (idx == m) ? f[m] : k;
+    return k;
+}
+
+// The block's decoding layout lives in shared memory (one copy per block,
+// written by thread 0 before a barrier): the decoder reads its fields there
+// again after each out-of-line per-round call instead of keeping them live
+// in registers across the call.
+// decode_tmem_begin: called by all threads after that barrier; warp 0
+// allocates the TMEM columns for the saved heaps (the address lands in
+// Lsh.tmem_addr).  decode_tmem_end frees them; every thread of the block
+// must reach it.
+__device__ __forceinline__ void decode_tmem_begin(DecodeLayout &Lsh)
+{
+    if (Lsh.tmem_cols == 0) return;
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&Lsh.tmem_addr, Lsh.tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ __forceinline__ void decode_tmem_end(const DecodeLayout &Lsh)
+{
+    if (Lsh.tmem_cols == 0) return;
+    tc::tmem_wait_st();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(Lsh.tmem_addr, Lsh.tmem_cols);
+}
 
 // Shared-memory table of processing times (uint16): row s holds n + 1
 // entries (padded to an even count), entry j + 1 = p[j][s] (entry 0 = 0), so
 // the low bits of a key, (job + 1) << 1, are the byte offset of the job's entry.
-__device__ __forceinline__ uint32_t lds_u16(const uint16_t *row, uint32_t byte_off)
-{
-    return *reinterpret_cast<const uint16_t *>(reinterpret_cast<const char *>(row) + byte_off);
-}
-
 __host__ __device__ inline int table_row_halves(int n) { return (n + 2) & ~1; }
 
 // One dispatch: f[] sorted ascending, pops f[0], inserts the completion key
@@ -119,52 +259,46 @@ __device__ __forceinline__ uint32_t dispatch_pp(uint32_t (&f)[M], uint32_t in, u
     return f0;
 }
 
-template <int M>
-__device__ __forceinline__ uint32_t dispatch(uint32_t (&f)[M], uint32_t in, const uint16_t *prow,
-                                             uint32_t lowmask, uint32_t mulSH)
-{
-    return dispatch_pp<M>(f, in, lds_u16(prow, in & lowmask), lowmask, mulSH);
-}
-
 // Per-warp round bookkeeping lives in shared memory (identical in all lanes).
 struct WarpStageState {
     int32_t dispatched;
     int32_t flushed;
 };
 
-// Run one stage for one round.
-//   FIRST: inputs are the chromosome's genes (global int16), else buf.
-//   EMIT : write popped keys to buf (every stage but the last).
-// Returns the number of keys written to buf this round.
-// Scalars of a round passed by value to the per-round functions, which are
-// kept out of line (one call per stage and round, not per job): each is a
-// small function for the compiler, instead of every instantiation inlined
-// into one giant kernel.
-struct RoundIn {
-    int n, B, single;
-    uint32_t mulSH, lowmask;
-};
-
-struct StageOut {
-    int w;              // keys written to buf
-    int flushed;        // heap keys flushed from registers this round
-    uint32_t last_key;  // last stage: the largest key of its heap
-    int bad;            // a gene outside [0, n) was read
-};
-
+// ---------------------------------------------------------------------------
+// One stage for one round, out of line.  Arguments, packed into 32-bit words:
+//   nB   = n | B << 16              SH: key shift
+//   heap = saved-heap handle        buf, prow: shared addresses (the buffer's
+//          slot 0 of this thread, the stage's table row)
+//   genes: FIRST only, the chromosome's genes [d0, d0 + cnt) (global int16)
+//   dc   = d0 | cnt << 16           (jobs dispatched before; inputs this round)
+//   mf   = Mr | fl0 << 8            (real heap slots; keys flushed before)
+// FIRST: inputs are the genes, else buf.  EMIT: popped keys go to buf (every
+// stage but the last).  cnt = 0: a call that only continues the stage's
+// final flush.  Once the stage has dispatched all n jobs its heap (sorted)
+// follows its pops into buf, as far as the B slots allow this round.
+// Returns x = keys written | flushed total << 16 | bad gene << 24, y = the
+// heap's largest key (last stage).
 // The heap holds Mr <= M real entries; slots from Mr up hold maximal keys,
 // which never pop and never move (used when M is the 32-slot catch-all).
+// ---------------------------------------------------------------------------
 template <int M, bool FIRST, bool EMIT>
-__device__ __noinline__ StageOut stage_round(RoundIn L, uint32_t *__restrict__ heap, uint32_t *__restrict__ buf,
-                                             const uint16_t *prow, const int16_t *__restrict__ genes, int T, int d0,
-                                             int cnt, int Mr)
+__device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf, uint32_t prow,
+                                          const int16_t *__restrict__ genes, uint32_t dc, uint32_t mf)
 {
-    const uint32_t lowmask = L.lowmask;
+    const int n = (int)(nB & 0xFFFFu), B = (int)(nB >> 16);
+    const int d0 = (int)(dc & 0xFFFFu), cnt = (int)(dc >> 16);
+    const int Mr = (int)(mf & 0xFFu), fl0 = (int)(mf >> 8);
+    const uint32_t mulSH = 1u << SH, lowmask = mulSH - 1u, idmask = lowmask & ~1u;
+    const uint32_t stride = blockDim.x * 4u;
+    const bool single = B >= n;
     bool bad_gene = false;
-    StageOut out{0, 0, 0u, 0};
+    // every slot defined before the conditional load (a partly defined
+    // array here costs the whole kernel half its registers)
     uint32_t f[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) f[m] = m < Mr ? ((d0 > 0 && !L.single) ? heap[m * T] : 0u) : 0xFFFFFFFFu;
+    for (int m = 0; m < M; ++m) f[m] = m < Mr ? 0u : 0xFFFFFFFFu;
+    if (d0 > 0 && !single) heap_load<M>(heap, f, Mr, stride);
     int skip = Mr - d0;
     skip = skip < 0 ? 0 : (skip > cnt ? cnt : skip);
     int w = 0;
@@ -172,8 +306,7 @@ __device__ __noinline__ StageOut stage_round(RoundIn L, uint32_t *__restrict__ h
         // genes arrive 8 per 16-byte load, one load ahead; cnt is a multiple of 8
         // except at the tail (rows are padded to 8 genes, so the load stays in the row)
         const int4 *g4 = reinterpret_cast<const int4 *>(genes);
-        const uint32_t n = (uint32_t)L.n;
-        int4 vnext = g4[0];
+        int4 vnext = cnt > 0 ? g4[0] : make_int4(0, 0, 0, 0);
         for (int i0 = 0; i0 < cnt; i0 += 8) {
             const int4 v = vnext;
             if (i0 + 8 < cnt) vnext = g4[(i0 >> 3) + 1];
@@ -183,95 +316,91 @@ __device__ __noinline__ StageOut stage_round(RoundIn L, uint32_t *__restrict__ h
                 if (i0 + h < cnt) {
                     uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
                     g = (uint32_t)(int32_t)(int16_t)g;
-                    if (g >= n) { bad_gene = true; g = 0; }
+                    if (g >= (uint32_t)n) { bad_gene = true; g = 0; }
                     const uint32_t in = (g + 1u) << 1;
-                    const uint32_t popped = dispatch<M>(f, in, prow, lowmask, L.mulSH);
+                    const uint32_t popped = dispatch_pp<M>(f, in, lds16(prow + (in & idmask)), lowmask, mulSH);
                     if constexpr (EMIT) {
-                        if (i0 + h >= skip) { buf[w * T] = popped; ++w; }
+                        if (i0 + h >= skip) { sts32(buf + (uint32_t)w * stride, popped); ++w; }
                     }
                 }
             }
         }
-    } else {
-        // The next key and its processing time are loaded one step ahead: the
-        // store of step i goes to slot i - skip <= i, never to slot i + 1.
-        // Slot cnt may be read (the region has one spare word per thread).
-        const uint32_t idmask = lowmask & ~1u;
-        const uint32_t mulSH = L.mulSH;
-        uint32_t in = buf[0];
-        uint32_t pp = lds_u16(prow, in & idmask);
+    } else if (cnt > 0) {
+        // Keys are read two steps ahead and their processing times one step
+        // ahead: the store of step i goes to slot i - skip <= i, never to a
+        // slot still to be read.  Slots cnt and cnt + 1 may be read (the
+        // region has two spare words per thread).
+        uint32_t in = lds32(buf), in_n = lds32(buf + stride);
+        uint32_t pp = lds16(prow + (in & idmask));
+        uint32_t rd = buf + 2u * stride;
         int i = 0;
         for (; i < skip; ++i) {
-            const uint32_t in_n = buf[(i + 1) * T];
-            const uint32_t pp_n = lds_u16(prow, in_n & idmask);
+            const uint32_t in_nn = lds32(rd);
+            const uint32_t pp_n = lds16(prow + (in_n & idmask));
             (void)dispatch_pp<M>(f, in, pp, lowmask, mulSH);
             in = in_n;
+            in_n = in_nn;
             pp = pp_n;
+            rd += stride;
         }
+        uint32_t wr = buf;
 #pragma unroll 4
         for (; i < cnt; ++i) {
-            const uint32_t in_n = buf[(i + 1) * T];
-            const uint32_t pp_n = lds_u16(prow, in_n & idmask);
+            const uint32_t in_nn = lds32(rd);
+            const uint32_t pp_n = lds16(prow + (in_n & idmask));
             const uint32_t popped = dispatch_pp<M>(f, in, pp, lowmask, mulSH);
-            if constexpr (EMIT) buf[(i - skip) * T] = popped;
+            if constexpr (EMIT) {
+                sts32(wr, popped);
+                wr += stride;
+            }
             in = in_n;
+            in_n = in_nn;
             pp = pp_n;
+            rd += stride;
         }
         if constexpr (EMIT) w = cnt - skip;
     }
     const int d1 = d0 + cnt;
+    uint2 out;
+    out.y = 0u;
     if constexpr (EMIT) {
-        if (d1 == L.n && L.B - w >= Mr) {
-            // stage complete and the whole heap fits in this round: flush from registers
-#pragma unroll
-            for (int m = 0; m < M; ++m)
-                if (m < Mr) buf[(w + m) * T] = f[m];
-            w += Mr;
-            out.flushed = Mr;
-        } else if (!L.single) {
-#pragma unroll
-            for (int m = 0; m < M; ++m)
-                if (m < Mr) heap[m * T] = f[m];
+        int fl = fl0;
+        if (d1 == n && fl < Mr) {
+            // the stage is complete: its heap keys, in order, follow
+            const int room = B - w;
+            const int take = (Mr - fl) < room ? (Mr - fl) : room;
+            for (int t = 0; t < take; ++t) sts32(buf + (uint32_t)(w + t) * stride, pick_key<M>(f, fl + t));
+            w += take;
+            fl += take;
         }
+        if (!single && fl < Mr) heap_store<M>(heap, f, Mr, stride);
+        out.x = (uint32_t)w | (uint32_t)fl << 16;
     } else {
-        if (!L.single) {
-#pragma unroll
-            for (int m = 0; m < M; ++m)
-                if (m < Mr) heap[m * T] = f[m];
-        }
+        if (!single) heap_store<M>(heap, f, Mr, stride);
         uint32_t lk = f[0];
 #pragma unroll
         for (int m = 1; m < M; ++m)
             if (m == Mr - 1) lk = f[m];
-        out.last_key = lk;
+        out.y = lk;
+        out.x = (uint32_t)fl0 << 16;
     }
-    out.w = w;
-    out.bad = bad_gene ? 1 : 0;
+    if (bad_gene) out.x |= 1u << 24;
     return out;
 }
 
 template <bool FIRST, bool EMIT>
-__device__ __forceinline__ int stage_round_dispatch(int M, const DecodeLayout &L, uint32_t *heap,
-                                                    uint32_t *buf, const uint16_t *prow,
-                                                    const int16_t *genes, int T, int d0, int cnt,
-                                                    uint32_t lowmask, bool &bad, uint32_t *last,
-                                                    int &fl)
+__device__ __forceinline__ uint2 stage_round_dispatch(int M, uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf,
+                                                      uint32_t prow, const int16_t *genes, uint32_t dc, uint32_t mf)
 {
-    const RoundIn R{L.n, L.B, L.single, L.mulSH, lowmask};
-    StageOut o{0, 0, 0u, 0};
 #define FFS_CASE(MM) \
-    case MM: o = stage_round<MM, FIRST, EMIT>(R, heap, buf, prow, genes, T, d0, cnt, M); break;
+    case MM: return stage_round<MM, FIRST, EMIT>(nB, SH, heap, buf, prow, genes, dc, mf);
     switch (M) {
         FFS_CASE(1) FFS_CASE(2) FFS_CASE(3) FFS_CASE(4) FFS_CASE(5) FFS_CASE(6) FFS_CASE(7)
         FFS_CASE(8) FFS_CASE(9) FFS_CASE(10) FFS_CASE(11) FFS_CASE(12) FFS_CASE(13) FFS_CASE(14)
         FFS_CASE(15) FFS_CASE(16)
-        default: o = stage_round<kMaxM, FIRST, EMIT>(R, heap, buf, prow, genes, T, d0, cnt, M); break;
+        default: return stage_round<kMaxM, FIRST, EMIT>(nB, SH, heap, buf, prow, genes, dc, mf);
     }
 #undef FFS_CASE
-    if (o.bad) bad = true;
-    fl = o.flushed;
-    if (!EMIT) *last = o.last_key;
-    return o.w;
 }
 
 // ---------------------------------------------------------------------------
@@ -287,166 +416,158 @@ __device__ __forceinline__ int stage_round_dispatch(int M, const DecodeLayout &L
 // When a has dispatched all n jobs its heap flows into b, and when b has,
 // b's heap flows to the buffer, at most as many keys as the buffer holds
 // this round (the rest in later rounds, from the saved heaps).
+// Arguments as in stage_round, with mm = Ma | Mb << 8 | fa0 << 16 | fb0 << 24
+// and dd = da0 | db0 << 16.  Returns x = keys written | fa1 << 16 |
+// fb1 << 24, y = da1 | db1 << 16, z = b's largest key (last pair).
 // ---------------------------------------------------------------------------
-struct PairOut {
-    int w, da1, fa1, db1, fb1;
-    uint32_t last_key;
-};
-
 template <int M, bool EMIT_B>
-__device__ __noinline__ PairOut pair_round(RoundIn L, uint32_t *__restrict__ heap_a, uint32_t *__restrict__ heap_b,
-                                           uint32_t *__restrict__ buf, const uint16_t *prow_a, const uint16_t *prow_b,
-                                           int T, int Ma, int Mb, int da0, int fa0, int db0, int fb0, int cnt)
+__device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap_a, uint32_t heap_b, uint32_t buf,
+                                         uint32_t prow_a, uint32_t prow_b, uint32_t mm, uint32_t dd, int cnt)
 {
-    const uint32_t lowmask = L.lowmask;
-    const uint32_t idmask = lowmask & ~1u, mulSH = L.mulSH;
-    int da1, fa1, db1, fb1;
-    uint32_t last_key_out = 0u;
-    const bool chunked = !L.single;
-    const int n = L.n;
+    const int n = (int)(nB & 0xFFFFu), B = (int)(nB >> 16);
+    const int Ma = (int)(mm & 0xFFu), Mb = (int)((mm >> 8) & 0xFFu);
+    const int fa0 = (int)((mm >> 16) & 0xFFu), fb0 = (int)(mm >> 24);
+    const int da0 = (int)(dd & 0xFFFFu), db0 = (int)(dd >> 16);
+    const uint32_t mulSH = 1u << SH, lowmask = mulSH - 1u, idmask = lowmask & ~1u;
+    const uint32_t stride = blockDim.x * 4u;
+    const bool chunked = B < n;
     uint32_t fa[M], fb[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        fa[m] = m < Ma ? ((chunked && da0 > 0) ? heap_a[m * T] : 0u) : 0xFFFFFFFFu;
-        fb[m] = m < Mb ? ((chunked && db0 > 0) ? heap_b[m * T] : 0u) : 0xFFFFFFFFu;
+        fa[m] = m < Ma ? 0u : 0xFFFFFFFFu;
+        fb[m] = m < Mb ? 0u : 0xFFFFFFFFu;
     }
+    if (chunked && da0 > 0) heap_load<M>(heap_a, fa, Ma, stride);
+    if (chunked && db0 > 0) heap_load<M>(heap_b, fb, Mb, stride);
     int w = 0, db = db0, i = 0;
-    int skip_a = Ma - da0;
-    skip_a = skip_a < 0 ? 0 : (skip_a > cnt ? cnt : skip_a);
-    uint32_t in_a = buf[0];
-    uint32_t pp_a = lds_u16(prow_a, in_a & idmask);
-    for (; i < skip_a; ++i) {
-        const uint32_t in_n = buf[(i + 1) * T];
-        const uint32_t pp_n = lds_u16(prow_a, in_n & idmask);
-        (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
-        in_a = in_n;
-        pp_a = pp_n;
-    }
-    uint32_t e = fa[0];
-    uint32_t pp_e = lds_u16(prow_b, e & idmask);
-    int end2 = i + (Mb - db > 0 ? Mb - db : 0);
-    end2 = end2 > cnt ? cnt : end2;
-    for (; i < end2; ++i) {
-        const uint32_t in_n = buf[(i + 1) * T];
-        const uint32_t pp_n = lds_u16(prow_a, in_n & idmask);
-        (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
-        (void)dispatch_pp<M>(fb, e, pp_e, lowmask, mulSH);
-        ++db;
-        e = fa[0];
-        pp_e = lds_u16(prow_b, e & idmask);
-        in_a = in_n;
-        pp_a = pp_n;
-    }
-#pragma unroll 2
-    for (; i < cnt; ++i) {
-        const uint32_t in_n = buf[(i + 1) * T];
-        const uint32_t pp_n = lds_u16(prow_a, in_n & idmask);
-        (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
-        const uint32_t pb = dispatch_pp<M>(fb, e, pp_e, lowmask, mulSH);
-        ++db;
-        if constexpr (EMIT_B) buf[(w++) * T] = pb;
-        e = fa[0];
-        pp_e = lds_u16(prow_b, e & idmask);
-        in_a = in_n;
-        pp_a = pp_n;
-    }
-    da1 = da0 + cnt;
-    fa1 = fa0;
-    if (chunked) {
-#pragma unroll
-        for (int m = 0; m < M; ++m)
-            if (m < Ma) heap_a[m * T] = fa[m];
-    }
-    if (da1 == n && fa0 < Ma) {
-        // a is complete: its remaining keys, in order, are b's last inputs
-        if (!chunked) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                if (m < Ma) {
-                    const uint32_t k = fa[m];
-                    const uint32_t pb = dispatch_pp<M>(fb, k, lds_u16(prow_b, k & idmask), lowmask, mulSH);
-                    if (EMIT_B && db >= Mb) buf[(w++) * T] = pb;
-                    ++db;
-                }
+    uint32_t wr = buf;
+    if (cnt > 0) {
+        int skip_a = Ma - da0;
+        skip_a = skip_a < 0 ? 0 : (skip_a > cnt ? cnt : skip_a);
+        // buffer keys two steps ahead, their times at a one step ahead (see
+        // stage_round)
+        uint32_t in_a = lds32(buf), in_n = lds32(buf + stride);
+        uint32_t pp_a = lds16(prow_a + (in_a & idmask));
+        uint32_t rd = buf + 2u * stride;
+        for (; i < skip_a; ++i) {
+            const uint32_t in_nn = lds32(rd);
+            const uint32_t pp_n = lds16(prow_a + (in_n & idmask));
+            (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
+            in_a = in_n;
+            in_n = in_nn;
+            pp_a = pp_n;
+            rd += stride;
+        }
+        uint32_t e = fa[0];
+        uint32_t pp_e = lds16(prow_b + (e & idmask));
+        int end2 = i + (Mb - db > 0 ? Mb - db : 0);
+        end2 = end2 > cnt ? cnt : end2;
+        // Shared loads and stores keep their source order (volatile asm), so
+        // each step issues its loads first: the next buffer key and its time
+        // at a, then -- right after a's dispatch -- b's next key's time, and
+        // the store of b's pop last.
+        for (; i < end2; ++i) {
+            const uint32_t in_nn = lds32(rd);
+            const uint32_t pp_n = lds16(prow_a + (in_n & idmask));
+            (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
+            const uint32_t e_n = fa[0];
+            const uint32_t pp_e_n = lds16(prow_b + (e_n & idmask));
+            (void)dispatch_pp<M>(fb, e, pp_e, lowmask, mulSH);
+            ++db;
+            e = e_n;
+            pp_e = pp_e_n;
+            in_a = in_n;
+            in_n = in_nn;
+            pp_a = pp_n;
+            rd += stride;
+        }
+#pragma unroll 1
+        for (; i < cnt; ++i) {
+            const uint32_t in_nn = lds32(rd);
+            const uint32_t pp_n = lds16(prow_a + (in_n & idmask));
+            (void)dispatch_pp<M>(fa, in_a, pp_a, lowmask, mulSH);
+            const uint32_t e_n = fa[0];
+            const uint32_t pp_e_n = lds16(prow_b + (e_n & idmask));
+            const uint32_t pb = dispatch_pp<M>(fb, e, pp_e, lowmask, mulSH);
+            ++db;
+            if constexpr (EMIT_B) {
+                sts32(wr, pb);
+                wr += stride;
+                ++w;
             }
-            fa1 = Ma;
-        } else {
-            int take = Ma - fa0;
-            if (EMIT_B && take > L.B - w) take = L.B - w;
-            for (int t = 0; t < take; ++t) {
-                const uint32_t k = heap_a[(fa0 + t) * T];
-                const uint32_t pb = dispatch_pp<M>(fb, k, lds_u16(prow_b, k & idmask), lowmask, mulSH);
-                if (EMIT_B && db >= Mb) buf[(w++) * T] = pb;
-                ++db;
-            }
-            fa1 = fa0 + take;
+            e = e_n;
+            pp_e = pp_e_n;
+            in_a = in_n;
+            in_n = in_nn;
+            pp_a = pp_n;
+            rd += stride;
         }
     }
-    db1 = db;
-    fb1 = fb0;
-    if (chunked) {
-#pragma unroll
-        for (int m = 0; m < M; ++m)
-            if (m < Mb) heap_b[m * T] = fb[m];
+    const int da1 = da0 + cnt;
+    int fa1 = fa0;
+    if (da1 == n && fa0 < Ma) {
+        // a is complete: its heap keys, in order, are b's last inputs (as many
+        // as b's output fits in the buffer this round)
+        int take = Ma - fa0;
+        if (EMIT_B && take > B - w) take = B - w;
+        for (int t = 0; t < take; ++t) {
+            const uint32_t k = pick_key<M>(fa, fa0 + t);
+            const uint32_t pb = dispatch_pp<M>(fb, k, lds16(prow_b + (k & idmask)), lowmask, mulSH);
+            if (EMIT_B && db >= Mb) {
+                sts32(buf + (uint32_t)w * stride, pb);
+                ++w;
+            }
+            ++db;
+        }
+        fa1 = fa0 + take;
     }
+    if (chunked && fa1 < Ma) heap_store<M>(heap_a, fa, Ma, stride);
+    const int db1 = db;
+    int fb1 = fb0;
+    uint4 out;
+    out.z = 0u;
+    out.w = 0u;
     if constexpr (EMIT_B) {
         if (db1 == n && fb0 < Mb) {
-            if (!chunked) {
-#pragma unroll
-                for (int m = 0; m < M; ++m)
-                    if (m < Mb) buf[(w++) * T] = fb[m];
-                fb1 = Mb;
-            } else {
-                int take = Mb - fb0;
-                if (take > L.B - w) take = L.B - w;
-                for (int t = 0; t < take; ++t) buf[(w + t) * T] = heap_b[(fb0 + t) * T];
-                w += take;
-                fb1 = fb0 + take;
-            }
+            int take = Mb - fb0;
+            if (take > B - w) take = B - w;
+            for (int t = 0; t < take; ++t) sts32(buf + (uint32_t)(w + t) * stride, pick_key<M>(fb, fb0 + t));
+            w += take;
+            fb1 = fb0 + take;
         }
+        if (chunked && fb1 < Mb) heap_store<M>(heap_b, fb, Mb, stride);
     } else {
+        if (chunked) heap_store<M>(heap_b, fb, Mb, stride);
         uint32_t lk = fb[0];
 #pragma unroll
         for (int m = 1; m < M; ++m)
             if (m == Mb - 1) lk = fb[m];
-        last_key_out = lk;
+        out.z = lk;
     }
-    return PairOut{w, da1, fa1, db1, fb1, last_key_out};
+    out.x = (uint32_t)w | (uint32_t)fa1 << 16 | (uint32_t)fb1 << 24;
+    out.y = (uint32_t)da1 | (uint32_t)db1 << 16;
+    return out;
 }
 
 template <bool EMIT_B>
-__device__ __forceinline__ int pair_round_dispatch(int Mp, const DecodeLayout &L, uint32_t *heap_a, uint32_t *heap_b,
-                                                   uint32_t *buf, const uint16_t *prow_a, const uint16_t *prow_b,
-                                                   int T, int Ma, int Mb, int da0, int fa0, int db0, int fb0, int cnt,
-                                                   uint32_t lowmask, uint32_t *last_key, int &da1, int &fa1, int &db1,
-                                                   int &fb1)
+__device__ __forceinline__ uint4 pair_round_dispatch(int Mp, uint32_t nB, uint32_t SH, uint32_t heap_a,
+                                                     uint32_t heap_b, uint32_t buf, uint32_t prow_a, uint32_t prow_b,
+                                                     uint32_t mm, uint32_t dd, int cnt)
 {
-    const RoundIn R{L.n, L.B, L.single, L.mulSH, lowmask};
-    PairOut o{0, da0, fa0, db0, fb0, 0u};
-#define FFS_PCASE(MM)                                                                                        \
-    case MM:                                                                                                 \
-        o = pair_round<MM, EMIT_B>(R, heap_a, heap_b, buf, prow_a, prow_b, T, Ma, Mb, da0, fa0, db0, fb0, cnt); \
-        break;
+#define FFS_PCASE(MM) \
+    case MM: return pair_round<MM, EMIT_B>(nB, SH, heap_a, heap_b, buf, prow_a, prow_b, mm, dd, cnt);
     switch (Mp) {
         FFS_PCASE(1) FFS_PCASE(2) FFS_PCASE(3) FFS_PCASE(4) FFS_PCASE(5) FFS_PCASE(6) FFS_PCASE(7)
         FFS_PCASE(8) FFS_PCASE(9) FFS_PCASE(10) FFS_PCASE(11) FFS_PCASE(12) FFS_PCASE(13) FFS_PCASE(14)
-        FFS_PCASE(15) FFS_PCASE(16) FFS_PCASE(kMaxM)
-        default:
-            o = pair_round<kMaxM, EMIT_B>(R, heap_a, heap_b, buf, prow_a, prow_b, T, Ma, Mb, da0, fa0, db0, fb0, cnt);
-            break;
+        FFS_PCASE(15) FFS_PCASE(16)
+        default: return pair_round<kMaxM, EMIT_B>(nB, SH, heap_a, heap_b, buf, prow_a, prow_b, mm, dd, cnt);
     }
 #undef FFS_PCASE
-    da1 = o.da1;
-    fa1 = o.fa1;
-    db1 = o.db1;
-    fb1 = o.fb1;
-    if (!EMIT_B) *last_key = o.last_key;
-    return o.w;
 }
 
 // Stage-0 input keys of the genes [0, cnt) of a chunk, written to buf.
-__device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uint32_t n, uint32_t *buf, int T,
-                                              bool &bad)
+__device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uint32_t n, uint32_t buf,
+                                              uint32_t stride, bool &bad)
 {
     const int4 *g4 = reinterpret_cast<const int4 *>(genes);
     for (int i0 = 0; i0 < cnt; i0 += 8) {
@@ -458,28 +579,34 @@ __device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uin
                 uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
                 g = (uint32_t)(int32_t)(int16_t)g;
                 if (g >= n) { bad = true; g = 0; }
-                buf[(i0 + h) * T] = (g + 1u) << 1;
+                sts32(buf + (uint32_t)(i0 + h) * stride, (g + 1u) << 1);
             }
         }
     }
 }
 
 // Decode one chromosome (row of genes in global memory, 16-byte aligned).
+//   L     : the block's layout in shared memory (see decode_tmem_begin).
 //   region: this thread's interleaved shared words (base + tid), stride T.
 //   ptab  : shared uint16 table, row s at ptab + s * table_row_halves(n).
 //   wst   : this warp's per-stage state, S entries (shared).
-// All lanes of a warp must call this together for the same instance.
+// All lanes of a warp must call this together for the same instance (the
+// TMEM accesses are warp-collective).
 // Returns the makespan, or -1 if a gene is outside [0, n).
 __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, const int16_t *row,
                                                      uint32_t *region, int T, const uint16_t *ptab,
                                                      WarpStageState *wst)
 {
     const int n = L.n, S = L.S;
-    const uint32_t lowmask = (1u << L.SH) - 1u;
-    uint32_t *buf = region + L.heap_words * T;
-    // Every buffer slot holds a valid key (or 0) before the one-ahead reads
-    // can touch it: clear the buffer and its spare slot.
-    for (int w = 0; w <= L.B; ++w) buf[w * T] = 0u;
+    const uint32_t stride = (uint32_t)T * 4u;
+    const uint32_t region_sa = tc::smem_u32(region);
+    const uint32_t buf = region_sa + (uint32_t)L.heap_words * stride;
+    const uint32_t tab = tc::smem_u32(ptab);
+    const uint32_t row_bytes = (uint32_t)table_row_halves(n) * 2u;
+    const uint32_t nB = (uint32_t)n | (uint32_t)L.B << 16, SH = (uint32_t)L.SH;
+    // Every buffer slot holds a valid key (or 0) before the read-ahead can
+    // touch it: clear the buffer and its two spare slots.
+    for (int w = 0; w <= L.B + 1; ++w) sts32(buf + (uint32_t)w * stride, 0u);
     bool bad = false;
     uint32_t last_key = 0;
     const int lane = threadIdx.x & 31;
@@ -500,16 +627,15 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
                     const int M = L.M[s];
                     const int d0 = wst[s].dispatched;
                     const int cnt = (s == 0) ? min(L.B, n - d0) : avail;
-                    int fl = 0;
                     if (cnt > 0) {
-                        if (s == 0)
-                            (void)stage_round_dispatch<true, false>(M, L, region + L.heap_off[s] * T, buf,
-                                                                    ptab + s * table_row_halves(n), row + d0, T, d0,
-                                                                    cnt, lowmask, bad, &last_key, fl);
-                        else
-                            (void)stage_round_dispatch<false, false>(M, L, region + L.heap_off[s] * T, buf,
-                                                                     ptab + s * table_row_halves(n), nullptr, T, d0,
-                                                                     cnt, lowmask, bad, &last_key, fl);
+                        const uint32_t h = heap_handle(L, region_sa, T, s);
+                        const uint32_t prow = tab + (uint32_t)s * row_bytes;
+                        const uint32_t dc = (uint32_t)d0 | (uint32_t)cnt << 16, mf = (uint32_t)M;
+                        const uint2 o = (s == 0)
+                                            ? stage_round_dispatch<true, false>(M, nB, SH, h, buf, prow, row + d0, dc, mf)
+                                            : stage_round_dispatch<false, false>(M, nB, SH, h, buf, prow, nullptr, dc, mf);
+                        last_key = o.y;
+                        if (o.x >> 24) bad = true;
                     }
                     __syncwarp();
                     if (lane == 0) wst[s].dispatched = d0 + cnt;
@@ -525,16 +651,20 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
                 int w = 0, da1 = da0, fa1 = fa0, db1 = db0, fb1 = fb0;
                 const bool work = cnt > 0 || (da0 == n && fa0 < Ma) || (emit_b && db0 == n && fb0 < Mb);
                 if (work) {
-                    if (a == 0 && cnt > 0) genes_to_keys(row + da0, cnt, (uint32_t)n, buf, T, bad);
+                    if (a == 0 && cnt > 0) genes_to_keys(row + da0, cnt, (uint32_t)n, buf, stride, bad);
                     const int Mp = Ma > Mb ? Ma : Mb;
-                    const uint16_t *pa = ptab + a * table_row_halves(n), *pb = ptab + b * table_row_halves(n);
-                    uint32_t *ha = region + L.heap_off[a] * T, *hb = region + L.heap_off[b] * T;
-                    if (emit_b)
-                        w = pair_round_dispatch<true>(Mp, L, ha, hb, buf, pa, pb, T, Ma, Mb, da0, fa0, db0, fb0, cnt,
-                                                      lowmask, &last_key, da1, fa1, db1, fb1);
-                    else
-                        w = pair_round_dispatch<false>(Mp, L, ha, hb, buf, pa, pb, T, Ma, Mb, da0, fa0, db0, fb0, cnt,
-                                                       lowmask, &last_key, da1, fa1, db1, fb1);
+                    const uint32_t pa = tab + (uint32_t)a * row_bytes, pb = pa + row_bytes;
+                    const uint32_t ha = heap_handle(L, region_sa, T, a), hb = heap_handle(L, region_sa, T, b);
+                    const uint32_t mm = (uint32_t)Ma | (uint32_t)Mb << 8 | (uint32_t)fa0 << 16 | (uint32_t)fb0 << 24;
+                    const uint32_t dd = (uint32_t)da0 | (uint32_t)db0 << 16;
+                    const uint4 o = emit_b ? pair_round_dispatch<true>(Mp, nB, SH, ha, hb, buf, pa, pb, mm, dd, cnt)
+                                           : pair_round_dispatch<false>(Mp, nB, SH, ha, hb, buf, pa, pb, mm, dd, cnt);
+                    w = (int)(o.x & 0xFFFFu);
+                    fa1 = (int)((o.x >> 16) & 0xFFu);
+                    fb1 = (int)(o.x >> 24);
+                    da1 = (int)(o.y & 0xFFFFu);
+                    db1 = (int)(o.y >> 16);
+                    if (!emit_b) last_key = o.z;
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -553,7 +683,7 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
         }
         __syncwarp();
         if (bad) return -1;
-        if (!L.single) last_key = region[(L.heap_off[S - 1] + L.M[S - 1] - 1) * T];
+        if (!L.single) last_key = heap_read1(heap_handle(L, region_sa, T, S - 1), L.M[S - 1] - 1, stride);
         return (int32_t)(last_key >> L.SH);
     }
     int s_lo = 0;   // stages before s_lo have dispatched and emitted everything
@@ -561,44 +691,33 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
         int avail = 0;  // keys in buf for the next stage
         for (int s = s_lo; s < S; ++s) {
             const int M = L.M[s];
-            const int d0 = wst[s].dispatched;
+            const int d0 = wst[s].dispatched, fl0 = wst[s].flushed;
             const int cnt = (s == 0) ? min(L.B, n - d0) : avail;
-            const uint16_t *prow = ptab + s * table_row_halves(n);
-            uint32_t *heap = region + L.heap_off[s] * T;
             const bool last = (s == S - 1);
-            int w = 0, fl = 0;
-            if (cnt > 0) {
-                if (s == 0) {
-                    if (last)
-                        w = stage_round_dispatch<true, false>(M, L, heap, buf, prow, row + d0, T, d0, cnt,
-                                                              lowmask, bad, &last_key, fl);
-                    else
-                        w = stage_round_dispatch<true, true>(M, L, heap, buf, prow, row + d0, T, d0, cnt,
-                                                             lowmask, bad, &last_key, fl);
-                } else {
-                    if (last)
-                        w = stage_round_dispatch<false, false>(M, L, heap, buf, prow, nullptr, T, d0, cnt,
-                                                               lowmask, bad, &last_key, fl);
-                    else
-                        w = stage_round_dispatch<false, true>(M, L, heap, buf, prow, nullptr, T, d0, cnt,
-                                                              lowmask, bad, &last_key, fl);
-                }
+            int w = 0, fl = fl0;
+            if (cnt > 0 || (!last && d0 == n && fl0 < M)) {
+                const uint32_t h = heap_handle(L, region_sa, T, s);
+                const uint32_t prow = tab + (uint32_t)s * row_bytes;
+                const uint32_t dc = (uint32_t)d0 | (uint32_t)cnt << 16, mf = (uint32_t)M | (uint32_t)fl0 << 8;
+                const int16_t *g = row + d0;
+                uint2 o;
+                if (last)
+                    o = (s == 0) ? stage_round_dispatch<true, false>(M, nB, SH, h, buf, prow, g, dc, mf)
+                                 : stage_round_dispatch<false, false>(M, nB, SH, h, buf, prow, nullptr, dc, mf);
+                else
+                    o = (s == 0 && cnt > 0) ? stage_round_dispatch<true, true>(M, nB, SH, h, buf, prow, g, dc, mf)
+                                            : stage_round_dispatch<false, true>(M, nB, SH, h, buf, prow, nullptr, dc, mf);
+                w = (int)(o.x & 0xFFFFu);
+                fl = (int)((o.x >> 16) & 0xFFu);
+                if (o.x >> 24) bad = true;
+                if (last) last_key = o.y;
             }
             const int d1 = d0 + cnt;
-            int flushed = wst[s].flushed + fl;
-            if (!last && d1 == n && flushed < M) {
-                // finish (part of) the flush from the saved heap
-                const int room = L.B - w;
-                const int take = min(room, M - flushed);
-                for (int t = 0; t < take; ++t) buf[(w + t) * T] = heap[(flushed + t) * T];
-                w += take;
-                flushed += take;
-            }
             __syncwarp();
-            if (lane == 0) { wst[s].dispatched = d1; wst[s].flushed = flushed; }
+            if (lane == 0) { wst[s].dispatched = d1; wst[s].flushed = fl; }
             __syncwarp();
             avail = w;
-            const bool done = d1 == n && (last || flushed == M);
+            const bool done = d1 == n && (last || fl == M);
             if (done && s == s_lo) ++s_lo;
             // nothing reaches later stages this round unless this one is finished
             if (avail == 0 && !done) break;
@@ -607,7 +726,7 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     }
     __syncwarp();
     if (bad) return -1;
-    if (!L.single) last_key = region[(L.heap_off[S - 1] + L.M[S - 1] - 1) * T];
+    if (!L.single) last_key = heap_read1(heap_handle(L, region_sa, T, S - 1), L.M[S - 1] - 1, stride);
     return (int32_t)(last_key >> L.SH);
 }
 

@@ -22,16 +22,21 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
                                                   unsigned long long *decoded)
 {
     extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const int bits_per_warp = (L.n + 31) >> 5;
     const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    if (threadIdx.x == 0) {
+        s_L = L;
+        s_L.M = st;
+        s_L.heap_off = st + L.S;
+    }
     __syncthreads();
-    DecodeLayout Ls = L;
-    Ls.M = st;
-    Ls.heap_off = st + L.S;
+    DecodeLayout &Ls = s_L;
+    decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
     uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
@@ -49,6 +54,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
         const int c = (valid ? gc : total - 1) - bi * cells;
         cellular_warp_cells(Ls, g, batch.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
     }
+    decode_tmem_end(Ls);
 }
 
 const void *cellular_kernel() { return (const void *)k_cellular; }
@@ -256,16 +262,21 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
                                                      PseudoScratch ps, unsigned long long *decoded)
 {
     extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const int bits_per_warp = (L.n + 31) >> 5;
     const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    if (threadIdx.x == 0) {
+        s_L = L;
+        s_L.M = st;
+        s_L.heap_off = st + L.S;
+    }
     __syncthreads();
-    DecodeLayout Ls = L;
-    Ls.M = st;
-    Ls.heap_off = st + L.S;
+    DecodeLayout &Ls = s_L;
+    decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
     uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
@@ -296,7 +307,10 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
             if (valid) ps.child_ms[k] = ms;
         }
     }
+    decode_tmem_end(Ls);
 }
+
+const void *step_decode_kernel() { return (const void *)k_step_decode; }
 
 // A whole generation of the cellular batch `cb` and the pseudo batch `pb`
 // (same torus for cb, same size for pb): pseudo breed, the fused decode
@@ -1022,7 +1036,7 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
     int rc = FFS_OK;
     const int Ts[4] = {64, 128, 256, 512};
     const int Bs[6] = {8, 16, 32, 64, 128, 0};
-    for (int vi = 1; vi <= 2 && !rc; ++vi)
+    for (int vi = 1; vi <= kMaxVariant && !rc; ++vi)
     for (int ti = 0; ti < 4 && !rc; ++ti) {
         for (int bi = 0; bi < 6 && !rc; ++bi) {
             const int B = Bs[bi] == 0 ? round_up(S->inst->n, 8) : Bs[bi];

@@ -88,10 +88,15 @@ namespace fgpu {
 // Choose (B, T) for a decoding kernel, honouring requests (0 = choose).
 // bits_per_warp: shared words per warp the kernel needs besides decoding
 // (the crossover bitmask).  kernel: for the occupancy query.
-// variant: 0 = library choice, 1 = one stage at a time, 2 = stages in interleaved pairs.
+// variant: 0 = library choice (stage pairs, saved heaps in TMEM where that
+// raises the resident threads), 1 = one stage at a time, 2 = stages in
+// interleaved pairs, 3 / 4 = as 1 / 2 with saved heaps in TMEM wherever the
+// shape allows it (chunked decoding, block size a multiple of 128).
+constexpr int kMaxVariant = 4;
 int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp,
                 Plan *out, int variant = 0);
-inline int pairs_of(int variant) { return variant == 1 ? 0 : 1; }
+inline int pairs_of(int variant) { return (variant == 1 || variant == 3) ? 0 : 1; }
+inline int tmem_of(int variant) { return variant == 0 ? 1 : variant >= 3 ? 2 : 0; }
 
 // Grid size for N items (persistent, grid-stride).
 inline int grid_for(const ffs_instance *inst, const Plan &p, int64_t N)
@@ -178,6 +183,7 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
 int64_t pseudo_scratch_bytes(int size, int ld, int islands = 1);
 const void *cellular_kernel();
 const void *eval_kernel();
+const void *step_decode_kernel();
 
 int validate_rows(const void *p, int ld, int n);
 

@@ -6,14 +6,26 @@
 
 namespace fgpu {
 
-// Eight independent chains per thread of one 32-bit integer operation;
-// `kind` 0: min/max, 1: three-input logic, 2: three-input add, 3: multiply-add.
+// Eight independent chains per thread of one 32-bit operation;
+// `kind` 0: min/max, 1: three-input logic, 2: three-input add, 3: multiply-add,
+// 4: fp32 min/max on the same bit patterns (non-negative finite keys order as
+// floats the way they order as integers), 5: packed 16-bit min/max (two
+// halves per word), 6: three-input min/max, 7: add-then-max, 8: min/max and
+// multiply-add alternating between chains, 9: integer and fp32 min/max
+// alternating.  Kinds 8 and 9 show whether two operation kinds issue to
+// separate pipes (their mixed rate then exceeds either one alone).
 template <int KIND>
 __global__ void __launch_bounds__(512) k_int_rate(int iters, uint32_t seed, uint32_t *sink)
 {
     uint32_t a[8], b = seed ^ (threadIdx.x * 0x9E3779B9u), c = seed + blockIdx.x;
+    if constexpr (KIND == 4 || KIND == 9) {
+        // finite non-negative float patterns
+        b &= 0x3FFFFFFFu;
+        c &= 0x3FFFFFFFu;
+    }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = b + j * 0x85EBCA6Bu;
+    for (int j = 0; j < 8; ++j) a[j] = (KIND == 4 || KIND == 9) ? ((b + j * 0x85EBCA6Bu) & 0x3FFFFFFFu)
+                                                              : b + j * 0x85EBCA6Bu;
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -22,11 +34,28 @@ __global__ void __launch_bounds__(512) k_int_rate(int iters, uint32_t seed, uint
                 if constexpr (KIND == 0) a[j] = (u & 1) ? min(a[j], b) : max(a[j], c);
                 else if constexpr (KIND == 1) a[j] = (a[j] ^ b) & (c | a[j]);
                 else if constexpr (KIND == 2) a[j] = a[j] + a[(j + 1) & 7] + c;
-                else a[j] = a[j] * b + c;
+                else if constexpr (KIND == 3) a[j] = a[j] * b + c;
+                else if constexpr (KIND == 4)
+                    a[j] = __float_as_uint((u & 1) ? fminf(__uint_as_float(a[j]), __uint_as_float(b))
+                                                   : fmaxf(__uint_as_float(a[j]), __uint_as_float(c)));
+                else if constexpr (KIND == 5) a[j] = (u & 1) ? __vminu2(a[j], b) : __vmaxu2(a[j], c);
+                else if constexpr (KIND == 6)
+                    a[j] = (u & 1) ? __vimin3_u32(a[j], b, a[(j + 1) & 7]) : __vimax3_u32(a[j], c, a[(j + 3) & 7]);
+                else if constexpr (KIND == 7) a[j] = __viaddmax_u32(a[j], b, c);
+                else if constexpr (KIND == 8)
+                    a[j] = (j & 1) ? a[j] * b + c : ((u & 1) ? min(a[j], b) : max(a[j], c));
+                else
+                    a[j] = (j & 1) ? __float_as_uint((u & 1) ? fminf(__uint_as_float(a[j]), __uint_as_float(b))
+                                                             : fmaxf(__uint_as_float(a[j]), __uint_as_float(c)))
+                                   : ((u & 1) ? min(a[j], b) : max(a[j], c));
             }
         }
         b += 1u;
         c ^= b;
+        if constexpr (KIND == 4 || KIND == 9) {
+            b &= 0x3FFFFFFFu;
+            c &= 0x3FFFFFFFu;
+        }
     }
     uint32_t r = 0;
 #pragma unroll
@@ -56,7 +85,7 @@ extern "C" {
 int ffs_measure_int_rate(int32_t kind, double *lane_ops_per_s, float *ms, ffs_stream stream)
 {
     clear_error();
-    if (kind < 0 || kind > 3 || !lane_ops_per_s) return set_error(FFS_EINVAL, "kind %d", kind);
+    if (kind < 0 || kind > 9 || !lane_ops_per_s) return set_error(FFS_EINVAL, "kind %d", kind);
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     FFS_CUDA_TRY(cudaGetDevice(&dev));
@@ -74,7 +103,13 @@ int ffs_measure_int_rate(int32_t kind, double *lane_ops_per_s, float *ms, ffs_st
         case 0: k_int_rate<0><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
         case 1: k_int_rate<1><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
         case 2: k_int_rate<2><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
-        default: k_int_rate<3><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        case 3: k_int_rate<3><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        case 4: k_int_rate<4><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        case 5: k_int_rate<5><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        case 6: k_int_rate<6><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        case 7: k_int_rate<7><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        case 8: k_int_rate<8><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
+        default: k_int_rate<9><<<blocks, T, 0, st>>>(iters, 7u, sink); break;
         }
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -87,7 +122,8 @@ int ffs_measure_int_rate(int32_t kind, double *lane_ops_per_s, float *ms, ffs_st
     cudaEventDestroy(e1);
     cudaFreeAsync(sink, st);
     if (err != cudaSuccess) return set_error(FFS_ECUDA, "int rate kernel: %s", cudaGetErrorString(err));
-    // source-level operations: kind 0..1 one per update, kind 2 two adds, kind 3 one multiply-add
+    // one source-level operation per chain update (kind 2's two adds and kind
+    // 7's add-then-max are counted once: one instruction where the hardware has it)
     const double per_update = 1.0;
     const double ops = (double)blocks * T * iters * 16.0 * 8.0 * per_update;
     *lane_ops_per_s = ops / (best * 1e-3);

@@ -106,15 +106,20 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
                                                     unsigned long long *decoded)
 {
     extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const SmemMap map = smem_map(L.n, L.S, T);
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
+    if (threadIdx.x == 0) {
+        s_L = L;
+        s_L.M = st;
+        s_L.heap_off = st + L.S;
+    }
     __syncthreads();
-    DecodeLayout Ls = L;
-    Ls.M = st;
-    Ls.heap_off = st + L.S;
+    DecodeLayout &Ls = s_L;
+    decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
     uint32_t *region = smem + map.region + threadIdx.x;
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
         warp_copy_rows(keep, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
         warp_copy_rows(valid, drow, ring_rows + ((ring_base + gq) % ring_cap) * ld, ld);
     }
+    decode_tmem_end(Ls);
 }
 
 // Training batch: B rows drawn uniformly (Philox, purpose kPurposeTrainSample)

@@ -49,8 +49,11 @@ def test_eval_matches_oracle(gpu, shape):
         shapes.append((0, threads))
     if n > 8:
         shapes.append((8, 64))
+    for chunk, threads in ((8, 128), (16, 256), (32, 512), (8, 512)):
+        if chunk < n:
+            shapes.append((chunk, threads))
     ran = 0
-    shapes = [(c, t, v) for (c, t) in shapes for v in (1, 2)]
+    shapes = [(c, t, v) for (c, t) in shapes for v in (1, 2, 3, 4)]
     for chunk, threads, variant in shapes:
         out.fill_(-7)
         try:
@@ -124,3 +127,29 @@ def test_eval_host_buffers(gpu):
     out = np.zeros(500, dtype=np.int32)
     gpu.ffs_population_eval_host(g, pop, 500, pop.shape[1], out)
     assert np.array_equal(out.astype(np.int64), orc.eval_population(o, pop))
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_saved_heaps_in_tensor_memory(gpu, variant):
+    """The 500 x 20 instance at chunk 32: the TMEM variants keep a prefix of the
+    saved heaps in tensor memory (more resident threads), and decode exactly;
+    so does every block size that allows it."""
+    spec = make_instance(500, 20, 5, 10, seed=1)
+    o, g = _pair(spec, gpu)
+    plain = gpu.ffs_decode_plan(g, 0, 32, 0, variant - 2)
+    plan = gpu.ffs_decode_plan(g, 0, 32, 0, variant)
+    assert plain["tmem_cols"] == 0 and plan["tmem_cols"] in (128, 256, 512)
+    assert plan["threads"] * plan["blocks_per_sm"] > plain["threads"] * plain["blocks_per_sm"]
+    N = 700
+    pop = random_population(500, N, seed=21)
+    want = orc.eval_population(o, pop)
+    d = dev(pop)
+    out = torch.full((N,), -7, dtype=torch.int32, device="cuda")
+    for threads in (128, 256, 512):
+        p = gpu.ffs_decode_plan(g, 0, 32, threads, variant)
+        assert p["tmem_cols"] > 0, p
+        out.fill_(-7)
+        gpu.ffs_population_eval_tuned(g, d, N, pop.shape[1], out, 32, threads, variant)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.int64)
+        assert np.array_equal(got, want), (threads, np.flatnonzero(got != want)[:5])

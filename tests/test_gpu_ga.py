@@ -18,9 +18,10 @@ def _pair(spec, ffs):
 
 
 def _params(ffs, seed=7, cell_pc=1.0, cell_pm=0.05, pseudo_pc=0.75, le=False, always=False,
-            mode=1, gap=50, ring=(2, 100), theta=(1, 1), decode_variant=0):
+            mode=1, gap=50, ring=(2, 100), theta=(1, 1), decode_variant=0, chunk=0, threads=0):
     p = ffs.ffs_params_default()
     p.decode_variant = decode_variant
+    p.decode_chunk, p.block_threads = chunk, threads
     p.seed = seed
     p.cell_pc, p.cell_pm, p.pseudo_pc = ffs.threshold(cell_pc), ffs.threshold(cell_pm), ffs.threshold(pseudo_pc)
     p.cell_replace_le, p.pseudo_always = int(le), int(always)
@@ -64,7 +65,8 @@ def test_population_init_matches_oracle(gpu):
 
 @pytest.mark.parametrize("variant", [dict(), dict(cell_pc=0.6, cell_pm=1.0), dict(le=True, cell_pm=0.3),
                                      dict(cell_pc=0.0, cell_pm=0.0), dict(decode_variant=1),
-                                     dict(decode_variant=2, cell_pm=0.5)])
+                                     dict(decode_variant=2, cell_pm=0.5), dict(decode_variant=3),
+                                     dict(decode_variant=4)])
 def test_cellular_generations_match_oracle(gpu, variant):
     spec = make_instance(20, 5, 3, 3, seed=1)
     o, g = _pair(spec, gpu)
@@ -85,7 +87,7 @@ def test_cellular_generations_match_oracle(gpu, variant):
         a, b, ma, mb = b, a, mb, ma
 
 
-@pytest.mark.parametrize("always,dvar", [(False, 0), (True, 0), (False, 1)])
+@pytest.mark.parametrize("always,dvar", [(False, 0), (True, 0), (False, 1), (False, 3)])
 @pytest.mark.parametrize("shape", [(20, 5, 3, 3, 64), (100, 10, 2, 5, 512), (33, 4, 1, 6, 130), (45, 7, 1, 20, 96)])
 def test_pseudo_generations_match_oracle(gpu, always, dvar, shape):
     n, S, mlo, mhi, size = shape
@@ -170,6 +172,19 @@ def test_islands_ring_uneven_three(gpu):
     spec = make_instance(12, 3, 1, 4, seed=8)
     prm, oprm = _params(gpu, seed=3, mode=1, gap=3, ring=(10, 100))
     _islands_vs_oracle(gpu, spec, prm, oprm, 2, 5, 4, 1, 30, 12, 3, 1, check_every=3)
+
+
+@pytest.mark.parametrize("variant,threads,n_pseudo", [(4, 128, 1), (3, 256, 1), (4, 512, 0), (3, 128, 0)])
+def test_islands_tensor_memory_heaps(gpu, variant, threads, n_pseudo):
+    """Chunked decoding (8 jobs per round) with the saved heaps in tensor
+    memory, in the fused decode launch (cellular + pseudo) and the cellular
+    kernel alone."""
+    spec = make_instance(60, 9, 1, 6, seed=12)
+    prm, oprm = _params(gpu, seed=4, mode=1, gap=5, decode_variant=variant, chunk=8, threads=threads)
+    o, g = _pair(spec, gpu)
+    assert gpu.ffs_decode_plan(g, 2 if n_pseudo else 1, 8, threads, variant)["tmem_cols"] > 0
+    _islands_vs_oracle(gpu, spec, prm, oprm, 2, 12, 12, n_pseudo, 64 if n_pseudo else 0, 12, 5, 1,
+                       check_every=3)
 
 
 def test_explicit_migrate_and_set_get(gpu):
