@@ -87,9 +87,9 @@ int ffs_population_eval(const ffs_instance *inst, const int16_t *pop, int64_t N,
  * heaps saved between rounds in tensor memory where that fits more threads
  * per SM; 1 one stage at a time, 2 stages in interleaved pairs, both with
  * the saved heaps in shared memory; 3 / 4 as 1 / 2 with the saved heaps in
- * tensor memory whenever the shape allows it, i.e. chunked decoding and a
- * block size that is a multiple of 128; FFS_EINVAL outside 0..4); 0 lets the
- * library choose.  Results do not depend on the shape or variant. */
+ * tensor memory whenever the shape allows it (chunked decoding);
+ * FFS_EINVAL outside 0..4); 0 lets the library choose.  Results do not
+ * depend on the shape or variant. */
 int ffs_population_eval_tuned(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
                               int32_t *makespan, int32_t decode_chunk, int32_t block_threads,
                               int32_t variant, ffs_stream stream);

@@ -391,11 +391,11 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
     FFS_CUDA_TRY(cudaEventCreate(&e1));
     float best = -1.0f;
     int bestT = b->T, bestB = b->B, bestV = b->prm.decode_variant;
-    const int Ts[4] = {64, 128, 256, 512};
+    const int Ts[7] = {64, 128, 256, 320, 384, 448, 512};
     const int Bs[5] = {8, 16, 32, 64, 128};
     int rc = FFS_OK;
     for (int vi = 1; vi <= 2 && !rc; ++vi)
-    for (int ti = 0; ti < 4 && !rc; ++ti) {
+    for (int ti = 0; ti < 7 && !rc; ++ti) {
         for (int bi = 0; bi < 5 && !rc; ++bi) {
             BatchShape s;
             size_t smem;

@@ -105,8 +105,10 @@ static int occupancy(const void *kernel, int T, size_t smem)
 }
 
 // Candidate shapes: chunk B x block size T, saved heaps in shared memory
-// only, or (chunked decoding, T a multiple of 128) a prefix of the stages'
-// heaps in TMEM with `tb` blocks per SM sharing its 512 columns.  Each TMEM
+// only, or (chunked decoding) a prefix of the stages' heaps in TMEM with `tb`
+// blocks per SM sharing its 512 columns; a block's warps w, w + 4, ... share
+// lane quarter w mod 4 and split the block's columns in ceil(warps / 4)
+// groups.  Each TMEM
 // shape pads its shared memory, if needed, so that no more than tb blocks
 // are resident (a further block would wait in its TMEM allocation).  Score:
 // resident threads (saturating at 1024), then fewer rounds, then TMEM or not
@@ -132,13 +134,13 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
         for (int b : {8, 16, 32, 64, 128})
             if (b < n) Bs[nb++] = b;
     }
-    int Ts[5];
+    int Ts[8];
     int nt = 0;
     if (T_req > 0) {
         if (T_req % 32 || T_req > 512) return set_error(FFS_EINVAL, "block_threads %d must be a multiple of 32, <= 512", T_req);
         Ts[nt++] = T_req;
     } else {
-        for (int t : {64, 128, 256, 512}) Ts[nt++] = t;
+        for (int t : {64, 128, 256, 320, 384, 448, 512}) Ts[nt++] = t;
     }
     auto consider = [&](const Cand &c, bool single) {
         const long resident = (long)c.blocks * c.T;
@@ -163,9 +165,9 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
                 c.smem = (size_t)(m.region + tw * T) * 4u;
                 if (c.smem <= smem_cap && (c.blocks = occupancy(kernel, T, c.smem)) > 0) consider(c, single);
             }
-            if (tmem_pref == 0 || single || T % 128 != 0) continue;
+            if (tmem_pref == 0 || single) continue;
             for (int tb : {1, 2, 4}) {
-                const int groups = T / 128;                 // warps per lane quarter
+                const int groups = (T / 32 + 3) / 4;        // warps per lane quarter (at most)
                 const int cols_block = 512 / tb;
                 const int gcols = cols_block / groups;
                 int split = 0, ns = 0;

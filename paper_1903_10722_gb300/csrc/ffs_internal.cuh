@@ -91,7 +91,7 @@ namespace fgpu {
 // variant: 0 = library choice (stage pairs, saved heaps in TMEM where that
 // raises the resident threads), 1 = one stage at a time, 2 = stages in
 // interleaved pairs, 3 / 4 = as 1 / 2 with saved heaps in TMEM wherever the
-// shape allows it (chunked decoding, block size a multiple of 128).
+// shape allows it (chunked decoding).
 constexpr int kMaxVariant = 4;
 int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp,
                 Plan *out, int variant = 0);

@@ -145,7 +145,7 @@ def test_saved_heaps_in_tensor_memory(gpu, variant):
     want = orc.eval_population(o, pop)
     d = dev(pop)
     out = torch.full((N,), -7, dtype=torch.int32, device="cuda")
-    for threads in (128, 256, 512):
+    for threads in (96, 128, 256, 320, 448, 512):
         p = gpu.ffs_decode_plan(g, 0, 32, threads, variant)
         assert p["tmem_cols"] > 0, p
         out.fill_(-7)
