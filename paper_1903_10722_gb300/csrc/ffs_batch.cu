@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             L.single = shape.B >= n ? 1 : 0;
             L.B = L.single ? round_up(n, 8) : shape.B;
             L.heap_words = L.single ? 0 : I.heap_words;
-            L.thread_words = L.heap_words + L.B + 2;
+            L.thread_words = L.heap_words + L.B + 4;
             L.pairs = shape.pairs;
             L.tmem_cols = 0;   // saved heaps in shared memory
             L.tmem_group_cols = 0;
@@ -160,7 +160,7 @@ static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *sm
         s.max_n = std::max(s.max_n, I.n);
         s.max_S = std::max(s.max_S, I.S);
         const bool single = B >= I.n;
-        const int tw = (single ? 0 : I.heap_words) + (single ? round_up(I.n, 8) : B) + 2;
+        const int tw = (single ? 0 : I.heap_words) + (single ? round_up(I.n, 8) : B) + 4;
         s.max_tw = std::max(s.max_tw, tw);
     }
     const SmemMap m = smem_map(s.max_n, s.max_S, T, (s.max_n + 31) / 32);

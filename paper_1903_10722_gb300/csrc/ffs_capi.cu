@@ -158,7 +158,7 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
             const int T = Ts[ti];
             const SmemMap m = smem_map(n, S, T, bits_per_warp);
             {
-                const int tw = (single ? 0 : inst->heap_words) + B + 2;   // +2: read-ahead slots
+                const int tw = (single ? 0 : inst->heap_words) + B + 4;   // +4: read-ahead slots
                 Cand c;
                 c.T = T;
                 c.B = B;
@@ -180,7 +180,7 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
                 c.group_cols = gcols;
                 c.tstages = ns;
                 c.split = split;
-                const int tw = inst->heap_words - split + B + 2;
+                const int tw = inst->heap_words - split + B + 4;
                 c.smem = (size_t)(m.region + tw * T) * 4u;
                 if (c.smem > smem_cap) continue;
                 c.blocks = occupancy(kernel, T, c.smem);
@@ -206,7 +206,7 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
     L.single = best.B >= n ? 1 : 0;
     L.B = L.single ? single_B : best.B;
     L.heap_words = L.single ? 0 : inst->heap_words - best.split;
-    L.thread_words = L.heap_words + L.B + 2;
+    L.thread_words = L.heap_words + L.B + 4;
     if (best.tmem_blocks) {
         L.tmem_cols = (uint32_t)(512 / best.tmem_blocks);
         L.tmem_group_cols = best.group_cols;

@@ -71,7 +71,7 @@ __device__ __forceinline__ bool fires(uint32_t x, uint64_t threshold) { return (
 // To bound shared memory for long chromosomes, the jobs flow through the
 // stages in rounds of at most B keys: a stage consumes what the previous
 // stage emitted this round; its heap is saved between rounds.  Per-thread
-// shared words: the saved heaps (skipped when B >= n) + B (buffer) + 2
+// shared words: the saved heaps (skipped when B >= n) + B (buffer) + 4
 // (read-ahead slots), thread-interleaved (word w of thread t at w * T + t).
 //
 // Saved heaps in tensor memory: the decoder does no MMA, so the SM's 256 KB
@@ -259,6 +259,47 @@ __device__ __forceinline__ uint32_t dispatch_pp(uint32_t (&f)[M], uint32_t in, u
     return f0;
 }
 
+// Two dispatches at once: jobs in1 then in2 (processing times p1, p2).
+// The first pops f[0] and completes at x1; the second pops the smaller of
+// f[1] and x1 (q) and completes at x2.  The heap left is f[2..M-1] with the
+// larger of f[1] and x1 (y) and x2 added: a merge of the sorted f[2..] with
+// the sorted pair lo <= hi of {y, x2}, whose k-th smallest is
+//   max( min(f[k+2], lo), min(f[k+1], hi), f[k] )
+// (terms with an index past the heap dropped) -- three operations per slot,
+// one of them a three-input max, against four for two single insertions.
+// Same pops and same heap as two dispatch_pp calls.
+template <int M>
+__device__ __forceinline__ void dispatch2_pp(uint32_t (&f)[M], uint32_t in1, uint32_t p1, uint32_t in2, uint32_t p2,
+                                             uint32_t lowmask, uint32_t mulSH, uint32_t &pop1, uint32_t &pop2)
+{
+    const uint32_t f0 = f[0];
+    const uint32_t x1 = p1 * mulSH + max((f0 & ~lowmask) | (in1 & lowmask), in1);
+    if constexpr (M == 1) {
+        pop1 = f0;
+        pop2 = x1;
+        f[0] = p2 * mulSH + max((x1 & ~lowmask) | (in2 & lowmask), in2);
+    } else {
+        const uint32_t q = min(f[1], x1), y = max(f[1], x1);
+        const uint32_t x2 = p2 * mulSH + max((q & ~lowmask) | (in2 & lowmask), in2);
+        const uint32_t lo = min(y, x2), hi = max(y, x2);
+        uint32_t g[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const uint32_t t0 = (k + 2 < M) ? min(f[k + 2], lo) : lo;
+            if (k == 0) {
+                g[0] = t0;
+            } else {
+                const uint32_t t1 = (k + 1 < M) ? min(f[k + 1], hi) : hi;
+                g[k] = (k == 1) ? max(t0, t1) : __vimax3_u32(t0, t1, f[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) f[k] = g[k];
+        pop1 = f0;
+        pop2 = q;
+    }
+}
+
 // Per-warp round bookkeeping lives in shared memory (identical in all lanes).
 struct WarpStageState {
     int32_t dispatched;
@@ -326,37 +367,49 @@ __device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
             }
         }
     } else if (cnt > 0) {
-        // Keys are read two steps ahead and their processing times one step
-        // ahead: the store of step i goes to slot i - skip <= i, never to a
-        // slot still to be read.  Slots cnt and cnt + 1 may be read (the
-        // region has two spare words per thread).
-        uint32_t in = lds32(buf), in_n = lds32(buf + stride);
-        uint32_t pp = lds16(prow + (in & idmask));
-        uint32_t rd = buf + 2u * stride;
+        // The first `skip` dispatches pop initial keys (nothing emitted): one
+        // at a time.  Then two jobs per dispatch2_pp, with the keys read four
+        // steps ahead and their processing times two steps ahead; the stores
+        // of steps i, i + 1 go to slots i - skip, i + 1 - skip <= i + 1, never
+        // to a slot still to be read.  Slots up to cnt + 3 may be read (the
+        // region has four spare words per thread).
         int i = 0;
         for (; i < skip; ++i) {
-            const uint32_t in_nn = lds32(rd);
-            const uint32_t pp_n = lds16(prow + (in_n & idmask));
-            (void)dispatch_pp<M>(f, in, pp, lowmask, mulSH);
-            in = in_n;
-            in_n = in_nn;
-            pp = pp_n;
-            rd += stride;
+            const uint32_t in = lds32(buf + (uint32_t)i * stride);
+            (void)dispatch_pp<M>(f, in, lds16(prow + (in & idmask)), lowmask, mulSH);
         }
-        uint32_t wr = buf;
-#pragma unroll 4
-        for (; i < cnt; ++i) {
-            const uint32_t in_nn = lds32(rd);
-            const uint32_t pp_n = lds16(prow + (in_n & idmask));
-            const uint32_t popped = dispatch_pp<M>(f, in, pp, lowmask, mulSH);
-            if constexpr (EMIT) {
-                sts32(wr, popped);
-                wr += stride;
+        if (i < cnt) {
+            uint32_t rd = buf + (uint32_t)i * stride;
+            uint32_t k0 = lds32(rd), k1 = lds32(rd + stride), k2 = lds32(rd + 2u * stride),
+                     k3 = lds32(rd + 3u * stride);
+            uint32_t t0 = lds16(prow + (k0 & idmask)), t1 = lds16(prow + (k1 & idmask));
+            rd += 4u * stride;
+            uint32_t wr = buf;
+            // unrolled twice, the read-ahead registers alternate roles instead of
+            // being moved at every iteration
+#pragma unroll 2
+            for (; i + 2 <= cnt; i += 2) {
+                const uint32_t k4 = lds32(rd), k5 = lds32(rd + stride);
+                const uint32_t t2 = lds16(prow + (k2 & idmask)), t3 = lds16(prow + (k3 & idmask));
+                uint32_t pop1, pop2;
+                dispatch2_pp<M>(f, k0, t0, k1, t1, lowmask, mulSH, pop1, pop2);
+                if constexpr (EMIT) {
+                    sts32(wr, pop1);
+                    sts32(wr + stride, pop2);
+                    wr += 2u * stride;
+                }
+                k0 = k2;
+                k1 = k3;
+                k2 = k4;
+                k3 = k5;
+                t0 = t2;
+                t1 = t3;
+                rd += 2u * stride;
             }
-            in = in_n;
-            in_n = in_nn;
-            pp = pp_n;
-            rd += stride;
+            if (i < cnt) {
+                const uint32_t popped = dispatch_pp<M>(f, k0, t0, lowmask, mulSH);
+                if constexpr (EMIT) sts32(wr, popped);
+            }
         }
         if constexpr (EMIT) w = cnt - skip;
     }
@@ -605,8 +658,8 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     const uint32_t row_bytes = (uint32_t)table_row_halves(n) * 2u;
     const uint32_t nB = (uint32_t)n | (uint32_t)L.B << 16, SH = (uint32_t)L.SH;
     // Every buffer slot holds a valid key (or 0) before the read-ahead can
-    // touch it: clear the buffer and its two spare slots.
-    for (int w = 0; w <= L.B + 1; ++w) sts32(buf + (uint32_t)w * stride, 0u);
+    // touch it: clear the buffer and its four spare slots.
+    for (int w = 0; w < L.B + 4; ++w) sts32(buf + (uint32_t)w * stride, 0u);
     bool bad = false;
     uint32_t last_key = 0;
     const int lane = threadIdx.x & 31;
