@@ -305,6 +305,9 @@ int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream strea
  * chunk x decoder variant) that fits, `repeats` timed runs each, on
  * generations that do not advance the state, keeps the fastest and reports
  * it; synchronous.
+ * ffs_batch_info: instance count, generations done, launch shape and the
+ * decoder variant in use (1 / 2: one stage / stage pairs, saved heaps in
+ * shared memory; 3 / 4: the same with saved heaps in tensor memory).
  * ffs_batch_get: rows and makespans of one instance (host or device
  * pointers, cudaMemcpyDefault).  ffs_batch_best: best makespan of every
  * instance into best[count] (host), synchronous.

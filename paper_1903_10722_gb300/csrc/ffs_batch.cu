@@ -32,6 +32,8 @@ struct BatchShape {
     int B;          // jobs per round requested (instances with n <= B run in one round)
     int max_n, max_S, max_tw;
     int pairs;      // decoder variant: stages in interleaved pairs
+    int tmem_cols;  // TMEM columns per block for saved heaps (0: none)
+    int tmem_group_cols;  // columns per warp of a lane quarter
 };
 
 __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restrict__ insts, const int2 *__restrict__ units,
@@ -42,6 +44,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_unit;
     __shared__ DecodeLayout s_L;
+    __shared__ uint32_t s_tbase;
     const int T = blockDim.x;
     const int bits_per_warp = (shape.max_n + 31) >> 5;
     const SmemMap map = smem_map(shape.max_n, shape.max_S, T, bits_per_warp);
@@ -53,6 +56,13 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
     const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
     const int cells = rows * cols;
     if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, decoded_add);
+    // TMEM for saved heaps, held for the whole launch; freed after the loop
+    if (shape.tmem_cols) {
+        if (warp == 0) tc::tmem_alloc(&s_tbase, (uint32_t)shape.tmem_cols);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     for (;;) {
         __syncthreads();  // the previous unit is done with shared memory
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
@@ -72,16 +82,20 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             L.mulSH = I.mulSH;
             L.single = shape.B >= n ? 1 : 0;
             L.B = L.single ? round_up(n, 8) : shape.B;
-            L.heap_words = L.single ? 0 : I.heap_words;
-            L.thread_words = L.heap_words + L.B + 4;
             L.pairs = shape.pairs;
-            L.tmem_cols = 0;   // saved heaps in shared memory
-            L.tmem_group_cols = 0;
-            L.tmem_stages = 0;
-            L.tmem_split = 0;
-            L.tmem_addr = 0;
             L.M = st;
             L.heap_off = st + S;
+            // this instance's stages whose heaps fit the warp's TMEM columns
+            int ns = 0;
+            if (!L.single && shape.tmem_cols)
+                while (ns < S && st[S + ns] + st[ns] <= shape.tmem_group_cols) ++ns;
+            L.tmem_cols = (uint32_t)shape.tmem_cols;
+            L.tmem_group_cols = shape.tmem_group_cols;
+            L.tmem_stages = ns;
+            L.tmem_split = ns < S ? st[S + ns] : I.heap_words;
+            L.tmem_addr = s_tbase;
+            L.heap_words = L.single ? 0 : I.heap_words - L.tmem_split;
+            L.thread_words = L.heap_words + L.B + 4;
         }
         __syncthreads();
         const DecodeLayout &L = s_L;
@@ -100,6 +114,13 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             const bool valid = c < end;
             cellular_warp_cells(L, g, ref, valid ? c : end - 1, valid, rows, cols, I.ld, wbits, region, T, tab, wst);
         }
+    }
+    if (shape.tmem_cols) {
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0) tc::tmem_dealloc(s_tbase, (uint32_t)shape.tmem_cols);
     }
 }
 
@@ -150,34 +171,74 @@ static void batch_free(ffs_batch *b)
     delete b;
 }
 
-// Shape (threads per block T, chunk B): feasibility and occupancy.
+// Shape (threads per block T, chunk B): feasibility and occupancy.  The
+// decoder variant decides pairs and the TMEM option (as for a single
+// instance): saved heaps in shared memory only, or the prefix of each
+// instance's stages that fits the warp's TMEM column group, with `tb` blocks
+// per SM sharing the 512 columns (shared memory padded so that no further
+// block becomes resident).  Kept: most resident threads, then the TMEM
+// preference of the variant.
 static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *smem, int *blocks)
 {
-    BatchShape s{};
-    s.B = B;
-    s.pairs = pairs_of(b->prm.decode_variant);
-    for (const BatchInst &I : b->hinst) {
-        s.max_n = std::max(s.max_n, I.n);
-        s.max_S = std::max(s.max_S, I.S);
-        const bool single = B >= I.n;
-        const int tw = (single ? 0 : I.heap_words) + (single ? round_up(I.n, 8) : B) + 4;
-        s.max_tw = std::max(s.max_tw, tw);
+    const int pref = tmem_of(b->prm.decode_variant);
+    BatchShape best{};
+    size_t best_bytes = 0;
+    int best_nb = 0;
+    long best_score = -1;
+    for (int tb : {0, 1, 2, 4}) {
+        if (tb && pref == 0) continue;
+        BatchShape s{};
+        s.B = B;
+        s.pairs = pairs_of(b->prm.decode_variant);
+        const int groups = (T / 32 + 3) / 4;
+        s.tmem_cols = tb ? 512 / tb : 0;
+        s.tmem_group_cols = tb ? s.tmem_cols / groups : 0;
+        bool any_tmem = false;
+        for (size_t i = 0; i < b->hinst.size(); ++i) {
+            const BatchInst &I = b->hinst[i];
+            s.max_n = std::max(s.max_n, I.n);
+            s.max_S = std::max(s.max_S, I.S);
+            const bool single = B >= I.n;
+            int split = 0;
+            if (tb && !single) {
+                const ffs_instance *inst = b->insts[i];
+                for (int st = 0; st < I.S && split + inst->M_eff[st] <= s.tmem_group_cols; ++st) split += inst->M_eff[st];
+                any_tmem = any_tmem || split > 0;
+            }
+            const int tw = (single ? 0 : I.heap_words - split) + (single ? round_up(I.n, 8) : B) + 4;
+            s.max_tw = std::max(s.max_tw, tw);
+        }
+        if (tb && !any_tmem) continue;
+        const SmemMap m = smem_map(s.max_n, s.max_S, T, (s.max_n + 31) / 32);
+        size_t bytes = (size_t)(m.region + s.max_tw * T) * 4u;
+        if (bytes > 232448) continue;
+        auto occ = [&](size_t by) {
+            int nb = 0;
+            if (cudaFuncSetAttribute(k_batch_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)by) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_cellular, T, by) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return 0;
+            }
+            return nb;
+        };
+        int nb = occ(bytes);
+        while (tb && nb > tb && bytes + 4096 <= 232448) {
+            bytes += 4096;
+            nb = occ(bytes);
+        }
+        if (nb < 1 || (tb && nb != tb)) continue;
+        const long score = (long)nb * T * 4 + (tb ? (pref == 2 ? 2 : -2) : 0);
+        if (score > best_score) {
+            best_score = score;
+            best = s;
+            best_bytes = bytes;
+            best_nb = nb;
+        }
     }
-    const SmemMap m = smem_map(s.max_n, s.max_S, T, (s.max_n + 31) / 32);
-    const size_t bytes = (size_t)(m.region + s.max_tw * T) * 4u;
-    if (bytes > 232448) return FFS_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(k_batch_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return FFS_EUNSUPPORTED;
-    }
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_cellular, T, bytes) != cudaSuccess || nb < 1) {
-        (void)cudaGetLastError();
-        return FFS_EUNSUPPORTED;
-    }
-    *shape = s;
-    *smem = bytes;
-    *blocks = nb;
+    if (best_score < 0) return FFS_EUNSUPPORTED;
+    *shape = best;
+    *smem = best_bytes;
+    *blocks = best_nb;
     return FFS_OK;
 }
 
@@ -326,9 +387,11 @@ int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stag
         const int Breq = prm->decode_chunk > 0 ? prm->decode_chunk : 32;
         const int Ts[4] = {256, 128, 64, 32};
         rc = FFS_EUNSUPPORTED;
-        for (int t = 0; t < 4 && rc; ++t) {
-            if (prm->block_threads > 0 && Ts[t] != prm->block_threads) continue;
-            rc = batch_set_shape(b, Ts[t], Breq, st);
+        if (prm->block_threads > 0) {
+            if (prm->block_threads % 32 == 0 && prm->block_threads <= 512)
+                rc = batch_set_shape(b, prm->block_threads, Breq, st);
+        } else {
+            for (int t = 0; t < 4 && rc; ++t) rc = batch_set_shape(b, Ts[t], Breq, st);
         }
         if (rc) rc = set_error(FFS_EUNSUPPORTED, "no batch launch shape fits shared memory");
     }
@@ -394,7 +457,7 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
     const int Ts[7] = {64, 128, 256, 320, 384, 448, 512};
     const int Bs[5] = {8, 16, 32, 64, 128};
     int rc = FFS_OK;
-    for (int vi = 1; vi <= 2 && !rc; ++vi)
+    for (int vi = 1; vi <= kMaxVariant && !rc; ++vi)
     for (int ti = 0; ti < 7 && !rc; ++ti) {
         for (int bi = 0; bi < 5 && !rc; ++bi) {
             BatchShape s;
@@ -440,7 +503,7 @@ int ffs_batch_info(const ffs_batch *b, int32_t *count, int64_t *generation, int3
 {
     clear_error();
     if (!b) return set_error(FFS_EINVAL, "NULL batch");
-    if (variant) *variant = b->shape.pairs ? 2 : 1;
+    if (variant) *variant = (b->shape.pairs ? 2 : 1) + (b->shape.tmem_cols ? 2 : 0);
     if (count) *count = b->count;
     if (generation) *generation = b->host_gen;
     if (threads) *threads = b->T;

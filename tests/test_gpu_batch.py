@@ -93,3 +93,28 @@ def test_batch_256_uneven_sampled(gpu):
                 assert after[i][0][c].tolist() == child[:s.n].tolist() and after[i][1][c] == mc, (i, c)
             else:
                 assert after[i][0][c].tolist() == pop[c, :s.n].tolist() and after[i][1][c] == ms[c], (i, c)
+
+
+@pytest.mark.parametrize("variant,threads", [(3, 128), (4, 256), (3, 448), (4, 320)])
+def test_batch_tensor_memory_heaps_match_oracle(gpu, variant, threads):
+    """Chunked decoding (8 jobs per round) with each instance's saved heaps in
+    tensor memory as far as its stages fit the warp's columns."""
+    specs = _mixed_specs()
+    rows, cols = 6, 5
+    prm = gpu.ffs_params_default()
+    prm.decode_variant, prm.decode_chunk, prm.block_threads = variant, 8, threads
+    oprm = orc.Params(seed=7)
+    b = gpu.Batch(specs, prm, rows, cols)
+    assert b.info()["variant"] == variant
+    states = [_oracle_state(s, i, rows, cols) for i, s in enumerate(specs)]
+    gpu.ffs_batch_step(b, 4)
+    for gen in range(1, 5):
+        for i, s in enumerate(specs):
+            o, pop, ms = states[i]
+            pop, ms, _ = orc.cellular_generation(o, oprm, i, gen, rows, cols, pop, ms)
+            states[i] = (o, pop, ms)
+    for i, s in enumerate(specs):
+        pop, ms = gpu.batch_tensors(b, i)
+        torch.cuda.synchronize()
+        assert np.array_equal(pop.cpu().numpy(), states[i][1][:, :s.n]), i
+        assert np.array_equal(ms.cpu().numpy().astype(np.int64), states[i][2]), i
