@@ -176,6 +176,12 @@ def run_reference(args):
     return 0
 
 
+def _apply_shape(prm, args):
+    """--shape THREADS,CHUNK,VARIANT pins the launch shape (no autotuning)."""
+    if args.shape:
+        prm.block_threads, prm.decode_chunk, prm.decode_variant = (int(x) for x in args.shape.split(","))
+
+
 def _config(workload: str, ws: int) -> dict:
     from ffs_workloads import WORKLOADS
     w = WORKLOADS[workload]
@@ -215,6 +221,7 @@ def run_ours(args):
     prm.migration_mode = ffs.FFS_MIG_RING if w.get("migration", "ring") == "ring" else ffs.FFS_MIG_PENETRATION
     prm.migration_gap = int(w.get("gap", 1))
     prm.ring_num, prm.ring_den = w.get("mig_num", 2), w.get("mig_den", 100)
+    _apply_shape(prm, args)
     stream = torch.cuda.current_stream()
     isl = ffs.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
     tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=2)
@@ -360,6 +367,7 @@ def run_batch(args):
     w = WORKLOADS[args.workload]
     specs = make_batch(w["count"], seed=w["seed"])
     prm = ffs.ffs_params_default()
+    _apply_shape(prm, args)
     b = ffs.Batch(specs, prm, w["rows"], w["cols"])
     tuned = b.info() if args.no_autotune else ffs.ffs_batch_autotune(b, repeats=2)
     stream = torch.cuda.current_stream()
@@ -515,8 +523,12 @@ def run_decode(args):
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
     results = {}
     shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 64) for t in (64, 128, 256, 320, 384, 448, 512)]
+    variants = (1, 2, 3, 4)
+    if args.shape:
+        t, c, v = (int(x) for x in args.shape.split(","))
+        shapes, variants = [(c, t)], (v,)
     names = {1: "single_stage", 2: "stage_pairs", 3: "single_stage_tmem", 4: "stage_pairs_tmem"}
-    for variant in (1, 2, 3, 4):
+    for variant in variants:
         best = None
         for chunk, threads in shapes:
             try:
@@ -566,7 +578,11 @@ def main():
     ap.add_argument("--workload", default="scale_500x20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape THREADS,CHUNK,VARIANT instead of the autotuner (profiling)")
     args = ap.parse_args()
+    if args.shape:
+        args.no_autotune = True
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
