@@ -17,6 +17,8 @@ in for them):
                32x32 torus each
   paper_300x4  the paper's shape: 300 jobs x 4 stages x 2 machines,
                p ~ U[1,5] (Section 5, Table 1), for context runs
+  paper_obj_300x4  the same shape with Table 1's release and due times
+               and WT = 100 (objective WT * total tardiness + C_max)
 """
 from __future__ import annotations
 
@@ -31,6 +33,9 @@ class InstanceSpec:
     S: int
     M: np.ndarray   # int32 [S]
     p: np.ndarray   # int32 [n][S]
+    release: np.ndarray | None = None   # int32 [n]
+    due: np.ndarray | None = None       # int32 [n]
+    wt: int = 0
 
 
 def make_instance(n: int, S: int, m_lo: int, m_hi: int, p_lo: int = 1, p_hi: int = 99,
@@ -40,6 +45,23 @@ def make_instance(n: int, S: int, m_lo: int, m_hi: int, p_lo: int = 1, p_hi: int
     M = rng.integers(m_lo, m_hi + 1, size=S, dtype=np.int64).astype(np.int32)
     p = rng.integers(p_lo, p_hi + 1, size=(n, S), dtype=np.int64).astype(np.int32)
     return InstanceSpec(n, S, M, p)
+
+
+def make_paper_instance(n: int = 300, S: int = 4, m: int = 2, seed: int = 1, wt: int = 100) -> InstanceSpec:
+    """The paper's experimental instances (Section 5, Table 1) on identical
+    machines: p[j][s] ~ U{1..5}; Pbar_j = sum_s p[j][s] (the table's
+    sum_m P_jsm / M_s with P_jsm = p_js), Pbar = sum_j Pbar_j; R_j ~ U{0..Pbar};
+    sigma_j ~ U[0, 2) real, D_j = R_j + floor(Pbar_j (1 + sigma_j)); WT = 100.
+    Drawn in that order from one stream."""
+    rng = np.random.default_rng(seed)
+    M = np.full(S, m, dtype=np.int32)
+    p = rng.integers(1, 6, size=(n, S), dtype=np.int64).astype(np.int32)
+    pbar_j = p.sum(axis=1).astype(np.int64)
+    pbar = int(pbar_j.sum())
+    release = rng.integers(0, pbar + 1, size=n, dtype=np.int64)
+    sigma = rng.random(n) * 2.0
+    due = release + np.floor(pbar_j * (1.0 + sigma)).astype(np.int64)
+    return InstanceSpec(n, S, M, p, release.astype(np.int32), due.astype(np.int32), wt)
 
 
 def make_batch(count: int = 256, seed: int = 1, n_range=(20, 500), s_range=(5, 20),

@@ -52,6 +52,15 @@ class _Params(ctypes.Structure):
         ("pseudo_pc", ctypes.c_uint64),
         ("cell_replace_le", ctypes.c_int32),
         ("pseudo_always", ctypes.c_int32),
+        ("obj", ctypes.c_void_p),
+    ]
+
+
+class _Objective(ctypes.Structure):
+    _fields_ = [
+        ("release", ctypes.POINTER(ctypes.c_int32)),
+        ("due", ctypes.POINTER(ctypes.c_int32)),
+        ("wt", ctypes.c_int64),
     ]
 
 
@@ -87,6 +96,15 @@ def _load():
         lib.orc_bernoulli.restype = ctypes.c_int
         lib.orc_decode.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i16p, _i64p]
         lib.orc_decode.restype = ctypes.c_int64
+        lib.orc_decode_obj.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, _i16p,
+                                       _i64p]
+        lib.orc_decode_obj.restype = ctypes.c_int64
+        lib.orc_eval_population_obj.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p,
+                                                _i16p, ctypes.c_int64, ctypes.c_int64, _i64p]
+        lib.orc_eval_population_obj.restype = None
+        lib.orc_bruteforce_obj.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, _i64p,
+                                           _i16p]
+        lib.orc_bruteforce_obj.restype = ctypes.c_int64
         lib.orc_eval_population.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                             _i16p, ctypes.c_int64, ctypes.c_int64, _i64p]
         lib.orc_eval_population.restype = None
@@ -145,7 +163,8 @@ def _ptr(a: np.ndarray, ctype):
 
 # ---------------------------------------------------------------------------
 # Problem instance (Section 3): n jobs, S stages, M_s identical machines,
-# processing times p[j][s].
+# processing times p[j][s]; optionally release times R_j, due times D_j and
+# the tardiness weight WT (objective WT * sum_j max(0, C_j - D_j) + C_max).
 # ---------------------------------------------------------------------------
 @dataclass
 class Instance:
@@ -153,10 +172,26 @@ class Instance:
     S: int
     M: np.ndarray   # int32 [S]
     p: np.ndarray   # int32 [n][S], job-major
+    release: np.ndarray | None = None   # int32 [n]
+    due: np.ndarray | None = None       # int32 [n]
+    wt: int = 0
 
     def __post_init__(self):
         self.M = np.ascontiguousarray(self.M, dtype=np.int32)
         self.p = np.ascontiguousarray(self.p, dtype=np.int32).reshape(self.n, self.S)
+        self._obj = None
+        if self.release is not None or self.due is not None:
+            if self.release is not None:
+                self.release = np.ascontiguousarray(self.release, dtype=np.int32).reshape(self.n)
+            if self.due is not None:
+                self.due = np.ascontiguousarray(self.due, dtype=np.int32).reshape(self.n)
+            self._obj = _Objective(
+                _ptr(self.release, ctypes.c_int32) if self.release is not None else None,
+                _ptr(self.due, ctypes.c_int32) if self.due is not None else None, int(self.wt))
+
+    def obj_addr(self):
+        """Address of the C objective record (None: the makespan alone)."""
+        return ctypes.addressof(self._obj) if self._obj is not None else None
 
 
 def lower_bound(inst: Instance) -> int:
@@ -200,12 +235,14 @@ def threshold(prob: float) -> int:
 # Decoder
 # ---------------------------------------------------------------------------
 def decode(inst: Instance, perm, gantt: bool = False):
+    """The instance's objective (the makespan without due times) of one job
+    order; with gantt, also its (stage, job, machine, start, end) records."""
     lib = _load()
     perm = np.ascontiguousarray(perm, dtype=np.int16)
     g = np.zeros((inst.n * inst.S, 5), dtype=np.int64) if gantt else None
-    cmax = lib.orc_decode(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
-                          _ptr(perm, ctypes.c_int16), _ptr(g, ctypes.c_int64) if gantt else None)
-    return (int(cmax), g) if gantt else int(cmax)
+    v = lib.orc_decode_obj(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
+                           inst.obj_addr(), _ptr(perm, ctypes.c_int16), _ptr(g, ctypes.c_int64) if gantt else None)
+    return (int(v), g) if gantt else int(v)
 
 
 def eval_population(inst: Instance, pop: np.ndarray) -> np.ndarray:
@@ -213,8 +250,8 @@ def eval_population(inst: Instance, pop: np.ndarray) -> np.ndarray:
     pop = np.ascontiguousarray(pop, dtype=np.int16)
     N, ld = pop.shape
     out = np.zeros(N, dtype=np.int64)
-    lib.orc_eval_population(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
-                            _ptr(pop, ctypes.c_int16), N, ld, _ptr(out, ctypes.c_int64))
+    lib.orc_eval_population_obj(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
+                                inst.obj_addr(), _ptr(pop, ctypes.c_int16), N, ld, _ptr(out, ctypes.c_int64))
     return out
 
 
@@ -224,8 +261,8 @@ def bruteforce(inst: Instance):
     lib = _load()
     worst = ctypes.c_int64(0)
     bp = np.zeros(inst.n, dtype=np.int16)
-    best = lib.orc_bruteforce(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
-                              ctypes.byref(worst), _ptr(bp, ctypes.c_int16))
+    best = lib.orc_bruteforce_obj(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
+                                  inst.obj_addr(), ctypes.byref(worst), _ptr(bp, ctypes.c_int16))
     return int(best), int(worst.value), bp
 
 
@@ -270,9 +307,10 @@ class Params:
     cell_replace_le: bool = False
     pseudo_always: bool = False
 
-    def _c(self) -> _Params:
+    def _c(self, inst: Instance | None = None) -> _Params:
         return _Params(self.seed, threshold(self.cell_pc), threshold(self.cell_pm),
-                       threshold(self.pseudo_pc), int(self.cell_replace_le), int(self.pseudo_always))
+                       threshold(self.pseudo_pc), int(self.cell_replace_le), int(self.pseudo_always),
+                       inst.obj_addr() if inst is not None else None)
 
 
 def cellular_child(inst: Instance, prm: Params, rows: int, cols: int, c: int, x,
@@ -283,7 +321,7 @@ def cellular_child(inst: Instance, prm: Params, rows: int, cols: int, c: int, x,
     ms = np.ascontiguousarray(ms, dtype=np.int64)
     child = np.zeros(inst.n, dtype=np.int16)
     parents = np.zeros(2, dtype=np.int32)
-    cp = prm._c()
+    cp = prm._c(inst)
     _load().orc_cellular_child(inst.n, rows, cols, c, _ptr(x, ctypes.c_uint32), ctypes.byref(cp),
                                _ptr(pop, ctypes.c_int16), pop.shape[1], _ptr(ms, ctypes.c_int64),
                                _ptr(child, ctypes.c_int16), _ptr(parents, ctypes.c_int32))
@@ -298,7 +336,7 @@ def cellular_generation(inst: Instance, prm: Params, island: int, generation: in
     ms = np.ascontiguousarray(ms, dtype=np.int64)
     out = np.zeros_like(pop)
     out_ms = np.zeros_like(ms)
-    cp = prm._c()
+    cp = prm._c(inst)
     k = lib.orc_cellular_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
                                     _ptr(inst.p, ctypes.c_int32), ctypes.byref(cp), island, generation,
                                     rows, cols, pop.shape[1], _ptr(pop, ctypes.c_int16),
@@ -320,7 +358,7 @@ def screened_cellular_generation(inst: Instance, prm: Params, island: int, gener
     cells = rows * cols
     chosen = np.zeros(cells, dtype=np.int32)
     cands = np.zeros((cells * K, inst.n), dtype=np.int16)
-    cp = prm._c()
+    cp = prm._c(inst)
     lib.orc_screened_cellular_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
                                          ctypes.byref(cp), island, generation, rows, cols, pop.shape[1],
                                          _ptr(pop, ctypes.c_int16), _ptr(ms, ctypes.c_int64),
@@ -346,7 +384,7 @@ def pseudo_generation(inst: Instance, prm: Params, island: int, generation: int,
     ms = np.ascontiguousarray(ms, dtype=np.int64)
     out = np.zeros_like(pop)
     out_ms = np.zeros_like(ms)
-    cp = prm._c()
+    cp = prm._c(inst)
     k = lib.orc_pseudo_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
                                   _ptr(inst.p, ctypes.c_int32), ctypes.byref(cp), island, generation,
                                   pop.shape[0], pop.shape[1], _ptr(pop, ctypes.c_int16),

@@ -13,7 +13,10 @@
  * Solving Large Size Flexible Flow Shop Scheduling Problems on Hybrid
  * multi-core CPU and GPU Platforms", arXiv:1903.10722):
  *   - Section 3: the FFS problem (jobs pass all stages in order, each
- *     operation on exactly one of M_s identical machines, no preemption).
+ *     operation on exactly one of M_s identical machines, no preemption),
+ *     release times R_j, due times D_j and the objective
+ *     WT * sum_j T_j + C_max with tardiness T_j = max(0, C_j - D_j).
+ *   - Section 5, Table 1: WT = 100 and the release / due time generator.
  *   - Section 4.1: the two islands (cellular GA on a 2D grid, pseudo GA with
  *     complementary parents whose children replace them).
  *   - Section 4.2: the cellular step (recombine two neighbours, mutate,
@@ -29,9 +32,10 @@
  * Philox4x32-10 follows Salmon, Moraes, Dror and Shaw, "Parallel Random
  * Numbers: As Easy as 1, 2, 3", SC 2011 (Section 4, the Philox S-box).
  *
- * Parity status: the decoder, the operators, Philox and the migration
- * formulas are pinned by tests (hand-worked Gantt charts, closed forms,
- * brute force, library cross-checks).  The GA loop as a whole (the sequence
+ * Parity status: the decoder (makespan and the Section 3 objective), the
+ * operators, Philox and the migration formulas are pinned by tests
+ * (hand-worked Gantt charts, closed forms, brute force, library
+ * cross-checks).  The GA loop as a whole (the sequence
  * of generations) has no published trajectory: "parity unpinned" beyond
  * those component pins.
  */
@@ -109,11 +113,20 @@ int orc_bernoulli(uint32_t x, uint64_t threshold)
  * in ascending (completion time at the previous stage, job index) order.
  * Each job goes to the machine that is free earliest, the lowest machine
  * index on ties, and starts at max(machine free time, release from the
- * previous stage).  Stage-1 release time is 0.  Returns C_max.
+ * previous stage).  Stage-1 release time is R_j (0 without release times).
+ *
+ * Objective (Section 3): C_max, plus WT * sum_j max(0, C_j - D_j) when due
+ * times are given, C_j being job j's completion at the last stage.
  *
  * p is [n][S] row-major (job-major).  If gantt is not NULL it receives
  * n*S records of 5 int64 (stage, job, machine, start, end) in dispatch
  * order, stage by stage. */
+typedef struct {
+    const int32_t *release;   /* R_j [n], or NULL (all 0) */
+    const int32_t *due;       /* D_j [n], or NULL (no tardiness term) */
+    int64_t wt;               /* WT, the weight of the total tardiness */
+} orc_objective;
+
 typedef struct { int64_t c; int32_t j; } orc_pair;
 
 static int orc_pair_cmp(const void *a, const void *b)
@@ -126,13 +139,14 @@ static int orc_pair_cmp(const void *a, const void *b)
     return 0;
 }
 
-int64_t orc_decode(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
-                   const int16_t *perm, int64_t *gantt)
+int64_t orc_decode_obj(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                       const orc_objective *obj, const int16_t *perm, int64_t *gantt)
 {
     int64_t *c_prev = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     int64_t *c_cur = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     orc_pair *pairs = (orc_pair *)malloc((size_t)n * sizeof(orc_pair));
+    const int32_t *release = obj ? obj->release : NULL;
     int64_t rec = 0;
     for (int32_t s = 0; s < S; ++s) {
         if (s == 0) {
@@ -149,7 +163,7 @@ int64_t orc_decode(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
             int32_t best = 0;
             for (int32_t m = 1; m < ms; ++m)
                 if (free_at[m] < free_at[best]) best = m;
-            int64_t ready = (s == 0) ? 0 : c_prev[j];
+            int64_t ready = (s == 0) ? (release ? (int64_t)release[j] : 0) : c_prev[j];
             int64_t start = free_at[best] > ready ? free_at[best] : ready;
             int64_t end = start + (int64_t)p[(int64_t)j * S + s];
             c_cur[j] = end;
@@ -168,28 +182,47 @@ int64_t orc_decode(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
     }
     int64_t cmax = 0;
     for (int32_t j = 0; j < n; ++j) if (c_prev[j] > cmax) cmax = c_prev[j];
+    int64_t total_tardiness = 0;
+    if (obj && obj->due)
+        for (int32_t j = 0; j < n; ++j)
+            if (c_prev[j] > obj->due[j]) total_tardiness += c_prev[j] - obj->due[j];
     free(c_prev); free(c_cur); free(order); free(pairs);
-    return cmax;
+    return (obj && obj->due ? obj->wt * total_tardiness : 0) + cmax;
 }
 
-/* Makespan of every row of a population [N][ld] (int16 genes). */
+/* The makespan alone (no release or due times). */
+int64_t orc_decode(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                   const int16_t *perm, int64_t *gantt)
+{
+    return orc_decode_obj(n, S, M, p, NULL, perm, gantt);
+}
+
+/* Objective of every row of a population [N][ld] (int16 genes); obj NULL:
+ * the makespan. */
+void orc_eval_population_obj(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                             const orc_objective *obj, const int16_t *pop, int64_t N, int64_t ld,
+                             int64_t *out)
+{
+    for (int64_t i = 0; i < N; ++i)
+        out[i] = orc_decode_obj(n, S, M, p, obj, pop + i * ld, NULL);
+}
+
 void orc_eval_population(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
                          const int16_t *pop, int64_t N, int64_t ld, int64_t *out)
 {
-    for (int64_t i = 0; i < N; ++i)
-        out[i] = orc_decode(n, S, M, p, pop + i * ld, NULL);
+    orc_eval_population_obj(n, S, M, p, NULL, pop, N, ld, out);
 }
 
 /* Brute force over all n! orders (n <= 10): returns the minimum makespan and
  * writes the maximum to *worst.  Uses the lexicographic next-permutation walk. */
-int64_t orc_bruteforce(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
-                       int64_t *worst, int16_t *best_perm)
+int64_t orc_bruteforce_obj(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                           const orc_objective *obj, int64_t *worst, int16_t *best_perm)
 {
     int16_t perm[16];
     for (int32_t i = 0; i < n; ++i) perm[i] = (int16_t)i;
     int64_t best = -1, wst = -1;
     for (;;) {
-        int64_t c = orc_decode(n, S, M, p, perm, NULL);
+        int64_t c = orc_decode_obj(n, S, M, p, obj, perm, NULL);
         if (best < 0 || c < best) {
             best = c;
             if (best_perm) memcpy(best_perm, perm, (size_t)n * sizeof(int16_t));
@@ -207,6 +240,12 @@ int64_t orc_bruteforce(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
     }
     if (worst) *worst = wst;
     return best;
+}
+
+int64_t orc_bruteforce(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                       int64_t *worst, int16_t *best_perm)
+{
+    return orc_bruteforce_obj(n, S, M, p, NULL, worst, best_perm);
 }
 
 /* ------------------------------------------------------------------ */
@@ -271,6 +310,8 @@ typedef struct {
     uint64_t pseudo_pc;    /* pseudo crossover threshold */
     int32_t cell_replace_le;   /* 0: replace iff child < cell; 1: iff child <= cell */
     int32_t pseudo_always;     /* 0: pair keeps the 2 best of {c1,c2,a,b}; 1: children replace parents */
+    const orc_objective *obj;  /* the instance's objective (NULL: makespan); every "makespan"
+                                  below is then this objective */
 } orc_params;
 
 /* One child of the cellular island for cell c (Section 4.2), given its ten
@@ -325,7 +366,7 @@ int64_t orc_cellular_generation(int32_t n, int32_t S, const int32_t *M, const in
         for (uint32_t d = 0; d < 10u; ++d)
             x[d] = orc_draw(prm->seed, ORC_PURPOSE_CELLULAR, island, generation, (uint32_t)c, d);
         orc_cellular_child(n, rows, cols, c, x, prm, pop_in, ld, ms_in, child, NULL);
-        int64_t mc = orc_decode(n, S, M, p, child, NULL);
+        int64_t mc = orc_decode_obj(n, S, M, p, prm->obj, child, NULL);
         int better = prm->cell_replace_le ? (mc <= ms_in[c]) : (mc < ms_in[c]);
         int16_t *dst = pop_out + (int64_t)c * ld;
         if (better) {
@@ -402,8 +443,8 @@ int64_t orc_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int3
         int32_t l = u < v ? u : v, r = u < v ? v : u;
         orc_order_crossover(n, a, b, l, r, c1);
         orc_order_crossover(n, b, a, l, r, c2);
-        int64_t m1 = orc_decode(n, S, M, p, c1, NULL);
-        int64_t m2 = orc_decode(n, S, M, p, c2, NULL);
+        int64_t m1 = orc_decode_obj(n, S, M, p, prm->obj, c1, NULL);
+        int64_t m2 = orc_decode_obj(n, S, M, p, prm->obj, c2, NULL);
         decoded += 2;
         if (prm->pseudo_always) {
             memcpy(oa, c1, (size_t)n * sizeof(int16_t));
@@ -579,7 +620,7 @@ int64_t orc_screened_cellular_generation(int32_t n, int32_t S, const int32_t *M,
             }
         }
         if (chosen) chosen[c] = pick;
-        int64_t mc = orc_decode(n, S, M, p, best, NULL);
+        int64_t mc = orc_decode_obj(n, S, M, p, prm->obj, best, NULL);
         int better = prm->cell_replace_le ? (mc <= ms_in[c]) : (mc < ms_in[c]);
         int16_t *dst = pop_out + (int64_t)c * ld;
         if (better) {
