@@ -63,6 +63,21 @@ const char *ffs_last_error(void);
  * ---------------------------------------------------------------------- */
 int ffs_instance_create(int32_t n_jobs, int32_t n_stages, const int32_t *machines_per_stage,
                         const int32_t *proc_time, ffs_instance **out);
+
+/* The same problem with the paper's objective (Section 3): job j may not
+ * start its first operation before release[j], has due time due[j], and a
+ * schedule costs  wt * sum_j max(0, C_j - due[j]) + C_max  (C_j = job j's
+ * completion at the last stage); with Section 5 / Table 1, wt = 100.
+ * release, due: host int32[n] (>= 0) or NULL (no release times / the
+ * makespan alone; wt is then ignored).  Every "makespan" that the
+ * evaluation and GA entry points below read or write is then this
+ * objective.  Additional limits: max release + sum of proc_time within the
+ * key bound above, and wt * n * (that bound) + (that bound) < 2^31 (the
+ * objective is an int32), else FFS_EOVERFLOW; wt < 0: FFS_EINVAL.
+ * Batches (ffs_batch_*) take the makespan alone. */
+int ffs_instance_create_objective(int32_t n_jobs, int32_t n_stages, const int32_t *machines_per_stage,
+                                  const int32_t *proc_time, const int32_t *release, const int32_t *due,
+                                  int32_t wt, ffs_instance **out);
 int ffs_instance_destroy(ffs_instance *inst);
 
 /* ------------------------------------------------------------------------

@@ -51,6 +51,7 @@ class ffs_params(ctypes.Structure):
 _SIGS = [
     ("ffs_last_error", ctypes.c_char_p, []),
     ("ffs_instance_create", _i32, [_i32, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
+    ("ffs_instance_create_objective", _i32, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
     ("ffs_instance_destroy", _i32, [_vp]),
     ("ffs_population_eval", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ffs_population_eval_tuned", _i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i32, _i32, _vp]),
@@ -175,16 +176,22 @@ def threshold(prob: float) -> int:
 # Instances
 # ---------------------------------------------------------------------------
 class Instance:
-    """Owner of an ffs_instance handle (Section 3 problem tables)."""
+    """Owner of an ffs_instance handle (Section 3 problem tables; with release
+    and/or due times the objective WT * total tardiness + C_max)."""
 
-    def __init__(self, n: int, S: int, M, p):
+    def __init__(self, n: int, S: int, M, p, release=None, due=None, wt: int = 0):
         import numpy as np
         self.n, self.S = int(n), int(S)
         self.M = np.ascontiguousarray(M, dtype=np.int32)
         self.p = np.ascontiguousarray(p, dtype=np.int32).reshape(self.n, self.S)
+        self.release = None if release is None else np.ascontiguousarray(release, dtype=np.int32).reshape(self.n)
+        self.due = None if due is None else np.ascontiguousarray(due, dtype=np.int32).reshape(self.n)
+        self.wt = int(wt)
         h = _vp()
-        _check(load().ffs_instance_create(self.n, self.S, self.M.ctypes.data, self.p.ctypes.data,
-                                          ctypes.byref(h)))
+        _check(load().ffs_instance_create_objective(
+            self.n, self.S, self.M.ctypes.data, self.p.ctypes.data,
+            None if self.release is None else self.release.ctypes.data,
+            None if self.due is None else self.due.ctypes.data, self.wt, ctypes.byref(h)))
         self.handle = h
 
     @property
@@ -205,6 +212,10 @@ class Instance:
 
 def ffs_instance_create(n, S, M, p) -> Instance:
     return Instance(n, S, M, p)
+
+
+def ffs_instance_create_objective(n, S, M, p, release, due, wt) -> Instance:
+    return Instance(n, S, M, p, release=release, due=due, wt=wt)
 
 
 def ffs_population_eval(inst: Instance, pop, N: int, ld: int, makespan, stream=None):

@@ -16,7 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libffs_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# relocatable device code: the decoder's per-round functions are compiled once
+# (ffs_decoder_*.cu) and called from the kernels of the other units
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-rdc=true"]
 
 
 def _nvcc() -> str:
@@ -48,12 +50,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    srcs = sources()
+    # the decoder units are the longest compiles: start them first
+    srcs = sorted(sources(), key=lambda p: (0 if "ffs_decoder" in p else 1, p))
     objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
-        cmd = [nvcc, *ARCH, *FLAGS, *(extra or []), "-c", src, "-o", obj]
+        # the per-round functions run inside kernels launched with up to 512
+        # threads: at most 128 registers (the kernels' launch bounds)
+        regs = ["-maxrregcount=128"] if "ffs_decoder" in os.path.basename(src) else []
+        cmd = [nvcc, *ARCH, *FLAGS, *regs, *(extra or []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -63,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-rdc=true", "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -94,6 +94,10 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             L.tmem_stages = ns;
             L.tmem_split = ns < S ? st[S + ns] : I.heap_words;
             L.tmem_addr = s_tbase;
+            L.obj_words = 0;   // batches decode the makespan
+            L.has_rel = L.has_due = 0;
+            L.wt = 0u;
+            L.rel_sa = L.due_sa = 0u;
             L.heap_words = L.single ? 0 : I.heap_words - L.tmem_split;
             L.thread_words = L.heap_words + L.B + 4;
         }

@@ -1,5 +1,6 @@
 // ffs_capi.cu -- C ABI entry points: errors, instances, the batched decoder,
 // Philox draws and population initialisation.
+#include <climits>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -44,15 +45,18 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
-    const SmemMap map = smem_map(L.n, L.S, T);
+    const SmemMap map = smem_map(L.n, L.S, T, 0, L.obj_words);
     if (count_dev) N = *count_dev;
-    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
+    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
     if (threadIdx.x == 0) {
         s_L = L;
         s_L.M = st;
         s_L.heap_off = st + L.S;
+        const uint32_t objt = tc::smem_u32(smem + map.tab + table_words(L.n, L.S));
+        s_L.rel_sa = L.has_rel ? objt : 0u;
+        s_L.due_sa = L.has_due ? objt + (uint32_t)L.obj_words * 2u : 0u;
     }
     __syncthreads();
     DecodeLayout &Ls = s_L;
@@ -156,7 +160,7 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
         const bool single = B >= n;
         for (int ti = 0; ti < nt; ++ti) {
             const int T = Ts[ti];
-            const SmemMap m = smem_map(n, S, T, bits_per_warp);
+            const SmemMap m = smem_map(n, S, T, bits_per_warp, inst->obj_words);
             {
                 const int tw = (single ? 0 : inst->heap_words) + B + 4;   // +4: read-ahead slots
                 Cand c;
@@ -213,7 +217,11 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
         L.tmem_stages = best.tstages;
         L.tmem_split = best.split;
     }
-    p.smem_words_fixed = smem_map(n, S, best.T, bits_per_warp).region;
+    L.obj_words = inst->obj_words;
+    L.has_rel = inst->has_rel;
+    L.has_due = inst->has_due;
+    L.wt = (uint32_t)inst->wt;
+    p.smem_words_fixed = smem_map(n, S, best.T, bits_per_warp, inst->obj_words).region;
     *out = p;
     return FFS_OK;
 }
@@ -320,13 +328,15 @@ void ffs_params_default(ffs_params *p)
     p->theta_den = 1;
 }
 
-int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p, ffs_instance **out)
+int ffs_instance_create_objective(int32_t n, int32_t S, const int32_t *M, const int32_t *p, const int32_t *release,
+                                  const int32_t *due, int32_t wt, ffs_instance **out)
 {
     clear_error();
     if (!out || !M || !p) return set_error(FFS_EINVAL, "NULL argument");
     *out = nullptr;
     if (n < 1 || n > 32767) return set_error(FFS_EINVAL, "n_jobs = %d outside [1, 32767]", n);
     if (S < 1 || S > kMaxStages) return set_error(FFS_EINVAL, "n_stages = %d outside [1, %d]", S, kMaxStages);
+    if (due && wt < 0) return set_error(FFS_EINVAL, "tardiness weight %d < 0", wt);
     int64_t total = 0;
     for (int s = 0; s < S; ++s) {
         if (M[s] < 1) return set_error(FFS_EINVAL, "machines_per_stage[%d] = %d < 1", s, M[s]);
@@ -340,18 +350,36 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
                                            (long long)(i / S), (long long)(i % S), p[i]);
         total += p[i];
     }
+    int64_t max_rel = 0;
+    for (int j = 0; release && j < n; ++j) {
+        if (release[j] < 0) return set_error(FFS_EINVAL, "release[%d] = %d < 0", j, release[j]);
+        if (release[j] > max_rel) max_rel = release[j];
+    }
+    for (int j = 0; due && j < n; ++j)
+        if (due[j] < 0) return set_error(FFS_EINVAL, "due[%d] = %d < 0", j, due[j]);
     int bits = 0;
     while ((1 << bits) <= n) ++bits;            // ids 1..n fit in `bits`
     const int SH = bits + 1;
-    if (total >= (int64_t(1) << (32 - SH)))
-        return set_error(FFS_EOVERFLOW, "total processing time %lld needs more than %d bits of key",
-                         (long long)total, 32 - SH);
+    // every completion time is below max release + total processing time
+    const int64_t horizon = max_rel + total;
+    if (horizon >= (int64_t(1) << (32 - SH)))
+        return set_error(FFS_EOVERFLOW, "latest completion bound %lld needs more than %d bits of key",
+                         (long long)horizon, 32 - SH);
+    if (due && (int64_t)wt * n * horizon + horizon > INT32_MAX)
+        return set_error(FFS_EOVERFLOW, "objective bound WT * n * %lld + %lld exceeds int32", (long long)horizon,
+                         (long long)horizon);
     ffs_instance *I = new ffs_instance();
     I->n = n; I->S = S; I->SH = SH; I->total_p = total;
     cudaGetDevice(&I->device);
     cudaDeviceGetAttribute(&I->num_sms, cudaDevAttrMultiProcessorCount, I->device);
     I->host_M.assign(M, M + S);
     I->host_p.assign(p, p + (size_t)n * S);
+    I->has_rel = release ? 1 : 0;
+    I->has_due = due ? 1 : 0;
+    I->wt = due ? wt : 0;
+    if (release) I->host_R.assign(release, release + n);
+    if (due) I->host_D.assign(due, due + n);
+    I->obj_words = (release || due) ? objective_words(n) : 0;
     I->M_eff.resize(S);
     I->heap_off.resize(S);
     int off = 0;
@@ -362,22 +390,30 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
     }
     I->heap_words = off;
     I->tab_words = table_words(n, S);
-    std::vector<uint16_t> tab((size_t)I->tab_words * 2, 0u);
+    // the time table (uint16), then the release and due tables (uint32, entry j + 1 = job j)
+    std::vector<uint16_t> tab((size_t)(I->tab_words + I->obj_words) * 2, 0u);
     const int rowh = table_row_halves(n);
     for (int s = 0; s < S; ++s)
         for (int j = 0; j < n; ++j) tab[(size_t)s * rowh + j + 1] = (uint16_t)p[(size_t)j * S + s];
+    if (I->obj_words) {
+        uint32_t *w = reinterpret_cast<uint32_t *>(tab.data()) + I->tab_words;
+        const int half = I->obj_words / 2;
+        for (int j = 0; j < n; ++j) {
+            w[j + 1] = release ? (uint32_t)release[j] : 0u;
+            w[half + j + 1] = due ? (uint32_t)due[j] : 0u;
+        }
+    }
     std::vector<int32_t> stage(2 * S);
     for (int s = 0; s < S; ++s) { stage[s] = I->M_eff[s]; stage[S + s] = I->heap_off[s]; }
-    // table_words is a multiple of 4: the 16-byte staging loads stay inside
-    const size_t tab_bytes = (size_t)I->tab_words * 4;
+    // table_words and obj_words are multiples of 4: the 16-byte staging loads stay inside
+    const size_t tab_bytes = (size_t)(I->tab_words + I->obj_words) * 4;
     if (cudaMalloc(&I->d_tab, tab_bytes) != cudaSuccess || cudaMalloc(&I->d_stage, 8 * S) != cudaSuccess) {
         cudaFree(I->d_tab);
         delete I;
         (void)cudaGetLastError();
         return set_error(FFS_ENOMEM, "device allocation of the instance tables failed");
     }
-    cudaMemset(I->d_tab, 0, tab_bytes);
-    if (cudaMemcpy(I->d_tab, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(I->d_tab, tab.data(), tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(I->d_stage, stage.data(), stage.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(I->d_tab);
         cudaFree(I->d_stage);
@@ -386,6 +422,11 @@ int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p
     }
     *out = I;
     return FFS_OK;
+}
+
+int ffs_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p, ffs_instance **out)
+{
+    return ffs_instance_create_objective(n, S, M, p, nullptr, nullptr, 0, out);
 }
 
 int ffs_instance_destroy(ffs_instance *I)

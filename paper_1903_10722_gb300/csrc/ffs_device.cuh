@@ -96,6 +96,10 @@ struct DecodeLayout {
     int32_t tmem_stages;   // stages [0, tmem_stages) keep their heaps in TMEM
     int32_t tmem_split;    // their heap words (= heap_off[tmem_stages])
     uint32_t tmem_addr;    // the block's TMEM base address, written by the allocation
+    int32_t obj_words;     // words of the release / due tables after the time table (0: none)
+    int32_t has_rel, has_due;
+    uint32_t wt;           // weight of the total tardiness in the objective
+    uint32_t rel_sa, due_sa;  // shared addresses of the release / due tables (0: none), set in the kernel
     const int32_t *M;        // [S] machines per stage (clamped to n), shared memory
     const int32_t *heap_off; // [S] word offset of each stage's heap (prefix sums of M), shared memory
 };
@@ -200,6 +204,15 @@ __device__ __forceinline__ uint32_t pick_key(const uint32_t (&f)[M], int idx)
 #pragma unroll
     for (int m = 1; m < M; ++m) k = (idx == m) ? f[m] : k;
     return k;
+}
+
+// Tardiness of the completion key k at the last stage: max(0, time - D_j),
+// D_j read from the due table (entry j + 1 = D_j at byte offset 4 (j + 1) =
+// the key's low bits << 1; entry 0 = 0, so the initial keys count 0).
+__device__ __forceinline__ uint32_t key_tardiness(uint32_t k, uint32_t due, uint32_t SH, uint32_t idmask)
+{
+    const uint32_t t = k >> SH, d = lds32(due + ((k & idmask) << 1));
+    return max(t, d) - d;
 }
 
 // The block's decoding layout lives in shared memory (one copy per block,
@@ -307,6 +320,11 @@ struct WarpStageState {
 };
 
 // ---------------------------------------------------------------------------
+// The per-round functions are compiled once, in ffs_decoder_stage.cu and
+// ffs_decoder_pair.cu (explicit instantiations, FFS_DECODER_BODIES defined);
+// every other unit sees their declarations and calls them across units
+// (relocatable device code).
+//
 // One stage for one round, out of line.  Arguments, packed into 32-bit words:
 //   nB   = n | B << 16              SH: key shift
 //   heap = saved-heap handle        buf, prow: shared addresses (the buffer's
@@ -314,18 +332,28 @@ struct WarpStageState {
 //   genes: FIRST only, the chromosome's genes [d0, d0 + cnt) (global int16)
 //   dc   = d0 | cnt << 16           (jobs dispatched before; inputs this round)
 //   mf   = Mr | fl0 << 8            (real heap slots; keys flushed before)
+//   obj  = release table address >> 2 | due table address >> 2 << 16 (the
+//          objective's shared tables, 0 = none): FIRST reads job j's release
+//          time into its stage-0 key; the last stage (!EMIT) sums the
+//          tardiness of its completions
 // FIRST: inputs are the genes, else buf.  EMIT: popped keys go to buf (every
 // stage but the last).  cnt = 0: a call that only continues the stage's
 // final flush.  Once the stage has dispatched all n jobs its heap (sorted)
 // follows its pops into buf, as far as the B slots allow this round.
 // Returns x = keys written | flushed total << 16 | bad gene << 24, y = the
-// heap's largest key (last stage).
+// heap's largest key (last stage), z = the tardiness summed this call (last
+// stage with due times).
 // The heap holds Mr <= M real entries; slots from Mr up hold maximal keys,
 // which never pop and never move (used when M is the 32-slot catch-all).
 // ---------------------------------------------------------------------------
 template <int M, bool FIRST, bool EMIT>
-__device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf, uint32_t prow,
-                                          const int16_t *__restrict__ genes, uint32_t dc, uint32_t mf)
+__device__ __noinline__ uint4 stage_round(uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf, uint32_t prow,
+                                          const int16_t *__restrict__ genes, uint32_t dc, uint32_t mf, uint32_t obj);
+
+#ifdef FFS_DECODER_BODIES
+template <int M, bool FIRST, bool EMIT>
+__device__ __noinline__ uint4 stage_round(uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf, uint32_t prow,
+                                          const int16_t *__restrict__ genes, uint32_t dc, uint32_t mf, uint32_t obj)
 {
     const int n = (int)(nB & 0xFFFFu), B = (int)(nB >> 16);
     const int d0 = (int)(dc & 0xFFFFu), cnt = (int)(dc >> 16);
@@ -333,6 +361,8 @@ __device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
     const uint32_t mulSH = 1u << SH, lowmask = mulSH - 1u, idmask = lowmask & ~1u;
     const uint32_t stride = blockDim.x * 4u;
     const bool single = B >= n;
+    const uint32_t rel = (obj & 0xFFFFu) << 2, due = EMIT ? 0u : (obj >> 16) << 2;
+    uint32_t tard = 0;
     bool bad_gene = false;
     // every slot defined before the conditional load (a partly defined
     // array here costs the whole kernel half its registers)
@@ -358,10 +388,13 @@ __device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
                     uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
                     g = (uint32_t)(int32_t)(int16_t)g;
                     if (g >= (uint32_t)n) { bad_gene = true; g = 0; }
-                    const uint32_t in = (g + 1u) << 1;
+                    uint32_t in = (g + 1u) << 1;
+                    if (rel) in |= lds32(rel + (in << 1)) << SH;   // stage-1 ready time R_j
                     const uint32_t popped = dispatch_pp<M>(f, in, lds16(prow + (in & idmask)), lowmask, mulSH);
                     if constexpr (EMIT) {
                         if (i0 + h >= skip) { sts32(buf + (uint32_t)w * stride, popped); ++w; }
+                    } else {
+                        if (due) tard += key_tardiness(popped, due, SH, idmask);
                     }
                 }
             }
@@ -397,6 +430,8 @@ __device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
                     sts32(wr, pop1);
                     sts32(wr + stride, pop2);
                     wr += 2u * stride;
+                } else {
+                    if (due) tard += key_tardiness(pop1, due, SH, idmask) + key_tardiness(pop2, due, SH, idmask);
                 }
                 k0 = k2;
                 k1 = k3;
@@ -409,13 +444,15 @@ __device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
             if (i < cnt) {
                 const uint32_t popped = dispatch_pp<M>(f, k0, t0, lowmask, mulSH);
                 if constexpr (EMIT) sts32(wr, popped);
+                else if (due) tard += key_tardiness(popped, due, SH, idmask);
             }
         }
         if constexpr (EMIT) w = cnt - skip;
     }
     const int d1 = d0 + cnt;
-    uint2 out;
+    uint4 out;
     out.y = 0u;
+    out.w = 0u;
     if constexpr (EMIT) {
         int fl = fl0;
         if (d1 == n && fl < Mr) {
@@ -436,22 +473,31 @@ __device__ __noinline__ uint2 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
             if (m == Mr - 1) lk = f[m];
         out.y = lk;
         out.x = (uint32_t)fl0 << 16;
+        // all jobs dispatched: the completions still in the heap
+        if (due && d1 == n) {
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (m < Mr) tard += key_tardiness(f[m], due, SH, idmask);
+        }
     }
+    out.z = tard;
     if (bad_gene) out.x |= 1u << 24;
     return out;
 }
+#endif  // FFS_DECODER_BODIES
 
 template <bool FIRST, bool EMIT>
-__device__ __forceinline__ uint2 stage_round_dispatch(int M, uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf,
-                                                      uint32_t prow, const int16_t *genes, uint32_t dc, uint32_t mf)
+__device__ __forceinline__ uint4 stage_round_dispatch(int M, uint32_t nB, uint32_t SH, uint32_t heap, uint32_t buf,
+                                                      uint32_t prow, const int16_t *genes, uint32_t dc, uint32_t mf,
+                                                      uint32_t obj)
 {
 #define FFS_CASE(MM) \
-    case MM: return stage_round<MM, FIRST, EMIT>(nB, SH, heap, buf, prow, genes, dc, mf);
+    case MM: return stage_round<MM, FIRST, EMIT>(nB, SH, heap, buf, prow, genes, dc, mf, obj);
     switch (M) {
         FFS_CASE(1) FFS_CASE(2) FFS_CASE(3) FFS_CASE(4) FFS_CASE(5) FFS_CASE(6) FFS_CASE(7)
         FFS_CASE(8) FFS_CASE(9) FFS_CASE(10) FFS_CASE(11) FFS_CASE(12) FFS_CASE(13) FFS_CASE(14)
         FFS_CASE(15) FFS_CASE(16)
-        default: return stage_round<kMaxM, FIRST, EMIT>(nB, SH, heap, buf, prow, genes, dc, mf);
+        default: return stage_round<kMaxM, FIRST, EMIT>(nB, SH, heap, buf, prow, genes, dc, mf, obj);
     }
 #undef FFS_CASE
 }
@@ -469,13 +515,22 @@ __device__ __forceinline__ uint2 stage_round_dispatch(int M, uint32_t nB, uint32
 // When a has dispatched all n jobs its heap flows into b, and when b has,
 // b's heap flows to the buffer, at most as many keys as the buffer holds
 // this round (the rest in later rounds, from the saved heaps).
-// Arguments as in stage_round, with mm = Ma | Mb << 8 | fa0 << 16 | fb0 << 24
-// and dd = da0 | db0 << 16.  Returns x = keys written | fa1 << 16 |
-// fb1 << 24, y = da1 | db1 << 16, z = b's largest key (last pair).
+// Arguments as in stage_round, with mm = Ma | Mb << 8 | fa0 << 16 | fb0 << 24,
+// dd = da0 | db0 << 16 and due = the due table's shared address when b is
+// the last stage of an instance with due times (else 0).  Returns x = keys
+// written | fa1 << 16 | fb1 << 24, y = da1 | db1 << 16, z = b's largest key
+// (last pair), w = the tardiness of b's completions summed this call.
 // ---------------------------------------------------------------------------
 template <int M, bool EMIT_B>
 __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap_a, uint32_t heap_b, uint32_t buf,
-                                         uint32_t prow_a, uint32_t prow_b, uint32_t mm, uint32_t dd, int cnt)
+                                         uint32_t prow_a, uint32_t prow_b, uint32_t mm, uint32_t dd, int cnt,
+                                         uint32_t due);
+
+#ifdef FFS_DECODER_BODIES
+template <int M, bool EMIT_B>
+__device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap_a, uint32_t heap_b, uint32_t buf,
+                                         uint32_t prow_a, uint32_t prow_b, uint32_t mm, uint32_t dd, int cnt,
+                                         uint32_t due)
 {
     const int n = (int)(nB & 0xFFFFu), B = (int)(nB >> 16);
     const int Ma = (int)(mm & 0xFFu), Mb = (int)((mm >> 8) & 0xFFu);
@@ -484,6 +539,8 @@ __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap
     const uint32_t mulSH = 1u << SH, lowmask = mulSH - 1u, idmask = lowmask & ~1u;
     const uint32_t stride = blockDim.x * 4u;
     const bool chunked = B < n;
+    if constexpr (EMIT_B) due = 0u;
+    uint32_t tard = 0;
     uint32_t fa[M], fb[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -547,6 +604,8 @@ __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap
                 sts32(wr, pb);
                 wr += stride;
                 ++w;
+            } else {
+                if (due) tard += key_tardiness(pb, due, SH, idmask);
             }
             e = e_n;
             pp_e = pp_e_n;
@@ -570,6 +629,7 @@ __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap
                 sts32(buf + (uint32_t)w * stride, pb);
                 ++w;
             }
+            if (!EMIT_B && due) tard += key_tardiness(pb, due, SH, idmask);
             ++db;
         }
         fa1 = fa0 + take;
@@ -596,31 +656,39 @@ __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap
         for (int m = 1; m < M; ++m)
             if (m == Mb - 1) lk = fb[m];
         out.z = lk;
+        // b has dispatched all jobs: the completions still in its heap
+        if (due && db1 == n) {
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (m < Mb) tard += key_tardiness(fb[m], due, SH, idmask);
+        }
     }
+    out.w = tard;
     out.x = (uint32_t)w | (uint32_t)fa1 << 16 | (uint32_t)fb1 << 24;
     out.y = (uint32_t)da1 | (uint32_t)db1 << 16;
     return out;
 }
+#endif  // FFS_DECODER_BODIES
 
 template <bool EMIT_B>
 __device__ __forceinline__ uint4 pair_round_dispatch(int Mp, uint32_t nB, uint32_t SH, uint32_t heap_a,
                                                      uint32_t heap_b, uint32_t buf, uint32_t prow_a, uint32_t prow_b,
-                                                     uint32_t mm, uint32_t dd, int cnt)
+                                                     uint32_t mm, uint32_t dd, int cnt, uint32_t due)
 {
 #define FFS_PCASE(MM) \
-    case MM: return pair_round<MM, EMIT_B>(nB, SH, heap_a, heap_b, buf, prow_a, prow_b, mm, dd, cnt);
+    case MM: return pair_round<MM, EMIT_B>(nB, SH, heap_a, heap_b, buf, prow_a, prow_b, mm, dd, cnt, due);
     switch (Mp) {
         FFS_PCASE(1) FFS_PCASE(2) FFS_PCASE(3) FFS_PCASE(4) FFS_PCASE(5) FFS_PCASE(6) FFS_PCASE(7)
         FFS_PCASE(8) FFS_PCASE(9) FFS_PCASE(10) FFS_PCASE(11) FFS_PCASE(12) FFS_PCASE(13) FFS_PCASE(14)
         FFS_PCASE(15) FFS_PCASE(16)
-        default: return pair_round<kMaxM, EMIT_B>(nB, SH, heap_a, heap_b, buf, prow_a, prow_b, mm, dd, cnt);
+        default: return pair_round<kMaxM, EMIT_B>(nB, SH, heap_a, heap_b, buf, prow_a, prow_b, mm, dd, cnt, due);
     }
 #undef FFS_PCASE
 }
 
 // Stage-0 input keys of the genes [0, cnt) of a chunk, written to buf.
 __device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uint32_t n, uint32_t buf,
-                                              uint32_t stride, bool &bad)
+                                              uint32_t stride, uint32_t rel, uint32_t SH, bool &bad)
 {
     const int4 *g4 = reinterpret_cast<const int4 *>(genes);
     for (int i0 = 0; i0 < cnt; i0 += 8) {
@@ -632,7 +700,9 @@ __device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uin
                 uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
                 g = (uint32_t)(int32_t)(int16_t)g;
                 if (g >= n) { bad = true; g = 0; }
-                sts32(buf + (uint32_t)(i0 + h) * stride, (g + 1u) << 1);
+                uint32_t key = (g + 1u) << 1;
+                if (rel) key |= lds32(rel + (key << 1)) << SH;   // stage-1 ready time R_j
+                sts32(buf + (uint32_t)(i0 + h) * stride, key);
             }
         }
     }
@@ -645,7 +715,8 @@ __device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uin
 //   wst   : this warp's per-stage state, S entries (shared).
 // All lanes of a warp must call this together for the same instance (the
 // TMEM accesses are warp-collective).
-// Returns the makespan, or -1 if a gene is outside [0, n).
+// Returns the objective -- the makespan, plus WT x total tardiness when the
+// instance has due times -- or -1 if a gene is outside [0, n).
 __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, const int16_t *row,
                                                      uint32_t *region, int T, const uint16_t *ptab,
                                                      WarpStageState *wst)
@@ -657,6 +728,9 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     const uint32_t tab = tc::smem_u32(ptab);
     const uint32_t row_bytes = (uint32_t)table_row_halves(n) * 2u;
     const uint32_t nB = (uint32_t)n | (uint32_t)L.B << 16, SH = (uint32_t)L.SH;
+    // the objective's tables for the per-round calls (0: none)
+    const uint32_t obj = (L.rel_sa >> 2) | (L.due_sa >> 2) << 16;
+    uint32_t tard = 0;
     // Every buffer slot holds a valid key (or 0) before the read-ahead can
     // touch it: clear the buffer and its four spare slots.
     for (int w = 0; w < L.B + 4; ++w) sts32(buf + (uint32_t)w * stride, 0u);
@@ -684,10 +758,11 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
                         const uint32_t h = heap_handle(L, region_sa, T, s);
                         const uint32_t prow = tab + (uint32_t)s * row_bytes;
                         const uint32_t dc = (uint32_t)d0 | (uint32_t)cnt << 16, mf = (uint32_t)M;
-                        const uint2 o = (s == 0)
-                                            ? stage_round_dispatch<true, false>(M, nB, SH, h, buf, prow, row + d0, dc, mf)
-                                            : stage_round_dispatch<false, false>(M, nB, SH, h, buf, prow, nullptr, dc, mf);
+                        const uint4 o = (s == 0)
+                                            ? stage_round_dispatch<true, false>(M, nB, SH, h, buf, prow, row + d0, dc, mf, obj)
+                                            : stage_round_dispatch<false, false>(M, nB, SH, h, buf, prow, nullptr, dc, mf, obj);
                         last_key = o.y;
+                        tard += o.z;
                         if (o.x >> 24) bad = true;
                     }
                     __syncwarp();
@@ -704,20 +779,24 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
                 int w = 0, da1 = da0, fa1 = fa0, db1 = db0, fb1 = fb0;
                 const bool work = cnt > 0 || (da0 == n && fa0 < Ma) || (emit_b && db0 == n && fb0 < Mb);
                 if (work) {
-                    if (a == 0 && cnt > 0) genes_to_keys(row + da0, cnt, (uint32_t)n, buf, stride, bad);
+                    if (a == 0 && cnt > 0) genes_to_keys(row + da0, cnt, (uint32_t)n, buf, stride, L.rel_sa, SH, bad);
                     const int Mp = Ma > Mb ? Ma : Mb;
                     const uint32_t pa = tab + (uint32_t)a * row_bytes, pb = pa + row_bytes;
                     const uint32_t ha = heap_handle(L, region_sa, T, a), hb = heap_handle(L, region_sa, T, b);
                     const uint32_t mm = (uint32_t)Ma | (uint32_t)Mb << 8 | (uint32_t)fa0 << 16 | (uint32_t)fb0 << 24;
                     const uint32_t dd = (uint32_t)da0 | (uint32_t)db0 << 16;
-                    const uint4 o = emit_b ? pair_round_dispatch<true>(Mp, nB, SH, ha, hb, buf, pa, pb, mm, dd, cnt)
-                                           : pair_round_dispatch<false>(Mp, nB, SH, ha, hb, buf, pa, pb, mm, dd, cnt);
+                    const uint4 o = emit_b ? pair_round_dispatch<true>(Mp, nB, SH, ha, hb, buf, pa, pb, mm, dd, cnt, 0u)
+                                           : pair_round_dispatch<false>(Mp, nB, SH, ha, hb, buf, pa, pb, mm, dd, cnt,
+                                                                        L.due_sa);
                     w = (int)(o.x & 0xFFFFu);
                     fa1 = (int)((o.x >> 16) & 0xFFu);
                     fb1 = (int)(o.x >> 24);
                     da1 = (int)(o.y & 0xFFFFu);
                     db1 = (int)(o.y >> 16);
-                    if (!emit_b) last_key = o.z;
+                    if (!emit_b) {
+                        last_key = o.z;
+                        tard += o.w;
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -737,7 +816,7 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
         __syncwarp();
         if (bad) return -1;
         if (!L.single) last_key = heap_read1(heap_handle(L, region_sa, T, S - 1), L.M[S - 1] - 1, stride);
-        return (int32_t)(last_key >> L.SH);
+        return (int32_t)((last_key >> L.SH) + L.wt * tard);
     }
     int s_lo = 0;   // stages before s_lo have dispatched and emitted everything
     for (int round = 0; round < max_rounds; ++round) {
@@ -753,17 +832,21 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
                 const uint32_t prow = tab + (uint32_t)s * row_bytes;
                 const uint32_t dc = (uint32_t)d0 | (uint32_t)cnt << 16, mf = (uint32_t)M | (uint32_t)fl0 << 8;
                 const int16_t *g = row + d0;
-                uint2 o;
+                uint4 o;
                 if (last)
-                    o = (s == 0) ? stage_round_dispatch<true, false>(M, nB, SH, h, buf, prow, g, dc, mf)
-                                 : stage_round_dispatch<false, false>(M, nB, SH, h, buf, prow, nullptr, dc, mf);
+                    o = (s == 0) ? stage_round_dispatch<true, false>(M, nB, SH, h, buf, prow, g, dc, mf, obj)
+                                 : stage_round_dispatch<false, false>(M, nB, SH, h, buf, prow, nullptr, dc, mf, obj);
                 else
-                    o = (s == 0 && cnt > 0) ? stage_round_dispatch<true, true>(M, nB, SH, h, buf, prow, g, dc, mf)
-                                            : stage_round_dispatch<false, true>(M, nB, SH, h, buf, prow, nullptr, dc, mf);
+                    o = (s == 0 && cnt > 0) ? stage_round_dispatch<true, true>(M, nB, SH, h, buf, prow, g, dc, mf, obj)
+                                            : stage_round_dispatch<false, true>(M, nB, SH, h, buf, prow, nullptr, dc, mf,
+                                                                                obj);
                 w = (int)(o.x & 0xFFFFu);
                 fl = (int)((o.x >> 16) & 0xFFu);
                 if (o.x >> 24) bad = true;
-                if (last) last_key = o.y;
+                if (last) {
+                    last_key = o.y;
+                    tard += o.z;
+                }
             }
             const int d1 = d0 + cnt;
             __syncwarp();
@@ -780,7 +863,7 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
     __syncwarp();
     if (bad) return -1;
     if (!L.single) last_key = heap_read1(heap_handle(L, region_sa, T, S - 1), L.M[S - 1] - 1, stride);
-    return (int32_t)(last_key >> L.SH);
+    return (int32_t)((last_key >> L.SH) + L.wt * tard);
 }
 
 // Copy the instance's processing-time table (global, already laid out as

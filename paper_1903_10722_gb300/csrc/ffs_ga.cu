@@ -25,14 +25,17 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const int bits_per_warp = (L.n + 31) >> 5;
-    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
-    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
+    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp, L.obj_words);
+    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
     if (threadIdx.x == 0) {
         s_L = L;
         s_L.M = st;
         s_L.heap_off = st + L.S;
+        const uint32_t objt = tc::smem_u32(smem + map.tab + table_words(L.n, L.S));
+        s_L.rel_sa = L.has_rel ? objt : 0u;
+        s_L.due_sa = L.has_due ? objt + (uint32_t)L.obj_words * 2u : 0u;
     }
     __syncthreads();
     DecodeLayout &Ls = s_L;
@@ -265,14 +268,17 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
     const int bits_per_warp = (L.n + 31) >> 5;
-    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp);
-    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S));
+    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp, L.obj_words);
+    stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
     if (threadIdx.x == 0) {
         s_L = L;
         s_L.M = st;
         s_L.heap_off = st + L.S;
+        const uint32_t objt = tc::smem_u32(smem + map.tab + table_words(L.n, L.S));
+        s_L.rel_sa = L.has_rel ? objt : 0u;
+        s_L.due_sa = L.has_due ? objt + (uint32_t)L.obj_words * 2u : 0u;
     }
     __syncthreads();
     DecodeLayout &Ls = s_L;

@@ -36,7 +36,7 @@ struct Plan {
 
 // Shared-memory word offsets inside a decoding block.
 struct SmemMap {
-    int tab;       // processing-time table
+    int tab;       // processing-time table, then the objective's release / due tables
     int stage;     // [2S]: M_s, heap offset
     int warp;      // warp state, (T/32) * S * 2 words
     int bits;      // per-warp crossover bitmask, (T/32) * bits_per_warp words
@@ -49,11 +49,15 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 // table_row_halves(n) entries), rounded to 16 bytes.
 __host__ __device__ inline int table_words(int n, int S) { return round_up(S * table_row_halves(n) / 2, 4); }
 
-__host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_warp = 0)
+// Words of the objective's tables (release and due times of job j at entry
+// j + 1 of two uint32 arrays, entry 0 = 0), or 0 for the makespan alone.
+__host__ __device__ inline int objective_words(int n) { return 2 * round_up(n + 1, 4); }
+
+__host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_warp = 0, int obj_words = 0)
 {
     SmemMap m;
     m.tab = 0;
-    m.stage = table_words(n, S);
+    m.stage = table_words(n, S) + obj_words;
     m.warp = m.stage + round_up(2 * S, 4);
     m.bits = m.warp + round_up((T / 32) * S * 2, 4);
     m.region = m.bits + round_up((T / 32) * bits_per_warp, 4);
@@ -70,7 +74,12 @@ struct ffs_instance {
     std::vector<int32_t> M_eff;      // min(M_s, n)
     std::vector<int32_t> heap_off;   // prefix sums of M_eff
     int heap_words = 0;
-    uint32_t *d_tab = nullptr;       // uint16 [S][table_row_halves(n)] times, as words
+    uint32_t *d_tab = nullptr;       // uint16 [S][table_row_halves(n)] times, as words; then the
+                                     // objective's release and due tables (obj_words)
+    int obj_words = 0;               // objective_words(n) with release or due times, else 0
+    int has_rel = 0, has_due = 0;
+    int32_t wt = 0;                  // WT of the objective (0 without due times)
+    std::vector<int32_t> host_R, host_D;
     int32_t *d_stage = nullptr;      // [2S]: M_eff, heap_off
     int tab_words = 0;
     int num_sms = 0;
