@@ -584,6 +584,75 @@ def run_decode(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's Section 5 experiments on a synthetic Table 1 instance
+    (300 jobs x 4 stages x 2 machines, p ~ U[1,5], release and due times,
+    objective 100 * total tardiness + C_max): population 512, 2000
+    generations, 50 GA seeds.  Table 2 setup: the dual GA (16 x 16 cellular
+    island + 256-row pseudo island, penetration migration with theta = 1.00
+    every 500 generations) against a cellular GA (16 x 32 torus) and a pseudo
+    GA (512 rows) alone; Fig. 4 setup: the dual GA's final best for migration
+    gaps 10 .. 800.  One JSON line; the paper's own values come from an
+    unpublished instance and another genotype, so only the comparisons carry
+    over."""
+    import numpy as np
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    from ffs_workloads import make_paper_instance
+
+    torch.cuda.set_device(0)
+    spec = make_paper_instance(300, 4, 2, seed=1)
+    inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p, release=spec.release, due=spec.due, wt=spec.wt)
+    gens, runs = 2000, 50
+    seeds = list(range(7, 7 + runs))
+
+    def run(kind, seed, gap=500):
+        prm = ffs.ffs_params_default()
+        prm.seed = seed
+        prm.migration_mode = ffs.FFS_MIG_PENETRATION
+        prm.theta_num, prm.theta_den = 1, 1
+        prm.migration_gap = gap
+        if kind == "dual":
+            isl = ffs.Islands(inst, prm, 1, 16, 16, 1, 256)
+        elif kind == "cellular":
+            prm.migration_gap = 0
+            isl = ffs.Islands(inst, prm, 1, 16, 32, 0, 0)
+        else:
+            prm.migration_gap = 0
+            isl = ffs.Islands(inst, prm, 0, 0, 0, 1, 512)
+        ffs.ffs_island_step(isl, -1, gens)
+        best = ffs.ffs_islands_best(isl)[0]
+        decoded = ffs.ffs_islands_decoded(isl)
+        isl.close()
+        return int(best), int(decoded)
+
+    def summary(vals):
+        a = np.array(vals, dtype=np.float64)
+        return {"best": float(a.min()), "average": float(a.mean()), "variance": float(a.var(ddof=1)),
+                "runs": len(vals)}
+
+    table2, times = {}, {}
+    for kind in ("dual", "cellular", "pseudo"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = [run(kind, sd) for sd in seeds]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        table2[kind] = summary([r[0] for r in res])
+        times[kind] = {"s_per_run": dt / runs, "evals_per_s": sum(r[1] for r in res) / dt}
+    sweep = {}
+    for gap in (10, 50, 100, 200, 500, 800):
+        sweep[str(gap)] = summary([run("dual", sd, gap)[0] for sd in seeds])["average"]
+    line = {"metric": "best objective (100 x total tardiness + C_max) after 2000 generations",
+            "workload": "paper_obj_300x4", "lower_is_better": True,
+            "instance": "300 x 4 x 2, p ~ U[1,5], Table 1 release / due times, seed 1",
+            "population": 512, "generations": gens, "seeds": f"{seeds[0]}..{seeds[-1]}",
+            "table2": table2, "time": times, "migration_gap_sweep_average": sweep}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def launches_per_generation(w) -> int:
     """Kernels of one generation: pseudo breed, the fused decode launch of
     all cellular cells and pseudo children, pseudo replace, the generation
@@ -618,6 +687,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "decode_500x20":
         return run_decode(args)
+    if args.workload == "paper_obj_300x4":
+        return run_paper(args)
     return run_ours(args)
 
 
