@@ -292,26 +292,25 @@ def run_ours(args):
                                            "min3_max3", "add_max", "min_max+imad", "min_max+fmnmx"))}
 
     # ---- e2e: the same steps with populations from / to pinned host memory ----
-    # host rows with the library's row stride: each copy is one contiguous transfer
-    host_pops = [torch.empty((n_i, isl.ld), dtype=torch.int16).pin_memory() for n_i in isl.sizes]
-    host_ms = [torch.empty(n_i, dtype=torch.int32).pin_memory() for n_i in isl.sizes]
-    for i in range(isl.n_islands):
-        ffs.ffs_islands_get(isl, i, host_pops[i], isl.ld, host_ms[i])
+    # all islands' rows in one host buffer with the library's row stride: each
+    # step is one set_all (H2D), the generation, one get_all (D2H) and a sync
+    total_rows = sum(isl.sizes)
+    host_pop = torch.empty((total_rows, isl.ld), dtype=torch.int16).pin_memory()
+    host_ms = torch.empty(total_rows, dtype=torch.int32).pin_memory()
+    ffs.ffs_islands_get_all(isl, host_pop, isl.ld, host_ms)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 3))
-    h2d = sum(p.numel() * 2 for p in host_pops)
-    d2h = h2d + sum(m.numel() * 4 for m in host_ms)
+    e2e_steps = max(3, min(args.steps, 10))
+    h2d = host_pop.numel() * 2
+    d2h = h2d + host_ms.numel() * 4
     e_d0 = ffs.ffs_islands_decoded(isl)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for i in range(isl.n_islands):
-            ffs.ffs_islands_set(isl, i, host_pops[i], isl.ld, None)
+        ffs.ffs_islands_set_all(isl, host_pop, isl.ld, None)
         ffs.ffs_island_step(isl, -1, 1)
-        for i in range(isl.n_islands):
-            ffs.ffs_islands_get(isl, i, host_pops[i], isl.ld, host_ms[i])
+        ffs.ffs_islands_get_all(isl, host_pop, isl.ld, host_ms)
         torch.cuda.synchronize()
     e2e_time = time.perf_counter() - t0
     e2e_evals = ffs.ffs_islands_decoded(isl) - e_d0

@@ -293,6 +293,12 @@ int ffs_islands_get(const ffs_islands *isl, int32_t island, int16_t *pop, int32_
                     int32_t *makespan, ffs_stream stream);
 int ffs_islands_set(ffs_islands *isl, int32_t island, const int16_t *pop, int32_t ld_in,
                     const int32_t *makespan, ffs_stream stream);
+/* The same for every island in one call: the islands' rows back to back in
+ * ring order (island i from row sum_{k<i} size_k), makespans likewise. */
+int ffs_islands_get_all(const ffs_islands *isl, int16_t *pop, int32_t ld_out, int32_t *makespan,
+                        ffs_stream stream);
+int ffs_islands_set_all(ffs_islands *isl, const int16_t *pop, int32_t ld_in, const int32_t *makespan,
+                        ffs_stream stream);
 
 /* Best makespan over all islands and where it is (lowest island, then
  * lowest row on ties).  Synchronises `stream`.  Outputs are host pointers. */

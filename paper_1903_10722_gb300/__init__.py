@@ -75,6 +75,8 @@ _SIGS = [
     ("ffs_migrate", _i32, [_vp, _i32, _vp]),
     ("ffs_islands_get", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
     ("ffs_islands_set", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
+    ("ffs_islands_get_all", _i32, [_vp, _vp, _i32, _vp, _vp]),
+    ("ffs_islands_set_all", _i32, [_vp, _vp, _i32, _vp, _vp]),
     ("ffs_islands_best", _i32, [_vp, _vp, _vp, _vp, _vp]),
     ("ffs_islands_decoded", _i32, [_vp, _vp, _vp]),
     ("ffs_batch_create", _i32, [_i32, _vp, _vp, _vp, _vp, ctypes.POINTER(ffs_params), _i32, _i32, _vp,
@@ -340,6 +342,14 @@ def ffs_islands_get(isl: Islands, island: int, pop, ld_out: int, makespan, strea
 
 def ffs_islands_set(isl: Islands, island: int, pop, ld_in: int, makespan, stream=None):
     _check(load().ffs_islands_set(isl.handle, island, _ptr(pop), ld_in, _ptr(makespan), _stream(stream)))
+
+
+def ffs_islands_get_all(isl: Islands, pop, ld_out: int, makespan, stream=None):
+    _check(load().ffs_islands_get_all(isl.handle, _ptr(pop), ld_out, _ptr(makespan), _stream(stream)))
+
+
+def ffs_islands_set_all(isl: Islands, pop, ld_in: int, makespan, stream=None):
+    _check(load().ffs_islands_set_all(isl.handle, _ptr(pop), ld_in, _ptr(makespan), _stream(stream)))
 
 
 def ffs_islands_best(isl: Islands, stream=None):

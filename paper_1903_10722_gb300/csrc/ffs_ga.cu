@@ -1236,6 +1236,34 @@ int ffs_islands_set(ffs_islands *S, int32_t island, const int16_t *pop, int32_t 
     return FFS_OK;
 }
 
+int ffs_islands_get_all(const ffs_islands *S, int16_t *pop, int32_t ld_out, int32_t *ms, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    int64_t row = 0;
+    for (int i = 0; i < S->I; ++i) {
+        const int rc = ffs_islands_get(S, i, pop ? pop + row * ld_out : nullptr, ld_out, ms ? ms + row : nullptr,
+                                       stream);
+        if (rc) return rc;
+        row += S->size[i];
+    }
+    return FFS_OK;
+}
+
+int ffs_islands_set_all(ffs_islands *S, const int16_t *pop, int32_t ld_in, const int32_t *ms, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    int64_t row = 0;
+    for (int i = 0; i < S->I; ++i) {
+        const int rc = ffs_islands_set(S, i, pop ? pop + row * ld_in : nullptr, ld_in, ms ? ms + row : nullptr,
+                                       stream);
+        if (rc) return rc;
+        row += S->size[i];
+    }
+    return FFS_OK;
+}
+
 int ffs_islands_best(const ffs_islands *S, int32_t *best_ms, int32_t *best_island, int32_t *best_row,
                      ffs_stream stream)
 {

@@ -265,3 +265,33 @@ def test_scale_500x20_sampled_generation(gpu):
             for t in range(2):
                 assert after[i][0][2 * k + t].tolist() == want[t][0].tolist()
                 assert after[i][1][2 * k + t] == want[t][1]
+
+
+def test_get_set_all_islands(gpu):
+    """ffs_islands_get_all / set_all move every island's rows in ring order in one call."""
+    spec = make_instance(24, 3, 2, 3, seed=2)
+    o, g = _pair(spec, gpu)
+    prm, _ = _params(gpu, mode=0, gap=0)
+    isl = gpu.Islands(g, prm, 2, 4, 4, 1, 10)
+    gpu.ffs_island_step(isl, -1, 2)
+    total = sum(isl.sizes)
+    pop = torch.zeros((total, isl.ld), dtype=torch.int16)
+    ms = torch.zeros(total, dtype=torch.int32)
+    gpu.ffs_islands_get_all(isl, pop, isl.ld, ms)
+    torch.cuda.synchronize()
+    row = 0
+    for i in range(isl.n_islands):
+        p_i, m_i = gpu.island_tensors(isl, i)
+        torch.cuda.synchronize()
+        N = isl.sizes[i]
+        assert np.array_equal(pop[row:row + N, :spec.n].numpy(), p_i.cpu().numpy())
+        assert np.array_equal(ms[row:row + N].numpy(), m_i.cpu().numpy())
+        row += N
+    rev = torch.flip(pop, dims=[0]).contiguous()
+    rms = torch.flip(ms, dims=[0]).contiguous()
+    gpu.ffs_islands_set_all(isl, rev, isl.ld, rms)
+    back = torch.zeros_like(pop)
+    bms = torch.zeros_like(ms)
+    gpu.ffs_islands_get_all(isl, back, isl.ld, bms)
+    torch.cuda.synchronize()
+    assert torch.equal(back, rev) and torch.equal(bms, rms)
