@@ -59,6 +59,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(values, dist, device: str = "cuda"):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    rank's times); identity without a process group."""
+    if not dist:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, max_time_s: float) -> float:
+    """Units processed by all ranks (each processes units_per_rank) / the slowest rank's time."""
+    return units_per_rank * world_size / max_time_s
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -316,13 +332,8 @@ def run_ours(args):
     e2e_evals = ffs.ffs_islands_decoded(isl) - e_d0
 
     # ---- reduce over ranks (max time) ----
-    value_time = elapsed
-    if dist:
-        t = torch.tensor([elapsed, e2e_time], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value_time, e2e_time = float(t[0]), float(t[1])
-    total_evals = evals * ws
-    value = total_evals / value_time
+    value_time, e2e_time = max_over_ranks([elapsed, e2e_time], dist)
+    value = whole_job_rate(evals, ws, value_time)
 
     peaks, peak_kind = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MHZ))
@@ -413,10 +424,7 @@ def run_batch(args):
     elapsed = e0.elapsed_time(e1) / 1000.0
     clock_info = clocks.stop()
     evals = ffs.ffs_batch_decoded(b) - d0
-    if dist:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t[0])
+    elapsed = max_over_ranks([elapsed], dist)[0]
     cells = w["rows"] * w["cols"]
     ops_gen = sum(cells * ops_per_eval(s.n, s.M) for s in specs)
     peaks, peak_kind = _peaks()
