@@ -355,8 +355,8 @@ def run_ours(args):
         "gpu_launches": args.steps * launches_per_generation(w),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": "k_step_decode (all cellular cells: tournament + OX + swap + decode + replace; "
-                               "all pseudo children: decode), timed with its pseudo breed and replace launches",
+                     "kernel": "k_step_decode (all cellular children: decode + replace; all pseudo children: decode), "
+                               "timed with the cellular and pseudo breed and the pseudo replace launches",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": decodes_per_launch * ops_eval,
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
                      "launch_shape": ffs.ffs_decode_plan(inst, 2, prm.decode_chunk, prm.block_threads,
@@ -661,10 +661,11 @@ def run_paper(args):
 
 
 def launches_per_generation(w) -> int:
-    """Kernels of one generation: pseudo breed, the fused decode launch of
-    all cellular cells and pseudo children, pseudo replace, the generation
-    advance, and when migrating the ranking plus the copy kernel."""
-    n = 4
+    """Kernels of one generation: cellular breed, pseudo breed, the fused
+    decode launch of all cellular children and pseudo children, pseudo
+    replace, the generation advance, and when migrating the ranking plus the
+    copy kernel."""
+    n = 5
     if w.get("gap", 0) == 1 and w["n_cellular"] + w["n_pseudo"] > 1:
         n += 2
     return n

@@ -215,6 +215,40 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
     warp_copy_rows(valid, src[1], pout + (int64_t)(2 * k + 1) * ld, ld);
 }
 
+// The breeding half of a cellular generation for every cell of a batch of
+// cellular islands (children into the output rows), warp per 32 cells, at
+// high occupancy: its order crossover waits on memory, which many warps hide.
+__global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int rows,
+                                                        int cols, int n, int ld)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int bits_per_warp = (n + 31) >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *wbits = smem + warp * bits_per_warp;
+    const int cells = rows * cols, total = cells * batch.count;
+    const int base = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+    if (base >= total) return;   // whole warps leave together
+    const int gc = base + lane;
+    const bool valid = gc < total;
+    const int gq = valid ? gc : total - 1;
+    const int bi = gq / cells, c = gq - bi * cells;
+    cellular_warp_breed(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits);
+}
+
+static int launch_cellular_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows,
+                                 int cols, int ld, cudaStream_t st)
+{
+    const int total = rows * cols * batch.count;
+    const int T = 256;
+    const size_t smem = (size_t)(T / 32) * ((inst->n + 31) / 32) * 4;
+    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int warps = (total + 31) / 32;
+    k_cellular_breed<<<(warps + T / 32 - 1) / (T / 32), T, smem, st>>>(g, batch, rows, cols, inst->n, ld);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
 static int launch_pseudo_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
                                int ld, const PseudoScratch &s, cudaStream_t st)
 {
@@ -253,11 +287,13 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
 }
 
 // ---------------------------------------------------------------------------
-// One launch for the decoding work of a generation: the fused cellular
-// cells of all cellular islands and the pseudo islands' compacted children.
-// Warps take 32-unit work items from a device counter (cellular items first,
-// they carry the crossover too), so the two kinds share one launch and its
-// last wave instead of each leaving a partly idle wave.
+// One launch for the decoding work of a generation: the children of all
+// cellular islands (bred by k_cellular_breed into the output rows; decoded
+// here, then replace-if-better) and the pseudo islands' compacted children.
+// Warps take 32-unit work items from a device counter (cellular items first:
+// they also replace and copy rows, and the heavier items go first), so the
+// two kinds share one launch and its last wave instead of each leaving a
+// partly idle wave.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint32_t *__restrict__ tab_g,
                                                      const int32_t *__restrict__ stage_g, GaScalars g,
@@ -267,8 +303,7 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
-    const int bits_per_warp = (L.n + 31) >> 5;
-    const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp, L.obj_words);
+    const SmemMap map = smem_map(L.n, L.S, T, 0, L.obj_words);   // the crossover ran in k_cellular_breed
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
@@ -285,7 +320,6 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
     decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
-    uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
     uint32_t *region = smem + map.region + threadIdx.x;
     const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
     const int cells = rows * cols;
@@ -304,7 +338,7 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
             const bool valid = gc < C;
             const int gq = valid ? gc : C - 1;
             const int bi = gq / cells, c = gq - bi * cells;
-            cellular_warp_cells(Ls, g, cb.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
+            cellular_warp_decode(Ls, g, cb.ref[bi], c, valid, ld, region, T, tab, wst);
         } else {
             const int k = u0 - C32 + lane;
             const bool valid = k < P;
@@ -326,11 +360,11 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
                              unsigned long long *decoded, cudaStream_t st)
 {
     PseudoScratch s = carve(scratch, psize, ld, pb.count);
-    int rc = launch_pseudo_breed(inst, g, pb, psize, ld, s, st);
+    int rc = launch_cellular_breed(inst, g, cb, rows, cols, ld, st);
     if (rc) return rc;
+    if ((rc = launch_pseudo_breed(inst, g, pb, psize, ld, s, st))) return rc;
     Plan p;
-    const int bits_per_warp = (inst->n + 31) / 32;
-    if ((rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_req, bits_per_warp, &p, g.variant))) return rc;
+    if ((rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_req, 0, &p, g.variant))) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_step_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int64_t units = (int64_t)rows * cols * cb.count + (int64_t)psize * pb.count;
     const int grid = grid_for(inst, p, units);

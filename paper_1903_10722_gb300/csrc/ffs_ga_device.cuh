@@ -105,17 +105,14 @@ __device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, 
 }
 
 
-// One cellular generation for the cell `c` of each lane (lanes with !valid
-// only keep the warp in lock step): draws, two binary tournaments over the
-// von Neumann neighbourhood (previous generation's makespans), order
-// crossover, swap mutation, decoding, replace-if-better.  The child is built
-// in the cell's output row.
-__device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, const GaScalars &g, const IslandRef &ref,
-                                                    int c, bool valid, int rows, int cols, int ld, uint32_t *wbits,
-                                                    uint32_t *region, int T, const uint16_t *tab,
-                                                    WarpStageState *wst)
+// The breeding half of a cellular generation for the cell `c` of each lane
+// (lanes with !valid only keep the warp in lock step): draws, two binary
+// tournaments over the von Neumann neighbourhood (previous generation's
+// makespans), order crossover, swap mutation.  The child is built in the
+// cell's output row.
+__device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const GaScalars &g, int n, int c, bool valid,
+                                                    int rows, int cols, int ld, uint32_t *wbits)
 {
-    const int n = Ls.n;
     const int16_t *pin;
     const int32_t *msin;
     int16_t *pout;
@@ -163,8 +160,22 @@ __device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, cons
         child[j] = t;
     }
     __syncwarp();
+}
+
+// The other half: decode the child in the cell's output row and replace the
+// cell iff the child is better (else the output row takes the old cell back).
+__device__ __forceinline__ void cellular_warp_decode(const DecodeLayout &Ls, const GaScalars &g, const IslandRef &ref,
+                                                     int c, bool valid, int ld, uint32_t *region, int T,
+                                                     const uint16_t *tab, WarpStageState *wst)
+{
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(ref, pin, msin, pout, msout, gen);
     // lanes past the end decode a row of their island in lock step; nothing is written
-    const int16_t *drow = valid ? job.child : pin + (int64_t)c * ld;
+    const int16_t *drow = valid ? pout + (int64_t)c * ld : pin + (int64_t)c * ld;
     const int32_t ms = decode_chromosome(Ls, drow, region, T, tab, wst);
     bool keep_old = false;
     if (valid) {
@@ -174,6 +185,17 @@ __device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, cons
         keep_old = !better;
     }
     warp_copy_rows(keep_old, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
+}
+
+// One cellular generation for the cell `c` of each lane: breeding, then
+// decoding and replacement (see the two halves above).
+__device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, const GaScalars &g, const IslandRef &ref,
+                                                    int c, bool valid, int rows, int cols, int ld, uint32_t *wbits,
+                                                    uint32_t *region, int T, const uint16_t *tab,
+                                                    WarpStageState *wst)
+{
+    cellular_warp_breed(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
+    cellular_warp_decode(Ls, g, ref, c, valid, ld, region, T, tab, wst);
 }
 
 }  // namespace fgpu
