@@ -112,18 +112,29 @@ static PseudoScratch carve(void *base, int size, int ld, int islands)
     return s;
 }
 
-// Thread per pair: crossover decision, compacted child slots; the warp then
-// builds the two children of each crossing pair cooperatively.
+// Pairs per warp of k_pseudo_breed / k_pseudo_replace, and cells per warp
+// of k_cellular_breed: the warp builds (copies) its rows one after the other,
+// so few rows per warp and many warps hide the memory latency of each.
+constexpr int kPairsPerWarp = 4;
+constexpr int kCellsPerWarp = 8;
+
+// Lane l < kPairsPerWarp of a warp takes one pair: crossover decision,
+// compacted child slots; the warp then builds the two children of each
+// crossing pair cooperatively.
 __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n, int ld,
                                PseudoScratch s)
 {
     extern __shared__ uint32_t bits_smem[];
-    const int T = blockDim.x;
     const int pairs = size / 2;
     const int total = pairs * batch.count;
-    const int gp = blockIdx.x * T + threadIdx.x;
-    const int bi = (gp < total ? gp : total - 1) / pairs;
-    const int k = (gp < total ? gp : total - 1) - bi * pairs;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw * kPairsPerWarp >= total) return;   // whole warps leave together
+    const int gp = gw * kPairsPerWarp + lane;
+    const bool mine = lane < kPairsPerWarp && gp < total;
+    const int gq = mine ? gp : gw * kPairsPerWarp;
+    const int bi = gq / pairs;
+    const int k = gq - bi * pairs;
     const IslandRef &ref = batch.ref[bi];
     const int16_t *pin;
     const int32_t *msin;
@@ -133,17 +144,16 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     resolve(ref, pin, msin, pout, msout, gen);
     bool cross = false;
     U4 d{0, 0, 0, 0};
-    if (gp < total) {
+    if (mine) {
         d = draw_block(g.seed, kPurposePseudo, ref.island, gen, (uint32_t)k, 0u);
         cross = fires(d.x, g.pseudo_pc);
     }
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, cross);
-    const int lane = threadIdx.x & 31;
     int base = 0;
     if (lane == 0 && mask) base = atomicAdd(s.count, 2 * __popc(mask));
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     const int slot = base + 2 * __popc(mask & ((1u << lane) - 1u));
-    if (gp < total) s.pair_slot[gp] = cross ? slot : -1;
+    if (mine) s.pair_slot[gp] = cross ? slot : -1;
     const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
     const int16_t *b = a + ld;
@@ -163,16 +173,19 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     warp_build_children(job, n, ld, bits);
 }
 
-// Thread per pair: the pair keeps the two best of (c1, c2, a, b), or the
-// children, or itself when it did not cross.
+// Lane l < kPairsPerWarp of a warp takes one pair: it keeps the two best of
+// (c1, c2, a, b), or the children, or itself when it did not cross.
 __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int ld,
                                  PseudoScratch s)
 {
     const int pairs = size / 2;
     const int total = pairs * batch.count;
-    const int gp = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = gp < total;
-    const int gq = valid ? gp : total - 1;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw * kPairsPerWarp >= total) return;   // whole warps leave together
+    const int gp = gw * kPairsPerWarp + lane;
+    const bool valid = lane < kPairsPerWarp && gp < total;
+    const int gq = valid ? gp : gw * kPairsPerWarp;
     const int bi = gq / pairs, k = gq - bi * pairs;
     const int16_t *pin;
     const int32_t *msin;
@@ -216,8 +229,9 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
 }
 
 // The breeding half of a cellular generation for every cell of a batch of
-// cellular islands (children into the output rows), warp per 32 cells, at
-// high occupancy: its order crossover waits on memory, which many warps hide.
+// cellular islands (children into the output rows), kCellsPerWarp cells per
+// warp, at high occupancy: its order crossover waits on memory, which many
+// warps hide.
 __global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int rows,
                                                         int cols, int n, int ld)
 {
@@ -226,11 +240,11 @@ __global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __gri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *wbits = smem + warp * bits_per_warp;
     const int cells = rows * cols, total = cells * batch.count;
-    const int base = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+    const int base = (blockIdx.x * (blockDim.x >> 5) + warp) * kCellsPerWarp;
     if (base >= total) return;   // whole warps leave together
     const int gc = base + lane;
-    const bool valid = gc < total;
-    const int gq = valid ? gc : total - 1;
+    const bool valid = lane < kCellsPerWarp && gc < total;
+    const int gq = valid ? gc : base;
     const int bi = gq / cells, c = gq - bi * cells;
     cellular_warp_breed(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits);
 }
@@ -243,10 +257,17 @@ static int launch_cellular_breed(const ffs_instance *inst, const GaScalars &g, c
     const size_t smem = (size_t)(T / 32) * ((inst->n + 31) / 32) * 4;
     if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int warps = (total + 31) / 32;
+    const int warps = (total + kCellsPerWarp - 1) / kCellsPerWarp;
     k_cellular_breed<<<(warps + T / 32 - 1) / (T / 32), T, smem, st>>>(g, batch, rows, cols, inst->n, ld);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
+}
+
+// Blocks of T threads for kPairsPerWarp pairs per warp.
+static int pair_blocks(int pairs, int T)
+{
+    const long long warps = (pairs + kPairsPerWarp - 1) / kPairsPerWarp;
+    return (int)((warps * 32 + T - 1) / T);
 }
 
 static int launch_pseudo_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
@@ -259,7 +280,7 @@ static int launch_pseudo_breed(const ffs_instance *inst, const GaScalars &g, con
     const size_t smem = (size_t)(T / 32) * words * 4;
     if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, batch, size, inst->n, ld, s);
+    k_pseudo_breed<<<pair_blocks(pairs, T), T, smem, st>>>(g, batch, size, inst->n, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -276,12 +297,12 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
     const size_t smem = (size_t)(T / 32) * words * 4;
     if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_pseudo_breed<<<(pairs + T - 1) / T, T, smem, st>>>(g, batch, size, inst->n, ld, s);
+    k_pseudo_breed<<<pair_blocks(pairs, T), T, smem, st>>>(g, batch, size, inst->n, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
     int rc = launch_eval(inst, s.children, 2 * (int64_t)pairs, ld, s.child_ms, s.count, B_req, T_req, decoded, st,
                          g.variant);
     if (rc) return rc;
-    k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, batch, size, ld, s);
+    k_pseudo_replace<<<pair_blocks(pairs, 128), 128, 0, st>>>(g, batch, size, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -371,14 +392,17 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
     k_step_decode<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, cb, rows, cols, ld, s, decoded);
     FFS_CUDA_TRY(cudaGetLastError());
     const int pairs = psize / 2 * pb.count;
-    k_pseudo_replace<<<(pairs + 127) / 128, 128, 0, st>>>(g, pb, psize, ld, s);
+    k_pseudo_replace<<<pair_blocks(pairs, 128), 128, 0, st>>>(g, pb, psize, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Migration.  Islands are ranked by (makespan, row) with a bitonic sort in
-// shared memory (one block per island), then rows are copied warp by warp.
+// Migration.  Islands are ranked by (makespan, row): blocks sort chunks of
+// 2048 keys (bitonic network in registers, shuffles and shared memory), then
+// every key's rank in its island is its position in its chunk plus the keys
+// below it in the island's other chunks (binary search); rows are then
+// copied warp by warp.
 // ---------------------------------------------------------------------------
 struct IslandDesc {
     int16_t *pop[2];
@@ -388,6 +412,7 @@ struct IslandDesc {
     int32_t kind;
     int32_t k_ring;    // rows sent to the next island by ring migration
     int32_t ring_off;  // prefix sum of k_ring
+    int32_t row_off;   // prefix sum of N (the island's keys in the ranking scratch)
 };
 
 constexpr int kMaxMigrationRows = 16384;
@@ -401,32 +426,118 @@ __device__ __forceinline__ bool migration_due(const int32_t *gate, int gap)
     return gap > 0 && g > 0 && (g % gap) == 0;
 }
 
-__global__ void __launch_bounds__(1024) k_rank(const IslandDesc *desc, const int32_t *cur, const int32_t *gate,
-                                               int gap)
+// Keys are (makespan << 32 | row), unique within an island.  A chunk of
+// kRankChunk keys is sorted by one block of kRankChunk / 16 threads; a thread
+// holds 16 consecutive keys e = 16 t + r in registers.  In shared memory key
+// e sits at slot e + e / 16 (one pad slot per 16), so a thread's 16 keys load
+// and store without bank conflicts.
+constexpr int kRankChunk = 2048;
+__device__ __forceinline__ int rank_slot(int e) { return e + (e >> 4); }
+
+// One compare-exchange step of distance J < 16 inside a thread's registers.
+template <int J>
+__device__ __forceinline__ void rank_reg_step(unsigned long long (&x)[16], int e0, int k)
+{
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        if ((r & J) == 0) {
+            const unsigned long long a = x[r], b = x[r | J];
+            const bool sw = (a > b) == (((e0 + r) & k) == 0);
+            x[r] = sw ? b : a;
+            x[r | J] = sw ? a : b;
+        }
+    }
+}
+
+// Block (chunk, island): sort keys [chunk * kRankChunk, ...) of the island
+// into the scratch.  For each merge size k of the bitonic network the steps
+// of distance j >= 512 run in shared memory, 16 <= j < 512 across the warp by
+// shuffles (the partner of key 16 t + r is key 16 (t ^ j / 16) + r), j < 16
+// in registers.  Missing keys are padded with ~0 (they sort last).
+__global__ void __launch_bounds__(kRankChunk / 16) k_rank_chunks(const IslandDesc *desc, const int32_t *cur,
+                                                                 const int32_t *gate, int gap,
+                                                                 unsigned long long *scratch)
 {
     if (!migration_due(gate, gap)) return;
-    extern __shared__ unsigned long long keys[];
-    const IslandDesc d = desc[blockIdx.x];
-    const int32_t *ms = d.ms[cur[blockIdx.x]];
-    int npad = 1;
-    while (npad < d.N) npad <<= 1;
-    for (int t = threadIdx.x; t < npad; t += blockDim.x)
-        keys[t] = t < d.N ? ((unsigned long long)(uint32_t)ms[t] << 32) | (uint32_t)t : ~0ull;
+    __shared__ unsigned long long keys[kRankChunk + kRankChunk / 16];
+    const IslandDesc d = desc[blockIdx.y];
+    const int c0 = blockIdx.x * kRankChunk;
+    if (c0 >= d.N) return;   // the whole block
+    const int len = min(kRankChunk, d.N - c0);
+    const int32_t *ms = cur[blockIdx.y] ? d.ms[1] : d.ms[0];
+    for (int e = threadIdx.x; e < kRankChunk; e += blockDim.x)
+        keys[rank_slot(e)] = e < len ? ((unsigned long long)(uint32_t)ms[c0 + e] << 32) | (uint32_t)(c0 + e) : ~0ull;
     __syncthreads();
-    for (int k = 2; k <= npad; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < npad; t += blockDim.x) {
-                const int o = t ^ j;
-                if (o > t) {
-                    const unsigned long long x = keys[t], y = keys[o];
-                    const bool up = (t & k) == 0;
-                    if ((x > y) == up) { keys[t] = y; keys[o] = x; }
+    const int t = threadIdx.x, e0 = 16 * t;
+    for (int k = 2; k <= kRankChunk; k <<= 1) {
+        int j = k >> 1;
+        for (; j >= 512; j >>= 1) {
+            for (int e = threadIdx.x; e < kRankChunk; e += blockDim.x) {
+                const int o = e ^ j;
+                if (o > e) {
+                    const unsigned long long x = keys[rank_slot(e)], y = keys[rank_slot(o)];
+                    if ((x > y) == ((e & k) == 0)) {
+                        keys[rank_slot(e)] = y;
+                        keys[rank_slot(o)] = x;
+                    }
                 }
             }
             __syncthreads();
         }
+        unsigned long long x[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = keys[rank_slot(e0 + r)];
+        for (; j >= 16; j >>= 1) {
+            const int lm = j >> 4;
+            const bool lower = (t & lm) == 0;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, x[r], lm);
+                const bool keep_min = lower == (((e0 + r) & k) == 0);
+                x[r] = keep_min ? (x[r] < y ? x[r] : y) : (x[r] < y ? y : x[r]);
+            }
+        }
+        if (j >= 8) rank_reg_step<8>(x, e0, k);
+        if (j >= 4) rank_reg_step<4>(x, e0, k);
+        if (j >= 2) rank_reg_step<2>(x, e0, k);
+        rank_reg_step<1>(x, e0, k);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) keys[rank_slot(e0 + r)] = x[r];
+        __syncthreads();
     }
-    for (int t = threadIdx.x; t < d.N; t += blockDim.x) d.order[t] = (int32_t)(keys[t] & 0xFFFFFFFFu);
+    unsigned long long *out = scratch + d.row_off + c0;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) out[e] = keys[rank_slot(e)];
+}
+
+// Thread per key: its rank in the island = its position in its sorted chunk
+// + the keys below it in each other chunk (lower bound by binary search);
+// order[rank] = its row.  Keys are unique, so the ranks are a permutation.
+__global__ void k_rank_merge(const IslandDesc *desc, int I, const int32_t *gate, int gap,
+                             const unsigned long long *scratch, int total_rows)
+{
+    if (!migration_due(gate, gap)) return;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total_rows) return;
+    int i = 0;
+    while (i + 1 < I && desc[i + 1].row_off <= gid) ++i;
+    const IslandDesc &d = desc[i];
+    const unsigned long long *base = scratch + d.row_off;
+    const int e = gid - d.row_off;
+    const unsigned long long key = base[e];
+    const int c = e / kRankChunk;
+    int rank = e - c * kRankChunk;
+    for (int c2 = 0; c2 * kRankChunk < d.N; ++c2) {
+        if (c2 == c) continue;
+        const unsigned long long *a = base + c2 * kRankChunk;
+        int lo = 0, hi = min(kRankChunk, d.N - c2 * kRankChunk);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        rank += lo;
+    }
+    d.order[rank] = (int32_t)(key & 0xFFFFFFFFu);
 }
 
 // One warp per migrated row: island i's t-th best onto island (i+1)'s t-th worst.
@@ -538,6 +649,8 @@ struct ffs_islands {
     std::vector<IslandDesc> desc;
     IslandDesc *d_desc = nullptr;
     int32_t *d_cur = nullptr, *d_gen = nullptr, *d_counts = nullptr;
+    unsigned long long *d_rank_keys = nullptr;   // [total_rows] sorted chunks of the ranking
+    int total_rows = 0;
     void *d_scratch = nullptr;        // pseudo scratch (shared by the pseudo islands)
     unsigned long long *d_decoded = nullptr;
     int ring_rows = 0, max_N = 0, min_pair_rows = 0;
@@ -619,11 +732,11 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
         return set_error(FFS_EUNSUPPORTED, "migration ranks islands of at most %d rows", kMaxMigrationRows);
     const int32_t *gate = gated ? S->d_gen : nullptr;
     const int gap = S->prm.migration_gap;
-    int npad = 1;
-    while (npad < S->max_N) npad <<= 1;
-    const size_t smem = (size_t)npad * 8;
-    FFS_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rank<<<S->I, 1024, smem, st>>>(S->d_desc, S->d_cur, gate, gap);
+    k_rank_chunks<<<dim3((S->max_N + kRankChunk - 1) / kRankChunk, S->I), kRankChunk / 16, 0, st>>>(
+        S->d_desc, S->d_cur, gate, gap, S->d_rank_keys);
+    FFS_CUDA_TRY(cudaGetLastError());
+    k_rank_merge<<<(S->total_rows + 255) / 256, 256, 0, st>>>(S->d_desc, S->I, gate, gap, S->d_rank_keys,
+                                                              S->total_rows);
     FFS_CUDA_TRY(cudaGetLastError());
     if (mode == FFS_MIG_RING) {
         const int warps = S->ring_rows;
@@ -830,12 +943,15 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
         return p;
     };
     int ring_off = 0, max_pseudo = 0;
+    S->total_rows = 0;
     for (int i = 0; i < S->I; ++i) {
         const int N = S->size[i];
         S->max_N = std::max(S->max_N, N);
         IslandDesc &d = S->desc[i];
         memset(&d, 0, sizeof(d));
         d.N = N;
+        d.row_off = S->total_rows;
+        S->total_rows += N;
         d.kind = S->kind[i];
         for (int b = 0; b < 2; ++b) {
             d.pop[b] = (int16_t *)alloc((size_t)N * S->ld * 2);
@@ -873,11 +989,13 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
     S->d_gen = (int32_t *)alloc(4 * S->I);
     S->d_counts = (int32_t *)alloc(4 * (S->I / 2 + 1));
     S->d_decoded = (unsigned long long *)alloc(8);
+    S->d_rank_keys = (unsigned long long *)alloc((size_t)S->total_rows * 8);
     int n_pseudo_islands = 0;
     for (int i = 0; i < S->I; ++i) n_pseudo_islands += S->kind[i] == 1;
     if (max_pseudo > 0)
         S->d_scratch = alloc((size_t)pseudo_scratch_bytes(max_pseudo, S->ld, std::min(n_pseudo_islands, kMaxBatch)));
-    if (!S->d_desc || !S->d_cur || !S->d_gen || !S->d_counts || !S->d_decoded || (max_pseudo > 0 && !S->d_scratch)) {
+    if (!S->d_desc || !S->d_cur || !S->d_gen || !S->d_counts || !S->d_decoded || !S->d_rank_keys ||
+        (max_pseudo > 0 && !S->d_scratch)) {
         islands_free(S);
         return set_error(FFS_ENOMEM, "island state");
     }

@@ -89,17 +89,37 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
     }
 }
 
-// Warp-cooperative row copies: lane j's (src, dst) pair when `active`.
+// Warp-cooperative row copies: lane j's (src, dst) pair when `active`.  Four
+// rows at a time, their loads issued before their stores (no destination row
+// may overlap a source row of the same call).
 __device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, int16_t *dst, int ld)
 {
     const int lane = threadIdx.x & 31;
+    const int q = ld >> 3;
     unsigned todo = __ballot_sync(0xFFFFFFFFu, active);
     while (todo) {
-        const int j = __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const int4 *s4 = (const int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)src, j);
-        int4 *d4 = (int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)dst, j);
-        for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
+        const int4 *s4[4];
+        int4 *d4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            s4[u] = nullptr;
+            d4[u] = nullptr;
+            if (todo) {   // warp-uniform
+                const int j = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                s4[u] = (const int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)src, j);
+                d4[u] = (int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)dst, j);
+            }
+        }
+        for (int k = lane; k < q; k += 32) {
+            int4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (s4[u]) v[u] = s4[u][k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (d4[u]) d4[u][k] = v[u];
+        }
     }
     __syncwarp();
 }

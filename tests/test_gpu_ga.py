@@ -174,6 +174,16 @@ def test_islands_ring_uneven_three(gpu):
     _islands_vs_oracle(gpu, spec, prm, oprm, 2, 5, 4, 1, 30, 12, 3, 1, check_every=3)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_islands_migration_full_size_islands(gpu, mode):
+    """Migration every generation between islands of 16384 rows (128 x 128
+    tori and 16384-row pseudo islands), the bench's island size: the ranking
+    sorts eight chunks per island and merges them."""
+    spec = make_instance(20, 5, 2, 4, seed=5)
+    prm, oprm = _params(gpu, seed=5, mode=mode, gap=1, ring=(2, 100), theta=(1, 1))
+    _islands_vs_oracle(gpu, spec, prm, oprm, 2, 128, 128, 2, 16384, 3, 1, mode, check_every=1)
+
+
 @pytest.mark.parametrize("variant,threads,n_pseudo", [(4, 128, 1), (3, 256, 1), (4, 512, 0), (3, 128, 0)])
 def test_islands_tensor_memory_heaps(gpu, variant, threads, n_pseudo):
     """Chunked decoding (8 jobs per round) with the saved heaps in tensor
