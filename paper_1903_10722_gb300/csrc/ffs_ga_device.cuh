@@ -30,7 +30,6 @@ struct ChildJob {
 __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, int ld, uint32_t *bits)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const int words = (n + 31) >> 5;
     unsigned todo = __ballot_sync(0xFFFFFFFFu, me.active);
     while (todo) {
@@ -51,39 +50,68 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
         }
         for (int w = lane; w < words; w += 32) bits[w] = 0u;
         __syncwarp();
-        for (int k = l + lane; k <= r; k += 32) {
-            const int g = p1[k];
-            child[k] = (int16_t)g;
-            if ((unsigned)g < (unsigned)n) atomicOr(&bits[g >> 5], 1u << (g & 31));
+        // the segment p1[l..r], eight genes (one 16-byte block) per lane
+        const int4 *p1v = reinterpret_cast<const int4 *>(p1);
+        int4 *cv = reinterpret_cast<int4 *>(child);
+        for (int q = (l >> 3) + lane; q <= (r >> 3); q += 32) {
+            const int4 v = p1v[q];
+            const uint32_t wv[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+            const bool full = 8 * q >= l && 8 * q + 7 <= r;
+            if (full) cv[q] = v;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = 8 * q + u;
+                if (idx >= l && idx <= r) {
+                    const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
+                    if (!full) child[idx] = (int16_t)g;
+                    if ((unsigned)g < (unsigned)n) atomicOr(&bits[g >> 5], 1u << (g & 31));
+                }
+            }
         }
         __syncwarp();
+        // p2 from position start = r + 1 onward cyclically, in 16-byte blocks:
+        // pass t takes block (start / 8 + t) mod nb; pass 0 keeps the genes
+        // from start on, pass nb those before start.  A lane's taken genes
+        // get consecutive ranks after a warp prefix sum of the lanes' counts.
         const int start = (r + 1 == n) ? 0 : r + 1;
+        const int nb = (n + 7) >> 3, b0 = start >> 3;
+        const int4 *p2v = reinterpret_cast<const int4 *>(p2);
         int placed = 0;
-        // p2 in groups of 8 x 32 genes: the 8 loads of a group are issued
-        // before the ballots that place them
-        for (int t0 = 0; t0 < n; t0 += 256) {
+        for (int t0 = 0; t0 <= nb; t0 += 32) {
+            const int t = t0 + lane;
+            int q = b0 + t;
+            if (q >= nb) q -= nb;
+            int4 v = make_int4(0, 0, 0, 0);
+            if (t <= nb) v = p2v[q];
+            const uint32_t wv[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+            const int lo = t == 0 ? start : 0, hi = t == nb ? start : n;   // natural indices kept in this pass
+            unsigned take = 0u;
             int gv[8];
 #pragma unroll
-            for (int c8 = 0; c8 < 8; ++c8) {
-                const int t = t0 + 32 * c8 + lane;
-                int idx = start + t;
-                if (idx >= n) idx -= n;
-                gv[c8] = t < n ? (int)p2[idx] : 0;
+            for (int u = 0; u < 8; ++u) {
+                const int idx = 8 * q + u;
+                const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
+                gv[u] = g;
+                const bool in_seg = (unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u);
+                if (t <= nb && idx >= lo && idx < hi && !in_seg) take |= 1u << u;
             }
+            const int cnt = __popc(take);
+            int incl = cnt;
 #pragma unroll
-            for (int c8 = 0; c8 < 8; ++c8) {
-                const int t = t0 + 32 * c8 + lane;
-                if (t0 + 32 * c8 >= n) break;
-                const int g = gv[c8];
-                const bool take = t < n && !((unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u));
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
-                if (take) {
-                    int pos = start + placed + __popc(m & lt);
-                    if (pos >= n) pos -= n;
-                    child[pos] = (int16_t)g;
-                }
-                placed += __popc(m);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
             }
+            const int first = start + placed + incl - cnt;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if ((take >> u) & 1u) {
+                    int pos = first + __popc(take & ((1u << u) - 1u));
+                    if (pos >= n) pos -= n;
+                    child[pos] = (int16_t)gv[u];
+                }
+            }
+            placed += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         __syncwarp();
     }
