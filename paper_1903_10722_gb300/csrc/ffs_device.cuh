@@ -358,7 +358,12 @@ __device__ __noinline__ uint4 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
     const int n = (int)(nB & 0xFFFFu), B = (int)(nB >> 16);
     const int d0 = (int)(dc & 0xFFFFu), cnt = (int)(dc >> 16);
     const int Mr = (int)(mf & 0xFFu), fl0 = (int)(mf >> 8);
-    const uint32_t mulSH = 1u << SH, lowmask = mulSH - 1u, idmask = lowmask & ~1u;
+    // 2^SH through an opaque move: the compiler then keeps p * 2^SH + t as one
+    // multiply-add (FMA pipe) instead of a shift and an add (ALU pipe, the
+    // decoder's bottleneck)
+    uint32_t mulSH;
+    asm("mov.b32 %0, %1;" : "=r"(mulSH) : "r"(1u << SH));
+    const uint32_t lowmask = mulSH - 1u, idmask = lowmask & ~1u;
     const uint32_t stride = blockDim.x * 4u;
     const bool single = B >= n;
     const uint32_t rel = (obj & 0xFFFFu) << 2, due = EMIT ? 0u : (obj >> 16) << 2;
@@ -536,7 +541,12 @@ __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap
     const int Ma = (int)(mm & 0xFFu), Mb = (int)((mm >> 8) & 0xFFu);
     const int fa0 = (int)((mm >> 16) & 0xFFu), fb0 = (int)(mm >> 24);
     const int da0 = (int)(dd & 0xFFFFu), db0 = (int)(dd >> 16);
-    const uint32_t mulSH = 1u << SH, lowmask = mulSH - 1u, idmask = lowmask & ~1u;
+    // 2^SH through an opaque move: the compiler then keeps p * 2^SH + t as one
+    // multiply-add (FMA pipe) instead of a shift and an add (ALU pipe, the
+    // decoder's bottleneck)
+    uint32_t mulSH;
+    asm("mov.b32 %0, %1;" : "=r"(mulSH) : "r"(1u << SH));
+    const uint32_t lowmask = mulSH - 1u, idmask = lowmask & ~1u;
     const uint32_t stride = blockDim.x * 4u;
     const bool chunked = B < n;
     if constexpr (EMIT_B) due = 0u;
