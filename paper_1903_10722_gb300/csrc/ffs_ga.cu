@@ -157,7 +157,7 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
     const int16_t *b = a + ld;
-    uint32_t *bits = bits_smem + (threadIdx.x >> 5) * ((n + 31) >> 5);
+    uint32_t *bits = bits_smem + (threadIdx.x >> 5) * mark_words(n, true);
     ChildJob job;
     job.active = cross;
     job.cross = true;
@@ -166,11 +166,11 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     job.p1 = a;
     job.p2 = b;
     job.child = s.children + (int64_t)slot * ld;
-    warp_build_children(job, n, ld, bits);
+    warp_build_children<true>(job, n, ld, bits);
     job.p1 = b;
     job.p2 = a;
     job.child = s.children + (int64_t)(slot + 1) * ld;
-    warp_build_children(job, n, ld, bits);
+    warp_build_children<true>(job, n, ld, bits);
 }
 
 // Lane l < kPairsPerWarp of a warp takes one pair: it keeps the two best of
@@ -236,9 +236,8 @@ __global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __gri
                                                         int cols, int n, int ld)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    const int bits_per_warp = (n + 31) >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *wbits = smem + warp * bits_per_warp;
+    uint32_t *wbits = smem + warp * mark_words(n, true);
     const int cells = rows * cols, total = cells * batch.count;
     const int base = (blockIdx.x * (blockDim.x >> 5) + warp) * kCellsPerWarp;
     if (base >= total) return;   // whole warps leave together
@@ -246,7 +245,7 @@ __global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __gri
     const bool valid = lane < kCellsPerWarp && gc < total;
     const int gq = valid ? gc : base;
     const int bi = gq / cells, c = gq - bi * cells;
-    cellular_warp_breed(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits);
+    cellular_warp_breed<true>(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits);
 }
 
 static int launch_cellular_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows,
@@ -254,8 +253,8 @@ static int launch_cellular_breed(const ffs_instance *inst, const GaScalars &g, c
 {
     const int total = rows * cols * batch.count;
     const int T = 256;
-    const size_t smem = (size_t)(T / 32) * ((inst->n + 31) / 32) * 4;
-    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
+    const size_t smem = (size_t)(T / 32) * mark_words(inst->n, true) * 4;
+    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int warps = (total + kCellsPerWarp - 1) / kCellsPerWarp;
     k_cellular_breed<<<(warps + T / 32 - 1) / (T / 32), T, smem, st>>>(g, batch, rows, cols, inst->n, ld);
@@ -275,10 +274,10 @@ static int launch_pseudo_breed(const ffs_instance *inst, const GaScalars &g, con
 {
     const int pairs = size / 2 * batch.count;
     FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));   // count and work
-    const int words = (inst->n + 31) / 32;
+    const int words = mark_words(inst->n, true);
     const int T = 128;
     const size_t smem = (size_t)(T / 32) * words * 4;
-    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
+    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_pseudo_breed<<<pair_blocks(pairs, T), T, smem, st>>>(g, batch, size, inst->n, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
@@ -292,10 +291,10 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
     if (pairs <= 0) return FFS_OK;
     PseudoScratch s = carve(scratch, size, ld, batch.count);
     FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));
-    const int words = (inst->n + 31) / 32;
+    const int words = mark_words(inst->n, true);
     const int T = 128;
     const size_t smem = (size_t)(T / 32) * words * 4;
-    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover bitmask too large");
+    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_pseudo_breed<<<pair_blocks(pairs, T), T, smem, st>>>(g, batch, size, inst->n, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
@@ -412,7 +411,7 @@ struct IslandDesc {
     int32_t kind;
     int32_t k_ring;    // rows sent to the next island by ring migration
     int32_t ring_off;  // prefix sum of k_ring
-    int32_t row_off;   // prefix sum of N (the island's keys in the ranking scratch)
+    int32_t row_off;   // the island's keys in the ranking scratch (prefix sum of N, each rounded up to even)
 };
 
 constexpr int kMaxMigrationRows = 16384;
@@ -427,19 +426,20 @@ __device__ __forceinline__ bool migration_due(const int32_t *gate, int gap)
 }
 
 // Keys are (makespan << 32 | row), unique within an island.  A chunk of
-// kRankChunk keys is sorted by one block of kRankChunk / 16 threads; a thread
-// holds 16 consecutive keys e = 16 t + r in registers.  In shared memory key
-// e sits at slot e + e / 16 (one pad slot per 16), so a thread's 16 keys load
-// and store without bank conflicts.
+// kRankChunk keys is sorted by one block of kRankChunk / 8 threads; a thread
+// holds 8 consecutive keys e = 8 t + r in registers.  In shared memory key e
+// sits at slot e + e / 8 (one pad slot per 8), so a thread's 8 keys load and
+// store without bank conflicts.
 constexpr int kRankChunk = 2048;
-__device__ __forceinline__ int rank_slot(int e) { return e + (e >> 4); }
+constexpr int kRankThreads = kRankChunk / 8;
+__device__ __forceinline__ int rank_slot(int e) { return e + (e >> 3); }
 
-// One compare-exchange step of distance J < 16 inside a thread's registers.
+// One compare-exchange step of distance J < 8 inside a thread's registers.
 template <int J>
-__device__ __forceinline__ void rank_reg_step(unsigned long long (&x)[16], int e0, int k)
+__device__ __forceinline__ void rank_reg_step(unsigned long long (&x)[8], int e0, int k)
 {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < 8; ++r) {
         if ((r & J) == 0) {
             const unsigned long long a = x[r], b = x[r | J];
             const bool sw = (a > b) == (((e0 + r) & k) == 0);
@@ -451,27 +451,38 @@ __device__ __forceinline__ void rank_reg_step(unsigned long long (&x)[16], int e
 
 // Block (chunk, island): sort keys [chunk * kRankChunk, ...) of the island
 // into the scratch.  For each merge size k of the bitonic network the steps
-// of distance j >= 512 run in shared memory, 16 <= j < 512 across the warp by
-// shuffles (the partner of key 16 t + r is key 16 (t ^ j / 16) + r), j < 16
-// in registers.  Missing keys are padded with ~0 (they sort last).
-__global__ void __launch_bounds__(kRankChunk / 16) k_rank_chunks(const IslandDesc *desc, const int32_t *cur,
-                                                                 const int32_t *gate, int gap,
-                                                                 unsigned long long *scratch)
+// of distance j >= 256 run in shared memory, 8 <= j < 256 across the warp by
+// shuffles (the partner of key 8 t + r is key 8 (t ^ j / 8) + r), j < 8 in
+// registers.  Missing keys are padded with ~0 (they sort last).
+__global__ void __launch_bounds__(kRankThreads) k_rank_chunks(const IslandDesc *desc, const int32_t *cur,
+                                                              const int32_t *gate, int gap,
+                                                              unsigned long long *scratch)
 {
     if (!migration_due(gate, gap)) return;
-    __shared__ unsigned long long keys[kRankChunk + kRankChunk / 16];
+    __shared__ unsigned long long keys[kRankChunk + kRankChunk / 8];
     const IslandDesc d = desc[blockIdx.y];
     const int c0 = blockIdx.x * kRankChunk;
     if (c0 >= d.N) return;   // the whole block
     const int len = min(kRankChunk, d.N - c0);
     const int32_t *ms = cur[blockIdx.y] ? d.ms[1] : d.ms[0];
-    for (int e = threadIdx.x; e < kRankChunk; e += blockDim.x)
-        keys[rank_slot(e)] = e < len ? ((unsigned long long)(uint32_t)ms[c0 + e] << 32) | (uint32_t)(c0 + e) : ~0ull;
+    {
+        uint32_t v[8];   // all loads in flight before the stores
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = threadIdx.x + i * kRankThreads;
+            v[i] = e < len ? (uint32_t)ms[c0 + e] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = threadIdx.x + i * kRankThreads;
+            keys[rank_slot(e)] = e < len ? ((unsigned long long)v[i] << 32) | (uint32_t)(c0 + e) : ~0ull;
+        }
+    }
     __syncthreads();
-    const int t = threadIdx.x, e0 = 16 * t;
+    const int t = threadIdx.x, e0 = 8 * t;
     for (int k = 2; k <= kRankChunk; k <<= 1) {
         int j = k >> 1;
-        for (; j >= 512; j >>= 1) {
+        for (; j >= 256; j >>= 1) {
             for (int e = threadIdx.x; e < kRankChunk; e += blockDim.x) {
                 const int o = e ^ j;
                 if (o > e) {
@@ -484,60 +495,99 @@ __global__ void __launch_bounds__(kRankChunk / 16) k_rank_chunks(const IslandDes
             }
             __syncthreads();
         }
-        unsigned long long x[16];
+        unsigned long long x[8];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) x[r] = keys[rank_slot(e0 + r)];
-        for (; j >= 16; j >>= 1) {
-            const int lm = j >> 4;
+        for (int r = 0; r < 8; ++r) x[r] = keys[rank_slot(e0 + r)];
+        for (; j >= 8; j >>= 1) {
+            const int lm = j >> 3;
             const bool lower = (t & lm) == 0;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < 8; ++r) {
                 const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, x[r], lm);
                 const bool keep_min = lower == (((e0 + r) & k) == 0);
                 x[r] = keep_min ? (x[r] < y ? x[r] : y) : (x[r] < y ? y : x[r]);
             }
         }
-        if (j >= 8) rank_reg_step<8>(x, e0, k);
         if (j >= 4) rank_reg_step<4>(x, e0, k);
         if (j >= 2) rank_reg_step<2>(x, e0, k);
         rank_reg_step<1>(x, e0, k);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) keys[rank_slot(e0 + r)] = x[r];
+        for (int r = 0; r < 8; ++r) keys[rank_slot(e0 + r)] = x[r];
         __syncthreads();
     }
     unsigned long long *out = scratch + d.row_off + c0;
     for (int e = threadIdx.x; e < len; e += blockDim.x) out[e] = keys[rank_slot(e)];
 }
 
-// Thread per key: its rank in the island = its position in its sorted chunk
-// + the keys below it in each other chunk (lower bound by binary search);
-// order[rank] = its row.  Keys are unique, so the ranks are a permutation.
-__global__ void k_rank_merge(const IslandDesc *desc, int I, const int32_t *gate, int gap,
-                             const unsigned long long *scratch, int total_rows)
+// Block (chunk c, island): the island's sorted chunks are staged in shared
+// memory; a thread takes 8 consecutive keys of chunk c.  A key's rank in the
+// island = its position in chunk c + its lower bound in each other chunk;
+// the thread's first key finds its lower bound by binary search, the next
+// ones by galloping on from there (keys increase).  order[rank] = row; keys
+// are unique, so the ranks are a permutation.
+__global__ void __launch_bounds__(kRankThreads) k_rank_merge(const IslandDesc *desc, const int32_t *gate, int gap,
+                                                             const unsigned long long *scratch)
 {
     if (!migration_due(gate, gap)) return;
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= total_rows) return;
-    int i = 0;
-    while (i + 1 < I && desc[i + 1].row_off <= gid) ++i;
-    const IslandDesc &d = desc[i];
+    extern __shared__ unsigned long long isl_keys[];
+    const IslandDesc &d = desc[blockIdx.y];
+    const int c0 = blockIdx.x * kRankChunk;
+    if (c0 >= d.N) return;   // the whole block
+    // row_off is even, so the island's keys start on a 16-byte boundary:
+    // 16-byte asynchronous copies, all in flight at once
     const unsigned long long *base = scratch + d.row_off;
-    const int e = gid - d.row_off;
-    const unsigned long long key = base[e];
-    const int c = e / kRankChunk;
-    int rank = e - c * kRankChunk;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(isl_keys);
+    for (int q = threadIdx.x; q < (d.N >> 1); q += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 16u * (uint32_t)q), "l"(base + 2 * q)
+                     : "memory");
+    if ((d.N & 1) && threadIdx.x == 0) isl_keys[d.N - 1] = base[d.N - 1];
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int len = min(kRankChunk, d.N - c0);
+    const int e0 = 8 * threadIdx.x;
+    if (e0 >= len) return;
+    const int m = min(8, len - e0);
+    unsigned long long key[8];
+    int rank[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        key[u] = u < m ? isl_keys[c0 + e0 + u] : ~0ull;
+        rank[u] = e0 + u;
+    }
     for (int c2 = 0; c2 * kRankChunk < d.N; ++c2) {
-        if (c2 == c) continue;
-        const unsigned long long *a = base + c2 * kRankChunk;
-        int lo = 0, hi = min(kRankChunk, d.N - c2 * kRankChunk);
+        if (c2 * kRankChunk == c0) continue;
+        const unsigned long long *a = isl_keys + c2 * kRankChunk;
+        const int alen = min(kRankChunk, d.N - c2 * kRankChunk);
+        int lo = 0, hi = alen;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (a[mid] < key) lo = mid + 1;
+            if (a[mid] < key[0]) lo = mid + 1;
             else hi = mid;
         }
-        rank += lo;
+        rank[0] += lo;
+#pragma unroll
+        for (int u = 1; u < 8; ++u) {
+            if (u < m) {
+                // lower bound of key[u] in a[lo..alen): gallop, then bisect
+                int step = 1, top = lo;
+                while (top < alen && a[top] < key[u]) {
+                    lo = top + 1;
+                    top = lo + step;
+                    step <<= 1;
+                }
+                hi = top < alen ? top : alen;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a[mid] < key[u]) lo = mid + 1;
+                    else hi = mid;
+                }
+                rank[u] += lo;
+            }
+        }
     }
-    d.order[rank] = (int32_t)(key & 0xFFFFFFFFu);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        if (u < m) d.order[rank[u]] = (int32_t)(key[u] & 0xFFFFFFFFu);
 }
 
 // One warp per migrated row: island i's t-th best onto island (i+1)'s t-th worst.
@@ -732,11 +782,12 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
         return set_error(FFS_EUNSUPPORTED, "migration ranks islands of at most %d rows", kMaxMigrationRows);
     const int32_t *gate = gated ? S->d_gen : nullptr;
     const int gap = S->prm.migration_gap;
-    k_rank_chunks<<<dim3((S->max_N + kRankChunk - 1) / kRankChunk, S->I), kRankChunk / 16, 0, st>>>(
-        S->d_desc, S->d_cur, gate, gap, S->d_rank_keys);
+    const int chunks = (S->max_N + kRankChunk - 1) / kRankChunk;
+    k_rank_chunks<<<dim3(chunks, S->I), kRankThreads, 0, st>>>(S->d_desc, S->d_cur, gate, gap, S->d_rank_keys);
     FFS_CUDA_TRY(cudaGetLastError());
-    k_rank_merge<<<(S->total_rows + 255) / 256, 256, 0, st>>>(S->d_desc, S->I, gate, gap, S->d_rank_keys,
-                                                              S->total_rows);
+    const size_t msmem = (size_t)S->max_N * 8;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_rank_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+    k_rank_merge<<<dim3(chunks, S->I), kRankThreads, msmem, st>>>(S->d_desc, gate, gap, S->d_rank_keys);
     FFS_CUDA_TRY(cudaGetLastError());
     if (mode == FFS_MIG_RING) {
         const int warps = S->ring_rows;
@@ -951,7 +1002,7 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
         memset(&d, 0, sizeof(d));
         d.N = N;
         d.row_off = S->total_rows;
-        S->total_rows += N;
+        S->total_rows += N + (N & 1);   // keeps every island's keys 16-byte aligned
         d.kind = S->kind[i];
         for (int b = 0; b < 2; ++b) {
             d.pop[b] = (int16_t *)alloc((size_t)N * S->ld * 2);

@@ -16,7 +16,8 @@ namespace fgpu {
 // Order crossover: the child keeps p1[l..r]; the other positions, from r+1
 // onward cyclically, take p2's genes met from position r+1 onward
 // cyclically, skipping genes already placed.  Without crossover the child
-// copies p1.  `bits` is a warp-private shared bitmask of ceil(n/32) words.
+// copies p1.  `mark` is the warp's shared mark of mark_words(n, BYTES) words:
+// one byte per gene (BYTES) or one bit.
 // ---------------------------------------------------------------------------
 struct ChildJob {
     const int16_t *p1;
@@ -27,10 +28,12 @@ struct ChildJob {
     bool active;
 };
 
-__device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, int ld, uint32_t *bits)
+template <bool BYTES>
+__device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, int ld, uint32_t *mark)
 {
+    uint8_t *flag = reinterpret_cast<uint8_t *>(mark);
     const int lane = threadIdx.x & 31;
-    const int words = (n + 31) >> 5;
+    const int words = mark_words(n, BYTES);
     unsigned todo = __ballot_sync(0xFFFFFFFFu, me.active);
     while (todo) {
         const int j = __ffs(todo) - 1;
@@ -48,7 +51,11 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
             __syncwarp();
             continue;
         }
-        for (int w = lane; w < words; w += 32) bits[w] = 0u;
+        if constexpr (BYTES) {
+            for (int w = lane; 4 * w < words; w += 32) reinterpret_cast<uint4 *>(mark)[w] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            for (int w = lane; w < words; w += 32) mark[w] = 0u;
+        }
         __syncwarp();
         // the segment p1[l..r], eight genes (one 16-byte block) per lane
         const int4 *p1v = reinterpret_cast<const int4 *>(p1);
@@ -64,7 +71,10 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
                 if (idx >= l && idx <= r) {
                     const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
                     if (!full) child[idx] = (int16_t)g;
-                    if ((unsigned)g < (unsigned)n) atomicOr(&bits[g >> 5], 1u << (g & 31));
+                    if ((unsigned)g < (unsigned)n) {
+                        if constexpr (BYTES) flag[g] = 1u;
+                        else atomicOr(&mark[g >> 5], 1u << (g & 31));
+                    }
                 }
             }
         }
@@ -92,7 +102,9 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
                 const int idx = 8 * q + u;
                 const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
                 gv[u] = g;
-                const bool in_seg = (unsigned)g < (unsigned)n && ((bits[g >> 5] >> (g & 31)) & 1u);
+                bool in_seg;
+                if constexpr (BYTES) in_seg = (unsigned)g < (unsigned)n && flag[g] != 0u;
+                else in_seg = (unsigned)g < (unsigned)n && ((mark[g >> 5] >> (g & 31)) & 1u);
                 if (t <= nb && idx >= lo && idx < hi && !in_seg) take |= 1u << u;
             }
             const int cnt = __popc(take);
@@ -157,7 +169,9 @@ __device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, 
 // (lanes with !valid only keep the warp in lock step): draws, two binary
 // tournaments over the von Neumann neighbourhood (previous generation's
 // makespans), order crossover, swap mutation.  The child is built in the
-// cell's output row.
+// cell's output row.  `wbits`: the warp's crossover mark (BYTES as in
+// warp_build_children).
+template <bool BYTES>
 __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const GaScalars &g, int n, int c, bool valid,
                                                     int rows, int cols, int ld, uint32_t *wbits)
 {
@@ -199,7 +213,7 @@ __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const 
         job.r = max(u, v);
         mutate = fires(b1.w, g.cell_pm);
     }
-    warp_build_children(job, n, ld, wbits);
+    warp_build_children<BYTES>(job, n, ld, wbits);
     if (mutate) {
         int16_t *child = job.child;
         const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
@@ -242,7 +256,7 @@ __device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, cons
                                                     uint32_t *region, int T, const uint16_t *tab,
                                                     WarpStageState *wst)
 {
-    cellular_warp_breed(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
+    cellular_warp_breed<false>(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
     cellular_warp_decode(Ls, g, ref, c, valid, ld, region, T, tab, wst);
 }
 
