@@ -519,20 +519,21 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_chunks(const IslandDesc *
     for (int e = threadIdx.x; e < len; e += blockDim.x) out[e] = keys[rank_slot(e)];
 }
 
-// Block (chunk c, island): the island's sorted chunks are staged in shared
-// memory; a thread takes 8 consecutive keys of chunk c.  A key's rank in the
-// island = its position in chunk c + its lower bound in each other chunk;
-// the thread's first key finds its lower bound by binary search, the next
-// ones by galloping on from there (keys increase).  order[rank] = row; keys
-// are unique, so the ranks are a permutation.
-__global__ void __launch_bounds__(kRankThreads) k_rank_merge(const IslandDesc *desc, const int32_t *gate, int gap,
-                                                             const unsigned long long *scratch)
+// Block (1024 keys, island): the island's sorted chunks are staged in shared
+// memory; a thread takes one key.  Its rank in the island = its position in
+// its chunk + its lower bound in each other chunk, the lower bounds found by
+// binary searches run side by side (independent shared loads).
+// order[rank] = row; keys are unique, so the ranks are a permutation.
+constexpr int kRankMergeThreads = 1024;
+constexpr int kRankMaxChunks = kMaxMigrationRows / kRankChunk;
+
+__global__ void __launch_bounds__(kRankMergeThreads) k_rank_merge(const IslandDesc *desc, const int32_t *gate, int gap,
+                                                                  const unsigned long long *scratch)
 {
     if (!migration_due(gate, gap)) return;
     extern __shared__ unsigned long long isl_keys[];
     const IslandDesc &d = desc[blockIdx.y];
-    const int c0 = blockIdx.x * kRankChunk;
-    if (c0 >= d.N) return;   // the whole block
+    if (blockIdx.x * kRankMergeThreads >= d.N) return;   // the whole block
     // row_off is even, so the island's keys start on a 16-byte boundary:
     // 16-byte asynchronous copies, all in flight at once
     const unsigned long long *base = scratch + d.row_off;
@@ -543,51 +544,33 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_merge(const IslandDesc *d
     if ((d.N & 1) && threadIdx.x == 0) isl_keys[d.N - 1] = base[d.N - 1];
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    const int len = min(kRankChunk, d.N - c0);
-    const int e0 = 8 * threadIdx.x;
-    if (e0 >= len) return;
-    const int m = min(8, len - e0);
-    unsigned long long key[8];
-    int rank[8];
+    const int e = blockIdx.x * kRankMergeThreads + threadIdx.x;
+    if (e >= d.N) return;
+    const unsigned long long key = isl_keys[e];
+    const int c = e / kRankChunk;
+    int lo[kRankMaxChunks], hi[kRankMaxChunks];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        key[u] = u < m ? isl_keys[c0 + e0 + u] : ~0ull;
-        rank[u] = e0 + u;
+    for (int c2 = 0; c2 < kRankMaxChunks; ++c2) {
+        const int a0 = c2 * kRankChunk;
+        lo[c2] = 0;
+        hi[c2] = (c2 != c && a0 < d.N) ? min(kRankChunk, d.N - a0) : 0;
     }
-    for (int c2 = 0; c2 * kRankChunk < d.N; ++c2) {
-        if (c2 * kRankChunk == c0) continue;
-        const unsigned long long *a = isl_keys + c2 * kRankChunk;
-        const int alen = min(kRankChunk, d.N - c2 * kRankChunk);
-        int lo = 0, hi = alen;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (a[mid] < key[0]) lo = mid + 1;
-            else hi = mid;
-        }
-        rank[0] += lo;
+    // a range of at most 2048 keys is empty after 12 halvings
+#pragma unroll 1
+    for (int step = 0; step < 12; ++step) {
 #pragma unroll
-        for (int u = 1; u < 8; ++u) {
-            if (u < m) {
-                // lower bound of key[u] in a[lo..alen): gallop, then bisect
-                int step = 1, top = lo;
-                while (top < alen && a[top] < key[u]) {
-                    lo = top + 1;
-                    top = lo + step;
-                    step <<= 1;
-                }
-                hi = top < alen ? top : alen;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (a[mid] < key[u]) lo = mid + 1;
-                    else hi = mid;
-                }
-                rank[u] += lo;
+        for (int c2 = 0; c2 < kRankMaxChunks; ++c2) {
+            if (lo[c2] < hi[c2]) {
+                const int mid = (lo[c2] + hi[c2]) >> 1;
+                if (isl_keys[c2 * kRankChunk + mid] < key) lo[c2] = mid + 1;
+                else hi[c2] = mid;
             }
         }
     }
+    int rank = e - c * kRankChunk;
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-        if (u < m) d.order[rank[u]] = (int32_t)(key[u] & 0xFFFFFFFFu);
+    for (int c2 = 0; c2 < kRankMaxChunks; ++c2) rank += lo[c2];
+    d.order[rank] = (int32_t)(key & 0xFFFFFFFFu);
 }
 
 // One warp per migrated row: island i's t-th best onto island (i+1)'s t-th worst.
@@ -787,7 +770,8 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
     FFS_CUDA_TRY(cudaGetLastError());
     const size_t msmem = (size_t)S->max_N * 8;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_rank_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
-    k_rank_merge<<<dim3(chunks, S->I), kRankThreads, msmem, st>>>(S->d_desc, gate, gap, S->d_rank_keys);
+    k_rank_merge<<<dim3((S->max_N + kRankMergeThreads - 1) / kRankMergeThreads, S->I), kRankMergeThreads, msmem, st>>>(
+        S->d_desc, gate, gap, S->d_rank_keys);
     FFS_CUDA_TRY(cudaGetLastError());
     if (mode == FFS_MIG_RING) {
         const int warps = S->ring_rows;
