@@ -554,7 +554,7 @@ def run_decode(args):
     num_sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
     results = {}
-    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 64, 128) for t in (64, 128, 256, 320, 384, 448, 512)]
+    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 48, 64, 96, 112, 128) for t in (64, 128, 256, 320, 384, 448, 512)]
     variants = (1, 2, 3, 4)
     if args.shape:
         t, c, v = (int(x) for x in args.shape.split(","))

@@ -95,14 +95,15 @@ def test_batch_256_uneven_sampled(gpu):
                 assert after[i][0][c].tolist() == pop[c, :s.n].tolist() and after[i][1][c] == ms[c], (i, c)
 
 
-@pytest.mark.parametrize("variant,threads", [(3, 128), (4, 256), (3, 448), (4, 320)])
-def test_batch_tensor_memory_heaps_match_oracle(gpu, variant, threads):
+@pytest.mark.parametrize("variant,threads,chunk", [(3, 128, 8), (4, 256, 8), (3, 448, 8), (4, 320, 8), (3, 384, 24),
+                                                   (4, 448, 40)])
+def test_batch_tensor_memory_heaps_match_oracle(gpu, variant, threads, chunk):
     """Chunked decoding (8 jobs per round) with each instance's saved heaps in
     tensor memory as far as its stages fit the warp's columns."""
     specs = _mixed_specs()
     rows, cols = 6, 5
     prm = gpu.ffs_params_default()
-    prm.decode_variant, prm.decode_chunk, prm.block_threads = variant, 8, threads
+    prm.decode_variant, prm.decode_chunk, prm.block_threads = variant, chunk, threads
     oprm = orc.Params(seed=7)
     b = gpu.Batch(specs, prm, rows, cols)
     assert b.info()["variant"] == variant

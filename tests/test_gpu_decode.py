@@ -42,14 +42,14 @@ def test_eval_matches_oracle(gpu, shape):
     d = dev(pop)
     out = torch.full((N,), -7, dtype=torch.int32, device="cuda")
     shapes = [(0, 0)]
-    for chunk in (8, 16, 32, 64):
+    for chunk in (8, 16, 32, 48, 64, 96, 112, 128):
         if chunk < n:
             shapes.append((chunk, 0))
     for threads in (32, 96, 128, 256, 512):
         shapes.append((0, threads))
     if n > 8:
         shapes.append((8, 64))
-    for chunk, threads in ((8, 128), (16, 256), (32, 512), (8, 512)):
+    for chunk, threads in ((8, 128), (16, 256), (32, 512), (8, 512), (96, 384), (112, 448), (48, 320)):
         if chunk < n:
             shapes.append((chunk, threads))
     ran = 0
