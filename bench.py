@@ -303,9 +303,13 @@ def run_ours(args):
     clock_info = clocks.stop()
     d1 = ffs.ffs_islands_decoded(isl)
     evals = d1 - d0
-    int_rates = {name: round(ffs.ffs_measure_int_rate(k)["lane_ops_per_s"] / 1e12, 2)
-                 for k, name in enumerate(("min_max", "lop3", "iadd3", "imad", "fmnmx", "vminmax_u16x2",
-                                           "min3_max3", "add_max", "min_max+imad", "min_max+fmnmx"))}
+    # per-pipe integer rates (probe kernels, outside the timed regions; opt-in so
+    # that the launch list of a plain run holds the generation's kernels only)
+    int_rates = None
+    if args.int_rates:
+        int_rates = {name: round(ffs.ffs_measure_int_rate(k)["lane_ops_per_s"] / 1e12, 2)
+                     for k, name in enumerate(("min_max", "lop3", "iadd3", "imad", "fmnmx", "vminmax_u16x2",
+                                               "min3_max3", "add_max", "min_max+imad", "min_max+fmnmx"))}
 
     # ---- e2e: the same steps with populations from / to pinned host memory ----
     # all islands' rows in one host buffer with the library's row stride: each
@@ -354,7 +358,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches_per_generation(w),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops,
+                     "traffic": K_STEP_DECODE_DRAM_BYTES if _shape_is(prm, 384, 128, 3) else None,
                      "kernel": "k_step_decode (all cellular children: decode + replace; all pseudo children: decode), "
                                "timed with the cellular and pseudo breed and the pseudo replace launches",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": decodes_per_launch * ops_eval,
@@ -660,6 +665,16 @@ def run_paper(args):
     return 0
 
 
+# DRAM bytes (read + write) of one k_step_decode launch of scale_500x20 at
+# 384 threads, chunk 128, variant 3, from one ncu capture of the current
+# kernel (160.1 MB read + 28.4 MB written); other shapes report null.
+K_STEP_DECODE_DRAM_BYTES = 188_516_352
+
+
+def _shape_is(prm, threads, chunk, variant) -> bool:
+    return (prm.block_threads, prm.decode_chunk, prm.decode_variant) == (threads, chunk, variant)
+
+
 def launches_per_generation(w) -> int:
     """Kernels of one generation: cellular breed, pseudo breed, the fused
     decode launch of all cellular children and pseudo children, pseudo
@@ -679,6 +694,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="scale_500x20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--int-rates", action="store_true",
+                    help="also measure per-pipe integer issue rates with the probe kernels")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape THREADS,CHUNK,VARIANT instead of the autotuner (profiling)")
