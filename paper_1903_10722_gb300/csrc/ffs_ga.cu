@@ -113,7 +113,7 @@ static PseudoScratch carve(void *base, int size, int ld, int islands)
 }
 
 // Pairs per warp of k_pseudo_breed / k_pseudo_replace, and cells per warp
-// of k_cellular_breed: the warp builds (copies) its rows one after the other,
+// of the cellular breeding: the warp builds (copies) its rows one after the other,
 // so few rows per warp and many warps hide the memory latency of each.
 constexpr int kPairsPerWarp = 4;
 constexpr int kCellsPerWarp = 8;
@@ -121,14 +121,12 @@ constexpr int kCellsPerWarp = 8;
 // Lane l < kPairsPerWarp of a warp takes one pair: crossover decision,
 // compacted child slots; the warp then builds the two children of each
 // crossing pair cooperatively.
-__global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n, int ld,
-                               PseudoScratch s)
+__device__ __forceinline__ void pseudo_breed_warp(const GaScalars &g, const IslandBatch &batch, int size, int n, int ld,
+                                                  const PseudoScratch &s, int gw, uint32_t *bits)
 {
-    extern __shared__ uint32_t bits_smem[];
     const int pairs = size / 2;
     const int total = pairs * batch.count;
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw * kPairsPerWarp >= total) return;   // whole warps leave together
     const int gp = gw * kPairsPerWarp + lane;
     const bool mine = lane < kPairsPerWarp && gp < total;
@@ -157,7 +155,6 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
     const int16_t *a = pin + (int64_t)(2 * k) * ld;
     const int16_t *b = a + ld;
-    uint32_t *bits = bits_smem + (threadIdx.x >> 5) * mark_words(n, true);
     ChildJob job;
     job.active = cross;
     job.cross = true;
@@ -171,6 +168,14 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
     job.p2 = a;
     job.child = s.children + (int64_t)(slot + 1) * ld;
     warp_build_children<true>(job, n, ld, bits);
+}
+
+__global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n, int ld,
+                               PseudoScratch s)
+{
+    extern __shared__ uint32_t bits_smem[];
+    pseudo_breed_warp(g, batch, size, n, ld, s, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                      bits_smem + (threadIdx.x >> 5) * mark_words(n, true));
 }
 
 // Lane l < kPairsPerWarp of a warp takes one pair: it keeps the two best of
@@ -232,14 +237,12 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
 // cellular islands (children into the output rows), kCellsPerWarp cells per
 // warp, at high occupancy: its order crossover waits on memory, which many
 // warps hide.
-__global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int rows,
-                                                        int cols, int n, int ld)
+__device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const IslandBatch &batch, int rows, int cols,
+                                                    int n, int ld, int gw, uint32_t *wbits)
 {
-    extern __shared__ __align__(16) uint32_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *wbits = smem + warp * mark_words(n, true);
+    const int lane = threadIdx.x & 31;
     const int cells = rows * cols, total = cells * batch.count;
-    const int base = (blockIdx.x * (blockDim.x >> 5) + warp) * kCellsPerWarp;
+    const int base = gw * kCellsPerWarp;
     if (base >= total) return;   // whole warps leave together
     const int gc = base + lane;
     const bool valid = lane < kCellsPerWarp && gc < total;
@@ -248,18 +251,20 @@ __global__ void __launch_bounds__(256) k_cellular_breed(GaScalars g, const __gri
     cellular_warp_breed<true>(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits);
 }
 
-static int launch_cellular_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows,
-                                 int cols, int ld, cudaStream_t st)
+// Both breeding halves of a dual generation in one launch: the first
+// `cell_blocks` blocks breed the cellular cells, the others the pseudo pairs;
+// the two kinds of warps share the SMs and hide each other's memory latency.
+__global__ void __launch_bounds__(256) k_breed_dual(GaScalars g, const __grid_constant__ IslandBatch cb, int rows,
+                                                    int cols, const __grid_constant__ IslandBatch pb, int psize,
+                                                    int n, int ld, PseudoScratch s, int cell_blocks)
 {
-    const int total = rows * cols * batch.count;
-    const int T = 256;
-    const size_t smem = (size_t)(T / 32) * mark_words(inst->n, true) * 4;
-    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
-    FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int warps = (total + kCellsPerWarp - 1) / kCellsPerWarp;
-    k_cellular_breed<<<(warps + T / 32 - 1) / (T / 32), T, smem, st>>>(g, batch, rows, cols, inst->n, ld);
-    FFS_CUDA_TRY(cudaGetLastError());
-    return FFS_OK;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    uint32_t *wbits = smem + warp * mark_words(n, true);
+    if ((int)blockIdx.x < cell_blocks)
+        cellular_breed_warp(g, cb, rows, cols, n, ld, blockIdx.x * wpb + warp, wbits);
+    else
+        pseudo_breed_warp(g, pb, psize, n, ld, s, (blockIdx.x - cell_blocks) * wpb + warp, wbits);
 }
 
 // Blocks of T threads for kPairsPerWarp pairs per warp.
@@ -267,21 +272,6 @@ static int pair_blocks(int pairs, int T)
 {
     const long long warps = (pairs + kPairsPerWarp - 1) / kPairsPerWarp;
     return (int)((warps * 32 + T - 1) / T);
-}
-
-static int launch_pseudo_breed(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
-                               int ld, const PseudoScratch &s, cudaStream_t st)
-{
-    const int pairs = size / 2 * batch.count;
-    FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));   // count and work
-    const int words = mark_words(inst->n, true);
-    const int T = 128;
-    const size_t smem = (size_t)(T / 32) * words * 4;
-    if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
-    FFS_CUDA_TRY(cudaFuncSetAttribute(k_pseudo_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_pseudo_breed<<<pair_blocks(pairs, T), T, smem, st>>>(g, batch, size, inst->n, ld, s);
-    FFS_CUDA_TRY(cudaGetLastError());
-    return FFS_OK;
 }
 
 int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size, int ld,
@@ -308,7 +298,7 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
 
 // ---------------------------------------------------------------------------
 // One launch for the decoding work of a generation: the children of all
-// cellular islands (bred by k_cellular_breed into the output rows; decoded
+// cellular islands (bred by k_breed_dual into the output rows; decoded
 // here, then replace-if-better) and the pseudo islands' compacted children.
 // Warps take 32-unit work items from a device counter (cellular items first:
 // they also replace and copy rows, and the heavier items go first), so the
@@ -323,7 +313,7 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
-    const SmemMap map = smem_map(L.n, L.S, T, 0, L.obj_words);   // the crossover ran in k_cellular_breed
+    const SmemMap map = smem_map(L.n, L.S, T, 0, L.obj_words);   // the crossover ran in k_breed_dual
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     for (int i = threadIdx.x; i < 2 * L.S; i += T) st[i] = stage_g[i];
@@ -380,9 +370,21 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
                              unsigned long long *decoded, cudaStream_t st)
 {
     PseudoScratch s = carve(scratch, psize, ld, pb.count);
-    int rc = launch_cellular_breed(inst, g, cb, rows, cols, ld, st);
-    if (rc) return rc;
-    if ((rc = launch_pseudo_breed(inst, g, pb, psize, ld, s, st))) return rc;
+    {
+        // cellular and pseudo breeding in one launch
+        FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));   // count and work
+        const int T = 256;
+        const size_t smem = (size_t)(T / 32) * mark_words(inst->n, true) * 4;
+        if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
+        const int cell_warps = (rows * cols * cb.count + kCellsPerWarp - 1) / kCellsPerWarp;
+        const int cell_blocks = (cell_warps + T / 32 - 1) / (T / 32);
+        const int pseudo_blocks = pair_blocks(psize / 2 * pb.count, T);
+        FFS_CUDA_TRY(cudaFuncSetAttribute(k_breed_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_breed_dual<<<cell_blocks + pseudo_blocks, T, smem, st>>>(g, cb, rows, cols, pb, psize, inst->n, ld, s,
+                                                                   cell_blocks);
+        FFS_CUDA_TRY(cudaGetLastError());
+    }
+    int rc;
     Plan p;
     if ((rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_req, 0, &p, g.variant))) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_step_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
