@@ -676,13 +676,13 @@ def _shape_is(prm, threads, chunk, variant) -> bool:
 
 
 def launches_per_generation(w) -> int:
-    """Kernels of one generation: cellular breed, pseudo breed, the fused
-    decode launch of all cellular children and pseudo children, pseudo
-    replace, the generation advance, and when migrating the ranking plus the
-    copy kernel."""
-    n = 5
+    """Kernels of one generation: the breeding launch (cellular cells and
+    pseudo pairs), the fused decode launch of all children, the pseudo pair
+    replacement, the generation advance, and when migrating the two ranking
+    launches plus the copy kernel."""
+    n = 4
     if w.get("gap", 0) == 1 and w["n_cellular"] + w["n_pseudo"] > 1:
-        n += 2
+        n += 3
     return n
 
 
