@@ -237,8 +237,10 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
 // cellular islands (children into the output rows), kCellsPerWarp cells per
 // warp, at high occupancy: its order crossover waits on memory, which many
 // warps hide.
+// children: child rows of the batch's cells (cell c of island bi at row
+// bi * rows * cols + c), the cells copied to their output rows.
 __device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const IslandBatch &batch, int rows, int cols,
-                                                    int n, int ld, int gw, uint32_t *wbits)
+                                                    int n, int ld, int gw, uint32_t *wbits, int16_t *children)
 {
     const int lane = threadIdx.x & 31;
     const int cells = rows * cols, total = cells * batch.count;
@@ -248,7 +250,7 @@ __device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const Is
     const bool valid = lane < kCellsPerWarp && gc < total;
     const int gq = valid ? gc : base;
     const int bi = gq / cells, c = gq - bi * cells;
-    cellular_warp_breed<true>(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits);
+    cellular_warp_breed<true>(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits, children + (int64_t)gq * ld);
 }
 
 // Both breeding halves of a dual generation in one launch: the first
@@ -256,13 +258,14 @@ __device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const Is
 // the two kinds of warps share the SMs and hide each other's memory latency.
 __global__ void __launch_bounds__(256) k_breed_dual(GaScalars g, const __grid_constant__ IslandBatch cb, int rows,
                                                     int cols, const __grid_constant__ IslandBatch pb, int psize,
-                                                    int n, int ld, PseudoScratch s, int cell_blocks)
+                                                    int n, int ld, PseudoScratch s, int cell_blocks,
+                                                    int16_t *cell_children)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     uint32_t *wbits = smem + warp * mark_words(n, true);
     if ((int)blockIdx.x < cell_blocks)
-        cellular_breed_warp(g, cb, rows, cols, n, ld, blockIdx.x * wpb + warp, wbits);
+        cellular_breed_warp(g, cb, rows, cols, n, ld, blockIdx.x * wpb + warp, wbits, cell_children);
     else
         pseudo_breed_warp(g, pb, psize, n, ld, s, (blockIdx.x - cell_blocks) * wpb + warp, wbits);
 }
@@ -308,7 +311,8 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
 __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint32_t *__restrict__ tab_g,
                                                      const int32_t *__restrict__ stage_g, GaScalars g,
                                                      const __grid_constant__ IslandBatch cb, int rows, int cols, int ld,
-                                                     PseudoScratch ps, unsigned long long *decoded)
+                                                     PseudoScratch ps, const int16_t *cell_children,
+                                                     unsigned long long *decoded)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
@@ -348,7 +352,8 @@ __global__ void __launch_bounds__(512) k_step_decode(DecodeLayout L, const uint3
             const bool valid = gc < C;
             const int gq = valid ? gc : C - 1;
             const int bi = gq / cells, c = gq - bi * cells;
-            cellular_warp_decode(Ls, g, cb.ref[bi], c, valid, ld, region, T, tab, wst);
+            cellular_warp_decode_child(Ls, g, cb.ref[bi], c, valid, ld, cell_children + (int64_t)gq * ld, region, T,
+                                       tab, wst);
         } else {
             const int k = u0 - C32 + lane;
             const bool valid = k < P;
@@ -366,8 +371,8 @@ const void *step_decode_kernel() { return (const void *)k_step_decode; }
 // (same torus for cb, same size for pb): pseudo breed, the fused decode
 // launch, pseudo replace.
 static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const IslandBatch &cb, int rows, int cols,
-                             const IslandBatch &pb, int psize, int ld, void *scratch, int B_req, int T_req,
-                             unsigned long long *decoded, cudaStream_t st)
+                             const IslandBatch &pb, int psize, int ld, void *scratch, int16_t *cell_children,
+                             int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
     PseudoScratch s = carve(scratch, psize, ld, pb.count);
     {
@@ -381,7 +386,7 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
         const int pseudo_blocks = pair_blocks(psize / 2 * pb.count, T);
         FFS_CUDA_TRY(cudaFuncSetAttribute(k_breed_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_breed_dual<<<cell_blocks + pseudo_blocks, T, smem, st>>>(g, cb, rows, cols, pb, psize, inst->n, ld, s,
-                                                                   cell_blocks);
+                                                                   cell_blocks, cell_children);
         FFS_CUDA_TRY(cudaGetLastError());
     }
     int rc;
@@ -390,7 +395,8 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_step_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int64_t units = (int64_t)rows * cols * cb.count + (int64_t)psize * pb.count;
     const int grid = grid_for(inst, p, units);
-    k_step_decode<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, cb, rows, cols, ld, s, decoded);
+    k_step_decode<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, cb, rows, cols, ld, s, cell_children,
+                                             decoded);
     FFS_CUDA_TRY(cudaGetLastError());
     const int pairs = psize / 2 * pb.count;
     k_pseudo_replace<<<pair_blocks(pairs, 128), 128, 0, st>>>(g, pb, psize, ld, s);
@@ -687,6 +693,7 @@ struct ffs_islands {
     unsigned long long *d_rank_keys = nullptr;   // [total_rows] sorted chunks of the ranking
     int total_rows = 0;
     void *d_scratch = nullptr;        // pseudo scratch (shared by the pseudo islands)
+    int16_t *d_cell_children = nullptr;   // child rows of the cellular cells (fused generations)
     unsigned long long *d_decoded = nullptr;
     int ring_rows = 0, max_N = 0, min_pair_rows = 0;
     cudaStream_t cap_stream = nullptr;
@@ -723,7 +730,8 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
         // both kinds present and each fits one batch: one fused decode launch
         std::vector<int> cel, pse;
         for (int i : ids) (S->kind[i] == 0 ? cel : pse).push_back(i);
-        if (!cel.empty() && !pse.empty() && (int)cel.size() <= kMaxBatch && (int)pse.size() <= kMaxBatch) {
+        if (!cel.empty() && !pse.empty() && (int)cel.size() <= kMaxBatch && (int)pse.size() <= kMaxBatch &&
+            S->d_cell_children) {
             IslandBatch cb, pb;
             memset(&cb, 0, sizeof(cb));
             memset(&pb, 0, sizeof(pb));
@@ -732,7 +740,7 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
             for (int t = 0; t < cb.count; ++t) cb.ref[t] = device_ref(S, cel[t]);
             for (int t = 0; t < pb.count; ++t) pb.ref[t] = device_ref(S, pse[t]);
             return launch_step_fused(S->inst, g, cb, S->rows, S->cols, pb, S->size[pse[0]], S->ld, S->d_scratch,
-                                     S->prm.decode_chunk, S->prm.block_threads, S->d_decoded, st);
+                                     S->d_cell_children, S->prm.decode_chunk, S->prm.block_threads, S->d_decoded, st);
         }
     }
     for (int kind = 0; kind < 2; ++kind) {
@@ -1031,8 +1039,14 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
     for (int i = 0; i < S->I; ++i) n_pseudo_islands += S->kind[i] == 1;
     if (max_pseudo > 0)
         S->d_scratch = alloc((size_t)pseudo_scratch_bytes(max_pseudo, S->ld, std::min(n_pseudo_islands, kMaxBatch)));
+    // child rows of the cellular cells, for generations of both kinds in one
+    // decode launch (at most kMaxBatch islands of each kind)
+    const int n_cellular_islands = S->I - n_pseudo_islands;
+    const bool fused = n_cellular_islands > 0 && n_pseudo_islands > 0 && n_cellular_islands <= kMaxBatch &&
+                       n_pseudo_islands <= kMaxBatch;
+    if (fused) S->d_cell_children = (int16_t *)alloc((size_t)n_cellular_islands * S->rows * S->cols * S->ld * 2);
     if (!S->d_desc || !S->d_cur || !S->d_gen || !S->d_counts || !S->d_decoded || !S->d_rank_keys ||
-        (max_pseudo > 0 && !S->d_scratch)) {
+        (max_pseudo > 0 && !S->d_scratch) || (fused && !S->d_cell_children)) {
         islands_free(S);
         return set_error(FFS_ENOMEM, "island state");
     }

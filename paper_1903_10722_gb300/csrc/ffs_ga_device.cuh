@@ -169,11 +169,14 @@ __device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, 
 // (lanes with !valid only keep the warp in lock step): draws, two binary
 // tournaments over the von Neumann neighbourhood (previous generation's
 // makespans), order crossover, swap mutation.  The child is built in the
-// cell's output row.  `wbits`: the warp's crossover mark (BYTES as in
-// warp_build_children).
+// cell's output row, or in `child_row` when that is given: then the cell
+// itself is copied to its output row (row and makespan), which the decoding
+// overwrites only if the child is better.  `wbits`: the warp's crossover
+// mark (BYTES as in warp_build_children).
 template <bool BYTES>
 __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const GaScalars &g, int n, int c, bool valid,
-                                                    int rows, int cols, int ld, uint32_t *wbits)
+                                                    int rows, int cols, int ld, uint32_t *wbits,
+                                                    int16_t *child_row = nullptr)
 {
     const int16_t *pin;
     const int32_t *msin;
@@ -183,7 +186,7 @@ __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const 
     resolve(ref, pin, msin, pout, msout, gen);
     ChildJob job;
     job.active = valid;
-    job.child = pout + (int64_t)c * ld;
+    job.child = child_row ? child_row : pout + (int64_t)c * ld;
     job.p1 = job.p2 = pin;
     job.l = job.r = 0;
     job.cross = false;
@@ -222,6 +225,10 @@ __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const 
         child[j] = t;
     }
     __syncwarp();
+    if (child_row) {   // warp-uniform
+        if (valid) msout[c] = msin[c];
+        warp_copy_rows(valid, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
+    }
 }
 
 // The other half: decode the child in the cell's output row and replace the
@@ -247,6 +254,31 @@ __device__ __forceinline__ void cellular_warp_decode(const DecodeLayout &Ls, con
         keep_old = !better;
     }
     warp_copy_rows(keep_old, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
+}
+
+// As cellular_warp_decode for a child bred into `child_row` (the cell was
+// already copied to its output row): decode the child and, iff it is
+// better, write it and its makespan over the copy.
+__device__ __forceinline__ void cellular_warp_decode_child(const DecodeLayout &Ls, const GaScalars &g,
+                                                           const IslandRef &ref, int c, bool valid, int ld,
+                                                           const int16_t *child_row, uint32_t *region, int T,
+                                                           const uint16_t *tab, WarpStageState *wst)
+{
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(ref, pin, msin, pout, msout, gen);
+    // lanes past the end decode a row of their island in lock step; nothing is written
+    const int32_t ms = decode_chromosome(Ls, valid ? child_row : pin + (int64_t)c * ld, region, T, tab, wst);
+    bool better = false;
+    if (valid) {
+        const int32_t old = msin[c];
+        better = ms >= 0 && (g.replace_le ? (uint32_t)ms <= (uint32_t)old : (uint32_t)ms < (uint32_t)old);
+        if (better) msout[c] = ms;
+    }
+    warp_copy_rows(better, child_row, pout + (int64_t)c * ld, ld);
 }
 
 // One cellular generation for the cell `c` of each lane: breeding, then
