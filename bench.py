@@ -667,8 +667,8 @@ def run_paper(args):
 
 # DRAM bytes (read + write) of one k_step_decode launch of scale_500x20 at
 # 384 threads, chunk 128, variant 3, from one ncu capture of the current
-# kernel (160.1 MB read + 28.4 MB written); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = 188_516_352
+# kernel (117.5 MB read + 12.1 MB written); other shapes report null.
+K_STEP_DECODE_DRAM_BYTES = 129_577_728
 
 
 def _shape_is(prm, threads, chunk, variant) -> bool:
