@@ -252,6 +252,12 @@ int ffs_pseudo_step_noalloc(const ffs_instance *inst, const ffs_params *prm, uin
  * a rows x cols torus, each pseudo island has pseudo_size rows (even).
  * ffs_islands_create allocates library-owned device memory, initialises
  * every island (ffs_population_init) and decodes it; generation = 0.
+ * Device memory: two row buffers and two makespan buffers per island
+ * (2 N ld 2 + 2 N 4 bytes), the rank order and ranking keys (12 N bytes),
+ * the pseudo scratch (ffs_pseudo_scratch_bytes of the largest pseudo
+ * island, for up to 16 pseudo islands at once) and, when both kinds are
+ * present with at most 16 islands of each, the cellular children of one
+ * generation (cells x ld x 2 bytes per cellular island).
  * ---------------------------------------------------------------------- */
 int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t n_cellular,
                        int32_t rows, int32_t cols, int32_t n_pseudo, int32_t pseudo_size,
