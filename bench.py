@@ -5,14 +5,16 @@ Workload (default ``scale_500x20``): 500 jobs x 20 stages, machines per stage
 uniform in [5, 10], processing times uniform in [1, 99] (instance seed 1);
 4 cellular islands on 128 x 128 tori + 4 pseudo islands of 16384 rows
 (131072 chromosomes of 500 int16 genes), GA seed 7.  A step is one
-generation of every island (fused cellular kernels, pseudo breed / decode /
-replace) followed by a ring migration of 2% (ranking + row copies), replayed
-from the library's CUDA graph.  ``value`` = exact makespan evaluations
+generation of every island (one breeding launch for the cellular cells and
+the pseudo pairs, one decode launch for all children, the pseudo pair
+replacement) followed by a ring migration of 2% (ranking + row copies),
+replayed from the library's CUDA graph.  ``value`` = exact makespan evaluations
 (children decoded) per second, counted by the library.
 
-Other keys: ``roofline`` for the dominant kernel (the fused cellular
-generation, integer-ALU bound; algorithmic ops per launch / its CUDA-event
-duration vs. SMs x 128 lanes x max SM clock), ``e2e`` (the same step with the
+Other keys: ``roofline`` for the dominant kernel (the decode launch,
+integer-ALU bound, timed with the breeding and replacement launches around
+it; algorithmic ops per launch / their CUDA-event duration vs. SMs x 128
+lanes x max SM clock), ``e2e`` (the same step with the
 populations uploaded from and downloaded to pinned host memory every step),
 ``cpu_baseline`` (the CPU oracle on a bounded sample), ``clocks`` (nvidia-smi
 sampled during the timed region).
@@ -288,10 +290,10 @@ def run_ours(args):
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
 
-    # ---- dominant kernel: the fused decode launch (all cellular cells and the
-    # pseudo children), replayed as in the step with its pseudo breed and replace
+    # ---- dominant kernel: the decode launch (all cellular and pseudo
+    # children), replayed as in the step with the breeding and replacement
     # launches (dry run: the state does not advance); CUDA events on the
-    # launching stream, so the time includes breed and replace ----
+    # launching stream, so the time includes breeding and replacement ----
     kernel_ms = []
     for r in range(max(3, min(args.steps, 10))):
         k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -361,7 +363,7 @@ def run_ours(args):
                      "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops,
                      "traffic": K_STEP_DECODE_DRAM_BYTES if _shape_is(prm, 384, 128, 3) else None,
                      "kernel": "k_step_decode (all cellular children: decode + replace; all pseudo children: decode), "
-                               "timed with the cellular and pseudo breed and the pseudo replace launches",
+                               "timed with the breeding launch (k_breed_dual) and the pseudo pair replacement",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": decodes_per_launch * ops_eval,
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
                      "launch_shape": ffs.ffs_decode_plan(inst, 2, prm.decode_chunk, prm.block_threads,

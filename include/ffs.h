@@ -454,8 +454,8 @@ int ffs_selftest_wait_timeout(int64_t limit_ns, int32_t *status, ffs_stream stre
 int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
 
 /* Launch one generation's kernels (kind 0: the cellular islands alone,
- * 1: the pseudo islands alone, 2: all islands -- pseudo breed, the fused
- * decode launch of all cellular cells and pseudo children, pseudo replace --
+ * 1: the pseudo islands alone, 2: all islands -- the breeding launch, the
+ * fused decode launch of all cellular and pseudo children, pseudo replace --
  * exactly as ffs_island_step does, migration and generation advance
  * excepted), without advancing the state: only the next-generation buffers
  * are rewritten (for timing and profiling).  Not with a surrogate attached.
