@@ -412,6 +412,7 @@ def run_batch(args):
     _apply_shape(prm, args)
     b = ffs.Batch(specs, prm, w["rows"], w["cols"])
     tuned = b.info() if args.no_autotune else ffs.ffs_batch_autotune(b, repeats=2)
+    tuned["variant"] = b.info()["variant"]
     stream = torch.cuda.current_stream()
     ffs.ffs_batch_step(b, args.warmup)
     torch.cuda.synchronize()

@@ -229,8 +229,7 @@ __global__ void k_pseudo_replace(GaScalars g, const __grid_constant__ IslandBatc
         msout[2 * k] = m[0];
         msout[2 * k + 1] = m[1];
     }
-    warp_copy_rows(valid, src[0], pout + (int64_t)(2 * k) * ld, ld);
-    warp_copy_rows(valid, src[1], pout + (int64_t)(2 * k + 1) * ld, ld);
+    warp_copy_row_pairs(valid, src[0], pout + (int64_t)(2 * k) * ld, src[1], pout + (int64_t)(2 * k + 1) * ld, ld);
 }
 
 // The breeding half of a cellular generation for every cell of a batch of

@@ -165,6 +165,44 @@ __device__ __forceinline__ void warp_copy_rows(bool active, const int16_t *src, 
 }
 
 
+// Two rows per active lane (s0 -> d0, s1 -> d1), four lanes at a time: the
+// loads of all eight rows are issued before their stores (no destination
+// row may overlap a source row of the same call).
+__device__ __forceinline__ void warp_copy_row_pairs(bool active, const int16_t *s0, int16_t *d0, const int16_t *s1,
+                                                    int16_t *d1, int ld)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = ld >> 3;
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, active);
+    while (todo) {
+        const int4 *src[8];
+        int4 *dst[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            src[2 * u] = src[2 * u + 1] = nullptr;
+            dst[2 * u] = dst[2 * u + 1] = nullptr;
+            if (todo) {   // warp-uniform
+                const int j = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                src[2 * u] = (const int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)s0, j);
+                dst[2 * u] = (int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)d0, j);
+                src[2 * u + 1] = (const int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)s1, j);
+                dst[2 * u + 1] = (int4 *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)d1, j);
+            }
+        }
+        for (int k = lane; k < q; k += 32) {
+            int4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (src[u]) v[u] = src[u][k];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (dst[u]) dst[u][k] = v[u];
+        }
+    }
+    __syncwarp();
+}
+
 // The breeding half of a cellular generation for the cell `c` of each lane
 // (lanes with !valid only keep the warp in lock step): draws, two binary
 // tournaments over the von Neumann neighbourhood (previous generation's
