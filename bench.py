@@ -450,7 +450,9 @@ def run_batch(args):
                    "chromosomes": w["count"] * cells, "launch_shape": tuned, "parallelism": f"replicas x{ws}"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": ops_gen / step_s / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s (int32 lane ops)", "frac": ops_gen / step_s / peak_ops, "traffic": None,
+                     "unit": "Tops/s (int32 lane ops)", "frac": ops_gen / step_s / peak_ops,
+                     "traffic": (K_BATCH_CELLULAR_DRAM_BYTES
+                                 if (tuned["threads"], tuned["chunk"], tuned["variant"]) == (512, 64, 3) else None),
                      "kernel": "k_batch_cellular (one persistent launch per generation; step time incl. "
                                "the counter reset and generation advance)"},
         "clocks": clock_info,
@@ -672,6 +674,11 @@ def run_paper(args):
 # 384 threads, chunk 128, variant 3, from one ncu capture of the current
 # kernel (117.5 MB read + 12.1 MB written); other shapes report null.
 K_STEP_DECODE_DRAM_BYTES = 129_577_728
+
+
+# DRAM bytes of one k_batch_cellular launch of batch_256 at 512 threads,
+# chunk 64, variant 3 (ncu: 223.0 MB read + 178.8 MB written).
+K_BATCH_CELLULAR_DRAM_BYTES = 401_807_616
 
 
 def _shape_is(prm, threads, chunk, variant) -> bool:
