@@ -174,6 +174,22 @@ def test_islands_ring_uneven_three(gpu):
     _islands_vs_oracle(gpu, spec, prm, oprm, 2, 5, 4, 1, 30, 12, 3, 1, check_every=3)
 
 
+def test_islands_fused_generation_flags(gpu):
+    """Both kinds in one generation (breeding launch + decode launch) with the
+    replace-if-not-worse flag and the children-always-replace flag."""
+    spec = make_instance(40, 6, 2, 4, seed=14)
+    prm, oprm = _params(gpu, seed=21, le=True, always=True, cell_pm=0.4, mode=1, gap=3)
+    _islands_vs_oracle(gpu, spec, prm, oprm, 2, 8, 8, 2, 48, 9, 3, 1, check_every=3)
+
+
+def test_islands_more_than_one_batch_of_a_kind(gpu):
+    """17 cellular islands (more than one launch batch) beside a pseudo island:
+    generations take the per-kind launches instead of the fused pair."""
+    spec = make_instance(16, 3, 1, 3, seed=15)
+    prm, oprm = _params(gpu, seed=3, mode=1, gap=2, ring=(10, 100))
+    _islands_vs_oracle(gpu, spec, prm, oprm, 17, 4, 4, 1, 16, 4, 2, 1, check_every=2)
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_islands_migration_full_size_islands(gpu, mode):
     """Migration every generation between islands of 16384 rows (128 x 128
