@@ -314,8 +314,14 @@ def run_ours(args):
                                                "min3_max3", "add_max", "min_max+imad", "min_max+fmnmx"))}
 
     # ---- e2e: the same steps with populations from / to pinned host memory ----
-    # all islands' rows in one host buffer with the library's row stride: each
-    # step is one set_all (H2D), the generation, one get_all (D2H) and a sync
+    # all islands' rows in one host buffer with the library's row stride.
+    # Every step uploads every island's rows (ffs_islands_set), runs the
+    # generation and downloads every island's rows and makespans
+    # (ffs_islands_get); each island's upload for step k + 1 reads what its
+    # download of step k wrote (ordered by events), so the round trip through
+    # host memory is kept, while island i's upload overlaps island i + 1's
+    # download on the other copy stream (the host link carries both
+    # directions at once)
     total_rows = sum(isl.sizes)
     host_pop = torch.empty((total_rows, isl.ld), dtype=torch.int16).pin_memory()
     host_ms = torch.empty(total_rows, dtype=torch.int32).pin_memory()
@@ -324,16 +330,35 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 10))
     h2d = host_pop.numel() * 2
     d2h = h2d + host_ms.numel() * 4
+    offs = [0]
+    for size in isl.sizes:
+        offs.append(offs[-1] + size)
+    hp = [host_pop[offs[i]:offs[i + 1]] for i in range(isl.n_islands)]
+    hm = [host_ms[offs[i]:offs[i + 1]] for i in range(isl.n_islands)]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    down_done = [None] * isl.n_islands
     e_d0 = ffs.ffs_islands_decoded(isl)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ffs.ffs_islands_set_all(isl, host_pop, isl.ld, None)
-        ffs.ffs_island_step(isl, -1, 1)
-        ffs.ffs_islands_get_all(isl, host_pop, isl.ld, host_ms)
-        torch.cuda.synchronize()
+        for i in range(isl.n_islands):
+            if down_done[i] is not None:
+                up.wait_event(down_done[i])
+            ffs.ffs_islands_set(isl, i, hp[i], isl.ld, None, stream=up)
+        uploaded = torch.cuda.Event()
+        uploaded.record(up)
+        stream.wait_event(uploaded)
+        ffs.ffs_island_step(isl, -1, 1, stream=stream)
+        stepped = torch.cuda.Event()
+        stepped.record(stream)
+        down.wait_event(stepped)
+        for i in range(isl.n_islands):
+            ffs.ffs_islands_get(isl, i, hp[i], isl.ld, hm[i], stream=down)
+            down_done[i] = torch.cuda.Event()
+            down_done[i].record(down)
+    torch.cuda.synchronize()
     e2e_time = time.perf_counter() - t0
     e2e_evals = ffs.ffs_islands_decoded(isl) - e_d0
 
