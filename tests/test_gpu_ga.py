@@ -246,12 +246,16 @@ def test_explicit_migrate_and_set_get(gpu):
         gpu.ffs_island_step(isl, -1, 1)
 
 
-def test_scale_500x20_sampled_generation(gpu):
+@pytest.mark.parametrize("shape", [(0, 0, 0), (384, 128, 3)], ids=["library", "bench"])
+def test_scale_500x20_sampled_generation(gpu, shape):
     """4 x 128^2 cellular + 4 x 16384 pseudo at 500 x 20: one generation of
-    every island, checked on sampled cells and pairs with the oracle."""
+    every island, checked on sampled cells and pairs with the oracle, at the
+    library's launch shape and at the one bench.py times (384 threads,
+    chunk 128, variant 3)."""
     spec = make_instance(500, 20, 5, 10, seed=1)
     o, g = _pair(spec, gpu)
-    prm, oprm = _params(gpu, mode=0, gap=0)
+    threads, chunk, variant = shape
+    prm, oprm = _params(gpu, mode=0, gap=0, decode_variant=variant, chunk=chunk, threads=threads)
     isl = gpu.Islands(g, prm, 4, 128, 128, 4, 16384)
     before = [gpu.island_tensors(isl, i) for i in range(isl.n_islands)]
     before = [(p.cpu().numpy(), m.cpu().numpy().astype(np.int64)) for p, m in before]
