@@ -19,6 +19,8 @@ in for them):
                p ~ U[1,5] (Section 5, Table 1), for context runs
   paper_obj_300x4  the same shape with Table 1's release and due times
                and WT = 100 (objective WT * total tardiness + C_max)
+  assign_500x20  the paper's genotype (machine-assignment strings of 500 x 20
+               genes) on unrelated machines: M_s ~ U[5,10], P_jsm ~ U[1,99]
 """
 from __future__ import annotations
 
@@ -85,6 +87,36 @@ def random_population(n: int, N: int, ld: int | None = None, seed: int = 0) -> n
     pop = np.zeros((N, ld), dtype=np.int16)
     keys = rng.random((N, n))
     pop[:, :n] = np.argsort(keys, axis=1).astype(np.int16)
+    return pop
+
+
+@dataclass
+class AssignSpec:
+    n: int
+    S: int
+    M: np.ndarray     # int32 [S]
+    p_u: np.ndarray   # int32 [n][sum M]: job j, stage s, machine m at [j][M_0 + ... + M_{s-1} + m]
+
+
+def make_assign_instance(n: int, S: int, m_lo: int, m_hi: int, p_lo: int = 1, p_hi: int = 99,
+                         seed: int = 1) -> AssignSpec:
+    """Unrelated machines: M_s ~ U{m_lo..m_hi}, then every P_jsm ~ U{p_lo..p_hi}
+    (job-major, stage, machine), drawn in that order."""
+    rng = np.random.default_rng(seed)
+    M = rng.integers(m_lo, m_hi + 1, size=S, dtype=np.int64).astype(np.int32)
+    p_u = rng.integers(p_lo, p_hi + 1, size=(n, int(M.sum())), dtype=np.int64).astype(np.int32)
+    return AssignSpec(n, S, M, p_u)
+
+
+def random_assignments(n: int, S: int, M, N: int, ld: int | None = None, seed: int = 0) -> np.ndarray:
+    """N random machine-assignment strings (gene j*S + s ~ U{0..M_s - 1}) as
+    int16 rows of length ld (padding = 0)."""
+    M = np.asarray(M, dtype=np.int64)
+    ld = ld if ld is not None else ((n * S + 7) // 8) * 8
+    rng = np.random.default_rng(seed)
+    pop = np.zeros((N, ld), dtype=np.int16)
+    u = rng.random((N, n, S))
+    pop[:, :n * S] = np.floor(u * M[None, None, :]).astype(np.int16).reshape(N, n * S)
     return pop
 
 

@@ -105,6 +105,12 @@ def _load():
         lib.orc_bruteforce_obj.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, _i64p,
                                            _i16p]
         lib.orc_bruteforce_obj.restype = ctypes.c_int64
+        lib.orc_decode_assign.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p, _i16p,
+                                          _i64p]
+        lib.orc_decode_assign.restype = ctypes.c_int64
+        lib.orc_eval_population_assign.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p,
+                                                   _i16p, ctypes.c_int64, ctypes.c_int64, _i64p]
+        lib.orc_eval_population_assign.restype = None
         lib.orc_eval_population.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                             _i16p, ctypes.c_int64, ctypes.c_int64, _i64p]
         lib.orc_eval_population.restype = None
@@ -252,6 +258,52 @@ def eval_population(inst: Instance, pop: np.ndarray) -> np.ndarray:
     out = np.zeros(N, dtype=np.int64)
     lib.orc_eval_population_obj(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
                                 inst.obj_addr(), _ptr(pop, ctypes.c_int16), N, ld, _ptr(out, ctypes.c_int64))
+    return out
+
+
+class AssignInstance:
+    """An instance with unrelated machines for the paper's genotype (Section
+    3, P_jsm; Section 4.1): p_u[j][off_s + m] = time of job j at stage s on
+    machine m, off_s = M_0 + ... + M_{s-1}; optional release / due times and
+    WT as in Instance."""
+
+    def __init__(self, n, S, M, p_u, release=None, due=None, wt=0):
+        self.n, self.S, self.wt = int(n), int(S), int(wt)
+        self.M = np.ascontiguousarray(M, dtype=np.int32)
+        self.W = int(self.M.sum())
+        self.p_u = np.ascontiguousarray(p_u, dtype=np.int32).reshape(self.n, self.W)
+        self.release = None if release is None else np.ascontiguousarray(release, dtype=np.int32).reshape(self.n)
+        self.due = None if due is None else np.ascontiguousarray(due, dtype=np.int32).reshape(self.n)
+        self._obj = None
+        if self.release is not None or self.due is not None:
+            self._obj = _Objective(
+                _ptr(self.release, ctypes.c_int32) if self.release is not None else None,
+                _ptr(self.due, ctypes.c_int32) if self.due is not None else None, self.wt)
+
+    def obj_addr(self):
+        return ctypes.addressof(self._obj) if self._obj is not None else None
+
+
+def decode_assign(inst: AssignInstance, genes, gantt: bool = False):
+    """Objective of one machine-assignment string (n*S genes, gene j*S + s =
+    machine of job j at stage s; -1 if a gene is out of range); with gantt,
+    also the (stage, job, machine, start, end) records."""
+    lib = _load()
+    genes = np.ascontiguousarray(genes, dtype=np.int16)
+    g = np.zeros((inst.n * inst.S, 5), dtype=np.int64) if gantt else None
+    v = lib.orc_decode_assign(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p_u, ctypes.c_int32),
+                              inst.obj_addr(), _ptr(genes, ctypes.c_int16),
+                              _ptr(g, ctypes.c_int64) if gantt else None)
+    return (int(v), g) if gantt else int(v)
+
+
+def eval_population_assign(inst: AssignInstance, pop: np.ndarray) -> np.ndarray:
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    N, ld = pop.shape
+    out = np.zeros(N, dtype=np.int64)
+    lib.orc_eval_population_assign(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p_u, ctypes.c_int32),
+                                   inst.obj_addr(), _ptr(pop, ctypes.c_int16), N, ld, _ptr(out, ctypes.c_int64))
     return out
 
 

@@ -197,6 +197,78 @@ int64_t orc_decode(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
     return orc_decode_obj(n, S, M, p, NULL, perm, gantt);
 }
 
+/* The paper's genotype (Section 4.1, genotype level; Section 3, P_jsm): a
+ * string of n*S genes, gene i = the index (0-based) of the target machine of
+ * job floor(i/S) at stage i mod S, on unrelated machines: p_u is [n][W],
+ * W = M_0 + ... + M_{S-1}, the time of job j at stage s on machine m at
+ * p_u[j*W + off_s + m], off_s = M_0 + ... + M_{s-1}.
+ *
+ * Sequencing (the paper leaves it unstated): every machine processes the
+ * jobs assigned to it in order of arrival -- stage 1: release time R_j (0
+ * without release times), later stages: completion at the previous stage
+ * -- ties by job index; a job starts at max(machine free time, arrival).
+ * This is the definition above with the machine fixed by the gene instead
+ * of chosen as the earliest free one, and stage 1 in (R_j, j) order.
+ *
+ * Objective as orc_decode_obj.  Returns -1 if a gene is outside [0, M_s).
+ * gantt as orc_decode_obj. */
+int64_t orc_decode_assign(int32_t n, int32_t S, const int32_t *M, const int32_t *p_u,
+                          const orc_objective *obj, const int16_t *genes, int64_t *gantt)
+{
+    for (int32_t j = 0; j < n; ++j)
+        for (int32_t s = 0; s < S; ++s)
+            if (genes[(int64_t)j * S + s] < 0 || genes[(int64_t)j * S + s] >= M[s]) return -1;
+    int64_t W = 0;
+    for (int32_t s = 0; s < S; ++s) W += M[s];
+    int64_t *arrive = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *done = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    orc_pair *pairs = (orc_pair *)malloc((size_t)n * sizeof(orc_pair));
+    const int32_t *release = obj ? obj->release : NULL;
+    for (int32_t j = 0; j < n; ++j) arrive[j] = release ? (int64_t)release[j] : 0;
+    int64_t rec = 0, off = 0;
+    for (int32_t s = 0; s < S; ++s) {
+        for (int32_t j = 0; j < n; ++j) { pairs[j].c = arrive[j]; pairs[j].j = j; }
+        qsort(pairs, (size_t)n, sizeof(orc_pair), orc_pair_cmp);
+        int64_t *free_at = (int64_t *)calloc((size_t)M[s], sizeof(int64_t));
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t j = pairs[k].j;
+            const int32_t m = genes[(int64_t)j * S + s];
+            const int64_t start = free_at[m] > arrive[j] ? free_at[m] : arrive[j];
+            const int64_t end = start + (int64_t)p_u[(int64_t)j * W + off + m];
+            done[j] = end;
+            free_at[m] = end;
+            if (gantt) {
+                gantt[rec * 5 + 0] = s;
+                gantt[rec * 5 + 1] = j;
+                gantt[rec * 5 + 2] = m;
+                gantt[rec * 5 + 3] = start;
+                gantt[rec * 5 + 4] = end;
+                ++rec;
+            }
+        }
+        free(free_at);
+        off += M[s];
+        int64_t *t = arrive; arrive = done; done = t;
+    }
+    int64_t cmax = 0;
+    for (int32_t j = 0; j < n; ++j) if (arrive[j] > cmax) cmax = arrive[j];
+    int64_t total_tardiness = 0;
+    if (obj && obj->due)
+        for (int32_t j = 0; j < n; ++j)
+            if (arrive[j] > obj->due[j]) total_tardiness += arrive[j] - obj->due[j];
+    free(arrive); free(done); free(pairs);
+    return (obj && obj->due ? obj->wt * total_tardiness : 0) + cmax;
+}
+
+/* orc_decode_assign of every row of a population [N][ld] of genes. */
+void orc_eval_population_assign(int32_t n, int32_t S, const int32_t *M, const int32_t *p_u,
+                                const orc_objective *obj, const int16_t *pop, int64_t N, int64_t ld,
+                                int64_t *out)
+{
+    for (int64_t i = 0; i < N; ++i)
+        out[i] = orc_decode_assign(n, S, M, p_u, obj, pop + i * ld, NULL);
+}
+
 /* Objective of every row of a population [N][ld] (int16 genes); obj NULL:
  * the makespan. */
 void orc_eval_population_obj(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
