@@ -626,6 +626,48 @@ def run_decode(args):
     return 0
 
 
+def run_assign(args):
+    """The paper's genotype: objectives of N random machine-assignment strings
+    (500 jobs x 20 stages = 10000 genes per row) on unrelated machines
+    (M_s ~ U[5,10], P_jsm ~ U[1,99]); one ffs_assign_eval per step; one JSON
+    line.  Algorithmic bytes per row: its 2 n S bytes of genes, read once."""
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    from ffs_workloads import make_assign_instance, random_assignments
+
+    torch.cuda.set_device(0)
+    spec = make_assign_instance(500, 20, 5, 10, seed=1)
+    inst = ffs.AssignInstance(spec.n, spec.S, spec.M, spec.p_u)
+    N = 65536
+    pop = torch.from_numpy(random_assignments(spec.n, spec.S, spec.M, N, seed=11)).cuda()
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        ffs.ffs_assign_eval(inst, pop, N, inst.ld, out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_assign_eval(inst, pop, N, inst.ld, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    peaks, peak_kind = _peaks()
+    gbs = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_per_launch = N * spec.n * spec.S * 2
+    line = {"metric": "exact FFS objective evals/sec (machine-assignment genotype)", "workload": "assign_500x20",
+            "value": N / (ms / 1000.0), "unit": "evals/s", "ms_per_step": ms, "steps": args.steps,
+            "rows": N, "genes_per_row": spec.n * spec.S, "machines_per_stage": [int(spec.M.min()), int(spec.M.max())],
+            "roofline": {"bound": "latency", "achieved": bytes_per_launch / (ms / 1000.0) / 1e9,
+                         "peak": gbs, "unit": "GB/s", "frac": bytes_per_launch / (ms / 1000.0) / 1e9 / gbs,
+                         "kernel": "k_eval_assign", "peak_basis": f"HBM copy ({peak_kind})"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_paper(args):
     """The paper's Section 5 experiments on a synthetic Table 1 instance
     (300 jobs x 4 stages x 2 machines, p ~ U[1,5], release and due times,
@@ -747,6 +789,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "decode_500x20":
         return run_decode(args)
+    if args.workload == "assign_500x20":
+        return run_assign(args)
     if args.workload == "paper_obj_300x4":
         return run_paper(args)
     return run_ours(args)

@@ -81,6 +81,39 @@ int ffs_instance_create_objective(int32_t n_jobs, int32_t n_stages, const int32_
 int ffs_instance_destroy(ffs_instance *inst);
 
 /* ------------------------------------------------------------------------
+ * The paper's own genotype (Section 4.1, genotype level; Section 3, P_jsm):
+ * a string of n*S genes per row, gene j*S + s = the index (0-based) of the
+ * machine that processes job j at stage s, on unrelated machines.
+ *
+ * ffs_assign_instance_create copies the instance: machines_per_stage[S]
+ * (1..32), proc_time[n][W] int32 with W = sum_s M_s, the time of job j at
+ * stage s on machine m at proc_time[j*W + M_0 + ... + M_{s-1} + m], every
+ * time in [1, 65535]; release[n] and due[n] (host, nullable, >= 0) and WT as
+ * in ffs_instance_create_objective.  FFS_EOVERFLOW when the latest possible
+ * completion (max release + sum over jobs and stages of the slowest
+ * machine) does not fit the key, or the objective bound does not fit int32.
+ * Allocates library-owned device memory (the instance and a stream scratch
+ * of up to 1 GiB); synchronous.
+ *
+ * ffs_assign_eval: objective[i] of row i of pop (device int16[N][ld], ld a
+ * multiple of 8 and >= n*S; objective device int32[N]).  Sequencing, which
+ * the paper leaves unstated: every machine processes the jobs assigned to it
+ * in order of arrival -- stage 1: release time (0 without), later stages:
+ * completion at the previous stage -- ties by job index; a job starts at
+ * max(machine free time, arrival).  objective = C_max (+ WT * total
+ * tardiness with due times); -1 for a row with a gene outside [0, M_s).
+ * N = 0 is a no-op.  Asynchronous on `stream`; calls on one instance must
+ * not overlap on the GPU (they share the stream scratch).
+ * ---------------------------------------------------------------------- */
+typedef struct ffs_assign_instance ffs_assign_instance;
+int ffs_assign_instance_create(int32_t n_jobs, int32_t n_stages, const int32_t *machines_per_stage,
+                               const int32_t *proc_time, const int32_t *release, const int32_t *due, int32_t wt,
+                               ffs_assign_instance **out);
+int ffs_assign_instance_destroy(ffs_assign_instance *inst);
+int ffs_assign_eval(const ffs_assign_instance *inst, const int16_t *pop, int64_t N, int32_t ld, int32_t *objective,
+                    ffs_stream stream);
+
+/* ------------------------------------------------------------------------
  * Batched makespan evaluation (the decoder).  Each row is decoded by
  * stage-wise list scheduling: stage 0 takes the jobs in row order; every
  * later stage takes them in ascending (completion time at the previous

@@ -53,6 +53,9 @@ _SIGS = [
     ("ffs_instance_create", _i32, [_i32, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
     ("ffs_instance_create_objective", _i32, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
     ("ffs_instance_destroy", _i32, [_vp]),
+    ("ffs_assign_instance_create", _i32, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
+    ("ffs_assign_instance_destroy", _i32, [_vp]),
+    ("ffs_assign_eval", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ffs_population_eval", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     ("ffs_population_eval_tuned", _i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i32, _i32, _vp]),
     ("ffs_population_eval_host", _i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
@@ -218,6 +221,47 @@ def ffs_instance_create(n, S, M, p) -> Instance:
 
 def ffs_instance_create_objective(n, S, M, p, release, due, wt) -> Instance:
     return Instance(n, S, M, p, release=release, due=due, wt=wt)
+
+
+class AssignInstance:
+    """Owner of an ffs_assign_instance handle: the paper's genotype (n*S
+    machine-assignment genes per row) on unrelated machines, p_u[j][off_s + m]
+    (Section 3, P_jsm; Section 4.1)."""
+
+    def __init__(self, n: int, S: int, M, p_u, release=None, due=None, wt: int = 0):
+        import numpy as np
+        self.n, self.S = int(n), int(S)
+        self.M = np.ascontiguousarray(M, dtype=np.int32)
+        self.W = int(self.M.sum())
+        self.p_u = np.ascontiguousarray(p_u, dtype=np.int32).reshape(self.n, self.W)
+        self.release = None if release is None else np.ascontiguousarray(release, dtype=np.int32).reshape(self.n)
+        self.due = None if due is None else np.ascontiguousarray(due, dtype=np.int32).reshape(self.n)
+        self.wt = int(wt)
+        h = _vp()
+        _check(load().ffs_assign_instance_create(
+            self.n, self.S, self.M.ctypes.data, self.p_u.ctypes.data,
+            None if self.release is None else self.release.ctypes.data,
+            None if self.due is None else self.due.ctypes.data, self.wt, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def ld(self) -> int:
+        return (self.n * self.S + 7) // 8 * 8
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ffs_assign_instance_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ffs_assign_eval(inst: AssignInstance, pop, N: int, ld: int, objective, stream=None):
+    _check(load().ffs_assign_eval(inst.handle, _ptr(pop), N, ld, _ptr(objective), _stream(stream)))
 
 
 def ffs_population_eval(inst: Instance, pop, N: int, ld: int, makespan, stream=None):

@@ -1,0 +1,267 @@
+// ffs_assign.cu -- exact evaluation of the paper's own genotype: strings of
+// n*S genes, gene j*S + s = the machine of job j at stage s (Section 4.1,
+// genotype level), on unrelated machines P_jsm (Section 3).
+//
+// Sequencing, which the paper leaves unstated: every machine processes the
+// jobs assigned to it in order of arrival (stage 1: release time R_j, later
+// stages: completion at the previous stage), ties by job index; a job starts
+// at max(machine free time, arrival).  Objective: C_max, plus WT * sum_j
+// max(0, C_j - D_j) with due times.
+//
+// One thread decodes one string.  A stage's arrivals are the machines' job
+// streams of the previous stage merged in (completion, job) order: every
+// stream is already in that order (a machine completes its jobs one after
+// the other, processing times >= 1), so the merge takes the smallest head
+// key at each step and never sorts.  Keys are completion << SH | (job+1) << 1
+// as in the permutation decoder.  The streams live in a per-thread scratch of
+// 2n keys in global memory; the per-machine counters in local memory.
+#include <algorithm>
+#include <vector>
+
+#include "ffs_internal.cuh"
+
+namespace fgpu {
+
+constexpr int kAssignMaxM = 32;        // machines per stage
+constexpr int kAssignThreads = 128;
+constexpr size_t kAssignScratchCap = size_t(1) << 30;   // bytes of stream scratch at most
+
+struct AssignView {
+    int32_t n, S, W, SH;
+    uint32_t wt;
+    const int32_t *M;        // [S]
+    const int32_t *off;      // [S] M_0 + ... + M_{s-1}
+    const uint16_t *p;       // [n][W]
+    const uint32_t *order0;  // [n] stage-1 arrival keys R_j << SH | (j+1) << 1, ascending
+    const uint32_t *due;     // [n] or NULL
+};
+
+__global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, const int16_t *__restrict__ pop,
+                                                                int64_t N, int ld, int32_t *__restrict__ out,
+                                                                uint32_t *scratch)
+{
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = V.n, S = V.S;
+    const uint32_t SH = (uint32_t)V.SH, idmask = ((1u << SH) - 1u) & ~1u;
+    uint32_t *bufA = scratch + tid * 2 * (int64_t)n, *bufB = bufA + n;
+    // input runs (the previous stage's machine streams) and output streams
+    uint32_t hk[kAssignMaxM];
+    int pos[kAssignMaxM], endp[kAssignMaxM], cnt[kAssignMaxM], fill[kAssignMaxM];
+    uint32_t freeT[kAssignMaxM];
+    for (int64_t r = tid; r < N; r += T) {
+        const int16_t *row = pop + r * ld;
+        bool bad = false;
+        const uint32_t *in = V.order0;
+        int R = 1;
+        pos[0] = 0;
+        endp[0] = n;
+        hk[0] = in[0];
+        uint32_t *outb = bufA;
+        uint32_t cmax = 0, tard = 0;
+        for (int s = 0; s < S; ++s) {
+            const int Ms = V.M[s], off = V.off[s];
+            const bool last = s == S - 1;
+            for (int m = 0; m < Ms; ++m) cnt[m] = 0;
+            for (int j = 0; j < n; ++j) {
+                int g = row[(int64_t)j * S + s];
+                if ((unsigned)g >= (unsigned)Ms) {
+                    bad = true;
+                    g = 0;   // decoded as machine 0 (memory-safe); the row reports -1
+                }
+                ++cnt[g];
+            }
+            for (int m = 0, acc = 0; m < Ms; ++m) {
+                fill[m] = acc;
+                acc += cnt[m];
+                freeT[m] = 0u;
+            }
+            for (int k = 0; k < n; ++k) {
+                // the next arrival: the smallest head key of the input runs
+                int rb = 0;
+                uint32_t kb = hk[0];
+                for (int q = 1; q < R; ++q)
+                    if (hk[q] < kb) {
+                        kb = hk[q];
+                        rb = q;
+                    }
+                const int p1 = pos[rb] + 1;
+                pos[rb] = p1;
+                hk[rb] = p1 < endp[rb] ? in[p1] : 0xFFFFFFFFu;
+                const int j = (int)((kb & idmask) >> 1) - 1;
+                int m = row[(int64_t)j * S + s];
+                if ((unsigned)m >= (unsigned)Ms) m = 0;
+                const uint32_t c = max(freeT[m], kb >> SH) + (uint32_t)V.p[(int64_t)j * V.W + off + m];
+                freeT[m] = c;
+                if (!last) {
+                    outb[fill[m]++] = (c << SH) | ((uint32_t)(j + 1) << 1);
+                } else {
+                    cmax = max(cmax, c);
+                    if (V.due && c > V.due[j]) tard += c - V.due[j];
+                }
+            }
+            if (!last) {
+                // the next stage merges this stage's machine streams
+                in = outb;
+                R = Ms;
+                for (int m = 0, acc = 0; m < Ms; ++m) {
+                    pos[m] = acc;
+                    endp[m] = acc + cnt[m];
+                    hk[m] = cnt[m] > 0 ? in[acc] : 0xFFFFFFFFu;
+                    acc += cnt[m];
+                }
+                outb = outb == bufA ? bufB : bufA;
+            }
+        }
+        out[r] = bad ? -1 : (int32_t)(cmax + V.wt * tard);
+    }
+}
+
+}  // namespace fgpu
+
+using namespace fgpu;
+
+struct ffs_assign_instance {
+    int n = 0, S = 0, W = 0, SH = 0;
+    int32_t wt = 0;
+    int32_t *d_M = nullptr, *d_off = nullptr;
+    uint16_t *d_p = nullptr;
+    uint32_t *d_order0 = nullptr, *d_due = nullptr;
+    uint32_t *d_scratch = nullptr;
+    int64_t scratch_threads = 0;   // threads the scratch serves (a multiple of kAssignThreads)
+    int num_sms = 0;
+};
+
+int ffs_assign_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p_u, const int32_t *release,
+                               const int32_t *due, int32_t wt, ffs_assign_instance **out)
+{
+    clear_error();
+    if (!out || !M || !p_u) return set_error(FFS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1 || n > 32767) return set_error(FFS_EINVAL, "n_jobs = %d outside [1, 32767]", n);
+    if (S < 1 || S > kMaxStages) return set_error(FFS_EINVAL, "n_stages = %d outside [1, %d]", S, kMaxStages);
+    if ((int64_t)n * S > (int64_t(1) << 28)) return set_error(FFS_EUNSUPPORTED, "n * S = %lld genes", (long long)n * S);
+    if (due && wt < 0) return set_error(FFS_EINVAL, "tardiness weight %d < 0", wt);
+    int W = 0;
+    for (int s = 0; s < S; ++s) {
+        if (M[s] < 1) return set_error(FFS_EINVAL, "machines_per_stage[%d] = %d < 1", s, M[s]);
+        if (M[s] > kAssignMaxM) return set_error(FFS_EUNSUPPORTED, "stage %d: %d machines (> %d)", s, M[s], kAssignMaxM);
+        W += M[s];
+    }
+    // the latest completion: max release + the sum over jobs and stages of the slowest machine
+    int64_t horizon = 0, max_rel = 0;
+    for (int j = 0; j < n; ++j) {
+        int off = 0;
+        for (int s = 0; s < S; ++s) {
+            int64_t worst = 0;
+            for (int m = 0; m < M[s]; ++m) {
+                const int32_t v = p_u[(int64_t)j * W + off + m];
+                if (v < 1) return set_error(FFS_EINVAL, "proc_time[%d][%d][%d] = %d < 1", j, s, m, v);
+                if (v > 65535) return set_error(FFS_EUNSUPPORTED, "proc_time[%d][%d][%d] = %d > 65535", j, s, m, v);
+                worst = std::max<int64_t>(worst, v);
+            }
+            horizon += worst;
+            off += M[s];
+        }
+    }
+    for (int j = 0; release && j < n; ++j) {
+        if (release[j] < 0) return set_error(FFS_EINVAL, "release[%d] = %d < 0", j, release[j]);
+        max_rel = std::max<int64_t>(max_rel, release[j]);
+    }
+    for (int j = 0; due && j < n; ++j)
+        if (due[j] < 0) return set_error(FFS_EINVAL, "due[%d] = %d < 0", j, due[j]);
+    horizon += max_rel;
+    int bits = 0;
+    while ((1 << bits) <= n) ++bits;
+    const int SH = bits + 1;
+    if (horizon >= (int64_t(1) << (32 - SH)))
+        return set_error(FFS_EOVERFLOW, "latest completion bound %lld needs more than %d bits of key",
+                         (long long)horizon, 32 - SH);
+    if ((due ? (int64_t)wt * n * horizon : 0) + horizon > INT32_MAX)
+        return set_error(FFS_EOVERFLOW, "objective bound exceeds int32");
+
+    ffs_assign_instance *A = new ffs_assign_instance();
+    A->n = n;
+    A->S = S;
+    A->W = W;
+    A->SH = SH;
+    A->wt = due ? wt : 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&A->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<int32_t> off(S);
+    for (int s = 0, acc = 0; s < S; ++s) {
+        off[s] = acc;
+        acc += M[s];
+    }
+    std::vector<uint16_t> p16((size_t)n * W);
+    for (size_t i = 0; i < p16.size(); ++i) p16[i] = (uint16_t)p_u[i];
+    std::vector<uint32_t> order0(n);
+    for (int j = 0; j < n; ++j)
+        order0[j] = ((uint32_t)(release ? release[j] : 0) << SH) | ((uint32_t)(j + 1) << 1);
+    std::sort(order0.begin(), order0.end());   // (R_j, j) ascending: the stage-1 arrival order
+    // scratch: 2n keys per thread, for two blocks per SM, at most kAssignScratchCap bytes
+    int64_t threads = (int64_t)A->num_sms * 2 * kAssignThreads;
+    const int64_t per = (int64_t)2 * n * 4;
+    threads = std::min<int64_t>(threads, (int64_t)(kAssignScratchCap / per) / kAssignThreads * kAssignThreads);
+    if (threads < kAssignThreads) threads = kAssignThreads;
+    A->scratch_threads = threads;
+    bool ok = cudaMalloc(&A->d_M, 4 * S) == cudaSuccess && cudaMalloc(&A->d_off, 4 * S) == cudaSuccess &&
+              cudaMalloc(&A->d_p, p16.size() * 2) == cudaSuccess && cudaMalloc(&A->d_order0, 4 * n) == cudaSuccess &&
+              (!due || cudaMalloc(&A->d_due, 4 * n) == cudaSuccess) &&
+              cudaMalloc(&A->d_scratch, (size_t)threads * per) == cudaSuccess;
+    ok = ok && cudaMemcpy(A->d_M, M, 4 * S, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A->d_off, off.data(), 4 * S, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A->d_p, p16.data(), p16.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A->d_order0, order0.data(), 4 * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         (!due || cudaMemcpy(A->d_due, due, 4 * n, cudaMemcpyHostToDevice) == cudaSuccess);
+    if (!ok) {
+        (void)cudaGetLastError();
+        ffs_assign_instance_destroy(A);
+        return set_error(FFS_ENOMEM, "assignment instance device buffers");
+    }
+    *out = A;
+    return FFS_OK;
+}
+
+int ffs_assign_instance_destroy(ffs_assign_instance *A)
+{
+    if (!A) return FFS_OK;
+    cudaFree(A->d_M);
+    cudaFree(A->d_off);
+    cudaFree(A->d_p);
+    cudaFree(A->d_order0);
+    cudaFree(A->d_due);
+    cudaFree(A->d_scratch);
+    delete A;
+    return FFS_OK;
+}
+
+int ffs_assign_eval(const ffs_assign_instance *A, const int16_t *pop, int64_t N, int32_t ld, int32_t *objective,
+                    ffs_stream stream)
+{
+    clear_error();
+    if (!A) return set_error(FFS_EINVAL, "NULL instance");
+    if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
+    if (N == 0) return FFS_OK;
+    if (!pop || !objective) return set_error(FFS_EINVAL, "NULL population or output");
+    if ((int64_t)ld < (int64_t)A->n * A->S || (ld & 7))
+        return set_error(FFS_EINVAL, "ld = %d must be >= n * S = %lld and a multiple of 8", ld,
+                         (long long)A->n * A->S);
+    AssignView V;
+    V.n = A->n;
+    V.S = A->S;
+    V.W = A->W;
+    V.SH = A->SH;
+    V.wt = (uint32_t)A->wt;
+    V.M = A->d_M;
+    V.off = A->d_off;
+    V.p = A->d_p;
+    V.order0 = A->d_order0;
+    V.due = A->d_due;
+    const int64_t want = (N + kAssignThreads - 1) / kAssignThreads;
+    const int grid = (int)std::min<int64_t>(want, A->scratch_threads / kAssignThreads);
+    k_eval_assign<<<grid, kAssignThreads, 0, (cudaStream_t)stream>>>(V, pop, N, ld, objective, A->d_scratch);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
