@@ -14,7 +14,8 @@
 // the other, processing times >= 1), so the merge takes the smallest head
 // key at each step and never sorts.  Keys are completion << SH | (job+1) << 1
 // as in the permutation decoder.  The streams live in a per-thread scratch of
-// 2n keys in global memory; the per-machine counters in local memory.
+// 2n keys in global memory; the runs' heads and the per-machine counters, and
+// (when they fit) the stage's genes, in shared memory.
 #include <algorithm>
 #include <vector>
 
@@ -36,20 +37,29 @@ struct AssignView {
     const uint32_t *due;     // [n] or NULL
 };
 
+// Per-thread arrays in shared memory, interleaved by thread (element k of
+// thread t at k * T + t, so lanes indexing by their own k never conflict):
+// the input runs' head keys, positions and ends, and per machine of the
+// stage its job count, fill position and free time -- 6 * MX words.  With
+// GENES, the stage's genes are first copied there as bytes (n per thread),
+// so the dispatch reads the machine of a job from shared memory.
+template <bool GENES>
 __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, const int16_t *__restrict__ pop,
                                                                 int64_t N, int ld, int32_t *__restrict__ out,
-                                                                uint32_t *scratch)
+                                                                uint32_t *scratch, int MX)
 {
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int T = kAssignThreads, t = threadIdx.x;
+    uint32_t *hk = sm + t, *freeT = sm + MX * T + t;
+    int *pos = reinterpret_cast<int *>(sm) + 2 * MX * T + t, *endp = pos + MX * T, *cnt = endp + MX * T,
+        *fill = cnt + MX * T;
+    uint8_t *gsm = reinterpret_cast<uint8_t *>(sm + 6 * MX * T) + t;   // gene of job j at gsm[j * T]
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + t;
     const int n = V.n, S = V.S;
     const uint32_t SH = (uint32_t)V.SH, idmask = ((1u << SH) - 1u) & ~1u;
     uint32_t *bufA = scratch + tid * 2 * (int64_t)n, *bufB = bufA + n;
-    // input runs (the previous stage's machine streams) and output streams
-    uint32_t hk[kAssignMaxM];
-    int pos[kAssignMaxM], endp[kAssignMaxM], cnt[kAssignMaxM], fill[kAssignMaxM];
-    uint32_t freeT[kAssignMaxM];
-    for (int64_t r = tid; r < N; r += T) {
+    for (int64_t r = tid; r < N; r += nthreads) {
         const int16_t *row = pop + r * ld;
         bool bad = false;
         const uint32_t *in = V.order0;
@@ -62,39 +72,49 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
         for (int s = 0; s < S; ++s) {
             const int Ms = V.M[s], off = V.off[s];
             const bool last = s == S - 1;
-            for (int m = 0; m < Ms; ++m) cnt[m] = 0;
+            for (int m = 0; m < Ms; ++m) cnt[m * T] = 0;
             for (int j = 0; j < n; ++j) {
                 int g = row[(int64_t)j * S + s];
                 if ((unsigned)g >= (unsigned)Ms) {
                     bad = true;
                     g = 0;   // decoded as machine 0 (memory-safe); the row reports -1
                 }
-                ++cnt[g];
+                ++cnt[g * T];
+                if constexpr (GENES) gsm[j * T] = (uint8_t)g;
             }
             for (int m = 0, acc = 0; m < Ms; ++m) {
-                fill[m] = acc;
-                acc += cnt[m];
-                freeT[m] = 0u;
+                fill[m * T] = acc;
+                acc += cnt[m * T];
+                freeT[m * T] = 0u;
             }
             for (int k = 0; k < n; ++k) {
                 // the next arrival: the smallest head key of the input runs
                 int rb = 0;
                 uint32_t kb = hk[0];
-                for (int q = 1; q < R; ++q)
-                    if (hk[q] < kb) {
-                        kb = hk[q];
+                for (int q = 1; q < R; ++q) {
+                    const uint32_t h = hk[q * T];
+                    if (h < kb) {
+                        kb = h;
                         rb = q;
                     }
-                const int p1 = pos[rb] + 1;
-                pos[rb] = p1;
-                hk[rb] = p1 < endp[rb] ? in[p1] : 0xFFFFFFFFu;
+                }
+                const int p1 = pos[rb * T] + 1;
+                pos[rb * T] = p1;
+                hk[rb * T] = p1 < endp[rb * T] ? in[p1] : 0xFFFFFFFFu;
                 const int j = (int)((kb & idmask) >> 1) - 1;
-                int m = row[(int64_t)j * S + s];
-                if ((unsigned)m >= (unsigned)Ms) m = 0;
-                const uint32_t c = max(freeT[m], kb >> SH) + (uint32_t)V.p[(int64_t)j * V.W + off + m];
-                freeT[m] = c;
+                int m;
+                if constexpr (GENES) {
+                    m = gsm[j * T];
+                } else {
+                    m = row[(int64_t)j * S + s];
+                    if ((unsigned)m >= (unsigned)Ms) m = 0;
+                }
+                const uint32_t c = max(freeT[m * T], kb >> SH) + (uint32_t)V.p[(int64_t)j * V.W + off + m];
+                freeT[m * T] = c;
                 if (!last) {
-                    outb[fill[m]++] = (c << SH) | ((uint32_t)(j + 1) << 1);
+                    const int f = fill[m * T];
+                    fill[m * T] = f + 1;
+                    outb[f] = (c << SH) | ((uint32_t)(j + 1) << 1);
                 } else {
                     cmax = max(cmax, c);
                     if (V.due && c > V.due[j]) tard += c - V.due[j];
@@ -105,10 +125,11 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
                 in = outb;
                 R = Ms;
                 for (int m = 0, acc = 0; m < Ms; ++m) {
-                    pos[m] = acc;
-                    endp[m] = acc + cnt[m];
-                    hk[m] = cnt[m] > 0 ? in[acc] : 0xFFFFFFFFu;
-                    acc += cnt[m];
+                    const int c = cnt[m * T];
+                    pos[m * T] = acc;
+                    endp[m * T] = acc + c;
+                    hk[m * T] = c > 0 ? in[acc] : 0xFFFFFFFFu;
+                    acc += c;
                 }
                 outb = outb == bufA ? bufB : bufA;
             }
@@ -130,6 +151,7 @@ struct ffs_assign_instance {
     uint32_t *d_scratch = nullptr;
     int64_t scratch_threads = 0;   // threads the scratch serves (a multiple of kAssignThreads)
     int num_sms = 0;
+    int MX = 0;                    // largest M_s
 };
 
 int ffs_assign_instance_create(int32_t n, int32_t S, const int32_t *M, const int32_t *p_u, const int32_t *release,
@@ -184,6 +206,7 @@ int ffs_assign_instance_create(int32_t n, int32_t S, const int32_t *M, const int
     A->n = n;
     A->S = S;
     A->W = W;
+    for (int s = 0; s < S; ++s) A->MX = std::max(A->MX, M[s]);
     A->SH = SH;
     A->wt = due ? wt : 0;
     int dev = 0;
@@ -261,7 +284,19 @@ int ffs_assign_eval(const ffs_assign_instance *A, const int16_t *pop, int64_t N,
     V.due = A->d_due;
     const int64_t want = (N + kAssignThreads - 1) / kAssignThreads;
     const int grid = (int)std::min<int64_t>(want, A->scratch_threads / kAssignThreads);
-    k_eval_assign<<<grid, kAssignThreads, 0, (cudaStream_t)stream>>>(V, pop, N, ld, objective, A->d_scratch);
+    // shared memory: 6 * MX words per thread, plus n gene bytes when that
+    // still leaves room for two blocks per SM
+    const size_t base = (size_t)6 * A->MX * 4 * kAssignThreads;
+    const size_t genes = (size_t)((A->n + 3) / 4 * 4) * kAssignThreads;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (base + genes <= 110 * 1024) {
+        FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval_assign<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(base + genes)));
+        k_eval_assign<true><<<grid, kAssignThreads, base + genes, st>>>(V, pop, N, ld, objective, A->d_scratch, A->MX);
+    } else {
+        FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval_assign<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base));
+        k_eval_assign<false><<<grid, kAssignThreads, base, st>>>(V, pop, N, ld, objective, A->d_scratch, A->MX);
+    }
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
