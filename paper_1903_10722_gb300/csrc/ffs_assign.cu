@@ -37,6 +37,23 @@ struct AssignView {
     const uint32_t *due;     // [n] or NULL
 };
 
+// Stage-major copy of rows [0, count) of a population chunk: the gene of job
+// j at stage s goes to byte s * nstride + j of the row's output block (genes
+// outside [0, 255] become 255, which no stage accepts).  Block per row; the
+// row's output block stays in L2 while its scattered bytes are written.
+__global__ void k_assign_transpose(const int16_t *__restrict__ pop, int ld, int n, int S, int nstride,
+                                   uint8_t *__restrict__ out)
+{
+    const int16_t *row = pop + (int64_t)blockIdx.x * ld;
+    uint8_t *o = out + (int64_t)blockIdx.x * S * nstride;
+    const int total = n * S;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int g = row[i];
+        const int j = i / S, s = i - j * S;
+        o[(int64_t)s * nstride + j] = (uint8_t)((unsigned)g > 255u ? 255 : g);
+    }
+}
+
 // Per-thread arrays in shared memory, interleaved by thread (element k of
 // thread t at k * T + t, so lanes indexing by their own k never conflict):
 // the input runs' head keys, positions and ends, and per machine of the
@@ -44,8 +61,8 @@ struct AssignView {
 // GENES, the stage's genes are first copied there as bytes (n per thread),
 // so the dispatch reads the machine of a job from shared memory.
 template <bool GENES>
-__global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, const int16_t *__restrict__ pop,
-                                                                int64_t N, int ld, int32_t *__restrict__ out,
+__global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, const uint8_t *__restrict__ tpop,
+                                                                int64_t N, int nstride, int32_t *__restrict__ out,
                                                                 uint32_t *scratch, int MX)
 {
     extern __shared__ __align__(16) uint32_t sm[];
@@ -60,7 +77,7 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
     const uint32_t SH = (uint32_t)V.SH, idmask = ((1u << SH) - 1u) & ~1u;
     uint32_t *bufA = scratch + tid * 2 * (int64_t)n, *bufB = bufA + n;
     for (int64_t r = tid; r < N; r += nthreads) {
-        const int16_t *row = pop + r * ld;
+        const uint8_t *rowt = tpop + r * (int64_t)V.S * nstride;   // stage-major genes
         bool bad = false;
         const uint32_t *in = V.order0;
         int R = 1;
@@ -73,14 +90,22 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
             const int Ms = V.M[s], off = V.off[s];
             const bool last = s == S - 1;
             for (int m = 0; m < Ms; ++m) cnt[m * T] = 0;
-            for (int j = 0; j < n; ++j) {
-                int g = row[(int64_t)j * S + s];
-                if ((unsigned)g >= (unsigned)Ms) {
-                    bad = true;
-                    g = 0;   // decoded as machine 0 (memory-safe); the row reports -1
+            const uint8_t *gs = rowt + (int64_t)s * nstride;   // 16-byte aligned
+            for (int j0 = 0; j0 < n; j0 += 16) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(gs + j0);
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    if (j0 + u < n) {
+                        int g = (int)((w[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+                        if (g >= Ms) {
+                            bad = true;
+                            g = 0;   // decoded as machine 0 (memory-safe); the row reports -1
+                        }
+                        ++cnt[g * T];
+                        if constexpr (GENES) gsm[(j0 + u) * T] = (uint8_t)g;
+                    }
                 }
-                ++cnt[g * T];
-                if constexpr (GENES) gsm[j * T] = (uint8_t)g;
             }
             for (int m = 0, acc = 0; m < Ms; ++m) {
                 fill[m * T] = acc;
@@ -106,8 +131,8 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
                 if constexpr (GENES) {
                     m = gsm[j * T];
                 } else {
-                    m = row[(int64_t)j * S + s];
-                    if ((unsigned)m >= (unsigned)Ms) m = 0;
+                    m = gs[j];
+                    if (m >= Ms) m = 0;
                 }
                 const uint32_t c = max(freeT[m * T], kb >> SH) + (uint32_t)V.p[(int64_t)j * V.W + off + m];
                 freeT[m * T] = c;
@@ -149,7 +174,9 @@ struct ffs_assign_instance {
     uint16_t *d_p = nullptr;
     uint32_t *d_order0 = nullptr, *d_due = nullptr;
     uint32_t *d_scratch = nullptr;
-    int64_t scratch_threads = 0;   // threads the scratch serves (a multiple of kAssignThreads)
+    uint8_t *d_tpop = nullptr;     // stage-major genes of one chunk of rows
+    int nstride = 0;               // round_up(n, 16)
+    int64_t scratch_threads = 0;   // rows of one chunk = threads the scratch serves (a multiple of kAssignThreads)
     int num_sms = 0;
     int MX = 0;                    // largest M_s
 };
@@ -223,16 +250,20 @@ int ffs_assign_instance_create(int32_t n, int32_t S, const int32_t *M, const int
     for (int j = 0; j < n; ++j)
         order0[j] = ((uint32_t)(release ? release[j] : 0) << SH) | ((uint32_t)(j + 1) << 1);
     std::sort(order0.begin(), order0.end());   // (R_j, j) ascending: the stage-1 arrival order
-    // scratch: 2n keys per thread, for two blocks per SM, at most kAssignScratchCap bytes
+    // scratch per thread (= per row of a chunk): 2n stream keys and the row's
+    // stage-major genes; two blocks per SM, at most kAssignScratchCap bytes
+    A->nstride = (n + 15) / 16 * 16;
     int64_t threads = (int64_t)A->num_sms * 2 * kAssignThreads;
-    const int64_t per = (int64_t)2 * n * 4;
+    const int64_t per_keys = (int64_t)2 * n * 4, per_genes = (int64_t)S * A->nstride;
+    const int64_t per = per_keys + per_genes;
     threads = std::min<int64_t>(threads, (int64_t)(kAssignScratchCap / per) / kAssignThreads * kAssignThreads);
     if (threads < kAssignThreads) threads = kAssignThreads;
     A->scratch_threads = threads;
     bool ok = cudaMalloc(&A->d_M, 4 * S) == cudaSuccess && cudaMalloc(&A->d_off, 4 * S) == cudaSuccess &&
               cudaMalloc(&A->d_p, p16.size() * 2) == cudaSuccess && cudaMalloc(&A->d_order0, 4 * n) == cudaSuccess &&
               (!due || cudaMalloc(&A->d_due, 4 * n) == cudaSuccess) &&
-              cudaMalloc(&A->d_scratch, (size_t)threads * per) == cudaSuccess;
+              cudaMalloc(&A->d_scratch, (size_t)threads * per_keys) == cudaSuccess &&
+              cudaMalloc(&A->d_tpop, (size_t)threads * per_genes) == cudaSuccess;
     ok = ok && cudaMemcpy(A->d_M, M, 4 * S, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(A->d_off, off.data(), 4 * S, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(A->d_p, p16.data(), p16.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -256,6 +287,7 @@ int ffs_assign_instance_destroy(ffs_assign_instance *A)
     cudaFree(A->d_order0);
     cudaFree(A->d_due);
     cudaFree(A->d_scratch);
+    cudaFree(A->d_tpop);
     delete A;
     return FFS_OK;
 }
@@ -282,20 +314,28 @@ int ffs_assign_eval(const ffs_assign_instance *A, const int16_t *pop, int64_t N,
     V.p = A->d_p;
     V.order0 = A->d_order0;
     V.due = A->d_due;
-    const int64_t want = (N + kAssignThreads - 1) / kAssignThreads;
-    const int grid = (int)std::min<int64_t>(want, A->scratch_threads / kAssignThreads);
     // shared memory: 6 * MX words per thread, plus n gene bytes when that
     // still leaves room for two blocks per SM
     const size_t base = (size_t)6 * A->MX * 4 * kAssignThreads;
     const size_t genes = (size_t)((A->n + 3) / 4 * 4) * kAssignThreads;
+    const bool in_smem = base + genes <= 110 * 1024;
+    const size_t smem = in_smem ? base + genes : base;
     cudaStream_t st = (cudaStream_t)stream;
-    if (base + genes <= 110 * 1024) {
-        FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval_assign<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(base + genes)));
-        k_eval_assign<true><<<grid, kAssignThreads, base + genes, st>>>(V, pop, N, ld, objective, A->d_scratch, A->MX);
-    } else {
-        FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval_assign<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base));
-        k_eval_assign<false><<<grid, kAssignThreads, base, st>>>(V, pop, N, ld, objective, A->d_scratch, A->MX);
+    FFS_CUDA_TRY(cudaFuncSetAttribute(in_smem ? (const void *)k_eval_assign<true> : (const void *)k_eval_assign<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // chunks of scratch_threads rows: stage-major copy, then one thread per row
+    for (int64_t r0 = 0; r0 < N; r0 += A->scratch_threads) {
+        const int64_t cnt = std::min<int64_t>(A->scratch_threads, N - r0);
+        k_assign_transpose<<<(unsigned)cnt, 256, 0, st>>>(pop + r0 * ld, ld, A->n, A->S, A->nstride, A->d_tpop);
+        FFS_CUDA_TRY(cudaGetLastError());
+        const int grid = (int)((cnt + kAssignThreads - 1) / kAssignThreads);
+        if (in_smem)
+            k_eval_assign<true><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride, objective + r0,
+                                                                    A->d_scratch, A->MX);
+        else
+            k_eval_assign<false><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride, objective + r0,
+                                                                     A->d_scratch, A->MX);
+        FFS_CUDA_TRY(cudaGetLastError());
     }
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
