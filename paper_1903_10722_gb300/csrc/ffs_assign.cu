@@ -60,7 +60,11 @@ __global__ void k_assign_transpose(const int16_t *__restrict__ pop, int ld, int 
 // stage its job count, fill position and free time -- 6 * MX words.  With
 // GENES, the stage's genes are first copied there as bytes (n per thread),
 // so the dispatch reads the machine of a job from shared memory.
-template <bool GENES>
+// PSLICE (with GENES, one row per thread): the block's threads run the
+// stages in step (a barrier per stage) and share the stage's slice of the
+// processing-time table, p[j][M_0 + ... + M_{s-1} + m] at pst[j * MX + m],
+// copied to shared memory after the per-thread arrays and genes.
+template <bool GENES, bool PSLICE>
 __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, const uint8_t *__restrict__ tpop,
                                                                 int64_t N, int nstride, int32_t *__restrict__ out,
                                                                 uint32_t *scratch, int MX)
@@ -71,12 +75,15 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
     int *pos = reinterpret_cast<int *>(sm) + 2 * MX * T + t, *endp = pos + MX * T, *cnt = endp + MX * T,
         *fill = cnt + MX * T;
     uint8_t *gsm = reinterpret_cast<uint8_t *>(sm + 6 * MX * T) + t;   // gene of job j at gsm[j * T]
+    uint16_t *pst = reinterpret_cast<uint16_t *>(sm + 6 * MX * T + (V.n + 3) / 4 * T);
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + t;
     const int n = V.n, S = V.S;
     const uint32_t SH = (uint32_t)V.SH, idmask = ((1u << SH) - 1u) & ~1u;
     uint32_t *bufA = scratch + tid * 2 * (int64_t)n, *bufB = bufA + n;
-    for (int64_t r = tid; r < N; r += nthreads) {
+    // PSLICE: one pass, rows beyond N run the stages without work (barriers)
+    for (int64_t r = tid; PSLICE ? r == tid : r < N; r += nthreads) {
+        const bool live = r < N;
         const uint8_t *rowt = tpop + r * (int64_t)V.S * nstride;   // stage-major genes
         bool bad = false;
         const uint32_t *in = V.order0;
@@ -89,6 +96,15 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
         for (int s = 0; s < S; ++s) {
             const int Ms = V.M[s], off = V.off[s];
             const bool last = s == S - 1;
+            if constexpr (PSLICE) {
+                __syncthreads();   // every thread is done with the previous slice
+                for (int i = t; i < n * Ms; i += T) {
+                    const int j = i / Ms, m = i - j * Ms;
+                    pst[j * MX + m] = V.p[(int64_t)j * V.W + off + m];
+                }
+                __syncthreads();
+                if (!live) continue;
+            }
             for (int m = 0; m < Ms; ++m) cnt[m * T] = 0;
             const uint8_t *gs = rowt + (int64_t)s * nstride;   // 16-byte aligned
             for (int j0 = 0; j0 < n; j0 += 16) {
@@ -134,7 +150,10 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
                     m = gs[j];
                     if (m >= Ms) m = 0;
                 }
-                const uint32_t c = max(freeT[m * T], kb >> SH) + (uint32_t)V.p[(int64_t)j * V.W + off + m];
+                uint32_t pj;
+                if constexpr (PSLICE) pj = pst[j * MX + m];
+                else pj = V.p[(int64_t)j * V.W + off + m];
+                const uint32_t c = max(freeT[m * T], kb >> SH) + pj;
                 freeT[m * T] = c;
                 if (!last) {
                     const int f = fill[m * T];
@@ -159,7 +178,7 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
                 outb = outb == bufA ? bufB : bufA;
             }
         }
-        out[r] = bad ? -1 : (int32_t)(cmax + V.wt * tard);
+        if (live) out[r] = bad ? -1 : (int32_t)(cmax + V.wt * tard);
     }
 }
 
@@ -314,27 +333,33 @@ int ffs_assign_eval(const ffs_assign_instance *A, const int16_t *pop, int64_t N,
     V.p = A->d_p;
     V.order0 = A->d_order0;
     V.due = A->d_due;
-    // shared memory: 6 * MX words per thread, plus n gene bytes when that
-    // still leaves room for two blocks per SM
+    // shared memory: 6 * MX words per thread, plus n gene bytes and the
+    // stage's table slice (shared by the block) when they still leave room
+    // for two blocks per SM
     const size_t base = (size_t)6 * A->MX * 4 * kAssignThreads;
     const size_t genes = (size_t)((A->n + 3) / 4 * 4) * kAssignThreads;
-    const bool in_smem = base + genes <= 110 * 1024;
-    const size_t smem = in_smem ? base + genes : base;
+    const size_t slice = ((size_t)A->n * A->MX * 2 + 15) / 16 * 16;
+    const int mode = base + genes + slice <= 110 * 1024 ? 2 : base + genes <= 110 * 1024 ? 1 : 0;
+    const size_t smem = base + (mode >= 1 ? genes : 0) + (mode == 2 ? slice : 0);
+    const void *kern = mode == 2 ? (const void *)k_eval_assign<true, true>
+                     : mode == 1 ? (const void *)k_eval_assign<true, false> : (const void *)k_eval_assign<false, false>;
     cudaStream_t st = (cudaStream_t)stream;
-    FFS_CUDA_TRY(cudaFuncSetAttribute(in_smem ? (const void *)k_eval_assign<true> : (const void *)k_eval_assign<false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FFS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // chunks of scratch_threads rows: stage-major copy, then one thread per row
     for (int64_t r0 = 0; r0 < N; r0 += A->scratch_threads) {
         const int64_t cnt = std::min<int64_t>(A->scratch_threads, N - r0);
         k_assign_transpose<<<(unsigned)cnt, 256, 0, st>>>(pop + r0 * ld, ld, A->n, A->S, A->nstride, A->d_tpop);
         FFS_CUDA_TRY(cudaGetLastError());
         const int grid = (int)((cnt + kAssignThreads - 1) / kAssignThreads);
-        if (in_smem)
-            k_eval_assign<true><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride, objective + r0,
-                                                                    A->d_scratch, A->MX);
+        if (mode == 2)
+            k_eval_assign<true, true><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride,
+                                                                          objective + r0, A->d_scratch, A->MX);
+        else if (mode == 1)
+            k_eval_assign<true, false><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride,
+                                                                           objective + r0, A->d_scratch, A->MX);
         else
-            k_eval_assign<false><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride, objective + r0,
-                                                                     A->d_scratch, A->MX);
+            k_eval_assign<false, false><<<grid, kAssignThreads, smem, st>>>(V, A->d_tpop, cnt, A->nstride,
+                                                                            objective + r0, A->d_scratch, A->MX);
         FFS_CUDA_TRY(cudaGetLastError());
     }
     FFS_CUDA_TRY(cudaGetLastError());
