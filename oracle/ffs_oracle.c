@@ -33,6 +33,7 @@
  * Numbers: As Easy as 1, 2, 3", SC 2011 (Section 4, the Philox S-box).
  *
  * Parity status: the decoder (makespan and the Section 3 objective), the
+ * decoder of the paper's own genotype (machine-assignment strings), the
  * operators, Philox and the migration formulas are pinned by tests
  * (hand-worked Gantt charts, closed forms, brute force, library
  * cross-checks).  The GA loop as a whole (the sequence
