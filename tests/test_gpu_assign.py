@@ -20,6 +20,9 @@ SHAPES = [
     (100, 10, 2, 5, 300),
     (257, 7, 1, 9, 130),
     (500, 20, 5, 10, 64),
+    (100, 4, 32, 32, 50),     # per-thread genes in shared memory, table slice not
+    (3000, 2, 2, 3, 20),      # genes read from the stage-major copy in global memory
+    (20, 5, 1, 4, 40000),     # more rows than one chunk
 ]
 
 
