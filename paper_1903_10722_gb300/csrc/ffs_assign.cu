@@ -56,8 +56,11 @@ __global__ void k_assign_transpose(const int16_t *__restrict__ pop, int ld, int 
 
 // Per-thread arrays in shared memory, interleaved by thread (element k of
 // thread t at k * T + t, so lanes indexing by their own k never conflict):
-// the input runs' head keys, positions and ends, and per machine of the
-// stage its job count, fill position and free time -- 6 * MX words.  With
+// the input runs' first two keys (hk0, hk1), position of hk1's key and end,
+// and per machine of the stage its job count, fill position and free time --
+// 7 * MX words.  Popping a run shifts hk1 into hk0 and refills hk1 with an
+// asynchronous 4-byte copy from the run in global memory, which the next
+// pop of that run waits for (one pop later at least).  With
 // GENES, the stage's genes are first copied there as bytes (n per thread),
 // so the dispatch reads the machine of a job from shared memory.
 // PSLICE (with GENES, one row per thread): the block's threads run the
@@ -71,11 +74,12 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
 {
     extern __shared__ __align__(16) uint32_t sm[];
     const int T = kAssignThreads, t = threadIdx.x;
-    uint32_t *hk = sm + t, *freeT = sm + MX * T + t;
-    int *pos = reinterpret_cast<int *>(sm) + 2 * MX * T + t, *endp = pos + MX * T, *cnt = endp + MX * T,
+    uint32_t *hk0 = sm + t, *hk1 = sm + MX * T + t, *freeT = sm + 2 * MX * T + t;
+    int *pos = reinterpret_cast<int *>(sm) + 3 * MX * T + t, *endp = pos + MX * T, *cnt = endp + MX * T,
         *fill = cnt + MX * T;
-    uint8_t *gsm = reinterpret_cast<uint8_t *>(sm + 6 * MX * T) + t;   // gene of job j at gsm[j * T]
-    uint16_t *pst = reinterpret_cast<uint16_t *>(sm + 6 * MX * T + (V.n + 3) / 4 * T);
+    uint8_t *gsm = reinterpret_cast<uint8_t *>(sm + 7 * MX * T) + t;   // gene of job j at gsm[j * T]
+    uint16_t *pst = reinterpret_cast<uint16_t *>(sm + 7 * MX * T + (V.n + 3) / 4 * T);
+    const uint32_t hk1_sa = (uint32_t)__cvta_generic_to_shared(hk1);
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + t;
     const int n = V.n, S = V.S;
@@ -88,9 +92,10 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
         bool bad = false;
         const uint32_t *in = V.order0;
         int R = 1;
-        pos[0] = 0;
+        pos[0] = 1;
         endp[0] = n;
-        hk[0] = in[0];
+        hk0[0] = in[0];
+        hk1[0] = n > 1 ? in[1] : 0xFFFFFFFFu;
         uint32_t *outb = bufA;
         uint32_t cmax = 0, tard = 0;
         for (int s = 0; s < S; ++s) {
@@ -128,20 +133,33 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
                 acc += cnt[m * T];
                 freeT[m * T] = 0u;
             }
+            int prev = -1;
             for (int k = 0; k < n; ++k) {
                 // the next arrival: the smallest head key of the input runs
                 int rb = 0;
-                uint32_t kb = hk[0];
+                uint32_t kb = hk0[0];
                 for (int q = 1; q < R; ++q) {
-                    const uint32_t h = hk[q * T];
+                    const uint32_t h = hk0[q * T];
                     if (h < kb) {
                         kb = h;
                         rb = q;
                     }
                 }
+                // hk1 of run rb: refilled by the previous pop's copy when rb was
+                // popped then, else by an older one
+                if (rb == prev) asm volatile("cp.async.wait_group 0;" ::: "memory");
+                else asm volatile("cp.async.wait_group 1;" ::: "memory");
+                hk0[rb * T] = hk1[rb * T];
                 const int p1 = pos[rb * T] + 1;
                 pos[rb * T] = p1;
-                hk[rb * T] = p1 < endp[rb * T] ? in[p1] : 0xFFFFFFFFu;
+                if (p1 < endp[rb * T])
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(hk1_sa + (uint32_t)(rb * T) * 4u),
+                                 "l"(in + p1)
+                                 : "memory");
+                else
+                    hk1[rb * T] = 0xFFFFFFFFu;
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                prev = rb;
                 const int j = (int)((kb & idmask) >> 1) - 1;
                 int m;
                 if constexpr (GENES) {
@@ -164,15 +182,18 @@ __global__ void __launch_bounds__(kAssignThreads) k_eval_assign(AssignView V, co
                     if (V.due && c > V.due[j]) tard += c - V.due[j];
                 }
             }
+            // no copy in flight reads a stream the next stage overwrites
+            asm volatile("cp.async.wait_all;" ::: "memory");
             if (!last) {
                 // the next stage merges this stage's machine streams
                 in = outb;
                 R = Ms;
                 for (int m = 0, acc = 0; m < Ms; ++m) {
                     const int c = cnt[m * T];
-                    pos[m * T] = acc;
+                    pos[m * T] = acc + 1;
                     endp[m * T] = acc + c;
-                    hk[m * T] = c > 0 ? in[acc] : 0xFFFFFFFFu;
+                    hk0[m * T] = c > 0 ? in[acc] : 0xFFFFFFFFu;
+                    hk1[m * T] = c > 1 ? in[acc + 1] : 0xFFFFFFFFu;
                     acc += c;
                 }
                 outb = outb == bufA ? bufB : bufA;
@@ -333,10 +354,10 @@ int ffs_assign_eval(const ffs_assign_instance *A, const int16_t *pop, int64_t N,
     V.p = A->d_p;
     V.order0 = A->d_order0;
     V.due = A->d_due;
-    // shared memory: 6 * MX words per thread, plus n gene bytes and the
+    // shared memory: 7 * MX words per thread, plus n gene bytes and the
     // stage's table slice (shared by the block) when they still leave room
     // for two blocks per SM
-    const size_t base = (size_t)6 * A->MX * 4 * kAssignThreads;
+    const size_t base = (size_t)7 * A->MX * 4 * kAssignThreads;
     const size_t genes = (size_t)((A->n + 3) / 4 * 4) * kAssignThreads;
     const size_t slice = ((size_t)A->n * A->MX * 2 + 15) / 16 * 16;
     const int mode = base + genes + slice <= 110 * 1024 ? 2 : base + genes <= 110 * 1024 ? 1 : 0;
