@@ -320,13 +320,15 @@ __device__ __forceinline__ void cellular_warp_decode_child(const DecodeLayout &L
 }
 
 // One cellular generation for the cell `c` of each lane: breeding, then
-// decoding and replacement (see the two halves above).
+// decoding and replacement (see the two halves above).  BYTES: the
+// crossover mark's form (warp_build_children).
+template <bool BYTES = false>
 __device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, const GaScalars &g, const IslandRef &ref,
                                                     int c, bool valid, int rows, int cols, int ld, uint32_t *wbits,
                                                     uint32_t *region, int T, const uint16_t *tab,
                                                     WarpStageState *wst)
 {
-    cellular_warp_breed<false>(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
+    cellular_warp_breed<BYTES>(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
     cellular_warp_decode(Ls, g, ref, c, valid, ld, region, T, tab, wst);
 }
 
