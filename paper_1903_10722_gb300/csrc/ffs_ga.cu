@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
-    const int bits_per_warp = (L.n + 31) >> 5;
+    const int bits_per_warp = mark_words(L.n, true);   // crossover mark: one byte per gene
     const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp, L.obj_words);
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
         const bool valid = gc < total;
         const int bi = (valid ? gc : total - 1) / cells;
         const int c = (valid ? gc : total - 1) - bi * cells;
-        cellular_warp_cells(Ls, g, batch.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
+        cellular_warp_cells<true>(Ls, g, batch.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
     }
     decode_tmem_end(Ls);
 }
@@ -66,7 +66,7 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBa
                     int ld, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
     Plan p;
-    const int bits_per_warp = (inst->n + 31) / 32;
+    const int bits_per_warp = mark_words(inst->n, true);
     int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p, g.variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
@@ -1252,7 +1252,7 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
             const int B = Bs[bi] == 0 ? round_up(S->inst->n, 8) : Bs[bi];
             if (Bs[bi] != 0 && B >= S->inst->n) continue;
             Plan p;
-            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], (S->inst->n + 31) / 32, &p, vi)) continue;
+            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], mark_words(S->inst->n, true), &p, vi)) continue;
             S->prm.decode_chunk = B;
             S->prm.block_threads = Ts[ti];
             S->prm.decode_variant = vi;

@@ -54,9 +54,9 @@ __host__ __device__ inline int table_words(int n, int S) { return round_up(S * t
 __host__ __device__ inline int objective_words(int n) { return 2 * round_up(n + 1, 4); }
 
 // Per-warp shared words for the order crossover's mark of the segment genes:
-// one byte per gene in the breeding kernels (a plain store to set, a byte
-// load to test), or a bitmask of n bits in the fused kernels that breed and
-// decode in one launch, where the decoder needs the shared memory.
+// one byte per gene (a plain store to set, a byte load to test; every kernel
+// uses it), or a bitmask of n bits (atomic OR to set; a third of the shared
+// memory at n = 500).
 __host__ __device__ inline int mark_words(int n, bool bytes) { return bytes ? round_up(n, 16) / 4 : (n + 31) / 32; }
 
 __host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_warp = 0, int obj_words = 0)
