@@ -1,5 +1,8 @@
-// ffs_ga.cu -- GA generations on the GPU: the fused cellular generation, the
-// pseudo island (complementary pairs), migration, and the islands handle
+// ffs_ga.cu -- GA generations on the GPU: the fused cellular generation
+// (cellular-only islands), the pseudo island (complementary pairs), the
+// generation of both kinds in two launches (k_breed_dual: every child built;
+// k_step_decode: every child decoded and the cells replaced), migration
+// (chunked ranking, ring and penetration copies), and the islands handle
 // that replays one generation of every island from a CUDA graph.
 #include <algorithm>
 #include <cmath>
