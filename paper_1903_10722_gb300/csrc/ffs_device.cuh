@@ -387,20 +387,35 @@ __device__ __noinline__ uint4 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
             const int4 v = vnext;
             if (i0 + 8 < cnt) vnext = g4[(i0 >> 3) + 1];
             const uint32_t words[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+            // the stage-1 key of gene h of the block (its release time R_j as the time)
+            auto key_of = [&](int h) {
+                uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
+                g = (uint32_t)(int32_t)(int16_t)g;
+                if (g >= (uint32_t)n) { bad_gene = true; g = 0; }
+                uint32_t in = (g + 1u) << 1;
+                if (rel) in |= lds32(rel + (in << 1)) << SH;
+                return in;
+            };
+            auto take = [&](int i, uint32_t popped) {
+                if constexpr (EMIT) {
+                    if (i >= skip) { sts32(buf + (uint32_t)w * stride, popped); ++w; }
+                } else {
+                    if (due) tard += key_tardiness(popped, due, SH, idmask);
+                }
+            };
+            // two jobs per dispatch, one at the block's ragged end
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                if (i0 + h < cnt) {
-                    uint32_t g = (h & 1) ? (words[h >> 1] >> 16) : (words[h >> 1] & 0xFFFFu);
-                    g = (uint32_t)(int32_t)(int16_t)g;
-                    if (g >= (uint32_t)n) { bad_gene = true; g = 0; }
-                    uint32_t in = (g + 1u) << 1;
-                    if (rel) in |= lds32(rel + (in << 1)) << SH;   // stage-1 ready time R_j
-                    const uint32_t popped = dispatch_pp<M>(f, in, lds16(prow + (in & idmask)), lowmask, mulSH);
-                    if constexpr (EMIT) {
-                        if (i0 + h >= skip) { sts32(buf + (uint32_t)w * stride, popped); ++w; }
-                    } else {
-                        if (due) tard += key_tardiness(popped, due, SH, idmask);
-                    }
+            for (int h = 0; h < 8; h += 2) {
+                if (i0 + h + 1 < cnt) {
+                    const uint32_t ka = key_of(h), kb = key_of(h + 1);
+                    uint32_t pop1, pop2;
+                    dispatch2_pp<M>(f, ka, lds16(prow + (ka & idmask)), kb, lds16(prow + (kb & idmask)), lowmask,
+                                    mulSH, pop1, pop2);
+                    take(i0 + h, pop1);
+                    take(i0 + h + 1, pop2);
+                } else if (i0 + h < cnt) {
+                    const uint32_t ka = key_of(h);
+                    take(i0 + h, dispatch_pp<M>(f, ka, lds16(prow + (ka & idmask)), lowmask, mulSH));
                 }
             }
         }
