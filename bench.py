@@ -739,8 +739,8 @@ def run_paper(args):
 
 # DRAM bytes (read + write) of one k_step_decode launch of scale_500x20 at
 # 384 threads, chunk 128, variant 3, from one ncu capture of the current
-# kernel (117.5 MB read + 12.1 MB written); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = 129_577_728
+# kernel (118.0 MB read + 12.2 MB written); other shapes report null.
+K_STEP_DECODE_DRAM_BYTES = 130_257_152
 
 
 # DRAM bytes of one k_batch_cellular launch of batch_256 at 512 threads,
