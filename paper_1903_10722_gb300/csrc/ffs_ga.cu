@@ -255,9 +255,10 @@ __device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const Is
     cellular_warp_breed<true>(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits, children + (int64_t)gq * ld);
 }
 
-// Both breeding halves of a dual generation in one launch: the first
-// `cell_blocks` blocks breed the cellular cells, the others the pseudo pairs;
-// the two kinds of warps share the SMs and hide each other's memory latency.
+// Both breeding halves of a dual generation in one launch: `cell_blocks`
+// blocks breed the cellular cells, the others (launched first) the pseudo
+// pairs; the two kinds of warps share the SMs and hide each other's memory
+// latency.
 __global__ void __launch_bounds__(256) k_breed_dual(GaScalars g, const __grid_constant__ IslandBatch cb, int rows,
                                                     int cols, const __grid_constant__ IslandBatch pb, int psize,
                                                     int n, int ld, PseudoScratch s, int cell_blocks,
@@ -266,10 +267,12 @@ __global__ void __launch_bounds__(256) k_breed_dual(GaScalars g, const __grid_co
     extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     uint32_t *wbits = smem + warp * mark_words(n, true);
-    if ((int)blockIdx.x < cell_blocks)
-        cellular_breed_warp(g, cb, rows, cols, n, ld, blockIdx.x * wpb + warp, wbits, cell_children);
+    // the pseudo blocks first (0.3 % faster than the cellular ones first)
+    const int P = gridDim.x - cell_blocks;
+    if ((int)blockIdx.x >= P)
+        cellular_breed_warp(g, cb, rows, cols, n, ld, (blockIdx.x - P) * wpb + warp, wbits, cell_children);
     else
-        pseudo_breed_warp(g, pb, psize, n, ld, s, (blockIdx.x - cell_blocks) * wpb + warp, wbits);
+        pseudo_breed_warp(g, pb, psize, n, ld, s, blockIdx.x * wpb + warp, wbits);
 }
 
 // Blocks of T threads for kPairsPerWarp pairs per warp.
