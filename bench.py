@@ -386,7 +386,8 @@ def run_ours(args):
         "gpu_launches": args.steps * launches_per_generation(w),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops,
-                     "traffic": K_STEP_DECODE_DRAM_BYTES if _shape_is(prm, 384, 128, 3) else None,
+                     "traffic": K_STEP_DECODE_DRAM_BYTES.get(
+                         (prm.block_threads, prm.decode_chunk, prm.decode_variant)),
                      "kernel": "k_step_decode (all cellular children: decode + replace; all pseudo children: decode), "
                                "timed with the breeding launch (k_breed_dual) and the pseudo pair replacement",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": decodes_per_launch * ops_eval,
@@ -738,18 +739,15 @@ def run_paper(args):
 
 
 # DRAM bytes (read + write) of one k_step_decode launch of scale_500x20 at
-# 384 threads, chunk 128, variant 3, from one ncu capture of the current
-# kernel (118.0 MB read + 12.2 MB written); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = 130_257_152
+# the launch shapes the autotuner picks, (threads, chunk, variant) -> bytes,
+# from ncu captures of the current kernel (--metrics dram__bytes_read.sum,
+# dram__bytes_write.sum); other shapes report null.
+K_STEP_DECODE_DRAM_BYTES = {(384, 128, 3): 117_337_088 + 9_407_744, (384, 96, 3): 116_727_552 + 9_374_720}
 
 
 # DRAM bytes of one k_batch_cellular launch of batch_256 at 512 threads,
 # chunk 64, variant 3 (ncu: 223.0 MB read + 178.9 MB written).
 K_BATCH_CELLULAR_DRAM_BYTES = 401_944_064
-
-
-def _shape_is(prm, threads, chunk, variant) -> bool:
-    return (prm.block_threads, prm.decode_chunk, prm.decode_variant) == (threads, chunk, variant)
 
 
 def launches_per_generation(w) -> int:
