@@ -590,7 +590,7 @@ def run_decode(args):
     num_sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
     results = {}
-    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 48, 64, 96, 112, 128) for t in (64, 128, 256, 320, 384, 448, 512)]
+    shapes = [(0, 0)] if args.no_autotune else [(c, t) for c in (8, 16, 32, 48, 64, 96, 104, 112, 128) for t in (64, 128, 256, 320, 384, 448, 512)]
     variants = (1, 2, 3, 4)
     if args.shape:
         t, c, v = (int(x) for x in args.shape.split(","))
@@ -742,7 +742,8 @@ def run_paper(args):
 # the launch shapes the autotuner picks, (threads, chunk, variant) -> bytes,
 # from ncu captures of the current kernel (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = {(384, 128, 3): 117_337_088 + 9_407_744, (384, 96, 3): 116_727_552 + 9_374_720}
+K_STEP_DECODE_DRAM_BYTES = {(384, 128, 3): 117_337_088 + 9_407_744, (384, 104, 3): 116_720_896 + 9_434_368,
+                            (384, 96, 3): 116_727_552 + 9_374_720}
 
 
 # DRAM bytes of one k_batch_cellular launch of batch_256 at 512 threads,

@@ -460,11 +460,11 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
     float best = -1.0f;
     int bestT = b->T, bestB = b->B, bestV = b->prm.decode_variant;
     const int Ts[7] = {64, 128, 256, 320, 384, 448, 512};
-    const int Bs[8] = {8, 16, 32, 48, 64, 96, 112, 128};
+    const int Bs[9] = {8, 16, 32, 48, 64, 96, 104, 112, 128};
     int rc = FFS_OK;
     for (int vi = 1; vi <= kMaxVariant && !rc; ++vi)
     for (int ti = 0; ti < 7 && !rc; ++ti) {
-        for (int bi = 0; bi < 8 && !rc; ++bi) {
+        for (int bi = 0; bi < 9 && !rc; ++bi) {
             BatchShape s;
             size_t smem;
             int nb;

@@ -1251,10 +1251,10 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
     // 320 .. 448 threads are in the list for their balance: warp work items
     // are whole decodes, and the last wave of a launch is as long as one item
     const int Ts[7] = {64, 128, 256, 320, 384, 448, 512};
-    const int Bs[9] = {8, 16, 32, 48, 64, 96, 112, 128, 0};
+    const int Bs[10] = {8, 16, 32, 48, 64, 96, 104, 112, 128, 0};
     for (int vi = 1; vi <= kMaxVariant && !rc; ++vi)
     for (int ti = 0; ti < 7 && !rc; ++ti) {
-        for (int bi = 0; bi < 9 && !rc; ++bi) {
+        for (int bi = 0; bi < 10 && !rc; ++bi) {
             const int B = Bs[bi] == 0 ? round_up(S->inst->n, 8) : Bs[bi];
             if (Bs[bi] != 0 && B >= S->inst->n) continue;
             Plan p;

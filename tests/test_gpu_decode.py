@@ -42,7 +42,7 @@ def test_eval_matches_oracle(gpu, shape):
     d = dev(pop)
     out = torch.full((N,), -7, dtype=torch.int32, device="cuda")
     shapes = [(0, 0)]
-    for chunk in (8, 16, 32, 48, 64, 96, 112, 128):
+    for chunk in (8, 16, 32, 48, 64, 96, 104, 112, 128):
         if chunk < n:
             shapes.append((chunk, 0))
     for threads in (32, 96, 128, 256, 512):

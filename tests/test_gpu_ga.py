@@ -246,7 +246,7 @@ def test_explicit_migrate_and_set_get(gpu):
         gpu.ffs_island_step(isl, -1, 1)
 
 
-@pytest.mark.parametrize("shape", [(0, 0, 0), (384, 128, 3)], ids=["library", "bench"])
+@pytest.mark.parametrize("shape", [(0, 0, 0), (384, 128, 3), (384, 104, 3)], ids=["library", "bench128", "bench104"])
 def test_scale_500x20_sampled_generation(gpu, shape):
     """4 x 128^2 cellular + 4 x 16384 pseudo at 500 x 20: one generation of
     every island, checked on sampled cells and pairs with the oracle, at the
