@@ -263,7 +263,7 @@ def run_ours(args):
     _apply_shape(prm, args)
     stream = torch.cuda.current_stream()
     isl = ffs.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
-    tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=2)
+    tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=4)
     if tuned:
         used = ffs.ffs_islands_params(isl)
         prm.decode_chunk, prm.block_threads, prm.decode_variant = used.decode_chunk, used.block_threads, used.decode_variant
@@ -437,7 +437,7 @@ def run_batch(args):
     prm = ffs.ffs_params_default()
     _apply_shape(prm, args)
     b = ffs.Batch(specs, prm, w["rows"], w["cols"])
-    tuned = b.info() if args.no_autotune else ffs.ffs_batch_autotune(b, repeats=2)
+    tuned = b.info() if args.no_autotune else ffs.ffs_batch_autotune(b, repeats=4)
     tuned["variant"] = b.info()["variant"]
     stream = torch.cuda.current_stream()
     ffs.ffs_batch_step(b, args.warmup)

@@ -362,8 +362,9 @@ int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream strea
  * initialises every island and decodes it; synchronous.
  * ffs_batch_step: n_generations generations of every instance; async.
  * ffs_batch_autotune: times every launch shape (threads per block x decode
- * chunk x decoder variant) that fits, `repeats` timed runs each, on
- * generations that do not advance the state, keeps the fastest and reports
+ * chunk x decoder variant) that fits, `repeats` timed runs each (a shape's
+ * time is its fastest run), on generations that do not advance the state,
+ * keeps the fastest shape and reports
  * it; synchronous.
  * ffs_batch_info: instance count, generations done, launch shape and the
  * decoder variant in use (1 / 2: one stage / stage pairs, saved heaps in
@@ -496,10 +497,11 @@ int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
 int ffs_islands_dry_run(ffs_islands *isl, int32_t kind, ffs_stream stream);
 int ffs_islands_params(const ffs_islands *isl, ffs_params *out);
 
-/* Time the fused cellular kernel (and the decoder used by the pseudo
- * islands) at every launch shape and decoder variant that fits, on
- * generations that do not advance the state, keep the fastest for both and
- * report it (ffs_islands_params returns the parameters in use); synchronous. */
+/* Time one generation of every island at every launch shape and decoder
+ * variant that fits, `repeats` timed runs each (a shape's time is its
+ * fastest run), on generations that do not advance the state, keep the
+ * fastest shape and report it (ffs_islands_params returns the parameters in
+ * use); synchronous. */
 int ffs_islands_autotune(ffs_islands *isl, int32_t repeats, ffs_stream stream, int32_t *threads_out,
                          int32_t *chunk_out, float *best_ms);
 

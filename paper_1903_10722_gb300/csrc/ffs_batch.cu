@@ -473,7 +473,7 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
             if ((rc = batch_set_shape(b, Ts[ti], Bs[bi], st))) break;
             // writes the next-generation buffers only; the state does not advance
             if ((rc = batch_generation(b, false, nullptr, st))) break;
-            float total = 0.0f;
+            float fastest = -1.0f;   // the fastest of the timed runs: the least disturbed
             for (int r = 0; r < repeats && !rc; ++r) {
                 cudaEventRecord(e0, st);
                 rc = batch_generation(b, false, nullptr, st);
@@ -481,9 +481,9 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
                 if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(FFS_ECUDA, "autotune timing");
                 float ms = 0.0f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                total += ms;
+                if (fastest < 0.0f || ms < fastest) fastest = ms;
             }
-            const float avg = total / repeats;
+            const float avg = fastest;
             if (!rc && (best < 0.0f || avg < best)) {
                 best = avg;
                 bestT = Ts[ti];

@@ -1264,7 +1264,7 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
             S->prm.decode_variant = vi;
             // one untimed run, then the timed ones; they only rewrite the next-generation buffers
             if ((rc = islands_generation_launch(S, all, st))) break;
-            float total = 0.0f;
+            float fastest = -1.0f;   // the fastest of the timed runs: the least disturbed
             for (int r = 0; r < repeats && !rc; ++r) {
                 cudaEventRecord(e0, st);
                 rc = islands_generation_launch(S, all, st);
@@ -1272,9 +1272,9 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
                 if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(FFS_ECUDA, "autotune timing");
                 float ms = 0.0f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                total += ms;
+                if (fastest < 0.0f || ms < fastest) fastest = ms;
             }
-            const float avg = total / repeats;
+            const float avg = fastest;
             if (!rc && (best < 0.0f || avg < best)) {
                 best = avg;
                 bestT = Ts[ti];
