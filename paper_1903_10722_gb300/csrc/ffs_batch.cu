@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
     __shared__ DecodeLayout s_L;
     __shared__ uint32_t s_tbase;
     const int T = blockDim.x;
-    const int bits_per_warp = mark_words(shape.max_n, true);   // one byte per gene
+    const int bits_per_warp = mark_words(shape.max_n);   // one byte per gene
     const SmemMap map = smem_map(shape.max_n, shape.max_S, T, bits_per_warp);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * shape.max_S;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
         for (int base = un.y + warp * 32; base < end; base += T) {
             const int c = base + lane;
             const bool valid = c < end;
-            cellular_warp_cells<true>(L, g, ref, valid ? c : end - 1, valid, rows, cols, I.ld, wbits, region, T, tab,
+            cellular_warp_cells(L, g, ref, valid ? c : end - 1, valid, rows, cols, I.ld, wbits, region, T, tab,
                                       wst);
         }
     }
@@ -214,7 +214,7 @@ static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *sm
             s.max_tw = std::max(s.max_tw, tw);
         }
         if (tb && !any_tmem) continue;
-        const SmemMap m = smem_map(s.max_n, s.max_S, T, mark_words(s.max_n, true));
+        const SmemMap m = smem_map(s.max_n, s.max_S, T, mark_words(s.max_n));
         size_t bytes = (size_t)(m.region + s.max_tw * T) * 4u;
         if (bytes > 232448) continue;
         auto occ = [&](size_t by) {

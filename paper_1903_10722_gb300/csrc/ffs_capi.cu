@@ -479,7 +479,7 @@ int ffs_decode_plan(const ffs_instance *I, int32_t kernel, int32_t decode_chunk,
     if (variant < 0 || variant > kMaxVariant) return set_error(FFS_EINVAL, "decoder variant %d", variant);
     Plan p;
     const void *k = kernel == 0 ? eval_kernel() : kernel == 1 ? cellular_kernel() : step_decode_kernel();
-    int rc = plan_decode(I, k, decode_chunk, block_threads, kernel == 1 ? mark_words(I->n, true) : 0, &p, variant);
+    int rc = plan_decode(I, k, decode_chunk, block_threads, kernel == 1 ? mark_words(I->n) : 0, &p, variant);
     if (rc) return rc;
     if (chunk_out) *chunk_out = p.L.B;
     if (threads_out) *threads_out = p.T;

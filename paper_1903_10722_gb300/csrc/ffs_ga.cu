@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
-    const int bits_per_warp = mark_words(L.n, true);   // crossover mark: one byte per gene
+    const int bits_per_warp = mark_words(L.n);   // crossover mark: one byte per gene
     const SmemMap map = smem_map(L.n, L.S, T, bits_per_warp, L.obj_words);
     stage_table(smem + map.tab, tab_g, table_words(L.n, L.S) + L.obj_words);
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(512) k_cellular(DecodeLayout L, const uint32_t
         const bool valid = gc < total;
         const int bi = (valid ? gc : total - 1) / cells;
         const int c = (valid ? gc : total - 1) - bi * cells;
-        cellular_warp_cells<true>(Ls, g, batch.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
+        cellular_warp_cells(Ls, g, batch.ref[bi], c, valid, rows, cols, ld, wbits, region, T, tab, wst);
     }
     decode_tmem_end(Ls);
 }
@@ -69,7 +69,7 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBa
                     int ld, int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
 {
     Plan p;
-    const int bits_per_warp = mark_words(inst->n, true);
+    const int bits_per_warp = mark_words(inst->n);
     int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p, g.variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
@@ -166,11 +166,11 @@ __device__ __forceinline__ void pseudo_breed_warp(const GaScalars &g, const Isla
     job.p1 = a;
     job.p2 = b;
     job.child = s.children + (int64_t)slot * ld;
-    warp_build_children<true>(job, n, ld, bits);
+    warp_build_children(job, n, ld, bits);
     job.p1 = b;
     job.p2 = a;
     job.child = s.children + (int64_t)(slot + 1) * ld;
-    warp_build_children<true>(job, n, ld, bits);
+    warp_build_children(job, n, ld, bits);
 }
 
 __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n, int ld,
@@ -178,7 +178,7 @@ __global__ void k_pseudo_breed(GaScalars g, const __grid_constant__ IslandBatch 
 {
     extern __shared__ uint32_t bits_smem[];
     pseudo_breed_warp(g, batch, size, n, ld, s, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                      bits_smem + (threadIdx.x >> 5) * mark_words(n, true));
+                      bits_smem + (threadIdx.x >> 5) * mark_words(n));
 }
 
 // Lane l < kPairsPerWarp of a warp takes one pair: it keeps the two best of
@@ -252,7 +252,7 @@ __device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const Is
     const bool valid = lane < kCellsPerWarp && gc < total;
     const int gq = valid ? gc : base;
     const int bi = gq / cells, c = gq - bi * cells;
-    cellular_warp_breed<true>(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits, children + (int64_t)gq * ld);
+    cellular_warp_breed(batch.ref[bi], g, n, c, valid, rows, cols, ld, wbits, children + (int64_t)gq * ld);
 }
 
 // Both breeding halves of a dual generation in one launch: `cell_blocks`
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) k_breed_dual(GaScalars g, const __grid_co
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    uint32_t *wbits = smem + warp * mark_words(n, true);
+    uint32_t *wbits = smem + warp * mark_words(n);
     // the pseudo blocks first (0.3 % faster than the cellular ones first)
     const int P = gridDim.x - cell_blocks;
     if ((int)blockIdx.x >= P)
@@ -289,7 +289,7 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
     if (pairs <= 0) return FFS_OK;
     PseudoScratch s = carve(scratch, size, ld, batch.count);
     FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));
-    const int words = mark_words(inst->n, true);
+    const int words = mark_words(inst->n);
     const int T = 128;
     const size_t smem = (size_t)(T / 32) * words * 4;
     if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
@@ -384,7 +384,7 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
         // cellular and pseudo breeding in one launch
         FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));   // count and work
         const int T = 256;
-        const size_t smem = (size_t)(T / 32) * mark_words(inst->n, true) * 4;
+        const size_t smem = (size_t)(T / 32) * mark_words(inst->n) * 4;
         if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark too large");
         const int cell_warps = (rows * cols * cb.count + kCellsPerWarp - 1) / kCellsPerWarp;
         const int cell_blocks = (cell_warps + T / 32 - 1) / (T / 32);
@@ -1258,7 +1258,7 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
             const int B = Bs[bi] == 0 ? round_up(S->inst->n, 8) : Bs[bi];
             if (Bs[bi] != 0 && B >= S->inst->n) continue;
             Plan p;
-            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], mark_words(S->inst->n, true), &p, vi)) continue;
+            if (plan_decode(S->inst, cellular_kernel(), B, Ts[ti], mark_words(S->inst->n), &p, vi)) continue;
             S->prm.decode_chunk = B;
             S->prm.block_threads = Ts[ti];
             S->prm.decode_variant = vi;

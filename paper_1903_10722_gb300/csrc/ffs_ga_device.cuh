@@ -16,8 +16,8 @@ namespace fgpu {
 // Order crossover: the child keeps p1[l..r]; the other positions, from r+1
 // onward cyclically, take p2's genes met from position r+1 onward
 // cyclically, skipping genes already placed.  Without crossover the child
-// copies p1.  `mark` is the warp's shared mark of mark_words(n, BYTES) words:
-// one byte per gene (BYTES) or one bit.
+// copies p1.  `mark` is the warp's shared mark of mark_words(n) words, one
+// byte per gene.
 // ---------------------------------------------------------------------------
 struct ChildJob {
     const int16_t *p1;
@@ -28,12 +28,11 @@ struct ChildJob {
     bool active;
 };
 
-template <bool BYTES>
 __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, int ld, uint32_t *mark)
 {
     uint8_t *flag = reinterpret_cast<uint8_t *>(mark);
     const int lane = threadIdx.x & 31;
-    const int words = mark_words(n, BYTES);
+    const int words = mark_words(n);
     unsigned todo = __ballot_sync(0xFFFFFFFFu, me.active);
     while (todo) {
         const int j = __ffs(todo) - 1;
@@ -51,11 +50,7 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
             __syncwarp();
             continue;
         }
-        if constexpr (BYTES) {
-            for (int w = lane; 4 * w < words; w += 32) reinterpret_cast<uint4 *>(mark)[w] = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-            for (int w = lane; w < words; w += 32) mark[w] = 0u;
-        }
+        for (int w = lane; 4 * w < words; w += 32) reinterpret_cast<uint4 *>(mark)[w] = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
         // the segment p1[l..r], eight genes (one 16-byte block) per lane
         const int4 *p1v = reinterpret_cast<const int4 *>(p1);
@@ -71,10 +66,7 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
                 if (idx >= l && idx <= r) {
                     const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
                     if (!full) child[idx] = (int16_t)g;
-                    if ((unsigned)g < (unsigned)n) {
-                        if constexpr (BYTES) flag[g] = 1u;
-                        else atomicOr(&mark[g >> 5], 1u << (g & 31));
-                    }
+                    if ((unsigned)g < (unsigned)n) flag[g] = 1u;
                 }
             }
         }
@@ -102,9 +94,7 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
                 const int idx = 8 * q + u;
                 const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
                 gv[u] = g;
-                bool in_seg;
-                if constexpr (BYTES) in_seg = (unsigned)g < (unsigned)n && flag[g] != 0u;
-                else in_seg = (unsigned)g < (unsigned)n && ((mark[g >> 5] >> (g & 31)) & 1u);
+                const bool in_seg = (unsigned)g < (unsigned)n && flag[g] != 0u;
                 if (t <= nb && idx >= lo && idx < hi && !in_seg) take |= 1u << u;
             }
             const int cnt = __popc(take);
@@ -210,8 +200,7 @@ __device__ __forceinline__ void warp_copy_row_pairs(bool active, const int16_t *
 // cell's output row, or in `child_row` when that is given: then the cell
 // itself is copied to its output row (row and makespan), which the decoding
 // overwrites only if the child is better.  `wbits`: the warp's crossover
-// mark (BYTES as in warp_build_children).
-template <bool BYTES>
+// mark (warp_build_children).
 __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const GaScalars &g, int n, int c, bool valid,
                                                     int rows, int cols, int ld, uint32_t *wbits,
                                                     int16_t *child_row = nullptr)
@@ -254,7 +243,7 @@ __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const 
         job.r = max(u, v);
         mutate = fires(b1.w, g.cell_pm);
     }
-    warp_build_children<BYTES>(job, n, ld, wbits);
+    warp_build_children(job, n, ld, wbits);
     if (mutate) {
         int16_t *child = job.child;
         const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
@@ -320,15 +309,13 @@ __device__ __forceinline__ void cellular_warp_decode_child(const DecodeLayout &L
 }
 
 // One cellular generation for the cell `c` of each lane: breeding, then
-// decoding and replacement (see the two halves above).  BYTES: the
-// crossover mark's form (warp_build_children).
-template <bool BYTES = false>
+// decoding and replacement (see the two halves above).
 __device__ __forceinline__ void cellular_warp_cells(const DecodeLayout &Ls, const GaScalars &g, const IslandRef &ref,
                                                     int c, bool valid, int rows, int cols, int ld, uint32_t *wbits,
                                                     uint32_t *region, int T, const uint16_t *tab,
                                                     WarpStageState *wst)
 {
-    cellular_warp_breed<BYTES>(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
+    cellular_warp_breed(ref, g, Ls.n, c, valid, rows, cols, ld, wbits);
     cellular_warp_decode(Ls, g, ref, c, valid, ld, region, T, tab, wst);
 }
 

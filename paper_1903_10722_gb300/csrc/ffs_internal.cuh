@@ -39,7 +39,7 @@ struct SmemMap {
     int tab;       // processing-time table, then the objective's release / due tables
     int stage;     // [2S]: M_s, heap offset
     int warp;      // warp state, (T/32) * S * 2 words
-    int bits;      // per-warp crossover bitmask, (T/32) * bits_per_warp words
+    int bits;      // per-warp crossover mark, (T/32) * bits_per_warp words
     int region;    // per-thread interleaved region
 };
 
@@ -54,10 +54,9 @@ __host__ __device__ inline int table_words(int n, int S) { return round_up(S * t
 __host__ __device__ inline int objective_words(int n) { return 2 * round_up(n + 1, 4); }
 
 // Per-warp shared words for the order crossover's mark of the segment genes:
-// one byte per gene (a plain store to set, a byte load to test; every kernel
-// uses it), or a bitmask of n bits (atomic OR to set; a third of the shared
-// memory at n = 500).
-__host__ __device__ inline int mark_words(int n, bool bytes) { return bytes ? round_up(n, 16) / 4 : (n + 31) / 32; }
+// one byte per gene (a plain store to set, a byte load to test), rounded to
+// 16 bytes.
+__host__ __device__ inline int mark_words(int n) { return round_up(n, 16) / 4; }
 
 __host__ __device__ inline SmemMap smem_map(int n, int S, int T, int bits_per_warp = 0, int obj_words = 0)
 {
