@@ -182,6 +182,15 @@ def test_islands_fused_generation_flags(gpu):
     _islands_vs_oracle(gpu, spec, prm, oprm, 2, 8, 8, 2, 48, 9, 3, 1, check_every=3)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_islands_odd_sizes_migration(gpu, mode):
+    """Islands of an odd number of rows (5 x 5 tori): the ranking's per-island
+    key offsets and shared-memory staging take their odd-length paths."""
+    spec = make_instance(18, 4, 1, 4, seed=16)
+    prm, oprm = _params(gpu, seed=13, mode=mode, gap=2, ring=(10, 100), theta=(1, 1))
+    _islands_vs_oracle(gpu, spec, prm, oprm, 2, 5, 5, 2, 26, 6, 2, mode, check_every=2)
+
+
 def test_islands_more_than_one_batch_of_a_kind(gpu):
     """17 cellular islands (more than one launch batch) beside a pseudo island:
     generations take the per-kind launches instead of the fused pair."""
