@@ -8,8 +8,9 @@
  * sm_103a.  Conventions shared by all calls:
  *   - Every call returns an ffs_status; FFS_OK is 0.  No call exits, aborts
  *     or traps; on failure ffs_last_error() (per host thread) says why.
- *   - Handles (ffs_instance, ffs_islands) are opaque, owned by the library
- *     and released by their *_destroy call.
+ *   - Handles (ffs_instance, ffs_assign_instance, ffs_islands, ffs_batch,
+ *     ffs_mlp) are opaque, owned by the library and released by their
+ *     *_destroy call.
  *   - Host arrays given to *_create calls are copied; the caller keeps them.
  *   - "device" pointers must be CUDA device (or managed) memory of the
  *     current device; the call only enqueues work on `stream` and returns
@@ -17,7 +18,8 @@
  *     synchronises.  `stream` is a cudaStream_t (NULL = legacy default).
  *   - Chromosomes are job orders: a row of n int16 genes, a permutation of
  *     0..n-1, rows `ld` genes apart (ld >= n, ld a multiple of 8, row base
- *     16-byte aligned).
+ *     16-byte aligned) -- except for ffs_assign_eval, whose rows are the
+ *     paper's machine-assignment strings (see there).
  *   - Makespans are int32.  A row holding a gene outside [0, n) gets
  *     makespan -1 (it is not decoded).
  */
