@@ -1,0 +1,145 @@
+"""CPU re-statements of the schedules the CUDA kernels use, checked against
+the oracle's plain definitions (no GPU): the chunked ranking for migration
+(bitonic network split into register, shuffle and shared-memory steps, then
+binary-search merge), the order crossover placed in 16-byte blocks with a
+warp prefix sum, and the assignment decoder's merge of machine streams.
+These pin the kernels' reformulations; the GPU tests pin the kernels."""
+import numpy as np
+
+import oracle as orc
+
+U64 = np.iinfo(np.uint64).max
+
+
+def _chunk_sort(keys, C=2048, P=8):
+    """k_rank_chunks: C keys, P per thread; steps of distance >= 32 P in
+    shared memory, P <= j < 32 P by shuffles, j < P in registers."""
+    a = np.full(C, U64, dtype=np.uint64)
+    a[:len(keys)] = keys
+    nt, k = C // P, 2
+    while k <= C:
+        j = k >> 1
+        while j >= 32 * P:
+            e = np.arange(C)
+            o = e ^ j
+            m = o > e
+            ee, oo = e[m], o[m]
+            x, y = a[ee].copy(), a[oo].copy()
+            sw = (x > y) == ((ee & k) == 0)
+            a[ee], a[oo] = np.where(sw, y, x), np.where(sw, x, y)
+            j >>= 1
+        X = a.reshape(nt, P).copy()
+        t = np.arange(nt)[:, None]
+        e = P * t + np.arange(P)[None, :]
+        while j >= P:
+            lm = j // P
+            Y = X[np.arange(nt) ^ lm, :]
+            keep_min = ((np.arange(nt) & lm) == 0)[:, None] == ((e & k) == 0)
+            X = np.where(keep_min, np.minimum(X, Y), np.maximum(X, Y))
+            j >>= 1
+        for J in (4, 2, 1):
+            if J > j and J != 1:
+                continue
+            for r in range(P):
+                if r & J == 0:
+                    A, B = X[:, r].copy(), X[:, r | J].copy()
+                    sw = (A > B) == (((P * np.arange(nt) + r) & k) == 0)
+                    X[:, r], X[:, r | J] = np.where(sw, B, A), np.where(sw, A, B)
+        a = X.reshape(-1)
+        k <<= 1
+    return a[:len(keys)]
+
+
+def test_chunked_ranking_equals_the_plain_order():
+    rng = np.random.default_rng(2)
+    for N in [1, 5, 64, 2047, 2048, 2049, 5000, 16384]:
+        ms = rng.integers(0, 30 if N > 100 else 5, N)
+        keys = (ms.astype(np.uint64) << np.uint64(32)) | np.arange(N, dtype=np.uint64)
+        srt = np.concatenate([_chunk_sort(keys[c:c + 2048]) for c in range(0, N, 2048)])
+        order = np.full(N, -1)
+        for e in range(N):   # k_rank_merge: position in the chunk + lower bounds in the others
+            c0 = e // 2048 * 2048
+            rank = e - c0 + sum(int(np.searchsorted(srt[c2:c2 + 2048], srt[e])) for c2 in range(0, N, 2048) if c2 != c0)
+            assert order[rank] == -1
+            order[rank] = int(srt[e]) & 0xFFFFFFFF
+        assert np.array_equal(order, orc.rank_island(ms.astype(np.int64))), N
+
+
+def _ox_blocks(p1, p2, l, r):
+    """warp_build_children: the segment, then p2 in 16-byte blocks from block
+    (r+1)/8 cyclically, each lane's kept genes placed after a prefix sum."""
+    n = len(p1)
+    ld = (n + 7) // 8 * 8
+    P2 = np.zeros(ld, dtype=np.int64)
+    P2[:n] = p2
+    child = [None] * n
+    for k in range(l, r + 1):
+        child[k] = p1[k]
+    seg = set(p1[l:r + 1])
+    start = 0 if r + 1 == n else r + 1
+    nb, b0, placed = (n + 7) >> 3, start >> 3, 0
+    for t0 in range(0, nb + 1, 32):
+        takes, cnt = [], []
+        for lane in range(32):
+            t = t0 + lane
+            q = b0 + t - (nb if b0 + t >= nb else 0)
+            lo, hi = (start if t == 0 else 0), (start if t == nb else n)
+            if t > nb:   # lanes past the last pass load nothing
+                tk = [(False, 0)] * 8
+            else:
+                tk = [(lo <= 8 * q + u < hi and int(P2[8 * q + u]) not in seg, int(P2[8 * q + u])) for u in range(8)]
+            takes.append(tk)
+            cnt.append(sum(x for x, _ in tk))
+        incl = np.cumsum(cnt)
+        for lane in range(32):
+            pos = start + placed + incl[lane] - cnt[lane]
+            for take, g in takes[lane]:
+                if take:
+                    child[pos - n if pos >= n else pos] = g
+                    pos += 1
+        placed += int(incl[31])
+    return np.array(child, dtype=np.int16)
+
+
+def test_block_crossover_equals_the_oracle_ox():
+    rng = np.random.default_rng(3)
+    for trial in range(600):
+        n = int(rng.integers(1, 700)) if trial % 3 else int(rng.integers(1, 20))
+        p1, p2 = rng.permutation(n).astype(np.int16), rng.permutation(n).astype(np.int16)
+        u, v = rng.integers(0, n, 2)
+        l, r = int(min(u, v)), int(max(u, v))
+        assert np.array_equal(_ox_blocks(p1, p2, l, r), orc.order_crossover(p1, p2, l, r)), (n, l, r)
+
+
+def test_stream_merge_equals_the_sorted_arrival_order():
+    """k_eval_assign: a stage's arrivals are the previous stage's machine
+    streams merged by smallest head; every stream is in (completion, job)
+    order because a machine's completions increase (times >= 1).  Decoding
+    by that merge gives the oracle's objective."""
+    rng = np.random.default_rng(4)
+    for trial in range(40):
+        n, S = int(rng.integers(1, 40)), int(rng.integers(1, 6))
+        M = rng.integers(1, 5, size=S)
+        p_u = rng.integers(1, 30, size=(n, int(M.sum())))
+        R = rng.integers(0, 50, size=n)
+        genes = np.array([rng.integers(0, M[s]) for j in range(n) for s in range(S)], dtype=np.int16)
+        off = np.concatenate([[0], np.cumsum(M)[:-1]])
+        runs = [sorted((int(R[j]), j) for j in range(n))]
+        cmax = 0
+        for s in range(S):
+            streams = [[] for _ in range(M[s])]
+            free = [0] * M[s]
+            heads = [0] * len(runs)
+            for _ in range(n):
+                q = min((i for i in range(len(runs)) if heads[i] < len(runs[i])), key=lambda i: runs[i][heads[i]])
+                ready, j = runs[q][heads[q]]
+                heads[q] += 1
+                m = genes[j * S + s]
+                c = max(free[m], ready) + int(p_u[j, off[s] + m])
+                free[m] = c
+                streams[m].append((c, j))
+                cmax = max(cmax, c)
+            assert all(st == sorted(st) for st in streams)
+            runs = streams
+        inst = orc.AssignInstance(n, S, M, p_u, release=R)
+        assert orc.decode_assign(inst, genes) == max(c for st in runs for c, _ in st)
