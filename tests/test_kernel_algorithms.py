@@ -143,3 +143,67 @@ def test_stream_merge_equals_the_sorted_arrival_order():
             runs = streams
         inst = orc.AssignInstance(n, S, M, p_u, release=R)
         assert orc.decode_assign(inst, genes) == max(c for st in runs for c, _ in st)
+
+
+def _single(f, key, p, SH):
+    """One dispatch on the sorted key array f: pop f[0], insert the new key."""
+    low = (1 << SH) - 1
+    f0 = f[0]
+    x = p * (1 << SH) + max((f0 & ~low) | (key & low), key)
+    return f0, sorted(f[1:] + [x])
+
+
+def _pair(f, k1, p1, k2, p2, SH):
+    """The decoder's two-job dispatch: pop f[0], x1; q = min(f[1], x1) popped
+    second; x2; the sorted pair (lo, hi) of {max(f[1], x1), x2} merged into
+    f[2..]: slot k = max(min(f[k+2], lo), min(f[k+1], hi), f[k])."""
+    low = (1 << SH) - 1
+    M = len(f)
+    f0 = f[0]
+    x1 = p1 * (1 << SH) + max((f0 & ~low) | (k1 & low), k1)
+    if M == 1:
+        return f0, x1, [p2 * (1 << SH) + max((x1 & ~low) | (k2 & low), k2)]
+    q, y = min(f[1], x1), max(f[1], x1)
+    x2 = p2 * (1 << SH) + max((q & ~low) | (k2 & low), k2)
+    lo, hi = min(y, x2), max(y, x2)
+    g = []
+    for k in range(M):
+        t0 = min(f[k + 2], lo) if k + 2 < M else lo
+        if k == 0:
+            g.append(t0)
+        else:
+            t1 = min(f[k + 1], hi) if k + 1 < M else hi
+            g.append(max(t0, t1) if k == 1 else max(t0, t1, f[k]))
+    return f0, q, g
+
+
+def test_two_job_dispatch_equals_two_single_dispatches():
+    """Same pops and same heap as two single dispatches, for every heap size
+    the decoder instantiates, with ties in time (keys differ in the job bits)."""
+    rng = np.random.default_rng(7)
+    SH = 10
+    for trial in range(4000):
+        M = int(rng.integers(1, 33))
+        times = sorted(int(x) for x in rng.integers(0, 60, size=M))
+        f = sorted(t << SH | (int(rng.integers(1, 500)) << 1) for t in times)
+        k1 = int(rng.integers(0, 60)) << SH | (int(rng.integers(1, 500)) << 1)
+        k2 = int(rng.integers(0, 60)) << SH | (int(rng.integers(1, 500)) << 1)
+        p1, p2 = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+        a1, fa = _single(f, k1, p1, SH)
+        a2, fb = _single(fa, k2, p2, SH)
+        b1, b2, g = _pair(f, k1, p1, k2, p2, SH)
+        assert (a1, a2, fb) == (b1, b2, g), (M, trial)
+
+
+def test_completion_key_carries_the_job_and_the_later_start():
+    """x = p 2^SH + max((f & ~low) | (in & low), in): time max(time(f), time(in)) + p,
+    the incoming job's bits."""
+    rng = np.random.default_rng(8)
+    SH = 11
+    low = (1 << SH) - 1
+    for _ in range(2000):
+        tf, ti, p = (int(v) for v in rng.integers(0, 1 << 15, size=3))
+        jf, ji = (int(v) for v in rng.integers(1, 1000, size=2))
+        f, key = tf << SH | jf << 1, ti << SH | ji << 1
+        x = p * (1 << SH) + max((f & ~low) | (key & low), key)
+        assert x >> SH == max(tf, ti) + p and x & low == ji << 1
