@@ -15,7 +15,9 @@
 // key at each step and never sorts.  Keys are completion << SH | (job+1) << 1
 // as in the permutation decoder.  The streams live in a per-thread scratch of
 // 2n keys in global memory; the runs' heads and the per-machine counters, and
-// (when they fit) the stage's genes, in shared memory.
+// (when they fit) the stage's genes and table slice, in shared memory.  A call
+// runs in chunks of rows: k_assign_transpose copies a chunk's genes stage-major
+// (one byte each), then k_eval_assign decodes it, one row per thread.
 #include <algorithm>
 #include <vector>
 
@@ -25,7 +27,7 @@ namespace fgpu {
 
 constexpr int kAssignMaxM = 32;        // machines per stage
 constexpr int kAssignThreads = 128;
-constexpr size_t kAssignScratchCap = size_t(1) << 30;   // bytes of stream scratch at most
+constexpr size_t kAssignScratchCap = size_t(1) << 30;   // bytes of per-row scratch (streams + genes) at most
 
 struct AssignView {
     int32_t n, S, W, SH;
