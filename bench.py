@@ -511,7 +511,6 @@ def run_surrogate(args):
 
     import paper_1903_10722_gb300 as ffs
     from ffs_workloads import WORKLOADS, workload_instance
-    from oracle import mlp as omlp   # parameter initialisation (numpy) only
 
     torch.cuda.set_device(0)
     w = WORKLOADS["dual_100x10"]
@@ -527,7 +526,7 @@ def run_surrogate(args):
         net = None
         if mode == "screened":
             net = ffs.MLP(540, 512, 256, w["rows"] * w["cols"] * 8)
-            net.set_params(omlp.init_params(540, 512, 256, seed=3))
+            net.init(3)
             sp = ffs.ffs_surrogate_params_default()
             ffs.ffs_islands_attach_surrogate(isl, net, sp)
         torch.cuda.synchronize()

@@ -141,3 +141,18 @@ def workload_instance(name: str) -> InstanceSpec:
     w = WORKLOADS[name]
     p = w.get("p", (1, 99))
     return make_instance(w["n"], w["S"], w["m"][0], w["m"][1], p[0], p[1], seed=w["seed"])
+
+
+def mlp_params(in_dim: int, h1: int, h2: int, seed: int = 0) -> dict:
+    """Random network parameters for tests (numpy PCG64, He-style uniform
+    limits sqrt(6 / fan_in), the output weights scaled by 0.1, biases 0): an
+    input, like the instances above.  The library draws its own with
+    ffs_mlp_init."""
+    rng = np.random.default_rng(seed)
+
+    def u(shape, fan_in):
+        lim = np.sqrt(6.0 / fan_in)
+        return rng.uniform(-lim, lim, size=shape).astype(np.float32)
+    return {"W1": u((h1, in_dim), in_dim), "b1": np.zeros(h1, np.float32),
+            "W2": u((h2, h1), h1), "b2": np.zeros(h2, np.float32),
+            "w3": u((h2,), h2) * 0.1, "b3": np.float32(0.0)}

@@ -168,12 +168,14 @@ int ffs_population_eval_host(const ffs_instance *inst, const int16_t *pop, int64
  * of Philox applied to the counter (d / 4, cell, generation,
  * island | purpose << 24) under the key (low, high halves of seed).
  * Purposes: 1 initial population, 2 cellular generation, 3 pseudo
- * generation, 15 surrogate training batches, 16 + k surrogate candidate k.
+ * generation, 14 surrogate weight initialisation, 15 surrogate training
+ * batches, 16 + k surrogate candidate k.
  * out: device uint32[n_cells][n_draws], row c holding cell cell0 + c.
  * ---------------------------------------------------------------------- */
 #define FFS_PURPOSE_INIT 1
 #define FFS_PURPOSE_CELLULAR 2
 #define FFS_PURPOSE_PSEUDO 3
+#define FFS_PURPOSE_MLP_INIT 14
 #define FFS_PURPOSE_TRAIN_SAMPLE 15
 #define FFS_PURPOSE_SURROGATE 16   /* + candidate index */
 int ffs_philox_draws(uint64_t seed, uint32_t purpose, uint32_t island, uint32_t generation,
@@ -267,9 +269,11 @@ int ffs_pseudo_step(const ffs_instance *inst, const ffs_params *prm, uint32_t is
  *     array are rejected with FFS_EUNSUPPORTED, e.g. size 4096 with ld 480
  *     fits, size 16384 with ld 504 does not.
  *   - It calls no cudaMalloc / cudaFree and no allocating library routine.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - The first call in a CUDA context (per device, and again in the new
+ *     primary context after cudaDeviceReset) looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.  The address is cached per
+ *     context (keyed on the driver's context ID).
  *   - Every call on a device shares the one array and leaves its contents
  *     behind; the slot counter is cleared on the stream at the start of each
  *     call.  Calls that overlap on the GPU (different streams, or
@@ -371,9 +375,17 @@ int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream strea
  * ffs_batch_info: instance count, generations done, launch shape and the
  * decoder variant in use (1 / 2: one stage / stage pairs, saved heaps in
  * shared memory; 3 / 4: the same with saved heaps in tensor memory).
- * ffs_batch_get: rows and makespans of one instance (host or device
- * pointers, cudaMemcpyDefault).  ffs_batch_best: best makespan of every
- * instance into best[count] (host), synchronous.
+ * ffs_batch_get / ffs_batch_set: rows and makespans of one instance out /
+ * in (host or device pointers, cudaMemcpyDefault; either may be NULL).
+ * ffs_batch_best: best makespan of every instance into best[count] (host),
+ * synchronous.
+ * ffs_batch_checkpoint_bytes / _save / _load: the whole batch state (every
+ * instance's rows and makespans, the generation count, the decode count and
+ * the GA parameters) to or from a host blob of ffs_batch_checkpoint_bytes
+ * bytes; both synchronise `stream`.  Load accepts only a blob of a batch of
+ * the same instances and torus (FFS_EINVAL otherwise, nothing written); the
+ * launch shape in use is kept.  Generations after a load draw the same
+ * Philox streams as the uninterrupted run, so the results are identical.
  * ---------------------------------------------------------------------- */
 typedef struct ffs_batch ffs_batch;
 int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stages, const int32_t *machines,
@@ -387,7 +399,12 @@ int ffs_batch_info(const ffs_batch *b, int32_t *count, int64_t *generation, int3
                    int32_t *chunk, int32_t *blocks_per_sm, int32_t *variant);
 int ffs_batch_get(const ffs_batch *b, int32_t instance, int16_t *pop, int32_t ld_out, int32_t *makespan,
                   ffs_stream stream);
+int ffs_batch_set(ffs_batch *b, int32_t instance, const int16_t *pop, int32_t ld_in, const int32_t *makespan,
+                  ffs_stream stream);
 int ffs_batch_best(const ffs_batch *b, int32_t *best, ffs_stream stream);
+int64_t ffs_batch_checkpoint_bytes(const ffs_batch *b);
+int ffs_batch_checkpoint_save(const ffs_batch *b, void *host, int64_t capacity, ffs_stream stream);
+int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_stream stream);
 int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream);
 
 /* ------------------------------------------------------------------------
@@ -407,8 +424,21 @@ int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream);
  * activations and FP32 accumulation.  in_dim <= 4096; h1, h2 multiples of
  * 64 in [64, 1024]; batches up to max_batch (a multiple of 128).
  *   set_params/get take host FP32 arrays W1[h1][in_dim], b1[h1],
- *   W2[h2][h1], b2[h2], w3[h2], b3 (get with grads = 1 returns the last
- *   training step's gradients); both synchronise the device.
+ *   W2[h2][h1], b2[h2], w3[h2], b3; get returns the parameters (which = 0),
+ *   the last training step's gradients (1), or Adam's first (2) or second
+ *   (3) moment estimates; both synchronise the device.  set_params resets
+ *   Adam (moments 0, step count 0); ffs_mlp_adam_steps reports the count.
+ *   ffs_mlp_init: He-uniform initialisation (limit sqrt(6 / fan_in)) drawn
+ *   from Philox: W1[o][i] = lim1 * u(seed, purpose 14, island 1, cell o,
+ *   draw i), W2 likewise with island 2 and fan_in h1, w3[j] = (lim3 * u(seed,
+ *   14, 3, cell 0, draw j)) * 0.1, biases 0, where u(x) = ((x >> 8) - 2^23) /
+ *   2^23 of the draw x and each product is rounded once to FP32; resets
+ *   Adam.  Asynchronous on `stream`.
+ *   ffs_mlp_state_bytes / ffs_mlp_save / ffs_mlp_load: parameters, Adam
+ *   moments and step count to or from a host blob (a 40-byte header, then
+ *   n_params FP32 parameters, first moments and second moments in the
+ *   library's order); load accepts only a blob of a network of the same
+ *   sizes.  Both synchronise `stream`.
  *   forward: x device BF16 [B][ldx] (ldx >= in_dim, multiple of 8), y
  *   device FP32 [B].  train_step: one Adam step (beta 0.9/0.999, eps 1e-8)
  *   on the mean squared error to target (device FP32 [B]); B a multiple of
@@ -424,8 +454,13 @@ int ffs_mlp_destroy(ffs_mlp *mlp);
 int ffs_mlp_input_width(const ffs_mlp *mlp);
 int ffs_mlp_set_params(ffs_mlp *mlp, const float *W1, const float *b1, const float *W2, const float *b2,
                        const float *w3, float b3);
-int ffs_mlp_get(const ffs_mlp *mlp, int32_t grads, float *W1, float *b1, float *W2, float *b2, float *w3,
+int ffs_mlp_get(const ffs_mlp *mlp, int32_t which, float *W1, float *b1, float *W2, float *b2, float *w3,
                 float *b3);
+int ffs_mlp_init(ffs_mlp *mlp, uint64_t seed, ffs_stream stream);
+int ffs_mlp_adam_steps(const ffs_mlp *mlp, int64_t *steps);
+int64_t ffs_mlp_state_bytes(const ffs_mlp *mlp);
+int ffs_mlp_save(const ffs_mlp *mlp, void *host, int64_t capacity, ffs_stream stream);
+int ffs_mlp_load(ffs_mlp *mlp, const void *host, int64_t size, ffs_stream stream);
 int ffs_mlp_forward(ffs_mlp *mlp, const uint16_t *x, int32_t ldx, int32_t B, float *y, ffs_stream stream);
 int ffs_mlp_train_step(ffs_mlp *mlp, const uint16_t *x, int32_t ldx, const float *target, int32_t B, float lr,
                        float *loss, ffs_stream stream);
@@ -488,6 +523,21 @@ int ffs_selftest_wait_timeout(int64_t limit_ns, int32_t *status, ffs_stream stre
  * populations come back with ffs_islands_set); the next generation then
  * draws the same Philox streams as an uninterrupted run.  Synchronous. */
 int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
+
+/* Checkpoint / resume of the whole islands state to or from a host blob of
+ * ffs_checkpoint_bytes(isl) bytes: every island's current rows and
+ * makespans and generation count, the decode count, the GA parameters, and
+ * with a surrogate attached its ring buffer (filled slots and counters),
+ * training-round count and the network's parameters, Adam moments and step
+ * count.  Save and load synchronise `stream`.  Load checks that the blob
+ * comes from a handle of the same instance (a fingerprint of n, S, M, p and
+ * the objective's tables), islands, row stride and surrogate shape (attach
+ * the surrogate before loading), else FFS_EINVAL with nothing written; the
+ * launch shape in use is kept.  Generations after a load are identical to
+ * those of the uninterrupted run. */
+int64_t ffs_checkpoint_bytes(const ffs_islands *isl);
+int ffs_checkpoint_save(const ffs_islands *isl, void *host, int64_t capacity, ffs_stream stream);
+int ffs_checkpoint_load(ffs_islands *isl, const void *host, int64_t size, ffs_stream stream);
 
 /* Launch one generation's kernels (kind 0: the cellular islands alone,
  * 1: the pseudo islands alone, 2: all islands -- the breeding launch, the

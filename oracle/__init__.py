@@ -136,6 +136,12 @@ def _load():
         lib.orc_pseudo_generation.argtypes = gen_args + [ctypes.c_int32, ctypes.c_int64,
                                                          _i16p, _i64p, _i16p, _i64p]
         lib.orc_pseudo_generation.restype = ctypes.c_int64
+        lib.orc_cellular_generation_range.argtypes = lib.orc_cellular_generation.argtypes + [ctypes.c_int32,
+                                                                                             ctypes.c_int32]
+        lib.orc_cellular_generation_range.restype = ctypes.c_int64
+        lib.orc_pseudo_generation_range.argtypes = lib.orc_pseudo_generation.argtypes + [ctypes.c_int32,
+                                                                                         ctypes.c_int32]
+        lib.orc_pseudo_generation_range.restype = ctypes.c_int64
         lib.orc_screened_cellular_generation.argtypes = gen_args + [
             ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _i16p, _i64p, _i16p, _i64p,
             ctypes.POINTER(ctypes.c_float), ctypes.c_int32, _i32p, _i16p]
@@ -259,6 +265,13 @@ def eval_population(inst: Instance, pop: np.ndarray) -> np.ndarray:
     lib.orc_eval_population_obj(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), _ptr(inst.p, ctypes.c_int32),
                                 inst.obj_addr(), _ptr(pop, ctypes.c_int16), N, ld, _ptr(out, ctypes.c_int64))
     return out
+
+
+def eval_population_threads(inst: Instance, pop: np.ndarray, pool, parts: int) -> np.ndarray:
+    """eval_population with the rows split into `parts` ranges on a thread pool."""
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    chunks = [(a, b) for a, b in _split(pop.shape[0], parts) if b > a]
+    return np.concatenate([r for r in pool.map(lambda ab: eval_population(inst, pop[ab[0]:ab[1]]), chunks)])
 
 
 class AssignInstance:
@@ -397,6 +410,53 @@ def cellular_generation(inst: Instance, prm: Params, island: int, generation: in
     return out, out_ms, int(k)
 
 
+def _split(total: int, parts: int):
+    parts = max(1, min(parts, total))
+    edges = [total * i // parts for i in range(parts + 1)]
+    return [(edges[i], edges[i + 1]) for i in range(parts)]
+
+
+def cellular_generation_threads(inst: Instance, prm: Params, island: int, generation: int, rows: int, cols: int,
+                                pop: np.ndarray, ms: np.ndarray, pool, parts: int):
+    """cellular_generation with the cells split into `parts` ranges run on a
+    thread pool (the C calls release the GIL); the same result."""
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    ms = np.ascontiguousarray(ms, dtype=np.int64)
+    out = np.zeros_like(pop)
+    out_ms = np.zeros_like(ms)
+    cp = prm._c(inst)
+
+    def run(r):
+        return lib.orc_cellular_generation_range(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
+                                                 _ptr(inst.p, ctypes.c_int32), ctypes.byref(cp), island, generation,
+                                                 rows, cols, pop.shape[1], _ptr(pop, ctypes.c_int16),
+                                                 _ptr(ms, ctypes.c_int64), _ptr(out, ctypes.c_int16),
+                                                 _ptr(out_ms, ctypes.c_int64), r[0], r[1])
+    k = sum(pool.map(run, _split(rows * cols, parts)))
+    return out, out_ms, int(k)
+
+
+def pseudo_generation_threads(inst: Instance, prm: Params, island: int, generation: int, pop: np.ndarray,
+                              ms: np.ndarray, pool, parts: int):
+    """pseudo_generation with the pairs split into `parts` ranges on a thread pool."""
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    ms = np.ascontiguousarray(ms, dtype=np.int64)
+    out = np.zeros_like(pop)
+    out_ms = np.zeros_like(ms)
+    cp = prm._c(inst)
+
+    def run(r):
+        return lib.orc_pseudo_generation_range(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
+                                               _ptr(inst.p, ctypes.c_int32), ctypes.byref(cp), island, generation,
+                                               pop.shape[0], pop.shape[1], _ptr(pop, ctypes.c_int16),
+                                               _ptr(ms, ctypes.c_int64), _ptr(out, ctypes.c_int16),
+                                               _ptr(out_ms, ctypes.c_int64), r[0], r[1])
+    k = sum(pool.map(run, _split(pop.shape[0] // 2, parts)))
+    return out, out_ms, int(k)
+
+
 def screened_cellular_generation(inst: Instance, prm: Params, island: int, generation: int, rows: int,
                                  cols: int, pop: np.ndarray, ms: np.ndarray, scores: np.ndarray, K: int):
     """One surrogate-screened cellular generation given the candidates' scores;
@@ -485,7 +545,7 @@ def migrate_penetration(popA, msA, popB, msB, n: int, theta_num: int = 1, theta_
 # ---------------------------------------------------------------------------
 class IslandGA:
     def __init__(self, inst: Instance, prm: Params, n_cellular: int, rows: int, cols: int,
-                 n_pseudo: int, pseudo_size: int, ld: int | None = None):
+                 n_pseudo: int, pseudo_size: int, ld: int | None = None, pool=None, parts: int = 1):
         self.inst, self.prm = inst, prm
         self.rows, self.cols = rows, cols
         self.ld = ld if ld is not None else ((inst.n + 7) // 8) * 8
@@ -510,7 +570,7 @@ class IslandGA:
                     pop[2 * q, :inst.n] = a
                     pop[2 * q + 1, :inst.n] = b
             self.pops.append(pop)
-            self.mss.append(eval_population(inst, pop))
+            self.mss.append(eval_population_threads(inst, pop, pool, parts) if pool else eval_population(inst, pop))
         self.decoded = 0
 
     def step(self):
@@ -522,6 +582,20 @@ class IslandGA:
                                               self.pops[i], self.mss[i])
             else:
                 p, m, d = pseudo_generation(self.inst, self.prm, i, g, self.pops[i], self.mss[i])
+            self.pops[i], self.mss[i] = p, m
+            self.decoded += d
+
+    def step_threads(self, pool, parts: int):
+        """step() with every island's cells or pairs split over a thread pool."""
+        self.generation += 1
+        g = self.generation
+        for i, k in enumerate(self.kinds):
+            if k == "cellular":
+                p, m, d = cellular_generation_threads(self.inst, self.prm, i, g, self.rows, self.cols,
+                                                      self.pops[i], self.mss[i], pool, parts)
+            else:
+                p, m, d = pseudo_generation_threads(self.inst, self.prm, i, g, self.pops[i], self.mss[i], pool,
+                                                    parts)
             self.pops[i], self.mss[i] = p, m
             self.decoded += d
 

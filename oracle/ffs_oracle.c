@@ -426,15 +426,16 @@ void orc_cellular_child(int32_t n, int32_t rows, int32_t cols, int32_t c,
  * (pop_out, ms_out); the child replaces the cell iff its makespan is lower
  * (or not higher, with cell_replace_le).  Returns the number of children
  * decoded. */
-int64_t orc_cellular_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
-                                const orc_params *prm, uint32_t island, uint32_t generation,
-                                int32_t rows, int32_t cols, int64_t ld,
-                                const int16_t *pop_in, const int64_t *ms_in,
-                                int16_t *pop_out, int64_t *ms_out)
+/* Cells c0 .. c1-1 of one cellular generation (the cells are independent
+ * within a generation: each reads only the previous generation). */
+int64_t orc_cellular_generation_range(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                                      const orc_params *prm, uint32_t island, uint32_t generation,
+                                      int32_t rows, int32_t cols, int64_t ld,
+                                      const int16_t *pop_in, const int64_t *ms_in,
+                                      int16_t *pop_out, int64_t *ms_out, int32_t c0, int32_t c1)
 {
-    int32_t cells = rows * cols;
     int16_t *child = (int16_t *)malloc((size_t)n * sizeof(int16_t));
-    for (int32_t c = 0; c < cells; ++c) {
+    for (int32_t c = c0; c < c1; ++c) {
         uint32_t x[10];
         for (uint32_t d = 0; d < 10u; ++d)
             x[d] = orc_draw(prm->seed, ORC_PURPOSE_CELLULAR, island, generation, (uint32_t)c, d);
@@ -451,7 +452,17 @@ int64_t orc_cellular_generation(int32_t n, int32_t S, const int32_t *M, const in
         }
     }
     free(child);
-    return cells;
+    return c1 - c0;
+}
+
+int64_t orc_cellular_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                                const orc_params *prm, uint32_t island, uint32_t generation,
+                                int32_t rows, int32_t cols, int64_t ld,
+                                const int16_t *pop_in, const int64_t *ms_in,
+                                int16_t *pop_out, int64_t *ms_out)
+{
+    return orc_cellular_generation_range(n, S, M, p, prm, island, generation, rows, cols, ld, pop_in, ms_in,
+                                         pop_out, ms_out, 0, rows * cols);
 }
 
 /* Complementary parents of the pseudo island (Section 4.1): a pair is a
@@ -487,16 +498,18 @@ void orc_family_best2(const int64_t fms[4], int32_t out[2])
  * (c1, c2, a, b) ranked by (makespan, that role order), best in slot 2k.
  * Without crossover the pair is copied unchanged.  Returns the number of
  * children decoded. */
-int64_t orc_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
-                              const orc_params *prm, uint32_t island, uint32_t generation,
-                              int32_t size, int64_t ld,
-                              const int16_t *pop_in, const int64_t *ms_in,
-                              int16_t *pop_out, int64_t *ms_out)
+/* Pairs k0 .. k1-1 of one pseudo generation (pairs are independent). */
+int64_t orc_pseudo_generation_range(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                                    const orc_params *prm, uint32_t island, uint32_t generation,
+                                    int32_t size, int64_t ld,
+                                    const int16_t *pop_in, const int64_t *ms_in,
+                                    int16_t *pop_out, int64_t *ms_out, int32_t k0, int32_t k1)
 {
+    (void)size;
     int16_t *c1 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
     int16_t *c2 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
     int64_t decoded = 0;
-    for (int32_t k = 0; k < size / 2; ++k) {
+    for (int32_t k = k0; k < k1; ++k) {
         const int16_t *a = pop_in + (int64_t)(2 * k) * ld;
         const int16_t *b = pop_in + (int64_t)(2 * k + 1) * ld;
         int16_t *oa = pop_out + (int64_t)(2 * k) * ld;
@@ -540,6 +553,16 @@ int64_t orc_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int3
     }
     free(c1); free(c2);
     return decoded;
+}
+
+int64_t orc_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                              const orc_params *prm, uint32_t island, uint32_t generation,
+                              int32_t size, int64_t ld,
+                              const int16_t *pop_in, const int64_t *ms_in,
+                              int16_t *pop_out, int64_t *ms_out)
+{
+    return orc_pseudo_generation_range(n, S, M, p, prm, island, generation, size, ld, pop_in, ms_in, pop_out,
+                                       ms_out, 0, size / 2);
 }
 
 /* ------------------------------------------------------------------ */

@@ -29,16 +29,29 @@ def bf16_round(x) -> np.ndarray:
     return out
 
 
-def init_params(in_dim: int, h1: int, h2: int, seed: int = 0) -> dict:
-    """He-style uniform initialisation, drawn with numpy (an input, not the method)."""
-    rng = np.random.default_rng(seed)
+def init_params_philox(in_dim: int, h1: int, h2: int, seed: int) -> dict:
+    """The library's documented weight initialisation restated with the
+    oracle's own Philox: He-uniform (He et al. 2015; limit sqrt(6 / fan_in)
+    in float32), element (o, i) of layer L (1: W1, 2: W2, 3: w3 as one row)
+    from draw i of the stream (seed, purpose 14, island L, generation 0,
+    cell o), u = ((x >> 8) - 2^23) / 2^23, value lim * u (then * 0.1 for w3),
+    each product rounded once to float32; biases 0."""
+    from oracle import draw
 
-    def u(shape, fan_in):
-        lim = np.sqrt(6.0 / fan_in)
-        return rng.uniform(-lim, lim, size=shape).astype(np.float32)
-    return {"W1": u((h1, in_dim), in_dim), "b1": np.zeros(h1, np.float32),
-            "W2": u((h2, h1), h1), "b2": np.zeros(h2, np.float32),
-            "w3": u((h2,), h2) * 0.1, "b3": np.float32(0.0)}
+    def layer(rows, cols, fan_in, L, scale=None):
+        lim = np.sqrt(np.float32(6.0) / np.float32(fan_in), dtype=np.float32)
+        W = np.zeros((rows, cols), dtype=np.float32)
+        for o in range(rows):
+            x = np.array([draw(seed, 14, L, 0, o, i) for i in range(cols)], dtype=np.int64)
+            u = (((x >> 8) - (1 << 23)).astype(np.float32) * np.float32(1.0 / 8388608.0)).astype(np.float32)
+            v = (lim * u).astype(np.float32)
+            if scale is not None:
+                v = (v * np.float32(scale)).astype(np.float32)
+            W[o] = v
+        return W
+    return {"W1": layer(h1, in_dim, in_dim, 1), "b1": np.zeros(h1, np.float32),
+            "W2": layer(h2, h1, h1, 2), "b2": np.zeros(h2, np.float32),
+            "w3": layer(1, h2, h2, 3, scale=0.1)[0], "b3": np.float32(0.0)}
 
 
 def forward(params: dict, X, rounded: bool = True):

@@ -22,6 +22,7 @@ _lib = None
 
 FFS_OK, FFS_EINVAL, FFS_ENOMEM, FFS_ECUDA, FFS_EOVERFLOW, FFS_ETIMEOUT, FFS_EDEVICE, FFS_EUNSUPPORTED = range(8)
 FFS_PURPOSE_INIT, FFS_PURPOSE_CELLULAR, FFS_PURPOSE_PSEUDO, FFS_PURPOSE_SURROGATE = 1, 2, 3, 16
+FFS_PURPOSE_MLP_INIT = 14
 FFS_MIG_NONE, FFS_MIG_RING, FFS_MIG_PENETRATION = 0, 1, 2
 
 _vp = ctypes.c_void_p
@@ -109,6 +110,18 @@ _SIGS = [
     ("ffs_islands_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     ("ffs_islands_dry_run", _i32, [_vp, _i32, _vp]),
     ("ffs_islands_params", _i32, [_vp, ctypes.POINTER(ffs_params)]),
+    ("ffs_mlp_init", _i32, [_vp, _u64, _vp]),
+    ("ffs_mlp_adam_steps", _i32, [_vp, _vp]),
+    ("ffs_mlp_state_bytes", _i64, [_vp]),
+    ("ffs_mlp_save", _i32, [_vp, _vp, _i64, _vp]),
+    ("ffs_mlp_load", _i32, [_vp, _vp, _i64, _vp]),
+    ("ffs_checkpoint_bytes", _i64, [_vp]),
+    ("ffs_checkpoint_save", _i32, [_vp, _vp, _i64, _vp]),
+    ("ffs_checkpoint_load", _i32, [_vp, _vp, _i64, _vp]),
+    ("ffs_batch_set", _i32, [_vp, _i32, _vp, _i32, _vp, _vp]),
+    ("ffs_batch_checkpoint_bytes", _i64, [_vp]),
+    ("ffs_batch_checkpoint_save", _i32, [_vp, _vp, _i64, _vp]),
+    ("ffs_batch_checkpoint_load", _i32, [_vp, _vp, _i64, _vp]),
 ]
 
 
@@ -409,6 +422,23 @@ def ffs_islands_decoded(isl: Islands, stream=None) -> int:
     return c.value
 
 
+def ffs_checkpoint_save(isl: Islands, stream=None):
+    """The islands' whole state as a host byte array (numpy uint8)."""
+    import numpy as np
+    n = int(load().ffs_checkpoint_bytes(isl.handle))
+    if n < 0:
+        _check(FFS_EINVAL)
+    buf = np.zeros(n, dtype=np.uint8)
+    _check(load().ffs_checkpoint_save(isl.handle, buf.ctypes.data, n, _stream(stream)))
+    return buf
+
+
+def ffs_checkpoint_load(isl: Islands, blob, stream=None):
+    import numpy as np
+    b = np.ascontiguousarray(blob, dtype=np.uint8)
+    _check(load().ffs_checkpoint_load(isl.handle, b.ctypes.data, b.size, _stream(stream)))
+
+
 def island_tensors(isl: Islands, island: int):
     """(pop int16 [N][n], makespans int32 [N]) of one island, as CUDA tensors."""
     import torch
@@ -475,6 +505,27 @@ def ffs_batch_get(b: Batch, instance: int, pop, ld_out: int, makespan, stream=No
     _check(load().ffs_batch_get(b.handle, instance, _ptr(pop), ld_out, _ptr(makespan), _stream(stream)))
 
 
+def ffs_batch_set(b: Batch, instance: int, pop, ld_in: int, makespan, stream=None):
+    _check(load().ffs_batch_set(b.handle, instance, _ptr(pop), ld_in, _ptr(makespan), _stream(stream)))
+
+
+def ffs_batch_checkpoint_save(b: Batch, stream=None):
+    """The batch's whole state as a host byte array (numpy uint8)."""
+    import numpy as np
+    n = int(load().ffs_batch_checkpoint_bytes(b.handle))
+    if n < 0:
+        _check(FFS_EINVAL)
+    buf = np.zeros(n, dtype=np.uint8)
+    _check(load().ffs_batch_checkpoint_save(b.handle, buf.ctypes.data, n, _stream(stream)))
+    return buf
+
+
+def ffs_batch_checkpoint_load(b: Batch, blob, stream=None):
+    import numpy as np
+    buf = np.ascontiguousarray(blob, dtype=np.uint8)
+    _check(load().ffs_batch_checkpoint_load(b.handle, buf.ctypes.data, buf.size, _stream(stream)))
+
+
 def ffs_batch_best(b: Batch, stream=None):
     import numpy as np
     out = np.zeros(b.count, dtype=np.int32)
@@ -522,16 +573,40 @@ class MLP:
         arrs = [np.ascontiguousarray(p[k], dtype=np.float32) for k in ("W1", "b1", "W2", "b2", "w3")]
         _check(load().ffs_mlp_set_params(self.handle, *[a.ctypes.data for a in arrs], float(p["b3"])))
 
-    def get(self, grads: bool = False) -> dict:
+    def get(self, grads: bool = False, which: int | None = None) -> dict:
+        """Parameters (which 0), last gradients (1, or grads=True), Adam's
+        first (2) or second (3) moments, as host float32 arrays."""
         import numpy as np
+        w = int(grads) if which is None else int(which)
         out = {"W1": np.zeros((self.h1, self.in_dim), np.float32), "b1": np.zeros(self.h1, np.float32),
                "W2": np.zeros((self.h2, self.h1), np.float32), "b2": np.zeros(self.h2, np.float32),
                "w3": np.zeros(self.h2, np.float32)}
         b3 = ctypes.c_float()
-        _check(load().ffs_mlp_get(self.handle, int(grads), *[out[k].ctypes.data for k in ("W1", "b1", "W2", "b2", "w3")],
+        _check(load().ffs_mlp_get(self.handle, w, *[out[k].ctypes.data for k in ("W1", "b1", "W2", "b2", "w3")],
                                   ctypes.byref(b3)))
         out["b3"] = np.float32(b3.value)
         return out
+
+    def init(self, seed: int, stream=None):
+        """He-uniform weights drawn from Philox (ffs_mlp_init), biases 0."""
+        _check(load().ffs_mlp_init(self.handle, seed, _stream(stream)))
+
+    def adam_steps(self) -> int:
+        t = _i64()
+        _check(load().ffs_mlp_adam_steps(self.handle, ctypes.byref(t)))
+        return t.value
+
+    def save(self, stream=None):
+        import numpy as np
+        n = int(load().ffs_mlp_state_bytes(self.handle))
+        buf = np.zeros(n, dtype=np.uint8)
+        _check(load().ffs_mlp_save(self.handle, buf.ctypes.data, n, _stream(stream)))
+        return buf
+
+    def load_state(self, blob, stream=None):
+        import numpy as np
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(load().ffs_mlp_load(self.handle, b.ctypes.data, b.size, _stream(stream)))
 
     def close(self):
         if getattr(self, "handle", None):

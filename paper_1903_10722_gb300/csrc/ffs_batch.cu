@@ -564,3 +564,145 @@ int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Rows in, and checkpoint / resume of a batch.  Blob (host memory), every
+// section padded to 16 bytes: BatchBlobHeader, then per instance its
+// current rows [cells][ld_i] int16 and makespans [cells] int32.
+// ---------------------------------------------------------------------------
+namespace fgpu {
+
+struct BatchBlobHeader {
+    uint32_t magic, version;
+    int32_t count, rows, cols, pad;
+    uint64_t fingerprint;
+    int64_t generation, decoded;
+    ffs_params prm;
+};
+constexpr uint32_t kBatchBlobMagic = 0x42534646u, kBatchBlobVersion = 1;
+
+static int64_t b16(int64_t b) { return (b + 15) / 16 * 16; }
+
+static uint64_t batch_fingerprint(const ffs_batch *b)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (const ffs_instance *I : b->insts) h = instance_fingerprint(I, h);
+    return h;
+}
+
+static int64_t batch_blob_bytes(const ffs_batch *b)
+{
+    const int64_t cells = (int64_t)b->rows * b->cols;
+    int64_t s = b16(sizeof(BatchBlobHeader));
+    for (const BatchInst &h : b->hinst) s += b16(cells * h.ld * 2) + b16(cells * 4);
+    return s;
+}
+
+}  // namespace fgpu
+
+extern "C" {
+
+int ffs_batch_set(ffs_batch *b, int32_t instance, const int16_t *pop, int32_t ld_in, const int32_t *ms,
+                  ffs_stream stream)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (instance < 0 || instance >= b->count) return set_error(FFS_EINVAL, "instance %d", instance);
+    const BatchInst &h = b->hinst[instance];
+    const int cells = b->rows * b->cols;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pop) {
+        if (ld_in < h.n) return set_error(FFS_EINVAL, "ld_in %d < n %d", ld_in, h.n);
+        FFS_CUDA_TRY(cudaMemcpy2DAsync(h.pop[b->host_cur], (size_t)h.ld * 2, pop, (size_t)ld_in * 2, (size_t)h.n * 2,
+                                       cells, cudaMemcpyDefault, st));
+    }
+    if (ms) FFS_CUDA_TRY(cudaMemcpyAsync(h.ms[b->host_cur], ms, (size_t)cells * 4, cudaMemcpyDefault, st));
+    return FFS_OK;
+}
+
+int64_t ffs_batch_checkpoint_bytes(const ffs_batch *b) { return b ? batch_blob_bytes(b) : -1; }
+
+int ffs_batch_checkpoint_save(const ffs_batch *b, void *host, int64_t capacity, ffs_stream stream)
+{
+    clear_error();
+    if (!b || !host) return set_error(FFS_EINVAL, "NULL argument");
+    const int64_t need = batch_blob_bytes(b);
+    if (capacity < need) return set_error(FFS_EINVAL, "capacity %lld < %lld bytes", (long long)capacity, (long long)need);
+    cudaStream_t st = (cudaStream_t)stream;
+    BlobWriter w{static_cast<char *>(host), capacity};
+    BatchBlobHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = kBatchBlobMagic;
+    hd.version = kBatchBlobVersion;
+    hd.count = b->count;
+    hd.rows = b->rows;
+    hd.cols = b->cols;
+    hd.fingerprint = batch_fingerprint(b);
+    hd.generation = b->host_gen;
+    hd.prm = b->prm;
+    unsigned long long dec = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&dec, b->d_decoded, 8, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    hd.decoded = (int64_t)dec;
+    memcpy(w.take(b16(sizeof(hd))), &hd, sizeof(hd));
+    const int64_t cells = (int64_t)b->rows * b->cols;
+    for (const BatchInst &h : b->hinst) {
+        char *rows = w.take(b16(cells * h.ld * 2));
+        char *ms = w.take(b16(cells * 4));
+        FFS_CUDA_TRY(cudaMemcpyAsync(rows, h.pop[b->host_cur], (size_t)cells * h.ld * 2, cudaMemcpyDefault, st));
+        FFS_CUDA_TRY(cudaMemcpyAsync(ms, h.ms[b->host_cur], (size_t)cells * 4, cudaMemcpyDefault, st));
+    }
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
+int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_stream stream)
+{
+    clear_error();
+    if (!b || !host) return set_error(FFS_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    BlobReader r{static_cast<const char *>(host), size};
+    const char *hp = r.take(b16(sizeof(BatchBlobHeader)));
+    if (!hp) return set_error(FFS_EINVAL, "checkpoint truncated (header)");
+    BatchBlobHeader hd;
+    memcpy(&hd, hp, sizeof(hd));
+    if (hd.magic != kBatchBlobMagic || hd.version != kBatchBlobVersion)
+        return set_error(FFS_EINVAL, "not a batch checkpoint of this version");
+    if (hd.count != b->count || hd.rows != b->rows || hd.cols != b->cols)
+        return set_error(FFS_EINVAL, "checkpoint of %d instances on %dx%d tori; this batch: %d on %dx%d", hd.count,
+                         hd.rows, hd.cols, b->count, b->rows, b->cols);
+    if (hd.fingerprint != batch_fingerprint(b)) return set_error(FFS_EINVAL, "checkpoint of other instances");
+    if (hd.generation < 0 || hd.generation > 0x7FFFFFFF)
+        return set_error(FFS_EINVAL, "generation %lld", (long long)hd.generation);
+    const int64_t cells = (int64_t)b->rows * b->cols;
+    std::vector<const char *> rows(b->count), mss(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        rows[i] = r.take(b16(cells * b->hinst[i].ld * 2));
+        mss[i] = r.take(b16(cells * 4));
+        if (!rows[i] || !mss[i]) return set_error(FFS_EINVAL, "checkpoint truncated (instance %d)", i);
+    }
+    for (int i = 0; i < b->count; ++i) {
+        const BatchInst &h = b->hinst[i];
+        FFS_CUDA_TRY(cudaMemcpyAsync(h.pop[b->host_cur], rows[i], (size_t)cells * h.ld * 2, cudaMemcpyDefault, st));
+        FFS_CUDA_TRY(cudaMemcpyAsync(h.ms[b->host_cur], mss[i], (size_t)cells * 4, cudaMemcpyDefault, st));
+    }
+    const int32_t g32 = (int32_t)hd.generation;
+    FFS_CUDA_TRY(cudaMemcpyAsync(b->d_gen, &g32, 4, cudaMemcpyHostToDevice, st));
+    const unsigned long long dec = (unsigned long long)hd.decoded;
+    FFS_CUDA_TRY(cudaMemcpyAsync(b->d_decoded, &dec, 8, cudaMemcpyHostToDevice, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    b->host_gen = hd.generation;
+    // the GA parameters come back; the launch shape stays the one in use
+    const ffs_params keep = b->prm;
+    b->prm = hd.prm;
+    b->prm.decode_chunk = keep.decode_chunk;
+    b->prm.block_threads = keep.block_threads;
+    b->prm.decode_variant = keep.decode_variant;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return FFS_OK;
+}
+
+}  // extern "C"

@@ -15,8 +15,9 @@ constexpr int kMaxStages = 64;
 
 // Purpose codes of the Philox counter's fourth word (bits 24..31):
 // surrogate candidate k of a cell uses kPurposeSurrogateBase + k (k < 16),
-// the surrogate's training-batch sampling kPurposeTrainSample.
-constexpr uint32_t kPurposeInit = 1, kPurposeCellular = 2, kPurposePseudo = 3,
+// the surrogate's training-batch sampling kPurposeTrainSample, its weight
+// initialisation kPurposeMlpInit.
+constexpr uint32_t kPurposeInit = 1, kPurposeCellular = 2, kPurposePseudo = 3, kPurposeMlpInit = 14,
                    kPurposeTrainSample = 15, kPurposeSurrogateBase = 16;
 
 // ---------------------------------------------------------------------------

@@ -1505,3 +1505,205 @@ int ffs_islands_decoded(const ffs_islands *S, int64_t *count, ffs_stream stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume of an islands handle.  Blob (host memory), every
+// section padded to 16 bytes:
+//   IslandsBlobHeader; per island (kind, size, generation);
+//   per island its current rows [size][ld] int16 and makespans [size] int32;
+//   with a surrogate attached: SurrogateBlob, the filled ring slots' rows
+//   [valid][ld] and makespans [valid], and the network's state (parameters,
+//   Adam moments and step count).
+// ---------------------------------------------------------------------------
+namespace fgpu {
+
+struct IslandsBlobHeader {
+    uint32_t magic, version;
+    int32_t I, ld, n, has_surrogate;
+    uint64_t fingerprint;
+    int64_t decoded;
+    ffs_params prm;
+};
+struct IslandBlobEntry {
+    int32_t kind, size;
+    int64_t generation;
+};
+struct SurrogateBlob {
+    int32_t candidates, pad;
+    int64_t ring_cap, ring_count, train_rounds, valid;
+};
+constexpr uint32_t kIslandsBlobMagic = 0x49534646u, kIslandsBlobVersion = 1;
+
+static int64_t r16(int64_t b) { return (b + 15) / 16 * 16; }
+
+static int64_t islands_blob_bytes(const ffs_islands *S)
+{
+    int64_t b = r16(sizeof(IslandsBlobHeader)) + r16((int64_t)S->I * sizeof(IslandBlobEntry));
+    for (int i = 0; i < S->I; ++i) b += r16((int64_t)S->size[i] * S->ld * 2) + r16((int64_t)S->size[i] * 4);
+    if (S->sur) {
+        const SurrogateState *R = S->sur;
+        const int64_t valid = std::min(R->ring_count, R->ring_cap);
+        b += r16(sizeof(SurrogateBlob)) + r16(valid * S->ld * 2) + r16(valid * 4) + r16(mlp_state_bytes(R->mlp));
+    }
+    return b;
+}
+
+}  // namespace fgpu
+
+extern "C" {
+
+int64_t ffs_checkpoint_bytes(const ffs_islands *S) { return S ? islands_blob_bytes(S) : -1; }
+
+int ffs_checkpoint_save(const ffs_islands *S, void *host, int64_t capacity, ffs_stream stream)
+{
+    clear_error();
+    if (!S || !host) return set_error(FFS_EINVAL, "NULL argument");
+    const int64_t need = islands_blob_bytes(S);
+    if (capacity < need) return set_error(FFS_EINVAL, "capacity %lld < %lld bytes", (long long)capacity, (long long)need);
+    cudaStream_t st = (cudaStream_t)stream;
+    BlobWriter w{static_cast<char *>(host), capacity};
+    IslandsBlobHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kIslandsBlobMagic;
+    h.version = kIslandsBlobVersion;
+    h.I = S->I;
+    h.ld = S->ld;
+    h.n = S->inst->n;
+    h.has_surrogate = S->sur ? 1 : 0;
+    h.fingerprint = instance_fingerprint(S->inst);
+    h.prm = S->prm;
+    unsigned long long dec = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&dec, S->d_decoded, 8, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    h.decoded = (int64_t)dec;
+    memcpy(w.take(r16(sizeof(h))), &h, sizeof(h));
+    char *ent = w.take(r16((int64_t)S->I * sizeof(IslandBlobEntry)));
+    for (int i = 0; i < S->I; ++i) {
+        const IslandBlobEntry e{S->kind[i], S->size[i], S->host_gen[i]};
+        memcpy(ent + i * sizeof(IslandBlobEntry), &e, sizeof(e));
+    }
+    for (int i = 0; i < S->I; ++i) {
+        const int c = S->host_cur[i];
+        char *rows = w.take(r16((int64_t)S->size[i] * S->ld * 2));
+        char *ms = w.take(r16((int64_t)S->size[i] * 4));
+        FFS_CUDA_TRY(cudaMemcpyAsync(rows, S->desc[i].pop[c], (size_t)S->size[i] * S->ld * 2, cudaMemcpyDefault, st));
+        FFS_CUDA_TRY(cudaMemcpyAsync(ms, S->desc[i].ms[c], (size_t)S->size[i] * 4, cudaMemcpyDefault, st));
+    }
+    if (S->sur) {
+        const SurrogateState *R = S->sur;
+        SurrogateBlob sb;
+        memset(&sb, 0, sizeof(sb));
+        sb.candidates = R->sp.candidates;
+        sb.ring_cap = R->ring_cap;
+        sb.ring_count = R->ring_count;
+        sb.train_rounds = R->train_rounds;
+        sb.valid = std::min(R->ring_count, R->ring_cap);
+        memcpy(w.take(r16(sizeof(sb))), &sb, sizeof(sb));
+        char *rows = w.take(r16(sb.valid * S->ld * 2));
+        char *ms = w.take(r16(sb.valid * 4));
+        if (sb.valid > 0) {
+            FFS_CUDA_TRY(cudaMemcpyAsync(rows, R->ring_rows, (size_t)sb.valid * S->ld * 2, cudaMemcpyDefault, st));
+            FFS_CUDA_TRY(cudaMemcpyAsync(ms, R->ring_ms, (size_t)sb.valid * 4, cudaMemcpyDefault, st));
+        }
+        char *net = w.take(r16(mlp_state_bytes(R->mlp)));
+        int rc = mlp_save(R->mlp, net, st);
+        if (rc) return rc;
+    }
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
+int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stream stream)
+{
+    clear_error();
+    if (!S || !host) return set_error(FFS_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    BlobReader r{static_cast<const char *>(host), size};
+    const char *hp = r.take(r16(sizeof(IslandsBlobHeader)));
+    if (!hp) return set_error(FFS_EINVAL, "checkpoint truncated (header)");
+    IslandsBlobHeader h;
+    memcpy(&h, hp, sizeof(h));
+    if (h.magic != kIslandsBlobMagic || h.version != kIslandsBlobVersion)
+        return set_error(FFS_EINVAL, "not an islands checkpoint of this version");
+    if (h.I != S->I || h.ld != S->ld || h.n != S->inst->n)
+        return set_error(FFS_EINVAL, "checkpoint of %d islands (ld %d, n %d); this handle has %d (ld %d, n %d)", h.I, h.ld,
+                         h.n, S->I, S->ld, S->inst->n);
+    if (h.fingerprint != instance_fingerprint(S->inst))
+        return set_error(FFS_EINVAL, "checkpoint of another instance (fingerprint differs)");
+    if (h.has_surrogate != (S->sur ? 1 : 0))
+        return set_error(FFS_EINVAL, h.has_surrogate ? "checkpoint has a surrogate; attach one first"
+                                                     : "checkpoint has no surrogate but one is attached");
+    const char *ent = r.take(r16((int64_t)S->I * sizeof(IslandBlobEntry)));
+    if (!ent) return set_error(FFS_EINVAL, "checkpoint truncated (islands)");
+    std::vector<IslandBlobEntry> es(S->I);
+    for (int i = 0; i < S->I; ++i) {
+        memcpy(&es[i], ent + i * sizeof(IslandBlobEntry), sizeof(IslandBlobEntry));
+        if (es[i].kind != S->kind[i] || es[i].size != S->size[i])
+            return set_error(FFS_EINVAL, "island %d differs in kind or size", i);
+        if (es[i].generation < 0 || es[i].generation > 0x7FFFFFFF)
+            return set_error(FFS_EINVAL, "island %d generation %lld", i, (long long)es[i].generation);
+    }
+    std::vector<const char *> rows(S->I), mss(S->I);
+    for (int i = 0; i < S->I; ++i) {
+        rows[i] = r.take(r16((int64_t)S->size[i] * S->ld * 2));
+        mss[i] = r.take(r16((int64_t)S->size[i] * 4));
+        if (!rows[i] || !mss[i]) return set_error(FFS_EINVAL, "checkpoint truncated (island %d)", i);
+    }
+    SurrogateBlob sb;
+    memset(&sb, 0, sizeof(sb));
+    const char *ring_rows = nullptr, *ring_ms = nullptr, *net = nullptr;
+    int64_t net_bytes = 0;
+    if (S->sur) {
+        const SurrogateState *R = S->sur;
+        const char *sp = r.take(r16(sizeof(SurrogateBlob)));
+        if (!sp) return set_error(FFS_EINVAL, "checkpoint truncated (surrogate)");
+        memcpy(&sb, sp, sizeof(sb));
+        if (sb.candidates != R->sp.candidates || sb.ring_cap != R->ring_cap)
+            return set_error(FFS_EINVAL, "surrogate of %d candidates / ring %lld; attached: %d / %lld", sb.candidates,
+                             (long long)sb.ring_cap, R->sp.candidates, (long long)R->ring_cap);
+        if (sb.ring_count < 0 || sb.train_rounds < 0 || sb.valid != std::min(sb.ring_count, sb.ring_cap))
+            return set_error(FFS_EINVAL, "surrogate ring counters inconsistent");
+        ring_rows = r.take(r16(sb.valid * S->ld * 2));
+        ring_ms = r.take(r16(sb.valid * 4));
+        net_bytes = r16(mlp_state_bytes(R->mlp));
+        net = r.take(net_bytes);
+        if (!ring_rows || !ring_ms || !net) return set_error(FFS_EINVAL, "checkpoint truncated (surrogate state)");
+    }
+    // everything validated: write the state
+    for (int i = 0; i < S->I; ++i) {
+        const int c = S->host_cur[i];
+        FFS_CUDA_TRY(cudaMemcpyAsync(S->desc[i].pop[c], rows[i], (size_t)S->size[i] * S->ld * 2, cudaMemcpyDefault, st));
+        FFS_CUDA_TRY(cudaMemcpyAsync(S->desc[i].ms[c], mss[i], (size_t)S->size[i] * 4, cudaMemcpyDefault, st));
+    }
+    std::vector<int32_t> gen(S->I);
+    for (int i = 0; i < S->I; ++i) gen[i] = (int32_t)es[i].generation;
+    FFS_CUDA_TRY(cudaMemcpyAsync(S->d_gen, gen.data(), 4 * (size_t)S->I, cudaMemcpyHostToDevice, st));
+    const unsigned long long dec = (unsigned long long)h.decoded;
+    FFS_CUDA_TRY(cudaMemcpyAsync(S->d_decoded, &dec, 8, cudaMemcpyHostToDevice, st));
+    if (S->sur) {
+        SurrogateState *R = S->sur;
+        if (sb.valid > 0) {
+            FFS_CUDA_TRY(cudaMemcpyAsync(R->ring_rows, ring_rows, (size_t)sb.valid * S->ld * 2, cudaMemcpyDefault, st));
+            FFS_CUDA_TRY(cudaMemcpyAsync(R->ring_ms, ring_ms, (size_t)sb.valid * 4, cudaMemcpyDefault, st));
+        }
+        int rc = mlp_load(R->mlp, net, net_bytes, st);
+        if (rc) return rc;
+        R->ring_count = sb.ring_count;
+        R->train_rounds = sb.train_rounds;
+    }
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < S->I; ++i) S->host_gen[i] = es[i].generation;
+    // the GA parameters come back; the launch shape stays the one in use
+    const ffs_params keep = S->prm;
+    S->prm = h.prm;
+    S->prm.decode_chunk = keep.decode_chunk;
+    S->prm.block_threads = keep.block_threads;
+    S->prm.decode_variant = keep.decode_variant;
+    if (S->graph_all) {
+        cudaGraphExecDestroy(S->graph_all);
+        S->graph_all = nullptr;
+    }
+    return FFS_OK;
+}
+
+}  // extern "C"

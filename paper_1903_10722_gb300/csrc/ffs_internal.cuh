@@ -99,6 +99,51 @@ struct ffs_instance {
 
 namespace fgpu {
 
+// FNV-1a (64-bit) fingerprint of an instance as given (n, S, M, p, release,
+// due, WT): a checkpoint records it so that it is only loaded into a handle
+// of the same problem.
+inline uint64_t instance_fingerprint(const ffs_instance *I, uint64_t h = 1469598103934665603ull)
+{
+    auto mix = [&h](int64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (uint64_t)((v >> (8 * b)) & 0xFF);
+            h *= 1099511628211ull;
+        }
+    };
+    mix(I->n);
+    mix(I->S);
+    for (int32_t v : I->host_M) mix(v);
+    for (int32_t v : I->host_p) mix(v);
+    mix((int64_t)I->host_R.size());
+    for (int32_t v : I->host_R) mix(v);
+    mix((int64_t)I->host_D.size());
+    for (int32_t v : I->host_D) mix(v);
+    mix(I->wt);
+    return h;
+}
+
+// Bounds-checked writer / reader of a host checkpoint blob.
+struct BlobWriter {
+    char *p;
+    int64_t cap, off = 0;
+    char *take(int64_t bytes) {
+        if (off + bytes > cap) return nullptr;
+        char *q = p + off;
+        off += bytes;
+        return q;
+    }
+};
+struct BlobReader {
+    const char *p;
+    int64_t size, off = 0;
+    const char *take(int64_t bytes) {
+        if (bytes < 0 || off + bytes > size) return nullptr;
+        const char *q = p + off;
+        off += bytes;
+        return q;
+    }
+};
+
 // Choose (B, T) for a decoding kernel, honouring requests (0 = choose).
 // bits_per_warp: shared words per warp the kernel needs besides decoding
 // (the crossover bitmask).  kernel: for the occupancy query.
@@ -215,5 +260,8 @@ int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long lon
 int launch_fill_f32(float *p, int64_t n, float v, cudaStream_t st);
 int mlp_in_dim(const ffs_mlp *m);
 int mlp_max_batch(const ffs_mlp *m);
+int64_t mlp_state_bytes(const ffs_mlp *m);
+int mlp_save(const ffs_mlp *m, void *host, cudaStream_t st);                   // synchronises
+int mlp_load(ffs_mlp *m, const void *host, int64_t size, cudaStream_t st);     // synchronises
 
 }  // namespace fgpu

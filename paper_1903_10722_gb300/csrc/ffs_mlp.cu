@@ -8,6 +8,7 @@
 // operands into that layout with small CUDA-core kernels.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -321,6 +322,32 @@ __global__ void k_sum(const float *x, int n, float *out)
     }
 }
 
+// He-uniform initialisation (He et al. 2015, uniform form: limit
+// sqrt(6 / fan_in)) of a [rows][ld] FP32 matrix with `cols` valid columns
+// (the rest set to 0).  Element (o, i) takes word i mod 4 of the Philox block
+// i / 4 of the stream (seed, kPurposeMlpInit, layer, generation 0, cell o):
+// u = ((x >> 8) - 2^23) / 2^23, exactly representable in [-1, 1), and the
+// value is lim * u (then * scale), each product rounded once to FP32.
+__global__ void k_mlp_init(float *W, int rows, int cols, int ld, uint64_t seed, uint32_t layer, int fan_in,
+                           float scale)
+{
+    const float lim = __fsqrt_rn(__fdiv_rn(6.0f, (float)fan_in));
+    const int64_t total = (int64_t)rows * ld;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(idx / ld), i = (int)(idx - (int64_t)o * ld);
+        float v = 0.0f;
+        if (i < cols) {
+            const U4 b = draw_block(seed, kPurposeMlpInit, layer, 0u, (uint32_t)o, (uint32_t)(i >> 2));
+            const uint32_t x = (i & 3) == 0 ? b.x : (i & 3) == 1 ? b.y : (i & 3) == 2 ? b.z : b.w;
+            const float u = (float)((int32_t)(x >> 8) - (1 << 23)) * (1.0f / 8388608.0f);
+            v = __fmul_rn(lim, u);
+            if (scale != 1.0f) v = __fmul_rn(v, scale);
+        }
+        W[idx] = v;
+    }
+}
+
 // Adam (Kingma & Ba 2015) on n parameters; step t >= 1.
 __global__ void k_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
                        float c1, float c2)
@@ -396,6 +423,53 @@ static int mlp_forward(ffs_mlp *M, const void *x, int ldx, int B, float *y, cuda
     if ((rc = gemm_bf16(M->H1, M->h1, M->W2b, M->h1, B, M->h2, M->h1, e, st))) return rc;
     k_out_layer<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, M->h2, M->w3, M->b3, y);
     FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// Checkpoint blob of a network: this header, then the FP32 parameters, the
+// Adam first and second moments (n_params each, the internal order: W1
+// [h1][K1] with its zero columns, b1, W2, b2, w3, b3).
+struct MlpBlobHeader {
+    uint32_t magic, version;
+    int32_t in_dim, h1, h2, K1;
+    int64_t adam_t, n_params;
+};
+constexpr uint32_t kMlpBlobMagic = 0x4D534646u, kMlpBlobVersion = 1;
+
+int64_t mlp_state_bytes(const ffs_mlp *M) { return (int64_t)sizeof(MlpBlobHeader) + 3 * (int64_t)M->n_params * 4; }
+
+int mlp_save(const ffs_mlp *M, void *host, cudaStream_t st)
+{
+    MlpBlobHeader h{kMlpBlobMagic, kMlpBlobVersion, M->in_dim, M->h1, M->h2, M->K1, M->adam_t, (int64_t)M->n_params};
+    memcpy(host, &h, sizeof(h));
+    float *p = reinterpret_cast<float *>(static_cast<char *>(host) + sizeof(h));
+    FFS_CUDA_TRY(cudaMemcpyAsync(p, M->params, M->n_params * 4, cudaMemcpyDefault, st));
+    FFS_CUDA_TRY(cudaMemcpyAsync(p + M->n_params, M->m, M->n_params * 4, cudaMemcpyDefault, st));
+    FFS_CUDA_TRY(cudaMemcpyAsync(p + 2 * M->n_params, M->v, M->n_params * 4, cudaMemcpyDefault, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
+int mlp_load(ffs_mlp *M, const void *host, int64_t size, cudaStream_t st)
+{
+    if (size < (int64_t)sizeof(MlpBlobHeader)) return set_error(FFS_EINVAL, "network state: %lld bytes", (long long)size);
+    MlpBlobHeader h;
+    memcpy(&h, host, sizeof(h));
+    if (h.magic != kMlpBlobMagic || h.version != kMlpBlobVersion)
+        return set_error(FFS_EINVAL, "network state: bad magic or version");
+    if (h.in_dim != M->in_dim || h.h1 != M->h1 || h.h2 != M->h2 || h.K1 != M->K1 || h.n_params != (int64_t)M->n_params)
+        return set_error(FFS_EINVAL, "network state of a %d-%d-%d network, this one is %d-%d-%d", h.in_dim, h.h1, h.h2,
+                         M->in_dim, M->h1, M->h2);
+    if (size < mlp_state_bytes(M)) return set_error(FFS_EINVAL, "network state truncated");
+    if (h.adam_t < 0) return set_error(FFS_EINVAL, "network state: step count %lld", (long long)h.adam_t);
+    const float *p = reinterpret_cast<const float *>(static_cast<const char *>(host) + sizeof(h));
+    FFS_CUDA_TRY(cudaMemcpyAsync(M->params, p, M->n_params * 4, cudaMemcpyDefault, st));
+    FFS_CUDA_TRY(cudaMemcpyAsync(M->m, p + M->n_params, M->n_params * 4, cudaMemcpyDefault, st));
+    FFS_CUDA_TRY(cudaMemcpyAsync(M->v, p + 2 * M->n_params, M->n_params * 4, cudaMemcpyDefault, st));
+    M->adam_t = h.adam_t;
+    int rc = refresh_bf16(M, st);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
     return FFS_OK;
 }
 
@@ -515,13 +589,15 @@ int ffs_mlp_set_params(ffs_mlp *M, const float *W1, const float *b1, const float
     return FFS_OK;
 }
 
-// Host copies of the parameters (grads = 0) or of the last step's gradients (grads = 1).
-int ffs_mlp_get(const ffs_mlp *M, int32_t grads, float *W1, float *b1, float *W2, float *b2, float *w3, float *b3)
+// Host copies of the parameters (which = 0), the last step's gradients (1),
+// or Adam's first (2) or second (3) moment estimates.
+int ffs_mlp_get(const ffs_mlp *M, int32_t which, float *W1, float *b1, float *W2, float *b2, float *w3, float *b3)
 {
     clear_error();
     if (!M) return set_error(FFS_EINVAL, "NULL MLP");
+    if (which < 0 || which > 3) return set_error(FFS_EINVAL, "which %d outside 0..3", which);
     FFS_CUDA_TRY(cudaDeviceSynchronize());
-    const float *src = grads ? M->grads : M->params;
+    const float *src = which == 0 ? M->params : which == 1 ? M->grads : which == 2 ? M->m : M->v;
     std::vector<float> all(M->n_params);
     FFS_CUDA_TRY(cudaMemcpy(all.data(), src, all.size() * 4, cudaMemcpyDeviceToHost));
     size_t off = 0;
@@ -539,6 +615,53 @@ int ffs_mlp_get(const ffs_mlp *M, int32_t grads, float *W1, float *b1, float *W2
     off += M->h2;
     if (b3) *b3 = all[off];
     return FFS_OK;
+}
+
+int ffs_mlp_init(ffs_mlp *M, uint64_t seed, ffs_stream stream)
+{
+    clear_error();
+    if (!M) return set_error(FFS_EINVAL, "NULL MLP");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto blocks = [](int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); };
+    k_mlp_init<<<blocks((int64_t)M->h1 * M->K1), 256, 0, st>>>(M->W1, M->h1, M->in_dim, M->K1, seed, 1u, M->in_dim,
+                                                               1.0f);
+    k_mlp_init<<<blocks((int64_t)M->h2 * M->h1), 256, 0, st>>>(M->W2, M->h2, M->h1, M->h1, seed, 2u, M->h1, 1.0f);
+    k_mlp_init<<<blocks(M->h2), 256, 0, st>>>(M->w3, 1, M->h2, M->h2, seed, 3u, M->h2, 0.1f);
+    FFS_CUDA_TRY(cudaGetLastError());
+    FFS_CUDA_TRY(cudaMemsetAsync(M->b1, 0, (size_t)M->h1 * 4, st));
+    FFS_CUDA_TRY(cudaMemsetAsync(M->b2, 0, (size_t)M->h2 * 4, st));
+    FFS_CUDA_TRY(cudaMemsetAsync(M->b3, 0, 4, st));
+    FFS_CUDA_TRY(cudaMemsetAsync(M->m, 0, M->n_params * 4, st));
+    FFS_CUDA_TRY(cudaMemsetAsync(M->v, 0, M->n_params * 4, st));
+    FFS_CUDA_TRY(cudaMemsetAsync(M->grads, 0, M->n_params * 4, st));
+    M->adam_t = 0;
+    return refresh_bf16(M, st);
+}
+
+int ffs_mlp_adam_steps(const ffs_mlp *M, int64_t *steps)
+{
+    clear_error();
+    if (!M || !steps) return set_error(FFS_EINVAL, "NULL argument");
+    *steps = M->adam_t;
+    return FFS_OK;
+}
+
+int64_t ffs_mlp_state_bytes(const ffs_mlp *M) { return M ? mlp_state_bytes(M) : -1; }
+
+int ffs_mlp_save(const ffs_mlp *M, void *host, int64_t capacity, ffs_stream stream)
+{
+    clear_error();
+    if (!M || !host) return set_error(FFS_EINVAL, "NULL argument");
+    if (capacity < mlp_state_bytes(M))
+        return set_error(FFS_EINVAL, "capacity %lld < %lld bytes", (long long)capacity, (long long)mlp_state_bytes(M));
+    return mlp_save(M, host, (cudaStream_t)stream);
+}
+
+int ffs_mlp_load(ffs_mlp *M, const void *host, int64_t size, ffs_stream stream)
+{
+    clear_error();
+    if (!M || !host) return set_error(FFS_EINVAL, "NULL argument");
+    return mlp_load(M, host, size, (cudaStream_t)stream);
 }
 
 int ffs_mlp_forward(ffs_mlp *M, const uint16_t *x, int32_t ldx, int32_t B, float *y, ffs_stream stream)

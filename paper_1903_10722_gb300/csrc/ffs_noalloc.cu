@@ -14,6 +14,10 @@
 // every call on that GPU shares it.
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
+
+#include <cuda.h>
 
 #include "ffs_internal.cuh"
 
@@ -21,28 +25,64 @@ namespace fgpu {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FFS_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device ordinal.  In host code the
-// array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, taken once per device with that device current.
-constexpr int kMaxDevices = 64;
+// Device address of g_noalloc_scratch in the current CUDA context.  In host
+// code the array's name is only a host-side stand-in, so the address comes
+// from cudaGetSymbolAddress, taken with the device current.  It is cached per
+// context, keyed on the driver's context ID (unique for the life of the
+// process, never reused), so a call under another context -- a non-primary
+// one, or the primary context created anew after cudaDeviceReset -- looks
+// the address up again instead of using one that belongs to a dead or
+// different context.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
 static std::mutex g_noalloc_mutex;
-static void *g_noalloc_addr[kMaxDevices] = {};
+static std::vector<std::pair<unsigned long long, void *>> g_noalloc_addr;   // (context ID, address)
+
+static bool current_context_id(unsigned long long *id)
+{
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        (void)cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 static int noalloc_scratch_address(void **out)
 {
     int dev = -1;
     FFS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(FFS_EUNSUPPORTED, "device ordinal %d", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(FFS_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed: %s",
-                             cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (have_id)
+        for (const auto &e : g_noalloc_addr)
+            if (e.first == id) {
+                *out = e.second;
+                return FFS_OK;
+            }
+    // first call in this context (cudaGetSymbolAddress also initialises the
+    // device's primary context when no context is current yet)
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(FFS_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed on device %d: %s", dev,
+                         cudaGetErrorString(e));
+    if (have_id || current_context_id(&id)) g_noalloc_addr.emplace_back(id, p);
+    *out = p;
     return FFS_OK;
 }
 

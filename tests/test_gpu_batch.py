@@ -119,3 +119,17 @@ def test_batch_tensor_memory_heaps_match_oracle(gpu, variant, threads, chunk):
         torch.cuda.synchronize()
         assert np.array_equal(pop.cpu().numpy(), states[i][1][:, :s.n]), i
         assert np.array_equal(ms.cpu().numpy().astype(np.int64), states[i][2]), i
+
+
+def test_batch_rejects_more_than_32_machines_below_n(gpu):
+    """The decoder keeps at most 32 machine free times per stage in registers:
+    an instance with min(M_s, n) > 32 is refused with FFS_EUNSUPPORTED (and
+    the batch is not created); M_s >= n clamps to n and is accepted."""
+    prm = gpu.ffs_params_default()
+    specs = [make_instance(20, 3, 2, 4, seed=1), make_instance(100, 3, 40, 40, seed=2)]
+    with pytest.raises(gpu.FFSError) as e:
+        gpu.Batch(specs, prm, 4, 4)
+    assert e.value.status == gpu.FFS_EUNSUPPORTED and "instance 1" in str(e.value)
+    ok = gpu.Batch([make_instance(20, 3, 2, 4, seed=1), make_instance(30, 3, 40, 40, seed=2)], prm, 4, 4)
+    gpu.ffs_batch_step(ok, 1)
+    assert (gpu.ffs_batch_best(ok) > 0).all()

@@ -1,0 +1,162 @@
+"""Checkpoint / resume: running G generations equals running G/2, saving the
+whole state to a host blob, loading it into a fresh handle and running G/2
+more -- for a plain dual-island run, a surrogate-screened run (ring buffer,
+network weights, Adam moments and step count included) and a batch of
+uneven instances.  Integer results, so equality is exact; the network's
+parameters are compared bit for bit (every kernel of the training step is
+deterministic).  Blobs of another shape or instance are refused before
+anything is written."""
+import numpy as np
+import pytest
+import torch
+
+from ffs_workloads import make_batch, make_instance
+
+pytestmark = pytest.mark.gpu
+
+
+def _islands_state(gpu, isl):
+    out = []
+    for i in range(isl.n_islands):
+        pop, ms = gpu.island_tensors(isl, i)
+        torch.cuda.synchronize()
+        out.append((pop.cpu().numpy(), ms.cpu().numpy()))
+    return out
+
+
+def _assert_same_islands(gpu, a, b):
+    sa, sb = _islands_state(gpu, a), _islands_state(gpu, b)
+    for i, ((pa, ma), (pb, mb)) in enumerate(zip(sa, sb)):
+        assert np.array_equal(pa, pb), i
+        assert np.array_equal(ma, mb), i
+    assert a.generation() == b.generation()
+    assert gpu.ffs_islands_decoded(a) == gpu.ffs_islands_decoded(b)
+    assert gpu.ffs_islands_best(a) == gpu.ffs_islands_best(b)
+
+
+def _dual(gpu, inst, mode=1, gap=3):
+    prm = gpu.ffs_params_default()
+    prm.migration_mode, prm.migration_gap = mode, gap
+    return gpu.Islands(inst, prm, 2, 8, 8, 2, 64)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_islands_checkpoint_resume_equals_uninterrupted_run(gpu, mode):
+    spec = make_instance(30, 6, 2, 4, seed=31)
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    G = 10
+    a = _dual(gpu, inst, mode)
+    gpu.ffs_island_step(a, -1, G // 2)
+    blob = gpu.ffs_checkpoint_save(a)
+    gpu.ffs_island_step(a, -1, G - G // 2)
+    b = _dual(gpu, inst, mode)
+    gpu.ffs_island_step(b, -1, 2)          # some other state, overwritten by the load
+    gpu.ffs_checkpoint_load(b, blob)
+    assert b.generation() == G // 2
+    gpu.ffs_island_step(b, -1, G - G // 2)
+    _assert_same_islands(gpu, a, b)
+
+
+def test_screened_islands_checkpoint_resume_equals_uninterrupted_run(gpu):
+    spec = make_instance(40, 6, 2, 5, seed=41)
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    rows = cols = 8
+    K = 4
+
+    def make(net_seed):
+        prm = gpu.ffs_params_default()
+        prm.migration_mode, prm.migration_gap = 1, 4
+        isl = gpu.Islands(inst, prm, 1, rows, cols, 1, 64)
+        net = gpu.MLP(540, 512, 256, 1024)
+        net.init(net_seed)
+        sp = gpu.ffs_surrogate_params_default()
+        sp.candidates, sp.warmup_generations, sp.train_every, sp.train_steps = K, 2, 1, 2
+        sp.train_batch, sp.ring_capacity = 128, 512      # the ring wraps within the run
+        gpu.ffs_islands_attach_surrogate(isl, net, sp)
+        return isl, net
+
+    a, net_a = make(3)
+    gpu.ffs_island_step(a, -1, 6)
+    blob = gpu.ffs_checkpoint_save(a)
+    gpu.ffs_island_step(a, -1, 6)
+    b, net_b = make(99)                    # other weights: the load must bring the saved ones
+    gpu.ffs_checkpoint_load(b, blob)
+    gpu.ffs_island_step(b, -1, 6)
+    _assert_same_islands(gpu, a, b)
+    assert net_a.adam_steps() == net_b.adam_steps() > 0
+    for which in (0, 2, 3):
+        pa, pb = net_a.get(which=which), net_b.get(which=which)
+        for k in pa:
+            assert np.array_equal(np.asarray(pa[k]), np.asarray(pb[k])), (which, k)
+    sa = np.zeros(rows * cols * K, np.float32)
+    sb = np.zeros(rows * cols * K, np.float32)
+    pairs_a = gpu.ffs_islands_surrogate_last(a, sa)
+    pairs_b = gpu.ffs_islands_surrogate_last(b, sb)
+    torch.cuda.synchronize()
+    assert pairs_a == pairs_b and np.array_equal(sa, sb)
+    # a plain handle cannot take a screened checkpoint
+    plain = gpu.Islands(inst, gpu.ffs_params_default(), 1, rows, cols, 1, 64)
+    with pytest.raises(gpu.FFSError) as e:
+        gpu.ffs_checkpoint_load(plain, blob)
+    assert e.value.status == gpu.FFS_EINVAL
+
+
+def test_islands_checkpoint_refuses_other_shapes_and_instances(gpu):
+    spec = make_instance(30, 6, 2, 4, seed=31)
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    a = _dual(gpu, inst)
+    gpu.ffs_island_step(a, -1, 2)
+    blob = gpu.ffs_checkpoint_save(a)
+    other = make_instance(30, 6, 2, 4, seed=32)
+    oinst = gpu.Instance(other.n, other.S, other.M, other.p)
+    before = _islands_state(gpu, _dual(gpu, oinst))
+    b = _dual(gpu, oinst)
+    for bad in (blob, blob[:100], blob[:len(blob) // 2]):
+        with pytest.raises(gpu.FFSError) as e:
+            gpu.ffs_checkpoint_load(b, bad)
+        assert e.value.status == gpu.FFS_EINVAL
+    after = _islands_state(gpu, b)
+    assert all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) for x, y in zip(before, after))
+    c = gpu.Islands(inst, gpu.ffs_params_default(), 1, 8, 8, 1, 64)
+    with pytest.raises(gpu.FFSError):
+        gpu.ffs_checkpoint_load(c, blob)
+
+
+def test_batch_checkpoint_resume_equals_uninterrupted_run(gpu):
+    specs = make_batch(count=7, seed=5, n_range=(5, 120), s_range=(2, 9), m_range=(1, 8))
+    prm = gpu.ffs_params_default()
+    a = gpu.Batch(specs, prm, 6, 6)
+    gpu.ffs_batch_step(a, 4)
+    blob = gpu.ffs_batch_checkpoint_save(a)
+    gpu.ffs_batch_step(a, 5)
+    b = gpu.Batch(specs, prm, 6, 6)
+    gpu.ffs_batch_checkpoint_load(b, blob)
+    assert b.info()["generation"] == 4
+    gpu.ffs_batch_step(b, 5)
+    for i in range(len(specs)):
+        pa, ma = gpu.batch_tensors(a, i)
+        pb, mb = gpu.batch_tensors(b, i)
+        torch.cuda.synchronize()
+        assert torch.equal(pa, pb) and torch.equal(ma, mb), i
+    assert gpu.ffs_batch_decoded(a) == gpu.ffs_batch_decoded(b)
+    assert np.array_equal(gpu.ffs_batch_best(a), gpu.ffs_batch_best(b))
+    # another torus or other instances: refused
+    c = gpu.Batch(specs, prm, 6, 5)
+    with pytest.raises(gpu.FFSError):
+        gpu.ffs_batch_checkpoint_load(c, blob)
+    d = gpu.Batch(make_batch(count=7, seed=6, n_range=(5, 120), s_range=(2, 9), m_range=(1, 8)), prm, 6, 6)
+    with pytest.raises(gpu.FFSError):
+        gpu.ffs_batch_checkpoint_load(d, blob)
+
+
+def test_batch_set_then_step_matches_get(gpu):
+    """ffs_batch_set writes rows and makespans that ffs_batch_get reads back."""
+    specs = make_batch(count=3, seed=8, n_range=(5, 40), s_range=(2, 5), m_range=(1, 4))
+    b = gpu.Batch(specs, gpu.ffs_params_default(), 4, 4)
+    pop, ms = gpu.batch_tensors(b, 1)
+    flipped = torch.flip(pop, dims=[0]).contiguous()
+    ms2 = torch.flip(ms, dims=[0]).contiguous()
+    gpu.ffs_batch_set(b, 1, flipped, specs[1].n, ms2)
+    back, bms = gpu.batch_tensors(b, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(back, flipped) and torch.equal(bms, ms2)

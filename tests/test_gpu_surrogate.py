@@ -8,6 +8,7 @@ import torch
 
 import oracle as orc
 from ffs_workloads import make_instance
+from ffs_workloads import mlp_params
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +22,7 @@ def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_ev
     prm.seed = seed
     prm.migration_mode, prm.migration_gap = 0, 0
     isl = gpu.Islands(g, prm, 1, rows, cols, n_pseudo, psize)
-    params = omlp.init_params(540, 512, 256, seed=11)
+    params = mlp_params(540, 512, 256, seed=11)
     params["b1"] = np.random.default_rng(1).normal(0, 0.05, 512).astype(np.float32)
     net = gpu.MLP(540, 512, 256, max(1024, ((rows * cols * K + 127) // 128) * 128))
     net.set_params(params)
@@ -107,7 +108,7 @@ def test_trained_screen_beats_plain_ga_at_equal_exact_decodes(gpu):
         isl = gpu.Islands(inst, prm, 1, w["rows"], w["cols"], 1, w["pseudo_size"])
         if mode == "screened":
             net = gpu.MLP(540, 512, 256, w["rows"] * w["cols"] * 8)
-            net.set_params(omlp.init_params(540, 512, 256, seed=3))
+            net.init(3)
             gpu.ffs_islands_attach_surrogate(isl, net, gpu.ffs_surrogate_params_default())
         gpu.ffs_island_step(isl, -1, 100)
         best[mode] = gpu.ffs_islands_best(isl)[0]

@@ -4,6 +4,7 @@ central finite differences of the unrounded network."""
 import numpy as np
 import pytest
 
+from ffs_workloads import mlp_params
 from oracle import mlp
 
 
@@ -37,7 +38,7 @@ def test_tiny_network_by_hand():
 
 def test_gradients_match_finite_differences():
     rng = np.random.default_rng(2)
-    p = mlp.init_params(7, 64, 64, seed=3)
+    p = mlp_params(7, 64, 64, seed=3)
     p["b1"] = rng.normal(0, 0.1, 64).astype(np.float32)
     p["b2"] = rng.normal(0, 0.1, 64).astype(np.float32)
     X = rng.normal(0, 1, (16, 7))
@@ -65,3 +66,24 @@ def test_adam_first_step_is_signed_lr():
     out = mlp.adam_step(p, g, {}, lr=0.01)
     # first Adam step: m_hat = g, v_hat = g^2 -> update = lr * sign(g) (0 for g = 0)
     assert np.allclose(out["a"], [0.99, -1.99, 0.5], atol=1e-9)
+
+
+def test_philox_initialisation_follows_its_definition():
+    """init_params_philox: values inside (-lim, lim) with lim = sqrt(6 / fan_in)
+    (He-uniform), spread like a uniform draw, w3 scaled by 0.1, biases 0, and
+    element (o, i) taken from the documented Philox counter."""
+    import oracle
+    p = mlp.init_params_philox(48, 64, 64, seed=3)
+    for k, fan in (("W1", 48), ("W2", 64)):
+        lim = np.sqrt(6.0 / fan)
+        W = p[k].astype(np.float64)
+        assert np.all(np.abs(W) <= lim)
+        assert abs(W.mean()) < 0.05 * lim
+        assert abs(W.var() / (lim * lim / 3.0) - 1.0) < 0.1          # variance of U(-lim, lim)
+    assert np.all(np.abs(p["w3"]) <= 0.1 * np.sqrt(6.0 / 64))
+    assert not p["b1"].any() and not p["b2"].any() and float(p["b3"]) == 0.0
+    # element (o = 5, i = 6) of W2: word 6 mod 4 of the block with counter (6 / 4, 5, 0, 2 | 14 << 24)
+    x = int(oracle.philox([1, 5, 0, 2 | (14 << 24)], [3, 0])[2])
+    u = ((x >> 8) - (1 << 23)) / 8388608.0
+    lim = float(np.sqrt(np.float32(6.0) / np.float32(64), dtype=np.float32))
+    assert abs(float(p["W2"][5, 6]) - lim * u) <= 1e-7 * lim
