@@ -291,16 +291,22 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1000.0
 
     # ---- dominant kernel: the decode launch (all cellular and pseudo
-    # children), replayed as in the step with the breeding and replacement
-    # launches (dry run: the state does not advance); CUDA events on the
-    # launching stream, so the time includes breeding and replacement ----
-    kernel_ms = []
+    # children) timed alone with CUDA events on its stream: a dry run of the
+    # breeding and replacement (untimed; the state does not advance), then
+    # the decode launch by itself over the children it bred; the group of
+    # breeding, decode and replacement launches is timed as well ----
+    kernel_ms, group_ms = [], []
     for r in range(max(3, min(args.steps, 10))):
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
+        g0.record(stream)
         ffs.ffs_islands_dry_run(isl, 2)
+        g1.record(stream)
+        k0.record(stream)
+        ffs.ffs_islands_dry_run(isl, 3)
         k1.record(stream)
         torch.cuda.synchronize()
+        group_ms.append(g0.elapsed_time(g1))
         kernel_ms.append(k0.elapsed_time(k1))
     clock_info = clocks.stop()
     d1 = ffs.ffs_islands_decoded(isl)
@@ -308,6 +314,9 @@ def run_ours(args):
     # per-pipe integer rates (probe kernels, outside the timed regions; opt-in so
     # that the launch list of a plain run holds the generation's kernels only)
     int_rates = None
+    # the measured issue rate of 32-bit min/max (the decoder's dominant
+    # instruction), beside the nominal 128-lane peak
+    minmax_rate = ffs.ffs_measure_int_rate(0)["lane_ops_per_s"]
     if args.int_rates:
         int_rates = {name: round(ffs.ffs_measure_int_rate(k)["lane_ops_per_s"] / 1e12, 2)
                      for k, name in enumerate(("min_max", "lop3", "iadd3", "imad", "fmnmx", "vminmax_u16x2",
@@ -372,8 +381,10 @@ def run_ours(args):
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
     ops_eval = ops_per_eval(spec.n, spec.M)
     kern_s = statistics.mean(kernel_ms) / 1000.0
+    group_s = statistics.mean(group_ms) / 1000.0
     decodes_per_launch = evals / args.steps          # cellular cells + pseudo children per generation
     achieved = decodes_per_launch * ops_eval / kern_s
+    achieved_group = decodes_per_launch * ops_eval / group_s
 
     line = {
         "metric": "exact FFS makespan evals/sec", "value": value, "unit": "evals/s",
@@ -388,9 +399,14 @@ def run_ours(args):
                      "unit": "Tops/s (int32 lane ops)", "frac": achieved / peak_ops,
                      "traffic": K_STEP_DECODE_DRAM_BYTES.get(
                          (prm.block_threads, prm.decode_chunk, prm.decode_variant)),
-                     "kernel": "k_step_decode (all cellular children: decode + replace; all pseudo children: decode), "
-                               "timed with the breeding launch (k_breed_dual) and the pseudo pair replacement",
+                     "kernel": "k_step_decode (all cellular children: decode + replace-if-better; all pseudo "
+                               "children: decode), its launch timed alone",
                      "kernel_ms": statistics.mean(kernel_ms), "ops_per_launch": decodes_per_launch * ops_eval,
+                     "frac_of_measured_minmax_rate": achieved / minmax_rate,
+                     "measured_minmax_tops": minmax_rate / 1e12,
+                     "group": {"what": "breeding (k_breed_dual) + decode (k_step_decode) + pseudo pair replacement "
+                                       "launches of one generation", "ms": statistics.mean(group_ms),
+                               "achieved": achieved_group / 1e12, "frac": achieved_group / peak_ops},
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)",
                      "launch_shape": ffs.ffs_decode_plan(inst, 2, prm.decode_chunk, prm.block_threads,
                                                          prm.decode_variant),
@@ -398,6 +414,17 @@ def run_ours(args):
                      "measured_int_rate_tops": int_rates},
         "clocks": clock_info,
     }
+    if ws == 1 and not args.no_subrecords:
+        # the other measured configuration: 256 uneven instances in one
+        # persistent launch per generation (its own timed region and clocks)
+        sub = batch_measure("batch_256", steps=20, warmup=3, autotune=True, shape=None)
+        sub["workload"] = ("batch_256: 256 instances, n ~ U[20,500], S ~ U[5,20], M_s ~ U[2,10], "
+                           "p ~ U[1,99], one 32x32 cellular island each")
+        line["batch_256"] = sub
+        # the surrogate comparison (config-5 protocol, GA seeds 7..11)
+        sur = surrogate_measure(list(range(7, 12)), plain_gens=1000, screened_gens=500)
+        sur.pop("median_curves", None)
+        line["surrogate_100x10"] = sur
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # all host cores, one island each (~8 s), and one thread alone (~8 s)
         cores = host_cores()
@@ -415,32 +442,27 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """256 uneven instances, one 32x32 cellular island each; a step is one
-    generation of every instance (one persistent launch from the graph)."""
+def batch_measure(workload: str, steps: int, warmup: int, autotune: bool, shape, dist=None, ws: int = 1) -> dict:
+    """The batch of uneven instances (one cellular island each): creation,
+    launch-shape autotuning, `warmup` generations, then `steps` generations
+    timed with CUDA events on the launching stream (one persistent launch per
+    generation, replayed from the CUDA graph).  Returns the measured fields."""
     import torch
 
     import paper_1903_10722_gb300 as ffs
     from ffs_workloads import WORKLOADS, make_batch
 
-    ws, rank, local = _dist()
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS[workload]
     specs = make_batch(w["count"], seed=w["seed"])
     prm = ffs.ffs_params_default()
-    _apply_shape(prm, args)
+    if shape is not None:
+        prm.block_threads, prm.decode_chunk, prm.decode_variant = shape
     b = ffs.Batch(specs, prm, w["rows"], w["cols"])
-    tuned = b.info() if args.no_autotune else ffs.ffs_batch_autotune(b, repeats=4)
+    tuned = ffs.ffs_batch_autotune(b, repeats=4) if autotune else b.info()
     tuned["variant"] = b.info()["variant"]
     stream = torch.cuda.current_stream()
-    ffs.ffs_batch_step(b, args.warmup)
+    ffs.ffs_batch_step(b, warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(dev_index)
     clocks.start()
@@ -450,7 +472,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ffs.ffs_batch_step(b, args.steps)
+    ffs.ffs_batch_step(b, steps)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -465,16 +487,11 @@ def run_batch(args):
     sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MHZ))
     num_sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
-    step_s = elapsed / args.steps
-    line = {
-        "metric": "exact FFS makespan evals/sec", "value": evals * ws / elapsed, "unit": "evals/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1000.0,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic (seeded instances and Philox GA)",
-        "config": {"workload": args.workload, "instances": w["count"], "n_jobs": list(w["n"]),
-                   "n_stages": list(w["S"]), "machines_per_stage": list(w["m"]), "torus": [w["rows"], w["cols"]],
-                   "chromosomes": w["count"] * cells, "launch_shape": tuned, "parallelism": f"replicas x{ws}"},
-        "gpu_launches": args.steps,
+    step_s = elapsed / steps
+    b.close()
+    return {
+        "value": evals * ws / elapsed, "unit": "evals/s", "steps": steps, "warmup": warmup,
+        "ms_per_step": step_s * 1000.0, "launch_shape": tuned, "chromosomes": w["count"] * cells,
         "roofline": {"bound": "alu", "achieved": ops_gen / step_s / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 lane ops)", "frac": ops_gen / step_s / peak_ops,
                      "traffic": (K_BATCH_CELLULAR_DRAM_BYTES
@@ -483,11 +500,44 @@ def run_batch(args):
                                "the counter reset and generation advance)"},
         "clocks": clock_info,
     }
+
+
+def run_batch(args):
+    """256 uneven instances, one 32x32 cellular island each; a step is one
+    generation of every instance (one persistent launch from the graph)."""
+    import torch
+
+    from ffs_workloads import WORKLOADS
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    w = WORKLOADS[args.workload]
+    shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
+    m = batch_measure(args.workload, args.steps, args.warmup, not args.no_autotune, shape, dist, ws)
+    cells = w["rows"] * w["cols"]
+    line = {
+        "metric": "exact FFS makespan evals/sec", "value": m["value"], "unit": "evals/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded instances and Philox GA)",
+        "config": {"workload": args.workload, "instances": w["count"], "n_jobs": list(w["n"]),
+                   "n_stages": list(w["S"]), "machines_per_stage": list(w["m"]), "torus": [w["rows"], w["cols"]],
+                   "chromosomes": w["count"] * cells, "launch_shape": m["launch_shape"],
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": args.steps,
+        "roofline": m["roofline"],
+        "clocks": m["clocks"],
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
-    b.close()
     return 0
 
 
@@ -500,69 +550,153 @@ def _spearman(a, b) -> float:
     return float((ra * rb).sum() / np.sqrt((ra * ra).sum() * (rb * rb).sum()))
 
 
-def run_surrogate(args):
+def _median_curve(curves, grid):
+    """Median over seeds of best-so-far at each time of `grid` (a curve is
+    [(seconds, best)] with the best at time 0 first)."""
+    import numpy as np
+    out = []
+    for t in grid:
+        vals = []
+        for c in curves:
+            b = c[0][1]
+            for ts, bs in c:
+                if ts <= t:
+                    b = bs
+            vals.append(b)
+        out.append(float(np.median(vals)))
+    return out
+
+
+def surrogate_measure(seeds, plain_gens: int = 1000, screened_gens: int = 500) -> dict:
     """Plain vs surrogate-screened dual-island GA on the 100 x 10 instance
-    family (64x64 cellular + 4096 pseudo): best makespan against wall-clock.
-    The screened GA scores 8 candidates per cell with the 540-512-256-1 BF16
-    network (tcgen05 GEMMs) and decodes only the best-scored one; the network
-    trains online on the exact pairs.  Prints one JSON line."""
+    family (64x64 cellular + 4096 pseudo, ring 2% every 50): for every GA seed
+    best makespan against wall-clock (host time around synchronised
+    ffs_island_step calls of 10 generations, CUDA graph capture done before
+    the clock starts), the median curves over the seeds, and the time the
+    screened GA takes to reach the plain GA's final best, as a fraction of
+    the plain GA's time.  The screen: 8 candidates per cell, the 540-512-256-1
+    BF16 network (tcgen05 GEMMs) seeded by ffs_mlp_init, trained online with
+    the library's default schedule; the exact decoder remains the source of
+    every makespan."""
     import numpy as np
     import torch
 
     import paper_1903_10722_gb300 as ffs
     from ffs_workloads import WORKLOADS, workload_instance
 
-    torch.cuda.set_device(0)
     w = WORKLOADS["dual_100x10"]
     spec = workload_instance("dual_100x10")
     inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p)
-    gens = args.steps
-    every = max(1, gens // 40)
-    curves, extra = {}, {}
-    for mode in ("plain", "screened"):
+    cells, K = w["rows"] * w["cols"], 8
+    sp0 = ffs.ffs_surrogate_params_default()
+
+    def make(seed, screened, train=True):
         prm = ffs.ffs_params_default()
+        prm.seed = seed
         prm.migration_mode, prm.migration_gap = ffs.FFS_MIG_RING, w["gap"]
         isl = ffs.Islands(inst, prm, 1, w["rows"], w["cols"], 1, w["pseudo_size"])
-        net = None
-        if mode == "screened":
-            net = ffs.MLP(540, 512, 256, w["rows"] * w["cols"] * 8)
+        if screened:
+            net = ffs.MLP(540, 512, 256, cells * K)
             net.init(3)
             sp = ffs.ffs_surrogate_params_default()
+            if not train:
+                sp.train_every = 0
             ffs.ffs_islands_attach_surrogate(isl, net, sp)
+        return isl
+
+    def run(isl, gens):
+        # the first generation (and the graph captures it triggers) before the clock
+        ffs.ffs_island_step(isl, -1, 1)
         torch.cuda.synchronize()
-        curve = [(0.0, ffs.ffs_islands_best(isl)[0], 0)]
-        t_total = 0.0
-        done = 0
+        curve, t, done = [(0.0, ffs.ffs_islands_best(isl)[0])], 0.0, 1
         while done < gens:
-            k = min(every, gens - done)
+            k = min(10, gens - done)
             t0 = time.perf_counter()
             ffs.ffs_island_step(isl, -1, k)
             torch.cuda.synchronize()
-            t_total += time.perf_counter() - t0
+            t += time.perf_counter() - t0
             done += k
-            curve.append((t_total, ffs.ffs_islands_best(isl)[0], done))
-        curves[mode] = curve
-        if mode == "screened":
-            cells, K = w["rows"] * w["cols"], 8
-            scores = np.zeros(cells * K, np.float32)
-            cands = np.zeros((cells * K, spec.n), np.int16)
-            loss = np.zeros(1, np.float32)
-            pairs = ffs.ffs_islands_surrogate_last(isl, scores, None, loss, cands, spec.n)
-            exact = np.zeros(cells * K, np.int32)
-            ffs.ffs_population_eval_host(inst, np.ascontiguousarray(np.pad(cands, ((0, 0), (0, inst.ld - spec.n)))),
-                                         cells * K, inst.ld, exact)
-            extra = {"spearman_last_generation_candidates": _spearman(scores, exact), "train_loss": float(loss[0]),
-                     "exact_pairs": pairs}
+            curve.append((t, ffs.ffs_islands_best(isl)[0]))
+        return curve
+
+    def spearman_cells(scores, exact):
+        rs = []
+        for c in range(cells):
+            a, b = scores[c * K:(c + 1) * K], exact[c * K:(c + 1) * K]
+            if np.ptp(b) > 0:
+                rs.append(_spearman(a, b))
+        return float(np.mean(rs)) if rs else None
+
+    per_seed, plain_curves, scr_curves = {}, [], []
+    rho_cell, rho_all, pick_best, pairs = [], [], [], 0
+    for seed in seeds:
+        isl = make(seed, False)
+        pc = run(isl, plain_gens)
         isl.close()
-    plain_t, plain_best = curves["plain"][-1][0], curves["plain"][-1][1]
-    reach = next((t for t, b, _ in curves["screened"] if b <= plain_best), None)
-    scr_t, scr_best = curves["screened"][-1][0], curves["screened"][-1][1]
-    line = {
+        isl = make(seed, True)
+        sc = run(isl, screened_gens)
+        # rank quality of the last generation's scores against its candidates' exact makespans
+        scores = np.zeros(cells * K, np.float32)
+        cands = np.zeros((cells * K, spec.n), np.int16)
+        pairs = ffs.ffs_islands_surrogate_last(isl, scores, None, None, cands, spec.n)
+        exact = np.zeros(cells * K, np.int32)
+        ffs.ffs_population_eval_host(inst, np.ascontiguousarray(np.pad(cands, ((0, 0), (0, inst.ld - spec.n)))),
+                                     cells * K, inst.ld, exact)
+        rho_cell.append(spearman_cells(scores, exact))
+        rho_all.append(_spearman(scores, exact))
+        picks = [int(np.argmin(scores[c * K:(c + 1) * K])) for c in range(cells)]
+        pick_best.append(float(np.mean([exact[c * K + picks[c]] == exact[c * K:(c + 1) * K].min()
+                                        for c in range(cells)])))
+        isl.close()
+        target, tp = pc[-1][1], pc[-1][0]
+        reach = next((t for t, b in sc if b <= target), None)
+        per_seed[str(seed)] = {"plain_best": target, "plain_s": tp, "screened_best": sc[-1][1],
+                               "screened_s": sc[-1][0], "time_to_plain_best_ratio": (reach / tp) if reach else None}
+        plain_curves.append(pc)
+        scr_curves.append(sc)
+    # median curves over the seeds on a common time grid
+    t_end = max(max(c[-1][0] for c in plain_curves), max(c[-1][0] for c in scr_curves))
+    grid = [t_end * i / 200 for i in range(201)]
+    mp, ms = _median_curve(plain_curves, grid), _median_curve(scr_curves, grid)
+    tp_end = float(np.median([c[-1][0] for c in plain_curves]))
+    plain_final = _median_curve(plain_curves, [tp_end])[0]
+    reach = next((t for t, b in zip(grid, ms) if b <= plain_final), None)
+    # cost split: a screened generation alone (no training), a training round
+    isl = make(seeds[0], True, train=False)
+    g_no_train = run(isl, 101)
+    isl.close()
+    gen_ms = g_no_train[-1][0] / 100 * 1e3
+    scr_ms = float(np.median([c[-1][0] for c in scr_curves])) / (screened_gens - 1) * 1e3
+    plain_ms = tp_end / (plain_gens - 1) * 1e3
+    te = max(sp0.train_every, 1)
+    return {
         "metric": "best makespan vs wall-clock, plain vs surrogate-screened GA", "workload": "dual_100x10",
-        "generations": gens, "plain": {"best": plain_best, "seconds": plain_t, "curve": curves["plain"]},
-        "screened": {"best": scr_best, "seconds": scr_t, "curve": curves["screened"]},
-        "time_to_plain_best_ratio": (reach / plain_t) if reach is not None else None, **extra,
+        "seeds": list(seeds), "plain_generations": plain_gens, "screened_generations": screened_gens,
+        "exact_pairs_per_seed": pairs,
+        "median": {"plain_final_best": plain_final, "plain_seconds": tp_end,
+                   "screened_final_best": ms[-1], "time_to_plain_best_s": reach,
+                   "time_to_plain_best_ratio": (reach / tp_end) if reach is not None else None,
+                   "target_ratio": 0.5},
+        "per_seed": per_seed,
+        "rank_quality_last_generation": {"spearman_within_cell_mean": float(np.mean(rho_cell)),
+                                         "spearman_all_candidates_mean": float(np.mean(rho_all)),
+                                         "pick_is_best_fraction": float(np.mean(pick_best))},
+        "ms_per_generation": {"plain": plain_ms, "screened_with_training": scr_ms,
+                              "screened_without_training": gen_ms,
+                              "training_round": (scr_ms - gen_ms) * te,
+                              "schedule": {"candidates": sp0.candidates, "train_every": sp0.train_every,
+                                           "train_steps": sp0.train_steps, "train_batch": sp0.train_batch,
+                                           "lr": sp0.lr, "warmup_generations": sp0.warmup_generations}},
+        "median_curves": {"t": [round(x, 5) for x in grid[::10]], "plain": mp[::10], "screened": ms[::10]},
     }
+
+
+def run_surrogate(args):
+    """Config-5 protocol: plain vs surrogate-screened GA over GA seeds 7..11;
+    prints one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    line = surrogate_measure(list(range(7, 12)), plain_gens=1000, screened_gens=500)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -768,6 +902,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="scale_500x20")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="default workload: skip the batch_256 and surrogate sub-records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--int-rates", action="store_true",
                     help="also measure per-pipe integer issue rates with the probe kernels")

@@ -544,8 +544,11 @@ int ffs_checkpoint_load(ffs_islands *isl, const void *host, int64_t size, ffs_st
  * fused decode launch of all cellular and pseudo children, pseudo replace --
  * exactly as ffs_island_step does, migration and generation advance
  * excepted), without advancing the state: only the next-generation buffers
- * are rewritten (for timing and profiling).  Not with a surrogate attached.
- * Asynchronous. */
+ * are rewritten (for timing and profiling).  kind 3: the fused decode launch
+ * alone, over the children the last kind-2 run (or generation) bred -- call
+ * it after kind 2 to time that launch by itself; FFS_EINVAL for handles
+ * whose generations do not use the fused launch.  Not with a surrogate
+ * attached.  Asynchronous. */
 int ffs_islands_dry_run(ffs_islands *isl, int32_t kind, ffs_stream stream);
 int ffs_islands_params(const ffs_islands *isl, ffs_params *out);
 

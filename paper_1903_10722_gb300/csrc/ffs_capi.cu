@@ -233,7 +233,9 @@ int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld,
                 cudaStream_t st, int variant)
 {
     Plan p;
-    int rc = plan_decode(inst, (const void *)k_eval, B_req, T_req, 0, &p, variant);
+    const int T_sp = spread_threads(inst, N, T_req);
+    int rc = plan_decode(inst, (const void *)k_eval, B_req, T_sp, 0, &p, variant);
+    if (rc && T_sp != T_req) rc = plan_decode(inst, (const void *)k_eval, B_req, T_req, 0, &p, variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, N);

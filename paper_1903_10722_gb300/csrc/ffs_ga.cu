@@ -70,7 +70,9 @@ int launch_cellular(const ffs_instance *inst, const GaScalars &g, const IslandBa
 {
     Plan p;
     const int bits_per_warp = mark_words(inst->n);
-    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p, g.variant);
+    const int T_sp = spread_threads(inst, (int64_t)rows * cols * batch.count, T_req);
+    int rc = plan_decode(inst, (const void *)k_cellular, B_req, T_sp, bits_per_warp, &p, g.variant);
+    if (rc && T_sp != T_req) rc = plan_decode(inst, (const void *)k_cellular, B_req, T_req, bits_per_warp, &p, g.variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, (int64_t)rows * cols * batch.count);
@@ -375,12 +377,18 @@ const void *step_decode_kernel() { return (const void *)k_step_decode; }
 // A whole generation of the cellular batch `cb` and the pseudo batch `pb`
 // (same torus for cb, same size for pb): pseudo breed, the fused decode
 // launch, pseudo replace.
+// decode_only: the decode launch alone, over the children that the last
+// breeding launch left in the scratch (its work counter reset first); it
+// rewrites the same next-generation rows, so it serves to time that launch.
 static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const IslandBatch &cb, int rows, int cols,
                              const IslandBatch &pb, int psize, int ld, void *scratch, int16_t *cell_children,
-                             int B_req, int T_req, unsigned long long *decoded, cudaStream_t st)
+                             int B_req, int T_req, unsigned long long *decoded, cudaStream_t st,
+                             bool decode_only = false)
 {
     PseudoScratch s = carve(scratch, psize, ld, pb.count);
-    {
+    if (decode_only) {
+        FFS_CUDA_TRY(cudaMemsetAsync(s.work, 0, sizeof(int32_t), st));
+    } else {
         // cellular and pseudo breeding in one launch
         FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));   // count and work
         const int T = 256;
@@ -396,13 +404,17 @@ static int launch_step_fused(const ffs_instance *inst, const GaScalars &g, const
     }
     int rc;
     Plan p;
-    if ((rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_req, 0, &p, g.variant))) return rc;
+    const int T_sp = spread_threads(inst, (int64_t)rows * cols * cb.count + (int64_t)psize * pb.count, T_req);
+    rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_sp, 0, &p, g.variant);
+    if (rc && T_sp != T_req) rc = plan_decode(inst, (const void *)k_step_decode, B_req, T_req, 0, &p, g.variant);
+    if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_step_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int64_t units = (int64_t)rows * cols * cb.count + (int64_t)psize * pb.count;
     const int grid = grid_for(inst, p, units);
     k_step_decode<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, cb, rows, cols, ld, s, cell_children,
                                              decoded);
     FFS_CUDA_TRY(cudaGetLastError());
+    if (decode_only) return FFS_OK;
     const int pairs = psize / 2 * pb.count;
     k_pseudo_replace<<<pair_blocks(pairs, 128), 128, 0, st>>>(g, pb, psize, ld, s);
     FFS_CUDA_TRY(cudaGetLastError());
@@ -676,12 +688,34 @@ struct SurrogateState {
     int32_t *ring_ms = nullptr;
     long long ring_cap = 0, ring_count = 0;
     float *inst_feat = nullptr;    // [nfeat]
-    float inv_lb = 0.0f;
     int16_t *train_rows = nullptr; // [train_batch][ld]
     void *train_X = nullptr;       // BF16 [train_batch][ldx]
     float *train_t = nullptr, *loss = nullptr;
     long long train_rounds = 0;
     std::vector<int> cell_islands;
+    // device counters read by the kernels: [0] ring pairs appended, [1]
+    // training batches drawn (host mirrors: ring_count, train_rounds)
+    long long *d_ctr = nullptr;
+    float *d_norm = nullptr;       // training-target standardisation (mean, 1 / std)
+    // generations (before / after the warm-up) and training rounds replayed
+    // from CUDA graphs; the pseudo islands run on `side`, beside the screen
+    cudaGraphExec_t g_gen[2] = {nullptr, nullptr};
+    cudaGraphExec_t g_train = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    void drop_graphs()
+    {
+        for (auto &g : g_gen)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        if (g_train) { cudaGraphExecDestroy(g_train); g_train = nullptr; }
+    }
+    ~SurrogateState()
+    {
+        drop_graphs();
+        if (side) cudaStreamDestroy(side);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
+    }
 };
 
 struct ffs_islands {
@@ -722,13 +756,14 @@ static IslandRef device_ref(const ffs_islands *S, int i)
     return r;
 }
 
-static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, cudaStream_t st);
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st);
 
 // One generation of the islands in `ids` (all of one kind): cellular islands
 // in launches of up to kMaxBatch, pseudo islands likewise, one decode of all
 // their children per launch.  With a surrogate attached, the cellular
 // islands take the screened path.
-static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids, cudaStream_t st)
+static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids, cudaStream_t st,
+                                     bool decode_only = false)
 {
     const GaScalars g = scalars_of(&S->prm);
     if (!S->sur) {
@@ -745,15 +780,18 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
             for (int t = 0; t < cb.count; ++t) cb.ref[t] = device_ref(S, cel[t]);
             for (int t = 0; t < pb.count; ++t) pb.ref[t] = device_ref(S, pse[t]);
             return launch_step_fused(S->inst, g, cb, S->rows, S->cols, pb, S->size[pse[0]], S->ld, S->d_scratch,
-                                     S->d_cell_children, S->prm.decode_chunk, S->prm.block_threads, S->d_decoded, st);
+                                     S->d_cell_children, S->prm.decode_chunk, S->prm.block_threads, S->d_decoded, st,
+                                     decode_only);
         }
     }
+    if (decode_only) return set_error(FFS_EINVAL, "the decode launch alone exists only for generations that decode both "
+                                                  "kinds in one launch");
     for (int kind = 0; kind < 2; ++kind) {
         std::vector<int> sel;
         for (int i : ids)
             if (S->kind[i] == kind) sel.push_back(i);
         if (kind == 0 && S->sur && !sel.empty()) {
-            int rc = screened_cellular_launch(S, sel, st);
+            int rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, st);
             if (rc) return rc;
             continue;
         }
@@ -810,9 +848,10 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
 }
 
 // Screened generation of the cellular islands in `sel`: candidates, network
-// scores (all zero during the warm-up generations: candidate 0 is taken),
-// best-scored candidate decoded exactly, ring buffer append.
-static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, cudaStream_t st)
+// scores (all zero during the warm-up generations, warm = false: candidate 0
+// is taken), best-scored candidate decoded exactly, ring buffer append (the
+// device ring counter advanced by the cells of each batch).
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st)
 {
     SurrogateState *R = S->sur;
     const GaScalars g = scalars_of(&S->prm);
@@ -826,40 +865,39 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
         const int ncells = batch.count * cells;
         int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
         float *scores = R->scores + (int64_t)offset * K;
-        int rc = launch_sur_candidates(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, st);
+        // the candidates, and in warm generations their network inputs in the same launch
+        void *X = static_cast<char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
+        int rc = launch_sur_candidates(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, R->P, R->inst_feat,
+                                       R->nfeat, warm ? X : nullptr, R->ldx, st);
         if (rc) return rc;
-        const bool warm = S->host_gen[sel[b0]] + 1 > R->sp.warmup_generations;
         if (warm) {
-            void *X = static_cast<char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
-            if ((rc = launch_sur_features(cand, (int64_t)ncells * K, S->inst->n, S->ld, R->P, R->inst_feat, R->nfeat, X,
-                                          R->ldx, st)))
-                return rc;
             if ((rc = ffs_mlp_forward(R->mlp, static_cast<const uint16_t *>(X), R->ldx, ncells * K, scores, st)))
                 return rc;
         } else if ((rc = launch_fill_f32(scores, (int64_t)ncells * K, 0.0f, st))) {
             return rc;
         }
         if ((rc = launch_sur_select(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, scores, R->chosen + offset,
-                                    R->ring_rows, R->ring_ms, R->ring_cap, R->ring_count, S->prm.decode_chunk,
+                                    R->ring_rows, R->ring_ms, R->ring_cap, R->d_ctr, S->prm.decode_chunk,
                                     S->prm.block_threads, S->d_decoded, st)))
             return rc;
-        R->ring_count += ncells;
+        if ((rc = launch_sur_tick(R->d_ctr, 0, ncells, st))) return rc;
         offset += ncells;
     }
     return FFS_OK;
 }
 
-// Online training of the surrogate on pairs from the ring buffer.
-static int surrogate_train(ffs_islands *S, cudaStream_t st)
+// One round of online training of the surrogate on pairs from the ring
+// buffer: train_steps batches, each drawn with the device's batch counter.
+static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
 {
     SurrogateState *R = S->sur;
-    const long long valid = std::min(R->ring_count, R->ring_cap);
-    if (valid < R->sp.train_batch) return FFS_OK;
+    int rc0 = launch_sur_norm(R->ring_ms, R->ring_cap, R->d_ctr, R->cells_total, R->d_norm, st);
+    if (rc0) return rc0;
     for (int s = 0; s < R->sp.train_steps; ++s) {
-        const uint32_t draw_gen = (uint32_t)(R->train_rounds * R->sp.train_steps + s);
-        int rc = launch_sur_gather(R->ring_rows, R->ring_ms, valid, S->ld, S->prm.seed, draw_gen, R->sp.train_batch,
-                                   R->train_rows, R->train_t, R->inv_lb, st);
+        int rc = launch_sur_gather(R->ring_rows, R->ring_ms, R->ring_cap, R->d_ctr, S->ld, S->prm.seed,
+                                   R->sp.train_batch, R->train_rows, R->train_t, R->d_norm, st);
         if (rc) return rc;
+        if ((rc = launch_sur_tick(R->d_ctr, 1, 1, st))) return rc;
         if ((rc = launch_sur_features(R->train_rows, R->sp.train_batch, S->inst->n, S->ld, R->P, R->inst_feat,
                                       R->nfeat, R->train_X, R->ldx, st)))
             return rc;
@@ -867,7 +905,55 @@ static int surrogate_train(ffs_islands *S, cudaStream_t st)
                                      R->sp.train_batch, R->sp.lr, R->loss, st)))
             return rc;
     }
-    R->train_rounds += 1;
+    return FFS_OK;
+}
+
+// One screened generation of every island: the pseudo islands on the side
+// stream beside the cellular screen (fork / join by events), then the
+// generation advance and migration, as generation_all does.
+static int screened_generation(ffs_islands *S, bool warm, cudaStream_t st)
+{
+    SurrogateState *R = S->sur;
+    std::vector<int> cel, pse;
+    for (int i = 0; i < S->I; ++i) (S->kind[i] == 0 ? cel : pse).push_back(i);
+    if (!pse.empty()) {
+        FFS_CUDA_TRY(cudaEventRecord(R->fork_ev, st));
+        FFS_CUDA_TRY(cudaStreamWaitEvent(R->side, R->fork_ev, 0));
+        int rc = islands_generation_launch(S, pse, R->side);
+        if (rc) return rc;
+    }
+    int rc = screened_cellular_launch(S, cel, warm, st);
+    if (rc) return rc;
+    if (!pse.empty()) {
+        FFS_CUDA_TRY(cudaEventRecord(R->join_ev, R->side));
+        FFS_CUDA_TRY(cudaStreamWaitEvent(st, R->join_ev, 0));
+    }
+    k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
+    FFS_CUDA_TRY(cudaGetLastError());
+    if (S->prm.migration_gap > 0) return migrate_launch(S, S->prm.migration_mode, true, st);
+    return FFS_OK;
+}
+
+// Capture `body` on the islands' capture stream into an executable graph.
+template <typename F>
+static int capture_graph(ffs_islands *S, cudaGraphExec_t *out, F body)
+{
+    if (!S->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    FFS_CUDA_TRY(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int rc = body(S->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(S->cap_stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return set_error(FFS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return set_error(FFS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
     return FFS_OK;
 }
 
@@ -1139,8 +1225,10 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     R->train_X = alloc((size_t)sp->train_batch * R->ldx * 2);
     R->train_t = (float *)alloc((size_t)sp->train_batch * 4);
     R->loss = (float *)alloc(4);
+    R->d_ctr = (long long *)alloc(2 * sizeof(long long));
+    R->d_norm = (float *)alloc(2 * sizeof(float));
     if (!R->cand || !R->X || !R->scores || !R->chosen || !R->ring_rows || !R->ring_ms || !R->inst_feat ||
-        !R->train_rows || !R->train_X || !R->train_t || !R->loss) {
+        !R->train_rows || !R->train_X || !R->train_t || !R->loss || !R->d_ctr || !R->d_norm) {
         delete R;
         return set_error(FFS_ENOMEM, "surrogate buffers");
     }
@@ -1168,10 +1256,14 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     f[36] = (float)(I->n / 500.0);
     f[37] = (float)(I->S / 20.0);
     f[38] = (float)(lb / total);
-    R->inv_lb = (float)(1.0 / lb);
-    if (cudaMemcpy(R->inst_feat, f.data(), nfeat * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(R->inst_feat, f.data(), nfeat * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(R->d_ctr, 0, 2 * sizeof(long long)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&R->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
         delete R;
-        return set_error(FFS_ECUDA, "surrogate features upload");
+        return set_error(FFS_ECUDA, "surrogate state initialisation");
     }
     (void)stream;
     S->sur = R;
@@ -1218,13 +1310,13 @@ int ffs_islands_dry_run(ffs_islands *S, int32_t kind, ffs_stream stream)
     clear_error();
     if (!S) return set_error(FFS_EINVAL, "NULL islands");
     if (S->sur) return set_error(FFS_EINVAL, "not with a surrogate attached");
-    if (kind < 0 || kind > 2) return set_error(FFS_EINVAL, "kind %d", kind);
+    if (kind < 0 || kind > 3) return set_error(FFS_EINVAL, "kind %d", kind);
     std::vector<int> ids;
     for (int i = 0; i < S->I; ++i)
-        if (kind == 2 || S->kind[i] == kind) ids.push_back(i);
+        if (kind >= 2 || S->kind[i] == kind) ids.push_back(i);
     unsigned long long *saved = S->d_decoded;
     S->d_decoded = nullptr;
-    const int rc = islands_generation_launch(S, ids, (cudaStream_t)stream);
+    const int rc = islands_generation_launch(S, ids, (cudaStream_t)stream, kind == 3);
     S->d_decoded = saved;
     return rc;
 }
@@ -1348,6 +1440,7 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
             FFS_CUDA_TRY(cudaGetLastError());
             S->host_cur[island] ^= 1;
             S->host_gen[island] += 1;
+            if (S->sur && S->kind[island] == 0) S->sur->ring_count += (long long)S->rows * S->cols;
         }
         return FFS_OK;
     }
@@ -1355,16 +1448,31 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
         if (S->host_gen[i] != S->host_gen[0])
             return set_error(FFS_EINVAL, "islands were stepped separately; generation counts differ");
     if (S->sur) {
-        // screened generations: direct launches (the training steps depend on host counters)
+        // screened generations and training rounds, each replayed from its
+        // CUDA graph; the kernels read the ring and batch counters on the
+        // device, the host keeps mirrors to decide warm-up and training
+        SurrogateState *R = S->sur;
         for (int g = 0; g < n_generations; ++g) {
-            int rc = generation_all(S, st);
-            if (rc) return rc;
+            const int warm = S->host_gen[0] + 1 > R->sp.warmup_generations ? 1 : 0;
+            if (!R->g_gen[warm]) {
+                int rc = capture_graph(S, &R->g_gen[warm],
+                                       [&](cudaStream_t cs) { return screened_generation(S, warm != 0, cs); });
+                if (rc) return rc;
+            }
+            FFS_CUDA_TRY(cudaGraphLaunch(R->g_gen[warm], st));
             for (int i = 0; i < S->I; ++i) {
                 S->host_cur[i] ^= 1;
                 S->host_gen[i] += 1;
             }
-            if (S->sur->sp.train_every > 0 && S->host_gen[0] % S->sur->sp.train_every == 0) {
-                if ((rc = surrogate_train(S, st))) return rc;
+            R->ring_count += R->cells_total;
+            if (R->sp.train_every > 0 && R->sp.train_steps > 0 && S->host_gen[0] % R->sp.train_every == 0 &&
+                std::min(R->ring_count, R->ring_cap) >= R->sp.train_batch) {
+                if (!R->g_train) {
+                    int rc = capture_graph(S, &R->g_train, [&](cudaStream_t cs) { return surrogate_train_launch(S, cs); });
+                    if (rc) return rc;
+                }
+                FFS_CUDA_TRY(cudaGraphLaunch(R->g_train, st));
+                R->train_rounds += 1;
             }
         }
         return FFS_OK;
@@ -1690,6 +1798,10 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
         if (rc) return rc;
         R->ring_count = sb.ring_count;
         R->train_rounds = sb.train_rounds;
+        const long long ctr[2] = {sb.ring_count, sb.train_rounds * (long long)R->sp.train_steps};
+        FFS_CUDA_TRY(cudaMemcpyAsync(R->d_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, st));
+        FFS_CUDA_TRY(cudaStreamSynchronize(st));
+        R->drop_graphs();   // they carry the GA parameters, which the load may change
     }
     FFS_CUDA_TRY(cudaStreamSynchronize(st));
     for (int i = 0; i < S->I; ++i) S->host_gen[i] = es[i].generation;

@@ -157,6 +157,13 @@ int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_r
 inline int pairs_of(int variant) { return (variant == 1 || variant == 3) ? 0 : 1; }
 inline int tmem_of(int variant) { return variant == 0 ? 1 : variant >= 3 ? 2 : 0; }
 
+// Threads per block for a decoding launch of `units` rows when the caller
+// asked for none (T_req = 0): with fewer than 512 rows per SM the planner's
+// widest block would leave most SMs idle, so the block gets about
+// rows / SMs threads (a multiple of 32, at least 32), which spreads the
+// latency-bound decodes over every SM.  Otherwise 0 (the planner chooses).
+inline int spread_threads(const ffs_instance *inst, int64_t units, int T_req);
+
 // Grid size for N items (persistent, grid-stride).
 inline int grid_for(const ffs_instance *inst, const Plan &p, int64_t N)
 {
@@ -248,20 +255,33 @@ int validate_rows(const void *p, int ld, int n);
 
 // Surrogate screening (ffs_surrogate.cu).
 int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
-                          int ld, int K, int16_t *cand, cudaStream_t st);
+                          int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat, void *X, int ldx,
+                          cudaStream_t st);
 int launch_sur_features(const int16_t *rows, int64_t nrows, int n, int ld, int P, const float *inst_feat, int nfeat,
                         void *X, int ldx, cudaStream_t st);
 int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
                       int ld, int K, const int16_t *cand, const float *scores, int32_t *chosen, int16_t *ring_rows,
-                      int32_t *ring_ms, long long ring_cap, long long ring_base, int B_req, int T_req,
+                      int32_t *ring_ms, long long ring_cap, const long long *ctr, int B_req, int T_req,
                       unsigned long long *decoded, cudaStream_t st);
-int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long valid, int ld, uint64_t seed,
-                      uint32_t draw_gen, int B, int16_t *out_rows, float *targets, float inv_lb, cudaStream_t st);
+int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm,
+                    cudaStream_t st);
+int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, const long long *ctr,
+                      int ld, uint64_t seed, int B, int16_t *out_rows, float *targets, const float *norm,
+                      cudaStream_t st);
+int launch_sur_tick(long long *ctr, int which, long long add, cudaStream_t st);
 int launch_fill_f32(float *p, int64_t n, float v, cudaStream_t st);
 int mlp_in_dim(const ffs_mlp *m);
 int mlp_max_batch(const ffs_mlp *m);
 int64_t mlp_state_bytes(const ffs_mlp *m);
 int mlp_save(const ffs_mlp *m, void *host, cudaStream_t st);                   // synchronises
 int mlp_load(ffs_mlp *m, const void *host, int64_t size, cudaStream_t st);     // synchronises
+
+inline int spread_threads(const ffs_instance *inst, int64_t units, int T_req)
+{
+    if (T_req > 0 || units <= 0 || inst->num_sms <= 0) return T_req;
+    const int64_t per_sm = (units + inst->num_sms - 1) / inst->num_sms;
+    if (per_sm >= 512) return 0;
+    return (int)((per_sm + 31) / 32 * 32);
+}
 
 }  // namespace fgpu

@@ -200,7 +200,23 @@ int gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int 
 {
     if (M < 1 || N < 64 || N % 64 || Kvalid < 1) return set_error(FFS_EINVAL, "GEMM shape M=%d N=%d K=%d", M, N, Kvalid);
     const int K = round_up(Kvalid, kBK);
-    const int BN = (N % 256 == 0) ? 256 : (N % 192 == 0) ? 192 : (N % 128 == 0) ? 128 : 64;
+    int BN = (N % 256 == 0) ? 256 : (N % 192 == 0) ? 192 : (N % 128 == 0) ? 128 : 64;
+    // few row tiles (the training batches): narrower column tiles, so that
+    // more CTAs share the (latency-bound) work; wide tiles once the grid
+    // covers the SMs
+    const int Mt = (M + kBM - 1) / kBM;
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (num_sms <= 0) num_sms = 1;
+    }
+    while (BN > 64 && (int64_t)Mt * (N / BN) < num_sms) {
+        const int nb = BN == 256 ? 128 : BN == 192 ? 64 : 64;
+        if (N % nb) break;
+        BN = nb;
+    }
     CUtensorMap ta, tb;
     int rc = make_map(&ta, A, M, Kvalid, lda, kBM);
     if (rc) return rc;
@@ -292,19 +308,31 @@ __global__ void k_dz1T(const float *dH1, const __nv_bfloat16 *H1, int B, int h1,
 }
 
 // out[j] = sum_b X[b][j] (* w[b] if w): column sums of a [B][C] matrix.
+// Block (32, 32): threadIdx.x picks the column of a 32-column tile,
+// threadIdx.y the rows b = y, y + 32, ...; the 32 partial sums of a column
+// are then added in a fixed order, so the result does not depend on timing.
 template <typename T>
 __global__ void k_colsum(const T *X, const float *w, int B, int C, float *out)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= C) return;
+    __shared__ float part[32][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
     float acc = 0.0f;
-    for (int b = 0; b < B; ++b) {
-        float x;
-        if constexpr (sizeof(T) == 2) x = __bfloat162float(X[(size_t)b * C + j]);
-        else x = (float)X[(size_t)b * C + j];
-        acc += w ? x * w[b] : x;
+    if (j < C) {
+#pragma unroll 4
+        for (int b = threadIdx.y; b < B; b += 32) {
+            float x;
+            if constexpr (sizeof(T) == 2) x = __bfloat162float(X[(size_t)b * C + j]);
+            else x = (float)X[(size_t)b * C + j];
+            acc += w ? x * w[b] : x;
+        }
     }
-    out[j] = acc;
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < C) {
+        float s = 0.0f;
+        for (int y = 0; y < 32; ++y) s += part[y][threadIdx.x];
+        out[j] = s;
+    }
 }
 
 __global__ void k_sum(const float *x, int n, float *out)
@@ -348,10 +376,15 @@ __global__ void k_mlp_init(float *W, int rows, int cols, int ld, uint64_t seed, 
     }
 }
 
-// Adam (Kingma & Ba 2015) on n parameters; step t >= 1.
+// Adam (Kingma & Ba 2015) on n parameters.  The step count lives on the
+// device (t_prev = steps taken so far), so a training step can be replayed
+// from a CUDA graph; this step is t = t_prev + 1, with the bias corrections
+// 1 - b1^t and 1 - b2^t.  k_adam_tick then advances the count.
 __global__ void k_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2)
+                       const long long *t_prev)
 {
+    const float t = (float)(*t_prev + 1);
+    const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gi;
@@ -362,13 +395,18 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, int n, floa
     }
 }
 
+__global__ void k_adam_tick(long long *t)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
+}
+
 }  // namespace fgpu
 
 using namespace fgpu;
 
 struct ffs_mlp {
     int in_dim = 0, K1 = 0, h1 = 0, h2 = 0, max_batch = 0;
-    long long adam_t = 0;
+    long long *d_adam_t = nullptr;   // Adam steps taken (device, so training steps can be graph-replayed)
     // parameters (FP32 masters): W1 [h1][K1] (columns >= in_dim stay 0), b1, W2 [h2][h1], b2, w3 [h2], b3 [1]
     float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *w3 = nullptr, *b3 = nullptr;
     float *gW1 = nullptr, *gb1 = nullptr, *gW2 = nullptr, *gb2 = nullptr, *gw3 = nullptr, *gb3 = nullptr;
@@ -440,7 +478,10 @@ int64_t mlp_state_bytes(const ffs_mlp *M) { return (int64_t)sizeof(MlpBlobHeader
 
 int mlp_save(const ffs_mlp *M, void *host, cudaStream_t st)
 {
-    MlpBlobHeader h{kMlpBlobMagic, kMlpBlobVersion, M->in_dim, M->h1, M->h2, M->K1, M->adam_t, (int64_t)M->n_params};
+    long long t = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&t, M->d_adam_t, 8, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    MlpBlobHeader h{kMlpBlobMagic, kMlpBlobVersion, M->in_dim, M->h1, M->h2, M->K1, (int64_t)t, (int64_t)M->n_params};
     memcpy(host, &h, sizeof(h));
     float *p = reinterpret_cast<float *>(static_cast<char *>(host) + sizeof(h));
     FFS_CUDA_TRY(cudaMemcpyAsync(p, M->params, M->n_params * 4, cudaMemcpyDefault, st));
@@ -466,7 +507,8 @@ int mlp_load(ffs_mlp *M, const void *host, int64_t size, cudaStream_t st)
     FFS_CUDA_TRY(cudaMemcpyAsync(M->params, p, M->n_params * 4, cudaMemcpyDefault, st));
     FFS_CUDA_TRY(cudaMemcpyAsync(M->m, p + M->n_params, M->n_params * 4, cudaMemcpyDefault, st));
     FFS_CUDA_TRY(cudaMemcpyAsync(M->v, p + 2 * M->n_params, M->n_params * 4, cudaMemcpyDefault, st));
-    M->adam_t = h.adam_t;
+    const long long t = h.adam_t;
+    FFS_CUDA_TRY(cudaMemcpyAsync(M->d_adam_t, &t, 8, cudaMemcpyHostToDevice, st));
     int rc = refresh_bf16(M, st);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -536,6 +578,7 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->dH1 = (float *)alloc(Bm * h1 * 4);
     M->dZ1 = (float *)alloc(Bm * h1 * 4);
     M->err = (int *)alloc(4);
+    M->d_adam_t = (long long *)alloc(8);
     for (void *p : M->allocs)
         if (!p) {
             mlp_free(M);
@@ -550,6 +593,7 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->b3 = p; M->gb3 = g;
     if (cudaMemset(M->params, 0, M->n_params * 4) || cudaMemset(M->m, 0, M->n_params * 4) ||
         cudaMemset(M->v, 0, M->n_params * 4) || cudaMemset(M->grads, 0, M->n_params * 4) || cudaMemset(M->err, 0, 4) ||
+        cudaMemset(M->d_adam_t, 0, 8) ||
         refresh_bf16(M, 0) || cudaDeviceSynchronize()) {
         mlp_free(M);
         return set_error(FFS_ECUDA, "MLP initialisation");
@@ -582,7 +626,7 @@ int ffs_mlp_set_params(ffs_mlp *M, const float *W1, const float *b1, const float
     FFS_CUDA_TRY(cudaMemcpy(M->b3, &b3, 4, cudaMemcpyHostToDevice));
     FFS_CUDA_TRY(cudaMemset(M->m, 0, M->n_params * 4));
     FFS_CUDA_TRY(cudaMemset(M->v, 0, M->n_params * 4));
-    M->adam_t = 0;
+    FFS_CUDA_TRY(cudaMemset(M->d_adam_t, 0, 8));
     int rc = refresh_bf16(M, 0);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaDeviceSynchronize());
@@ -634,7 +678,7 @@ int ffs_mlp_init(ffs_mlp *M, uint64_t seed, ffs_stream stream)
     FFS_CUDA_TRY(cudaMemsetAsync(M->m, 0, M->n_params * 4, st));
     FFS_CUDA_TRY(cudaMemsetAsync(M->v, 0, M->n_params * 4, st));
     FFS_CUDA_TRY(cudaMemsetAsync(M->grads, 0, M->n_params * 4, st));
-    M->adam_t = 0;
+    FFS_CUDA_TRY(cudaMemsetAsync(M->d_adam_t, 0, 8, st));
     return refresh_bf16(M, st);
 }
 
@@ -642,7 +686,10 @@ int ffs_mlp_adam_steps(const ffs_mlp *M, int64_t *steps)
 {
     clear_error();
     if (!M || !steps) return set_error(FFS_EINVAL, "NULL argument");
-    *steps = M->adam_t;
+    long long t = 0;
+    FFS_CUDA_TRY(cudaDeviceSynchronize());
+    FFS_CUDA_TRY(cudaMemcpy(&t, M->d_adam_t, 8, cudaMemcpyDeviceToHost));
+    *steps = (int64_t)t;
     return FFS_OK;
 }
 
@@ -688,10 +735,10 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, st));
     k_loss<<<(B + 255) / 256, 256, 0, st>>>(M->y, target, B, M->dy, loss);
     // output layer gradients
-    k_colsum<__nv_bfloat16><<<(h2 + 127) / 128, 128, 0, st>>>(M->H2, M->dy, B, h2, M->gw3);
+    k_colsum<__nv_bfloat16><<<(h2 + 31) / 32, dim3(32, 32), 0, st>>>(M->H2, M->dy, B, h2, M->gw3);
     k_sum<<<1, 256, 0, st>>>(M->dy, B, M->gb3);
     k_dz2<<<512, 256, 0, st>>>(M->dy, M->H2, M->w3, B, h2, M->dZ2, M->dZ2T);
-    k_colsum<__nv_bfloat16><<<(h2 + 127) / 128, 128, 0, st>>>(M->dZ2, nullptr, B, h2, M->gb2);
+    k_colsum<__nv_bfloat16><<<(h2 + 31) / 32, dim3(32, 32), 0, st>>>(M->dZ2, nullptr, B, h2, M->gb2);
     // gW2 = dZ2^T H1: A = dZ2T [h2][B], B = H1T [h1][B]
     k_transpose_bf16<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(M->H1, B, h1, h1, M->H1T, B);
     GemmEpi e;
@@ -706,7 +753,7 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     e.ldd = h1;
     if ((rc = gemm_bf16(M->dZ2, h2, M->W2Tb, h2, B, h1, h2, e, st))) return rc;
     k_dz1T<<<512, 256, 0, st>>>(M->dH1, M->H1, B, h1, M->dZ1T, M->dZ1);
-    k_colsum<float><<<(h1 + 127) / 128, 128, 0, st>>>(M->dZ1, nullptr, B, h1, M->gb1);
+    k_colsum<float><<<(h1 + 31) / 32, dim3(32, 32), 0, st>>>(M->dZ1, nullptr, B, h1, M->gb1);
     // gW1 = dZ1^T X: A = dZ1T [h1][B], B = XT [K1][B]
     k_transpose_bf16<<<dim3((K1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
         reinterpret_cast<const __nv_bfloat16 *>(x), B, M->in_dim, ldx, M->XT, B);
@@ -715,10 +762,9 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     e.ldd = K1;
     if ((rc = gemm_bf16(M->dZ1T, B, M->XT, B, h1, K1, B, e, st))) return rc;
     // Adam
-    M->adam_t += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - powf(b1, (float)M->adam_t), c2 = 1.0f - powf(b2, (float)M->adam_t);
-    k_adam<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, b1, b2, 1e-8f, c1, c2);
+    k_adam<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
+                                 M->d_adam_t);
+    k_adam_tick<<<1, 32, 0, st>>>(M->d_adam_t);
     FFS_CUDA_TRY(cudaGetLastError());
     return refresh_bf16(M, st);
 }

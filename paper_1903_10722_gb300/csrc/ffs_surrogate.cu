@@ -10,16 +10,26 @@
 
 namespace fgpu {
 
+// Candidates built per warp: a warp builds its children one after another
+// with all 32 lanes, so few children per warp and many warps hide the
+// parents' load latency.
+constexpr int kCandPerWarp = 4;
+
 // Candidate k of cell c: the cellular child (two tournaments, order
-// crossover, swap mutation) drawn from the stream of purpose kPurposeSurrogateBase + k.
+// crossover, swap mutation) drawn from the stream of purpose
+// kPurposeSurrogateBase + k.  Lane l < kCandPerWarp of warp w builds
+// candidate w * kCandPerWarp + l.  With X non-null, the warp then writes its
+// candidates' network inputs (as k_sur_features does).
 __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatch batch, int rows, int cols, int n,
-                                 int ld, int K, int16_t *cand)
+                                 int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat,
+                                 __nv_bfloat16 *X, int ldx)
 {
     extern __shared__ uint32_t bits_smem[];
     const int cells = rows * cols;
     const int total = batch.count * cells * K;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = t < total;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int t = gw * kCandPerWarp + lane;
+    const bool valid = lane < kCandPerWarp && t < total;
     const int tt = valid ? t : total - 1;
     const int bi = tt / (cells * K);
     const int rem = tt - bi * cells * K;
@@ -35,9 +45,12 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
     ChildJob job;
     job.active = valid;
     job.child = cand + (int64_t)tt * ld;
+    job.p1 = job.p2 = pin;
+    job.l = job.r = 0;
+    job.cross = false;
     bool mutate = false;
     U4 b2{0, 0, 0, 0};
-    {
+    if (valid) {
         const U4 b0 = draw_block(g.seed, purpose, ref.island, gen, (uint32_t)c, 0u);
         const U4 b1 = draw_block(g.seed, purpose, ref.island, gen, (uint32_t)c, 1u);
         b2 = draw_block(g.seed, purpose, ref.island, gen, (uint32_t)c, 2u);
@@ -59,7 +72,7 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
         const int u = (int)uniform_below(b1.y, (uint32_t)n), v = (int)uniform_below(b1.z, (uint32_t)n);
         job.l = min(u, v);
         job.r = max(u, v);
-        mutate = valid && fires(b1.w, g.cell_pm);
+        mutate = fires(b1.w, g.cell_pm);
     }
     uint32_t *bits = bits_smem + (threadIdx.x >> 5) * mark_words(n);
     warp_build_children(job, n, ld, bits);
@@ -69,6 +82,37 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
         const int16_t tmp = child[i];
         child[i] = child[j];
         child[j] = tmp;
+    }
+    if (!X) return;
+    __syncwarp();
+    // network inputs of the warp's candidates, all lanes on one row at a time
+    const float denom = (float)(n > 1 ? n - 1 : 1);
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, valid);
+    while (todo) {
+        const int j0 = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const int tj = gw * kCandPerWarp + j0;
+        const int16_t *row = cand + (int64_t)tj * ld;
+        __nv_bfloat16 *x = X + (int64_t)tj * ldx;
+        // zeros and the instance features, eight values (16 bytes) per store
+        for (int g8 = lane; g8 < (ldx >> 3); g8 += 32) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int j = 8 * g8 + 2 * h;
+                const float a = (j >= P && j < P + nfeat) ? inst_feat[j - P] : 0.0f;
+                const float b = (j + 1 >= P && j + 1 < P + nfeat) ? inst_feat[j + 1 - P] : 0.0f;
+                const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+                w4[h] = *reinterpret_cast<const uint32_t *>(&v);
+            }
+            reinterpret_cast<uint4 *>(x)[g8] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        __syncwarp();
+        for (int q = lane; q < n; q += 32) {
+            const int j = row[q];
+            if ((unsigned)j < (unsigned)n) x[j] = __float2bfloat16_rn((float)q / denom);
+        }
+        __syncwarp();
     }
 }
 
@@ -96,15 +140,18 @@ __global__ void k_sur_features(const int16_t *rows, int64_t nrows, int n, int ld
 
 // Per cell: the best-scored candidate (lowest score, lowest index on ties)
 // is decoded exactly and replaces the cell iff better; the pair is appended
-// to the ring buffer at slot (ring_base + cell) mod ring_cap.
+// to the ring buffer at slot (ring_base + cell) mod ring_cap, ring_base =
+// ctr[0], the pairs appended before this generation (a device counter, so
+// the generation can be replayed from a CUDA graph; k_sur_tick advances it).
 __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32_t *__restrict__ tab_g,
                                                     const int32_t *__restrict__ stage_g, GaScalars g,
                                                     const __grid_constant__ IslandBatch batch, int rows, int cols,
                                                     int ld, int K, const int16_t *cand, const float *scores,
                                                     int32_t *chosen, int16_t *ring_rows, int32_t *ring_ms,
-                                                    long long ring_cap, long long ring_base,
+                                                    long long ring_cap, const long long *ctr,
                                                     unsigned long long *decoded)
 {
+    const long long ring_base = ctr[0];
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ DecodeLayout s_L;
     const int T = blockDim.x;
@@ -164,11 +211,57 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
     decode_tmem_end(Ls);
 }
 
-// Training batch: B rows drawn uniformly (Philox, purpose kPurposeTrainSample)
-// from the first `valid` ring slots; target = makespan * inv_lb - 1.
-__global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long valid, int ld, uint64_t seed,
-                             uint32_t draw_gen, int B, int16_t *out_rows, float *targets, float inv_lb)
+// Standardisation of the training targets: mean and 1 / std (std at least 1)
+// of the makespans of the `recent` latest ring pairs (the last generation's
+// exact decodes), into norm[0..1].  The screen needs only the ranking of a
+// cell's candidates, whose makespans differ by a few tenths of a percent
+// late in a run: standardised targets keep those differences at the scale
+// the network learns.  One block.
+__global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm)
 {
+    __shared__ double part[2][32];
+    const long long cnt = ctr[0] < ring_cap ? ctr[0] : ring_cap;
+    const int m = (int)(cnt < recent ? cnt : recent);
+    double s = 0.0, q = 0.0;
+    const long long last = (ctr[0] - 1) % ring_cap;   // slot of the latest pair (m > 0 only)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const long long slot = last - i;
+        const double v = (double)ring_ms[slot >= 0 ? slot : slot + ring_cap];
+        s += v;
+        q += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[0][threadIdx.x >> 5] = s;
+        part[1][threadIdx.x >> 5] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, Q = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            S += part[0][w];
+            Q += part[1][w];
+        }
+        const double mean = m > 0 ? S / m : 0.0;
+        double var = m > 0 ? Q / m - mean * mean : 1.0;
+        if (var < 1.0) var = 1.0;
+        norm[0] = (float)mean;
+        norm[1] = (float)(1.0 / sqrt(var));
+    }
+}
+
+// Training batch: B rows drawn uniformly (Philox, purpose kPurposeTrainSample,
+// generation field = batches drawn before, ctr[1]) from the first valid =
+// min(ctr[0], ring_cap) ring slots; target = (makespan - norm[0]) * norm[1].
+__global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap,
+                             const long long *ctr, int ld, uint64_t seed, int B, int16_t *out_rows, float *targets,
+                             const float *norm)
+{
+    const long long valid = ctr[0] < ring_cap ? ctr[0] : ring_cap;
+    const uint32_t draw_gen = (uint32_t)ctr[1];
     const int lane = threadIdx.x & 31;
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B; b += (gridDim.x * blockDim.x) >> 5) {
         const U4 d = draw_block(seed, kPurposeTrainSample, 0u, draw_gen, (uint32_t)b, 0u);
@@ -176,8 +269,14 @@ __global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, l
         const int4 *s4 = reinterpret_cast<const int4 *>(ring_rows + idx * ld);
         int4 *d4 = reinterpret_cast<int4 *>(out_rows + (int64_t)b * ld);
         for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
-        if (lane == 0) targets[b] = (float)ring_ms[idx] * inv_lb - 1.0f;
+        if (lane == 0) targets[b] = ((float)ring_ms[idx] - norm[0]) * norm[1];
     }
+}
+
+// ctr[which] += add (one thread): the surrogate's device counters.
+__global__ void k_sur_tick(long long *ctr, int which, long long add)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctr[which] += add;
 }
 
 __global__ void k_fill_f32(float *p, int64_t n, float v)
@@ -186,13 +285,17 @@ __global__ void k_fill_f32(float *p, int64_t n, float v)
 }
 
 int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
-                          int ld, int K, int16_t *cand, cudaStream_t st)
+                          int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat, void *X, int ldx,
+                          cudaStream_t st)
 {
     const int total = batch.count * rows * cols * K;
     const int T = 128;
+    const int warps = (total + kCandPerWarp - 1) / kCandPerWarp;
     const size_t smem = (size_t)(T / 32) * mark_words(inst->n) * 4;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sur_candidates<<<(total + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand);
+    k_sur_candidates<<<(warps * 32 + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand, P,
+                                                                inst_feat, nfeat, static_cast<__nv_bfloat16 *>(X),
+                                                                ldx);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -211,25 +314,43 @@ int launch_sur_features(const int16_t *rows, int64_t nrows, int n, int ld, int P
 
 int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
                       int ld, int K, const int16_t *cand, const float *scores, int32_t *chosen, int16_t *ring_rows,
-                      int32_t *ring_ms, long long ring_cap, long long ring_base, int B_req, int T_req,
+                      int32_t *ring_ms, long long ring_cap, const long long *ctr, int B_req, int T_req,
                       unsigned long long *decoded, cudaStream_t st)
 {
     Plan p;
-    int rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_req, 0, &p, g.variant);
+    const int T_sp = spread_threads(inst, (int64_t)rows * cols * batch.count, T_req);
+    int rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_sp, 0, &p, g.variant);
+    if (rc && T_sp != T_req) rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_req, 0, &p, g.variant);
     if (rc) return rc;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     const int grid = grid_for(inst, p, (int64_t)rows * cols * batch.count);
     k_sur_select<<<grid, p.T, p.smem, st>>>(p.L, inst->d_tab, inst->d_stage, g, batch, rows, cols, ld, K, cand, scores,
-                                             chosen, ring_rows, ring_ms, ring_cap, ring_base, decoded);
+                                             chosen, ring_rows, ring_ms, ring_cap, ctr, decoded);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
 
-int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long valid, int ld, uint64_t seed,
-                      uint32_t draw_gen, int B, int16_t *out_rows, float *targets, float inv_lb, cudaStream_t st)
+int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm,
+                    cudaStream_t st)
 {
-    k_sur_gather<<<(B * 32 + 255) / 256, 256, 0, st>>>(ring_rows, ring_ms, valid, ld, seed, draw_gen, B, out_rows,
-                                                       targets, inv_lb);
+    k_sur_norm<<<1, 1024, 0, st>>>(ring_ms, ring_cap, ctr, recent, norm);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, const long long *ctr,
+                      int ld, uint64_t seed, int B, int16_t *out_rows, float *targets, const float *norm,
+                      cudaStream_t st)
+{
+    k_sur_gather<<<(B * 32 + 255) / 256, 256, 0, st>>>(ring_rows, ring_ms, ring_cap, ctr, ld, seed, B, out_rows,
+                                                       targets, norm);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int launch_sur_tick(long long *ctr, int which, long long add, cudaStream_t st)
+{
+    k_sur_tick<<<1, 32, 0, st>>>(ctr, which, add);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }

