@@ -476,21 +476,29 @@ int ffs_mlp_check(ffs_mlp *mlp, ffs_stream stream);
  * candidate (lowest k on ties) is decoded exactly and replaces the cell iff
  * better.  During the first warmup_generations every score is 0 (so
  * candidate 0 is taken).  Every exact (child, makespan) pair goes to a
- * device ring buffer; every train_every generations, train_steps Adam steps
- * on batches of train_batch pairs drawn from it (Philox purpose 15) fit the
- * network to makespan / LB - 1.  Pseudo islands are not screened.  The
- * network must have in_dim >= n + 40 and max_batch >= cellular cells x
- * candidates; it is used, not owned.  Generations then run as direct launches
- * (no graph).  ffs_islands_surrogate_last copies the last generation's
- * scores [cells x candidates] and picks [cells] (cellular islands in ring
- * order), the last training loss, the last generation's candidate rows
- * (candidates [cells x candidates][ld_out], may be NULL), and reports the
- * pairs produced so far.
+ * device ring buffer.  After every generation G (counted from 1) with G %
+ * train_every == 0, a training round of train_steps Adam steps on batches of
+ * train_batch pairs, drawn uniformly (Philox purpose 15) from the pairs of
+ * generations 1..G (the newest ring_capacity - cells pairs), with the
+ * targets standardised by generation G's makespans, (makespan - mean) / std
+ * (std at least 1): the screen needs only the ranking of a cell's
+ * candidates.  The round runs at the start of generation G + 1, beside its
+ * candidate building, and ends before G + 1's candidates are scored.
+ * Pseudo islands are not screened.  The network must have in_dim >= n + 40
+ * and max_batch >= cellular cells x candidates; it is used, not owned;
+ * ring_capacity must be at least cells + train_batch.  Generations are
+ * replayed from CUDA graphs (captured on first use; four forms: before /
+ * after the warm-up, with / without a training round).
+ * ffs_islands_surrogate_last copies the last generation's scores
+ * [cells x candidates] and picks [cells] (cellular islands in ring order),
+ * the last training loss (mean squared error on the standardised targets),
+ * the last generation's candidate rows (candidates [cells x
+ * candidates][ld_out], may be NULL), and reports the pairs produced so far.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int32_t candidates;          /* children per cell, 1..16 (8) */
     int32_t train_every;         /* generations between training rounds (1; 0 = never) */
-    int32_t train_steps;         /* Adam steps per round (4) */
+    int32_t train_steps;         /* Adam steps per round (2) */
     int32_t train_batch;         /* pairs per step, multiple of 128 (1024) */
     int32_t ring_capacity;       /* pairs kept (131072) */
     int32_t warmup_generations;  /* generations scored 0 while the ring fills (5) */

@@ -688,33 +688,35 @@ struct SurrogateState {
     int32_t *ring_ms = nullptr;
     long long ring_cap = 0, ring_count = 0;
     float *inst_feat = nullptr;    // [nfeat]
-    int16_t *train_rows = nullptr; // [train_batch][ld]
     void *train_X = nullptr;       // BF16 [train_batch][ldx]
     float *train_t = nullptr, *loss = nullptr;
     long long train_rounds = 0;
     std::vector<int> cell_islands;
     // device counters read by the kernels: [0] ring pairs appended, [1]
-    // training batches drawn (host mirrors: ring_count, train_rounds)
+    // training batches drawn (host mirrors: ring_count, train_rounds), [2]
+    // the ring count when the current generation began
     long long *d_ctr = nullptr;
     float *d_norm = nullptr;       // training-target standardisation (mean, 1 / std)
-    // generations (before / after the warm-up) and training rounds replayed
-    // from CUDA graphs; the pseudo islands run on `side`, beside the screen
-    cudaGraphExec_t g_gen[2] = {nullptr, nullptr};
-    cudaGraphExec_t g_train = nullptr;
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // generations replayed from CUDA graphs, [warm][train]: before / after
+    // the warm-up, without / with a training round; the pseudo islands run
+    // on `side` beside the screen, the training round on `side2` beside the
+    // selection (after the forward pass, which reads the weights it updates)
+    cudaGraphExec_t g_gen[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr;
     void drop_graphs()
     {
-        for (auto &g : g_gen)
-            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
-        if (g_train) { cudaGraphExecDestroy(g_train); g_train = nullptr; }
+        for (auto &row : g_gen)
+            for (auto &g : row)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     }
     ~SurrogateState()
     {
         drop_graphs();
         if (side) cudaStreamDestroy(side);
-        if (fork_ev) cudaEventDestroy(fork_ev);
-        if (join_ev) cudaEventDestroy(join_ev);
+        if (side2) cudaStreamDestroy(side2);
+        for (cudaEvent_t e : {fork_ev, join_ev, fork2_ev, join2_ev})
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -756,7 +758,9 @@ static IslandRef device_ref(const ffs_islands *S, int i)
     return r;
 }
 
-static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st);
+template <typename F>
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st,
+                                    F between);
 
 // One generation of the islands in `ids` (all of one kind): cellular islands
 // in launches of up to kMaxBatch, pseudo islands likewise, one decode of all
@@ -791,7 +795,12 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
         for (int i : ids)
             if (S->kind[i] == kind) sel.push_back(i);
         if (kind == 0 && S->sur && !sel.empty()) {
-            int rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, st);
+            // (single-island steps: no training round inside the generation)
+            FFS_CUDA_TRY(cudaGetLastError());
+            int rc = launch_sur_tick(S->sur->d_ctr, 2, -1, st);
+            if (rc) return rc;
+            rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, st,
+                                          [](cudaStream_t) { return (int)FFS_OK; });
             if (rc) return rc;
             continue;
         }
@@ -847,30 +856,48 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
     return FFS_OK;
 }
 
-// Screened generation of the cellular islands in `sel`: candidates, network
-// scores (all zero during the warm-up generations, warm = false: candidate 0
-// is taken), best-scored candidate decoded exactly, ring buffer append (the
-// device ring counter advanced by the cells of each batch).
-static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st)
+// Screened generation of the cellular islands in `sel`: phase 1 builds every
+// batch's candidates (with their network inputs when warm); `between` then
+// runs (the wait for the training round); phase 2 scores each batch with the
+// network (all scores 0 during the warm-up: candidate 0 is taken), decodes
+// each cell's best-scored candidate exactly, replaces the cell iff better and
+// appends the pair to the ring (the device ring counter advanced by the
+// cells of each batch).
+template <typename F>
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st,
+                                    F between)
 {
     SurrogateState *R = S->sur;
     const GaScalars g = scalars_of(&S->prm);
     const int K = R->sp.candidates, cells = S->rows * S->cols;
-    int offset = 0;   // cells before this batch among the cellular islands
+    std::vector<IslandBatch> batches;
     for (size_t b0 = 0; b0 < sel.size(); b0 += kMaxBatch) {
         IslandBatch batch;
         memset(&batch, 0, sizeof(batch));
         batch.count = (int)std::min(sel.size() - b0, (size_t)kMaxBatch);
         for (int t = 0; t < batch.count; ++t) batch.ref[t] = device_ref(S, sel[b0 + t]);
+        batches.push_back(batch);
+    }
+    int offset = 0;   // cells before this batch among the cellular islands
+    for (const IslandBatch &batch : batches) {
         const int ncells = batch.count * cells;
         int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
-        float *scores = R->scores + (int64_t)offset * K;
         // the candidates, and in warm generations their network inputs in the same launch
         void *X = static_cast<char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
         int rc = launch_sur_candidates(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, R->P, R->inst_feat,
                                        R->nfeat, warm ? X : nullptr, R->ldx, st);
         if (rc) return rc;
+        offset += ncells;
+    }
+    int rc = between(st);
+    if (rc) return rc;
+    offset = 0;
+    for (const IslandBatch &batch : batches) {
+        const int ncells = batch.count * cells;
+        const int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
+        float *scores = R->scores + (int64_t)offset * K;
         if (warm) {
+            const void *X = static_cast<const char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
             if ((rc = ffs_mlp_forward(R->mlp, static_cast<const uint16_t *>(X), R->ldx, ncells * K, scores, st)))
                 return rc;
         } else if ((rc = launch_fill_f32(scores, (int64_t)ncells * K, 0.0f, st))) {
@@ -894,13 +921,11 @@ static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
     int rc0 = launch_sur_norm(R->ring_ms, R->ring_cap, R->d_ctr, R->cells_total, R->d_norm, st);
     if (rc0) return rc0;
     for (int s = 0; s < R->sp.train_steps; ++s) {
-        int rc = launch_sur_gather(R->ring_rows, R->ring_ms, R->ring_cap, R->d_ctr, S->ld, S->prm.seed,
-                                   R->sp.train_batch, R->train_rows, R->train_t, R->d_norm, st);
+        int rc = launch_sur_gather(R->ring_rows, R->ring_ms, R->ring_cap, R->cells_total, R->d_ctr, S->ld, S->prm.seed,
+                                   R->sp.train_batch, R->train_t, R->d_norm, S->inst->n, R->P, R->inst_feat, R->nfeat,
+                                   R->train_X, R->ldx, st);
         if (rc) return rc;
         if ((rc = launch_sur_tick(R->d_ctr, 1, 1, st))) return rc;
-        if ((rc = launch_sur_features(R->train_rows, R->sp.train_batch, S->inst->n, S->ld, R->P, R->inst_feat,
-                                      R->nfeat, R->train_X, R->ldx, st)))
-            return rc;
         if ((rc = ffs_mlp_train_step(R->mlp, static_cast<const uint16_t *>(R->train_X), R->ldx, R->train_t,
                                      R->sp.train_batch, R->sp.lr, R->loss, st)))
             return rc;
@@ -908,21 +933,35 @@ static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
     return FFS_OK;
 }
 
-// One screened generation of every island: the pseudo islands on the side
-// stream beside the cellular screen (fork / join by events), then the
-// generation advance and migration, as generation_all does.
-static int screened_generation(ffs_islands *S, bool warm, cudaStream_t st)
+// One screened generation of every island: the ring-count snapshot (the
+// pairs of the generations before this one), the pseudo islands on the side
+// stream beside the cellular screen, and (train = true) the training round
+// on the previous generations' pairs on the second side stream, beside the
+// candidate building and joined before the forward pass that reads the
+// updated weights; then, everything joined, the generation advance and
+// migration, as generation_all does.
+static int screened_generation(ffs_islands *S, bool warm, bool train, cudaStream_t st)
 {
     SurrogateState *R = S->sur;
     std::vector<int> cel, pse;
     for (int i = 0; i < S->I; ++i) (S->kind[i] == 0 ? cel : pse).push_back(i);
+    int rc = launch_sur_tick(R->d_ctr, 2, -1, st);
+    if (rc) return rc;
     if (!pse.empty()) {
         FFS_CUDA_TRY(cudaEventRecord(R->fork_ev, st));
         FFS_CUDA_TRY(cudaStreamWaitEvent(R->side, R->fork_ev, 0));
-        int rc = islands_generation_launch(S, pse, R->side);
-        if (rc) return rc;
+        if ((rc = islands_generation_launch(S, pse, R->side))) return rc;
     }
-    int rc = screened_cellular_launch(S, cel, warm, st);
+    if (train) {
+        FFS_CUDA_TRY(cudaEventRecord(R->fork2_ev, st));
+        FFS_CUDA_TRY(cudaStreamWaitEvent(R->side2, R->fork2_ev, 0));
+        if ((rc = surrogate_train_launch(S, R->side2))) return rc;
+        FFS_CUDA_TRY(cudaEventRecord(R->join2_ev, R->side2));
+    }
+    rc = screened_cellular_launch(S, cel, warm, st, [&](cudaStream_t cs) -> int {
+        if (train) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
+        return FFS_OK;
+    });
     if (rc) return rc;
     if (!pse.empty()) {
         FFS_CUDA_TRY(cudaEventRecord(R->join_ev, R->side));
@@ -1167,7 +1206,7 @@ void ffs_surrogate_params_default(ffs_surrogate_params *p)
     memset(p, 0, sizeof(*p));
     p->candidates = 8;
     p->train_every = 1;
-    p->train_steps = 4;
+    p->train_steps = 2;
     p->train_batch = 1024;
     p->ring_capacity = 1 << 17;
     p->warmup_generations = 5;
@@ -1196,8 +1235,8 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
         return set_error(FFS_EINVAL, "network max_batch %d < %lld candidates per generation", mlp_max_batch(mlp),
                          (long long)cells_total * K);
     if (sp->train_batch > mlp_max_batch(mlp)) return set_error(FFS_EINVAL, "train_batch above the network's max_batch");
-    if (sp->ring_capacity < cells_total || sp->ring_capacity < sp->train_batch)
-        return set_error(FFS_EINVAL, "ring_capacity must hold one generation's pairs and a training batch");
+    if ((long long)sp->ring_capacity < (long long)cells_total + sp->train_batch)
+        return set_error(FFS_EINVAL, "ring_capacity must hold one generation's pairs plus a training batch");
     SurrogateState *R = new SurrogateState();
     R->mlp = mlp;
     R->sp = *sp;
@@ -1221,14 +1260,13 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     R->ring_rows = (int16_t *)alloc((size_t)R->ring_cap * S->ld * 2);
     R->ring_ms = (int32_t *)alloc((size_t)R->ring_cap * 4);
     R->inst_feat = (float *)alloc(nfeat * 4);
-    R->train_rows = (int16_t *)alloc((size_t)sp->train_batch * S->ld * 2);
     R->train_X = alloc((size_t)sp->train_batch * R->ldx * 2);
     R->train_t = (float *)alloc((size_t)sp->train_batch * 4);
     R->loss = (float *)alloc(4);
-    R->d_ctr = (long long *)alloc(2 * sizeof(long long));
+    R->d_ctr = (long long *)alloc(3 * sizeof(long long));
     R->d_norm = (float *)alloc(2 * sizeof(float));
     if (!R->cand || !R->X || !R->scores || !R->chosen || !R->ring_rows || !R->ring_ms || !R->inst_feat ||
-        !R->train_rows || !R->train_X || !R->train_t || !R->loss || !R->d_ctr || !R->d_norm) {
+        !R->train_X || !R->train_t || !R->loss || !R->d_ctr || !R->d_norm) {
         delete R;
         return set_error(FFS_ENOMEM, "surrogate buffers");
     }
@@ -1257,10 +1295,13 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     f[37] = (float)(I->S / 20.0);
     f[38] = (float)(lb / total);
     if (cudaMemcpy(R->inst_feat, f.data(), nfeat * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(R->d_ctr, 0, 2 * sizeof(long long)) != cudaSuccess ||
+        cudaMemset(R->d_ctr, 0, 3 * sizeof(long long)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&R->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&R->side2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&R->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&R->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->fork2_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->join2_ev, cudaEventDisableTiming) != cudaSuccess) {
         (void)cudaGetLastError();
         delete R;
         return set_error(FFS_ECUDA, "surrogate state initialisation");
@@ -1453,27 +1494,27 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
         // device, the host keeps mirrors to decide warm-up and training
         SurrogateState *R = S->sur;
         for (int g = 0; g < n_generations; ++g) {
-            const int warm = S->host_gen[0] + 1 > R->sp.warmup_generations ? 1 : 0;
-            if (!R->g_gen[warm]) {
-                int rc = capture_graph(S, &R->g_gen[warm],
-                                       [&](cudaStream_t cs) { return screened_generation(S, warm != 0, cs); });
+            const long long G = S->host_gen[0] + 1;   // the generation about to run
+            const int warm = G > R->sp.warmup_generations ? 1 : 0;
+            // the training round after every train_every-th generation runs at the start
+            // of the next one, on the pairs of the generations before it (at least a batch)
+            const int train = (R->sp.train_every > 0 && R->sp.train_steps > 0 && G >= 2 &&
+                               (G - 1) % R->sp.train_every == 0 &&
+                               std::min(R->ring_count, R->ring_cap - R->cells_total) >= R->sp.train_batch)
+                                  ? 1 : 0;
+            if (!R->g_gen[warm][train]) {
+                int rc = capture_graph(S, &R->g_gen[warm][train], [&](cudaStream_t cs) {
+                    return screened_generation(S, warm != 0, train != 0, cs);
+                });
                 if (rc) return rc;
             }
-            FFS_CUDA_TRY(cudaGraphLaunch(R->g_gen[warm], st));
+            FFS_CUDA_TRY(cudaGraphLaunch(R->g_gen[warm][train], st));
             for (int i = 0; i < S->I; ++i) {
                 S->host_cur[i] ^= 1;
                 S->host_gen[i] += 1;
             }
             R->ring_count += R->cells_total;
-            if (R->sp.train_every > 0 && R->sp.train_steps > 0 && S->host_gen[0] % R->sp.train_every == 0 &&
-                std::min(R->ring_count, R->ring_cap) >= R->sp.train_batch) {
-                if (!R->g_train) {
-                    int rc = capture_graph(S, &R->g_train, [&](cudaStream_t cs) { return surrogate_train_launch(S, cs); });
-                    if (rc) return rc;
-                }
-                FFS_CUDA_TRY(cudaGraphLaunch(R->g_train, st));
-                R->train_rounds += 1;
-            }
+            if (train) R->train_rounds += 1;
         }
         return FFS_OK;
     }

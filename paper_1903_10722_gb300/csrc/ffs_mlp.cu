@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CU
     using SM = GemmSmem<BN>;
     extern __shared__ uint8_t smem_dyn[];
     __shared__ int s_fail;
+    __shared__ float s_bias[256];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = base;
     uint8_t *sB = base + kGemmStages * SM::A_BYTES;
@@ -68,6 +69,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CU
         s_fail = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, SM::TCOLS);
+    // the epilogue's bias slice, read once per CTA
+    if (epi.mode == 1)
+        for (int c = threadIdx.x; c < BN; c += blockDim.x) s_bias[c] = epi.bias[n0 + c];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -125,8 +129,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CU
             uint32_t packed[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float x0 = fmaxf(v[2 * q] + epi.bias[n0 + c + 2 * q], 0.0f);
-                const float x1 = fmaxf(v[2 * q + 1] + epi.bias[n0 + c + 2 * q + 1], 0.0f);
+                const float x0 = fmaxf(v[2 * q] + s_bias[c + 2 * q], 0.0f);
+                const float x1 = fmaxf(v[2 * q + 1] + s_bias[c + 2 * q + 1], 0.0f);
                 const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
                 packed[q] = *reinterpret_cast<const uint32_t *>(&h);
             }
@@ -268,29 +272,29 @@ __global__ void k_out_layer(const __nv_bfloat16 *H2, int B, int h2, const float 
     if (lane == 0) y[warp] = acc + b3[0];
 }
 
-// dy = 2 (y - t) / B; loss accumulates mean squared error.
-__global__ void k_loss(const float *y, const float *t, int B, float *dy, float *loss)
+// Warp per row b of a training batch: y = H2[b] . w3 + b3, e = y - t[b],
+// dy[b] = 2 e / B (the MSE's derivative), loss += e^2 / B, and the output
+// layer's backpropagated signal dZ2[b][j] = dy[b] w3[j] [H2[b][j] > 0] as BF16,
+// row-major and transposed (dZ2T[j][b]).  Same arithmetic, in the same order,
+// as k_out_layer, k_loss and k_dz2 one after another.
+__global__ void k_out_loss_dz2(const __nv_bfloat16 *H2, int B, int h2, const float *w3, const float *b3,
+                               const float *t, float *dy, float *loss, __nv_bfloat16 *dZ2, __nv_bfloat16 *dZ2T)
 {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= B) return;
     float acc = 0.0f;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-        const float e = y[b] - t[b];
-        dy[b] = 2.0f * e / (float)B;
-        acc += e * e;
-    }
+    for (int j = lane; j < h2; j += 32) acc += __bfloat162float(H2[(size_t)b * h2 + j]) * w3[j];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc / (float)B);
-}
-
-// dZ2[b][j] = dy[b] w3[j] [H2[b][j] > 0]; written as BF16 row-major and transposed.
-__global__ void k_dz2(const float *dy, const __nv_bfloat16 *H2, const float *w3, int B, int h2, __nv_bfloat16 *dZ2,
-                      __nv_bfloat16 *dZ2T)
-{
-    const size_t total = (size_t)B * h2;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / h2), j = (int)(i % h2);
-        const float g = __bfloat162float(H2[i]) > 0.0f ? dy[b] * w3[j] : 0.0f;
+    const float e = (acc + b3[0]) - t[b];
+    const float d = 2.0f * e / (float)B;
+    if (lane == 0) {
+        dy[b] = d;
+        if (loss) atomicAdd(loss, e * e / (float)B);
+    }
+    for (int j = lane; j < h2; j += 32) {
+        const float g = __bfloat162float(H2[(size_t)b * h2 + j]) > 0.0f ? d * w3[j] : 0.0f;
         const __nv_bfloat16 gb = __float2bfloat16_rn(g);
-        dZ2[i] = gb;
+        dZ2[(size_t)b * h2 + j] = gb;
         dZ2T[(size_t)j * B + b] = gb;
     }
 }
@@ -335,18 +339,47 @@ __global__ void k_colsum(const T *X, const float *w, int B, int C, float *out)
     }
 }
 
-__global__ void k_sum(const float *x, int n, float *out)
+// The output layer's parameter gradients in one launch: gw3[j] = sum_b
+// H2[b][j] dy[b], gb2[j] = sum_b dZ2[b][j] (as k_colsum), and block 0 also
+// gb3 = sum_b dy[b] (threads b, b + 1024, ..., then a fixed-order sum).
+__global__ void k_out_grads(const __nv_bfloat16 *H2, const __nv_bfloat16 *dZ2, const float *dy, int B, int h2,
+                            float *gw3, float *gb2, float *gb3)
 {
-    float acc = 0.0f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += x[i];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    __shared__ float part[32];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __shared__ float part[2][32][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    float a = 0.0f, c = 0.0f;
+    if (j < h2) {
+#pragma unroll 4
+        for (int b = threadIdx.y; b < B; b += 32) {
+            a += __bfloat162float(H2[(size_t)b * h2 + j]) * dy[b];
+            c += __bfloat162float(dZ2[(size_t)b * h2 + j]);
+        }
+    }
+    part[0][threadIdx.y][threadIdx.x] = a;
+    part[1][threadIdx.y][threadIdx.x] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        out[0] = s;
+    if (threadIdx.y == 0 && j < h2) {
+        float sa = 0.0f, sc = 0.0f;
+        for (int y = 0; y < 32; ++y) {
+            sa += part[0][y][threadIdx.x];
+            sc += part[1][y][threadIdx.x];
+        }
+        gw3[j] = sa;
+        gb2[j] = sc;
+    }
+    if (blockIdx.x == 0) {
+        __syncthreads();
+        const int tid = threadIdx.y * 32 + threadIdx.x;
+        float sd = 0.0f;
+        for (int b = tid; b < B; b += 1024) sd += dy[b];
+        part[0][threadIdx.y][threadIdx.x] = sd;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.0f;
+            for (int y = 0; y < 32; ++y)
+                for (int x = 0; x < 32; ++x) t += part[0][y][x];
+            gb3[0] = t;
+        }
     }
 }
 
@@ -376,22 +409,36 @@ __global__ void k_mlp_init(float *W, int rows, int cols, int ld, uint64_t seed, 
     }
 }
 
-// Adam (Kingma & Ba 2015) on n parameters.  The step count lives on the
-// device (t_prev = steps taken so far), so a training step can be replayed
-// from a CUDA graph; this step is t = t_prev + 1, with the bias corrections
-// 1 - b1^t and 1 - b2^t.  k_adam_tick then advances the count.
-__global__ void k_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
-                       const long long *t_prev)
+// Adam (Kingma & Ba 2015) over the concatenated parameters.  The step count
+// lives on the device (t_prev = steps taken so far), so a training step can
+// be replayed from a CUDA graph; this step is t = t_prev + 1, with the bias
+// corrections 1 - b1^t and 1 - b2^t; k_adam_tick then advances the count.
+// It also writes the BF16 copies the GEMMs read: W1b[i] for the W1 block
+// [0, nW1) and, for the W2 block [w2_off, w2_off + h2 h1), W2b[o][c] and its
+// transpose W2Tb[c][o].
+__global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
+                            float eps, const long long *t_prev, int nW1, int w2_off, int h1, int h2,
+                            __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb)
 {
     const float t = (float)(*t_prev + 1);
     const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+    const int nW2 = h1 * h2;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.0f - b1) * gi;
         const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        if (i < nW1) {
+            W1b[i] = __float2bfloat16_rn(pi);
+        } else if (i >= w2_off && i < w2_off + nW2) {
+            const int r = i - w2_off, o = r / h1, c = r - o * h1;
+            const __nv_bfloat16 pb = __float2bfloat16_rn(pi);
+            W2b[r] = pb;
+            W2Tb[(size_t)c * h2 + o] = pb;
+        }
     }
 }
 
@@ -444,7 +491,8 @@ static int refresh_bf16(ffs_mlp *M, cudaStream_t st)
     return FFS_OK;
 }
 
-static int mlp_forward(ffs_mlp *M, const void *x, int ldx, int B, float *y, cudaStream_t st)
+// The two hidden layers: H1 = relu(x W1^T + b1), H2 = relu(H1 W2^T + b2), BF16.
+static int mlp_hidden(ffs_mlp *M, const void *x, int ldx, int B, cudaStream_t st)
 {
     GemmEpi e;
     memset(&e, 0, sizeof(e));
@@ -458,7 +506,13 @@ static int mlp_forward(ffs_mlp *M, const void *x, int ldx, int B, float *y, cuda
     e.Db = M->H2;
     e.bias = M->b2;
     e.ldd = M->h2;
-    if ((rc = gemm_bf16(M->H1, M->h1, M->W2b, M->h1, B, M->h2, M->h1, e, st))) return rc;
+    return gemm_bf16(M->H1, M->h1, M->W2b, M->h1, B, M->h2, M->h1, e, st);
+}
+
+static int mlp_forward(ffs_mlp *M, const void *x, int ldx, int B, float *y, cudaStream_t st)
+{
+    int rc = mlp_hidden(M, x, ldx, B, st);
+    if (rc) return rc;
     k_out_layer<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, M->h2, M->w3, M->b3, y);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
@@ -729,16 +783,14 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
         return set_error(FFS_EINVAL, "training batch %d must be a multiple of 128 and <= %d", B, M->max_batch);
     if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = mlp_forward(M, x, ldx, B, M->y, st);
+    int rc = mlp_hidden(M, x, ldx, B, st);
     if (rc) return rc;
     const int h1 = M->h1, h2 = M->h2, K1 = M->K1;
     if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, st));
-    k_loss<<<(B + 255) / 256, 256, 0, st>>>(M->y, target, B, M->dy, loss);
-    // output layer gradients
-    k_colsum<__nv_bfloat16><<<(h2 + 31) / 32, dim3(32, 32), 0, st>>>(M->H2, M->dy, B, h2, M->gw3);
-    k_sum<<<1, 256, 0, st>>>(M->dy, B, M->gb3);
-    k_dz2<<<512, 256, 0, st>>>(M->dy, M->H2, M->w3, B, h2, M->dZ2, M->dZ2T);
-    k_colsum<__nv_bfloat16><<<(h2 + 31) / 32, dim3(32, 32), 0, st>>>(M->dZ2, nullptr, B, h2, M->gb2);
+    // output layer, loss, its backpropagated signal, then its gradients
+    k_out_loss_dz2<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, h2, M->w3, M->b3, target, M->dy, loss, M->dZ2,
+                                                          M->dZ2T);
+    k_out_grads<<<(h2 + 31) / 32, dim3(32, 32), 0, st>>>(M->H2, M->dZ2, M->dy, B, h2, M->gw3, M->gb2, M->gb3);
     // gW2 = dZ2^T H1: A = dZ2T [h2][B], B = H1T [h1][B]
     k_transpose_bf16<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(M->H1, B, h1, h1, M->H1T, B);
     GemmEpi e;
@@ -761,12 +813,13 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     e.D = M->gW1;
     e.ldd = K1;
     if ((rc = gemm_bf16(M->dZ1T, B, M->XT, B, h1, K1, B, e, st))) return rc;
-    // Adam
-    k_adam<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
-                                 M->d_adam_t);
+    // Adam, writing the BF16 weight copies of the next forward pass as it goes
+    const int nW1 = h1 * K1, w2_off = nW1 + h1;
+    k_adam_bf16<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
+                                      M->d_adam_t, nW1, w2_off, h1, h2, M->W1b, M->W2b, M->W2Tb);
     k_adam_tick<<<1, 32, 0, st>>>(M->d_adam_t);
     FFS_CUDA_TRY(cudaGetLastError());
-    return refresh_bf16(M, st);
+    return FFS_OK;
 }
 
 // Non-zero if a tensor-core kernel of this MLP timed out waiting (then cleared).

@@ -10,6 +10,36 @@
 
 namespace fgpu {
 
+// Network input of one job-order row, written by the whole warp: x[j] =
+// position of job j / (n - 1) for j < n (0 when n = 1), zero for n <= j < P,
+// the instance features at [P, P + nfeat), zero beyond (BF16, ldx a multiple
+// of 8, x 16-byte aligned).  Zeros and features go eight values per 16-byte
+// store; the positions are then scattered by job.
+__device__ __forceinline__ void warp_write_features(const int16_t *row, int n, int P, const float *inst_feat,
+                                                    int nfeat, __nv_bfloat16 *x, int ldx)
+{
+    const int lane = threadIdx.x & 31;
+    const float denom = (float)(n > 1 ? n - 1 : 1);
+    for (int g8 = lane; g8 < (ldx >> 3); g8 += 32) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int j = 8 * g8 + 2 * h;
+            const float a = (j >= P && j < P + nfeat) ? inst_feat[j - P] : 0.0f;
+            const float b = (j + 1 >= P && j + 1 < P + nfeat) ? inst_feat[j + 1 - P] : 0.0f;
+            const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+            w4[h] = *reinterpret_cast<const uint32_t *>(&v);
+        }
+        reinterpret_cast<uint4 *>(x)[g8] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    __syncwarp();
+    for (int q = lane; q < n; q += 32) {
+        const int j = row[q];
+        if ((unsigned)j < (unsigned)n) x[j] = __float2bfloat16_rn((float)q / denom);
+    }
+    __syncwarp();
+}
+
 // Candidates built per warp: a warp builds its children one after another
 // with all 32 lanes, so few children per warp and many warps hide the
 // parents' load latency.
@@ -19,7 +49,7 @@ constexpr int kCandPerWarp = 4;
 // crossover, swap mutation) drawn from the stream of purpose
 // kPurposeSurrogateBase + k.  Lane l < kCandPerWarp of warp w builds
 // candidate w * kCandPerWarp + l.  With X non-null, the warp then writes its
-// candidates' network inputs (as k_sur_features does).
+// candidates' network inputs (warp_write_features).
 __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatch batch, int rows, int cols, int n,
                                  int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat,
                                  __nv_bfloat16 *X, int ldx)
@@ -86,55 +116,12 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
     if (!X) return;
     __syncwarp();
     // network inputs of the warp's candidates, all lanes on one row at a time
-    const float denom = (float)(n > 1 ? n - 1 : 1);
     unsigned todo = __ballot_sync(0xFFFFFFFFu, valid);
     while (todo) {
         const int j0 = __ffs(todo) - 1;
         todo &= todo - 1u;
         const int tj = gw * kCandPerWarp + j0;
-        const int16_t *row = cand + (int64_t)tj * ld;
-        __nv_bfloat16 *x = X + (int64_t)tj * ldx;
-        // zeros and the instance features, eight values (16 bytes) per store
-        for (int g8 = lane; g8 < (ldx >> 3); g8 += 32) {
-            uint32_t w4[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int j = 8 * g8 + 2 * h;
-                const float a = (j >= P && j < P + nfeat) ? inst_feat[j - P] : 0.0f;
-                const float b = (j + 1 >= P && j + 1 < P + nfeat) ? inst_feat[j + 1 - P] : 0.0f;
-                const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-                w4[h] = *reinterpret_cast<const uint32_t *>(&v);
-            }
-            reinterpret_cast<uint4 *>(x)[g8] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        }
-        __syncwarp();
-        for (int q = lane; q < n; q += 32) {
-            const int j = row[q];
-            if ((unsigned)j < (unsigned)n) x[j] = __float2bfloat16_rn((float)q / denom);
-        }
-        __syncwarp();
-    }
-}
-
-// Network input of job-order rows, one warp per row: x[j] = position of job j
-// / (n - 1) for j < n, 0 for n <= j < P, then the instance features; BF16.
-__global__ void k_sur_features(const int16_t *rows, int64_t nrows, int n, int ld, int P, const float *inst_feat,
-                               int nfeat, __nv_bfloat16 *X, int ldx)
-{
-    const int lane = threadIdx.x & 31;
-    const float denom = (float)(n > 1 ? n - 1 : 1);
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrows;
-         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        __nv_bfloat16 *x = X + r * ldx;
-        for (int j = lane; j < ldx; j += 32) x[j] = __float2bfloat16_rn(0.0f);
-        __syncwarp();
-        const int16_t *row = rows + r * ld;
-        for (int k = lane; k < n; k += 32) {
-            const int j = row[k];
-            if ((unsigned)j < (unsigned)n) x[j] = __float2bfloat16_rn((float)k / denom);
-        }
-        for (int f = lane; f < nfeat; f += 32) x[P + f] = __float2bfloat16_rn(inst_feat[f]);
-        __syncwarp();
+        warp_write_features(cand + (int64_t)tj * ld, n, P, inst_feat, nfeat, X + (int64_t)tj * ldx, ldx);
     }
 }
 
@@ -211,19 +198,25 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
     decode_tmem_end(Ls);
 }
 
+// The surrogate's device counters: ctr[0] ring pairs appended, ctr[1]
+// training batches drawn, ctr[2] the ring count when the current generation
+// began (set by k_sur_snapshot).  A training round runs beside the current
+// generation's selection, which appends to the ring; it reads only the
+// snapshot and the pairs before it, which the selection does not touch.
+
 // Standardisation of the training targets: mean and 1 / std (std at least 1)
-// of the makespans of the `recent` latest ring pairs (the last generation's
-// exact decodes), into norm[0..1].  The screen needs only the ranking of a
+// of the makespans of the `recent` newest ring pairs before the current
+// generation (the last generation's exact decodes), into norm[0..1].  The screen needs only the ranking of a
 // cell's candidates, whose makespans differ by a few tenths of a percent
 // late in a run: standardised targets keep those differences at the scale
 // the network learns.  One block.
 __global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm)
 {
     __shared__ double part[2][32];
-    const long long cnt = ctr[0] < ring_cap ? ctr[0] : ring_cap;
+    const long long cnt = ctr[2] < ring_cap ? ctr[2] : ring_cap;
     const int m = (int)(cnt < recent ? cnt : recent);
     double s = 0.0, q = 0.0;
-    const long long last = (ctr[0] - 1) % ring_cap;   // slot of the latest pair (m > 0 only)
+    const long long last = (ctr[2] - 1) % ring_cap;   // slot of the newest pair (m > 0 only)
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const long long slot = last - i;
         const double v = (double)ring_ms[slot >= 0 ? slot : slot + ring_cap];
@@ -253,30 +246,39 @@ __global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const lon
     }
 }
 
-// Training batch: B rows drawn uniformly (Philox, purpose kPurposeTrainSample,
-// generation field = batches drawn before, ctr[1]) from the first valid =
-// min(ctr[0], ring_cap) ring slots; target = (makespan - norm[0]) * norm[1].
-__global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap,
-                             const long long *ctr, int ld, uint64_t seed, int B, int16_t *out_rows, float *targets,
-                             const float *norm)
+// Training batch: B pairs drawn uniformly (Philox, purpose
+// kPurposeTrainSample, generation field = batches drawn before, ctr[1]) from
+// the V = min(ctr[2], ring_cap - recent) newest pairs before the current
+// generation (pair i = the i-th newest, slot (ctr[2] - 1 - i) mod ring_cap;
+// the current generation writes the `recent` slots after them), written as
+// network inputs X (one warp per sample); target = (makespan - norm[0]) *
+// norm[1].
+__global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
+                             const long long *ctr, int ld, uint64_t seed, int B, float *targets, const float *norm,
+                             int n, int P, const float *inst_feat, int nfeat, __nv_bfloat16 *X, int ldx)
 {
-    const long long valid = ctr[0] < ring_cap ? ctr[0] : ring_cap;
+    const long long room = ring_cap - recent;
+    const long long valid = ctr[2] < room ? ctr[2] : room;
+    const long long newest = (ctr[2] - 1) % ring_cap;
     const uint32_t draw_gen = (uint32_t)ctr[1];
     const int lane = threadIdx.x & 31;
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B; b += (gridDim.x * blockDim.x) >> 5) {
         const U4 d = draw_block(seed, kPurposeTrainSample, 0u, draw_gen, (uint32_t)b, 0u);
-        const long long idx = (long long)(((unsigned long long)d.x * (unsigned long long)valid) >> 32);
-        const int4 *s4 = reinterpret_cast<const int4 *>(ring_rows + idx * ld);
-        int4 *d4 = reinterpret_cast<int4 *>(out_rows + (int64_t)b * ld);
-        for (int k = lane; k < (ld >> 3); k += 32) d4[k] = s4[k];
-        if (lane == 0) targets[b] = ((float)ring_ms[idx] - norm[0]) * norm[1];
+        const long long i = (long long)(((unsigned long long)d.x * (unsigned long long)valid) >> 32);
+        const long long slot = newest - i >= 0 ? newest - i : newest - i + ring_cap;
+        warp_write_features(ring_rows + slot * ld, n, P, inst_feat, nfeat, X + (int64_t)b * ldx, ldx);
+        if (lane == 0) targets[b] = ((float)ring_ms[slot] - norm[0]) * norm[1];
     }
 }
 
-// ctr[which] += add (one thread): the surrogate's device counters.
+// ctr[which] += add (one thread): the surrogate's device counters; with
+// add < 0, the snapshot ctr[2] = ctr[0] instead.
 __global__ void k_sur_tick(long long *ctr, int which, long long add)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) ctr[which] += add;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (add < 0) ctr[2] = ctr[0];
+        else ctr[which] += add;
+    }
 }
 
 __global__ void k_fill_f32(float *p, int64_t n, float v)
@@ -296,18 +298,6 @@ int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const Is
     k_sur_candidates<<<(warps * 32 + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand, P,
                                                                 inst_feat, nfeat, static_cast<__nv_bfloat16 *>(X),
                                                                 ldx);
-    FFS_CUDA_TRY(cudaGetLastError());
-    return FFS_OK;
-}
-
-int launch_sur_features(const int16_t *rows, int64_t nrows, int n, int ld, int P, const float *inst_feat, int nfeat,
-                        void *X, int ldx, cudaStream_t st)
-{
-    if (nrows <= 0) return FFS_OK;
-    int64_t blocks = (nrows * 32 + 255) / 256;
-    if (blocks > 8192) blocks = 8192;
-    k_sur_features<<<(int)blocks, 256, 0, st>>>(rows, nrows, n, ld, P, inst_feat, nfeat,
-                                                static_cast<__nv_bfloat16 *>(X), ldx);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -338,12 +328,13 @@ int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long 
     return FFS_OK;
 }
 
-int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, const long long *ctr,
-                      int ld, uint64_t seed, int B, int16_t *out_rows, float *targets, const float *norm,
-                      cudaStream_t st)
+int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
+                      const long long *ctr, int ld, uint64_t seed, int B, float *targets, const float *norm, int n,
+                      int P, const float *inst_feat, int nfeat, void *X, int ldx, cudaStream_t st)
 {
-    k_sur_gather<<<(B * 32 + 255) / 256, 256, 0, st>>>(ring_rows, ring_ms, ring_cap, ctr, ld, seed, B, out_rows,
-                                                       targets, norm);
+    k_sur_gather<<<(B * 32 + 255) / 256, 256, 0, st>>>(ring_rows, ring_ms, ring_cap, recent, ctr, ld, seed, B, targets,
+                                                       norm, n, P, inst_feat, nfeat, static_cast<__nv_bfloat16 *>(X),
+                                                       ldx);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
