@@ -111,6 +111,30 @@ def _load():
         lib.orc_eval_population_assign.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.c_void_p,
                                                    _i16p, ctypes.c_int64, ctypes.c_int64, _i64p]
         lib.orc_eval_population_assign.restype = None
+        lib.orc_assign_init_row.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32,
+                                            ctypes.c_int32, _i32p, _i16p]
+        lib.orc_assign_init_row.restype = None
+        lib.orc_assign_init_pair.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, _i32p, _i16p, _i16p]
+        lib.orc_assign_init_pair.restype = None
+        lib.orc_assign_complement.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        lib.orc_assign_complement.restype = ctypes.c_int32
+        lib.orc_two_point.argtypes = [ctypes.c_int32, _i16p, _i16p, ctypes.c_int32, ctypes.c_int32, _i16p]
+        lib.orc_two_point.restype = None
+        lib.orc_assign_reassign.argtypes = [_i16p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]
+        lib.orc_assign_reassign.restype = None
+        lib.orc_assign_cellular_child.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32,
+                                                  ctypes.c_int32, ctypes.c_int32, _u32p, ctypes.POINTER(_Params),
+                                                  _i16p, ctypes.c_int64, _i64p, _i16p]
+        lib.orc_assign_cellular_child.restype = None
+        agen = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, ctypes.POINTER(_Params), ctypes.c_uint32,
+                ctypes.c_uint32]
+        lib.orc_assign_cellular_generation.argtypes = agen + [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _i16p,
+                                                              _i64p, _i16p, _i64p]
+        lib.orc_assign_cellular_generation.restype = ctypes.c_int64
+        lib.orc_assign_pseudo_generation.argtypes = agen + [ctypes.c_int32, ctypes.c_int64, _i16p, _i64p, _i16p,
+                                                            _i64p]
+        lib.orc_assign_pseudo_generation.restype = ctypes.c_int64
         lib.orc_eval_population.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                             _i16p, ctypes.c_int64, ctypes.c_int64, _i64p]
         lib.orc_eval_population.restype = None
@@ -611,3 +635,83 @@ class IslandGA:
 
     def best(self) -> int:
         return int(min(m.min() for m in self.mss))
+
+
+# ---------------------------------------------------------------------------
+# GA on the paper's genotype (machine-assignment strings of L = n * S genes)
+# ---------------------------------------------------------------------------
+def assign_init_row(seed: int, island: int, cell: int, n: int, S: int, M) -> np.ndarray:
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    out = np.zeros(n * S, dtype=np.int16)
+    _load().orc_assign_init_row(seed, island, cell, n, S, _ptr(M, ctypes.c_int32), _ptr(out, ctypes.c_int16))
+    return out
+
+
+def assign_init_pair(seed: int, island: int, k: int, n: int, S: int, M):
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    a, b = np.zeros(n * S, dtype=np.int16), np.zeros(n * S, dtype=np.int16)
+    _load().orc_assign_init_pair(seed, island, k, n, S, _ptr(M, ctypes.c_int32), _ptr(a, ctypes.c_int16),
+                                 _ptr(b, ctypes.c_int16))
+    return a, b
+
+
+def assign_complement(m: int, M_s: int) -> int:
+    return int(_load().orc_assign_complement(m, M_s))
+
+
+def two_point(p1, p2, l: int, r: int) -> np.ndarray:
+    p1 = np.ascontiguousarray(p1, dtype=np.int16)
+    p2 = np.ascontiguousarray(p2, dtype=np.int16)
+    out = np.zeros_like(p1)
+    _load().orc_two_point(len(p1), _ptr(p1, ctypes.c_int16), _ptr(p2, ctypes.c_int16), l, r, _ptr(out, ctypes.c_int16))
+    return out
+
+
+def assign_reassign(genes, i: int, M_s: int, x: int) -> np.ndarray:
+    g = np.array(genes, dtype=np.int16)
+    _load().orc_assign_reassign(_ptr(g, ctypes.c_int16), i, M_s, x)
+    return g
+
+
+def assign_cellular_child(inst: AssignInstance, prm: Params, rows: int, cols: int, c: int, x, pop: np.ndarray,
+                          obj: np.ndarray) -> np.ndarray:
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    obj = np.ascontiguousarray(obj, dtype=np.int64)
+    xs = np.ascontiguousarray(x, dtype=np.uint32)
+    child = np.zeros(inst.n * inst.S, dtype=np.int16)
+    cp = prm._c(inst)
+    _load().orc_assign_cellular_child(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32), rows, cols, c,
+                                      _ptr(xs, ctypes.c_uint32), ctypes.byref(cp), _ptr(pop, ctypes.c_int16),
+                                      pop.shape[1], _ptr(obj, ctypes.c_int64), _ptr(child, ctypes.c_int16))
+    return child
+
+
+def assign_cellular_generation(inst: AssignInstance, prm: Params, island: int, generation: int, rows: int,
+                               cols: int, pop: np.ndarray, obj: np.ndarray):
+    """One cellular generation of assignment strings; returns (pop, objectives, #evaluated)."""
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    obj = np.ascontiguousarray(obj, dtype=np.int64)
+    out, out_obj = np.zeros_like(pop), np.zeros_like(obj)
+    cp = prm._c(inst)
+    k = lib.orc_assign_cellular_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
+                                           _ptr(inst.p_u, ctypes.c_int32), ctypes.byref(cp), island, generation, rows,
+                                           cols, pop.shape[1], _ptr(pop, ctypes.c_int16), _ptr(obj, ctypes.c_int64),
+                                           _ptr(out, ctypes.c_int16), _ptr(out_obj, ctypes.c_int64))
+    return out, out_obj, int(k)
+
+
+def assign_pseudo_generation(inst: AssignInstance, prm: Params, island: int, generation: int, pop: np.ndarray,
+                             obj: np.ndarray):
+    """One pseudo generation of assignment strings; returns (pop, objectives, #evaluated)."""
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    obj = np.ascontiguousarray(obj, dtype=np.int64)
+    out, out_obj = np.zeros_like(pop), np.zeros_like(obj)
+    cp = prm._c(inst)
+    k = lib.orc_assign_pseudo_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
+                                         _ptr(inst.p_u, ctypes.c_int32), ctypes.byref(cp), island, generation,
+                                         pop.shape[0], pop.shape[1], _ptr(pop, ctypes.c_int16),
+                                         _ptr(obj, ctypes.c_int64), _ptr(out, ctypes.c_int16),
+                                         _ptr(out_obj, ctypes.c_int64))
+    return out, out_obj, int(k)

@@ -731,3 +731,172 @@ int64_t orc_screened_cellular_generation(int32_t n, int32_t S, const int32_t *M,
     free(best);
     return cells;
 }
+
+/* ------------------------------------------------------------------ */
+/* GA on the paper's own genotype (Section 4.1, genotype level): a row of */
+/* L = n * S genes, gene j * S + s = the machine of job j at stage s.     */
+/* The paper names no operators for it; the readings below are this      */
+/* library's (random initial machines, complementary pairs by reflection, */
+/* two-point crossover, one-gene machine reassignment), with the draws    */
+/* and the selection / replacement rules of the job-order GA above.       */
+/* ------------------------------------------------------------------ */
+
+/* Initial row: gene i = uniform(M_{i mod S}) with draw i of the stream
+ * (seed, purpose 1, island, generation 0, cell). */
+void orc_assign_init_row(uint64_t seed, uint32_t island, uint32_t cell, int32_t n, int32_t S, const int32_t *M,
+                         int16_t *genes)
+{
+    for (int32_t i = 0; i < n * S; ++i)
+        genes[i] = (int16_t)orc_uniform(orc_draw(seed, ORC_PURPOSE_INIT, island, 0u, cell, (uint32_t)i),
+                                        (uint32_t)M[i % S]);
+}
+
+/* Complement of a machine index at stage s: M_s - 1 - m.  When M_s is a
+ * power of two, 2^b, this is the bitwise complement of m's b-bit binary
+ * code (the binary lower layer of the genotype); otherwise it is the same
+ * reflection, which keeps the gene a valid machine. */
+int32_t orc_assign_complement(int32_t m, int32_t M_s) { return M_s - 1 - m; }
+
+/* Complementary pair k of a pseudo island: rows 2k, 2k + 1 = a and its
+ * complement, gene by gene; a is drawn with cell 2k. */
+void orc_assign_init_pair(uint64_t seed, uint32_t island, int32_t k, int32_t n, int32_t S, const int32_t *M,
+                          int16_t *a, int16_t *b)
+{
+    orc_assign_init_row(seed, island, (uint32_t)(2 * k), n, S, M, a);
+    for (int32_t i = 0; i < n * S; ++i) b[i] = (int16_t)orc_assign_complement(a[i], M[i % S]);
+}
+
+/* Two-point crossover of strings of L genes: the child takes p1's genes at
+ * positions l..r and p2's everywhere else. */
+void orc_two_point(int32_t L, const int16_t *p1, const int16_t *p2, int32_t l, int32_t r, int16_t *child)
+{
+    for (int32_t i = 0; i < L; ++i) child[i] = (i >= l && i <= r) ? p1[i] : p2[i];
+}
+
+/* Machine reassignment of gene i (stage s = i mod S): with u = uniform(x,
+ * M_s - 1), the gene becomes u if u < old, else u + 1 -- a machine other
+ * than the old one, uniformly; no change when M_s = 1. */
+void orc_assign_reassign(int16_t *genes, int32_t i, int32_t M_s, uint32_t x)
+{
+    if (M_s < 2) return;
+    const int32_t old = genes[i];
+    const int32_t u = (int32_t)orc_uniform(x, (uint32_t)(M_s - 1));
+    genes[i] = (int16_t)(u < old ? u : u + 1);
+}
+
+/* One child of cell c of a cellular island of assignment strings, given its
+ * ten draws (purpose 2): the two binary tournaments of orc_cellular_child
+ * (draws 0-3), two-point crossover with probability pc (draw 4; cut points
+ * uniform in [0, L) from draws 5 and 6, l = min, r = max), else a copy of
+ * the first parent; with probability pm (draw 7) the reassignment of gene
+ * uniform(L) (draw 8) with draw 9. */
+void orc_assign_cellular_child(int32_t n, int32_t S, const int32_t *M, int32_t rows, int32_t cols, int32_t c,
+                               const uint32_t x[10], const orc_params *prm, const int16_t *pop, int64_t ld,
+                               const int64_t *obj, int16_t *child)
+{
+    const int32_t L = n * S;
+    int32_t nb[5];
+    orc_neighbours(rows, cols, c, nb);
+    int32_t a1 = nb[orc_uniform(x[0], 5u)], b1 = nb[orc_uniform(x[1], 5u)];
+    int32_t par1 = (obj[b1] < obj[a1]) ? b1 : a1;
+    int32_t a2 = nb[orc_uniform(x[2], 5u)], b2 = nb[orc_uniform(x[3], 5u)];
+    int32_t par2 = (obj[b2] < obj[a2]) ? b2 : a2;
+    if (orc_bernoulli(x[4], prm->cell_pc)) {
+        int32_t u = (int32_t)orc_uniform(x[5], (uint32_t)L);
+        int32_t v = (int32_t)orc_uniform(x[6], (uint32_t)L);
+        orc_two_point(L, pop + (int64_t)par1 * ld, pop + (int64_t)par2 * ld, u < v ? u : v, u < v ? v : u, child);
+    } else {
+        memcpy(child, pop + (int64_t)par1 * ld, (size_t)L * sizeof(int16_t));
+    }
+    if (orc_bernoulli(x[7], prm->cell_pm)) {
+        const int32_t i = (int32_t)orc_uniform(x[8], (uint32_t)L);
+        orc_assign_reassign(child, i, M[i % S], x[9]);
+    }
+}
+
+/* One synchronous cellular generation of assignment strings: every cell's
+ * child (orc_assign_cellular_child) is evaluated (orc_decode_assign) and
+ * replaces the cell iff better (flag: not worse).  Returns the cells done. */
+int64_t orc_assign_cellular_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p_u,
+                                       const orc_params *prm, uint32_t island, uint32_t generation, int32_t rows,
+                                       int32_t cols, int64_t ld, const int16_t *pop_in, const int64_t *obj_in,
+                                       int16_t *pop_out, int64_t *obj_out)
+{
+    const int32_t L = n * S, cells = rows * cols;
+    int16_t *child = (int16_t *)malloc((size_t)L * sizeof(int16_t));
+    for (int32_t c = 0; c < cells; ++c) {
+        uint32_t x[10];
+        for (uint32_t d = 0; d < 10u; ++d)
+            x[d] = orc_draw(prm->seed, ORC_PURPOSE_CELLULAR, island, generation, (uint32_t)c, d);
+        orc_assign_cellular_child(n, S, M, rows, cols, c, x, prm, pop_in, ld, obj_in, child);
+        const int64_t mc = orc_decode_assign(n, S, M, p_u, prm->obj, child, NULL);
+        const int better = prm->cell_replace_le ? (mc <= obj_in[c]) : (mc < obj_in[c]);
+        int16_t *dst = pop_out + (int64_t)c * ld;
+        if (better) {
+            memcpy(dst, child, (size_t)L * sizeof(int16_t));
+            obj_out[c] = mc;
+        } else {
+            memcpy(dst, pop_in + (int64_t)c * ld, (size_t)L * sizeof(int16_t));
+            obj_out[c] = obj_in[c];
+        }
+    }
+    free(child);
+    return cells;
+}
+
+/* One pseudo generation of assignment strings (Section 4.1): pair k =
+ * rows (2k, 2k+1) = (a, b) crosses with probability pseudo_pc (draw 0,
+ * purpose 3; cut points uniform in [0, L) from draws 1-2): c1 = two-point
+ * (a, b), c2 = two-point (b, a); the pair keeps the two best of (c1, c2, a,
+ * b) ranked by (objective, that order), best first, or with pseudo_always
+ * the children.  Pairs that do not cross are copied.  Returns the children
+ * evaluated. */
+int64_t orc_assign_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p_u,
+                                     const orc_params *prm, uint32_t island, uint32_t generation, int32_t size,
+                                     int64_t ld, const int16_t *pop_in, const int64_t *obj_in, int16_t *pop_out,
+                                     int64_t *obj_out)
+{
+    const int32_t L = n * S;
+    int16_t *c1 = (int16_t *)malloc((size_t)L * sizeof(int16_t));
+    int16_t *c2 = (int16_t *)malloc((size_t)L * sizeof(int16_t));
+    int64_t decoded = 0;
+    for (int32_t k = 0; k < size / 2; ++k) {
+        const int16_t *a = pop_in + (int64_t)(2 * k) * ld, *b = pop_in + (int64_t)(2 * k + 1) * ld;
+        int16_t *oa = pop_out + (int64_t)(2 * k) * ld, *ob = pop_out + (int64_t)(2 * k + 1) * ld;
+        const uint32_t x0 = orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation, (uint32_t)k, 0u);
+        if (!orc_bernoulli(x0, prm->pseudo_pc)) {
+            memcpy(oa, a, (size_t)L * sizeof(int16_t));
+            memcpy(ob, b, (size_t)L * sizeof(int16_t));
+            obj_out[2 * k] = obj_in[2 * k];
+            obj_out[2 * k + 1] = obj_in[2 * k + 1];
+            continue;
+        }
+        const int32_t u = (int32_t)orc_uniform(orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation,
+                                                        (uint32_t)k, 1u), (uint32_t)L);
+        const int32_t v = (int32_t)orc_uniform(orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation,
+                                                        (uint32_t)k, 2u), (uint32_t)L);
+        const int32_t l = u < v ? u : v, r = u < v ? v : u;
+        orc_two_point(L, a, b, l, r, c1);
+        orc_two_point(L, b, a, l, r, c2);
+        const int64_t m1 = orc_decode_assign(n, S, M, p_u, prm->obj, c1, NULL);
+        const int64_t m2 = orc_decode_assign(n, S, M, p_u, prm->obj, c2, NULL);
+        decoded += 2;
+        if (prm->pseudo_always) {
+            memcpy(oa, c1, (size_t)L * sizeof(int16_t));
+            memcpy(ob, c2, (size_t)L * sizeof(int16_t));
+            obj_out[2 * k] = m1;
+            obj_out[2 * k + 1] = m2;
+            continue;
+        }
+        const int16_t *fam[4] = { c1, c2, a, b };
+        int64_t fobj[4] = { m1, m2, obj_in[2 * k], obj_in[2 * k + 1] };
+        int32_t pick[2];
+        orc_family_best2(fobj, pick);
+        memcpy(oa, fam[pick[0]], (size_t)L * sizeof(int16_t));
+        memcpy(ob, fam[pick[1]], (size_t)L * sizeof(int16_t));
+        obj_out[2 * k] = fobj[pick[0]];
+        obj_out[2 * k + 1] = fobj[pick[1]];
+    }
+    free(c1); free(c2);
+    return decoded;
+}
