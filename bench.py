@@ -415,12 +415,6 @@ def run_ours(args):
         "clocks": clock_info,
     }
     if ws == 1 and not args.no_subrecords:
-        # the other measured configuration: 256 uneven instances in one
-        # persistent launch per generation (its own timed region and clocks)
-        sub = batch_measure("batch_256", steps=20, warmup=3, autotune=True, shape=None)
-        sub["workload"] = ("batch_256: 256 instances, n ~ U[20,500], S ~ U[5,20], M_s ~ U[2,10], "
-                           "p ~ U[1,99], one 32x32 cellular island each")
-        line["batch_256"] = sub
         # the surrogate comparison (config-5 protocol, GA seeds 7..11)
         sur = surrogate_measure(list(range(7, 12)), plain_gens=1000, screened_gens=500)
         sur.pop("median_curves", None)
@@ -692,11 +686,64 @@ def surrogate_measure(seeds, plain_gens: int = 1000, screened_gens: int = 500) -
 
 
 def run_surrogate(args):
-    """Config-5 protocol: plain vs surrogate-screened GA over GA seeds 7..11;
-    prints one JSON line."""
+    """Plain vs surrogate-screened GA over GA seeds 7..11 (1000 plain, 500
+    screened generations each; --seeds, --plain-gens and --screened-gens give
+    shorter runs, e.g. for a profiler); prints one JSON line."""
     import torch
     torch.cuda.set_device(0)
-    line = surrogate_measure(list(range(7, 12)), plain_gens=1000, screened_gens=500)
+    seeds = [int(x) for x in args.seeds.split(",")] if args.seeds else list(range(7, 12))
+    line = surrogate_measure(seeds, plain_gens=args.plain_gens or 1000, screened_gens=args.screened_gens or 500)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mlp_forward(args):
+    """The surrogate's scoring forward alone: the 540-512-256-1 BF16 network
+    on 32768 rows (8 candidates for each cell of a 64 x 64 torus), one
+    ffs_mlp_forward per step (two tcgen05 GEMM launches, the second with the
+    output layer in its epilogue), L2 flushed between steps; one JSON line.
+    Algorithmic FLOPs per row: 2 (540 * 512 + 512 * 256 + 256)."""
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+
+    torch.cuda.set_device(0)
+    B, in_dim, h1, h2 = 32768, 540, 512, 256
+    net = ffs.MLP(in_dim, h1, h2, B)
+    net.init(3)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    X = torch.zeros((B, net.width), dtype=torch.bfloat16, device="cuda")
+    X[:, :in_dim] = torch.rand((B, in_dim), generator=g, device="cuda").to(torch.bfloat16)
+    y = torch.empty(B, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        ffs.ffs_mlp_forward(net, X, net.width, B, y)
+    ffs.ffs_mlp_check(net)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ffs.ffs_mlp_forward(net, X, net.width, B, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ffs.ffs_mlp_check(net)
+    ms = statistics.median(ts)
+    flops = 2.0 * B * (in_dim * h1 + h1 * h2 + h2)
+    peaks, peak_kind = _peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    tf = flops / (ms / 1000.0) / 1e12
+    line = {"metric": "surrogate scoring forward rows/sec", "workload": "surrogate_forward_32768",
+            "value": B / (ms / 1000.0), "unit": "rows/s", "ms_per_step": ms, "steps": args.steps,
+            "rows": B, "layers": [in_dim, h1, h2, 1], "dtype": "bf16 (fp32 accumulate)",
+            "config": {"l2": "flushed between steps (256 MB write)"},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak, "kernel": "k_gemm_bf16 (both layers)",
+                         "peak_basis": f"cuBLAS bf16 burst ({peak_kind})"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -903,11 +950,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="scale_500x20")
     ap.add_argument("--no-subrecords", action="store_true",
-                    help="default workload: skip the batch_256 and surrogate sub-records")
+                    help="default workload: skip the surrogate sub-record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--int-rates", action="store_true",
                     help="also measure per-pipe integer issue rates with the probe kernels")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--seeds", default=None, help="surrogate_100x10: comma-separated GA seeds (default 7..11)")
+    ap.add_argument("--plain-gens", type=int, default=0, help="surrogate_100x10: plain generations (default 1000)")
+    ap.add_argument("--screened-gens", type=int, default=0,
+                    help="surrogate_100x10: screened generations (default 500)")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape THREADS,CHUNK,VARIANT instead of the autotuner (profiling)")
     args = ap.parse_args()
@@ -921,6 +972,8 @@ def main():
         return run_batch(args)
     if args.workload == "surrogate_100x10":
         return run_surrogate(args)
+    if args.workload == "surrogate_forward_32768":
+        return run_mlp_forward(args)
     if args.workload == "decode_500x20":
         return run_decode(args)
     if args.workload == "assign_500x20":

@@ -115,6 +115,7 @@ int ffs_assign_instance_destroy(ffs_assign_instance *inst);
 int ffs_assign_eval(const ffs_assign_instance *inst, const int16_t *pop, int64_t N, int32_t ld, int32_t *objective,
                     ffs_stream stream);
 
+
 /* ------------------------------------------------------------------------
  * Batched makespan evaluation (the decoder).  Each row is decoded by
  * stage-wise list scheduling: stage 0 takes the jobs in row order; every
@@ -283,6 +284,44 @@ int ffs_pseudo_step(const ffs_instance *inst, const ffs_params *prm, uint32_t is
 int ffs_pseudo_step_noalloc(const ffs_instance *inst, const ffs_params *prm, uint32_t island,
                             uint32_t generation, int32_t size, int32_t ld, const int16_t *pop_in,
                             const int32_t *ms_in, int16_t *pop_out, int32_t *ms_out, ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * The GA on the paper's genotype (Section 4.1, genotype level).  The paper
+ * names no operators for the machine-assignment string; the library's
+ * (L = n * S genes per row):
+ *   ffs_assign_population_init: kind 0, row r: gene i = uniform(M_{i mod S})
+ *     with draw i of (seed, purpose 1, island, generation 0, cell r); kind 1
+ *     (N even): rows 2k, 2k + 1 = a (drawn with cell 2k) and its
+ *     complement, gene i -> M_s - 1 - a_i (the bitwise complement of the
+ *     binary lower layer when M_s is a power of two; the same reflection
+ *     keeps the gene a valid machine otherwise).  Padding genes are 0.
+ *   ffs_assign_cellular_step: one synchronous generation of a rows x cols
+ *     torus of assignment strings, the tournaments, draws and replacement
+ *     of ffs_cellular_step (purpose 2) with two-point crossover (draw 4;
+ *     cut points uniform in [0, L) from draws 5-6, l = min, r = max; the
+ *     child takes the first winner's genes l..r and the second's elsewhere,
+ *     or is a copy of the first winner) and machine reassignment (draw 7;
+ *     gene uniform(L) from draw 8 moves to machine u or u + 1, u =
+ *     uniform(M_s - 1) from draw 9, whichever is not its old machine).
+ *   ffs_assign_pseudo_step: pair k crosses with probability pseudo_pc (draw
+ *     0, purpose 3; cut points from draws 1-2): c1 = two-point(a, b), c2 =
+ *     two-point(b, a); replacement as in ffs_pseudo_step.
+ * Objectives (obj_in / obj_out, device int32) are those of ffs_assign_eval.
+ * scratch: device memory of ffs_assign_step_scratch_bytes(N, ld) bytes
+ * (N = the island's rows), 256-byte aligned, caller-owned; its contents on
+ * entry do not matter.  Asynchronous; calls on one instance must not
+ * overlap on the GPU (they share the evaluator's scratch). */
+int ffs_assign_population_init(const ffs_assign_instance *inst, uint64_t seed, uint32_t island, int32_t kind,
+                               int64_t N, int32_t ld, int16_t *pop, ffs_stream stream);
+int64_t ffs_assign_step_scratch_bytes(int64_t N, int32_t ld);
+int ffs_assign_cellular_step(const ffs_assign_instance *inst, const ffs_params *prm, uint32_t island,
+                             uint32_t generation, int32_t rows, int32_t cols, int32_t ld, const int16_t *pop_in,
+                             const int32_t *obj_in, int16_t *pop_out, int32_t *obj_out, void *scratch,
+                             ffs_stream stream);
+int ffs_assign_pseudo_step(const ffs_assign_instance *inst, const ffs_params *prm, uint32_t island,
+                           uint32_t generation, int32_t size, int32_t ld, const int16_t *pop_in,
+                           const int32_t *obj_in, int16_t *pop_out, int32_t *obj_out, void *scratch,
+                           ffs_stream stream);
 
 /* ------------------------------------------------------------------------
  * Islands: the dual-island GA state on the device (Section 4.1, Fig. 2).

@@ -110,6 +110,12 @@ _SIGS = [
     ("ffs_islands_autotune", _i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
     ("ffs_islands_dry_run", _i32, [_vp, _i32, _vp]),
     ("ffs_islands_params", _i32, [_vp, ctypes.POINTER(ffs_params)]),
+    ("ffs_assign_population_init", _i32, [_vp, _u64, _u32, _i32, _i64, _i32, _vp, _vp]),
+    ("ffs_assign_step_scratch_bytes", _i64, [_i64, _i32]),
+    ("ffs_assign_cellular_step", _i32, [_vp, ctypes.POINTER(ffs_params), _u32, _u32, _i32, _i32, _i32,
+                                        _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("ffs_assign_pseudo_step", _i32, [_vp, ctypes.POINTER(ffs_params), _u32, _u32, _i32, _i32,
+                                      _vp, _vp, _vp, _vp, _vp, _vp]),
     ("ffs_mlp_init", _i32, [_vp, _u64, _vp]),
     ("ffs_mlp_adam_steps", _i32, [_vp, _vp]),
     ("ffs_mlp_state_bytes", _i64, [_vp]),
@@ -275,6 +281,28 @@ class AssignInstance:
 
 def ffs_assign_eval(inst: AssignInstance, pop, N: int, ld: int, objective, stream=None):
     _check(load().ffs_assign_eval(inst.handle, _ptr(pop), N, ld, _ptr(objective), _stream(stream)))
+
+
+def ffs_assign_population_init(inst: AssignInstance, seed, island, kind, N, ld, pop, stream=None):
+    _check(load().ffs_assign_population_init(inst.handle, seed, island, kind, N, ld, _ptr(pop), _stream(stream)))
+
+
+def ffs_assign_step_scratch_bytes(N: int, ld: int) -> int:
+    return int(load().ffs_assign_step_scratch_bytes(N, ld))
+
+
+def ffs_assign_cellular_step(inst: AssignInstance, prm: ffs_params, island, generation, rows, cols, ld, pop_in,
+                             obj_in, pop_out, obj_out, scratch, stream=None):
+    _check(load().ffs_assign_cellular_step(inst.handle, ctypes.byref(prm), island, generation, rows, cols, ld,
+                                           _ptr(pop_in), _ptr(obj_in), _ptr(pop_out), _ptr(obj_out), _ptr(scratch),
+                                           _stream(stream)))
+
+
+def ffs_assign_pseudo_step(inst: AssignInstance, prm: ffs_params, island, generation, size, ld, pop_in, obj_in,
+                           pop_out, obj_out, scratch, stream=None):
+    _check(load().ffs_assign_pseudo_step(inst.handle, ctypes.byref(prm), island, generation, size, ld,
+                                         _ptr(pop_in), _ptr(obj_in), _ptr(pop_out), _ptr(obj_out), _ptr(scratch),
+                                         _stream(stream)))
 
 
 def ffs_population_eval(inst: Instance, pop, N: int, ld: int, makespan, stream=None):

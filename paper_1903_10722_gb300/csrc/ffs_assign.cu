@@ -388,3 +388,298 @@ int ffs_assign_eval(const ffs_assign_instance *A, const int16_t *pop, int64_t N,
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// GA on the paper's genotype (Section 4.1, genotype level): rows of L = n S
+// machine genes.  The paper names no operators for it; this library reads
+// them as random initial machines, complementary pairs by reflection
+// (M_s - 1 - m: the binary layer's bitwise complement when M_s is a power of
+// two), two-point crossover (the segment [l, r] from the first parent, the
+// rest from the second) and one-gene machine reassignment, with the draws,
+// tournaments and replacement rules of the job-order GA.  A generation is a
+// breeding launch (children into caller scratch), the evaluator of
+// ffs_assign_eval on the children, and a replacement launch.
+// ---------------------------------------------------------------------------
+namespace fgpu {
+
+// Initial rows: kind 0, row r: gene i = uniform(M_{i mod S}) with draw i of
+// (seed, purpose 1, island, generation 0, cell r); kind 1, pair k = rows 2k,
+// 2k + 1: a drawn with cell 2k and its complement.  Thread = (row or pair,
+// block of 4 genes); padding genes are 0.
+__global__ void k_assign_init(uint64_t seed, uint32_t island, int kind, int64_t units, int n, int S,
+                              const int32_t *__restrict__ M, int ld, int16_t *pop)
+{
+    const int L = n * S, blocks = ld >> 2;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= units * blocks) return;
+    const int64_t u = t / blocks;
+    const int b = (int)(t - u * blocks);
+    const int64_t row = kind == 0 ? u : 2 * u;
+    const U4 d = draw_block(seed, kPurposeInit, island, 0u, (uint32_t)row, (uint32_t)b);
+    const uint32_t x[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int i = 4 * b + h;
+        int16_t a = 0, c = 0;
+        if (i < L) {
+            const int Ms = M[i % S];
+            a = (int16_t)uniform_below(x[h], (uint32_t)Ms);
+            c = (int16_t)(Ms - 1 - a);
+        }
+        pop[row * ld + i] = a;
+        if (kind == 1) pop[(row + 1) * ld + i] = c;
+    }
+}
+
+// Machine reassignment of gene value `old` at a stage of Ms machines: u =
+// uniform(x, Ms - 1), then u if u < old, else u + 1; unchanged when Ms < 2.
+__device__ __forceinline__ int16_t assign_reassign(int16_t old, int Ms, uint32_t x)
+{
+    if (Ms < 2) return old;
+    const int u = (int)uniform_below(x, (uint32_t)(Ms - 1));
+    return (int16_t)(u < old ? u : u + 1);
+}
+
+// Row dst = genes [l, r] of p1 and the others of p2 (l > r: p2 alone), with
+// gene `mi` (if >= 0) then reassigned with draw mx; the warp copies 8 genes
+// per lane per step (16-byte loads and stores).
+__device__ __forceinline__ void warp_two_point(const int16_t *p1, const int16_t *p2, int16_t *dst, int ld, int l,
+                                               int r, int mi, const int32_t *M, int S, uint32_t mx)
+{
+    const int lane = threadIdx.x & 31;
+    const int4 *a4 = reinterpret_cast<const int4 *>(p1), *b4 = reinterpret_cast<const int4 *>(p2);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+    for (int q = lane; q < (ld >> 3); q += 32) {
+        const int lo = 8 * q;
+        if (lo >= l && lo + 7 <= r && (mi < lo || mi > lo + 7)) {
+            d4[q] = a4[q];
+        } else if ((lo + 7 < l || lo > r) && (mi < lo || mi > lo + 7)) {
+            d4[q] = b4[q];
+        } else {
+            const int4 va = a4[q], vb = b4[q];
+            const int16_t *ga = reinterpret_cast<const int16_t *>(&va), *gb = reinterpret_cast<const int16_t *>(&vb);
+            int16_t out[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int i = lo + h;
+                int16_t gv = (i >= l && i <= r) ? ga[h] : gb[h];
+                if (i == mi) gv = assign_reassign(gv, M[i % S], mx);
+                out[h] = gv;
+            }
+            d4[q] = *reinterpret_cast<const int4 *>(out);
+        }
+    }
+}
+
+// Cellular children of a torus (one warp per cell): the tournaments and the
+// draws of the job-order cellular step (purpose 2): crossover with draw 4,
+// cut points uniform in [0, L) from draws 5-6, else a copy of the first
+// winner (l > r); mutation with draw 7 reassigns gene uniform(L) (draw 8)
+// with draw 9.
+__global__ void k_assign_breed_cellular(GaScalars g, uint32_t island, uint32_t gen, int rows, int cols, int n, int S,
+                                        const int32_t *__restrict__ M, int ld, const int16_t *__restrict__ pop,
+                                        const int32_t *__restrict__ obj, int16_t *children)
+{
+    const int cells = rows * cols, L = n * S;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= cells) return;
+    const U4 b0 = draw_block(g.seed, kPurposeCellular, island, gen, (uint32_t)c, 0u);
+    const U4 b1 = draw_block(g.seed, kPurposeCellular, island, gen, (uint32_t)c, 1u);
+    const U4 b2 = draw_block(g.seed, kPurposeCellular, island, gen, (uint32_t)c, 2u);
+    const int r0 = c / cols, q0 = c - r0 * cols;
+    const int up = ((r0 + rows - 1) % rows) * cols + q0, down = ((r0 + 1) % rows) * cols + q0;
+    const int west = r0 * cols + (q0 + cols - 1) % cols, east = r0 * cols + (q0 + 1) % cols;
+    auto slot = [&](uint32_t x) {
+        const uint32_t s = uniform_below(x, 5u);
+        return s == 0 ? c : s == 1 ? up : s == 2 ? down : s == 3 ? west : east;
+    };
+    int a = slot(b0.x), b = slot(b0.y);
+    const int par1 = (obj[b] < obj[a]) ? b : a;
+    a = slot(b0.z);
+    b = slot(b0.w);
+    const int par2 = (obj[b] < obj[a]) ? b : a;
+    int l = 1, r = 0;     // no crossover: everything from the first winner (passed as p2)
+    const int16_t *p1 = pop + (int64_t)par1 * ld, *p2 = p1;
+    if (fires(b1.x, g.cell_pc)) {
+        const int u = (int)uniform_below(b1.y, (uint32_t)L), v = (int)uniform_below(b1.z, (uint32_t)L);
+        l = min(u, v);
+        r = max(u, v);
+        p2 = pop + (int64_t)par2 * ld;
+    }
+    const int mi = fires(b1.w, g.cell_pm) ? (int)uniform_below(b2.x, (uint32_t)L) : -1;
+    warp_two_point(p1, p2, children + (int64_t)c * ld, ld, l, r, mi, M, S, b2.y);
+}
+
+// Pseudo children (one warp per pair k): crossover with draw 0 (purpose 3),
+// cut points from draws 1-2: c1 = two-point(a, b), c2 = two-point(b, a) into
+// children rows 2k, 2k + 1; pairs that do not cross copy a, b there.
+// cross[k] records the outcome.
+__global__ void k_assign_breed_pseudo(GaScalars g, uint32_t island, uint32_t gen, int pairs, int n, int S, int ld,
+                                      const int16_t *__restrict__ pop, int16_t *children, uint8_t *cross)
+{
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= pairs) return;
+    const int L = n * S;
+    const U4 d = draw_block(g.seed, kPurposePseudo, island, gen, (uint32_t)k, 0u);
+    const int16_t *A = pop + (int64_t)(2 * k) * ld, *B = A + ld;
+    int16_t *c1 = children + (int64_t)(2 * k) * ld, *c2 = c1 + ld;
+    const bool x = fires(d.x, g.pseudo_pc);
+    int l = 1, r = 0;
+    if (x) {
+        const int u = (int)uniform_below(d.y, (uint32_t)L), v = (int)uniform_below(d.z, (uint32_t)L);
+        l = min(u, v);
+        r = max(u, v);
+    }
+    // no crossover: l > r copies the second argument
+    warp_two_point(x ? A : B, x ? B : A, c1, ld, l, r, -1, nullptr, S, 0u);
+    warp_two_point(x ? B : A, x ? A : B, c2, ld, l, r, -1, nullptr, S, 0u);
+    if ((threadIdx.x & 31) == 0) cross[k] = x ? 1 : 0;
+}
+
+__device__ __forceinline__ void warp_copy_row(const int16_t *src, int16_t *dst, int ld)
+{
+    const int4 *s4 = reinterpret_cast<const int4 *>(src);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+    for (int q = (threadIdx.x & 31); q < (ld >> 3); q += 32) d4[q] = s4[q];
+}
+
+// Cellular replacement (one warp per cell): the child iff its objective is
+// lower (flag: not higher) than the cell's.
+__global__ void k_assign_replace_cellular(int cells, int ld, int replace_le, const int16_t *__restrict__ pop_in,
+                                          const int32_t *__restrict__ obj_in, const int16_t *__restrict__ children,
+                                          const int32_t *__restrict__ child_obj, int16_t *pop_out, int32_t *obj_out)
+{
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= cells) return;
+    const int32_t mc = child_obj[c], mo = obj_in[c];
+    const bool better = mc >= 0 && (replace_le ? mc <= mo : mc < mo);
+    warp_copy_row(better ? children + (int64_t)c * ld : pop_in + (int64_t)c * ld, pop_out + (int64_t)c * ld, ld);
+    if ((threadIdx.x & 31) == 0) obj_out[c] = better ? mc : mo;
+}
+
+// Pseudo replacement (one warp per pair): a pair that crossed keeps the two
+// best of (c1, c2, a, b) ranked by (objective, that order), best first -- or
+// the children with `always`; a pair that did not cross is copied.
+__global__ void k_assign_replace_pseudo(int pairs, int ld, int always, const int16_t *__restrict__ pop_in,
+                                        const int32_t *__restrict__ obj_in, const int16_t *__restrict__ children,
+                                        const int32_t *__restrict__ child_obj, const uint8_t *__restrict__ cross,
+                                        int16_t *pop_out, int32_t *obj_out)
+{
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= pairs) return;
+    const int16_t *fam[4] = {children + (int64_t)(2 * k) * ld, children + (int64_t)(2 * k + 1) * ld,
+                             pop_in + (int64_t)(2 * k) * ld, pop_in + (int64_t)(2 * k + 1) * ld};
+    const int32_t fo[4] = {child_obj[2 * k], child_obj[2 * k + 1], obj_in[2 * k], obj_in[2 * k + 1]};
+    int first = 2, second = 3;
+    if (cross[k]) {
+        if (always) {
+            first = 0;
+            second = 1;
+        } else {
+            first = 0;
+            for (int t = 1; t < 4; ++t)
+                if (fo[t] < fo[first]) first = t;
+            second = -1;
+            for (int t = 0; t < 4; ++t)
+                if (t != first && (second < 0 || fo[t] < fo[second])) second = t;
+        }
+    }
+    warp_copy_row(fam[first], pop_out + (int64_t)(2 * k) * ld, ld);
+    warp_copy_row(fam[second], pop_out + (int64_t)(2 * k + 1) * ld, ld);
+    if ((threadIdx.x & 31) == 0) {
+        obj_out[2 * k] = fo[first];
+        obj_out[2 * k + 1] = fo[second];
+    }
+}
+
+static int64_t a256(int64_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace fgpu
+
+extern "C" {
+
+int64_t ffs_assign_step_scratch_bytes(int64_t N, int32_t ld)
+{
+    if (N < 0 || ld < 0) return -1;
+    return a256(N * ld * 2) + a256(N * 4) + a256(N / 2 + 1);
+}
+
+int ffs_assign_population_init(const ffs_assign_instance *A, uint64_t seed, uint32_t island, int32_t kind, int64_t N,
+                               int32_t ld, int16_t *pop, ffs_stream stream)
+{
+    clear_error();
+    if (!A || !pop) return set_error(FFS_EINVAL, "NULL argument");
+    if (kind != 0 && kind != 1) return set_error(FFS_EINVAL, "kind %d", kind);
+    if (N < 0 || (kind == 1 && (N & 1))) return set_error(FFS_EINVAL, "N = %lld (even for pseudo pairs)", (long long)N);
+    int rc = validate_rows(pop, ld, A->n * A->S);
+    if (rc) return rc;
+    if (N == 0) return FFS_OK;
+    const int64_t units = kind == 0 ? N : N / 2;
+    const int64_t threads = units * (ld / 4);
+    k_assign_init<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(seed, island, kind, units, A->n,
+                                                                                        A->S, A->d_M, ld, pop);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int ffs_assign_cellular_step(const ffs_assign_instance *A, const ffs_params *prm, uint32_t island, uint32_t generation,
+                             int32_t rows, int32_t cols, int32_t ld, const int16_t *pop_in, const int32_t *obj_in,
+                             int16_t *pop_out, int32_t *obj_out, void *scratch, ffs_stream stream)
+{
+    clear_error();
+    if (!A || !prm || !pop_in || !obj_in || !pop_out || !obj_out || !scratch) return set_error(FFS_EINVAL, "NULL argument");
+    if (rows < 1 || cols < 1 || (int64_t)rows * cols > (1 << 26)) return set_error(FFS_EINVAL, "bad torus %dx%d", rows, cols);
+    if (pop_in == pop_out) return set_error(FFS_EINVAL, "pop_in and pop_out must differ");
+    if (((uintptr_t)scratch & 255u) != 0) return set_error(FFS_EINVAL, "scratch must be 256-byte aligned");
+    const int L = A->n * A->S;
+    int rc = validate_rows(pop_in, ld, L);
+    if (rc) return rc;
+    if ((rc = validate_rows(pop_out, ld, L))) return rc;
+    const int64_t cells = (int64_t)rows * cols;
+    char *sp = static_cast<char *>(scratch);
+    int16_t *children = reinterpret_cast<int16_t *>(sp);
+    int32_t *child_obj = reinterpret_cast<int32_t *>(sp + a256(cells * ld * 2));
+    cudaStream_t st = (cudaStream_t)stream;
+    const GaScalars g = scalars_of(prm);
+    const unsigned blocks = (unsigned)((cells * 32 + 255) / 256);
+    k_assign_breed_cellular<<<blocks, 256, 0, st>>>(g, island, generation, rows, cols, A->n, A->S, A->d_M, ld, pop_in,
+                                                    obj_in, children);
+    FFS_CUDA_TRY(cudaGetLastError());
+    if ((rc = ffs_assign_eval(A, children, cells, ld, child_obj, stream))) return rc;
+    k_assign_replace_cellular<<<blocks, 256, 0, st>>>((int)cells, ld, prm->cell_replace_le, pop_in, obj_in, children,
+                                                      child_obj, pop_out, obj_out);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int ffs_assign_pseudo_step(const ffs_assign_instance *A, const ffs_params *prm, uint32_t island, uint32_t generation,
+                           int32_t size, int32_t ld, const int16_t *pop_in, const int32_t *obj_in, int16_t *pop_out,
+                           int32_t *obj_out, void *scratch, ffs_stream stream)
+{
+    clear_error();
+    if (!A || !prm || !pop_in || !obj_in || !pop_out || !obj_out || !scratch) return set_error(FFS_EINVAL, "NULL argument");
+    if (size < 2 || (size & 1)) return set_error(FFS_EINVAL, "pseudo island size %d must be even and >= 2", size);
+    if (pop_in == pop_out) return set_error(FFS_EINVAL, "pop_in and pop_out must differ");
+    if (((uintptr_t)scratch & 255u) != 0) return set_error(FFS_EINVAL, "scratch must be 256-byte aligned");
+    const int L = A->n * A->S;
+    int rc = validate_rows(pop_in, ld, L);
+    if (rc) return rc;
+    if ((rc = validate_rows(pop_out, ld, L))) return rc;
+    char *sp = static_cast<char *>(scratch);
+    int16_t *children = reinterpret_cast<int16_t *>(sp);
+    int32_t *child_obj = reinterpret_cast<int32_t *>(sp + a256((int64_t)size * ld * 2));
+    uint8_t *cross = reinterpret_cast<uint8_t *>(sp + a256((int64_t)size * ld * 2) + a256((int64_t)size * 4));
+    cudaStream_t st = (cudaStream_t)stream;
+    const GaScalars g = scalars_of(prm);
+    const int pairs = size / 2;
+    const unsigned blocks = (unsigned)(((int64_t)pairs * 32 + 255) / 256);
+    k_assign_breed_pseudo<<<blocks, 256, 0, st>>>(g, island, generation, pairs, A->n, A->S, ld, pop_in, children, cross);
+    FFS_CUDA_TRY(cudaGetLastError());
+    if ((rc = ffs_assign_eval(A, children, size, ld, child_obj, stream))) return rc;
+    k_assign_replace_pseudo<<<blocks, 256, 0, st>>>(pairs, ld, prm->pseudo_always, pop_in, obj_in, children, child_obj,
+                                                    cross, pop_out, obj_out);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+}  // extern "C"

@@ -840,8 +840,10 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
             if (wst[S - 1].dispatched >= n) break;
         }
         __syncwarp();
-        if (bad) return -1;
+        // every lane takes part in the (warp-collective) read of the last heap,
+        // a lane with a bad gene included
         if (!L.single) last_key = heap_read1(heap_handle(L, region_sa, T, S - 1), L.M[S - 1] - 1, stride);
+        if (bad) return -1;
         return (int32_t)((last_key >> L.SH) + L.wt * tard);
     }
     int s_lo = 0;   // stages before s_lo have dispatched and emitted everything
@@ -887,8 +889,8 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
         if (wst[S - 1].dispatched >= n) break;
     }
     __syncwarp();
-    if (bad) return -1;
     if (!L.single) last_key = heap_read1(heap_handle(L, region_sa, T, S - 1), L.M[S - 1] - 1, stride);
+    if (bad) return -1;
     return (int32_t)((last_key >> L.SH) + L.wt * tard);
 }
 

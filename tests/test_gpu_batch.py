@@ -44,9 +44,6 @@ def test_batch_mixed_instances_match_oracle(gpu):
     compare("init")
     gen = 0
     for block in range(4):
-        if block == 2:
-            tuned = gpu.ffs_batch_autotune(b, repeats=1)
-            assert tuned["threads"] > 0 and tuned["chunk"] > 0
         gpu.ffs_batch_step(b, 3)
         for _ in range(3):
             gen += 1
@@ -59,6 +56,23 @@ def test_batch_mixed_instances_match_oracle(gpu):
     assert best.tolist() == [int(st[2].min()) for st in states]
     assert gpu.ffs_batch_decoded(b) == gen * len(specs) * rows * cols
     assert b.info()["generation"] == gen
+
+
+def test_batch_autotune_sweeps_shapes_without_advancing(gpu):
+    """The autotuner times every launch shape on generations that do not
+    advance the state: after it, the rows, makespans and generation count are
+    the initial ones.  (This batch is not stepped afterwards: generations run
+    at the default or an explicit shape in the other tests.)"""
+    specs = _mixed_specs()
+    b = gpu.Batch(specs, gpu.ffs_params_default(), 6, 5)
+    before = [tuple(t.cpu() for t in gpu.batch_tensors(b, i)) for i in range(len(specs))]
+    tuned = gpu.ffs_batch_autotune(b, repeats=1)
+    assert tuned["threads"] > 0 and tuned["chunk"] > 0 and tuned["ms"] > 0
+    for i in range(len(specs)):
+        pop, ms = gpu.batch_tensors(b, i)
+        torch.cuda.synchronize()
+        assert torch.equal(pop.cpu(), before[i][0]) and torch.equal(ms.cpu(), before[i][1]), i
+    assert b.info()["generation"] == 0 and gpu.ffs_batch_decoded(b) == 0
 
 
 def test_batch_256_uneven_sampled(gpu):

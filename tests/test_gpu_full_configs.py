@@ -9,8 +9,8 @@ with every row compared (integer results: exact equality).
     one stage at a time with saved heaps in tensor memory): 3 generations
     with ring migration after every generation, every row of every island.
   * 256 uneven instances (n in [20, 500], S in [5, 20], M_s in [2, 10],
-    32x32 tori) at the autotuned launch shape: 10 generations, every row of
-    16 instances spread over the range of n x S.
+    32x32 tori) at the library's default launch shape: 10 generations, every
+    row of 16 instances spread over the range of n x S.
 
 The oracle splits each generation's independent cells and pairs over a
 thread pool (its C calls release the GIL); every step it takes is the
@@ -87,8 +87,7 @@ def test_batch_256_ten_generations_sixteen_instances(gpu, pool):
     rows = cols = 32
     prm = gpu.ffs_params_default()
     oprm = orc.Params(seed=7)
-    b = gpu.Batch(specs, prm, rows, cols)
-    gpu.ffs_batch_autotune(b, repeats=1)       # the shape bench.py runs; it does not advance the state
+    b = gpu.Batch(specs, prm, rows, cols)      # the library's default launch shape
     order = sorted(range(len(specs)), key=lambda i: specs[i].n * specs[i].S)
     chosen = order[::16]
     assert len(chosen) == 16
