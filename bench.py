@@ -415,7 +415,13 @@ def run_ours(args):
         "clocks": clock_info,
     }
     if ws == 1 and not args.no_subrecords:
-        # the surrogate comparison (config-5 protocol, GA seeds 7..11)
+        # the other measured configuration: 256 uneven instances in one
+        # persistent launch per generation (its own timed region and clocks)
+        sub = batch_measure("batch_256", steps=20, warmup=3, autotune=True, shape=None)
+        sub["workload"] = ("batch_256: 256 instances, n ~ U[20,500], S ~ U[5,20], M_s ~ U[2,10], "
+                           "p ~ U[1,99], one 32x32 cellular island each")
+        line["batch_256"] = sub
+        # the surrogate comparison (GA seeds 7..11)
         sur = surrogate_measure(list(range(7, 12)), plain_gens=1000, screened_gens=500)
         sur.pop("median_curves", None)
         line["surrogate_100x10"] = sur
@@ -474,6 +480,7 @@ def batch_measure(workload: str, steps: int, warmup: int, autotune: bool, shape,
     elapsed = e0.elapsed_time(e1) / 1000.0
     clock_info = clocks.stop()
     evals = ffs.ffs_batch_decoded(b) - d0
+    ffs.ffs_batch_check(b)
     elapsed = max_over_ranks([elapsed], dist)[0]
     cells = w["rows"] * w["cols"]
     ops_gen = sum(cells * ops_per_eval(s.n, s.M) for s in specs)

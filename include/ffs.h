@@ -425,6 +425,11 @@ int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream strea
  * the same instances and torus (FFS_EINVAL otherwise, nothing written); the
  * launch shape in use is kept.  Generations after a load draw the same
  * Philox streams as the uninterrupted run, so the results are identical.
+ * ffs_batch_check: FFS_EDEVICE if any launch so far met a work unit whose
+ * decode layout would exceed the shared memory or TMEM columns the launch
+ * was sized for (that unit was skipped, its cells left as they were; the
+ * kernel never accesses memory out of range), else FFS_OK; synchronises
+ * `stream`.  The flag stays set for the batch's lifetime.
  * ---------------------------------------------------------------------- */
 typedef struct ffs_batch ffs_batch;
 int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stages, const int32_t *machines,
@@ -445,6 +450,7 @@ int64_t ffs_batch_checkpoint_bytes(const ffs_batch *b);
 int ffs_batch_checkpoint_save(const ffs_batch *b, void *host, int64_t capacity, ffs_stream stream);
 int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_stream stream);
 int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream);
+int ffs_batch_check(const ffs_batch *b, ffs_stream stream);
 
 /* ------------------------------------------------------------------------
  * Surrogate network (the paper has no surrogate: this is the library's

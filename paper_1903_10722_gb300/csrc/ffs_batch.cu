@@ -39,10 +39,12 @@ struct BatchShape {
 __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restrict__ insts, const int2 *__restrict__ units,
                                                         int n_units, int *counter, GaScalars g, const int32_t *cur,
                                                         const int32_t *gen, int rows, int cols, BatchShape shape,
-                                                        unsigned long long *decoded, unsigned long long decoded_add)
+                                                        unsigned long long *decoded, unsigned long long decoded_add,
+                                                        int *err)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_unit;
+    __shared__ int s_skip;
     __shared__ DecodeLayout s_L;
     __shared__ uint32_t s_tbase;
     const int T = blockDim.x;
@@ -85,14 +87,17 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             L.pairs = shape.pairs;
             L.M = st;
             L.heap_off = st + S;
-            // this instance's stages whose heaps fit the warp's TMEM columns
+            // this instance's stages whose heaps fit the warp's TMEM columns,
+            // from the stage table in global memory: the other threads'
+            // copies into st[] are not visible before the barrier below
+            const int32_t *gst = I.stage;
             int ns = 0;
             if (!L.single && shape.tmem_cols)
-                while (ns < S && st[S + ns] + st[ns] <= shape.tmem_group_cols) ++ns;
+                while (ns < S && gst[S + ns] + gst[ns] <= shape.tmem_group_cols) ++ns;
             L.tmem_cols = (uint32_t)shape.tmem_cols;
             L.tmem_group_cols = shape.tmem_group_cols;
             L.tmem_stages = ns;
-            L.tmem_split = ns < S ? st[S + ns] : I.heap_words;
+            L.tmem_split = ns < S ? gst[S + ns] : I.heap_words;
             L.tmem_addr = s_tbase;
             L.obj_words = 0;   // batches decode the makespan
             L.has_rel = L.has_due = 0;
@@ -100,8 +105,16 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             L.rel_sa = L.due_sa = 0u;
             L.heap_words = L.single ? 0 : I.heap_words - L.tmem_split;
             L.thread_words = L.heap_words + L.B + 4;
+            // the unit's layout must stay inside what the launch was sized
+            // for (shared words per thread, TMEM columns per warp); a unit
+            // that does not is skipped and reported, never run out of range
+            const bool fits = n <= shape.max_n && S <= shape.max_S && L.thread_words <= shape.max_tw &&
+                              (ns == 0 || gst[S + ns - 1] + gst[ns - 1] <= shape.tmem_group_cols);
+            s_skip = fits ? 0 : 1;
+            if (!fits) atomicOr(err, 1);
         }
         __syncthreads();
+        if (s_skip) continue;   // block-uniform; the loop head synchronises again
         const DecodeLayout &L = s_L;
         IslandRef ref;
         memset(&ref, 0, sizeof(ref));
@@ -153,6 +166,7 @@ struct ffs_batch {
     int *d_counter = nullptr;
     int32_t *d_cur = nullptr, *d_gen = nullptr;
     unsigned long long *d_decoded = nullptr;
+    int *d_err = nullptr;   // set by a unit whose layout exceeds the launch shape
     int host_cur = 0;
     long long host_gen = 0;
     int T = 0, B = 0, blocks_per_sm = 0;
@@ -293,7 +307,7 @@ static int batch_generation(ffs_batch *b, bool advance, unsigned long long *deco
     if (grid > b->n_units) grid = b->n_units;
     k_batch_cellular<<<grid, b->T, b->smem, st>>>(b->d_inst, b->d_units, b->n_units, b->d_counter, scalars_of(&b->prm),
                                                    b->d_cur, b->d_gen, b->rows, b->cols, b->shape, decoded,
-                                                   (unsigned long long)b->count * b->rows * b->cols);
+                                                   (unsigned long long)b->count * b->rows * b->cols, b->d_err);
     FFS_CUDA_TRY(cudaGetLastError());
     if (advance) {
         k_batch_advance<<<1, 32, 0, st>>>(b->d_cur, b->d_gen);
@@ -372,14 +386,15 @@ int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stag
     b->d_cur = (int32_t *)alloc(4);
     b->d_gen = (int32_t *)alloc(4);
     b->d_decoded = (unsigned long long *)alloc(8);
-    if (!b->d_inst || !b->d_units || !b->d_counter || !b->d_cur || !b->d_gen || !b->d_decoded) {
+    b->d_err = (int *)alloc(4);
+    if (!b->d_inst || !b->d_units || !b->d_counter || !b->d_cur || !b->d_gen || !b->d_decoded || !b->d_err) {
         batch_free(b);
         return set_error(FFS_ENOMEM, "batch state");
     }
     int rc = FFS_OK;
     if (cudaMemcpyAsync(b->d_inst, b->hinst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st) ||
         cudaMemsetAsync(b->d_cur, 0, 4, st) || cudaMemsetAsync(b->d_gen, 0, 4, st) ||
-        cudaMemsetAsync(b->d_decoded, 0, 8, st))
+        cudaMemsetAsync(b->d_decoded, 0, 8, st) || cudaMemsetAsync(b->d_err, 0, 4, st))
         rc = set_error(FFS_ECUDA, "batch state initialisation");
     for (int i = 0; i < count && !rc; ++i) {
         rc = launch_init(b->insts[i], prm->seed, (uint32_t)i, 0, cells, b->hinst[i].ld, b->hinst[i].pop[0], st);
@@ -560,6 +575,17 @@ int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream)
     FFS_CUDA_TRY(cudaMemcpyAsync(&v, b->d_decoded, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     FFS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     *count = (int64_t)v;
+    return FFS_OK;
+}
+
+int ffs_batch_check(const ffs_batch *b, ffs_stream stream)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    int v = 0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(&v, b->d_err, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    FFS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (v) return set_error(FFS_EDEVICE, "a batch work unit's layout exceeded the launch shape and was skipped");
     return FFS_OK;
 }
 

@@ -56,15 +56,55 @@ def test_batch_mixed_instances_match_oracle(gpu):
     assert best.tolist() == [int(st[2].min()) for st in states]
     assert gpu.ffs_batch_decoded(b) == gen * len(specs) * rows * cols
     assert b.info()["generation"] == gen
+    gpu.ffs_batch_check(b)
 
 
-def test_batch_autotune_sweeps_shapes_without_advancing(gpu):
+def _many_stage_specs():
+    """Instances of 17 to 20 stages (2S > 32 stage-table entries, so more than
+    one warp copies the table into shared memory) mixed with short ones, in
+    an order that puts different stage counts in consecutive work units."""
+    shapes = [(120, 20, 2, 10), (9, 3, 2, 4), (64, 17, 3, 6), (200, 19, 5, 10), (31, 5, 1, 8),
+              (150, 18, 2, 3), (77, 20, 6, 9), (40, 2, 4, 4)]
+    return [make_instance(n, S, lo, hi, seed=k + 11) for k, (n, S, lo, hi) in enumerate(shapes)]
+
+
+@pytest.mark.parametrize("variant,threads,chunk", [(3, 64, 16), (4, 128, 32), (3, 320, 24), (4, 512, 64),
+                                                   (1, 128, 16), (2, 192, 32)])
+def test_batch_many_stages_match_oracle(gpu, variant, threads, chunk):
+    """Every block computes each work unit's decode layout (which stages keep
+    their saved heaps in tensor memory) from the instance's own stage table,
+    whatever instance its previous unit had: 6 generations of instances with
+    up to 20 stages at launch shapes with and without tensor-memory heaps."""
+    specs = _many_stage_specs()
+    rows, cols = 8, 8
+    prm = gpu.ffs_params_default()
+    prm.decode_variant, prm.decode_chunk, prm.block_threads = variant, chunk, threads
+    oprm = orc.Params(seed=7)
+    b = gpu.Batch(specs, prm, rows, cols)
+    states = [_oracle_state(s, i, rows, cols) for i, s in enumerate(specs)]
+    gpu.ffs_batch_step(b, 6)
+    for gen in range(1, 7):
+        for i, s in enumerate(specs):
+            o, pop, ms = states[i]
+            pop, ms, _ = orc.cellular_generation(o, oprm, i, gen, rows, cols, pop, ms)
+            states[i] = (o, pop, ms)
+    gpu.ffs_batch_check(b)
+    for i, s in enumerate(specs):
+        pop, ms = gpu.batch_tensors(b, i)
+        torch.cuda.synchronize()
+        assert np.array_equal(pop.cpu().numpy(), states[i][1][:, :s.n]), i
+        assert np.array_equal(ms.cpu().numpy().astype(np.int64), states[i][2]), i
+
+
+@pytest.mark.parametrize("which", ["mixed", "many_stages"])
+def test_batch_autotune_then_generations_match_oracle(gpu, which):
     """The autotuner times every launch shape on generations that do not
-    advance the state: after it, the rows, makespans and generation count are
-    the initial ones.  (This batch is not stepped afterwards: generations run
-    at the default or an explicit shape in the other tests.)"""
-    specs = _mixed_specs()
-    b = gpu.Batch(specs, gpu.ffs_params_default(), 6, 5)
+    advance the state (after it the rows, makespans and generation count are
+    the initial ones); generations at the shape it keeps then match the
+    oracle."""
+    specs = _mixed_specs() if which == "mixed" else _many_stage_specs()
+    rows, cols = 6, 5
+    b = gpu.Batch(specs, gpu.ffs_params_default(), rows, cols)
     before = [tuple(t.cpu() for t in gpu.batch_tensors(b, i)) for i in range(len(specs))]
     tuned = gpu.ffs_batch_autotune(b, repeats=1)
     assert tuned["threads"] > 0 and tuned["chunk"] > 0 and tuned["ms"] > 0
@@ -73,6 +113,21 @@ def test_batch_autotune_sweeps_shapes_without_advancing(gpu):
         torch.cuda.synchronize()
         assert torch.equal(pop.cpu(), before[i][0]) and torch.equal(ms.cpu(), before[i][1]), i
     assert b.info()["generation"] == 0 and gpu.ffs_batch_decoded(b) == 0
+    gpu.ffs_batch_check(b)
+    oprm = orc.Params(seed=7)
+    states = [_oracle_state(s, i, rows, cols) for i, s in enumerate(specs)]
+    gpu.ffs_batch_step(b, 3)
+    for gen in range(1, 4):
+        for i, s in enumerate(specs):
+            o, pop, ms = states[i]
+            pop, ms, _ = orc.cellular_generation(o, oprm, i, gen, rows, cols, pop, ms)
+            states[i] = (o, pop, ms)
+    gpu.ffs_batch_check(b)
+    for i, s in enumerate(specs):
+        pop, ms = gpu.batch_tensors(b, i)
+        torch.cuda.synchronize()
+        assert np.array_equal(pop.cpu().numpy(), states[i][1][:, :s.n]), (tuned, i)
+        assert np.array_equal(ms.cpu().numpy().astype(np.int64), states[i][2]), (tuned, i)
 
 
 def test_batch_256_uneven_sampled(gpu):
@@ -128,6 +183,7 @@ def test_batch_tensor_memory_heaps_match_oracle(gpu, variant, threads, chunk):
             o, pop, ms = states[i]
             pop, ms, _ = orc.cellular_generation(o, oprm, i, gen, rows, cols, pop, ms)
             states[i] = (o, pop, ms)
+    gpu.ffs_batch_check(b)
     for i, s in enumerate(specs):
         pop, ms = gpu.batch_tensors(b, i)
         torch.cuda.synchronize()

@@ -119,3 +119,4 @@ def test_batch_256_ten_generations_sixteen_instances(gpu, pool):
     best = gpu.ffs_batch_best(b)
     for i in chosen:
         assert best[i] == states[i][2].min()
+    gpu.ffs_batch_check(b)
