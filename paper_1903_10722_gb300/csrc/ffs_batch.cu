@@ -2,11 +2,15 @@
 // island, evolved together: one persistent launch per generation, replayed
 // from a CUDA graph, with the launch shape chosen by a timing autotuner.
 //
-// Work is split into units (instance, tile of `threads` cells).  Units are
-// ordered heaviest first (decode cost ~ n * sum_s (2 M_s + 6)) and blocks of
-// the persistent grid take the next unit from a device counter, stage that
-// instance's processing-time table into shared memory and run the fused
-// cellular generation on the tile.  Shared memory is sized for the largest
+// A generation is two launches.  k_batch_breed builds every instance's
+// children (8 cells per warp, many warps: the crossover waits on the
+// parents' loads) into per-instance child rows and copies each cell to its
+// output row.  k_batch_cellular then decodes: work is split into units
+// (instance, tile of `threads` cells), ordered heaviest first (decode cost ~
+// n * sum_s (2 M_s + 6)); blocks of the persistent grid take the next unit
+// from a device counter, stage that instance's processing-time table into
+// shared memory, decode the tile's children and write each child that is
+// better over its cell's copy.  Shared memory is sized for the largest
 // instance.
 #include <algorithm>
 #include <cstring>
@@ -26,6 +30,7 @@ struct BatchInst {
     const int32_t *stage;
     int16_t *pop[2];
     int32_t *ms[2];
+    int16_t *child;   // [cells][ld]: this generation's children
 };
 
 struct BatchShape {
@@ -35,6 +40,46 @@ struct BatchShape {
     int tmem_cols;  // TMEM columns per block for saved heaps (0: none)
     int tmem_group_cols;  // columns per warp of a lane quarter
 };
+
+constexpr int kBatchCellsPerWarp = 8;
+
+__device__ __forceinline__ IslandRef batch_ref(const BatchInst &I, const int32_t *cur, const int32_t *gen, int i)
+{
+    IslandRef ref;
+    memset(&ref, 0, sizeof(ref));
+    ref.pop[0] = I.pop[0];
+    ref.pop[1] = I.pop[1];
+    ref.ms[0] = I.ms[0];
+    ref.ms[1] = I.ms[1];
+    ref.dev_cur = cur;
+    ref.dev_gen = gen;
+    ref.island = (uint32_t)i;
+    return ref;
+}
+
+// The breeding half of a generation of every instance: warp gw takes cells
+// [8 q, 8 q + 8) of instance i (gw = i * warps_per_inst + q), lane l < 8 one
+// cell: draws, tournaments, order crossover and swap into the instance's
+// child row, the cell copied to its output row.  wbits: the warp's
+// crossover mark, mark_words(max_n) words.
+__global__ void __launch_bounds__(256) k_batch_breed(const BatchInst *__restrict__ insts, int count, GaScalars g,
+                                                     const int32_t *cur, const int32_t *gen, int rows, int cols,
+                                                     int warps_per_inst, int mark_words_max)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int i = gw / warps_per_inst;
+    if (i >= count) return;   // whole warps leave together
+    const int cells = rows * cols;
+    const int base = (gw - i * warps_per_inst) * kBatchCellsPerWarp;
+    const BatchInst &I = insts[i];
+    const int c = base + lane;
+    const bool valid = lane < kBatchCellsPerWarp && c < cells;
+    const int cq = valid ? c : base;
+    cellular_warp_breed(batch_ref(I, cur, gen, i), g, I.n, cq, valid, rows, cols, I.ld, smem + warp * mark_words_max,
+                        I.child + (int64_t)cq * I.ld);
+}
 
 __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restrict__ insts, const int2 *__restrict__ units,
                                                         int n_units, int *counter, GaScalars g, const int32_t *cur,
@@ -48,11 +93,9 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
     __shared__ DecodeLayout s_L;
     __shared__ uint32_t s_tbase;
     const int T = blockDim.x;
-    const int bits_per_warp = mark_words(shape.max_n);   // one byte per gene
-    const SmemMap map = smem_map(shape.max_n, shape.max_S, T, bits_per_warp);
+    const SmemMap map = smem_map(shape.max_n, shape.max_S, T, 0);   // the crossover ran in k_batch_breed
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * shape.max_S;
-    uint32_t *wbits = smem + map.bits + warp * bits_per_warp;
     uint32_t *region = smem + map.region + threadIdx.x;
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
@@ -116,21 +159,13 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
         __syncthreads();
         if (s_skip) continue;   // block-uniform; the loop head synchronises again
         const DecodeLayout &L = s_L;
-        IslandRef ref;
-        memset(&ref, 0, sizeof(ref));
-        ref.pop[0] = I.pop[0];
-        ref.pop[1] = I.pop[1];
-        ref.ms[0] = I.ms[0];
-        ref.ms[1] = I.ms[1];
-        ref.dev_cur = cur;
-        ref.dev_gen = gen;
-        ref.island = (uint32_t)un.x;
+        const IslandRef ref = batch_ref(I, cur, gen, un.x);
         const int end = min(un.y + T, cells);
         for (int base = un.y + warp * 32; base < end; base += T) {
             const int c = base + lane;
             const bool valid = c < end;
-            cellular_warp_cells(L, g, ref, valid ? c : end - 1, valid, rows, cols, I.ld, wbits, region, T, tab,
-                                      wst);
+            const int cq = valid ? c : end - 1;
+            cellular_warp_decode_child(L, g, ref, cq, valid, I.ld, I.child + (int64_t)cq * I.ld, region, T, tab, wst);
         }
     }
     if (shape.tmem_cols) {
@@ -170,6 +205,7 @@ struct ffs_batch {
     int host_cur = 0;
     long long host_gen = 0;
     int T = 0, B = 0, blocks_per_sm = 0;
+    int max_n = 0;
     size_t smem = 0;
     BatchShape shape{};
     int num_sms = 0;
@@ -228,7 +264,7 @@ static int batch_shape(ffs_batch *b, int T, int B, BatchShape *shape, size_t *sm
             s.max_tw = std::max(s.max_tw, tw);
         }
         if (tb && !any_tmem) continue;
-        const SmemMap m = smem_map(s.max_n, s.max_S, T, mark_words(s.max_n));
+        const SmemMap m = smem_map(s.max_n, s.max_S, T, 0);
         size_t bytes = (size_t)(m.region + s.max_tw * T) * 4u;
         if (bytes > 232448) continue;
         auto occ = [&](size_t by) {
@@ -302,6 +338,20 @@ static int batch_set_shape(ffs_batch *b, int T, int B, cudaStream_t st)
 static int batch_generation(ffs_batch *b, bool advance, unsigned long long *decoded, cudaStream_t st)
 {
     FFS_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    {
+        const int cells = b->rows * b->cols;
+        const int wpi = (cells + kBatchCellsPerWarp - 1) / kBatchCellsPerWarp;
+        const int mw = mark_words(b->max_n);
+        int Tb = 256;
+        while (Tb > 32 && (size_t)(Tb / 32) * mw * 4 > 232448) Tb >>= 1;
+        const size_t smem = (size_t)(Tb / 32) * mw * 4;
+        if (smem > 232448) return set_error(FFS_EUNSUPPORTED, "crossover mark of n = %d too large", b->max_n);
+        const long long warps = (long long)wpi * b->count;
+        FFS_CUDA_TRY(cudaFuncSetAttribute(k_batch_breed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_batch_breed<<<(unsigned)((warps * 32 + Tb - 1) / Tb), Tb, smem, st>>>(
+            b->d_inst, b->count, scalars_of(&b->prm), b->d_cur, b->d_gen, b->rows, b->cols, wpi, mw);
+        FFS_CUDA_TRY(cudaGetLastError());
+    }
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_batch_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     int grid = b->num_sms * b->blocks_per_sm;
     if (grid > b->n_units) grid = b->n_units;
@@ -376,6 +426,12 @@ int ffs_batch_create(int32_t count, const int32_t *n_jobs, const int32_t *n_stag
                 return set_error(FFS_ENOMEM, "populations of instance %d", i);
             }
         }
+        h.child = (int16_t *)alloc((size_t)cells * h.ld * 2);
+        if (!h.child) {
+            batch_free(b);
+            return set_error(FFS_ENOMEM, "child rows of instance %d", i);
+        }
+        b->max_n = std::max(b->max_n, h.n);
         b->hinst.push_back(h);
         moff += n_stages[i];
         poff += (int64_t)n_jobs[i] * n_stages[i];
