@@ -482,6 +482,21 @@ def batch_measure(workload: str, steps: int, warmup: int, autotune: bool, shape,
     evals = ffs.ffs_batch_decoded(b) - d0
     ffs.ffs_batch_check(b)
     elapsed = max_over_ranks([elapsed], dist)[0]
+    # the dominant kernel alone: the decode launch on one breeding launch's
+    # children (a generation that does not advance, then the decode launch
+    # repeated), CUDA events on the launching stream
+    ffs.ffs_batch_dry_run(b, 0)
+    kts = []
+    for _ in range(max(5, min(steps, 20))):
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        ffs.ffs_batch_dry_run(b, 1)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        kts.append(k0.elapsed_time(k1))
+    ffs.ffs_batch_check(b)
+    kernel_s = statistics.median(kts) / 1000.0
+    minmax_rate = ffs.ffs_measure_int_rate(0)["lane_ops_per_s"]
     cells = w["rows"] * w["cols"]
     ops_gen = sum(cells * ops_per_eval(s.n, s.M) for s in specs)
     peaks, peak_kind = _peaks()
@@ -490,15 +505,23 @@ def batch_measure(workload: str, steps: int, warmup: int, autotune: bool, shape,
     peak_ops = num_sms * LANES_PER_SM * sm_max * 1e6
     step_s = elapsed / steps
     b.close()
+    shape_key = (tuned["threads"], tuned["chunk"], tuned["variant"])
     return {
         "value": evals * ws / elapsed, "unit": "evals/s", "steps": steps, "warmup": warmup,
         "ms_per_step": step_s * 1000.0, "launch_shape": tuned, "chromosomes": w["count"] * cells,
-        "roofline": {"bound": "alu", "achieved": ops_gen / step_s / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s (int32 lane ops)", "frac": ops_gen / step_s / peak_ops,
-                     "traffic": (K_BATCH_CELLULAR_DRAM_BYTES
-                                 if (tuned["threads"], tuned["chunk"], tuned["variant"]) == (512, 64, 3) else None),
-                     "kernel": "k_batch_cellular (one persistent launch per generation; step time incl. "
-                               "the counter reset and generation advance)"},
+        "gpu_launches": 3 * steps,
+        "roofline": {"bound": "alu", "achieved": ops_gen / kernel_s / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s (int32 lane ops)", "frac": ops_gen / kernel_s / peak_ops,
+                     "traffic": K_BATCH_CELLULAR_DRAM_BYTES.get(shape_key),
+                     "kernel": "k_batch_cellular (the persistent decode launch of one generation), timed alone",
+                     "kernel_ms": kernel_s * 1000.0, "ops_per_launch": ops_gen,
+                     "frac_of_measured_minmax_rate": ops_gen / kernel_s / minmax_rate,
+                     "measured_minmax_tops": minmax_rate / 1e12,
+                     "group": {"what": "one generation: breeding (k_batch_breed), counter reset, decode "
+                                       "(k_batch_cellular) and generation advance",
+                               "ms": step_s * 1000.0, "achieved": ops_gen / step_s / 1e12,
+                               "frac": ops_gen / step_s / peak_ops},
+                     "peak_basis": f"{num_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz ({peak_kind} max clock)"},
         "clocks": clock_info,
     }
 
@@ -531,7 +554,7 @@ def run_batch(args):
                    "n_stages": list(w["S"]), "machines_per_stage": list(w["m"]), "torus": [w["rows"], w["cols"]],
                    "chromosomes": w["count"] * cells, "launch_shape": m["launch_shape"],
                    "parallelism": f"replicas x{ws}"},
-        "gpu_launches": args.steps,
+        "gpu_launches": m["gpu_launches"],
         "roofline": m["roofline"],
         "clocks": m["clocks"],
     }
@@ -933,9 +956,10 @@ K_STEP_DECODE_DRAM_BYTES = {(384, 128, 3): 117_337_088 + 9_407_744, (384, 104, 3
                             (384, 96, 3): 116_727_552 + 9_374_720}
 
 
-# DRAM bytes of one k_batch_cellular launch of batch_256 at 512 threads,
-# chunk 64, variant 3 (ncu: 223.0 MB read + 178.9 MB written).
-K_BATCH_CELLULAR_DRAM_BYTES = 401_944_064
+# DRAM bytes of one k_batch_cellular (decode) launch of batch_256, per
+# launch shape (threads, chunk, variant), from ncu captures of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum); other shapes null.
+K_BATCH_CELLULAR_DRAM_BYTES = {(384, 128, 3): 143_038_976 + 30_597_632}
 
 
 def launches_per_generation(w) -> int:

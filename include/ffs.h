@@ -425,6 +425,12 @@ int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream strea
  * the same instances and torus (FFS_EINVAL otherwise, nothing written); the
  * launch shape in use is kept.  Generations after a load draw the same
  * Philox streams as the uninterrupted run, so the results are identical.
+ * ffs_batch_dry_run: kind 0 runs one generation's launches (breeding and
+ * decoding) without advancing: the current rows, makespans, generation and
+ * decode counts are unchanged, only the next generation's buffers are
+ * written (as ffs_batch_autotune does); kind 1 runs the decoding launch
+ * alone on the children of the last breeding launch (for timing it; run
+ * kind 0 first).  Asynchronous.
  * ffs_batch_check: FFS_EDEVICE if any launch so far met a work unit whose
  * decode layout would exceed the shared memory or TMEM columns the launch
  * was sized for (that unit was skipped, its cells left as they were; the
@@ -451,6 +457,7 @@ int ffs_batch_checkpoint_save(const ffs_batch *b, void *host, int64_t capacity, 
 int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_stream stream);
 int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream);
 int ffs_batch_check(const ffs_batch *b, ffs_stream stream);
+int ffs_batch_dry_run(ffs_batch *b, int32_t kind, ffs_stream stream);
 
 /* ------------------------------------------------------------------------
  * Surrogate network (the paper has no surrogate: this is the library's

@@ -121,7 +121,8 @@ int orc_bernoulli(uint32_t x, uint64_t threshold)
  *
  * p is [n][S] row-major (job-major).  If gantt is not NULL it receives
  * n*S records of 5 int64 (stage, job, machine, start, end) in dispatch
- * order, stage by stage. */
+ * order, stage by stage.  A row with a gene outside [0, n) has objective
+ * -1 (nothing is scheduled). */
 typedef struct {
     const int32_t *release;   /* R_j [n], or NULL (all 0) */
     const int32_t *due;       /* D_j [n], or NULL (no tardiness term) */
@@ -143,6 +144,10 @@ static int orc_pair_cmp(const void *a, const void *b)
 int64_t orc_decode_obj(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
                        const orc_objective *obj, const int16_t *perm, int64_t *gantt)
 {
+    /* a gene that names no job makes the row invalid: objective -1 (the
+     * same reading as for the machine-assignment strings below) */
+    for (int32_t k = 0; k < n; ++k)
+        if (perm[k] < 0 || perm[k] >= n) return -1;
     int64_t *c_prev = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     int64_t *c_cur = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));

@@ -93,6 +93,7 @@ _SIGS = [
     ("ffs_batch_best", _i32, [_vp, _vp, _vp]),
     ("ffs_batch_decoded", _i32, [_vp, _vp, _vp]),
     ("ffs_batch_check", _i32, [_vp, _vp]),
+    ("ffs_batch_dry_run", _i32, [_vp, _i32, _vp]),
     ("ffs_gemm_bf16", _i32, [_vp, _i32, _vp, _i32, _vp, _i32, _i32, _i32, _i32, _vp, _vp]),
     ("ffs_mlp_create", _i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
     ("ffs_mlp_destroy", _i32, [_vp]),
@@ -570,6 +571,10 @@ def ffs_batch_decoded(b: Batch, stream=None) -> int:
 
 def ffs_batch_check(b: Batch, stream=None):
     _check(load().ffs_batch_check(b.handle, _stream(stream)))
+
+
+def ffs_batch_dry_run(b: Batch, kind: int, stream=None):
+    _check(load().ffs_batch_dry_run(b.handle, kind, _stream(stream)))
 
 
 def batch_tensors(b: Batch, instance: int):

@@ -333,12 +333,15 @@ static int batch_set_shape(ffs_batch *b, int T, int B, cudaStream_t st)
     return batch_units(b, T, st);
 }
 
-// One generation's launch (the counter reset and the persistent kernel);
-// advance = false leaves the generation state untouched (autotuning).
-static int batch_generation(ffs_batch *b, bool advance, unsigned long long *decoded, cudaStream_t st)
+// One generation's launches: the breeding launch, the counter reset and the
+// persistent decode launch (breed = false: the decode launch alone, on the
+// children of the last breeding launch); advance = false leaves the
+// generation state untouched (autotuning, timing).
+static int batch_generation(ffs_batch *b, bool advance, unsigned long long *decoded, cudaStream_t st,
+                            bool breed = true)
 {
     FFS_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
-    {
+    if (breed) {
         const int cells = b->rows * b->cols;
         const int wpi = (cells + kBatchCellsPerWarp - 1) / kBatchCellsPerWarp;
         const int mw = mark_words(b->max_n);
@@ -632,6 +635,14 @@ int ffs_batch_decoded(const ffs_batch *b, int64_t *count, ffs_stream stream)
     FFS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     *count = (int64_t)v;
     return FFS_OK;
+}
+
+int ffs_batch_dry_run(ffs_batch *b, int32_t kind, ffs_stream stream)
+{
+    clear_error();
+    if (!b) return set_error(FFS_EINVAL, "NULL batch");
+    if (kind != 0 && kind != 1) return set_error(FFS_EINVAL, "dry-run kind %d", kind);
+    return batch_generation(b, false, nullptr, (cudaStream_t)stream, kind == 0);
 }
 
 int ffs_batch_check(const ffs_batch *b, ffs_stream stream)

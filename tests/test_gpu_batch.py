@@ -113,6 +113,17 @@ def test_batch_autotune_then_generations_match_oracle(gpu, which):
         torch.cuda.synchronize()
         assert torch.equal(pop.cpu(), before[i][0]) and torch.equal(ms.cpu(), before[i][1]), i
     assert b.info()["generation"] == 0 and gpu.ffs_batch_decoded(b) == 0
+    # dry runs (a whole generation, then the decode launch alone) change nothing either
+    gpu.ffs_batch_dry_run(b, 0)
+    gpu.ffs_batch_dry_run(b, 1)
+    gpu.ffs_batch_dry_run(b, 1)
+    for i in range(len(specs)):
+        pop, ms = gpu.batch_tensors(b, i)
+        torch.cuda.synchronize()
+        assert torch.equal(pop.cpu(), before[i][0]) and torch.equal(ms.cpu(), before[i][1]), i
+    assert b.info()["generation"] == 0 and gpu.ffs_batch_decoded(b) == 0
+    with pytest.raises(gpu.FFSError):
+        gpu.ffs_batch_dry_run(b, 2)
     gpu.ffs_batch_check(b)
     oprm = orc.Params(seed=7)
     states = [_oracle_state(s, i, rows, cols) for i, s in enumerate(specs)]
