@@ -952,8 +952,7 @@ def run_paper(args):
 # the launch shapes the autotuner picks, (threads, chunk, variant) -> bytes,
 # from ncu captures of the current kernel (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = {(384, 128, 3): 117_337_088 + 9_407_744, (384, 104, 3): 116_720_896 + 9_434_368,
-                            (384, 96, 3): 116_727_552 + 9_374_720}
+K_STEP_DECODE_DRAM_BYTES = {(384, 104, 3): 116_367_872 + 7_662_592}
 
 
 # DRAM bytes of one k_batch_cellular (decode) launch of batch_256, per

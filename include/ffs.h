@@ -392,6 +392,34 @@ int ffs_islands_best(const ffs_islands *isl, int32_t *best_makespan, int32_t *be
 /* Number of exact decodes (children evaluated) since creation; synchronises. */
 int ffs_islands_decoded(const ffs_islands *isl, int64_t *count, ffs_stream stream);
 
+/* Per-island metrics (no counterpart in the paper).  A record is
+ * FFS_STAT_WORDS int64 values for one island at one generation:
+ *   [0] generation, [1] best makespan (-1 if no row is valid), [2] worst,
+ *   [3] sum of the valid makespans (mean = [3] / [4]), [4] valid rows,
+ *   [5] best makespan any metrics pass has seen since creation (-1: none),
+ *   [6] migrations the island has received (ring or penetration events
+ *   that delivered rows to it), [7] rows received by migration.
+ * Makespans are the instance's objective when it has one.
+ * ffs_islands_stats: the current generation's record of every island into
+ * out[n_islands][FFS_STAT_WORDS] (host); synchronises `stream`.
+ * ffs_islands_record_stats: from now on, one record per island at the end
+ * of every generation (after migration), kept on the device in a ring of
+ * `capacity` generations (0 switches recording off and frees it); the
+ * current generation is recorded at once.  The records are written by a
+ * kernel inside the captured generation graphs (one small launch per
+ * generation); switching re-captures them.  All islands must be at the
+ * same generation.  Synchronises `stream`.
+ * ffs_islands_stats_history: *count = the records kept, the oldest kept
+ * generation first (at most `capacity`); with out != NULL also copies them
+ * to out[*count][n_islands][FFS_STAT_WORDS] (host; max_records >= *count,
+ * else FFS_EINVAL).  Synchronises `stream`.
+ * The best-so-far value and the migration counters travel in checkpoints. */
+#define FFS_STAT_WORDS 8
+int ffs_islands_stats(ffs_islands *isl, int64_t *out, ffs_stream stream);
+int ffs_islands_record_stats(ffs_islands *isl, int32_t capacity, ffs_stream stream);
+int ffs_islands_stats_history(const ffs_islands *isl, int64_t *out, int32_t max_records, int32_t *count,
+                              ffs_stream stream);
+
 /* ------------------------------------------------------------------------
  * Batch: many instances of uneven size, each evolving one cellular island
  * on a rows x cols torus (the island step of Sections 4.1-4.2 per instance;
@@ -561,6 +589,25 @@ int ffs_islands_attach_surrogate(ffs_islands *isl, ffs_mlp *mlp, const ffs_surro
                                  ffs_stream stream);
 int ffs_islands_surrogate_last(const ffs_islands *isl, float *scores, int32_t *chosen, float *loss,
                                int64_t *pairs, int16_t *candidates, int32_t ld_out, ffs_stream stream);
+
+/* ------------------------------------------------------------------------
+ * The checked build (no counterpart in the paper).  The library built with
+ * -DFFS_DEBUG_CHECKS (libffs_gb300_debug.so) checks, on the device, the
+ * index at each of the GA's indexing sites (tournament parents, crossover
+ * cuts and writes, migration rows, the surrogate's ring slots and picks,
+ * reassigned machine genes) and, after every generation of islands or of a
+ * batch, that every row is a permutation of [0, n) with a makespan >= 0.
+ * A failing check skips the access it guards and leaves its code in a
+ * device error word (the first failure wins): 1 row not a permutation,
+ * 2 tournament parent, 3 crossover cut, 4 crossover write, 5 migration row,
+ * 6 ring slot, 7 surrogate pick, 8 machine gene.
+ * ffs_debug_checks: *enabled = 1 in the checked build, 0 otherwise.
+ * ffs_debug_check_error: synchronises `stream` and returns the error word in
+ * *code (0: no check failed; always 0 in the normal build), clearing it when
+ * reset != 0.
+ * ---------------------------------------------------------------------- */
+int ffs_debug_checks(int32_t *enabled);
+int ffs_debug_check_error(int32_t *code, int32_t reset, ffs_stream stream);
 
 /* ------------------------------------------------------------------------
  * Measurement and self-tests (no counterpart in the paper).

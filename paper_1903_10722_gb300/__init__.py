@@ -51,6 +51,8 @@ class ffs_params(ctypes.Structure):
 # (name, restype, argtypes) of every exported call; the names follow include/ffs.h
 _SIGS = [
     ("ffs_last_error", ctypes.c_char_p, []),
+    ("ffs_debug_checks", _i32, [ctypes.POINTER(_i32)]),
+    ("ffs_debug_check_error", _i32, [ctypes.POINTER(_i32), _i32, _vp]),
     ("ffs_instance_create", _i32, [_i32, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
     ("ffs_instance_create_objective", _i32, [_i32, _i32, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
     ("ffs_instance_destroy", _i32, [_vp]),
@@ -83,6 +85,9 @@ _SIGS = [
     ("ffs_islands_set_all", _i32, [_vp, _vp, _i32, _vp, _vp]),
     ("ffs_islands_best", _i32, [_vp, _vp, _vp, _vp, _vp]),
     ("ffs_islands_decoded", _i32, [_vp, _vp, _vp]),
+    ("ffs_islands_stats", _i32, [_vp, _vp, _vp]),
+    ("ffs_islands_record_stats", _i32, [_vp, _i32, _vp]),
+    ("ffs_islands_stats_history", _i32, [_vp, _vp, _i32, _vp, _vp]),
     ("ffs_batch_create", _i32, [_i32, _vp, _vp, _vp, _vp, ctypes.POINTER(ffs_params), _i32, _i32, _vp,
                                 ctypes.POINTER(_vp)]),
     ("ffs_batch_destroy", _i32, [_vp]),
@@ -137,14 +142,21 @@ def library_path() -> str:
     return _build.LIB
 
 
+def debug_checks_requested() -> bool:
+    """FFS_DEBUG_CHECKS=1 in the environment selects the checked library."""
+    return os.environ.get("FFS_DEBUG_CHECKS", "0") not in ("", "0")
+
+
 def load(build_if_missing: bool = True):
-    """Load libffs_gb300.so (building it with nvcc if needed)."""
+    """Load libffs_gb300.so, or libffs_gb300_debug.so when FFS_DEBUG_CHECKS=1
+    (building it with nvcc if needed)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
+    debug = debug_checks_requested()
+    path = _build.LIB_DEBUG if debug else _build.LIB
+    if build_if_missing and not _build.up_to_date(debug):
+        _build.build(debug=debug)
     if not os.path.exists(path):
         raise FFSError(FFS_EUNSUPPORTED, f"CUDA library not built: {path}")
     lib = ctypes.CDLL(path)
@@ -154,6 +166,20 @@ def load(build_if_missing: bool = True):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def ffs_debug_checks() -> bool:
+    """True when the loaded library is the checked build."""
+    v = _i32()
+    _check(load().ffs_debug_checks(ctypes.byref(v)))
+    return bool(v.value)
+
+
+def ffs_debug_check_error(reset: bool = False, stream=None) -> int:
+    """The checked build's device error word (0: no check failed)."""
+    v = _i32()
+    _check(load().ffs_debug_check_error(ctypes.byref(v), int(reset), _stream(stream)))
+    return v.value
 
 
 def exported_names() -> list[str]:
@@ -444,6 +470,36 @@ def ffs_islands_best(isl: Islands, stream=None):
     _check(load().ffs_islands_best(isl.handle, ctypes.byref(m), ctypes.byref(i), ctypes.byref(r),
                                    _stream(stream)))
     return m.value, i.value, r.value
+
+
+FFS_STAT_WORDS = 8
+STAT_FIELDS = ("generation", "best", "worst", "sum", "valid", "best_so_far", "migrations", "migrated_rows")
+
+
+def ffs_islands_stats(isl: Islands, stream=None):
+    """The current generation's metrics of every island: int64 [n_islands][8]
+    (fields in STAT_FIELDS order)."""
+    import numpy as np
+    out = np.zeros((isl.n_islands, FFS_STAT_WORDS), dtype=np.int64)
+    _check(load().ffs_islands_stats(isl.handle, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def ffs_islands_record_stats(isl: Islands, capacity: int, stream=None):
+    _check(load().ffs_islands_record_stats(isl.handle, capacity, _stream(stream)))
+
+
+def ffs_islands_stats_history(isl: Islands, stream=None):
+    """The recorded metrics, oldest generation first: int64
+    [records][n_islands][8]."""
+    import numpy as np
+    n = _i32()
+    _check(load().ffs_islands_stats_history(isl.handle, None, 0, ctypes.byref(n), _stream(stream)))
+    out = np.zeros((n.value, isl.n_islands, FFS_STAT_WORDS), dtype=np.int64)
+    if n.value:
+        _check(load().ffs_islands_stats_history(isl.handle, out.ctypes.data, n.value, ctypes.byref(n),
+                                                _stream(stream)))
+    return out
 
 
 def ffs_islands_decoded(isl: Islands, stream=None) -> int:

@@ -2,7 +2,10 @@
 
 Each .cu file is compiled in its own nvcc process (in parallel) and the
 objects are linked into one shared library with the CUDA runtime linked
-statically.  Output: paper_1903_10722_gb300/_build/libffs_gb300.so.
+statically.  Output: paper_1903_10722_gb300/_build/libffs_gb300.so, and the
+variant with device-side checks (-DFFS_DEBUG_CHECKS: index bounds at the GA's
+indexing sites and permutation validity of every generation's rows, recorded
+in a device error word) in _build_debug/libffs_gb300_debug.so.
 """
 from __future__ import annotations
 
@@ -15,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libffs_gb300.so")
+OUT_DIR_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DIR_DEBUG, "libffs_gb300_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # relocatable device code: the decoder's per-round functions are compiled once
 # (ffs_decoder_*.cu) and called from the kernels of the other units
@@ -38,21 +43,30 @@ def _deps() -> list[str]:
     return d
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build_all(force: bool = False) -> list[str]:
+    """The library and its checked variant."""
+    return [build(force=force), build(force=force, debug=True)]
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
+    out_dir, lib = (OUT_DIR_DEBUG, LIB_DEBUG) if debug else (OUT_DIR, LIB)
+    if not force and up_to_date(debug):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
+    if debug:
+        extra = [*(extra or []), "-DFFS_DEBUG_CHECKS"]
     # the decoder units are the longest compiles: start them first
     srcs = sorted(sources(), key=lambda p: (0 if "ffs_decoder" in p else 1, p))
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
@@ -68,16 +82,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-rdc=true", "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))

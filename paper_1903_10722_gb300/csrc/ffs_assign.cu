@@ -463,7 +463,10 @@ __device__ __forceinline__ void warp_two_point(const int16_t *p1, const int16_t 
             for (int h = 0; h < 8; ++h) {
                 const int i = lo + h;
                 int16_t gv = (i >= l && i <= r) ? ga[h] : gb[h];
-                if (i == mi) gv = assign_reassign(gv, M[i % S], mx);
+                if (i == mi) {
+                    gv = assign_reassign(gv, M[i % S], mx);
+                    if (!FFS_DCHECK(gv >= 0 && gv < M[i % S], kCheckMachineGene)) gv = 0;
+                }
                 out[h] = gv;
             }
             d4[q] = *reinterpret_cast<const int4 *>(out);
@@ -494,10 +497,11 @@ __global__ void k_assign_breed_cellular(GaScalars g, uint32_t island, uint32_t g
         return s == 0 ? c : s == 1 ? up : s == 2 ? down : s == 3 ? west : east;
     };
     int a = slot(b0.x), b = slot(b0.y);
-    const int par1 = (obj[b] < obj[a]) ? b : a;
+    int par1 = (obj[b] < obj[a]) ? b : a;
     a = slot(b0.z);
     b = slot(b0.w);
-    const int par2 = (obj[b] < obj[a]) ? b : a;
+    int par2 = (obj[b] < obj[a]) ? b : a;
+    if (!FFS_DCHECK(par1 >= 0 && par1 < cells && par2 >= 0 && par2 < cells, kCheckParent)) par1 = par2 = c;
     int l = 1, r = 0;     // no crossover: everything from the first winner (passed as p2)
     const int16_t *p1 = pop + (int64_t)par1 * ld, *p2 = p1;
     if (fires(b1.x, g.cell_pc)) {

@@ -177,6 +177,20 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
     }
 }
 
+// The FFS_DEBUG_CHECKS build's validity pass over every instance's current
+// rows (blockIdx.y = instance, one warp per row): warp_check_row.
+__global__ void __launch_bounds__(128) k_check_batch(const BatchInst *insts, int count, const int32_t *cur,
+                                                     int cells, int words_max)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5;
+    for (int i = blockIdx.y; i < count; i += gridDim.y) {
+        const BatchInst &I = insts[i];
+        for (int r = blockIdx.x * 4 + warp; r < cells; r += gridDim.x * 4)
+            warp_check_row(I.pop[cur[0]] + (int64_t)r * I.ld, I.n, I.ms[cur[0]][r], smem + warp * words_max);
+    }
+}
+
 __global__ void k_batch_advance(int32_t *cur, int32_t *gen)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -342,6 +356,7 @@ static int batch_generation(ffs_batch *b, bool advance, unsigned long long *deco
 {
     FFS_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
     if (breed) {
+        NvtxRange r("ffs batch breed");
         const int cells = b->rows * b->cols;
         const int wpi = (cells + kBatchCellsPerWarp - 1) / kBatchCellsPerWarp;
         const int mw = mark_words(b->max_n);
@@ -355,6 +370,7 @@ static int batch_generation(ffs_batch *b, bool advance, unsigned long long *deco
             b->d_inst, b->count, scalars_of(&b->prm), b->d_cur, b->d_gen, b->rows, b->cols, wpi, mw);
         FFS_CUDA_TRY(cudaGetLastError());
     }
+    NvtxRange r("ffs batch decode + replace");
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_batch_cellular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     int grid = b->num_sms * b->blocks_per_sm;
     if (grid > b->n_units) grid = b->n_units;
@@ -365,6 +381,12 @@ static int batch_generation(ffs_batch *b, bool advance, unsigned long long *deco
     if (advance) {
         k_batch_advance<<<1, 32, 0, st>>>(b->d_cur, b->d_gen);
         FFS_CUDA_TRY(cudaGetLastError());
+#ifdef FFS_DEBUG_CHECKS
+        const int cells = b->rows * b->cols, words = (b->max_n + 31) >> 5;
+        k_check_batch<<<dim3(std::min((cells + 3) / 4, 1024), std::min(b->count, 65535)), 128, 4 * words * 4, st>>>(
+            b->d_inst, b->count, b->d_cur, cells, words);
+        FFS_CUDA_TRY(cudaGetLastError());
+#endif
     }
     return FFS_OK;
 }
@@ -495,6 +517,17 @@ int ffs_batch_step(ffs_batch *b, int32_t n_generations, ffs_stream stream)
     if (!b) return set_error(FFS_EINVAL, "NULL batch");
     if (n_generations < 0) return set_error(FFS_EINVAL, "n_generations %d < 0", n_generations);
     if (n_generations == 0) return FFS_OK;
+    NvtxRange call("ffs_batch_step");
+    if (eager_generations()) {
+        for (int g = 0; g < n_generations; ++g) {
+            NvtxRange gen("ffs batch generation");
+            int rc = batch_generation(b, true, b->d_decoded, (cudaStream_t)stream);
+            if (rc) return rc;
+            b->host_cur ^= 1;
+            b->host_gen += 1;
+        }
+        return FFS_OK;
+    }
     if (!b->graph) {
         if (!b->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
@@ -525,6 +558,7 @@ int ffs_batch_autotune(ffs_batch *b, int32_t repeats, ffs_stream stream, int32_t
                        float *best_ms)
 {
     clear_error();
+    NvtxRange call("ffs_batch_autotune");
     if (!b) return set_error(FFS_EINVAL, "NULL batch");
     if (repeats < 1) repeats = 1;
     cudaStream_t st = (cudaStream_t)stream;

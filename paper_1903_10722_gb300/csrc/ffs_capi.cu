@@ -1,6 +1,7 @@
 // ffs_capi.cu -- C ABI entry points: errors, instances, the batched decoder,
 // Philox draws and population initialisation.
 #include <climits>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -306,11 +307,60 @@ int launch_init(const ffs_instance *inst, uint64_t seed, uint32_t island, int ki
 
 }  // namespace fgpu
 
+#ifdef FFS_DEBUG_CHECKS
+namespace fgpu {
+__device__ int g_ffs_check_error = 0;
+}
+#endif
+
+namespace fgpu {
+bool eager_generations()
+{
+    static const bool eager = [] {
+        const char *v = getenv("FFS_EAGER");
+        return v && v[0] && strcmp(v, "0") != 0;
+    }();
+    return eager;
+}
+}  // namespace fgpu
+
 using namespace fgpu;
 
 extern "C" {
 
 const char *ffs_last_error(void) { return g_err.c_str(); }
+
+int ffs_debug_checks(int32_t *enabled)
+{
+    clear_error();
+    if (!enabled) return set_error(FFS_EINVAL, "NULL argument");
+#ifdef FFS_DEBUG_CHECKS
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    return FFS_OK;
+}
+
+int ffs_debug_check_error(int32_t *code, int32_t reset, ffs_stream stream)
+{
+    clear_error();
+    if (!code) return set_error(FFS_EINVAL, "NULL argument");
+    *code = 0;
+#ifdef FFS_DEBUG_CHECKS
+    cudaStream_t st = (cudaStream_t)stream;
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    FFS_CUDA_TRY(cudaMemcpyFromSymbol(code, g_ffs_check_error, sizeof(int32_t)));
+    if (reset) {
+        const int32_t zero = 0;
+        FFS_CUDA_TRY(cudaMemcpyToSymbol(g_ffs_check_error, &zero, sizeof(int32_t)));
+    }
+#else
+    (void)reset;
+    (void)stream;
+#endif
+    return FFS_OK;
+}
 
 void ffs_params_default(ffs_params *p)
 {

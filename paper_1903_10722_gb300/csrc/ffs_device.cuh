@@ -13,6 +13,32 @@ namespace fgpu {
 constexpr int kMaxM = 32;        // machines per stage after clamping to n
 constexpr int kMaxStages = 64;
 
+// Device-side checks of the FFS_DEBUG_CHECKS build: FFS_DCHECK(cond, code)
+// is cond; when it fails, the first failing check's code goes to the device
+// error word (read with ffs_debug_check_error) and the caller skips the
+// access it guards.  In the normal build it is `true` and costs nothing.
+// Codes: 1 a generation's row is not a permutation of [0, n) (or its
+// makespan is negative), 2 a tournament parent outside the torus, 3 a
+// crossover cut outside the row, 4 a crossover write outside the row, 5 a
+// migration row outside its island, 6 a surrogate ring slot outside the
+// ring, 7 a surrogate pick outside the candidates, 8 a machine gene outside
+// its stage.
+enum : int {
+    kCheckPermutation = 1, kCheckParent = 2, kCheckCut = 3, kCheckWrite = 4, kCheckMigrationRow = 5,
+    kCheckRingSlot = 6, kCheckPick = 7, kCheckMachineGene = 8
+};
+#ifdef FFS_DEBUG_CHECKS
+extern __device__ int g_ffs_check_error;
+__device__ __forceinline__ bool ffs_dcheck(bool ok, int code)
+{
+    if (!ok) atomicCAS(&g_ffs_check_error, 0, code);
+    return ok;
+}
+#define FFS_DCHECK(cond, code) ::fgpu::ffs_dcheck((cond), (code))
+#else
+#define FFS_DCHECK(cond, code) true
+#endif
+
 // Purpose codes of the Philox counter's fourth word (bits 24..31):
 // surrogate candidate k of a cell uses kPurposeSurrogateBase + k (k < 16),
 // the surrogate's training-batch sampling kPurposeTrainSample, its weight

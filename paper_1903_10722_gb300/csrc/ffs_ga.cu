@@ -600,10 +600,17 @@ __global__ void __launch_bounds__(kRankMergeThreads) k_rank_merge(const IslandDe
 
 // One warp per migrated row: island i's t-th best onto island (i+1)'s t-th worst.
 __global__ void k_ring_copy(const IslandDesc *desc, int I, const int32_t *cur, int ld, int total_rows,
-                            const int32_t *gate, int gap)
+                            const int32_t *gate, int gap, unsigned long long *mig)
 {
     if (!migration_due(gate, gap)) return;
     const int lane = threadIdx.x & 31;
+    // migrations received: island j takes the rows its ring predecessor sends
+    if (blockIdx.x == 0 && (int)threadIdx.x < I) {
+        const int j = threadIdx.x, i = (j + I - 1) % I;
+        const int sent = desc[i].k_ring;
+        mig[2 * j] += 1ull;
+        mig[2 * j + 1] += (unsigned long long)sent;
+    }
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total_rows; w += (gridDim.x * blockDim.x) >> 5) {
         int i = 0;
         while (i + 1 < I && desc[i + 1].ring_off <= w) ++i;
@@ -611,6 +618,7 @@ __global__ void k_ring_copy(const IslandDesc *desc, int I, const int32_t *cur, i
         const int j = (i + 1) % I;
         const IslandDesc &s = desc[i], &dd = desc[j];
         const int src = s.order[t], dst = dd.order[dd.N - 1 - t];
+        if (!FFS_DCHECK(src >= 0 && src < s.N && dst >= 0 && dst < dd.N, kCheckMigrationRow)) continue;
         const int4 *from = reinterpret_cast<const int4 *>(s.pop[cur[i]] + (int64_t)src * ld);
         int4 *to = reinterpret_cast<int4 *>(dd.pop[cur[j]] + (int64_t)dst * ld);
         for (int k = lane; k < (ld >> 3); k += 32) to[k] = from[k];
@@ -621,7 +629,8 @@ __global__ void k_ring_copy(const IslandDesc *desc, int I, const int32_t *cur, i
 // Penetration (Eq. (1)-(2) for makespans): one thread per pair (2q, 2q+1)
 // decides the signed count; then one warp per candidate row copies.
 __global__ void k_penetration(const IslandDesc *desc, int pairs, const int32_t *cur, long long theta_num,
-                              long long theta_den, int32_t *counts, const int32_t *gate, int gap)
+                              long long theta_den, int32_t *counts, const int32_t *gate, int gap,
+                              unsigned long long *mig)
 {
     if (!migration_due(gate, gap)) return;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -637,6 +646,11 @@ __global__ void k_penetration(const IslandDesc *desc, int pairs, const int32_t *
         if (cA > cB) cnt = -cnt;
     }
     counts[q] = (int32_t)cnt;
+    if (cnt != 0) {   // migrations received by the pair's other island
+        const int di = cnt > 0 ? 2 * q + 1 : 2 * q;
+        mig[2 * di] += 1ull;
+        mig[2 * di + 1] += (unsigned long long)(cnt > 0 ? cnt : -cnt);
+    }
 }
 
 __global__ void k_penetration_copy(const IslandDesc *desc, int pairs, const int32_t *cur, int ld,
@@ -653,11 +667,87 @@ __global__ void k_penetration_copy(const IslandDesc *desc, int pairs, const int3
         const int si = c > 0 ? 2 * q : 2 * q + 1, di = c > 0 ? 2 * q + 1 : 2 * q;
         const IslandDesc &s = desc[si], &dd = desc[di];
         const int src = s.order[t], dst = dd.order[dd.N - 1 - t];
+        if (!FFS_DCHECK(src >= 0 && src < s.N && dst >= 0 && dst < dd.N, kCheckMigrationRow)) continue;
         const int4 *from = reinterpret_cast<const int4 *>(s.pop[cur[si]] + (int64_t)src * ld);
         int4 *to = reinterpret_cast<int4 *>(dd.pop[cur[di]] + (int64_t)dst * ld);
         for (int kk = lane; kk < (ld >> 3); kk += 32) to[kk] = from[kk];
         if (lane == 0) dd.ms[cur[di]][dst] = s.ms[cur[si]][src];
     }
+}
+
+// Per-island metrics of the current generation, one block per island: the
+// best, worst and sum of the valid makespans (a row with -1 is not
+// counted), the valid rows, the best makespan any pass has seen so far
+// (best_so_far[i], updated here) and the migrations the island has
+// received (events, rows).  Record r of island i goes to
+// out[((gen[i] % cap) * I + i) * kStatWords].
+constexpr int kStatWords = 8;
+
+__global__ void __launch_bounds__(256) k_island_stats(const IslandDesc *desc, int I, const int32_t *cur,
+                                                     const int32_t *gen, int32_t *best_so_far,
+                                                     const unsigned long long *mig, long long *out, int cap)
+{
+    __shared__ int s_lo[8], s_hi[8], s_cnt[8];
+    __shared__ long long s_sum[8];
+    const int i = blockIdx.x;
+    const IslandDesc &D = desc[i];
+    const int32_t *ms = D.ms[cur[i]];
+    int lo = 0x7FFFFFFF, hi = -1, cnt = 0;
+    long long sum = 0;
+    for (int r = threadIdx.x; r < D.N; r += blockDim.x) {
+        const int v = ms[r];
+        if (v >= 0) {
+            lo = min(lo, v);
+            hi = max(hi, v);
+            sum += v;
+            ++cnt;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+        s_cnt[warp] = cnt;
+        s_sum[warp] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = min(lo, s_lo[w]);
+            hi = max(hi, s_hi[w]);
+            cnt += s_cnt[w];
+            sum += s_sum[w];
+        }
+        const int bsf = cnt > 0 ? min(best_so_far[i], lo) : best_so_far[i];
+        best_so_far[i] = bsf;
+        long long *rec = out + ((long long)(gen[i] % cap) * I + i) * kStatWords;
+        rec[0] = gen[i];
+        rec[1] = cnt > 0 ? lo : -1;
+        rec[2] = hi;
+        rec[3] = sum;
+        rec[4] = cnt;
+        rec[5] = bsf == 0x7FFFFFFF ? -1 : bsf;
+        rec[6] = (long long)mig[2 * i];
+        rec[7] = (long long)mig[2 * i + 1];
+    }
+}
+
+// The FFS_DEBUG_CHECKS build's validity pass over every island's current
+// rows (blockIdx.y = island, one warp per row): warp_check_row.
+__global__ void __launch_bounds__(128) k_check_islands(const IslandDesc *desc, const int32_t *cur, int n, int ld)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int i = blockIdx.y, warp = threadIdx.x >> 5;
+    const int words = (n + 31) >> 5;
+    const IslandDesc &D = desc[i];
+    for (int r = blockIdx.x * 4 + warp; r < D.N; r += gridDim.x * 4)
+        warp_check_row(D.pop[cur[i]] + (int64_t)r * ld, n, D.ms[cur[i]][r], smem + warp * words);
 }
 
 // Advance the generation counter and flip the buffers of islands [i0, i1).
@@ -736,6 +826,12 @@ struct ffs_islands {
     void *d_scratch = nullptr;        // pseudo scratch (shared by the pseudo islands)
     int16_t *d_cell_children = nullptr;   // child rows of the cellular cells (fused generations)
     unsigned long long *d_decoded = nullptr;
+    int32_t *d_best_so_far = nullptr;     // [I] lowest makespan a metrics pass has seen
+    unsigned long long *d_mig = nullptr;  // [I][2] migrations received: events, rows
+    long long *d_stats_now = nullptr;     // [I][kStatWords] the last ffs_islands_stats pass
+    long long *d_hist = nullptr;          // [stats_cap][I][kStatWords] per-generation records
+    int stats_cap = 0;
+    long long stats_from = 0;             // generation of the oldest record kept
     int ring_rows = 0, max_N = 0, min_pair_rows = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_all = nullptr;
@@ -839,12 +935,12 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
         const int warps = S->ring_rows;
         int blocks = (warps * 32 + 255) / 256;
         if (blocks > 1024) blocks = 1024;
-        k_ring_copy<<<blocks, 256, 0, st>>>(S->d_desc, S->I, S->d_cur, S->ld, S->ring_rows, gate, gap);
+        k_ring_copy<<<blocks, 256, 0, st>>>(S->d_desc, S->I, S->d_cur, S->ld, S->ring_rows, gate, gap, S->d_mig);
         FFS_CUDA_TRY(cudaGetLastError());
     } else {
         const int pairs = S->I / 2;
         k_penetration<<<1, 64, 0, st>>>(S->d_desc, pairs, S->d_cur, S->prm.theta_num, S->prm.theta_den,
-                                       S->d_counts, gate, gap);
+                                       S->d_counts, gate, gap, S->d_mig);
         FFS_CUDA_TRY(cudaGetLastError());
         int blocks = (pairs * S->min_pair_rows * 32 + 255) / 256;
         if (blocks > 2048) blocks = 2048;
@@ -854,6 +950,28 @@ static int migrate_launch(ffs_islands *S, int mode, bool gated, cudaStream_t st)
         FFS_CUDA_TRY(cudaGetLastError());
     }
     return FFS_OK;
+}
+
+// The metrics pass over every island (k_island_stats) into `out` (cap
+// records per island).
+static int stats_launch(ffs_islands *S, long long *out, int cap, cudaStream_t st)
+{
+    k_island_stats<<<S->I, 256, 0, st>>>(S->d_desc, S->I, S->d_cur, S->d_gen, S->d_best_so_far, S->d_mig, out, cap);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+// The end of every generation: the metrics record when recording is on, and
+// in the FFS_DEBUG_CHECKS build the validity pass over every island's rows.
+static int record_launch(ffs_islands *S, cudaStream_t st)
+{
+#ifdef FFS_DEBUG_CHECKS
+    const int words = (S->inst->n + 31) >> 5;
+    const int bx = std::min((S->max_N + 3) / 4, 1024);
+    k_check_islands<<<dim3(bx, S->I), 128, 4 * words * 4, st>>>(S->d_desc, S->d_cur, S->inst->n, S->ld);
+    FFS_CUDA_TRY(cudaGetLastError());
+#endif
+    return S->stats_cap > 0 ? stats_launch(S, S->d_hist, S->stats_cap, st) : FFS_OK;
 }
 
 // Screened generation of the cellular islands in `sel`: phase 1 builds every
@@ -948,29 +1066,39 @@ static int screened_generation(ffs_islands *S, bool warm, bool train, cudaStream
     int rc = launch_sur_tick(R->d_ctr, 2, -1, st);
     if (rc) return rc;
     if (!pse.empty()) {
+        NvtxRange r("ffs pseudo islands (side stream)");
         FFS_CUDA_TRY(cudaEventRecord(R->fork_ev, st));
         FFS_CUDA_TRY(cudaStreamWaitEvent(R->side, R->fork_ev, 0));
         if ((rc = islands_generation_launch(S, pse, R->side))) return rc;
     }
     if (train) {
+        NvtxRange r("ffs surrogate training round (side stream)");
         FFS_CUDA_TRY(cudaEventRecord(R->fork2_ev, st));
         FFS_CUDA_TRY(cudaStreamWaitEvent(R->side2, R->fork2_ev, 0));
         if ((rc = surrogate_train_launch(S, R->side2))) return rc;
         FFS_CUDA_TRY(cudaEventRecord(R->join2_ev, R->side2));
     }
-    rc = screened_cellular_launch(S, cel, warm, st, [&](cudaStream_t cs) -> int {
-        if (train) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
-        return FFS_OK;
-    });
-    if (rc) return rc;
+    {
+        NvtxRange r("ffs screened cellular islands: candidates, scores, select");
+        rc = screened_cellular_launch(S, cel, warm, st, [&](cudaStream_t cs) -> int {
+            if (train) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
+            return FFS_OK;
+        });
+        if (rc) return rc;
+    }
     if (!pse.empty()) {
         FFS_CUDA_TRY(cudaEventRecord(R->join_ev, R->side));
         FFS_CUDA_TRY(cudaStreamWaitEvent(st, R->join_ev, 0));
     }
     k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
     FFS_CUDA_TRY(cudaGetLastError());
-    if (S->prm.migration_gap > 0) return migrate_launch(S, S->prm.migration_mode, true, st);
-    return FFS_OK;
+    if (S->prm.migration_gap > 0) {
+        NvtxRange r("ffs migration (gated by the gap)");
+        int rc = migrate_launch(S, S->prm.migration_mode, true, st);
+        if (rc) return rc;
+    }
+    NvtxRange r("ffs metrics / checks");
+    return record_launch(S, st);
 }
 
 // Capture `body` on the islands' capture stream into an executable graph.
@@ -1000,16 +1128,21 @@ static int generation_all(ffs_islands *S, cudaStream_t st)
 {
     std::vector<int> all(S->I);
     for (int i = 0; i < S->I; ++i) all[i] = i;
-    int rc0 = islands_generation_launch(S, all, st);
-    if (rc0) return rc0;
+    {
+        NvtxRange r("ffs breed + decode + replace");
+        int rc0 = islands_generation_launch(S, all, st);
+        if (rc0) return rc0;
+    }
     // flip to the new generation first: migration works on it
     k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
     FFS_CUDA_TRY(cudaGetLastError());
     if (S->prm.migration_gap > 0) {
+        NvtxRange r("ffs migration (gated by the gap)");
         int rc = migrate_launch(S, S->prm.migration_mode, true, st);
         if (rc) return rc;
     }
-    return FFS_OK;
+    NvtxRange r("ffs metrics / checks");
+    return record_launch(S, st);
 }
 
 }  // namespace fgpu
@@ -1075,7 +1208,19 @@ static void islands_free(ffs_islands *S)
     if (S->graph_all) cudaGraphExecDestroy(S->graph_all);
     if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void *p : S->allocs) cudaFree(p);
+    if (S->d_hist) cudaFree(S->d_hist);
     delete S;
+}
+
+// Captured generation graphs include the metrics record or not: after the
+// recording is switched, they are captured again.
+static void drop_generation_graphs(ffs_islands *S)
+{
+    if (S->graph_all) {
+        cudaGraphExecDestroy(S->graph_all);
+        S->graph_all = nullptr;
+    }
+    if (S->sur) S->sur->drop_graphs();
 }
 
 int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t n_cellular, int32_t rows,
@@ -1165,6 +1310,9 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
     S->d_counts = (int32_t *)alloc(4 * (S->I / 2 + 1));
     S->d_decoded = (unsigned long long *)alloc(8);
     S->d_rank_keys = (unsigned long long *)alloc((size_t)S->total_rows * 8);
+    S->d_best_so_far = (int32_t *)alloc(4 * (size_t)S->I);
+    S->d_mig = (unsigned long long *)alloc(16 * (size_t)S->I);
+    S->d_stats_now = (long long *)alloc(8 * (size_t)kStatWords * S->I);
     int n_pseudo_islands = 0;
     for (int i = 0; i < S->I; ++i) n_pseudo_islands += S->kind[i] == 1;
     if (max_pseudo > 0)
@@ -1176,14 +1324,18 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
                        n_pseudo_islands <= kMaxBatch;
     if (fused) S->d_cell_children = (int16_t *)alloc((size_t)n_cellular_islands * S->rows * S->cols * S->ld * 2);
     if (!S->d_desc || !S->d_cur || !S->d_gen || !S->d_counts || !S->d_decoded || !S->d_rank_keys ||
-        (max_pseudo > 0 && !S->d_scratch) || (fused && !S->d_cell_children)) {
+        !S->d_best_so_far || !S->d_mig || !S->d_stats_now || (max_pseudo > 0 && !S->d_scratch) ||
+        (fused && !S->d_cell_children)) {
         islands_free(S);
         return set_error(FFS_ENOMEM, "island state");
     }
     int rc = FFS_OK;
     if (cudaMemcpyAsync(S->d_desc, S->desc.data(), sizeof(IslandDesc) * S->I, cudaMemcpyHostToDevice, st) ||
         cudaMemsetAsync(S->d_cur, 0, 4 * S->I, st) || cudaMemsetAsync(S->d_gen, 0, 4 * S->I, st) ||
-        cudaMemsetAsync(S->d_decoded, 0, 8, st))
+        cudaMemsetAsync(S->d_decoded, 0, 8, st) || cudaMemsetAsync(S->d_mig, 0, 16 * (size_t)S->I, st))
+        rc = set_error(FFS_ECUDA, "island state initialisation");
+    const std::vector<int32_t> none(S->I, 0x7FFFFFFF);   // no makespan seen yet
+    if (!rc && cudaMemcpy(S->d_best_so_far, none.data(), 4 * (size_t)S->I, cudaMemcpyHostToDevice) != cudaSuccess)
         rc = set_error(FFS_ECUDA, "island state initialisation");
     for (int i = 0; i < S->I && !rc; ++i) {
         rc = launch_init(inst, prm->seed, (uint32_t)i, S->kind[i], S->size[i], S->ld, S->desc[i].pop[0], st);
@@ -1473,12 +1625,15 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
     if (n_generations < 0) return set_error(FFS_EINVAL, "n_generations %d < 0", n_generations);
     if (n_generations == 0) return FFS_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxRange call("ffs_island_step");
     if (island >= 0) {
         for (int g = 0; g < n_generations; ++g) {
+            NvtxRange gen("ffs generation (one island)");
             int rc = islands_generation_launch(S, std::vector<int>{island}, st);
             if (rc) return rc;
             k_advance<<<1, 32, 0, st>>>(S->d_cur, S->d_gen, island, island + 1);
             FFS_CUDA_TRY(cudaGetLastError());
+            if ((rc = record_launch(S, st))) return rc;
             S->host_cur[island] ^= 1;
             S->host_gen[island] += 1;
             if (S->sur && S->kind[island] == 0) S->sur->ring_count += (long long)S->rows * S->cols;
@@ -1502,13 +1657,19 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
                                (G - 1) % R->sp.train_every == 0 &&
                                std::min(R->ring_count, R->ring_cap - R->cells_total) >= R->sp.train_batch)
                                   ? 1 : 0;
-            if (!R->g_gen[warm][train]) {
-                int rc = capture_graph(S, &R->g_gen[warm][train], [&](cudaStream_t cs) {
-                    return screened_generation(S, warm != 0, train != 0, cs);
-                });
+            NvtxRange gen(train ? "ffs screened generation + training round" : "ffs screened generation");
+            if (eager_generations()) {
+                int rc = screened_generation(S, warm != 0, train != 0, st);
                 if (rc) return rc;
+            } else {
+                if (!R->g_gen[warm][train]) {
+                    int rc = capture_graph(S, &R->g_gen[warm][train], [&](cudaStream_t cs) {
+                        return screened_generation(S, warm != 0, train != 0, cs);
+                    });
+                    if (rc) return rc;
+                }
+                FFS_CUDA_TRY(cudaGraphLaunch(R->g_gen[warm][train], st));
             }
-            FFS_CUDA_TRY(cudaGraphLaunch(R->g_gen[warm][train], st));
             for (int i = 0; i < S->I; ++i) {
                 S->host_cur[i] ^= 1;
                 S->host_gen[i] += 1;
@@ -1518,7 +1679,20 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
         }
         return FFS_OK;
     }
+    if (eager_generations()) {
+        for (int g = 0; g < n_generations; ++g) {
+            NvtxRange gen("ffs generation");
+            int rc = generation_all(S, st);
+            if (rc) return rc;
+            for (int i = 0; i < S->I; ++i) {
+                S->host_cur[i] ^= 1;
+                S->host_gen[i] += 1;
+            }
+        }
+        return FFS_OK;
+    }
     if (!S->graph_all) {
+        NvtxRange cap("ffs capture of the generation graph");
         if (!S->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         FFS_CUDA_TRY(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -1537,6 +1711,7 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
         }
     }
     for (int g = 0; g < n_generations; ++g) {
+        NvtxRange gen("ffs generation (graph)");
         FFS_CUDA_TRY(cudaGraphLaunch(S->graph_all, st));
         for (int i = 0; i < S->I; ++i) {
             S->host_cur[i] ^= 1;
@@ -1549,6 +1724,7 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
 int ffs_migrate(ffs_islands *S, int32_t mode, ffs_stream stream)
 {
     clear_error();
+    NvtxRange call("ffs_migrate");
     if (!S) return set_error(FFS_EINVAL, "NULL islands");
     if (mode < FFS_MIG_NONE || mode > FFS_MIG_PENETRATION) return set_error(FFS_EINVAL, "mode %d", mode);
     return migrate_launch(S, mode, false, (cudaStream_t)stream);
@@ -1642,6 +1818,74 @@ int ffs_islands_best(const ffs_islands *S, int32_t *best_ms, int32_t *best_islan
     return FFS_OK;
 }
 
+int ffs_islands_stats(ffs_islands *S, int64_t *out, ffs_stream stream)
+{
+    clear_error();
+    if (!S || !out) return set_error(FFS_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = stats_launch(S, S->d_stats_now, 1, st);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaMemcpyAsync(out, S->d_stats_now, 8 * (size_t)kStatWords * S->I, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
+int ffs_islands_record_stats(ffs_islands *S, int32_t capacity, ffs_stream stream)
+{
+    clear_error();
+    if (!S) return set_error(FFS_EINVAL, "NULL islands");
+    if (capacity < 0 || capacity > (1 << 24)) return set_error(FFS_EINVAL, "capacity %d outside [0, 2^24]", capacity);
+    for (int i = 1; i < S->I; ++i)
+        if (S->host_gen[i] != S->host_gen[0])
+            return set_error(FFS_EINVAL, "islands were stepped separately; generation counts differ");
+    cudaStream_t st = (cudaStream_t)stream;
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (S->d_hist) {
+        FFS_CUDA_TRY(cudaFree(S->d_hist));
+        S->d_hist = nullptr;
+    }
+    S->stats_cap = 0;
+    drop_generation_graphs(S);
+    if (capacity == 0) return FFS_OK;
+    if (cudaMalloc(&S->d_hist, 8 * (size_t)kStatWords * S->I * capacity) != cudaSuccess) {
+        (void)cudaGetLastError();
+        S->d_hist = nullptr;
+        return set_error(FFS_ENOMEM, "metrics history of %d generations", capacity);
+    }
+    S->stats_cap = capacity;
+    S->stats_from = S->host_gen[0];
+    return record_launch(S, st);   // the current generation is the first record
+}
+
+int ffs_islands_stats_history(const ffs_islands *S, int64_t *out, int32_t max_records, int32_t *count,
+                              ffs_stream stream)
+{
+    clear_error();
+    if (!S || !count) return set_error(FFS_EINVAL, "NULL argument");
+    *count = 0;
+    if (!S->stats_cap) return FFS_OK;
+    for (int i = 1; i < S->I; ++i)
+        if (S->host_gen[i] != S->host_gen[0])
+            return set_error(FFS_EINVAL, "islands were stepped separately; generation counts differ");
+    const long long G = S->host_gen[0];
+    const long long first = std::max(S->stats_from, G - S->stats_cap + 1);
+    const int n = (int)(G - first + 1);
+    *count = n;
+    if (!out) return FFS_OK;
+    if (max_records < n) return set_error(FFS_EINVAL, "max_records %d < %d records kept", max_records, n);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the kept records are slots first % cap .. G % cap of the ring: one copy,
+    // or two where the range wraps
+    const long long per = (long long)kStatWords * S->I;   // words of one generation, every island
+    const long long s0 = first % S->stats_cap, s1 = G % S->stats_cap;
+    const long long a = s0 <= s1 ? n : S->stats_cap - s0;
+    FFS_CUDA_TRY(cudaMemcpyAsync(out, S->d_hist + s0 * per, (size_t)(a * per) * 8, cudaMemcpyDeviceToHost, st));
+    if (a < n)
+        FFS_CUDA_TRY(cudaMemcpyAsync(out + a * per, S->d_hist, (size_t)((n - a) * per) * 8, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    return FFS_OK;
+}
+
 int ffs_islands_decoded(const ffs_islands *S, int64_t *count, ffs_stream stream)
 {
     clear_error();
@@ -1676,12 +1920,14 @@ struct IslandsBlobHeader {
 struct IslandBlobEntry {
     int32_t kind, size;
     int64_t generation;
+    int32_t best_so_far, pad;
+    int64_t mig_events, mig_rows;
 };
 struct SurrogateBlob {
     int32_t candidates, pad;
     int64_t ring_cap, ring_count, train_rounds, valid;
 };
-constexpr uint32_t kIslandsBlobMagic = 0x49534646u, kIslandsBlobVersion = 1;
+constexpr uint32_t kIslandsBlobMagic = 0x49534646u, kIslandsBlobVersion = 2;
 
 static int64_t r16(int64_t b) { return (b + 15) / 16 * 16; }
 
@@ -1706,6 +1952,7 @@ int64_t ffs_checkpoint_bytes(const ffs_islands *S) { return S ? islands_blob_byt
 int ffs_checkpoint_save(const ffs_islands *S, void *host, int64_t capacity, ffs_stream stream)
 {
     clear_error();
+    NvtxRange call("ffs_checkpoint_save");
     if (!S || !host) return set_error(FFS_EINVAL, "NULL argument");
     const int64_t need = islands_blob_bytes(S);
     if (capacity < need) return set_error(FFS_EINVAL, "capacity %lld < %lld bytes", (long long)capacity, (long long)need);
@@ -1726,9 +1973,21 @@ int ffs_checkpoint_save(const ffs_islands *S, void *host, int64_t capacity, ffs_
     FFS_CUDA_TRY(cudaStreamSynchronize(st));
     h.decoded = (int64_t)dec;
     memcpy(w.take(r16(sizeof(h))), &h, sizeof(h));
+    std::vector<int32_t> bsf(S->I);
+    std::vector<unsigned long long> mig(2 * (size_t)S->I);
+    FFS_CUDA_TRY(cudaMemcpyAsync(bsf.data(), S->d_best_so_far, 4 * (size_t)S->I, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaMemcpyAsync(mig.data(), S->d_mig, 16 * (size_t)S->I, cudaMemcpyDeviceToHost, st));
+    FFS_CUDA_TRY(cudaStreamSynchronize(st));
     char *ent = w.take(r16((int64_t)S->I * sizeof(IslandBlobEntry)));
     for (int i = 0; i < S->I; ++i) {
-        const IslandBlobEntry e{S->kind[i], S->size[i], S->host_gen[i]};
+        IslandBlobEntry e;
+        memset(&e, 0, sizeof(e));
+        e.kind = S->kind[i];
+        e.size = S->size[i];
+        e.generation = S->host_gen[i];
+        e.best_so_far = bsf[i];
+        e.mig_events = (int64_t)mig[2 * i];
+        e.mig_rows = (int64_t)mig[2 * i + 1];
         memcpy(ent + i * sizeof(IslandBlobEntry), &e, sizeof(e));
     }
     for (int i = 0; i < S->I; ++i) {
@@ -1765,6 +2024,7 @@ int ffs_checkpoint_save(const ffs_islands *S, void *host, int64_t capacity, ffs_
 int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stream stream)
 {
     clear_error();
+    NvtxRange call("ffs_checkpoint_load");
     if (!S || !host) return set_error(FFS_EINVAL, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     BlobReader r{static_cast<const char *>(host), size};
@@ -1791,6 +2051,8 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
             return set_error(FFS_EINVAL, "island %d differs in kind or size", i);
         if (es[i].generation < 0 || es[i].generation > 0x7FFFFFFF)
             return set_error(FFS_EINVAL, "island %d generation %lld", i, (long long)es[i].generation);
+        if (es[i].best_so_far < 0 || es[i].mig_events < 0 || es[i].mig_rows < 0)
+            return set_error(FFS_EINVAL, "island %d metrics counters", i);
     }
     std::vector<const char *> rows(S->I), mss(S->I);
     for (int i = 0; i < S->I; ++i) {
@@ -1829,6 +2091,15 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
     FFS_CUDA_TRY(cudaMemcpyAsync(S->d_gen, gen.data(), 4 * (size_t)S->I, cudaMemcpyHostToDevice, st));
     const unsigned long long dec = (unsigned long long)h.decoded;
     FFS_CUDA_TRY(cudaMemcpyAsync(S->d_decoded, &dec, 8, cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> bsf(S->I);
+    std::vector<unsigned long long> mig(2 * (size_t)S->I);
+    for (int i = 0; i < S->I; ++i) {
+        bsf[i] = es[i].best_so_far;
+        mig[2 * i] = (unsigned long long)es[i].mig_events;
+        mig[2 * i + 1] = (unsigned long long)es[i].mig_rows;
+    }
+    FFS_CUDA_TRY(cudaMemcpyAsync(S->d_best_so_far, bsf.data(), 4 * (size_t)S->I, cudaMemcpyHostToDevice, st));
+    FFS_CUDA_TRY(cudaMemcpyAsync(S->d_mig, mig.data(), 16 * (size_t)S->I, cudaMemcpyHostToDevice, st));
     if (S->sur) {
         SurrogateState *R = S->sur;
         if (sb.valid > 0) {

@@ -42,7 +42,9 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
         int16_t *child = (int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.child, j);
         const int l = __shfl_sync(0xFFFFFFFFu, me.l, j);
         const int r = __shfl_sync(0xFFFFFFFFu, me.r, j);
-        const bool cross = __shfl_sync(0xFFFFFFFFu, (int)me.cross, j) != 0;
+        // (a cut outside the row is recorded and the child copies p1)
+        const bool cross = __shfl_sync(0xFFFFFFFFu, (int)me.cross, j) != 0 &&
+                           FFS_DCHECK(l >= 0 && l <= r && r < n, kCheckCut);
         if (!cross) {
             const int4 *s4 = reinterpret_cast<const int4 *>(p1);
             int4 *d4 = reinterpret_cast<int4 *>(child);
@@ -110,13 +112,38 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
                 if ((take >> u) & 1u) {
                     int pos = first + __popc(take & ((1u << u) - 1u));
                     if (pos >= n) pos -= n;
-                    child[pos] = (int16_t)gv[u];
+                    if (FFS_DCHECK(pos >= 0 && pos < n, kCheckWrite)) child[pos] = (int16_t)gv[u];
                 }
             }
             placed += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         __syncwarp();
     }
+}
+
+// The FFS_DEBUG_CHECKS build's validity check of one row by one warp: every
+// gene in [0, n), no gene twice (a bit per job in `bits`, (n + 31) / 32
+// words of this warp's shared memory), and a makespan >= 0; a failure is
+// recorded as kCheckPermutation.
+__device__ __forceinline__ void warp_check_row(const int16_t *row, int n, int32_t ms, uint32_t *bits)
+{
+    const int lane = threadIdx.x & 31;
+    const int words = (n + 31) >> 5;
+    for (int w = lane; w < words; w += 32) bits[w] = 0u;
+    __syncwarp();
+    bool ok = ms >= 0;
+    for (int i = lane; i < n; i += 32) {
+        const int gj = row[i];
+        if (gj < 0 || gj >= n) {
+            ok = false;
+        } else {
+            const uint32_t bit = 1u << (gj & 31);
+            if (atomicOr(&bits[gj >> 5], bit) & bit) ok = false;
+        }
+    }
+    ok = __all_sync(0xFFFFFFFFu, ok);
+    if (lane == 0) (void)FFS_DCHECK(ok, kCheckPermutation);
+    __syncwarp();
 }
 
 // Warp-cooperative row copies: lane j's (src, dst) pair when `active`.  Four
@@ -231,10 +258,12 @@ __device__ __forceinline__ void cellular_warp_breed(const IslandRef &ref, const 
             return k == 0 ? c : k == 1 ? up : k == 2 ? down : k == 3 ? west : east;
         };
         int a = slot(b0.x), b = slot(b0.y);
-        const int par1 = (msin[b] < msin[a]) ? b : a;
+        int par1 = (msin[b] < msin[a]) ? b : a;
         a = slot(b0.z);
         b = slot(b0.w);
-        const int par2 = (msin[b] < msin[a]) ? b : a;
+        int par2 = (msin[b] < msin[a]) ? b : a;
+        if (!FFS_DCHECK(par1 >= 0 && par1 < rows * cols && par2 >= 0 && par2 < rows * cols, kCheckParent))
+            par1 = par2 = c;
         job.p1 = pin + (int64_t)par1 * ld;
         job.p2 = pin + (int64_t)par2 * ld;
         job.cross = fires(b1.x, g.cell_pc);

@@ -7,11 +7,26 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ffs.h"
 #include "ffs_device.cuh"
 
 namespace fgpu {
+
+// An NVTX range for the scope (a profiler shows the library's calls and the
+// phases of a generation; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// FFS_EAGER=1 in the environment: generations run launch by launch instead
+// of being replayed from captured CUDA graphs, so that each phase's NVTX
+// range covers its own kernels in a profiler's timeline.
+bool eager_generations();
 
 // Thread-local error message; returns the status for one-line returns.
 int set_error(int status, const char *fmt, ...);

@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
         int pick = 0;
         for (int k = 1; k < K; ++k)
             if (sc[k] < sc[pick]) pick = k;
+        if (!FFS_DCHECK(pick >= 0 && pick < K, kCheckPick)) pick = 0;
         const int16_t *drow = cand + ((int64_t)gq * K + pick) * ld;
         const int32_t ms = decode_chromosome(Ls, drow, region, T, tab, wst);
         bool better = false, keep = false;
@@ -266,6 +267,7 @@ __global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, l
         const U4 d = draw_block(seed, kPurposeTrainSample, 0u, draw_gen, (uint32_t)b, 0u);
         const long long i = (long long)(((unsigned long long)d.x * (unsigned long long)valid) >> 32);
         const long long slot = newest - i >= 0 ? newest - i : newest - i + ring_cap;
+        if (!FFS_DCHECK(slot >= 0 && slot < ring_cap, kCheckRingSlot)) continue;   // warp-uniform
         warp_write_features(ring_rows + slot * ld, n, P, inst_feat, nfeat, X + (int64_t)b * ldx, ldx);
         if (lane == 0) targets[b] = ((float)ring_ms[slot] - norm[0]) * norm[1];
     }

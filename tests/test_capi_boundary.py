@@ -65,3 +65,13 @@ def test_null_handles_are_rejected():
     assert lib.ffs_migrate(None, 1, None) == ffs.FFS_EINVAL
     assert lib.ffs_pseudo_scratch_bytes(-1, 8) == -1
     assert lib.ffs_pseudo_scratch_bytes(4096, 104) >= 4096 * 104 * 2 + 4096 * 4
+
+
+def test_normal_build_reports_no_checks():
+    """The library loaded by default is the unchecked one; its check word is
+    always 0 (no device access)."""
+    import paper_1903_10722_gb300 as ffs
+    if ffs.debug_checks_requested():
+        pytest.skip("the checked build is selected in this environment")
+    assert ffs.ffs_debug_checks() is False
+    assert ffs.ffs_debug_check_error(stream=0) == 0
