@@ -181,6 +181,145 @@ def cpu_oracle_rate(workload: str, budget_s: float = 12.0, threads: int = 1):
     return evals / dt, sample, threads
 
 
+def _shard_eval(args):
+    """One process's shard of the sharded oracle figure: load the oracle,
+    wait for the start time, evaluate rows [a, b) of the seeded batch."""
+    import numpy as np
+
+    import oracle as orc
+    from ffs_workloads import random_population, workload_instance
+    a, b, start_at = args
+    spec = workload_instance("scale_500x20")
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    pop = random_population(spec.n, 4096, seed=11)[a:b]
+    orc.eval_population(o, pop[:1])           # library loaded before the clock
+    while time.time() < start_at:
+        time.sleep(0.001)
+    t0 = time.perf_counter()
+    ms = orc.eval_population(o, pop)
+    return float(time.perf_counter() - t0), int(np.asarray(ms).sum())
+
+
+def run_oracle_full(args):
+    """The oracle's full GA on the two small configurations, and the batch
+    decoder on every host core as chromosome-sharded processes; one JSON line.
+
+      * tiny (20 x 5, one 8 x 8 torus, 100 generations): the oracle on one
+        core;
+      * dual_100x10 (64 x 64 torus + pseudo 4096, ring 2 % every 50, 1000
+        generations): the oracle with each island's cells / pairs split over
+        one thread per core, and a 20-generation sample on one core;
+      * 4096 random job orders of the 500 x 20 instance decoded by `nproc`
+        processes (spawned; each takes a contiguous shard).
+    With a GPU, the same two GA runs through the library (one
+    ffs_island_step call each, CUDA-event time, graph capture before the
+    clock) and their final best makespans and decode counts against the
+    oracle's."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import oracle as orc
+    from ffs_workloads import WORKLOADS, workload_instance
+
+    cores = host_cores()
+    out = {"metric": "oracle wall-clock of the full GA (configs tiny and dual_100x10) and sharded decoding",
+           "workload": "oracle_full", "cores": cores}
+    gpu = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+            import paper_1903_10722_gb300 as gpu
+    except ImportError:
+        gpu = None
+
+    def gpu_run(name):
+        w = WORKLOADS[name]
+        spec = workload_instance(name)
+        inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+        prm = gpu.ffs_params_default()
+        if w.get("migration") == "ring":
+            prm.migration_mode, prm.migration_gap = gpu.FFS_MIG_RING, w["gap"]
+            prm.ring_num, prm.ring_den = w["mig_num"], w["mig_den"]
+        isl = gpu.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
+        gpu.ffs_island_step(isl, -1, 1)               # generation 1 captures the graph, before the clock
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        gpu.ffs_island_step(isl, -1, w["generations"] - 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        return {"seconds_generations_2_on": t, "full_run_estimate_s": t * w["generations"] / (w["generations"] - 1),
+                "best": int(gpu.ffs_islands_best(isl)[0]), "decoded": int(gpu.ffs_islands_decoded(isl))}
+
+    # config tiny: one core
+    w = WORKLOADS["tiny"]
+    spec = workload_instance("tiny")
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    ga = orc.IslandGA(o, orc.Params(seed=7), 1, w["rows"], w["cols"], 0, 0)
+    d0 = ga.decoded
+    t0 = time.perf_counter()
+    for _ in range(w["generations"]):
+        ga.step()
+    dt = time.perf_counter() - t0
+    tiny = {"generations": w["generations"], "oracle_seconds": dt, "oracle_cores": 1,
+            "oracle_evals_per_s": (ga.decoded - d0) / dt, "best": ga.best(), "decoded": ga.decoded}
+    if gpu is not None:
+        g = gpu_run("tiny")
+        tiny["gpu"] = g
+        tiny["gpu_matches_oracle"] = g["best"] == ga.best() and g["decoded"] == ga.decoded
+    out["tiny"] = tiny
+
+    # config dual_100x10: every core (threads over each island's cells / pairs), then a one-core sample
+    w = WORKLOADS["dual_100x10"]
+    spec = workload_instance("dual_100x10")
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    with cf.ThreadPoolExecutor(cores) as pool:
+        ga = orc.IslandGA(o, orc.Params(seed=7), 1, w["rows"], w["cols"], 1, w["pseudo_size"], pool=pool,
+                          parts=cores)
+        d0 = ga.decoded
+        t0 = time.perf_counter()
+        for g in range(1, w["generations"] + 1):
+            ga.step_threads(pool, cores)
+            if g % w["gap"] == 0:
+                ga.migrate_ring(w["mig_num"], w["mig_den"])
+        dt = time.perf_counter() - t0
+    dual = {"generations": w["generations"], "oracle_seconds": dt, "oracle_cores": cores,
+            "oracle_evals_per_s": (ga.decoded - d0) / dt, "best": ga.best(), "decoded": ga.decoded}
+    one = orc.IslandGA(o, orc.Params(seed=7), 1, w["rows"], w["cols"], 1, w["pseudo_size"])
+    d0 = one.decoded
+    t0 = time.perf_counter()
+    for _ in range(20):
+        one.step()
+    dt1 = time.perf_counter() - t0
+    dual["one_core_sample"] = {"generations": 20, "seconds": dt1, "evals_per_s": (one.decoded - d0) / dt1,
+                               "full_run_estimate_s": dt1 / 20 * w["generations"]}
+    if gpu is not None:
+        g = gpu_run("dual_100x10")
+        dual["gpu"] = g
+        dual["gpu_matches_oracle"] = g["best"] == ga.best() and g["decoded"] == ga.decoded
+    out["dual_100x10"] = dual
+
+    # 4096 rows of the 500 x 20 instance over `cores` spawned processes
+    N = 4096
+    bounds = [(N * k // cores, N * (k + 1) // cores) for k in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_shard_eval, [(0, 1, 0.0)] * cores)   # workers up, oracle built
+        start_at = time.time() + 1.0
+        t0 = time.perf_counter()
+        res = pool.map(_shard_eval, [(a, b, start_at) for a, b in bounds])
+        wall = time.perf_counter() - t0 - 1.0
+    slowest = max(r[0] for r in res)
+    out["sharded_decode_500x20"] = {"rows": N, "processes": cores, "slowest_process_s": slowest,
+                                    "evals_per_s": N / slowest, "wall_s_after_start": wall,
+                                    "checksum": sum(r[1] for r in res)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -1002,6 +1141,8 @@ def main():
         return run_batch(args)
     if args.workload == "surrogate_100x10":
         return run_surrogate(args)
+    if args.workload == "oracle_full":
+        return run_oracle_full(args)
     if args.workload == "surrogate_forward_32768":
         return run_mlp_forward(args)
     if args.workload == "decode_500x20":
