@@ -26,6 +26,7 @@ are not sharded across GPUs).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -730,7 +731,7 @@ def _median_curve(curves, grid):
     return out
 
 
-def surrogate_measure(seeds, plain_gens: int = 1000, screened_gens: int = 500) -> dict:
+def surrogate_measure(seeds, plain_gens: int = 1000, screened_gens: int = 500, schedule: dict | None = None) -> dict:
     """Plain vs surrogate-screened dual-island GA on the 100 x 10 instance
     family (64x64 cellular + 4096 pseudo, ring 2% every 50): for every GA seed
     best makespan against wall-clock (host time around synchronised
@@ -750,8 +751,10 @@ def surrogate_measure(seeds, plain_gens: int = 1000, screened_gens: int = 500) -
     w = WORKLOADS["dual_100x10"]
     spec = workload_instance("dual_100x10")
     inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p)
-    cells, K = w["rows"] * w["cols"], 8
     sp0 = ffs.ffs_surrogate_params_default()
+    for key, val in (schedule or {}).items():      # e.g. train_every, train_steps, candidates
+        setattr(sp0, key, type(getattr(sp0, key))(val))
+    cells, K = w["rows"] * w["cols"], sp0.candidates
 
     def make(seed, screened, train=True):
         prm = ffs.ffs_params_default()
@@ -759,9 +762,10 @@ def surrogate_measure(seeds, plain_gens: int = 1000, screened_gens: int = 500) -
         prm.migration_mode, prm.migration_gap = ffs.FFS_MIG_RING, w["gap"]
         isl = ffs.Islands(inst, prm, 1, w["rows"], w["cols"], 1, w["pseudo_size"])
         if screened:
-            net = ffs.MLP(540, 512, 256, cells * K)
+            net = ffs.MLP(540, 512, 256, (cells * K + 127) // 128 * 128)
             net.init(3)
-            sp = ffs.ffs_surrogate_params_default()
+            sp = ffs.ffs_surrogate_params()
+            ctypes.memmove(ctypes.addressof(sp), ctypes.addressof(sp0), ctypes.sizeof(sp))
             if not train:
                 sp.train_every = 0
             ffs.ffs_islands_attach_surrogate(isl, net, sp)
@@ -861,7 +865,9 @@ def run_surrogate(args):
     import torch
     torch.cuda.set_device(0)
     seeds = [int(x) for x in args.seeds.split(",")] if args.seeds else list(range(7, 12))
-    line = surrogate_measure(seeds, plain_gens=args.plain_gens or 1000, screened_gens=args.screened_gens or 500)
+    schedule = dict(kv.split("=") for kv in args.surrogate_schedule.split(",")) if args.surrogate_schedule else None
+    line = surrogate_measure(seeds, plain_gens=args.plain_gens or 1000, screened_gens=args.screened_gens or 500,
+                             schedule=schedule)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1128,6 +1134,8 @@ def main():
     ap.add_argument("--plain-gens", type=int, default=0, help="surrogate_100x10: plain generations (default 1000)")
     ap.add_argument("--screened-gens", type=int, default=0,
                     help="surrogate_100x10: screened generations (default 500)")
+    ap.add_argument("--surrogate-schedule", default=None,
+                    help="surrogate_100x10: overrides of the screen's schedule, e.g. train_every=2,train_steps=1")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape THREADS,CHUNK,VARIANT instead of the autotuner (profiling)")
     args = ap.parse_args()
