@@ -62,7 +62,7 @@ __device__ __forceinline__ IslandRef batch_ref(const BatchInst &I, const int32_t
 // cell: draws, tournaments, order crossover and swap into the instance's
 // child row, the cell copied to its output row.  wbits: the warp's
 // crossover mark, mark_words(max_n) words.
-__global__ void __launch_bounds__(256) k_batch_breed(const BatchInst *__restrict__ insts, int count, GaScalars g,
+__global__ void __launch_bounds__(256, 4) k_batch_breed(const BatchInst *__restrict__ insts, int count, GaScalars g,
                                                      const int32_t *cur, const int32_t *gen, int rows, int cols,
                                                      int warps_per_inst, int mark_words_max)
 {

@@ -261,7 +261,7 @@ __device__ __forceinline__ void cellular_breed_warp(const GaScalars &g, const Is
 // blocks breed the cellular cells, the others (launched first) the pseudo
 // pairs; the two kinds of warps share the SMs and hide each other's memory
 // latency.
-__global__ void __launch_bounds__(256) k_breed_dual(GaScalars g, const __grid_constant__ IslandBatch cb, int rows,
+__global__ void __launch_bounds__(256, 4) k_breed_dual(GaScalars g, const __grid_constant__ IslandBatch cb, int rows,
                                                     int cols, const __grid_constant__ IslandBatch pb, int psize,
                                                     int n, int ld, PseudoScratch s, int cell_blocks,
                                                     int16_t *cell_children)

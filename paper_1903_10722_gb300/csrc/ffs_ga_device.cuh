@@ -52,13 +52,30 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
             __syncwarp();
             continue;
         }
+        const int nb = (n + 7) >> 3;
+        const int4 *p1v = reinterpret_cast<const int4 *>(p1);
+        const int4 *p2v = reinterpret_cast<const int4 *>(p2);
+        int4 *cv = reinterpret_cast<int4 *>(child);
+        const int4 zero4 = make_int4(0, 0, 0, 0);
+        // rows of at most 64 blocks (512 genes): every block of both parents in
+        // registers first (block q with lane q % 32), so that a child costs one
+        // trip to memory instead of one per pass
+        const bool regs = nb <= 64;   // warp-uniform
+        int4 a0 = zero4, a1 = zero4, c0 = zero4, c1 = zero4;
+        if (regs) {
+            if (lane < nb) {
+                a0 = p1v[lane];
+                c0 = p2v[lane];
+            }
+            if (lane + 32 < nb) {
+                a1 = p1v[lane + 32];
+                c1 = p2v[lane + 32];
+            }
+        }
         for (int w = lane; 4 * w < words; w += 32) reinterpret_cast<uint4 *>(mark)[w] = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
         // the segment p1[l..r], eight genes (one 16-byte block) per lane
-        const int4 *p1v = reinterpret_cast<const int4 *>(p1);
-        int4 *cv = reinterpret_cast<int4 *>(child);
-        for (int q = (l >> 3) + lane; q <= (r >> 3); q += 32) {
-            const int4 v = p1v[q];
+        auto segment_block = [&](int q, const int4 &v) {
             const uint32_t wv[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
             const bool full = 8 * q >= l && 8 * q + 7 <= r;
             if (full) cv[q] = v;
@@ -71,6 +88,12 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
                     if ((unsigned)g < (unsigned)n) flag[g] = 1u;
                 }
             }
+        };
+        if (regs) {
+            if (lane < nb && 8 * lane <= r && 8 * lane + 7 >= l) segment_block(lane, a0);
+            if (lane + 32 < nb && 8 * (lane + 32) <= r && 8 * (lane + 32) + 7 >= l) segment_block(lane + 32, a1);
+        } else {
+            for (int q = (l >> 3) + lane; q <= (r >> 3); q += 32) segment_block(q, p1v[q]);
         }
         __syncwarp();
         // p2 from position start = r + 1 onward cyclically, in 16-byte blocks:
@@ -78,15 +101,28 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
         // from start on, pass nb those before start.  A lane's taken genes
         // get consecutive ranks after a warp prefix sum of the lanes' counts.
         const int start = (r + 1 == n) ? 0 : r + 1;
-        const int nb = (n + 7) >> 3, b0 = start >> 3;
-        const int4 *p2v = reinterpret_cast<const int4 *>(p2);
+        const int b0 = start >> 3;
         int placed = 0;
         for (int t0 = 0; t0 <= nb; t0 += 32) {
             const int t = t0 + lane;
             int q = b0 + t;
             if (q >= nb) q -= nb;
-            int4 v = make_int4(0, 0, 0, 0);
-            if (t <= nb) v = p2v[q];
+            int4 v = zero4;
+            if (regs) {   // block q from the lane that holds it (every lane shuffles)
+                const int src = q & 31;
+                int4 w0, w1;
+                w0.x = __shfl_sync(0xFFFFFFFFu, c0.x, src);
+                w0.y = __shfl_sync(0xFFFFFFFFu, c0.y, src);
+                w0.z = __shfl_sync(0xFFFFFFFFu, c0.z, src);
+                w0.w = __shfl_sync(0xFFFFFFFFu, c0.w, src);
+                w1.x = __shfl_sync(0xFFFFFFFFu, c1.x, src);
+                w1.y = __shfl_sync(0xFFFFFFFFu, c1.y, src);
+                w1.z = __shfl_sync(0xFFFFFFFFu, c1.z, src);
+                w1.w = __shfl_sync(0xFFFFFFFFu, c1.w, src);
+                if (t <= nb) v = q >= 32 ? w1 : w0;
+            } else if (t <= nb) {
+                v = p2v[q];
+            }
             const uint32_t wv[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
             const int lo = t == 0 ? start : 0, hi = t == nb ? start : n;   // natural indices kept in this pass
             unsigned take = 0u;
