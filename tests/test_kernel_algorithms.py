@@ -207,3 +207,91 @@ def test_completion_key_carries_the_job_and_the_later_start():
         f, key = tf << SH | jf << 1, ti << SH | ji << 1
         x = p * (1 << SH) + max((f & ~low) | (key & low), key)
         assert x >> SH == max(tf, ti) + p and x & low == ji << 1
+
+
+def _lane_pipeline(n, S, M, p, genes, release=None, due=None, wt=0):
+    """The stage-parallel decoder's schedule, step by step as the warp runs
+    it: lane s owns stage s's sorted machine keys; each step every lane
+    takes the key its predecessor emitted the step before (lane 0: the next
+    gene), dispatches a key that carries a job (pop, complete, insert), or,
+    once all n jobs are dispatched, drains one key (inserting +inf); a popped
+    key is emitted to the next lane, which ignores keys without a job (the
+    initial machines).  The last lane adds each completion's tardiness and
+    keeps the largest completion.  Returns (objective, steps)."""
+    SH = int(n + 1).bit_length() + 1
+    INF = (1 << 62)
+    Meff = [min(int(m), n) for m in M]
+    f = [[0] * Meff[s] for s in range(S)]
+    d = [0] * S
+    drained = [0] * S
+    emit = [0] * S
+    done = [False] * S
+    mk = tard = 0
+    bad = False
+    steps = 0
+    while not all(done):
+        recv = [0] + emit[:-1]          # shuffle up: what the predecessor emitted last step
+        emit = [0] * S
+        for s in range(S):
+            if done[s]:
+                continue
+            if s == 0:
+                g = int(genes[d[0]]) if d[0] < n else None
+                key = 0
+                if g is not None:
+                    if not 0 <= g < n:
+                        bad, g = True, 0
+                    key = (g + 1) << 1
+                    if release is not None:
+                        key |= int(release[g]) << SH
+            else:
+                key = recv[s]
+            job_bits = key & ((1 << SH) - 2)
+            if job_bits:
+                j = (job_bits >> 1) - 1
+                f0 = f[s][0]
+                low = (1 << SH) - 1
+                start_key = max((f0 & ~low) | (key & low), key)
+                x = int(p[j][s]) * (1 << SH) + start_key
+                f[s] = sorted(f[s][1:] + [x])
+                emit[s] = f0
+                d[s] += 1
+                if s == S - 1:
+                    mk = max(mk, x)
+                    if due is not None:
+                        tard += max(0, (x >> SH) - int(due[j]))
+            elif d[s] == n and s < S - 1 and drained[s] < Meff[s]:
+                emit[s] = f[s][0]
+                f[s] = f[s][1:] + [INF]
+                drained[s] += 1
+            done[s] = d[s] == n if s == S - 1 else (d[s] == n and drained[s] == Meff[s])
+        steps += 1
+    return (-1 if bad else (mk >> SH) + wt * tard), steps
+
+
+def test_stage_parallel_lanes_equal_the_oracle():
+    """The lane pipeline gives the oracle's objective on random instances
+    (ties in time included, M_s >= n, M_s = 1, releases and due times,
+    invalid genes) in about n + sum M_s + S steps instead of n * S."""
+    rng = np.random.default_rng(12)
+    for trial in range(300):
+        n = int(rng.integers(1, 40))
+        S = int(rng.integers(1, 9))
+        M = rng.integers(1, 7, size=S).astype(np.int32)
+        p = rng.integers(1, 6 if trial % 2 else 60, size=(n, S)).astype(np.int32)
+        genes = rng.permutation(n).astype(np.int16)
+        rel = due = None
+        wt = 0
+        if trial % 3 == 0:
+            rel = rng.integers(0, 40, size=n).astype(np.int32)
+            due = (rel + rng.integers(0, 80, size=n)).astype(np.int32)
+            wt = 100
+        o = orc.Instance(n, S, M, p, release=rel, due=due, wt=wt)
+        want = orc.decode(o, genes)
+        got, steps = _lane_pipeline(n, S, M, p, genes, rel, due, wt)
+        assert got == want, (trial, n, S, M.tolist())
+        assert steps <= n + int(np.minimum(M, n).sum()) + S + 1
+    # an invalid gene
+    M = np.array([2, 3], dtype=np.int32)
+    p = np.ones((5, 2), dtype=np.int32)
+    assert _lane_pipeline(5, 2, M, p, np.array([0, 1, 7, 3, 4]))[0] == -1
