@@ -138,8 +138,15 @@ int ffs_population_eval(const ffs_instance *inst, const int16_t *pop, int64_t N,
  * heaps saved between rounds in tensor memory where that fits more threads
  * per SM; 1 one stage at a time, 2 stages in interleaved pairs, both with
  * the saved heaps in shared memory; 3 / 4 as 1 / 2 with the saved heaps in
- * tensor memory whenever the shape allows it (chunked decoding);
- * FFS_EINVAL outside 0..4); 0 lets the library choose.  Results do not
+ * tensor memory whenever the shape allows it (chunked decoding); 5 the
+ * stage-parallel decoder: lane s of a group of S lanes runs stage s of one
+ * chromosome, consuming the completions stage s - 1 emits one step earlier,
+ * floor(32 / S) chromosomes per warp (S <= 32, else FFS_EUNSUPPORTED; chunk
+ * and threads are ignored); FFS_EINVAL outside 0..5); 0 lets the library
+ * choose: with chunk and threads 0 it takes the stage-parallel decoder where
+ * a cost model fitted to GB300 measurements predicts it at most 0.7x the
+ * time of one chromosome per lane (small launches of many-stage instances,
+ * whose one-lane chains leave the GPU latency-bound).  Results do not
  * depend on the shape or variant. */
 int ffs_population_eval_tuned(const ffs_instance *inst, const int16_t *pop, int64_t N, int32_t ld,
                               int32_t *makespan, int32_t decode_chunk, int32_t block_threads,

@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "ffs_internal.cuh"
+#include "ffs_lanes.cuh"
 
 namespace fgpu {
 
@@ -229,10 +230,104 @@ static int plan_decode_uncached(const ffs_instance *inst, const void *kernel, in
 
 const void *eval_kernel() { return (const void *)k_eval; }
 
+// ---------------------------------------------------------------------------
+// The stage-parallel decoder kernel (ffs_lanes.cuh): a warp decodes
+// floor(32 / S) chromosomes at a time, lane s of each group running stage s,
+// their rows staged in the warp's part of shared memory.  It serves decode
+// launches too small to fill the GPU with one chromosome per lane.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_eval_lanes(int n, int S, uint32_t SH, int MM, int obj_words, int has_rel,
+                                                    int has_due, uint32_t wt, const uint32_t *__restrict__ tab_g,
+                                                    const int32_t *__restrict__ stage_g,
+                                                    const int16_t *__restrict__ pop, int64_t N, int ld,
+                                                    int32_t *__restrict__ out, const int32_t *count_dev,
+                                                    unsigned long long *decoded)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, W = blockDim.x >> 5;
+    const LaneSetup u = lanes_block_setup(smem, n, S, obj_words, has_rel, has_due, tab_g, stage_g, ld);
+    if (count_dev) N = *count_dev;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0 && N > 0) atomicAdd(decoded, (unsigned long long)N);
+    const int C = u.C;
+    const int64_t items = (N + C - 1) / C;
+    for (int64_t it = (int64_t)blockIdx.x * W + warp; it < items; it += (int64_t)gridDim.x * W) {
+        const int64_t r0 = it * C;
+        const int nrows = (int)min((int64_t)C, N - r0);
+        const int4 *src = reinterpret_cast<const int4 *>(pop + r0 * ld);
+        int4 *dst = reinterpret_cast<int4 *>(u.rows);
+        for (int k = lane; k < nrows * (ld >> 3); k += 32) dst[k] = src[k];
+        __syncwarp();
+        const bool active = u.g < nrows;
+        const uint32_t sM = (active ? (uint32_t)u.s : 0xFFu) | (u.Ms << 8) | (SH << 16);
+        const uint32_t genes = u.rows_sa + (active ? (uint32_t)(u.g * ld * 2) : 0u);
+        const int32_t v = lane_decode_dispatch(MM, u.tab, u.row_bytes, genes, u.nS, sM, u.win, u.rel, u.due, wt);
+        if (active && u.s == S - 1) out[r0 + u.g] = v;
+        __syncwarp();   // the buffer is refilled next
+    }
+}
+
+// Which decoder a launch of N chromosomes takes: variant 5 asks for the
+// stage-parallel one; with the library's choice (variant 0) it is taken when
+// a cost model, fitted to GB300 measurements of both decoders, predicts it
+// at most 0.7x the one-lane decoder's time.  Each decoder's cycles are the
+// larger of a latency term (its chain: n S dispatches at about 60 cycles /
+// start_{S-1} + n steps at about 260) and an issue term (its warp
+// instructions -- about 30 per dispatch per 32 chromosomes / 58 per step per
+// floor(32 / S) chromosomes -- over the SMs' 4 schedulers at the issue
+// rates the two kernels reach, 0.6 / 0.55 per cycle).
+bool lanes_decode_pays(const ffs_instance *inst, int64_t N, int variant)
+{
+    if (inst->S > 32) return false;
+    if (variant == kVariantLanes) return true;
+    if (variant != 0 || N <= 0) return false;
+    const double n = inst->n, S = inst->S, sched = 4.0 * inst->num_sms;
+    double steps = n;
+    for (int j = 0; j + 1 < inst->S; ++j) steps += inst->M_eff[j] + 1;
+    const double C = (double)(32 / inst->S);
+    const double one_lane = std::max(n * S * 60.0, (double)N / 32.0 * n * S * 30.0 / (sched * 0.6));
+    const double lanes = std::max(steps * 260.0, (double)N / C * steps * 58.0 / (sched * 0.55));
+    return lanes <= 0.7 * one_lane;
+}
+
+int plan_lanes(const ffs_instance *inst, int64_t N, int ld, LanesPlan *out)
+{
+    const int S = inst->S, n = inst->n;
+    if (S > 32) return set_error(FFS_EUNSUPPORTED, "the stage-parallel decoder takes at most 32 stages, not %d", S);
+    LanesPlan p;
+    for (int m : inst->M_eff) p.MM = std::max(p.MM, m);
+    const int W = p.T / 32;
+    p.C = 32 / S;
+    p.smem = ((size_t)round_up(table_words(n, S) + inst->obj_words + S, 4) + (size_t)W * p.C * ld / 2) * 4;
+    if (p.smem > 232448) return set_error(FFS_EUNSUPPORTED, "stage-parallel decoder: %zu bytes of shared memory", p.smem);
+    const int64_t items = (N + p.C - 1) / p.C;
+    int64_t blocks = (items + W - 1) / W;
+    if (blocks > (int64_t)inst->num_sms * 16) blocks = (int64_t)inst->num_sms * 16;
+    p.blocks = (int)std::max<int64_t>(blocks, 1);
+    *out = p;
+    return FFS_OK;
+}
+
+int launch_eval_lanes(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
+                      const int32_t *count_dev, unsigned long long *decoded, cudaStream_t st)
+{
+    LanesPlan p;
+    int rc = plan_lanes(inst, N, ld, &p);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_eval_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
+    k_eval_lanes<<<p.blocks, p.T, p.smem, st>>>(inst->n, inst->S, (uint32_t)inst->SH, p.MM, inst->obj_words,
+                                                inst->has_rel, inst->has_due, (uint32_t)inst->wt, inst->d_tab,
+                                                inst->d_stage, pop, N, ld, out, count_dev, decoded);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
 int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
                 const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
                 cudaStream_t st, int variant)
 {
+    // an explicit launch shape (chunk, threads) keeps the one-lane decoder
+    if (lanes_decode_pays(inst, N, (B_req || T_req) && variant == 0 ? -1 : variant))
+        return launch_eval_lanes(inst, pop, N, ld, out, count_dev, decoded, st);
     Plan p;
     const int T_sp = spread_threads(inst, N, T_req);
     int rc = plan_decode(inst, (const void *)k_eval, B_req, T_sp, 0, &p, variant);
@@ -512,7 +607,10 @@ int ffs_population_eval_tuned(const ffs_instance *I, const int16_t *pop, int64_t
     if (!I) return set_error(FFS_EINVAL, "NULL instance");
     if (N < 0) return set_error(FFS_EINVAL, "N = %lld < 0", (long long)N);
     if (decode_chunk < 0 || block_threads < 0) return set_error(FFS_EINVAL, "negative launch shape");
-    if (variant < 0 || variant > kMaxVariant) return set_error(FFS_EINVAL, "decoder variant %d", variant);
+    if (variant < 0 || (variant > kMaxVariant && variant != kVariantLanes))
+        return set_error(FFS_EINVAL, "decoder variant %d", variant);
+    if (variant == kVariantLanes && I->S > 32)
+        return set_error(FFS_EUNSUPPORTED, "the stage-parallel decoder takes at most 32 stages, not %d", I->S);
     if (N == 0) return FFS_OK;
     if (!pop || !ms) return set_error(FFS_EINVAL, "NULL population or output");
     int rc = validate_rows(pop, ld, I->n);

@@ -167,6 +167,9 @@ struct BlobReader {
 // interleaved pairs, 3 / 4 = as 1 / 2 with saved heaps in TMEM wherever the
 // shape allows it (chunked decoding).
 constexpr int kMaxVariant = 4;
+// Variant 5: the stage-parallel decoder (ffs_lanes.cuh), for decode launches
+// that accept it; not one of the launch shapes the autotuners sweep.
+constexpr int kVariantLanes = 5;
 int plan_decode(const ffs_instance *inst, const void *kernel, int B_req, int T_req, int bits_per_warp,
                 Plan *out, int variant = 0);
 inline int pairs_of(int variant) { return (variant == 1 || variant == 3) ? 0 : 1; }
@@ -249,6 +252,16 @@ inline GaScalars scalars_of(const ffs_params *p)
 }
 
 // Launchers (defined in the .cu files).
+// Launch plan of a stage-parallel decoding kernel (ffs_lanes.cuh): the heap
+// size compiled for, chromosomes per warp, threads per block, dynamic shared
+// bytes (table, stage array, each warp's staged rows) and blocks.
+struct LanesPlan {
+    int MM = 1, C = 1, T = 128, blocks = 1;
+    size_t smem = 0;
+};
+bool lanes_decode_pays(const ffs_instance *inst, int64_t N, int variant);
+int plan_lanes(const ffs_instance *inst, int64_t N, int ld, LanesPlan *out);
+
 int launch_eval(const ffs_instance *inst, const int16_t *pop, int64_t N, int ld, int32_t *out,
                 const int32_t *count_dev, int B_req, int T_req, unsigned long long *decoded,
                 cudaStream_t st, int variant = 0);

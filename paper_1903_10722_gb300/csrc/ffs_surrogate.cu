@@ -7,6 +7,7 @@
 
 #include "ffs_internal.cuh"
 #include "ffs_ga_device.cuh"
+#include "ffs_lanes.cuh"
 
 namespace fgpu {
 
@@ -199,6 +200,80 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
     decode_tmem_end(Ls);
 }
 
+// k_sur_select with the stage-parallel decoder (ffs_lanes.cuh), for screens
+// too small to fill the GPU one cell per lane: a warp takes floor(32 / S)
+// cells at a time.  Lane l < C of the warp picks cell l's best-scored
+// candidate (lowest score, lowest k on ties), the warp stages the picked
+// rows in shared memory, each group of S lanes decodes one of them, and
+// lane l then replaces its cell iff better and appends the pair to the ring
+// exactly as k_sur_select does.
+__global__ void __launch_bounds__(128) k_sur_select_lanes(int n, int S, uint32_t SH, int MM, int obj_words,
+                                                          int has_rel, int has_due, uint32_t wt,
+                                                          const uint32_t *__restrict__ tab_g,
+                                                          const int32_t *__restrict__ stage_g, GaScalars g,
+                                                          const __grid_constant__ IslandBatch batch, int rows, int cols,
+                                                          int ld, int K, const int16_t *cand, const float *scores,
+                                                          int32_t *chosen, int16_t *ring_rows, int32_t *ring_ms,
+                                                          long long ring_cap, const long long *ctr,
+                                                          unsigned long long *decoded)
+{
+    const long long ring_base = ctr[0];
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, W = blockDim.x >> 5;
+    const LaneSetup u = lanes_block_setup(smem, n, S, obj_words, has_rel, has_due, tab_g, stage_g, ld);
+    const int cells = rows * cols, total = cells * batch.count, C = u.C;
+    if (decoded && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(decoded, (unsigned long long)total);
+    const int items = (total + C - 1) / C;
+    for (int it = blockIdx.x * W + warp; it < items; it += gridDim.x * W) {
+        const int gq0 = it * C;
+        const int nrows = min(C, total - gq0);
+        const bool mine = lane < nrows;          // lane l handles cell gq0 + l
+        const int gq = gq0 + (mine ? lane : 0);
+        int pick = 0;
+        if (mine) {
+            const float *sc = scores + (int64_t)gq * K;
+            for (int k = 1; k < K; ++k)
+                if (sc[k] < sc[pick]) pick = k;
+            if (!FFS_DCHECK(pick >= 0 && pick < K, kCheckPick)) pick = 0;
+        }
+        const int16_t *drow = cand + ((int64_t)gq * K + pick) * ld;
+        // the picked rows, one after the other, into the warp's buffer
+        int4 *dst = reinterpret_cast<int4 *>(u.rows);
+        for (int j = 0; j < nrows; ++j) {
+            const int4 *src = reinterpret_cast<const int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)drow, j));
+            for (int k = lane; k < (ld >> 3); k += 32) dst[j * (ld >> 3) + k] = src[k];
+        }
+        __syncwarp();
+        const bool active = u.g < nrows;
+        const uint32_t sM = (active ? (uint32_t)u.s : 0xFFu) | (u.Ms << 8) | (SH << 16);
+        const uint32_t genes = u.rows_sa + (active ? (uint32_t)(u.g * ld * 2) : 0u);
+        const int32_t v = lane_decode_dispatch(MM, u.tab, u.row_bytes, genes, u.nS, sM, u.win, u.rel, u.due, wt);
+        // lane l takes its cell's objective from its group's last lane
+        const int32_t ms = __shfl_sync(0xFFFFFFFFu, v, (mine ? lane : 0) * S + S - 1);
+        const int bi = gq / cells, c = gq - bi * cells;
+        const int16_t *pin;
+        const int32_t *msin;
+        int16_t *pout;
+        int32_t *msout;
+        uint32_t gen;
+        resolve(batch.ref[bi], pin, msin, pout, msout, gen);
+        bool better = false, keep = false;
+        if (mine) {
+            const int32_t old = msin[c];
+            better = ms >= 0 && (g.replace_le ? (uint32_t)ms <= (uint32_t)old : (uint32_t)ms < (uint32_t)old);
+            keep = !better;
+            msout[c] = better ? ms : old;
+            chosen[gq] = pick;
+            const long long slot = (ring_base + gq) % ring_cap;
+            ring_ms[slot] = ms;
+        }
+        warp_copy_rows(better, drow, pout + (int64_t)c * ld, ld);
+        warp_copy_rows(keep, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
+        warp_copy_rows(mine, drow, ring_rows + ((ring_base + gq) % ring_cap) * ld, ld);
+        __syncwarp();   // the buffer is refilled next
+    }
+}
+
 // The surrogate's device counters: ctr[0] ring pairs appended, ctr[1]
 // training batches drawn, ctr[2] the ring count when the current generation
 // began (set by k_sur_snapshot).  A training round runs beside the current
@@ -309,8 +384,22 @@ int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const Island
                       int32_t *ring_ms, long long ring_cap, const long long *ctr, int B_req, int T_req,
                       unsigned long long *decoded, cudaStream_t st)
 {
+    const int64_t total = (int64_t)rows * cols * batch.count;
+    if (lanes_decode_pays(inst, total, (B_req || T_req) && g.variant == 0 ? -1 : g.variant)) {
+        LanesPlan lp;
+        int rc = plan_lanes(inst, total, ld, &lp);
+        if (rc) return rc;
+        FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_select_lanes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lp.smem));
+        k_sur_select_lanes<<<lp.blocks, lp.T, lp.smem, st>>>(inst->n, inst->S, (uint32_t)inst->SH, lp.MM,
+                                                            inst->obj_words, inst->has_rel, inst->has_due,
+                                                            (uint32_t)inst->wt, inst->d_tab, inst->d_stage, g, batch,
+                                                            rows, cols, ld, K, cand, scores, chosen, ring_rows, ring_ms,
+                                                            ring_cap, ctr, decoded);
+        FFS_CUDA_TRY(cudaGetLastError());
+        return FFS_OK;
+    }
     Plan p;
-    const int T_sp = spread_threads(inst, (int64_t)rows * cols * batch.count, T_req);
+    const int T_sp = spread_threads(inst, total, T_req);
     int rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_sp, 0, &p, g.variant);
     if (rc && T_sp != T_req) rc = plan_decode(inst, (const void *)k_sur_select, B_req, T_req, 0, &p, g.variant);
     if (rc) return rc;

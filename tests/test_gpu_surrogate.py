@@ -14,12 +14,13 @@ from oracle import mlp as omlp
 pytestmark = pytest.mark.gpu
 
 
-def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_every, seed=7):
+def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_every, seed=7, variant=0):
     spec = make_instance(n, S, mlo, mhi, seed=n + S)
     o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
     g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
     prm = gpu.ffs_params_default()
     prm.seed = seed
+    prm.decode_variant = variant
     prm.migration_mode, prm.migration_gap = 0, 0
     isl = gpu.Islands(g, prm, 1, rows, cols, n_pseudo, psize)
     params = mlp_params(540, 512, 256, seed=11)
@@ -43,10 +44,12 @@ def _compare(gpu, isl, ga, n, tag):
         assert np.array_equal(ms.cpu().numpy().astype(np.int64), ga.mss[i]), (tag, i)
 
 
-@pytest.mark.parametrize("warmup", [0, 2])
-def test_screened_generations_match_oracle_given_scores(gpu, warmup):
+@pytest.mark.parametrize("warmup,variant", [(0, 0), (2, 0), (2, 5)])
+def test_screened_generations_match_oracle_given_scores(gpu, warmup, variant):
+    """variant 5: the picks decoded by the stage-parallel select kernel and
+    the pseudo children by the stage-parallel eval kernel."""
     rows, cols, K = 8, 8, 8
-    spec, o, g, isl, ga, params = _setup(gpu, 20, 5, 3, 3, rows, cols, 1, 32, K, warmup, 0)
+    spec, o, g, isl, ga, params = _setup(gpu, 20, 5, 3, 3, rows, cols, 1, 32, K, warmup, 0, variant=variant)
     inst_feat = omlp.instance_features(spec.n, spec.S, spec.M, spec.p)
     cells = rows * cols
     for gen in range(1, 5):

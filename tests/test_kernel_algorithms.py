@@ -269,6 +269,51 @@ def _lane_pipeline(n, S, M, p, genes, release=None, due=None, wt=0):
     return (-1 if bad else (mk >> SH) + wt * tard), steps
 
 
+def _lane_static(n, S, M, p, genes, release=None, due=None, wt=0):
+    """The same schedule as the kernel runs it, with the windows fixed in
+    advance: at step t lane s dispatches the key its predecessor emitted at
+    t - 1 if t - start_s is in [0, n) (lane 0: gene t), drains if it is in
+    [n, n + M_s) (all lanes but the last), and is idle otherwise; no test
+    of the keys' job bits."""
+    SH = int(n + 1).bit_length() + 1
+    INF = (1 << 62)
+    low = (1 << SH) - 1
+    Meff = [min(int(m), n) for m in M]
+    start = [sum(Meff[j] + 1 for j in range(s)) for s in range(S)]
+    total = start[S - 1] + n
+    f = [[0] * Meff[s] for s in range(S)]
+    emit = [0] * S
+    mk = tard = 0
+    bad = False
+    for t in range(total):
+        recv = [0] + emit[:-1]
+        emit = [0] * S
+        for s in range(S):
+            r = t - start[s]
+            if 0 <= r < n:
+                if s == 0:
+                    g = int(genes[r])
+                    if not 0 <= g < n:
+                        bad, g = True, 0
+                    key = (g + 1) << 1 | ((int(release[g]) << SH) if release is not None else 0)
+                else:
+                    key = recv[s]
+                j = ((key & (low - 1)) >> 1) - 1
+                assert j >= 0                       # a real job arrives in every dispatch step
+                f0 = f[s][0]
+                x = int(p[j][s]) * (1 << SH) + max((f0 & ~low) | (key & low), key)
+                f[s] = sorted(f[s][1:] + [x])
+                emit[s] = f0
+                if s == S - 1:
+                    mk = max(mk, x)
+                    if due is not None:
+                        tard += max(0, (x >> SH) - int(due[j]))
+            elif s < S - 1 and n <= r < n + Meff[s]:
+                emit[s] = f[s][0]
+                f[s] = f[s][1:] + [INF]
+    return -1 if bad else (mk >> SH) + wt * tard
+
+
 def test_stage_parallel_lanes_equal_the_oracle():
     """The lane pipeline gives the oracle's objective on random instances
     (ties in time included, M_s >= n, M_s = 1, releases and due times,
@@ -290,7 +335,13 @@ def test_stage_parallel_lanes_equal_the_oracle():
         want = orc.decode(o, genes)
         got, steps = _lane_pipeline(n, S, M, p, genes, rel, due, wt)
         assert got == want, (trial, n, S, M.tolist())
-        assert steps <= n + int(np.minimum(M, n).sum()) + S + 1
+        # the schedule is static: lane s receives its n jobs in the steps
+        # [start_s, start_s + n), start_s = sum_{j<s} (M_j + 1), so the last
+        # lane ends after start_{S-1} + n steps whatever the data
+        Meff = np.minimum(M, n)
+        assert steps == n + int((Meff[:-1] + 1).sum())
+        got_static = _lane_static(n, S, M, p, genes, rel, due, wt)
+        assert got_static == want, (trial, n, S, M.tolist())
     # an invalid gene
     M = np.array([2, 3], dtype=np.int32)
     p = np.ones((5, 2), dtype=np.int32)
