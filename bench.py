@@ -982,6 +982,56 @@ def run_decode(args):
     return 0
 
 
+def run_decode_small(args):
+    """Decode launches too small to fill the GPU one chromosome per lane:
+    the one-lane decoder (variant 3), the stage-parallel decoder (variant 5)
+    and the library's choice (variant 0) on the small configurations' shapes.
+    Per case and variant: 20 back-to-back calls between CUDA events (so that
+    the host's launch work overlaps the previous decode), median over
+    `steps` repetitions, L2 flushed between repetitions; one JSON line."""
+    import torch
+
+    import paper_1903_10722_gb300 as ffs
+    from ffs_workloads import random_population, workload_instance
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cases = [("dual_100x10", 4096), ("dual_100x10", 8192), ("paper_300x4", 512), ("tiny", 64),
+             ("scale_500x20", 4096)]
+    out = {"metric": "us per decode launch (small launches)", "workload": "decode_small", "calls_per_timing": 20,
+           "cases": []}
+    for name, N in cases:
+        spec = workload_instance(name)
+        g = ffs.Instance(spec.n, spec.S, spec.M, spec.p)
+        pop = torch.from_numpy(random_population(spec.n, N, seed=1)).cuda()
+        res = torch.empty(N, dtype=torch.int32, device="cuda")
+        row = {"case": name, "rows": N, "n_jobs": spec.n, "n_stages": spec.S}
+        ref = None
+        for v in (3, 5, 0):
+            for _ in range(max(3, args.warmup)):
+                ffs.ffs_population_eval_tuned(g, pop, N, pop.shape[1], res, 0, 0, v)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(max(1, args.steps)):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(20):
+                    ffs.ffs_population_eval_tuned(g, pop, N, pop.shape[1], res, 0, 0, v)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 20 * 1000.0)
+            row[{3: "one_lane_us", 5: "stage_parallel_us", 0: "library_choice_us"}[v]] = statistics.median(ts)
+            if ref is None:
+                ref = res.clone()
+            elif not torch.equal(ref, res):
+                raise RuntimeError(f"decoders disagree on {name} N={N}")
+        out["cases"].append(row)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_assign(args):
     """The paper's genotype: objectives of N random machine-assignment strings
     (500 jobs x 20 stages = 10000 genes per row) on unrelated machines
@@ -1153,6 +1203,8 @@ def main():
         return run_oracle_full(args)
     if args.workload == "surrogate_forward_32768":
         return run_mlp_forward(args)
+    if args.workload == "decode_small":
+        return run_decode_small(args)
     if args.workload == "decode_500x20":
         return run_decode(args)
     if args.workload == "assign_500x20":
