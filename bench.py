@@ -1092,10 +1092,32 @@ def run_paper(args):
     from ffs_workloads import make_paper_instance
 
     torch.cuda.set_device(0)
-    spec = make_paper_instance(300, 4, 2, seed=1)
-    inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p, release=spec.release, due=spec.due, wt=spec.wt)
-    gens, runs = 2000, 50
+    gens, runs = 2000, (args.runs or 50)
     seeds = list(range(7, 7 + runs))
+    per_instance = []
+    for iseed in range(1, (args.instances or 1) + 1):
+        spec = make_paper_instance(300, 4, 2, seed=iseed)
+        inst = ffs.Instance(spec.n, spec.S, spec.M, spec.p, release=spec.release, due=spec.due, wt=spec.wt)
+        per_instance.append(_paper_instance(ffs, inst, iseed, gens, seeds, sweep=iseed == 1))
+    first = per_instance[0]
+    line = {"metric": "best objective (100 x total tardiness + C_max) after 2000 generations",
+            "workload": "paper_obj_300x4", "lower_is_better": True,
+            "instance": "300 x 4 x 2, p ~ U[1,5], Table 1 release / due times, instance seeds 1.."
+                        f"{len(per_instance)}",
+            "population": 512, "generations": gens, "seeds": f"{seeds[0]}..{seeds[-1]}",
+            "table2": first["table2"], "time": first["time"],
+            "migration_gap_sweep_average": first["sweep"],
+            "instances": [{"instance_seed": r["instance_seed"], "table2": r["table2"]} for r in per_instance]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _paper_instance(ffs, inst, iseed, gens, seeds, sweep):
+    """Table 2 (dual, cellular, pseudo GA over the GA seeds) on one Table 1
+    instance, and with sweep the Fig. 4 migration-gap sweep of the dual GA."""
+    import numpy as np
+    import torch
+    runs = len(seeds)
 
     def run(kind, seed, gap=500):
         prm = ffs.ffs_params_default()
@@ -1131,16 +1153,11 @@ def run_paper(args):
         dt = time.perf_counter() - t0
         table2[kind] = summary([r[0] for r in res])
         times[kind] = {"s_per_run": dt / runs, "evals_per_s": sum(r[1] for r in res) / dt}
-    sweep = {}
-    for gap in (10, 50, 100, 200, 500, 800):
-        sweep[str(gap)] = summary([run("dual", sd, gap)[0] for sd in seeds])["average"]
-    line = {"metric": "best objective (100 x total tardiness + C_max) after 2000 generations",
-            "workload": "paper_obj_300x4", "lower_is_better": True,
-            "instance": "300 x 4 x 2, p ~ U[1,5], Table 1 release / due times, seed 1",
-            "population": 512, "generations": gens, "seeds": f"{seeds[0]}..{seeds[-1]}",
-            "table2": table2, "time": times, "migration_gap_sweep_average": sweep}
-    print(json.dumps(line), flush=True)
-    return 0
+    gap_sweep = {}
+    if sweep:
+        for gap in (10, 50, 100, 200, 500, 800):
+            gap_sweep[str(gap)] = summary([run("dual", sd, gap)[0] for sd in seeds])["average"]
+    return {"instance_seed": iseed, "table2": table2, "time": times, "sweep": gap_sweep}
 
 
 # DRAM bytes (read + write) of one k_step_decode launch of scale_500x20 at
@@ -1186,6 +1203,9 @@ def main():
                     help="surrogate_100x10: screened generations (default 500)")
     ap.add_argument("--surrogate-schedule", default=None,
                     help="surrogate_100x10: overrides of the screen's schedule, e.g. train_every=2,train_steps=1")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="paper_obj_300x4: synthetic Table 1 instances (seeds 1..K; default 1)")
+    ap.add_argument("--runs", type=int, default=0, help="paper_obj_300x4: GA seeds per setup (default 50)")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape THREADS,CHUNK,VARIANT instead of the autotuner (profiling)")
     args = ap.parse_args()
