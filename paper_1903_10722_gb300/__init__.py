@@ -728,7 +728,8 @@ def ffs_mlp_check(m: MLP, stream=None):
 
 class ffs_surrogate_params(ctypes.Structure):
     _fields_ = [("candidates", _i32), ("train_every", _i32), ("train_steps", _i32), ("train_batch", _i32),
-                ("ring_capacity", _i32), ("warmup_generations", _i32), ("lr", ctypes.c_float)]
+                ("ring_capacity", _i32), ("warmup_generations", _i32), ("lr", ctypes.c_float),
+                ("overlap", _i32)]
 
 
 def ffs_surrogate_params_default() -> ffs_surrogate_params:

@@ -855,8 +855,12 @@ static IslandRef device_ref(const ffs_islands *S, int i)
 }
 
 template <typename F>
-static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st,
-                                    F between);
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, bool use_copy,
+                                    cudaStream_t st, F between);
+
+// CTAs of the scoring forward's persistent GEMM while a training round runs
+// beside it: the SMs left over take the round's kernels.
+constexpr int kScreenForwardCtas = 112;
 
 // One generation of the islands in `ids` (all of one kind): cellular islands
 // in launches of up to kMaxBatch, pseudo islands likewise, one decode of all
@@ -895,8 +899,8 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
             FFS_CUDA_TRY(cudaGetLastError());
             int rc = launch_sur_tick(S->sur->d_ctr, 2, -1, st);
             if (rc) return rc;
-            rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, st,
-                                          [](cudaStream_t) { return (int)FFS_OK; });
+            rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, false,
+                                          st, [](cudaStream_t) { return (int)FFS_OK; });
             if (rc) return rc;
             continue;
         }
@@ -982,8 +986,8 @@ static int record_launch(ffs_islands *S, cudaStream_t st)
 // appends the pair to the ring (the device ring counter advanced by the
 // cells of each batch).
 template <typename F>
-static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, cudaStream_t st,
-                                    F between)
+static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, bool use_copy,
+                                    cudaStream_t st, F between)
 {
     SurrogateState *R = S->sur;
     const GaScalars g = scalars_of(&S->prm);
@@ -1016,8 +1020,9 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
         float *scores = R->scores + (int64_t)offset * K;
         if (warm) {
             const void *X = static_cast<const char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
-            if ((rc = ffs_mlp_forward(R->mlp, static_cast<const uint16_t *>(X), R->ldx, ncells * K, scores, st)))
-                return rc;
+            rc = use_copy ? mlp_forward_copy(R->mlp, X, R->ldx, ncells * K, scores, kScreenForwardCtas, st)
+                          : ffs_mlp_forward(R->mlp, static_cast<const uint16_t *>(X), R->ldx, ncells * K, scores, st);
+            if (rc) return rc;
         } else if ((rc = launch_fill_f32(scores, (int64_t)ncells * K, 0.0f, st))) {
             return rc;
         }
@@ -1056,15 +1061,21 @@ static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
 // stream beside the cellular screen, and (train = true) the training round
 // on the previous generations' pairs on the second side stream, beside the
 // candidate building and joined before the forward pass that reads the
-// updated weights; then, everything joined, the generation advance and
-// migration, as generation_all does.
+// updated weights -- or, with overlap, beside the whole screen, which then
+// scores with a copy of the weights taken before the round starts (the
+// round draws only pairs of earlier generations and the standardisation of
+// the latest one, slots that this generation's picks do not overwrite while
+// the ring holds two generations); then, everything joined, the generation
+// advance and migration, as generation_all does.
 static int screened_generation(ffs_islands *S, bool warm, bool train, cudaStream_t st)
 {
     SurrogateState *R = S->sur;
     std::vector<int> cel, pse;
     for (int i = 0; i < S->I; ++i) (S->kind[i] == 0 ? cel : pse).push_back(i);
+    const bool overlap = train && R->sp.overlap;
     int rc = launch_sur_tick(R->d_ctr, 2, -1, st);
     if (rc) return rc;
+    if (overlap && warm && (rc = mlp_take_copy(R->mlp, st))) return rc;
     if (!pse.empty()) {
         NvtxRange r("ffs pseudo islands (side stream)");
         FFS_CUDA_TRY(cudaEventRecord(R->fork_ev, st));
@@ -1080,12 +1091,13 @@ static int screened_generation(ffs_islands *S, bool warm, bool train, cudaStream
     }
     {
         NvtxRange r("ffs screened cellular islands: candidates, scores, select");
-        rc = screened_cellular_launch(S, cel, warm, st, [&](cudaStream_t cs) -> int {
-            if (train) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
+        rc = screened_cellular_launch(S, cel, warm, overlap, st, [&](cudaStream_t cs) -> int {
+            if (train && !overlap) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
             return FFS_OK;
         });
         if (rc) return rc;
     }
+    if (overlap) FFS_CUDA_TRY(cudaStreamWaitEvent(st, R->join2_ev, 0));
     if (!pse.empty()) {
         FFS_CUDA_TRY(cudaEventRecord(R->join_ev, R->side));
         FFS_CUDA_TRY(cudaStreamWaitEvent(st, R->join_ev, 0));
@@ -1115,7 +1127,7 @@ static int capture_graph(ffs_islands *S, cudaGraphExec_t *out, F body)
         return rc;
     }
     if (e != cudaSuccess) return set_error(FFS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(out, graph, 0);
+    e = cudaGraphInstantiateWithFlags(out, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         *out = nullptr;
@@ -1365,6 +1377,17 @@ void ffs_surrogate_params_default(ffs_surrogate_params *p)
     p->lr = 1e-3f;
 }
 
+// The training round's stream.  With overlap it takes the device's highest
+// stream priority (kept by the captured graphs' kernel nodes), so that its
+// short kernels take SMs as soon as the screen's blocks free them.
+static cudaError_t side2_create(cudaStream_t *st, bool high_priority)
+{
+    int least = 0, greatest = 0;
+    if (!high_priority || cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess)
+        return cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    return cudaStreamCreateWithPriority(st, cudaStreamNonBlocking, greatest);
+}
+
 int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surrogate_params *sp, ffs_stream stream)
 {
     clear_error();
@@ -1389,6 +1412,13 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     if (sp->train_batch > mlp_max_batch(mlp)) return set_error(FFS_EINVAL, "train_batch above the network's max_batch");
     if ((long long)sp->ring_capacity < (long long)cells_total + sp->train_batch)
         return set_error(FFS_EINVAL, "ring_capacity must hold one generation's pairs plus a training batch");
+    if (sp->overlap != 0 && sp->overlap != 1) return set_error(FFS_EINVAL, "overlap must be 0 or 1");
+    if (sp->overlap && (long long)sp->ring_capacity < 2LL * cells_total)
+        return set_error(FFS_EINVAL, "with overlap, ring_capacity must hold two generations' pairs");
+    if (sp->overlap) {
+        int rc = mlp_enable_copy(mlp);
+        if (rc) return rc;
+    }
     SurrogateState *R = new SurrogateState();
     R->mlp = mlp;
     R->sp = *sp;
@@ -1449,7 +1479,7 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     if (cudaMemcpy(R->inst_feat, f.data(), nfeat * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(R->d_ctr, 0, 3 * sizeof(long long)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&R->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&R->side2, cudaStreamNonBlocking) != cudaSuccess ||
+        side2_create(&R->side2, sp->overlap != 0) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->join_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->fork2_ev, cudaEventDisableTiming) != cudaSuccess ||

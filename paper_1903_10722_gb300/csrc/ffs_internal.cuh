@@ -301,6 +301,12 @@ int mlp_max_batch(const ffs_mlp *m);
 int64_t mlp_state_bytes(const ffs_mlp *m);
 int mlp_save(const ffs_mlp *m, void *host, cudaStream_t st);                   // synchronises
 int mlp_load(ffs_mlp *m, const void *host, int64_t size, cudaStream_t st);     // synchronises
+// The scoring copy: allocate it (idempotent), take it (stream-ordered), and a
+// forward pass that reads it (and writes activations of its own; max_ctas
+// > 0 caps the CTAs of its persistent GEMMs).
+int mlp_enable_copy(ffs_mlp *m);
+int mlp_take_copy(ffs_mlp *m, cudaStream_t st);
+int mlp_forward_copy(ffs_mlp *m, const void *x, int ldx, int B, float *y, int max_ctas, cudaStream_t st);
 
 inline int spread_threads(const ffs_instance *inst, int64_t units, int T_req)
 {

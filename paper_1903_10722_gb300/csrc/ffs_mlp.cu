@@ -25,11 +25,14 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
 struct GemmEpi {
     float *D;                 // mode 0: FP32 output [M][ldd]
     __nv_bfloat16 *Db;        // mode 1: BF16 relu(acc + bias) [M][ldd]
-    const float *bias;        // mode 1: [N]
+    const float *bias;        // modes 1, 2: [N]
+    const float *w3, *b3;     // mode 2 (persistent form, one column tile): y[row] =
+    float *y;                 //   sum_c BF16(relu(acc + bias))[c] w3[c] + b3, H never stored
     int ldd;
     int M_valid;
     int mode;
     int *err;                 // set to a non-zero code if a wait timed out
+    int max_ctas;             // host: CTAs of the persistent form at most (0: one per SM)
 };
 
 template <int BN>
@@ -39,6 +42,32 @@ struct GemmSmem {
     static constexpr uint32_t TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr size_t BYTES = 1024 + kGemmStages * (A_BYTES + B_BYTES) + 256;
 };
+
+// 32 accumulator columns of one row (col .. col + 31 of the output) to
+// memory: FP32 as they are (mode 0) or BF16 relu(acc + bias) (mode 1, the
+// bias slice starting at `bias`).
+__device__ __forceinline__ void gemm_store_32(const GemmEpi &epi, int row, int col, const float (&v)[32],
+                                              const float *bias)
+{
+    if (epi.mode == 0) {
+        float4 *dst = reinterpret_cast<float4 *>(epi.D + (size_t)row * epi.ldd + col);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+        uint32_t packed[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float x0 = fmaxf(v[2 * q] + bias[2 * q], 0.0f);
+            const float x1 = fmaxf(v[2 * q + 1] + bias[2 * q + 1], 0.0f);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            packed[q] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(epi.Db + (size_t)row * epi.ldd + col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+    }
+}
 
 template <int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
@@ -120,29 +149,172 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CU
     for (int c = 0; c < BN; c += 32) {
         float v[32];
         tc::tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-        if (!write) continue;
-        if (epi.mode == 0) {
-            float4 *dst = reinterpret_cast<float4 *>(epi.D + (size_t)row * epi.ldd + n0 + c);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
-            uint32_t packed[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float x0 = fmaxf(v[2 * q] + s_bias[c + 2 * q], 0.0f);
-                const float x1 = fmaxf(v[2 * q + 1] + s_bias[c + 2 * q + 1], 0.0f);
-                const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-                packed[q] = *reinterpret_cast<const uint32_t *>(&h);
-            }
-            uint4 *dst = reinterpret_cast<uint4 *>(epi.Db + (size_t)row * epi.ldd + n0 + c);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
-        }
+        if (write) gemm_store_32(epi, row, n0 + c, v, s_bias + c);
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, SM::TCOLS);
+    if (threadIdx.x == 0 && s_fail) atomicExch(epi.err, s_fail);
+}
+
+// Persistent form, for GEMMs of many row tiles (the scoring forward): at
+// most one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x,
+// ... (row tile t / Ntiles, column tile t % Ntiles, so that neighbouring
+// CTAs share A rows in L2).  Warp 0 (one lane) streams A and B through the
+// shared-memory ring; warp 1 allocates two BN-column accumulators in tensor
+// memory and (one lane) issues the MMAs of tile i into accumulator i & 1;
+// warps 2-5 read tile i's accumulator back (warp w owns TMEM lanes
+// 32 (w mod 4) ..) and store it while the MMAs of tile i + 1 fill the other.
+// Every wait is bounded; a timed-out wait records an error code and ends the
+// role's loop, and the other roles' waits then time out in turn.
+constexpr int kPersistThreads = 192;
+
+template <int BN>
+struct GemmPSmem {
+    static constexpr uint32_t A_BYTES = kBM * kBK * 2;
+    static constexpr uint32_t B_BYTES = BN * kBK * 2;
+    static constexpr uint32_t TCOLS = 2 * BN;   // BN 128 or 256
+    static constexpr size_t BYTES = 1024 + kGemmStages * (A_BYTES + B_BYTES);
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    k_gemm_bf16_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K,
+                           int Mtiles, int Ntiles, GemmEpi epi)
+{
+    static_assert(BN == 128 || BN == 256, "two accumulators must fit the 512 TMEM columns");
+    using SM = GemmPSmem<BN>;
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ int s_fail;
+    __shared__ uint32_t s_tmem;
+    __shared__ float s_bias[1024];
+    __shared__ float s_w3[BN];
+    __shared__ __align__(8) uint64_t bars[2 * kGemmStages + 4];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + kGemmStages * SM::A_BYTES;
+    uint64_t *full = bars, *empty = bars + kGemmStages;
+    uint64_t *acc_full = bars + 2 * kGemmStages, *acc_empty = acc_full + 2;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KC = K / kBK, tiles = Mtiles * Ntiles;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGemmStages; ++s) {
+            tc::mbar_init(full + s, 1);
+            tc::mbar_init(empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(acc_full + a, 1);    // the MMA thread's commit
+            tc::mbar_init(acc_empty + a, 4);   // one arrival per epilogue warp
+        }
+        tc::mbar_fence_init();
+        s_fail = 0;
+    }
+    if (warp == 1) tc::tmem_alloc(&s_tmem, SM::TCOLS);
+    if (epi.mode >= 1)
+        for (int c = threadIdx.x; c < Ntiles * BN; c += blockDim.x) s_bias[c] = epi.bias[c];
+    if (epi.mode == 2)
+        for (int c = threadIdx.x; c < BN; c += blockDim.x) s_w3[c] = epi.w3[c];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: k-step g of this CTA uses ring stage g mod stages
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+                const int m0 = (t / Ntiles) * kBM, n0 = (t % Ntiles) * BN;
+                bool ok = true;
+                for (int kc = 0; kc < KC; ++kc, ++g) {
+                    const uint32_t s = g % kGemmStages;
+                    if (g >= (uint32_t)kGemmStages &&
+                        !tc::mbar_wait(empty + s, ((g / kGemmStages) - 1) & 1, kWaitLimitNs)) {
+                        s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(full + s, SM::A_BYTES + SM::B_BYTES);
+                    tc::tma_load_2d(sA + s * SM::A_BYTES, &tmA, kc * kBK, m0, full + s);
+                    tc::tma_load_2d(sB + s * SM::B_BYTES, &tmB, kc * kBK, n0, full + s);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile i of this CTA accumulates into columns (i & 1) BN
+            const uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+            uint32_t g = 0;
+            int i = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+                const uint32_t a = (uint32_t)i & 1u;
+                if (i >= 2 && !tc::mbar_wait(acc_empty + a, (uint32_t)((i >> 1) - 1) & 1u, kWaitLimitNs)) {
+                    s_fail = 2;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d = tmem + a * (uint32_t)BN;
+                bool ok = true;
+                for (int kc = 0; kc < KC; ++kc, ++g) {
+                    const uint32_t s = g % kGemmStages;
+                    if (!tc::mbar_wait(full + s, (g / kGemmStages) & 1, kWaitLimitNs)) {
+                        s_fail = 3;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(sA + s * SM::A_BYTES), b0 = tc::smem_u32(sB + s * SM::B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k)
+                        tc::mma_bf16(d, tc::sdesc_k_sw128(a0 + 32u * k), tc::sdesc_k_sw128(b0 + 32u * k), idesc,
+                                     kc > 0 || k > 0);
+                    tc::mma_commit(empty + s);
+                }
+                if (!ok) break;
+                tc::mma_commit(acc_full + a);
+            }
+        }
+    } else {
+        // epilogue warps 2-5
+        const int q = warp & 3;
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const uint32_t a = (uint32_t)i & 1u;
+            const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(acc_full + a, (uint32_t)(i >> 1) & 1u, kWaitLimitNs));
+            if (!ok) {
+                if (lane == 0) s_fail = 4;
+                break;
+            }
+            tc::fence_after_sync();
+            const int m0 = (t / Ntiles) * kBM, n0 = (t % Ntiles) * BN;
+            const int row = m0 + q * 32 + lane;
+            const bool write = row < epi.M_valid;
+            float dot = 0.0f;   // mode 2: the output unit, columns in order
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                float v[32];
+                tc::tmem_ld_32cols(tmem + ((uint32_t)(q * 32) << 16) + a * (uint32_t)BN + (uint32_t)c, v);
+                if (epi.mode == 2) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + s_bias[c + j], 0.0f)));
+                        dot = fmaf(h, s_w3[c + j], dot);
+                    }
+                } else if (write) {
+                    gemm_store_32(epi, row, n0 + c, v, s_bias + n0 + c);
+                }
+            }
+            if (epi.mode == 2 && write) epi.y[row] = dot + epi.b3[0];
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(acc_empty + a);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, SM::TCOLS);
     if (threadIdx.x == 0 && s_fail) atomicExch(epi.err, s_fail);
 }
 
@@ -198,8 +370,41 @@ static int launch_gemm_bn(const CUtensorMap &ta, const CUtensorMap &tb, int Mtil
     return FFS_OK;
 }
 
+template <int BN>
+static int launch_gemm_persistent(const CUtensorMap &ta, const CUtensorMap &tb, int Mtiles, int N, int K,
+                                  const GemmEpi &epi, int ctas, cudaStream_t st)
+{
+    const size_t smem = GemmPSmem<BN>::BYTES;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16_persistent<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    k_gemm_bf16_persistent<BN><<<ctas, kPersistThreads, smem, st>>>(ta, tb, K, Mtiles, N / BN, epi);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+static int device_sms()
+{
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (num_sms <= 0) num_sms = 1;
+    }
+    return num_sms;
+}
+
+// The persistent form with one column tile: the output layer can be fused
+// into the last hidden layer's epilogue.
+static bool gemm_fused_output_ok(int M, int N)
+{
+    return (M + kBM - 1) / kBM >= device_sms() && (N == 128 || N == 256);
+}
+
 // D = A[M][K] * B[N][K]^T.  A rows beyond M read as zero (TMA fill); K is
 // rounded up to 64 with zero columns beyond Kvalid; N a multiple of 64.
+// At least one row tile per SM (and N a multiple of 128, at most 1024): the
+// persistent form with two accumulators; otherwise one CTA per tile.
 int gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int Kvalid, GemmEpi epi, cudaStream_t st)
 {
     if (M < 1 || N < 64 || N % 64 || Kvalid < 1) return set_error(FFS_EINVAL, "GEMM shape M=%d N=%d K=%d", M, N, Kvalid);
@@ -209,12 +414,21 @@ int gemm_bf16(const void *A, int lda, const void *B, int ldb, int M, int N, int 
     // more CTAs share the (latency-bound) work; wide tiles once the grid
     // covers the SMs
     const int Mt = (M + kBM - 1) / kBM;
-    static int num_sms = 0;
-    if (!num_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (num_sms <= 0) num_sms = 1;
+    const int num_sms = device_sms();
+    if (epi.mode == 2 && !gemm_fused_output_ok(M, N))
+        return set_error(FFS_EINVAL, "fused output layer: M=%d N=%d", M, N);
+    if (Mt >= num_sms && N % 128 == 0 && N <= 1024) {
+        const int pbn = N % 256 == 0 ? 256 : 128;
+        const int tiles = Mt * (N / pbn);
+        int ctas = std::min(tiles, num_sms);
+        if (epi.max_ctas > 0) ctas = std::min(ctas, epi.max_ctas);
+        CUtensorMap ta, tb;
+        int rc = make_map(&ta, A, M, Kvalid, lda, kBM);
+        if (rc) return rc;
+        if ((rc = make_map(&tb, B, N, Kvalid, ldb, pbn))) return rc;
+        epi.M_valid = M;
+        return pbn == 256 ? launch_gemm_persistent<256>(ta, tb, Mt, N, K, epi, ctas, st)
+                          : launch_gemm_persistent<128>(ta, tb, Mt, N, K, epi, ctas, st);
     }
     while (BN > 64 && (int64_t)Mt * (N / BN) < num_sms) {
         const int nb = BN == 256 ? 128 : BN == 192 ? 64 : 64;
@@ -466,6 +680,12 @@ struct ffs_mlp {
                   *dZ1T = nullptr;
     float *y = nullptr, *dy = nullptr, *dH1 = nullptr, *dZ1 = nullptr;
     int *err = nullptr;
+    // the scoring copy (allocated on demand): what a forward pass reads (BF16
+    // W1 and W2, FP32 b1, b2, w3, b3 at the parameters' offsets) and its own
+    // hidden activations, so that training steps may update the network
+    // while a forward pass scores with the weights of the last copy
+    __nv_bfloat16 *cW1b = nullptr, *cW2b = nullptr, *cH1 = nullptr, *cH2 = nullptr;
+    float *cparams = nullptr;
     std::vector<void *> allocs;
 };
 
@@ -491,31 +711,138 @@ static int refresh_bf16(ffs_mlp *M, cudaStream_t st)
     return FFS_OK;
 }
 
+// What a forward pass reads and writes: the network's own weights and
+// activations (training) or the scoring copy.
+struct MlpFwd {
+    const __nv_bfloat16 *W1b, *W2b;
+    const float *b1, *b2, *w3, *b3;
+    __nv_bfloat16 *H1, *H2;
+};
+
+static MlpFwd fwd_live(const ffs_mlp *M) { return {M->W1b, M->W2b, M->b1, M->b2, M->w3, M->b3, M->H1, M->H2}; }
+
+static MlpFwd fwd_copy(const ffs_mlp *M)
+{
+    const float *c = M->cparams;
+    return {M->cW1b, M->cW2b, c + (M->b1 - M->params), c + (M->b2 - M->params), c + (M->w3 - M->params),
+            c + (M->b3 - M->params), M->cH1, M->cH2};
+}
+
 // The two hidden layers: H1 = relu(x W1^T + b1), H2 = relu(H1 W2^T + b2), BF16.
-static int mlp_hidden(ffs_mlp *M, const void *x, int ldx, int B, cudaStream_t st)
+static int mlp_hidden(ffs_mlp *M, const MlpFwd &w, const void *x, int ldx, int B, cudaStream_t st, int max_ctas = 0)
 {
     GemmEpi e;
     memset(&e, 0, sizeof(e));
     e.err = M->err;
+    e.max_ctas = max_ctas;
     e.mode = 1;
-    e.Db = M->H1;
-    e.bias = M->b1;
+    e.Db = w.H1;
+    e.bias = w.b1;
     e.ldd = M->h1;
-    int rc = gemm_bf16(x, ldx, M->W1b, M->K1, B, M->h1, M->in_dim, e, st);
+    int rc = gemm_bf16(x, ldx, w.W1b, M->K1, B, M->h1, M->in_dim, e, st);
     if (rc) return rc;
-    e.Db = M->H2;
-    e.bias = M->b2;
+    e.Db = w.H2;
+    e.bias = w.b2;
     e.ldd = M->h2;
-    return gemm_bf16(M->H1, M->h1, M->W2b, M->h1, B, M->h2, M->h1, e, st);
+    return gemm_bf16(w.H1, M->h1, w.W2b, M->h1, B, M->h2, M->h1, e, st);
 }
 
-static int mlp_forward(ffs_mlp *M, const void *x, int ldx, int B, float *y, cudaStream_t st)
+static int mlp_forward(ffs_mlp *M, const MlpFwd &w, const void *x, int ldx, int B, float *y, cudaStream_t st,
+                       int max_ctas = 0)
 {
-    int rc = mlp_hidden(M, x, ldx, B, st);
+    if (gemm_fused_output_ok(B, M->h2)) {
+        // large batches: the output unit in layer 2's epilogue (H2 never stored)
+        GemmEpi e;
+        memset(&e, 0, sizeof(e));
+        e.err = M->err;
+        e.max_ctas = max_ctas;
+        e.mode = 1;
+        e.Db = w.H1;
+        e.bias = w.b1;
+        e.ldd = M->h1;
+        int rc = gemm_bf16(x, ldx, w.W1b, M->K1, B, M->h1, M->in_dim, e, st);
+        if (rc) return rc;
+        e.mode = 2;
+        e.Db = nullptr;
+        e.bias = w.b2;
+        e.w3 = w.w3;
+        e.b3 = w.b3;
+        e.y = y;
+        return gemm_bf16(w.H1, M->h1, w.W2b, M->h1, B, M->h2, M->h1, e, st);
+    }
+    int rc = mlp_hidden(M, w, x, ldx, B, st, max_ctas);
     if (rc) return rc;
-    k_out_layer<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, M->h2, M->w3, M->b3, y);
+    k_out_layer<<<(B * 32 + 255) / 256, 256, 0, st>>>(w.H2, B, M->h2, w.w3, w.b3, y);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
+}
+
+// Up to four word copies in one launch (the scoring copy's segments).
+struct CopySegs {
+    uint32_t *dst[4];
+    const uint32_t *src[4];
+    int64_t words[4];
+};
+
+__global__ void k_copy_words(CopySegs c)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int k = 0; k < 4; ++k)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.words[k]; i += stride)
+            c.dst[k][i] = c.src[k][i];
+}
+
+int mlp_enable_copy(ffs_mlp *M)
+{
+    if (M->cparams) return FFS_OK;
+    const size_t nW1 = (size_t)M->h1 * M->K1, nW2 = (size_t)M->h2 * M->h1, Bm = (size_t)M->max_batch;
+    void *p[5] = {};
+    const size_t bytes[5] = {nW1 * 2, nW2 * 2, Bm * M->h1 * 2, Bm * M->h2 * 2, M->n_params * 4};
+    for (int k = 0; k < 5; ++k)
+        if (cudaMalloc(&p[k], bytes[k]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            for (int j = 0; j < k; ++j) cudaFree(p[j]);
+            return set_error(FFS_ENOMEM, "MLP scoring copy");
+        }
+    for (int k = 0; k < 5; ++k) M->allocs.push_back(p[k]);
+    M->cW1b = (__nv_bfloat16 *)p[0];
+    M->cW2b = (__nv_bfloat16 *)p[1];
+    M->cH1 = (__nv_bfloat16 *)p[2];
+    M->cH2 = (__nv_bfloat16 *)p[3];
+    M->cparams = (float *)p[4];
+    return FFS_OK;
+}
+
+// The scoring copy := the weights a forward pass reads, as they are now (in
+// stream order).
+int mlp_take_copy(ffs_mlp *M, cudaStream_t st)
+{
+    if (!M->cparams) return set_error(FFS_EINVAL, "the network has no scoring copy");
+    const size_t nW1 = (size_t)M->h1 * M->K1, nW2 = (size_t)M->h2 * M->h1;
+    const int64_t ob1 = M->b1 - M->params, ob2 = M->b2 - M->params;
+    CopySegs c;
+    c.dst[0] = reinterpret_cast<uint32_t *>(M->cW1b);
+    c.src[0] = reinterpret_cast<const uint32_t *>(M->W1b);
+    c.words[0] = (int64_t)nW1 / 2;   // h1 and K1 are multiples of 64
+    c.dst[1] = reinterpret_cast<uint32_t *>(M->cW2b);
+    c.src[1] = reinterpret_cast<const uint32_t *>(M->W2b);
+    c.words[1] = (int64_t)nW2 / 2;
+    c.dst[2] = reinterpret_cast<uint32_t *>(M->cparams + ob1);
+    c.src[2] = reinterpret_cast<const uint32_t *>(M->params + ob1);
+    c.words[2] = M->h1;                                    // b1
+    c.dst[3] = reinterpret_cast<uint32_t *>(M->cparams + ob2);
+    c.src[3] = reinterpret_cast<const uint32_t *>(M->params + ob2);
+    c.words[3] = (int64_t)M->n_params - ob2;                // b2, w3, b3
+    k_copy_words<<<304, 256, 0, st>>>(c);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int mlp_forward_copy(ffs_mlp *M, const void *x, int ldx, int B, float *y, int max_ctas, cudaStream_t st)
+{
+    if (!M->cparams) return set_error(FFS_EINVAL, "the network has no scoring copy");
+    if (B < 1 || B > M->max_batch) return set_error(FFS_EINVAL, "batch %d outside [1, %d]", B, M->max_batch);
+    return mlp_forward(M, fwd_copy(M), x, ldx, B, y, st, max_ctas);
 }
 
 // Checkpoint blob of a network: this header, then the FP32 parameters, the
@@ -771,7 +1098,7 @@ int ffs_mlp_forward(ffs_mlp *M, const uint16_t *x, int32_t ldx, int32_t B, float
     if (!M || !x || !y) return set_error(FFS_EINVAL, "NULL argument");
     if (B < 1 || B > M->max_batch) return set_error(FFS_EINVAL, "batch %d outside [1, %d]", B, M->max_batch);
     if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
-    return mlp_forward(M, x, ldx, B, y, (cudaStream_t)stream);
+    return mlp_forward(M, fwd_live(M), x, ldx, B, y, (cudaStream_t)stream);
 }
 
 int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *target, int32_t B, float lr,
@@ -783,7 +1110,7 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
         return set_error(FFS_EINVAL, "training batch %d must be a multiple of 128 and <= %d", B, M->max_batch);
     if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = mlp_hidden(M, x, ldx, B, st);
+    int rc = mlp_hidden(M, fwd_live(M), x, ldx, B, st);
     if (rc) return rc;
     const int h1 = M->h1, h2 = M->h2, K1 = M->K1;
     if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, st));

@@ -30,7 +30,11 @@ def _bf16(a):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 256, 128), (300, 192, 540), (1024, 512, 576),
-                                   (128, 576, 1024), (77, 128, 16), (512, 256, 512)])
+                                   (128, 576, 1024), (77, 128, 16), (512, 256, 512),
+                                   # at least one row tile per SM: the persistent form (two
+                                   # accumulators; 128- and 256-column tiles, ragged rows and K)
+                                   (32768, 512, 576), (20000, 256, 512), (19584, 384, 200),
+                                   (40000, 128, 64)])
 def test_gemm_matches_float64(gpu, M, N, K):
     rng = np.random.default_rng(M + N + K)
     lda = (K + 7) // 8 * 8
@@ -73,18 +77,18 @@ def test_mlp_init_matches_oracle_philox_bit_exactly(gpu):
     assert float(got["b3"]) == 0.0 and m.adam_steps() == 0
 
 
-def test_mlp_forward_matches_oracle(gpu):
+@pytest.mark.parametrize("B", [1000, 20000])    # 20000: both layers on the persistent GEMM
+def test_mlp_forward_matches_oracle(gpu, B):
     in_dim, h1, h2 = 540, 512, 256
     p = mlp_params(in_dim, h1, h2, seed=1)
     rng = np.random.default_rng(2)
     p["b1"] = rng.normal(0, 0.05, h1).astype(np.float32)
     p["b2"] = rng.normal(0, 0.05, h2).astype(np.float32)
     p["b3"] = np.float32(0.25)
-    m = gpu.MLP(in_dim, h1, h2, 2048)
+    m = gpu.MLP(in_dim, h1, h2, max(2048, (B + 127) // 128 * 128))
     m.set_params(p)
     back = m.get()
     assert np.array_equal(back["W1"], p["W1"]) and np.array_equal(back["w3"], p["w3"])
-    B = 1000
     X = _features(rng, B, in_dim)
     y = torch.zeros(B, dtype=torch.float32, device="cuda")
     gpu.ffs_mlp_forward(m, _padded(X, 544), 544, B, y)

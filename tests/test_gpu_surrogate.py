@@ -14,7 +14,8 @@ from oracle import mlp as omlp
 pytestmark = pytest.mark.gpu
 
 
-def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_every, seed=7, variant=0):
+def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_every, seed=7, variant=0,
+           overlap=0):
     spec = make_instance(n, S, mlo, mhi, seed=n + S)
     o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
     g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
@@ -31,6 +32,7 @@ def _setup(gpu, n, S, mlo, mhi, rows, cols, n_pseudo, psize, K, warmup, train_ev
     sp.candidates, sp.warmup_generations, sp.train_every = K, warmup, train_every
     sp.train_batch, sp.train_steps = 256, 2
     sp.ring_capacity = max(4096, rows * cols * 4)
+    sp.overlap = overlap
     gpu.ffs_islands_attach_surrogate(isl, net, sp)
     ga = orc.IslandGA(o, orc.Params(seed=seed), 1, rows, cols, n_pseudo, psize)
     return spec, o, g, isl, ga, params
@@ -73,9 +75,10 @@ def test_screened_generations_match_oracle_given_scores(gpu, warmup, variant):
             assert np.max(np.abs(scores - want)) <= 2e-2 * scale, gen
 
 
-def test_screened_training_runs_and_keeps_parity(gpu):
+@pytest.mark.parametrize("overlap", [0, 1])
+def test_screened_training_runs_and_keeps_parity(gpu, overlap):
     rows, cols, K = 16, 16, 8
-    spec, o, g, isl, ga, params = _setup(gpu, 60, 6, 2, 4, rows, cols, 0, 0, K, 1, 1)
+    spec, o, g, isl, ga, params = _setup(gpu, 60, 6, 2, 4, rows, cols, 0, 0, K, 1, 1, overlap=overlap)
     cells = rows * cols
     losses = []
     for gen in range(1, 13):
@@ -98,6 +101,66 @@ def test_screened_training_runs_and_keeps_parity(gpu):
     assert all(np.isfinite(losses)) and all(x > 0 for x in losses)
     assert isl.surrogate.adam_steps() == 2 * 11
     assert np.ptp(scores) > 0
+
+
+@pytest.mark.parametrize("overlap", [0, 1])
+def test_overlap_scores_with_the_weights_of_the_generation_start(gpu, overlap):
+    """overlap = 1: the training round runs beside the whole screen, which
+    scores with the network as it stood when the generation began; overlap =
+    0: the round ends before the scoring, which reads its result.  A large
+    learning rate makes the two networks' scores differ far beyond the
+    forward pass's tolerance, so the test tells the two apart."""
+    rows, cols, K, n = 16, 16, 4, 24
+    spec = make_instance(n, 5, 2, 4, seed=9)
+    g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    prm = gpu.ffs_params_default()
+    prm.migration_mode, prm.migration_gap = 0, 0
+    isl = gpu.Islands(g, prm, 1, rows, cols, 0, 0)
+    net = gpu.MLP(540, 512, 256, rows * cols * K)
+    net.init(5)
+    sp = gpu.ffs_surrogate_params_default()
+    sp.candidates, sp.warmup_generations, sp.train_every = K, 0, 1
+    sp.train_batch, sp.train_steps, sp.lr, sp.ring_capacity = 128, 2, 0.02, 2048
+    sp.overlap = overlap
+    gpu.ffs_islands_attach_surrogate(isl, net, sp)
+    inst_feat = omlp.instance_features(spec.n, spec.S, spec.M, spec.p)
+    cells = rows * cols
+    told_apart = 0
+    for gen in range(1, 7):
+        before = net.get()
+        gpu.ffs_island_step(isl, -1, 1)
+        after = net.get()
+        scores = np.zeros(cells * K, np.float32)
+        cands = np.zeros((cells * K, n), np.int16)
+        gpu.ffs_islands_surrogate_last(isl, scores, None, None, cands, n)
+        torch.cuda.synchronize()
+        X = omlp.features(cands, n, 500, inst_feat)
+        y_before, _ = omlp.forward(before, X, rounded=True)
+        y_after, _ = omlp.forward(after, X, rounded=True)
+        want = y_before if overlap else y_after
+        tol = 2e-2 * (np.mean(np.abs(want)) + 1e-3)
+        assert np.max(np.abs(scores - want)) <= tol, gen
+        told_apart += int(np.max(np.abs(y_before - y_after)) > 10 * tol)
+    assert net.adam_steps() == 2 * 5      # rounds at the start of generations 2..6
+    assert told_apart >= 3
+
+
+def test_overlap_needs_a_ring_of_two_generations(gpu):
+    spec = make_instance(20, 4, 2, 3, seed=3)
+    g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    isl = gpu.Islands(g, gpu.ffs_params_default(), 1, 32, 32, 0, 0)
+    net = gpu.MLP(540, 512, 256, 4096)
+    sp = gpu.ffs_surrogate_params_default()
+    sp.candidates, sp.train_batch, sp.ring_capacity, sp.overlap = 4, 128, 1024 + 128, 1
+    with pytest.raises(gpu.FFSError) as e:
+        gpu.ffs_islands_attach_surrogate(isl, net, sp)
+    assert e.value.status == gpu.FFS_EINVAL
+    sp.overlap = 2
+    sp.ring_capacity = 4096
+    with pytest.raises(gpu.FFSError):
+        gpu.ffs_islands_attach_surrogate(isl, net, sp)
+    sp.overlap = 1
+    gpu.ffs_islands_attach_surrogate(isl, net, sp)
 
 
 def test_trained_screen_beats_plain_ga_at_equal_exact_decodes(gpu):
