@@ -569,13 +569,13 @@ int ffs_mlp_check(ffs_mlp *mlp, ffs_stream stream);
  * generations 1..G (the newest ring_capacity - cells pairs), with the
  * targets standardised by generation G's makespans, (makespan - mean) / std
  * (std at least 1): the screen needs only the ranking of a cell's
- * candidates.  The round runs at the start of generation G + 1, beside its
- * candidate building, and ends before G + 1's candidates are scored; with
- * overlap = 1 it runs beside the whole of generation G + 1 instead, which
- * scores its candidates with the network as it stood when G + 1 began (a
- * copy of the weights taken then: trained through the round after
- * generation G - 1), and ends with the generation (ring_capacity must then
- * hold two generations' pairs).
+ * candidates.  With overlap = 1 (the default) the round runs beside the
+ * whole of generation G + 1, which scores its candidates with the network
+ * as it stood when G + 1 began (a copy of the weights taken then: trained
+ * through the round after generation G - 1), and ends with the generation
+ * (ring_capacity must then hold two generations' pairs); with overlap = 0
+ * it runs beside G + 1's candidate building only and ends before G + 1's
+ * candidates are scored.
  * Pseudo islands are not screened.  The network must have in_dim >= n + 40
  * and max_batch >= cellular cells x candidates; it is used, not owned;
  * ring_capacity must be at least cells + train_batch.  Generations are
@@ -595,7 +595,7 @@ typedef struct {
     int32_t ring_capacity;       /* pairs kept (131072) */
     int32_t warmup_generations;  /* generations scored 0 while the ring fills (5) */
     float lr;                    /* Adam learning rate (1e-3) */
-    int32_t overlap;             /* 1: the training round runs beside the whole screen (0) */
+    int32_t overlap;             /* 1: the training round runs beside the whole screen (1) */
 } ffs_surrogate_params;
 void ffs_surrogate_params_default(ffs_surrogate_params *p);
 int ffs_islands_attach_surrogate(ffs_islands *isl, ffs_mlp *mlp, const ffs_surrogate_params *sp,

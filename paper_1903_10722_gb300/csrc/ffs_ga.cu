@@ -769,16 +769,17 @@ struct SurrogateState {
     ffs_mlp *mlp = nullptr;
     ffs_surrogate_params sp{};
     int P = 0, ldx = 0, nfeat = 40;
+    int xw = 0;                    // width of a candidate's scoring input row (the job positions)
     int cells_total = 0;           // cells of all cellular islands
     int16_t *cand = nullptr;       // [cells_total * K][ld]
-    void *X = nullptr;             // BF16 [cells_total * K][ldx]
+    void *X = nullptr;             // BF16 [cells_total * K][xw]
     float *scores = nullptr;       // [cells_total * K]
     int32_t *chosen = nullptr;     // [cells_total]
     int16_t *ring_rows = nullptr;  // [ring_cap][ld]
     int32_t *ring_ms = nullptr;
     long long ring_cap = 0, ring_count = 0;
     float *inst_feat = nullptr;    // [nfeat]
-    void *train_X = nullptr;       // BF16 [train_batch][ldx]
+    void *train_X = nullptr;       // BF16 [train_steps][train_batch][ldx]
     float *train_t = nullptr, *loss = nullptr;
     long long train_rounds = 0;
     std::vector<int> cell_islands;
@@ -1005,9 +1006,9 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
         const int ncells = batch.count * cells;
         int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
         // the candidates, and in warm generations their network inputs in the same launch
-        void *X = static_cast<char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
-        int rc = launch_sur_candidates(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, R->P, R->inst_feat,
-                                       R->nfeat, warm ? X : nullptr, R->ldx, st);
+        void *X = static_cast<char *>(R->X) + (int64_t)offset * K * R->xw * 2;
+        int rc = launch_sur_candidates(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, warm ? X : nullptr, R->xw,
+                                       st);
         if (rc) return rc;
         offset += ncells;
     }
@@ -1019,9 +1020,9 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
         const int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
         float *scores = R->scores + (int64_t)offset * K;
         if (warm) {
-            const void *X = static_cast<const char *>(R->X) + (int64_t)offset * K * R->ldx * 2;
-            rc = use_copy ? mlp_forward_copy(R->mlp, X, R->ldx, ncells * K, scores, kScreenForwardCtas, st)
-                          : ffs_mlp_forward(R->mlp, static_cast<const uint16_t *>(X), R->ldx, ncells * K, scores, st);
+            const void *X = static_cast<const char *>(R->X) + (int64_t)offset * K * R->xw * 2;
+            rc = mlp_forward_folded(R->mlp, use_copy, X, R->xw, S->inst->n, R->P, R->inst_feat, R->nfeat, ncells * K,
+                                    scores, use_copy ? kScreenForwardCtas : 0, st);
             if (rc) return rc;
         } else if ((rc = launch_fill_f32(scores, (int64_t)ncells * K, 0.0f, st))) {
             return rc;
@@ -1043,14 +1044,17 @@ static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
     SurrogateState *R = S->sur;
     int rc0 = launch_sur_norm(R->ring_ms, R->ring_cap, R->d_ctr, R->cells_total, R->d_norm, st);
     if (rc0) return rc0;
-    for (int s = 0; s < R->sp.train_steps; ++s) {
-        int rc = launch_sur_gather(R->ring_rows, R->ring_ms, R->ring_cap, R->cells_total, R->d_ctr, S->ld, S->prm.seed,
-                                   R->sp.train_batch, R->train_t, R->d_norm, S->inst->n, R->P, R->inst_feat, R->nfeat,
-                                   R->train_X, R->ldx, st);
-        if (rc) return rc;
-        if ((rc = launch_sur_tick(R->d_ctr, 1, 1, st))) return rc;
-        if ((rc = ffs_mlp_train_step(R->mlp, static_cast<const uint16_t *>(R->train_X), R->ldx, R->train_t,
-                                     R->sp.train_batch, R->sp.lr, R->loss, st)))
+    // every step's batch in one launch (batch k drawn as the (ctr[1] + k)-th)
+    const int B = R->sp.train_batch, steps = R->sp.train_steps;
+    int rc = launch_sur_gather(R->ring_rows, R->ring_ms, R->ring_cap, R->cells_total, R->d_ctr, S->ld, S->prm.seed, B,
+                               steps, R->train_t, R->d_norm, S->inst->n, R->P, R->inst_feat, R->nfeat, R->train_X,
+                               R->ldx, st);
+    if (rc) return rc;
+    if ((rc = launch_sur_tick(R->d_ctr, 1, steps, st))) return rc;
+    for (int s = 0; s < steps; ++s) {
+        const void *X = static_cast<const char *>(R->train_X) + (int64_t)s * B * R->ldx * 2;
+        if ((rc = ffs_mlp_train_step(R->mlp, static_cast<const uint16_t *>(X), R->ldx, R->train_t + (int64_t)s * B, B,
+                                     R->sp.lr, R->loss, st)))
             return rc;
     }
     return FFS_OK;
@@ -1375,6 +1379,7 @@ void ffs_surrogate_params_default(ffs_surrogate_params *p)
     p->ring_capacity = 1 << 17;
     p->warmup_generations = 5;
     p->lr = 1e-3f;
+    p->overlap = 1;
 }
 
 // The training round's stream.  With overlap it takes the device's highest
@@ -1436,14 +1441,16 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     };
     const size_t ncand = (size_t)cells_total * K;
     R->cand = (int16_t *)alloc(ncand * S->ld * 2);
-    R->X = alloc(ncand * R->ldx * 2);
+    R->xw = round_up(n, 8);
+    R->X = alloc(ncand * R->xw * 2);
     R->scores = (float *)alloc(ncand * 4);
     R->chosen = (int32_t *)alloc((size_t)cells_total * 4);
     R->ring_rows = (int16_t *)alloc((size_t)R->ring_cap * S->ld * 2);
     R->ring_ms = (int32_t *)alloc((size_t)R->ring_cap * 4);
     R->inst_feat = (float *)alloc(nfeat * 4);
-    R->train_X = alloc((size_t)sp->train_batch * R->ldx * 2);
-    R->train_t = (float *)alloc((size_t)sp->train_batch * 4);
+    const size_t train_rows = (size_t)sp->train_batch * std::max(sp->train_steps, 1);
+    R->train_X = alloc(train_rows * R->ldx * 2);
+    R->train_t = (float *)alloc(train_rows * 4);
     R->loss = (float *)alloc(4);
     R->d_ctr = (long long *)alloc(3 * sizeof(long long));
     R->d_norm = (float *)alloc(2 * sizeof(float));

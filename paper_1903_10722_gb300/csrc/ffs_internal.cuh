@@ -283,8 +283,7 @@ int validate_rows(const void *p, int ld, int n);
 
 // Surrogate screening (ffs_surrogate.cu).
 int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
-                          int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat, void *X, int ldx,
-                          cudaStream_t st);
+                          int ld, int K, int16_t *cand, void *X, int xw, cudaStream_t st);
 int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
                       int ld, int K, const int16_t *cand, const float *scores, int32_t *chosen, int16_t *ring_rows,
                       int32_t *ring_ms, long long ring_cap, const long long *ctr, int B_req, int T_req,
@@ -292,8 +291,9 @@ int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const Island
 int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm,
                     cudaStream_t st);
 int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
-                      const long long *ctr, int ld, uint64_t seed, int B, float *targets, const float *norm, int n,
-                      int P, const float *inst_feat, int nfeat, void *X, int ldx, cudaStream_t st);
+                      const long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
+                      const float *norm, int n, int P, const float *inst_feat, int nfeat, void *X, int ldx,
+                      cudaStream_t st);
 int launch_sur_tick(long long *ctr, int which, long long add, cudaStream_t st);
 int launch_fill_f32(float *p, int64_t n, float v, cudaStream_t st);
 int mlp_in_dim(const ffs_mlp *m);
@@ -301,12 +301,18 @@ int mlp_max_batch(const ffs_mlp *m);
 int64_t mlp_state_bytes(const ffs_mlp *m);
 int mlp_save(const ffs_mlp *m, void *host, cudaStream_t st);                   // synchronises
 int mlp_load(ffs_mlp *m, const void *host, int64_t size, cudaStream_t st);     // synchronises
-// The scoring copy: allocate it (idempotent), take it (stream-ordered), and a
-// forward pass that reads it (and writes activations of its own; max_ctas
-// > 0 caps the CTAs of its persistent GEMMs).
+// The scoring copy: allocate it (idempotent) and take it (stream-ordered);
+// mlp_forward_folded reads it when asked to (with activations of its own;
+// max_ctas > 0 caps the CTAs of its persistent GEMMs).
 int mlp_enable_copy(ffs_mlp *m);
 int mlp_take_copy(ffs_mlp *m, cudaStream_t st);
-int mlp_forward_copy(ffs_mlp *m, const void *x, int ldx, int B, float *y, int max_ctas, cudaStream_t st);
+// Forward of rows whose network input is xpos[j] for j < kpos, zero for
+// kpos <= j < P, the vector feat at [P, P + nfeat) and zero beyond: the
+// constant block is folded into layer 1's bias, layer 1 contracts over the
+// kpos leading columns (xpos rows of ldxpos BF16 values).  The weights read
+// are the scoring copy's (use_copy) or the network's own.
+int mlp_forward_folded(ffs_mlp *m, bool use_copy, const void *xpos, int ldxpos, int kpos, int P, const float *feat,
+                       int nfeat, int B, float *y, int max_ctas, cudaStream_t st);
 
 inline int spread_threads(const ffs_instance *inst, int64_t units, int T_req)
 {

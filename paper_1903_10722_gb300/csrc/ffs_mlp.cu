@@ -189,6 +189,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     __shared__ uint32_t s_tmem;
     __shared__ float s_bias[1024];
     __shared__ float s_w3[BN];
+    // each epilogue warp's 32 x 32 BF16 output chunk, rows padded to 80 bytes
+    // (conflict-free 16-byte writes by row and reads by 16-byte column)
+    __shared__ __align__(16) uint32_t s_stage[4][32 * 20];
     __shared__ __align__(8) uint64_t bars[2 * kGemmStages + 4];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = base;
@@ -289,22 +292,60 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             }
             tc::fence_after_sync();
             const int m0 = (t / Ntiles) * kBM, n0 = (t % Ntiles) * BN;
-            const int row = m0 + q * 32 + lane;
+            const int row0 = m0 + q * 32, row = row0 + lane;
             const bool write = row < epi.M_valid;
+            const uint32_t tacc = tmem + ((uint32_t)(q * 32) << 16) + a * (uint32_t)BN;
+            uint32_t *stage = s_stage[q];
             float dot = 0.0f;   // mode 2: the output unit, columns in order
-#pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                float v[32];
-                tc::tmem_ld_32cols(tmem + ((uint32_t)(q * 32) << 16) + a * (uint32_t)BN + (uint32_t)c, v);
+            // one 32-column chunk of this thread's row (values in u)
+            auto chunk = [&](const uint32_t (&u)[32], int c) {
                 if (epi.mode == 2) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + s_bias[c + j], 0.0f)));
-                        dot = fmaf(h, s_w3[c + j], dot);
+                        const float x = fmaxf(__uint_as_float(u[j]) + s_bias[c + j], 0.0f);
+                        dot = fmaf(__bfloat162float(__float2bfloat16_rn(x)), s_w3[c + j], dot);
                     }
+                } else if (epi.mode == 1) {
+                    // BF16 relu(acc + bias) into the warp's staging rows, then
+                    // out as 64-byte row segments, 8 rows per store
+                    uint32_t packed[16];
+#pragma unroll
+                    for (int h = 0; h < 16; ++h) {
+                        const float x0 = fmaxf(__uint_as_float(u[2 * h]) + s_bias[n0 + c + 2 * h], 0.0f);
+                        const float x1 = fmaxf(__uint_as_float(u[2 * h + 1]) + s_bias[n0 + c + 2 * h + 1], 0.0f);
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(x0, x1);
+                        packed[h] = *reinterpret_cast<const uint32_t *>(&b);
+                    }
+                    uint4 *srow = reinterpret_cast<uint4 *>(stage + lane * 20);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+                        srow[h] = make_uint4(packed[4 * h], packed[4 * h + 1], packed[4 * h + 2], packed[4 * h + 3]);
+                    __syncwarp();
+#pragma unroll
+                    for (int it = 0; it < 4; ++it) {
+                        const int r = 8 * it + (lane >> 2), h = lane & 3;
+                        const uint4 val = *reinterpret_cast<const uint4 *>(stage + r * 20 + 4 * h);
+                        if (row0 + r < epi.M_valid)
+                            *reinterpret_cast<uint4 *>(epi.Db + (size_t)(row0 + r) * epi.ldd + n0 + c + 8 * h) = val;
+                    }
+                    __syncwarp();   // the staging rows are rewritten by the next chunk
                 } else if (write) {
+                    float v[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
                     gemm_store_32(epi, row, n0 + c, v, s_bias + n0 + c);
                 }
+            };
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 64) {
+                uint32_t u0[32], u1[32];
+                tc::tmem_ld_32cols_async(tacc + (uint32_t)c, u0);
+                tc::tmem_ld_32cols_async(tacc + (uint32_t)c + 32u, u1);
+                tc::tmem_wait_ld();
+                tc::reg_fence32(u0);
+                tc::reg_fence32(u1);
+                chunk(u0, c);
+                chunk(u1, c + 32);
             }
             if (epi.mode == 2 && write) epi.y[row] = dot + epi.b3[0];
             tc::fence_before_sync();
@@ -475,6 +516,23 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *src, int rows, int cols, i
     }
 }
 
+// Layer 1's bias for inputs whose columns [P, P + nfeat) hold the same
+// vector `feat` in every row (warp per output unit o): out[o] = b1[o] +
+// sum_i W1b[o][P + i] BF16(feat[i]), the products as the tensor cores would
+// form them (BF16 operands, FP32 sums; per-lane partials, then a fixed
+// shuffle tree).
+__global__ void k_fold_bias(const __nv_bfloat16 *W1b, int K1, const float *b1, int P, const float *feat, int nfeat,
+                            int h1, float *out)
+{
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (o >= h1) return;
+    float acc = 0.0f;
+    for (int i = lane; i < nfeat; i += 32)
+        acc = fmaf(__bfloat162float(W1b[(size_t)o * K1 + P + i]), __bfloat162float(__float2bfloat16_rn(feat[i])), acc);
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, d);
+    if (lane == 0) out[o] = b1[o] + acc;
+}
+
 // y[b] = H2[b] . w3 + b3 (warp per row)
 __global__ void k_out_layer(const __nv_bfloat16 *H2, int B, int h2, const float *w3, const float *b3, float *y)
 {
@@ -626,13 +684,14 @@ __global__ void k_mlp_init(float *W, int rows, int cols, int ld, uint64_t seed, 
 // Adam (Kingma & Ba 2015) over the concatenated parameters.  The step count
 // lives on the device (t_prev = steps taken so far), so a training step can
 // be replayed from a CUDA graph; this step is t = t_prev + 1, with the bias
-// corrections 1 - b1^t and 1 - b2^t; k_adam_tick then advances the count.
+// corrections 1 - b1^t and 1 - b2^t; the last block to finish (counted in
+// blocks_done, reset by it) advances the count, after every block has read it.
 // It also writes the BF16 copies the GEMMs read: W1b[i] for the W1 block
 // [0, nW1) and, for the W2 block [w2_off, w2_off + h2 h1), W2b[o][c] and its
 // transpose W2Tb[c][o].
 __global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
-                            float eps, const long long *t_prev, int nW1, int w2_off, int h1, int h2,
-                            __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb)
+                            float eps, long long *t_prev, unsigned int *blocks_done, int nW1, int w2_off, int h1,
+                            int h2, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb)
 {
     const float t = (float)(*t_prev + 1);
     const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
@@ -654,11 +713,14 @@ __global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n,
             W2Tb[(size_t)c * h2 + o] = pb;
         }
     }
-}
-
-__global__ void k_adam_tick(long long *t)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
+    __syncthreads();   // this block's threads have read the count
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(blocks_done, 1u) == gridDim.x - 1) {
+            *t_prev += 1;
+            *blocks_done = 0u;
+        }
+    }
 }
 
 }  // namespace fgpu
@@ -668,6 +730,7 @@ using namespace fgpu;
 struct ffs_mlp {
     int in_dim = 0, K1 = 0, h1 = 0, h2 = 0, max_batch = 0;
     long long *d_adam_t = nullptr;   // Adam steps taken (device, so training steps can be graph-replayed)
+    unsigned int *d_adam_done = nullptr;   // blocks of the running Adam launch that have finished
     // parameters (FP32 masters): W1 [h1][K1] (columns >= in_dim stay 0), b1, W2 [h2][h1], b2, w3 [h2], b3 [1]
     float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *w3 = nullptr, *b3 = nullptr;
     float *gW1 = nullptr, *gb1 = nullptr, *gW2 = nullptr, *gb2 = nullptr, *gw3 = nullptr, *gb3 = nullptr;
@@ -686,6 +749,11 @@ struct ffs_mlp {
     // while a forward pass scores with the weights of the last copy
     __nv_bfloat16 *cW1b = nullptr, *cW2b = nullptr, *cH1 = nullptr, *cH2 = nullptr;
     float *cparams = nullptr;
+    float *fold = nullptr;   // [h1]: layer 1's bias with a constant input block folded in
+    // a training step's side branches (forked from and joined back into the
+    // caller's stream, so that a captured step keeps them in its graph)
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t ev[7] = {};
     std::vector<void *> allocs;
 };
 
@@ -698,6 +766,10 @@ static void mlp_free(ffs_mlp *M)
 {
     if (!M) return;
     for (void *p : M->allocs) cudaFree(p);
+    for (cudaStream_t s : M->aux)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : M->ev)
+        if (e) cudaEventDestroy(e);
     delete M;
 }
 
@@ -838,12 +910,48 @@ int mlp_take_copy(ffs_mlp *M, cudaStream_t st)
     return FFS_OK;
 }
 
-int mlp_forward_copy(ffs_mlp *M, const void *x, int ldx, int B, float *y, int max_ctas, cudaStream_t st)
+int mlp_forward_folded(ffs_mlp *M, bool use_copy, const void *xpos, int ldxpos, int kpos, int P, const float *feat,
+                       int nfeat, int B, float *y, int max_ctas, cudaStream_t st)
 {
-    if (!M->cparams) return set_error(FFS_EINVAL, "the network has no scoring copy");
+    if (use_copy && !M->cparams) return set_error(FFS_EINVAL, "the network has no scoring copy");
     if (B < 1 || B > M->max_batch) return set_error(FFS_EINVAL, "batch %d outside [1, %d]", B, M->max_batch);
-    return mlp_forward(M, fwd_copy(M), x, ldx, B, y, st, max_ctas);
+    if (kpos < 1 || kpos > P || P + nfeat > M->in_dim || ldxpos < kpos || ldxpos % 8)
+        return set_error(FFS_EINVAL, "folded input: kpos %d, P %d, nfeat %d, ld %d", kpos, P, nfeat, ldxpos);
+    const MlpFwd w = use_copy ? fwd_copy(M) : fwd_live(M);
+    k_fold_bias<<<(M->h1 * 32 + 255) / 256, 256, 0, st>>>(w.W1b, M->K1, w.b1, P, feat, nfeat, M->h1, M->fold);
+    FFS_CUDA_TRY(cudaGetLastError());
+    MlpFwd wf = w;
+    wf.b1 = M->fold;
+    // layer 1 over the kpos leading columns only (TMA reads the rest of the
+    // 64-column step as zeros), with the folded bias
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    e.err = M->err;
+    e.max_ctas = max_ctas;
+    e.mode = 1;
+    e.Db = wf.H1;
+    e.bias = wf.b1;
+    e.ldd = M->h1;
+    int rc = gemm_bf16(xpos, ldxpos, wf.W1b, M->K1, B, M->h1, kpos, e, st);
+    if (rc) return rc;
+    if (gemm_fused_output_ok(B, M->h2)) {
+        e.mode = 2;
+        e.Db = nullptr;
+        e.bias = wf.b2;
+        e.w3 = wf.w3;
+        e.b3 = wf.b3;
+        e.y = y;
+        return gemm_bf16(wf.H1, M->h1, wf.W2b, M->h1, B, M->h2, M->h1, e, st);
+    }
+    e.Db = wf.H2;
+    e.bias = wf.b2;
+    e.ldd = M->h2;
+    if ((rc = gemm_bf16(wf.H1, M->h1, wf.W2b, M->h1, B, M->h2, M->h1, e, st))) return rc;
+    k_out_layer<<<(B * 32 + 255) / 256, 256, 0, st>>>(wf.H2, B, M->h2, wf.w3, wf.b3, y);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
 }
+
 
 // Checkpoint blob of a network: this header, then the FP32 parameters, the
 // Adam first and second moments (n_params each, the internal order: W1
@@ -960,10 +1068,26 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->dZ1 = (float *)alloc(Bm * h1 * 4);
     M->err = (int *)alloc(4);
     M->d_adam_t = (long long *)alloc(8);
+    M->d_adam_done = (unsigned int *)alloc(4);
+    M->fold = (float *)alloc((size_t)h1 * 4);
     for (void *p : M->allocs)
         if (!p) {
             mlp_free(M);
             return set_error(FFS_ENOMEM, "MLP buffers");
+        }
+    for (cudaStream_t &s : M->aux)
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            s = nullptr;
+            mlp_free(M);
+            return set_error(FFS_ECUDA, "MLP streams");
+        }
+    for (cudaEvent_t &e : M->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            e = nullptr;
+            mlp_free(M);
+            return set_error(FFS_ECUDA, "MLP events");
         }
     float *p = M->params, *g = M->grads;
     M->W1 = p; M->gW1 = g; p += nW1; g += nW1;
@@ -974,7 +1098,7 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->b3 = p; M->gb3 = g;
     if (cudaMemset(M->params, 0, M->n_params * 4) || cudaMemset(M->m, 0, M->n_params * 4) ||
         cudaMemset(M->v, 0, M->n_params * 4) || cudaMemset(M->grads, 0, M->n_params * 4) || cudaMemset(M->err, 0, 4) ||
-        cudaMemset(M->d_adam_t, 0, 8) ||
+        cudaMemset(M->d_adam_t, 0, 8) || cudaMemset(M->d_adam_done, 0, 4) ||
         refresh_bf16(M, 0) || cudaDeviceSynchronize()) {
         mlp_free(M);
         return set_error(FFS_ECUDA, "MLP initialisation");
@@ -1109,42 +1233,73 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     if (B < 128 || B % 128 || B > M->max_batch)
         return set_error(FFS_EINVAL, "training batch %d must be a multiple of 128 and <= %d", B, M->max_batch);
     if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = mlp_hidden(M, fwd_live(M), x, ldx, B, st);
-    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream, s1 = M->aux[0], s2 = M->aux[1];
+    cudaEvent_t e_fork = M->ev[0], e_h1 = M->ev[1], e_dz2 = M->ev[2], e_xt = M->ev[3], e_dz1 = M->ev[4],
+                e_s1 = M->ev[5], e_s2 = M->ev[6];
     const int h1 = M->h1, h2 = M->h2, K1 = M->K1;
+    // The step's dependency graph on three streams; the caller's stream `st`
+    // carries the critical path (forward, loss, dH1, dZ1, gW1, Adam), s1 and
+    // s2 the work beside it, joined back into `st` before Adam.
+    FFS_CUDA_TRY(cudaEventRecord(e_fork, st));
+    FFS_CUDA_TRY(cudaStreamWaitEvent(s1, e_fork, 0));
+    FFS_CUDA_TRY(cudaStreamWaitEvent(s2, e_fork, 0));
+    // s1: X^T for gW1 = dZ1^T X (B = XT [K1][B], zero rows beyond in_dim)
+    k_transpose_bf16<<<dim3((K1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s1>>>(
+        reinterpret_cast<const __nv_bfloat16 *>(x), B, M->in_dim, ldx, M->XT, B);
+    if (K1 > M->in_dim) FFS_CUDA_TRY(cudaMemsetAsync(M->XT + (size_t)M->in_dim * B, 0, (size_t)(K1 - M->in_dim) * B * 2, s1));
+    FFS_CUDA_TRY(cudaEventRecord(e_xt, s1));
+    // st: the forward pass's hidden layers
     if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, st));
-    // output layer, loss, its backpropagated signal, then its gradients
-    k_out_loss_dz2<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, h2, M->w3, M->b3, target, M->dy, loss, M->dZ2,
-                                                          M->dZ2T);
-    k_out_grads<<<(h2 + 31) / 32, dim3(32, 32), 0, st>>>(M->H2, M->dZ2, M->dy, B, h2, M->gw3, M->gb2, M->gb3);
-    // gW2 = dZ2^T H1: A = dZ2T [h2][B], B = H1T [h1][B]
-    k_transpose_bf16<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(M->H1, B, h1, h1, M->H1T, B);
     GemmEpi e;
     memset(&e, 0, sizeof(e));
     e.err = M->err;
+    e.mode = 1;
+    e.Db = M->H1;
+    e.bias = M->b1;
+    e.ldd = h1;
+    int rc = gemm_bf16(x, ldx, M->W1b, K1, B, h1, M->in_dim, e, st);
+    if (rc) return rc;
+    FFS_CUDA_TRY(cudaEventRecord(e_h1, st));
+    e.Db = M->H2;
+    e.bias = M->b2;
+    e.ldd = h2;
+    if ((rc = gemm_bf16(M->H1, h1, M->W2b, h1, B, h2, h1, e, st))) return rc;
+    // s2: H1^T for gW2 = dZ2^T H1, beside layer 2
+    FFS_CUDA_TRY(cudaStreamWaitEvent(s2, e_h1, 0));
+    k_transpose_bf16<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s2>>>(M->H1, B, h1, h1, M->H1T, B);
+    // st: output layer, loss and its backpropagated signal
+    k_out_loss_dz2<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, h2, M->w3, M->b3, target, M->dy, loss, M->dZ2,
+                                                          M->dZ2T);
+    FFS_CUDA_TRY(cudaEventRecord(e_dz2, st));
+    // s2: the output layer's gradients and gW2 = dZ2^T H1 (A = dZ2T [h2][B], B = H1T [h1][B])
+    FFS_CUDA_TRY(cudaStreamWaitEvent(s2, e_dz2, 0));
+    k_out_grads<<<(h2 + 31) / 32, dim3(32, 32), 0, s2>>>(M->H2, M->dZ2, M->dy, B, h2, M->gw3, M->gb2, M->gb3);
     e.mode = 0;
     e.D = M->gW2;
     e.ldd = h1;
-    if ((rc = gemm_bf16(M->dZ2T, B, M->H1T, B, h2, h1, B, e, st))) return rc;
-    // dH1 = dZ2 W2: A = dZ2 [B][h2], B = W2T [h1][h2]
+    if ((rc = gemm_bf16(M->dZ2T, B, M->H1T, B, h2, h1, B, e, s2))) return rc;
+    FFS_CUDA_TRY(cudaEventRecord(e_s2, s2));
+    // st: dH1 = dZ2 W2 (A = dZ2 [B][h2], B = W2T [h1][h2]), then dZ1
     e.D = M->dH1;
     e.ldd = h1;
     if ((rc = gemm_bf16(M->dZ2, h2, M->W2Tb, h2, B, h1, h2, e, st))) return rc;
     k_dz1T<<<512, 256, 0, st>>>(M->dH1, M->H1, B, h1, M->dZ1T, M->dZ1);
-    k_colsum<float><<<(h1 + 31) / 32, dim3(32, 32), 0, st>>>(M->dZ1, nullptr, B, h1, M->gb1);
-    // gW1 = dZ1^T X: A = dZ1T [h1][B], B = XT [K1][B]
-    k_transpose_bf16<<<dim3((K1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
-        reinterpret_cast<const __nv_bfloat16 *>(x), B, M->in_dim, ldx, M->XT, B);
-    if (K1 > M->in_dim) FFS_CUDA_TRY(cudaMemsetAsync(M->XT + (size_t)M->in_dim * B, 0, (size_t)(K1 - M->in_dim) * B * 2, st));
+    FFS_CUDA_TRY(cudaEventRecord(e_dz1, st));
+    // s1: gb1 = column sums of dZ1, beside gW1
+    FFS_CUDA_TRY(cudaStreamWaitEvent(s1, e_dz1, 0));
+    k_colsum<float><<<(h1 + 31) / 32, dim3(32, 32), 0, s1>>>(M->dZ1, nullptr, B, h1, M->gb1);
+    FFS_CUDA_TRY(cudaEventRecord(e_s1, s1));
+    // st: gW1 = dZ1^T X (A = dZ1T [h1][B], B = XT [K1][B])
+    FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_xt, 0));
     e.D = M->gW1;
     e.ldd = K1;
     if ((rc = gemm_bf16(M->dZ1T, B, M->XT, B, h1, K1, B, e, st))) return rc;
-    // Adam, writing the BF16 weight copies of the next forward pass as it goes
+    // join, then Adam, writing the BF16 weight copies of the next forward pass as it goes
+    FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_s1, 0));
+    FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_s2, 0));
     const int nW1 = h1 * K1, w2_off = nW1 + h1;
     k_adam_bf16<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
-                                      M->d_adam_t, nW1, w2_off, h1, h2, M->W1b, M->W2b, M->W2Tb);
-    k_adam_tick<<<1, 32, 0, st>>>(M->d_adam_t);
+                                      M->d_adam_t, M->d_adam_done, nW1, w2_off, h1, h2, M->W1b, M->W2b, M->W2Tb);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }

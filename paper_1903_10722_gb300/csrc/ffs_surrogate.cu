@@ -41,6 +41,24 @@ __device__ __forceinline__ void warp_write_features(const int16_t *row, int n, i
     __syncwarp();
 }
 
+// The scoring form of a row's network input, written by the whole warp:
+// the job positions x[j] = position of job j / (n - 1) for j < n and zeros
+// up to xw (a multiple of 8); the constant rest of the input (zeros, the
+// instance features) is folded into the first layer's bias by the forward
+// pass that reads these rows.
+__device__ __forceinline__ void warp_write_positions(const int16_t *row, int n, int xw, __nv_bfloat16 *x)
+{
+    const int lane = threadIdx.x & 31;
+    const float denom = (float)(n > 1 ? n - 1 : 1);
+    for (int g8 = lane; g8 < (xw >> 3); g8 += 32) reinterpret_cast<uint4 *>(x)[g8] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    for (int q = lane; q < n; q += 32) {
+        const int j = row[q];
+        if ((unsigned)j < (unsigned)n) x[j] = __float2bfloat16_rn((float)q / denom);
+    }
+    __syncwarp();
+}
+
 // Candidates built per warp: a warp builds its children one after another
 // with all 32 lanes, so few children per warp and many warps hide the
 // parents' load latency.
@@ -50,10 +68,10 @@ constexpr int kCandPerWarp = 4;
 // crossover, swap mutation) drawn from the stream of purpose
 // kPurposeSurrogateBase + k.  Lane l < kCandPerWarp of warp w builds
 // candidate w * kCandPerWarp + l.  With X non-null, the warp then writes its
-// candidates' network inputs (warp_write_features).
+// candidates' job positions as network input rows of xw values
+// (warp_write_positions).
 __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatch batch, int rows, int cols, int n,
-                                 int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat,
-                                 __nv_bfloat16 *X, int ldx)
+                                 int ld, int K, int16_t *cand, __nv_bfloat16 *X, int xw)
 {
     extern __shared__ uint32_t bits_smem[];
     const int cells = rows * cols;
@@ -122,7 +140,7 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
         const int j0 = __ffs(todo) - 1;
         todo &= todo - 1u;
         const int tj = gw * kCandPerWarp + j0;
-        warp_write_features(cand + (int64_t)tj * ld, n, P, inst_feat, nfeat, X + (int64_t)tj * ldx, ldx);
+        warp_write_positions(cand + (int64_t)tj * ld, n, xw, X + (int64_t)tj * xw);
     }
 }
 
@@ -322,29 +340,31 @@ __global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const lon
     }
 }
 
-// Training batch: B pairs drawn uniformly (Philox, purpose
-// kPurposeTrainSample, generation field = batches drawn before, ctr[1]) from
-// the V = min(ctr[2], ring_cap - recent) newest pairs before the current
-// generation (pair i = the i-th newest, slot (ctr[2] - 1 - i) mod ring_cap;
-// the current generation writes the `recent` slots after them), written as
-// network inputs X (one warp per sample); target = (makespan - norm[0]) *
-// norm[1].
+// Training batches k = 0 .. batches - 1 of B pairs each, drawn uniformly
+// (Philox, purpose kPurposeTrainSample, generation field = batches drawn
+// before it, ctr[1] + k) from the V = min(ctr[2], ring_cap - recent) newest
+// pairs before the current generation (pair i = the i-th newest, slot
+// (ctr[2] - 1 - i) mod ring_cap; the current generation writes the `recent`
+// slots after them), written as network inputs X (row k B + b, one warp per
+// sample); target = (makespan - norm[0]) * norm[1].
 __global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
-                             const long long *ctr, int ld, uint64_t seed, int B, float *targets, const float *norm,
-                             int n, int P, const float *inst_feat, int nfeat, __nv_bfloat16 *X, int ldx)
+                             const long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
+                             const float *norm, int n, int P, const float *inst_feat, int nfeat, __nv_bfloat16 *X,
+                             int ldx)
 {
     const long long room = ring_cap - recent;
     const long long valid = ctr[2] < room ? ctr[2] : room;
     const long long newest = (ctr[2] - 1) % ring_cap;
-    const uint32_t draw_gen = (uint32_t)ctr[1];
     const int lane = threadIdx.x & 31;
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B; b += (gridDim.x * blockDim.x) >> 5) {
-        const U4 d = draw_block(seed, kPurposeTrainSample, 0u, draw_gen, (uint32_t)b, 0u);
+    const int rows = B * batches;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += (gridDim.x * blockDim.x) >> 5) {
+        const int k = r / B, b = r - k * B;
+        const U4 d = draw_block(seed, kPurposeTrainSample, 0u, (uint32_t)(ctr[1] + k), (uint32_t)b, 0u);
         const long long i = (long long)(((unsigned long long)d.x * (unsigned long long)valid) >> 32);
         const long long slot = newest - i >= 0 ? newest - i : newest - i + ring_cap;
         if (!FFS_DCHECK(slot >= 0 && slot < ring_cap, kCheckRingSlot)) continue;   // warp-uniform
-        warp_write_features(ring_rows + slot * ld, n, P, inst_feat, nfeat, X + (int64_t)b * ldx, ldx);
-        if (lane == 0) targets[b] = ((float)ring_ms[slot] - norm[0]) * norm[1];
+        warp_write_features(ring_rows + slot * ld, n, P, inst_feat, nfeat, X + (int64_t)r * ldx, ldx);
+        if (lane == 0) targets[r] = ((float)ring_ms[slot] - norm[0]) * norm[1];
     }
 }
 
@@ -364,17 +384,15 @@ __global__ void k_fill_f32(float *p, int64_t n, float v)
 }
 
 int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
-                          int ld, int K, int16_t *cand, int P, const float *inst_feat, int nfeat, void *X, int ldx,
-                          cudaStream_t st)
+                          int ld, int K, int16_t *cand, void *X, int xw, cudaStream_t st)
 {
     const int total = batch.count * rows * cols * K;
     const int T = 128;
     const int warps = (total + kCandPerWarp - 1) / kCandPerWarp;
     const size_t smem = (size_t)(T / 32) * mark_words(inst->n) * 4;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sur_candidates<<<(warps * 32 + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand, P,
-                                                                inst_feat, nfeat, static_cast<__nv_bfloat16 *>(X),
-                                                                ldx);
+    k_sur_candidates<<<(warps * 32 + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand,
+                                                                static_cast<__nv_bfloat16 *>(X), xw);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -420,12 +438,14 @@ int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long 
 }
 
 int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
-                      const long long *ctr, int ld, uint64_t seed, int B, float *targets, const float *norm, int n,
-                      int P, const float *inst_feat, int nfeat, void *X, int ldx, cudaStream_t st)
+                      const long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
+                      const float *norm, int n, int P, const float *inst_feat, int nfeat, void *X, int ldx,
+                      cudaStream_t st)
 {
-    k_sur_gather<<<(B * 32 + 255) / 256, 256, 0, st>>>(ring_rows, ring_ms, ring_cap, recent, ctr, ld, seed, B, targets,
-                                                       norm, n, P, inst_feat, nfeat, static_cast<__nv_bfloat16 *>(X),
-                                                       ldx);
+    const long long warps = (long long)B * batches;
+    k_sur_gather<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+        ring_rows, ring_ms, ring_cap, recent, ctr, ld, seed, B, batches, targets, norm, n, P, inst_feat, nfeat,
+        static_cast<__nv_bfloat16 *>(X), ldx);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
