@@ -792,14 +792,15 @@ struct SurrogateState {
     // the warm-up, without / with a training round; the pseudo islands run
     // on `side` beside the screen, the training round on `side2` beside the
     // selection (after the forward pass, which reads the weights it updates)
-    cudaGraphExec_t g_gen[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t g_gen[2][2][2] = {};   // [warm][train][migration due]
     cudaStream_t side = nullptr, side2 = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr;
     void drop_graphs()
     {
-        for (auto &row : g_gen)
-            for (auto &g : row)
-                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        for (auto &plane : g_gen)
+            for (auto &row : plane)
+                for (auto &g : row)
+                    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     }
     ~SurrogateState()
     {
@@ -835,7 +836,7 @@ struct ffs_islands {
     long long stats_from = 0;             // generation of the oldest record kept
     int ring_rows = 0, max_N = 0, min_pair_rows = 0;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph_all = nullptr;
+    cudaGraphExec_t graph_all[2] = {nullptr, nullptr};   // [migration launches included]
     std::vector<void *> allocs;
 };
 
@@ -1071,7 +1072,7 @@ static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
 // the latest one, slots that this generation's picks do not overwrite while
 // the ring holds two generations); then, everything joined, the generation
 // advance and migration, as generation_all does.
-static int screened_generation(ffs_islands *S, bool warm, bool train, cudaStream_t st)
+static int screened_generation(ffs_islands *S, bool warm, bool train, bool migrate, cudaStream_t st)
 {
     SurrogateState *R = S->sur;
     std::vector<int> cel, pse;
@@ -1108,7 +1109,7 @@ static int screened_generation(ffs_islands *S, bool warm, bool train, cudaStream
     }
     k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
     FFS_CUDA_TRY(cudaGetLastError());
-    if (S->prm.migration_gap > 0) {
+    if (migrate && S->prm.migration_gap > 0) {
         NvtxRange r("ffs migration (gated by the gap)");
         int rc = migrate_launch(S, S->prm.migration_mode, true, st);
         if (rc) return rc;
@@ -1140,7 +1141,10 @@ static int capture_graph(ffs_islands *S, cudaGraphExec_t *out, F body)
     return FFS_OK;
 }
 
-static int generation_all(ffs_islands *S, cudaStream_t st)
+// One generation of every island; `migrate`: this generation completes a
+// multiple of the migration gap, so the (device-gated) migration launches
+// are part of it.
+static int generation_all(ffs_islands *S, bool migrate, cudaStream_t st)
 {
     std::vector<int> all(S->I);
     for (int i = 0; i < S->I; ++i) all[i] = i;
@@ -1152,13 +1156,25 @@ static int generation_all(ffs_islands *S, cudaStream_t st)
     // flip to the new generation first: migration works on it
     k_advance<<<(S->I + 63) / 64, 64, 0, st>>>(S->d_cur, S->d_gen, 0, S->I);
     FFS_CUDA_TRY(cudaGetLastError());
-    if (S->prm.migration_gap > 0) {
+    if (migrate && S->prm.migration_gap > 0) {
         NvtxRange r("ffs migration (gated by the gap)");
         int rc = migrate_launch(S, S->prm.migration_mode, true, st);
         if (rc) return rc;
     }
     NvtxRange r("ffs metrics / checks");
     return record_launch(S, st);
+}
+
+// Whether the generation about to run (all islands at the same count)
+// completes a multiple of the migration gap: the host's choice of the
+// generation graph with or without the migration launches, which check the
+// same condition on the device.
+static int migration_due_host(const ffs_islands *S)
+{
+    const long long G = S->host_gen[0] + 1;
+    return S->prm.migration_mode != FFS_MIG_NONE && S->I >= 2 && S->prm.migration_gap > 0 &&
+                   G % S->prm.migration_gap == 0
+               ? 1 : 0;
 }
 
 }  // namespace fgpu
@@ -1221,7 +1237,8 @@ static void islands_free(ffs_islands *S)
 {
     if (!S) return;
     delete S->sur;
-    if (S->graph_all) cudaGraphExecDestroy(S->graph_all);
+    for (cudaGraphExec_t g : S->graph_all)
+        if (g) cudaGraphExecDestroy(g);
     if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void *p : S->allocs) cudaFree(p);
     if (S->d_hist) cudaFree(S->d_hist);
@@ -1232,10 +1249,11 @@ static void islands_free(ffs_islands *S)
 // recording is switched, they are captured again.
 static void drop_generation_graphs(ffs_islands *S)
 {
-    if (S->graph_all) {
-        cudaGraphExecDestroy(S->graph_all);
-        S->graph_all = nullptr;
-    }
+    for (cudaGraphExec_t &g : S->graph_all)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     if (S->sur) S->sur->drop_graphs();
 }
 
@@ -1497,10 +1515,11 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     }
     (void)stream;
     S->sur = R;
-    if (S->graph_all) {
-        cudaGraphExecDestroy(S->graph_all);
-        S->graph_all = nullptr;
-    }
+    for (cudaGraphExec_t &g : S->graph_all)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     return FFS_OK;
 }
 
@@ -1615,10 +1634,11 @@ int ffs_islands_autotune(ffs_islands *S, int32_t repeats, ffs_stream stream, int
     S->prm.decode_chunk = bestB;
     S->prm.block_threads = bestT;
     S->prm.decode_variant = bestV;
-    if (S->graph_all) {
-        cudaGraphExecDestroy(S->graph_all);
-        S->graph_all = nullptr;
-    }
+    for (cudaGraphExec_t &g : S->graph_all)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     if (threads_out) *threads_out = bestT;
     if (chunk_out) *chunk_out = bestB;
     if (best_ms) *best_ms = best;
@@ -1694,18 +1714,20 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
                                (G - 1) % R->sp.train_every == 0 &&
                                std::min(R->ring_count, R->ring_cap - R->cells_total) >= R->sp.train_batch)
                                   ? 1 : 0;
+            const int mig = migration_due_host(S);
             NvtxRange gen(train ? "ffs screened generation + training round" : "ffs screened generation");
             if (eager_generations()) {
-                int rc = screened_generation(S, warm != 0, train != 0, st);
+                int rc = screened_generation(S, warm != 0, train != 0, mig != 0, st);
                 if (rc) return rc;
             } else {
-                if (!R->g_gen[warm][train]) {
-                    int rc = capture_graph(S, &R->g_gen[warm][train], [&](cudaStream_t cs) {
-                        return screened_generation(S, warm != 0, train != 0, cs);
+                cudaGraphExec_t &ge = R->g_gen[warm][train][mig];
+                if (!ge) {
+                    int rc = capture_graph(S, &ge, [&](cudaStream_t cs) {
+                        return screened_generation(S, warm != 0, train != 0, mig != 0, cs);
                     });
                     if (rc) return rc;
                 }
-                FFS_CUDA_TRY(cudaGraphLaunch(R->g_gen[warm][train], st));
+                FFS_CUDA_TRY(cudaGraphLaunch(ge, st));
             }
             for (int i = 0; i < S->I; ++i) {
                 S->host_cur[i] ^= 1;
@@ -1719,7 +1741,7 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
     if (eager_generations()) {
         for (int g = 0; g < n_generations; ++g) {
             NvtxRange gen("ffs generation");
-            int rc = generation_all(S, st);
+            int rc = generation_all(S, migration_due_host(S) != 0, st);
             if (rc) return rc;
             for (int i = 0; i < S->I; ++i) {
                 S->host_cur[i] ^= 1;
@@ -1728,28 +1750,17 @@ int ffs_island_step(ffs_islands *S, int32_t island, int32_t n_generations, ffs_s
         }
         return FFS_OK;
     }
-    if (!S->graph_all) {
-        NvtxRange cap("ffs capture of the generation graph");
-        if (!S->cap_stream) FFS_CUDA_TRY(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        FFS_CUDA_TRY(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeRelaxed));
-        int rc = generation_all(S, S->cap_stream);
-        cudaError_t e = cudaStreamEndCapture(S->cap_stream, &graph);
-        if (rc) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e != cudaSuccess) return set_error(FFS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&S->graph_all, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            S->graph_all = nullptr;
-            return set_error(FFS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        }
-    }
+    // two graphs: the generation with and without the migration launches
     for (int g = 0; g < n_generations; ++g) {
+        const int mig = migration_due_host(S);
+        cudaGraphExec_t &ge = S->graph_all[mig];
+        if (!ge) {
+            NvtxRange cap("ffs capture of the generation graph");
+            int rc = capture_graph(S, &ge, [&](cudaStream_t cs) { return generation_all(S, mig != 0, cs); });
+            if (rc) return rc;
+        }
         NvtxRange gen("ffs generation (graph)");
-        FFS_CUDA_TRY(cudaGraphLaunch(S->graph_all, st));
+        FFS_CUDA_TRY(cudaGraphLaunch(ge, st));
         for (int i = 0; i < S->I; ++i) {
             S->host_cur[i] ^= 1;
             S->host_gen[i] += 1;
@@ -2160,10 +2171,11 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
     S->prm.decode_chunk = keep.decode_chunk;
     S->prm.block_threads = keep.block_threads;
     S->prm.decode_variant = keep.decode_variant;
-    if (S->graph_all) {
-        cudaGraphExecDestroy(S->graph_all);
-        S->graph_all = nullptr;
-    }
+    for (cudaGraphExec_t &g : S->graph_all)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     return FFS_OK;
 }
 
