@@ -794,7 +794,7 @@ struct SurrogateState {
     // selection (after the forward pass, which reads the weights it updates)
     cudaGraphExec_t g_gen[2][2][2] = {};   // [warm][train][migration due]
     cudaStream_t side = nullptr, side2 = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr, fold_ev = nullptr;
     void drop_graphs()
     {
         for (auto &plane : g_gen)
@@ -807,7 +807,7 @@ struct SurrogateState {
         drop_graphs();
         if (side) cudaStreamDestroy(side);
         if (side2) cudaStreamDestroy(side2);
-        for (cudaEvent_t e : {fork_ev, join_ev, fork2_ev, join2_ev})
+        for (cudaEvent_t e : {fork_ev, join_ev, fork2_ev, join2_ev, fold_ev})
             if (e) cudaEventDestroy(e);
     }
 };
@@ -858,7 +858,7 @@ static IslandRef device_ref(const ffs_islands *S, int i)
 
 template <typename F>
 static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, bool use_copy,
-                                    cudaStream_t st, F between);
+                                    bool fold_ready, cudaStream_t st, F between);
 
 // CTAs of the scoring forward's persistent GEMM while a training round runs
 // beside it: the SMs left over take the round's kernels.
@@ -902,7 +902,7 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
             int rc = launch_sur_tick(S->sur->d_ctr, 2, -1, st);
             if (rc) return rc;
             rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, false,
-                                          st, [](cudaStream_t) { return (int)FFS_OK; });
+                                          false, st, [](cudaStream_t) { return (int)FFS_OK; });
             if (rc) return rc;
             continue;
         }
@@ -989,7 +989,7 @@ static int record_launch(ffs_islands *S, cudaStream_t st)
 // cells of each batch).
 template <typename F>
 static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, bool use_copy,
-                                    cudaStream_t st, F between)
+                                    bool fold_ready, cudaStream_t st, F between)
 {
     SurrogateState *R = S->sur;
     const GaScalars g = scalars_of(&S->prm);
@@ -1015,6 +1015,10 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
     }
     int rc = between(st);
     if (rc) return rc;
+    // layer 1's folded bias (unless `between` made it ready on another stream)
+    if (warm && !fold_ready &&
+        (rc = mlp_fold_bias(R->mlp, use_copy, R->P, R->inst_feat, R->nfeat, st)))
+        return rc;
     offset = 0;
     for (const IslandBatch &batch : batches) {
         const int ncells = batch.count * cells;
@@ -1087,17 +1091,25 @@ static int screened_generation(ffs_islands *S, bool warm, bool train, bool migra
         FFS_CUDA_TRY(cudaStreamWaitEvent(R->side, R->fork_ev, 0));
         if ((rc = islands_generation_launch(S, pse, R->side))) return rc;
     }
+    // with overlap, the training stream first folds the copy's layer-1 bias
+    // (beside the candidate building), then runs the round
+    const bool fold_side = overlap && warm;
     if (train) {
         NvtxRange r("ffs surrogate training round (side stream)");
         FFS_CUDA_TRY(cudaEventRecord(R->fork2_ev, st));
         FFS_CUDA_TRY(cudaStreamWaitEvent(R->side2, R->fork2_ev, 0));
+        if (fold_side) {
+            if ((rc = mlp_fold_bias(R->mlp, true, R->P, R->inst_feat, R->nfeat, R->side2))) return rc;
+            FFS_CUDA_TRY(cudaEventRecord(R->fold_ev, R->side2));
+        }
         if ((rc = surrogate_train_launch(S, R->side2))) return rc;
         FFS_CUDA_TRY(cudaEventRecord(R->join2_ev, R->side2));
     }
     {
         NvtxRange r("ffs screened cellular islands: candidates, scores, select");
-        rc = screened_cellular_launch(S, cel, warm, overlap, st, [&](cudaStream_t cs) -> int {
+        rc = screened_cellular_launch(S, cel, warm, overlap, fold_side, st, [&](cudaStream_t cs) -> int {
             if (train && !overlap) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
+            if (fold_side) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->fold_ev, 0));
             return FFS_OK;
         });
         if (rc) return rc;
@@ -1508,7 +1520,8 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
         cudaEventCreateWithFlags(&R->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->join_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->fork2_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&R->join2_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&R->join2_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->fold_ev, cudaEventDisableTiming) != cudaSuccess) {
         (void)cudaGetLastError();
         delete R;
         return set_error(FFS_ECUDA, "surrogate state initialisation");

@@ -308,9 +308,11 @@ int mlp_enable_copy(ffs_mlp *m);
 int mlp_take_copy(ffs_mlp *m, cudaStream_t st);
 // Forward of rows whose network input is xpos[j] for j < kpos, zero for
 // kpos <= j < P, the vector feat at [P, P + nfeat) and zero beyond: the
-// constant block is folded into layer 1's bias, layer 1 contracts over the
-// kpos leading columns (xpos rows of ldxpos BF16 values).  The weights read
-// are the scoring copy's (use_copy) or the network's own.
+// constant block is folded into layer 1's bias (mlp_fold_bias, launched
+// before it in stream order with the same weights), layer 1 contracts over
+// the kpos leading columns (xpos rows of ldxpos BF16 values).  The weights
+// read are the scoring copy's (use_copy) or the network's own.
+int mlp_fold_bias(ffs_mlp *m, bool use_copy, int P, const float *feat, int nfeat, cudaStream_t st);
 int mlp_forward_folded(ffs_mlp *m, bool use_copy, const void *xpos, int ldxpos, int kpos, int P, const float *feat,
                        int nfeat, int B, float *y, int max_ctas, cudaStream_t st);
 

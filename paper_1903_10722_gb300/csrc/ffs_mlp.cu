@@ -910,6 +910,16 @@ int mlp_take_copy(ffs_mlp *M, cudaStream_t st)
     return FFS_OK;
 }
 
+int mlp_fold_bias(ffs_mlp *M, bool use_copy, int P, const float *feat, int nfeat, cudaStream_t st)
+{
+    if (use_copy && !M->cparams) return set_error(FFS_EINVAL, "the network has no scoring copy");
+    if (P < 1 || nfeat < 0 || P + nfeat > M->in_dim) return set_error(FFS_EINVAL, "fold: P %d, nfeat %d", P, nfeat);
+    const MlpFwd w = use_copy ? fwd_copy(M) : fwd_live(M);
+    k_fold_bias<<<(M->h1 * 32 + 255) / 256, 256, 0, st>>>(w.W1b, M->K1, w.b1, P, feat, nfeat, M->h1, M->fold);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
 int mlp_forward_folded(ffs_mlp *M, bool use_copy, const void *xpos, int ldxpos, int kpos, int P, const float *feat,
                        int nfeat, int B, float *y, int max_ctas, cudaStream_t st)
 {
@@ -918,8 +928,6 @@ int mlp_forward_folded(ffs_mlp *M, bool use_copy, const void *xpos, int ldxpos, 
     if (kpos < 1 || kpos > P || P + nfeat > M->in_dim || ldxpos < kpos || ldxpos % 8)
         return set_error(FFS_EINVAL, "folded input: kpos %d, P %d, nfeat %d, ld %d", kpos, P, nfeat, ldxpos);
     const MlpFwd w = use_copy ? fwd_copy(M) : fwd_live(M);
-    k_fold_bias<<<(M->h1 * 32 + 255) / 256, 256, 0, st>>>(w.W1b, M->K1, w.b1, P, feat, nfeat, M->h1, M->fold);
-    FFS_CUDA_TRY(cudaGetLastError());
     MlpFwd wf = w;
     wf.b1 = M->fold;
     // layer 1 over the kpos leading columns only (TMA reads the rest of the

@@ -249,25 +249,43 @@ __global__ void __launch_bounds__(128) k_sur_select_lanes(int n, int S, uint32_t
         const int gq = gq0 + (mine ? lane : 0);
         int pick = 0;
         if (mine) {
+            // the cell's K (<= 16) scores loaded together, then the lowest
+            // (the lowest k on ties)
             const float *sc = scores + (int64_t)gq * K;
-            for (int k = 1; k < K; ++k)
-                if (sc[k] < sc[pick]) pick = k;
+            float v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = k < K ? sc[k] : 0.0f;
+            float best = v[0];
+#pragma unroll
+            for (int k = 1; k < 16; ++k)
+                if (k < K && v[k] < best) {
+                    best = v[k];
+                    pick = k;
+                }
             if (!FFS_DCHECK(pick >= 0 && pick < K, kCheckPick)) pick = 0;
         }
         const int16_t *drow = cand + ((int64_t)gq * K + pick) * ld;
-        // the picked rows, one after the other, into the warp's buffer
-        int4 *dst = reinterpret_cast<int4 *>(u.rows);
-        for (int j = 0; j < nrows; ++j) {
-            const int4 *src = reinterpret_cast<const int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)drow, j));
-            for (int k = lane; k < (ld >> 3); k += 32) dst[j * (ld >> 3) + k] = src[k];
+        // the picked rows into the warp's buffer, every 16-byte block of them
+        // in flight at once (block w of the nrows x q: row w / q)
+        const int q = ld >> 3, tot = nrows * q;
+        int4 *buf = reinterpret_cast<int4 *>(u.rows);
+        for (int w0 = 0; w0 < tot; w0 += 128) {
+            int4 v4[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int w = w0 + 32 * h + lane;
+                const int j = w < tot ? w / q : 0;
+                const int4 *src = reinterpret_cast<const int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)drow, j));
+                if (w < tot) v4[h] = src[w - j * q];
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int w = w0 + 32 * h + lane;
+                if (w < tot) buf[w] = v4[h];
+            }
         }
         __syncwarp();
-        const bool active = u.g < nrows;
-        const uint32_t sM = (active ? (uint32_t)u.s : 0xFFu) | (u.Ms << 8) | (SH << 16);
-        const uint32_t genes = u.rows_sa + (active ? (uint32_t)(u.g * ld * 2) : 0u);
-        const int32_t v = lane_decode_dispatch(MM, u.tab, u.row_bytes, genes, u.nS, sM, u.win, u.rel, u.due, wt);
-        // lane l takes its cell's objective from its group's last lane
-        const int32_t ms = __shfl_sync(0xFFFFFFFFu, v, (mine ? lane : 0) * S + S - 1);
+        // the cell's current makespan, read before the decode
         const int bi = gq / cells, c = gq - bi * cells;
         const int16_t *pin;
         const int32_t *msin;
@@ -275,19 +293,50 @@ __global__ void __launch_bounds__(128) k_sur_select_lanes(int n, int S, uint32_t
         int32_t *msout;
         uint32_t gen;
         resolve(batch.ref[bi], pin, msin, pout, msout, gen);
-        bool better = false, keep = false;
+        const int32_t old = mine ? msin[c] : 0;
+        const bool active = u.g < nrows;
+        const uint32_t sM = (active ? (uint32_t)u.s : 0xFFu) | (u.Ms << 8) | (SH << 16);
+        const uint32_t genes = u.rows_sa + (active ? (uint32_t)(u.g * ld * 2) : 0u);
+        const int32_t v = lane_decode_dispatch(MM, u.tab, u.row_bytes, genes, u.nS, sM, u.win, u.rel, u.due, wt);
+        // lane l takes its cell's objective from its group's last lane
+        const int32_t ms = __shfl_sync(0xFFFFFFFFu, v, (mine ? lane : 0) * S + S - 1);
+        const long long slot = (ring_base + gq) % ring_cap;
+        bool better = false;
         if (mine) {
-            const int32_t old = msin[c];
             better = ms >= 0 && (g.replace_le ? (uint32_t)ms <= (uint32_t)old : (uint32_t)ms < (uint32_t)old);
-            keep = !better;
             msout[c] = better ? ms : old;
             chosen[gq] = pick;
-            const long long slot = (ring_base + gq) % ring_cap;
             ring_ms[slot] = ms;
         }
-        warp_copy_rows(better, drow, pout + (int64_t)c * ld, ld);
-        warp_copy_rows(keep, pin + (int64_t)c * ld, pout + (int64_t)c * ld, ld);
-        warp_copy_rows(mine, drow, ring_rows + ((ring_base + gq) % ring_cap) * ld, ld);
+        // rows out: the cell's output row takes the pick (from the buffer) or
+        // its old row, the ring slot the pick; all blocks in flight at once
+        const int16_t *staged = reinterpret_cast<const int16_t *>(u.rows) + (int64_t)(mine ? lane : 0) * ld;
+        const int16_t *out_src = better ? staged : pin + (int64_t)c * ld;
+        int16_t *out_dst = pout + (int64_t)c * ld;
+        int16_t *ring_dst = ring_rows + slot * ld;
+        for (int w0 = 0; w0 < tot; w0 += 64) {
+            int4 a4[2], b4[2];
+            int4 *da[2], *db[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int w = w0 + 32 * h + lane;
+                const int j = w < tot ? w / q : 0, k = w - j * q;
+                const int4 *sa = reinterpret_cast<const int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)out_src, j));
+                const int4 *sb = reinterpret_cast<const int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)staged, j));
+                da[h] = reinterpret_cast<int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)out_dst, j)) + k;
+                db[h] = reinterpret_cast<int4 *>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)ring_dst, j)) + k;
+                if (w < tot) {
+                    a4[h] = sa[k];
+                    b4[h] = sb[k];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (w0 + 32 * h + lane < tot) {
+                    *da[h] = a4[h];
+                    *db[h] = b4[h];
+                }
+        }
         __syncwarp();   // the buffer is refilled next
     }
 }
