@@ -785,11 +785,13 @@ struct SurrogateState {
     std::vector<int> cell_islands;
     // device counters read by the kernels: [0] ring pairs appended, [1]
     // training batches drawn (host mirrors: ring_count, train_rounds), [2]
-    // the ring count when the current generation began
+    // the ring count when the current generation began, [3] blocks of the
+    // running gather that have finished (0 between launches)
     long long *d_ctr = nullptr;
     float *d_norm = nullptr;       // training-target standardisation (mean, 1 / std)
-    // generations replayed from CUDA graphs, [warm][train]: before / after
-    // the warm-up, without / with a training round; the pseudo islands run
+    // generations replayed from CUDA graphs, [warm][train][migration]: before /
+    // after the warm-up, without / with a training round, without / with the
+    // migration launches; the pseudo islands run
     // on `side` beside the screen, the training round on `side2` beside the
     // selection (after the forward pass, which reads the weights it updates)
     cudaGraphExec_t g_gen[2][2][2] = {};   // [warm][train][migration due]
@@ -1047,15 +1049,12 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
 static int surrogate_train_launch(ffs_islands *S, cudaStream_t st)
 {
     SurrogateState *R = S->sur;
-    int rc0 = launch_sur_norm(R->ring_ms, R->ring_cap, R->d_ctr, R->cells_total, R->d_norm, st);
-    if (rc0) return rc0;
     // every step's batch in one launch (batch k drawn as the (ctr[1] + k)-th)
     const int B = R->sp.train_batch, steps = R->sp.train_steps;
     int rc = launch_sur_gather(R->ring_rows, R->ring_ms, R->ring_cap, R->cells_total, R->d_ctr, S->ld, S->prm.seed, B,
                                steps, R->train_t, R->d_norm, S->inst->n, R->P, R->inst_feat, R->nfeat, R->train_X,
                                R->ldx, st);
-    if (rc) return rc;
-    if ((rc = launch_sur_tick(R->d_ctr, 1, steps, st))) return rc;
+    if (rc) return rc;   // the gather also advanced the batch count ctr[1]
     for (int s = 0; s < steps; ++s) {
         const void *X = static_cast<const char *>(R->train_X) + (int64_t)s * B * R->ldx * 2;
         if ((rc = ffs_mlp_train_step(R->mlp, static_cast<const uint16_t *>(X), R->ldx, R->train_t + (int64_t)s * B, B,
@@ -1482,7 +1481,7 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     R->train_X = alloc(train_rows * R->ldx * 2);
     R->train_t = (float *)alloc(train_rows * 4);
     R->loss = (float *)alloc(4);
-    R->d_ctr = (long long *)alloc(3 * sizeof(long long));
+    R->d_ctr = (long long *)alloc(4 * sizeof(long long));
     R->d_norm = (float *)alloc(2 * sizeof(float));
     if (!R->cand || !R->X || !R->scores || !R->chosen || !R->ring_rows || !R->ring_ms || !R->inst_feat ||
         !R->train_X || !R->train_t || !R->loss || !R->d_ctr || !R->d_norm) {
@@ -1514,7 +1513,7 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     f[37] = (float)(I->S / 20.0);
     f[38] = (float)(lb / total);
     if (cudaMemcpy(R->inst_feat, f.data(), nfeat * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(R->d_ctr, 0, 3 * sizeof(long long)) != cudaSuccess ||
+        cudaMemset(R->d_ctr, 0, 4 * sizeof(long long)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&R->side, cudaStreamNonBlocking) != cudaSuccess ||
         side2_create(&R->side2, sp->overlap != 0) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->fork_ev, cudaEventDisableTiming) != cudaSuccess ||

@@ -288,11 +288,9 @@ int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const Island
                       int ld, int K, const int16_t *cand, const float *scores, int32_t *chosen, int16_t *ring_rows,
                       int32_t *ring_ms, long long ring_cap, const long long *ctr, int B_req, int T_req,
                       unsigned long long *decoded, cudaStream_t st);
-int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm,
-                    cudaStream_t st);
 int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
-                      const long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
-                      const float *norm, int n, int P, const float *inst_feat, int nfeat, void *X, int ldx,
+                      long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
+                      float *norm, int n, int P, const float *inst_feat, int nfeat, void *X, int ldx,
                       cudaStream_t st);
 int launch_sur_tick(long long *ctr, int which, long long add, cudaStream_t st);
 int launch_fill_f32(float *p, int64_t n, float v, cudaStream_t st);

@@ -28,6 +28,11 @@ struct GemmEpi {
     const float *bias;        // modes 1, 2: [N]
     const float *w3, *b3;     // mode 2 (persistent form, one column tile): y[row] =
     float *y;                 //   sum_c BF16(relu(acc + bias))[c] w3[c] + b3, H never stored
+    // mode 3 (a hidden layer's backpropagated signal): z = acc [mask > 0],
+    // FP32 into D [M][ldd] and BF16 transposed into Dt [N][ldt]
+    const __nv_bfloat16 *mask;
+    int ldm, ldt;
+    __nv_bfloat16 *Dt;
     int ldd;
     int M_valid;
     int mode;
@@ -53,6 +58,29 @@ __device__ __forceinline__ void gemm_store_32(const GemmEpi &epi, int row, int c
         float4 *dst = reinterpret_cast<float4 *>(epi.D + (size_t)row * epi.ldd + col);
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (epi.mode == 3) {
+        const uint4 *hm = reinterpret_cast<const uint4 *>(epi.mask + (size_t)row * epi.ldm + col);
+        uint32_t hw[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 x = hm[q];
+            hw[4 * q] = x.x;
+            hw[4 * q + 1] = x.y;
+            hw[4 * q + 2] = x.z;
+            hw[4 * q + 3] = x.w;
+        }
+        float z[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float h = __uint_as_float((j & 1) ? (hw[j >> 1] & 0xFFFF0000u) : (hw[j >> 1] << 16));
+            z[j] = h > 0.0f ? v[j] : 0.0f;
+        }
+        float4 *dst = reinterpret_cast<float4 *>(epi.D + (size_t)row * epi.ldd + col);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+        // column j of the warp's 32 rows: 32 consecutive BF16 of Dt's row col + j
+#pragma unroll
+        for (int j = 0; j < 32; ++j) epi.Dt[(size_t)(col + j) * epi.ldt + row] = __float2bfloat16_rn(z[j]);
     } else {
         uint32_t packed[16];
 #pragma unroll
@@ -571,18 +599,6 @@ __global__ void k_out_loss_dz2(const __nv_bfloat16 *H2, int B, int h2, const flo
     }
 }
 
-// dZ1T[j][b] = dH1[b][j] [H1[b][j] > 0] as BF16.
-__global__ void k_dz1T(const float *dH1, const __nv_bfloat16 *H1, int B, int h1, __nv_bfloat16 *dZ1T, float *dZ1)
-{
-    const size_t total = (size_t)B * h1;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / h1), j = (int)(i % h1);
-        const float g = __bfloat162float(H1[i]) > 0.0f ? dH1[i] : 0.0f;
-        dZ1[i] = g;
-        dZ1T[(size_t)j * B + b] = __float2bfloat16_rn(g);
-    }
-}
-
 // out[j] = sum_b X[b][j] (* w[b] if w): column sums of a [B][C] matrix.
 // Block (32, 32): threadIdx.x picks the column of a 32-column tile,
 // threadIdx.y the rows b = y, y + 32, ...; the 32 partial sums of a column
@@ -689,6 +705,17 @@ __global__ void k_mlp_init(float *W, int rows, int cols, int ld, uint64_t seed, 
 // It also writes the BF16 copies the GEMMs read: W1b[i] for the W1 block
 // [0, nW1) and, for the W2 block [w2_off, w2_off + h2 h1), W2b[o][c] and its
 // transpose W2Tb[c][o].
+__device__ __forceinline__ float adam_one(float &p, float gi, float &m, float &v, float lr, float b1, float b2,
+                                          float eps, float c1, float c2)
+{
+    const float mi = b1 * m + (1.0f - b1) * gi;
+    const float vi = b2 * v + (1.0f - b2) * gi * gi;
+    m = mi;
+    v = vi;
+    p = p - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    return p;
+}
+
 __global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
                             float eps, long long *t_prev, unsigned int *blocks_done, int nW1, int w2_off, int h1,
                             int h2, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb)
@@ -696,22 +723,44 @@ __global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n,
     const float t = (float)(*t_prev + 1);
     const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
     const int nW2 = h1 * h2;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.0f - b1) * gi;
-        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = pi;
+    // four parameters per step (the blocks W1, b1, W2, ... start at multiples
+    // of four), then the tail one by one
+    const int nq = n >> 2;
+    for (int iq = blockIdx.x * blockDim.x + threadIdx.x; iq < nq; iq += gridDim.x * blockDim.x) {
+        const int i = 4 * iq;
+        float4 P = reinterpret_cast<float4 *>(p)[iq];
+        const float4 G = reinterpret_cast<const float4 *>(g)[iq];
+        float4 Mv = reinterpret_cast<float4 *>(m)[iq];
+        float4 V = reinterpret_cast<float4 *>(v)[iq];
+        adam_one(P.x, G.x, Mv.x, V.x, lr, b1, b2, eps, c1, c2);
+        adam_one(P.y, G.y, Mv.y, V.y, lr, b1, b2, eps, c1, c2);
+        adam_one(P.z, G.z, Mv.z, V.z, lr, b1, b2, eps, c1, c2);
+        adam_one(P.w, G.w, Mv.w, V.w, lr, b1, b2, eps, c1, c2);
+        reinterpret_cast<float4 *>(p)[iq] = P;
+        reinterpret_cast<float4 *>(m)[iq] = Mv;
+        reinterpret_cast<float4 *>(v)[iq] = V;
         if (i < nW1) {
-            W1b[i] = __float2bfloat16_rn(pi);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<const uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(W1b + i) = pk;
         } else if (i >= w2_off && i < w2_off + nW2) {
-            const int r = i - w2_off, o = r / h1, c = r - o * h1;
-            const __nv_bfloat16 pb = __float2bfloat16_rn(pi);
-            W2b[r] = pb;
-            W2Tb[(size_t)c * h2 + o] = pb;
+            const int r = i - w2_off, o = r / h1, c = r - o * h1;   // c .. c + 3 in row o
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<const uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(W2b + r) = pk;
+            W2Tb[(size_t)c * h2 + o] = lo.x;
+            W2Tb[(size_t)(c + 1) * h2 + o] = lo.y;
+            W2Tb[(size_t)(c + 2) * h2 + o] = hi.x;
+            W2Tb[(size_t)(c + 3) * h2 + o] = hi.y;
         }
+    }
+    for (int i = 4 * nq + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        // the tail lies past W1 and W2 (b2, w3, b3)
+        adam_one(p[i], g[i], m[i], v[i], lr, b1, b2, eps, c1, c2);
     }
     __syncthreads();   // this block's threads have read the count
     if (threadIdx.x == 0) {
@@ -741,7 +790,7 @@ struct ffs_mlp {
     // activations / scratch for max_batch rows
     __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *H1T = nullptr, *XT = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
                   *dZ1T = nullptr;
-    float *y = nullptr, *dy = nullptr, *dH1 = nullptr, *dZ1 = nullptr;
+    float *y = nullptr, *dy = nullptr, *dZ1 = nullptr;
     int *err = nullptr;
     // the scoring copy (allocated on demand): what a forward pass reads (BF16
     // W1 and W2, FP32 b1, b2, w3, b3 at the parameters' offsets) and its own
@@ -1072,7 +1121,6 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->dZ1T = (__nv_bfloat16 *)alloc(Bm * h1 * 2);
     M->y = (float *)alloc(Bm * 4);
     M->dy = (float *)alloc(Bm * 4);
-    M->dH1 = (float *)alloc(Bm * h1 * 4);
     M->dZ1 = (float *)alloc(Bm * h1 * 4);
     M->err = (int *)alloc(4);
     M->d_adam_t = (long long *)alloc(8);
@@ -1246,7 +1294,7 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
                 e_s1 = M->ev[5], e_s2 = M->ev[6];
     const int h1 = M->h1, h2 = M->h2, K1 = M->K1;
     // The step's dependency graph on three streams; the caller's stream `st`
-    // carries the critical path (forward, loss, dH1, dZ1, gW1, Adam), s1 and
+    // carries the critical path (forward, loss, dZ1, gW1, Adam), s1 and
     // s2 the work beside it, joined back into `st` before Adam.
     FFS_CUDA_TRY(cudaEventRecord(e_fork, st));
     FFS_CUDA_TRY(cudaStreamWaitEvent(s1, e_fork, 0));
@@ -1287,11 +1335,17 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     e.ldd = h1;
     if ((rc = gemm_bf16(M->dZ2T, B, M->H1T, B, h2, h1, B, e, s2))) return rc;
     FFS_CUDA_TRY(cudaEventRecord(e_s2, s2));
-    // st: dH1 = dZ2 W2 (A = dZ2 [B][h2], B = W2T [h1][h2]), then dZ1
-    e.D = M->dH1;
+    // st: dZ1 = (dZ2 W2) [H1 > 0] (A = dZ2 [B][h2], B = W2T [h1][h2]), FP32 and
+    // BF16 transposed, in the GEMM's epilogue
+    e.mode = 3;
+    e.D = M->dZ1;
     e.ldd = h1;
+    e.mask = M->H1;
+    e.ldm = h1;
+    e.Dt = M->dZ1T;
+    e.ldt = B;
     if ((rc = gemm_bf16(M->dZ2, h2, M->W2Tb, h2, B, h1, h2, e, st))) return rc;
-    k_dz1T<<<512, 256, 0, st>>>(M->dH1, M->H1, B, h1, M->dZ1T, M->dZ1);
+    e.mode = 0;
     FFS_CUDA_TRY(cudaEventRecord(e_dz1, st));
     // s1: gb1 = column sums of dZ1, beside gW1
     FFS_CUDA_TRY(cudaStreamWaitEvent(s1, e_dz1, 0));
@@ -1306,7 +1360,8 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_s1, 0));
     FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_s2, 0));
     const int nW1 = h1 * K1, w2_off = nW1 + h1;
-    k_adam_bf16<<<1024, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
+    const int adam_blocks = std::min(1024, (int)((M->n_params / 4 + 255) / 256));
+    k_adam_bf16<<<adam_blocks, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
                                       M->d_adam_t, M->d_adam_done, nW1, w2_off, h1, h2, M->W1b, M->W2b, M->W2Tb);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;

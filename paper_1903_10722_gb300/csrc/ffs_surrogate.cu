@@ -349,22 +349,34 @@ __global__ void __launch_bounds__(128) k_sur_select_lanes(int n, int S, uint32_t
 
 // Standardisation of the training targets: mean and 1 / std (std at least 1)
 // of the makespans of the `recent` newest ring pairs before the current
-// generation (the last generation's exact decodes), into norm[0..1].  The screen needs only the ranking of a
-// cell's candidates, whose makespans differ by a few tenths of a percent
-// late in a run: standardised targets keep those differences at the scale
-// the network learns.  One block.
-__global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm)
+// generation (the last generation's exact decodes).  The screen needs only
+// the ranking of a cell's candidates, whose makespans differ by a few tenths
+// of a percent late in a run: standardised targets keep those differences at
+// the scale the network learns.  Computed by every block of the gather that
+// uses it (the ring's makespans are L2-resident): the sums of the makespans
+// and of their squares in exact integers, then mean = S / m and var = Q / m -
+// mean^2 in double.  The whole block calls it; the result is in norm[0..1].
+__device__ void block_target_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent,
+                                  float *norm)
 {
-    __shared__ double part[2][32];
+    __shared__ long long part[2][32];
     const long long cnt = ctr[2] < ring_cap ? ctr[2] : ring_cap;
     const int m = (int)(cnt < recent ? cnt : recent);
-    double s = 0.0, q = 0.0;
+    long long s = 0, q = 0;
     const long long last = (ctr[2] - 1) % ring_cap;   // slot of the newest pair (m > 0 only)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const long long slot = last - i;
-        const double v = (double)ring_ms[slot >= 0 ? slot : slot + ring_cap];
-        s += v;
-        q += v * v;
+    for (int i0 = threadIdx.x; i0 < m; i0 += 8 * blockDim.x) {
+        long long v[8];   // eight loads in flight
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            const long long slot = last - i;
+            v[u] = i < m ? ring_ms[slot >= 0 ? slot : slot + ring_cap] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            s += v[u];
+            q += v[u] * v[u];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
@@ -376,17 +388,18 @@ __global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const lon
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double S = 0.0, Q = 0.0;
+        long long S = 0, Q = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             S += part[0][w];
             Q += part[1][w];
         }
-        const double mean = m > 0 ? S / m : 0.0;
-        double var = m > 0 ? Q / m - mean * mean : 1.0;
+        const double mean = m > 0 ? (double)S / m : 0.0;
+        double var = m > 0 ? (double)Q / m - mean * mean : 1.0;
         if (var < 1.0) var = 1.0;
         norm[0] = (float)mean;
         norm[1] = (float)(1.0 / sqrt(var));
     }
+    __syncthreads();
 }
 
 // Training batches k = 0 .. batches - 1 of B pairs each, drawn uniformly
@@ -395,25 +408,41 @@ __global__ void k_sur_norm(const int32_t *ring_ms, long long ring_cap, const lon
 // pairs before the current generation (pair i = the i-th newest, slot
 // (ctr[2] - 1 - i) mod ring_cap; the current generation writes the `recent`
 // slots after them), written as network inputs X (row k B + b, one warp per
-// sample); target = (makespan - norm[0]) * norm[1].
+// sample); target = (makespan - norm[0]) * norm[1] (block_target_norm; block
+// 0 also leaves it in norm_out).  The last block to finish (counted in
+// ctr[3], reset by it) advances the batch count ctr[1] by `batches`, after
+// every block has read it.
 __global__ void k_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
-                             const long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
-                             const float *norm, int n, int P, const float *inst_feat, int nfeat, __nv_bfloat16 *X,
+                             long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
+                             float *norm_out, int n, int P, const float *inst_feat, int nfeat, __nv_bfloat16 *X,
                              int ldx)
 {
+    __shared__ float norm[2];
+    block_target_norm(ring_ms, ring_cap, ctr, recent, norm);
+    if (blockIdx.x == 0 && threadIdx.x < 2) norm_out[threadIdx.x] = norm[threadIdx.x];
     const long long room = ring_cap - recent;
     const long long valid = ctr[2] < room ? ctr[2] : room;
     const long long newest = (ctr[2] - 1) % ring_cap;
+    const long long drawn = ctr[1];   // batches drawn before this launch
     const int lane = threadIdx.x & 31;
     const int rows = B * batches;
     for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += (gridDim.x * blockDim.x) >> 5) {
         const int k = r / B, b = r - k * B;
-        const U4 d = draw_block(seed, kPurposeTrainSample, 0u, (uint32_t)(ctr[1] + k), (uint32_t)b, 0u);
+        const U4 d = draw_block(seed, kPurposeTrainSample, 0u, (uint32_t)(drawn + k), (uint32_t)b, 0u);
         const long long i = (long long)(((unsigned long long)d.x * (unsigned long long)valid) >> 32);
         const long long slot = newest - i >= 0 ? newest - i : newest - i + ring_cap;
         if (!FFS_DCHECK(slot >= 0 && slot < ring_cap, kCheckRingSlot)) continue;   // warp-uniform
         warp_write_features(ring_rows + slot * ld, n, P, inst_feat, nfeat, X + (int64_t)r * ldx, ldx);
         if (lane == 0) targets[r] = ((float)ring_ms[slot] - norm[0]) * norm[1];
+    }
+    __syncthreads();   // this block's warps have read ctr[1]
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned long long *done = reinterpret_cast<unsigned long long *>(ctr + 3);
+        if (atomicAdd(done, 1ull) == (unsigned long long)gridDim.x - 1ull) {
+            ctr[1] += batches;
+            *done = 0ull;
+        }
     }
 }
 
@@ -478,17 +507,9 @@ int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const Island
     return FFS_OK;
 }
 
-int launch_sur_norm(const int32_t *ring_ms, long long ring_cap, const long long *ctr, int recent, float *norm,
-                    cudaStream_t st)
-{
-    k_sur_norm<<<1, 1024, 0, st>>>(ring_ms, ring_cap, ctr, recent, norm);
-    FFS_CUDA_TRY(cudaGetLastError());
-    return FFS_OK;
-}
-
 int launch_sur_gather(const int16_t *ring_rows, const int32_t *ring_ms, long long ring_cap, int recent,
-                      const long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
-                      const float *norm, int n, int P, const float *inst_feat, int nfeat, void *X, int ldx,
+                      long long *ctr, int ld, uint64_t seed, int B, int batches, float *targets,
+                      float *norm, int n, int P, const float *inst_feat, int nfeat, void *X, int ldx,
                       cudaStream_t st)
 {
     const long long warps = (long long)B * batches;
