@@ -38,6 +38,7 @@ struct GemmEpi {
     int mode;
     int *err;                 // set to a non-zero code if a wait timed out
     int max_ctas;             // host: CTAs of the persistent form at most (0: one per SM)
+    int pdl;                  // host: launch as a programmatic dependent of the stream's previous kernel
 };
 
 template <int BN>
@@ -126,6 +127,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const __grid_constant__ CU
         s_fail = 0;
     }
     if (warp == 0) tc::tmem_alloc(tslot, SM::TCOLS);
+    // what follows reads what the kernels before this one wrote
+    tc::grid_dep_launch();
+    tc::grid_dep_wait();
     // the epilogue's bias slice, read once per CTA
     if (epi.mode == 1)
         for (int c = threadIdx.x; c < BN; c += blockDim.x) s_bias[c] = epi.bias[n0 + c];
@@ -427,6 +431,24 @@ static int make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld,
     return FFS_OK;
 }
 
+// Launch `k` as a programmatic dependent of the stream's previous kernel
+// (the kernel calls grid_dep_wait before it reads that kernel's results).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int BN>
 static int launch_gemm_bn(const CUtensorMap &ta, const CUtensorMap &tb, int Mtiles, int N, int K, const GemmEpi &epi,
                           cudaStream_t st)
@@ -434,6 +456,10 @@ static int launch_gemm_bn(const CUtensorMap &ta, const CUtensorMap &tb, int Mtil
     const size_t smem = GemmSmem<BN>::BYTES;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(Mtiles, N / BN);
+    if (epi.pdl) {
+        FFS_CUDA_TRY(launch_pdl(k_gemm_bf16<BN>, grid, dim3(128), smem, st, ta, tb, K, epi));
+        return FFS_OK;
+    }
     k_gemm_bf16<BN><<<grid, 128, smem, st>>>(ta, tb, K, epi);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
@@ -580,6 +606,8 @@ __global__ void k_out_layer(const __nv_bfloat16 *H2, int B, int h2, const float 
 __global__ void k_out_loss_dz2(const __nv_bfloat16 *H2, int B, int h2, const float *w3, const float *b3,
                                const float *t, float *dy, float *loss, __nv_bfloat16 *dZ2, __nv_bfloat16 *dZ2T)
 {
+    tc::grid_dep_launch();
+    tc::grid_dep_wait();
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (b >= B) return;
     float acc = 0.0f;
@@ -703,8 +731,8 @@ __global__ void k_mlp_init(float *W, int rows, int cols, int ld, uint64_t seed, 
 // corrections 1 - b1^t and 1 - b2^t; the last block to finish (counted in
 // blocks_done, reset by it) advances the count, after every block has read it.
 // It also writes the BF16 copies the GEMMs read: W1b[i] for the W1 block
-// [0, nW1) and, for the W2 block [w2_off, w2_off + h2 h1), W2b[o][c] and its
-// transpose W2Tb[c][o].
+// [0, nW1) and W2b[o][c] for the W2 block [w2_off, w2_off + h2 h1); the next
+// training step transposes W2b into W2Tb on a side stream.
 __device__ __forceinline__ float adam_one(float &p, float gi, float &m, float &v, float lr, float b1, float b2,
                                           float eps, float c1, float c2)
 {
@@ -718,8 +746,10 @@ __device__ __forceinline__ float adam_one(float &p, float gi, float &m, float &v
 
 __global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
                             float eps, long long *t_prev, unsigned int *blocks_done, int nW1, int w2_off, int h1,
-                            int h2, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W2Tb)
+                            int h2, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b)
 {
+    tc::grid_dep_launch();
+    tc::grid_dep_wait();
     const float t = (float)(*t_prev + 1);
     const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
     const int nW2 = h1 * h2;
@@ -746,16 +776,12 @@ __global__ void k_adam_bf16(float *p, const float *g, float *m, float *v, int n,
             pk.y = *reinterpret_cast<const uint32_t *>(&hi);
             *reinterpret_cast<uint2 *>(W1b + i) = pk;
         } else if (i >= w2_off && i < w2_off + nW2) {
-            const int r = i - w2_off, o = r / h1, c = r - o * h1;   // c .. c + 3 in row o
+            const int r = i - w2_off;
             const __nv_bfloat162 lo = __floats2bfloat162_rn(P.x, P.y), hi = __floats2bfloat162_rn(P.z, P.w);
             uint2 pk;
             pk.x = *reinterpret_cast<const uint32_t *>(&lo);
             pk.y = *reinterpret_cast<const uint32_t *>(&hi);
             *reinterpret_cast<uint2 *>(W2b + r) = pk;
-            W2Tb[(size_t)c * h2 + o] = lo.x;
-            W2Tb[(size_t)(c + 1) * h2 + o] = lo.y;
-            W2Tb[(size_t)(c + 2) * h2 + o] = hi.x;
-            W2Tb[(size_t)(c + 3) * h2 + o] = hi.y;
         }
     }
     for (int i = 4 * nq + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -802,7 +828,7 @@ struct ffs_mlp {
     // a training step's side branches (forked from and joined back into the
     // caller's stream, so that a captured step keeps them in its graph)
     cudaStream_t aux[2] = {nullptr, nullptr};
-    cudaEvent_t ev[7] = {};
+    cudaEvent_t ev[8] = {};
     std::vector<void *> allocs;
 };
 
@@ -826,8 +852,6 @@ static int refresh_bf16(ffs_mlp *M, cudaStream_t st)
 {
     k_f32_to_bf16_padded<<<dim3(4, M->h1), 128, 0, st>>>(M->W1, M->h1, M->K1, M->K1, M->W1b, M->K1);
     k_f32_to_bf16_padded<<<dim3(4, M->h2), 128, 0, st>>>(M->W2, M->h2, M->h1, M->h1, M->W2b, M->h1);
-    k_transpose_bf16<<<dim3((M->h1 + 31) / 32, (M->h2 + 31) / 32), dim3(32, 8), 0, st>>>(M->W2b, M->h2, M->h1, M->h1,
-                                                                                        M->W2Tb, M->h2);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }
@@ -1291,7 +1315,7 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     if (ldx < M->in_dim) return set_error(FFS_EINVAL, "ldx %d < in_dim %d", ldx, M->in_dim);
     cudaStream_t st = (cudaStream_t)stream, s1 = M->aux[0], s2 = M->aux[1];
     cudaEvent_t e_fork = M->ev[0], e_h1 = M->ev[1], e_dz2 = M->ev[2], e_xt = M->ev[3], e_dz1 = M->ev[4],
-                e_s1 = M->ev[5], e_s2 = M->ev[6];
+                e_s1 = M->ev[5], e_s2 = M->ev[6], e_w2t = M->ev[7];
     const int h1 = M->h1, h2 = M->h2, K1 = M->K1;
     // The step's dependency graph on three streams; the caller's stream `st`
     // carries the critical path (forward, loss, dZ1, gW1, Adam), s1 and
@@ -1299,16 +1323,22 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     FFS_CUDA_TRY(cudaEventRecord(e_fork, st));
     FFS_CUDA_TRY(cudaStreamWaitEvent(s1, e_fork, 0));
     FFS_CUDA_TRY(cudaStreamWaitEvent(s2, e_fork, 0));
-    // s1: X^T for gW1 = dZ1^T X (B = XT [K1][B], zero rows beyond in_dim)
+    // s2: W2^T (BF16) for dZ1 = dZ2 W2, from the weights as they are now
+    k_transpose_bf16<<<dim3((h1 + 31) / 32, (h2 + 31) / 32), dim3(32, 8), 0, s2>>>(M->W2b, h2, h1, h1, M->W2Tb, h2);
+    FFS_CUDA_TRY(cudaEventRecord(e_w2t, s2));
+    // s1: the loss zeroed, X^T for gW1 = dZ1^T X (B = XT [K1][B], zero rows
+    // beyond in_dim)
+    if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, s1));
     k_transpose_bf16<<<dim3((K1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s1>>>(
         reinterpret_cast<const __nv_bfloat16 *>(x), B, M->in_dim, ldx, M->XT, B);
     if (K1 > M->in_dim) FFS_CUDA_TRY(cudaMemsetAsync(M->XT + (size_t)M->in_dim * B, 0, (size_t)(K1 - M->in_dim) * B * 2, s1));
     FFS_CUDA_TRY(cudaEventRecord(e_xt, s1));
-    // st: the forward pass's hidden layers
-    if (loss) FFS_CUDA_TRY(cudaMemsetAsync(loss, 0, 4, st));
+    // st: the forward pass's hidden layers; the kernels of the critical path
+    // are launched as programmatic dependents of the one before them
     GemmEpi e;
     memset(&e, 0, sizeof(e));
     e.err = M->err;
+    e.pdl = 1;
     e.mode = 1;
     e.Db = M->H1;
     e.bias = M->b1;
@@ -1323,20 +1353,25 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     // s2: H1^T for gW2 = dZ2^T H1, beside layer 2
     FFS_CUDA_TRY(cudaStreamWaitEvent(s2, e_h1, 0));
     k_transpose_bf16<<<dim3((h1 + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s2>>>(M->H1, B, h1, h1, M->H1T, B);
-    // st: output layer, loss and its backpropagated signal
-    k_out_loss_dz2<<<(B * 32 + 255) / 256, 256, 0, st>>>(M->H2, B, h2, M->w3, M->b3, target, M->dy, loss, M->dZ2,
-                                                          M->dZ2T);
+    // st: output layer, loss and its backpropagated signal (after the loss
+    // was zeroed and X^T written on s1)
+    FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_xt, 0));
+    FFS_CUDA_TRY(launch_pdl(k_out_loss_dz2, dim3((B * 32 + 255) / 256), dim3(256), 0, st, (const __nv_bfloat16 *)M->H2,
+                            B, h2, (const float *)M->w3, (const float *)M->b3, target, M->dy, loss, M->dZ2, M->dZ2T));
     FFS_CUDA_TRY(cudaEventRecord(e_dz2, st));
     // s2: the output layer's gradients and gW2 = dZ2^T H1 (A = dZ2T [h2][B], B = H1T [h1][B])
     FFS_CUDA_TRY(cudaStreamWaitEvent(s2, e_dz2, 0));
     k_out_grads<<<(h2 + 31) / 32, dim3(32, 32), 0, s2>>>(M->H2, M->dZ2, M->dy, B, h2, M->gw3, M->gb2, M->gb3);
     e.mode = 0;
+    e.pdl = 0;
     e.D = M->gW2;
     e.ldd = h1;
     if ((rc = gemm_bf16(M->dZ2T, B, M->H1T, B, h2, h1, B, e, s2))) return rc;
+    e.pdl = 1;
     FFS_CUDA_TRY(cudaEventRecord(e_s2, s2));
     // st: dZ1 = (dZ2 W2) [H1 > 0] (A = dZ2 [B][h2], B = W2T [h1][h2]), FP32 and
     // BF16 transposed, in the GEMM's epilogue
+    FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_w2t, 0));
     e.mode = 3;
     e.D = M->dZ1;
     e.ldd = h1;
@@ -1352,7 +1387,6 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     k_colsum<float><<<(h1 + 31) / 32, dim3(32, 32), 0, s1>>>(M->dZ1, nullptr, B, h1, M->gb1);
     FFS_CUDA_TRY(cudaEventRecord(e_s1, s1));
     // st: gW1 = dZ1^T X (A = dZ1T [h1][B], B = XT [K1][B])
-    FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_xt, 0));
     e.D = M->gW1;
     e.ldd = K1;
     if ((rc = gemm_bf16(M->dZ1T, B, M->XT, B, h1, K1, B, e, st))) return rc;
@@ -1361,8 +1395,9 @@ int ffs_mlp_train_step(ffs_mlp *M, const uint16_t *x, int32_t ldx, const float *
     FFS_CUDA_TRY(cudaStreamWaitEvent(st, e_s2, 0));
     const int nW1 = h1 * K1, w2_off = nW1 + h1;
     const int adam_blocks = std::min(1024, (int)((M->n_params / 4 + 255) / 256));
-    k_adam_bf16<<<adam_blocks, 256, 0, st>>>(M->params, M->grads, M->m, M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f,
-                                      M->d_adam_t, M->d_adam_done, nW1, w2_off, h1, h2, M->W1b, M->W2b, M->W2Tb);
+    FFS_CUDA_TRY(launch_pdl(k_adam_bf16, dim3(adam_blocks), dim3(256), 0, st, M->params, (const float *)M->grads, M->m,
+                            M->v, (int)M->n_params, lr, 0.9f, 0.999f, 1e-8f, M->d_adam_t, M->d_adam_done, nW1, w2_off,
+                            h1, h2, M->W1b, M->W2b));
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }

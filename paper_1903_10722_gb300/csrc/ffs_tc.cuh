@@ -53,6 +53,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// Programmatic dependent launch: let the next kernel in the stream launch
+// (its blocks then wait in grid_dep_wait), and wait until every kernel this
+// one depends on has completed with its memory visible.  Both are no-ops for
+// a kernel launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // One arrival on `bar` (no transaction bytes).
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
