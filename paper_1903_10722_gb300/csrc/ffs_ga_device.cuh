@@ -157,6 +157,117 @@ __device__ __forceinline__ void warp_build_children(const ChildJob &me, int n, i
     }
 }
 
+// Two children at a time, one per 16-lane half of the warp, for rows of at
+// most 120 genes (nb = ceil(n / 8) blocks, nb + 1 <= 16 passes of the p2
+// sweep): the construction of warp_build_children, with shuffles and the
+// prefix sum confined to each half and a mark of mark_words(n) words per
+// half (`mark` holds two).  Children are identical to warp_build_children's.
+__host__ __device__ inline bool pairs_build_fits(int n) { return ((n + 7) >> 3) + 1 <= 16; }
+
+__device__ __forceinline__ void warp_build_children_pairs(const ChildJob &me, int n, int ld, uint32_t *mark)
+{
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const int words = mark_words(n);
+    uint8_t *flag = reinterpret_cast<uint8_t *>(mark + half * words);
+    const int nb = (n + 7) >> 3;
+    const int4 zero4 = make_int4(0, 0, 0, 0);
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, me.active);
+    while (todo) {
+        // the next two jobs: the lower half takes the first, the upper half
+        // the second (and idles when there is none)
+        const int j0 = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        int j1 = -1;
+        if (todo) {
+            j1 = __ffs(todo) - 1;
+            todo &= todo - 1u;
+        }
+        const bool mine = half == 0 || j1 >= 0;
+        const int j = (half && j1 >= 0) ? j1 : j0;
+        const int16_t *p1 = (const int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.p1, j);
+        const int16_t *p2 = (const int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.p2, j);
+        int16_t *child = (int16_t *)__shfl_sync(0xFFFFFFFFu, (unsigned long long)me.child, j);
+        const int l = __shfl_sync(0xFFFFFFFFu, me.l, j);
+        const int r = __shfl_sync(0xFFFFFFFFu, me.r, j);
+        // (a cut outside the row is recorded and the child copies p1)
+        const bool cross = __shfl_sync(0xFFFFFFFFu, (int)me.cross, j) != 0 &&
+                           FFS_DCHECK(l >= 0 && l <= r && r < n, kCheckCut);
+        const int4 *p1v = reinterpret_cast<const int4 *>(p1);
+        const int4 *p2v = reinterpret_cast<const int4 *>(p2);
+        int4 *cv = reinterpret_cast<int4 *>(child);
+        if (mine && !cross)
+            for (int k = hl; k < (ld >> 3); k += 16) cv[k] = p1v[k];
+        const bool xo = mine && cross;
+        // both parents' blocks in registers (block q with lane q of the half)
+        int4 a0 = zero4, c0 = zero4;
+        if (xo && hl < nb) {
+            a0 = p1v[hl];
+            c0 = p2v[hl];
+        }
+        if (xo)
+            for (int w = hl; 4 * w < words; w += 16) reinterpret_cast<uint4 *>(flag)[w] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        // the segment p1[l..r], eight genes (one 16-byte block) per lane
+        if (xo && hl < nb && 8 * hl <= r && 8 * hl + 7 >= l) {
+            const uint32_t wv[4] = {(uint32_t)a0.x, (uint32_t)a0.y, (uint32_t)a0.z, (uint32_t)a0.w};
+            const bool full = 8 * hl >= l && 8 * hl + 7 <= r;
+            if (full) cv[hl] = a0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = 8 * hl + u;
+                if (idx >= l && idx <= r) {
+                    const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
+                    if (!full) child[idx] = (int16_t)g;
+                    if ((unsigned)g < (unsigned)n) flag[g] = 1u;
+                }
+            }
+        }
+        __syncwarp();
+        // p2 from position start = r + 1 onward cyclically: pass t (lane t of
+        // the half) takes block (start / 8 + t) mod nb
+        const int start = (r + 1 == n) ? 0 : r + 1;
+        const int t = hl;
+        int q = (start >> 3) + t;
+        if (q >= nb) q -= nb;
+        const int src = q & 15;   // lanes with t > nb read an ignored block
+        int4 v;
+        v.x = __shfl_sync(0xFFFFFFFFu, c0.x, src, 16);
+        v.y = __shfl_sync(0xFFFFFFFFu, c0.y, src, 16);
+        v.z = __shfl_sync(0xFFFFFFFFu, c0.z, src, 16);
+        v.w = __shfl_sync(0xFFFFFFFFu, c0.w, src, 16);
+        const bool pass = xo && t <= nb;
+        const uint32_t wv[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+        const int lo = t == 0 ? start : 0, hi = t == nb ? start : n;   // natural indices kept in this pass
+        unsigned take = 0u;
+        int gv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = 8 * q + u;
+            const int g = (int)(int16_t)(wv[u >> 1] >> (16 * (u & 1)));
+            gv[u] = g;
+            const bool in_seg = (unsigned)g < (unsigned)n && flag[g] != 0u;
+            if (pass && idx >= lo && idx < hi && !in_seg) take |= 1u << u;
+        }
+        const int cnt = __popc(take);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o, 16);
+            if (hl >= o) incl += y;
+        }
+        const int first = start + incl - cnt;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if ((take >> u) & 1u) {
+                int pos = first + __popc(take & ((1u << u) - 1u));
+                if (pos >= n) pos -= n;
+                if (FFS_DCHECK(pos >= 0 && pos < n, kCheckWrite)) child[pos] = (int16_t)gv[u];
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // The FFS_DEBUG_CHECKS build's validity check of one row by one warp: every
 // gene in [0, n), no gene twice (a bit per job in `bits`, (n + 31) / 32
 // words of this warp's shared memory), and a makespan >= 0; a failure is

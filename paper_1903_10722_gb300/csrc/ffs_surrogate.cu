@@ -123,8 +123,11 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
         job.r = max(u, v);
         mutate = fires(b1.w, g.cell_pm);
     }
-    uint32_t *bits = bits_smem + (threadIdx.x >> 5) * mark_words(n);
-    warp_build_children(job, n, ld, bits);
+    if (pairs_build_fits(n)) {
+        warp_build_children_pairs(job, n, ld, bits_smem + (threadIdx.x >> 5) * 2 * mark_words(n));
+    } else {
+        warp_build_children(job, n, ld, bits_smem + (threadIdx.x >> 5) * mark_words(n));
+    }
     if (mutate) {
         int16_t *child = job.child;
         const int i = (int)uniform_below(b2.x, (uint32_t)n), j = (int)uniform_below(b2.y, (uint32_t)n);
@@ -467,7 +470,7 @@ int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const Is
     const int total = batch.count * rows * cols * K;
     const int T = 128;
     const int warps = (total + kCandPerWarp - 1) / kCandPerWarp;
-    const size_t smem = (size_t)(T / 32) * mark_words(inst->n) * 4;
+    const size_t smem = (size_t)(T / 32) * (pairs_build_fits(inst->n) ? 2 : 1) * mark_words(inst->n) * 4;
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_sur_candidates<<<(warps * 32 + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand,
                                                                 static_cast<__nv_bfloat16 *>(X), xw);

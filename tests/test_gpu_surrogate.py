@@ -46,12 +46,16 @@ def _compare(gpu, isl, ga, n, tag):
         assert np.array_equal(ms.cpu().numpy().astype(np.int64), ga.mss[i]), (tag, i)
 
 
-@pytest.mark.parametrize("warmup,variant", [(0, 0), (2, 0), (2, 5)])
-def test_screened_generations_match_oracle_given_scores(gpu, warmup, variant):
+@pytest.mark.parametrize("warmup,variant,n,rows,cols,K", [(0, 0, 20, 8, 8, 8), (2, 0, 20, 8, 8, 8),
+                                                         (2, 5, 20, 8, 8, 8), (2, 0, 130, 8, 8, 8),
+                                                         (2, 0, 37, 5, 5, 3)])
+def test_screened_generations_match_oracle_given_scores(gpu, warmup, variant, n, rows, cols, K):
     """variant 5: the picks decoded by the stage-parallel select kernel and
-    the pseudo children by the stage-parallel eval kernel."""
-    rows, cols, K = 8, 8, 8
-    spec, o, g, isl, ga, params = _setup(gpu, 20, 5, 3, 3, rows, cols, 1, 32, K, warmup, 0, variant=variant)
+    the pseudo children by the stage-parallel eval kernel.  n = 130: the
+    candidates built a whole warp per child (rows above 120 genes), else two
+    per warp; 5 x 5 cells x 3 candidates: a last warp with an odd number of
+    candidates (one half idle)."""
+    spec, o, g, isl, ga, params = _setup(gpu, n, 5, 3, 3, rows, cols, 1, 32, K, warmup, 0, variant=variant)
     inst_feat = omlp.instance_features(spec.n, spec.S, spec.M, spec.p)
     cells = rows * cols
     for gen in range(1, 5):
