@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
         const int n = I.n, S = I.S;
         stage_table(smem + map.tab, I.tab, table_words(n, S));
         for (int i = threadIdx.x; i < 2 * S; i += T) st[i] = I.stage[i];
+        __syncthreads();   // the table and the stage array are complete in shared memory
         if (threadIdx.x == 0) {
             DecodeLayout &L = s_L;
             L.n = n;
@@ -131,9 +132,9 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
             L.M = st;
             L.heap_off = st + S;
             // this instance's stages whose heaps fit the warp's TMEM columns,
-            // from the stage table in global memory: the other threads'
-            // copies into st[] are not visible before the barrier below
-            const int32_t *gst = I.stage;
+            // from the stage array in shared memory (complete since the
+            // barrier above)
+            const int32_t *gst = st;
             int ns = 0;
             if (!L.single && shape.tmem_cols)
                 while (ns < S && gst[S + ns] + gst[ns] <= shape.tmem_group_cols) ++ns;
