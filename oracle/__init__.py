@@ -170,6 +170,10 @@ def _load():
             ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _i16p, _i64p, _i16p, _i64p,
             ctypes.POINTER(ctypes.c_float), ctypes.c_int32, _i32p, _i16p]
         lib.orc_screened_cellular_generation.restype = ctypes.c_int64
+        lib.orc_screened_pseudo_generation.argtypes = gen_args + [
+            ctypes.c_int32, ctypes.c_int64, _i16p, _i64p, _i16p, _i64p,
+            ctypes.POINTER(ctypes.c_float), ctypes.c_int32, _i32p, _i16p]
+        lib.orc_screened_pseudo_generation.restype = ctypes.c_int64
         lib.orc_family_best2.argtypes = [_i64p, _i32p]
         lib.orc_family_best2.restype = None
         lib.orc_init_pseudo_pair.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
@@ -502,6 +506,31 @@ def screened_cellular_generation(inst: Instance, prm: Params, island: int, gener
                                          _ptr(sc, ctypes.c_float), K, _ptr(chosen, ctypes.c_int32),
                                          _ptr(cands, ctypes.c_int16))
     return out, out_ms, chosen, cands
+
+
+def screened_pseudo_generation(inst: Instance, prm: Params, island: int, generation: int, pop: np.ndarray,
+                               ms: np.ndarray, scores: np.ndarray, K: int):
+    """One surrogate-screened pseudo generation given the candidate children's
+    scores ([pairs][K][2], flattened); returns (new pop, new makespans, chosen
+    candidate per pair (-1: the pair did not cross), candidates
+    [pairs*K*2][n], #decoded)."""
+    lib = _load()
+    pop = np.ascontiguousarray(pop, dtype=np.int16)
+    ms = np.ascontiguousarray(ms, dtype=np.int64)
+    sc = np.ascontiguousarray(scores, dtype=np.float32)
+    out = np.zeros_like(pop)
+    out_ms = np.zeros_like(ms)
+    pairs = pop.shape[0] // 2
+    chosen = np.zeros(pairs, dtype=np.int32)
+    cands = np.zeros((pairs * K * 2, inst.n), dtype=np.int16)
+    cp = prm._c(inst)
+    k = lib.orc_screened_pseudo_generation(inst.n, inst.S, _ptr(inst.M, ctypes.c_int32),
+                                           _ptr(inst.p, ctypes.c_int32), ctypes.byref(cp), island, generation,
+                                           pop.shape[0], pop.shape[1], _ptr(pop, ctypes.c_int16),
+                                           _ptr(ms, ctypes.c_int64), _ptr(out, ctypes.c_int16),
+                                           _ptr(out_ms, ctypes.c_int64), _ptr(sc, ctypes.c_float), K,
+                                           _ptr(chosen, ctypes.c_int32), _ptr(cands, ctypes.c_int16))
+    return out, out_ms, chosen, cands, int(k)
 
 
 def family_best2(fms) -> list:

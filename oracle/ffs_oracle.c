@@ -79,7 +79,8 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
 
 /* Purpose codes of the counter's fourth word (top 8 bits). */
 enum { ORC_PURPOSE_INIT = 1, ORC_PURPOSE_CELLULAR = 2, ORC_PURPOSE_PSEUDO = 3,
-       ORC_PURPOSE_SURROGATE = 16 /* + candidate index */ };
+       ORC_PURPOSE_SURROGATE = 16 /* + candidate index */,
+       ORC_PURPOSE_SURROGATE_PSEUDO = 32 /* + candidate index */ };
 
 /* Draw number d of the stream keyed by (seed, island, generation, cell):
  * counter = (d / 4, cell, generation, island | purpose << 24),
@@ -735,6 +736,96 @@ int64_t orc_screened_cellular_generation(int32_t n, int32_t S, const int32_t *M,
     free(child);
     free(best);
     return cells;
+}
+
+/* Surrogate-screened pseudo generation.  Pair k (rows 2k, 2k+1 = a, b)
+ * crosses with probability pc, decided by draw 0 of purpose
+ * ORC_PURPOSE_PSEUDO as in the plain generation; a pair that does not cross
+ * is copied unchanged.  A crossing pair has K candidate cut pairs: candidate
+ * t takes its cuts from draws 1 and 2 of purpose ORC_PURPOSE_SURROGATE_PSEUDO
+ * + t (uniform in [0, n), l = min, r = max) and makes c1 = OX(a, b) and
+ * c2 = OX(b, a) on them, with the given scores scores[2 (k K + t)] and
+ * scores[2 (k K + t) + 1].  The candidate whose better child scores lowest,
+ * min(score c1, score c2), wins (the lowest t on ties); only its two
+ * children are decoded exactly, and the pair is replaced from them as in the
+ * plain generation.  chosen[k] = the winning t, or -1 for a pair that did
+ * not cross.  candidates (may be NULL) receives every pair's candidate
+ * children, crossing or not, as rows [pairs][K][2][n].  Returns the number
+ * of exact decodes. */
+int64_t orc_screened_pseudo_generation(int32_t n, int32_t S, const int32_t *M, const int32_t *p,
+                                       const orc_params *prm, uint32_t island, uint32_t generation,
+                                       int32_t size, int64_t ld,
+                                       const int16_t *pop_in, const int64_t *ms_in,
+                                       int16_t *pop_out, int64_t *ms_out,
+                                       const float *scores, int32_t K, int32_t *chosen,
+                                       int16_t *candidates)
+{
+    int16_t *c1 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int16_t *c2 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int16_t *b1 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int16_t *b2 = (int16_t *)malloc((size_t)n * sizeof(int16_t));
+    int64_t decoded = 0;
+    for (int32_t k = 0; k < size / 2; ++k) {
+        const int16_t *a = pop_in + (int64_t)(2 * k) * ld;
+        const int16_t *b = pop_in + (int64_t)(2 * k + 1) * ld;
+        int16_t *oa = pop_out + (int64_t)(2 * k) * ld;
+        int16_t *ob = pop_out + (int64_t)(2 * k + 1) * ld;
+        /* every candidate, and the winner by its better child's score */
+        int32_t pick = 0;
+        float pick_score = 0.0f;
+        for (int32_t t = 0; t < K; ++t) {
+            const uint32_t purpose = ORC_PURPOSE_SURROGATE_PSEUDO + (uint32_t)t;
+            const int32_t u = (int32_t)orc_uniform(orc_draw(prm->seed, purpose, island, generation, (uint32_t)k, 1u),
+                                                   (uint32_t)n);
+            const int32_t v = (int32_t)orc_uniform(orc_draw(prm->seed, purpose, island, generation, (uint32_t)k, 2u),
+                                                   (uint32_t)n);
+            const int32_t l = u < v ? u : v, r = u < v ? v : u;
+            orc_order_crossover(n, a, b, l, r, c1);
+            orc_order_crossover(n, b, a, l, r, c2);
+            if (candidates) {
+                memcpy(candidates + (((int64_t)k * K + t) * 2) * n, c1, (size_t)n * sizeof(int16_t));
+                memcpy(candidates + (((int64_t)k * K + t) * 2 + 1) * n, c2, (size_t)n * sizeof(int16_t));
+            }
+            const float s1 = scores[((int64_t)k * K + t) * 2], s2 = scores[((int64_t)k * K + t) * 2 + 1];
+            const float sc = s2 < s1 ? s2 : s1;
+            if (t == 0 || sc < pick_score) {
+                pick = t;
+                pick_score = sc;
+                memcpy(b1, c1, (size_t)n * sizeof(int16_t));
+                memcpy(b2, c2, (size_t)n * sizeof(int16_t));
+            }
+        }
+        const uint32_t x0 = orc_draw(prm->seed, ORC_PURPOSE_PSEUDO, island, generation, (uint32_t)k, 0u);
+        if (!orc_bernoulli(x0, prm->pseudo_pc)) {
+            if (chosen) chosen[k] = -1;
+            memcpy(oa, a, (size_t)n * sizeof(int16_t));
+            memcpy(ob, b, (size_t)n * sizeof(int16_t));
+            ms_out[2 * k] = ms_in[2 * k];
+            ms_out[2 * k + 1] = ms_in[2 * k + 1];
+            continue;
+        }
+        if (chosen) chosen[k] = pick;
+        const int64_t m1 = orc_decode_obj(n, S, M, p, prm->obj, b1, NULL);
+        const int64_t m2 = orc_decode_obj(n, S, M, p, prm->obj, b2, NULL);
+        decoded += 2;
+        if (prm->pseudo_always) {
+            memcpy(oa, b1, (size_t)n * sizeof(int16_t));
+            memcpy(ob, b2, (size_t)n * sizeof(int16_t));
+            ms_out[2 * k] = m1;
+            ms_out[2 * k + 1] = m2;
+            continue;
+        }
+        const int16_t *fam[4] = { b1, b2, a, b };
+        int64_t fms[4] = { m1, m2, ms_in[2 * k], ms_in[2 * k + 1] };
+        int32_t best2[2];
+        orc_family_best2(fms, best2);
+        memcpy(oa, fam[best2[0]], (size_t)n * sizeof(int16_t));
+        memcpy(ob, fam[best2[1]], (size_t)n * sizeof(int16_t));
+        ms_out[2 * k] = fms[best2[0]];
+        ms_out[2 * k + 1] = fms[best2[1]];
+    }
+    free(c1); free(c2); free(b1); free(b2);
+    return decoded;
 }
 
 /* ------------------------------------------------------------------ */
