@@ -576,8 +576,19 @@ int ffs_mlp_check(ffs_mlp *mlp, ffs_stream stream);
  * (ring_capacity must then hold two generations' pairs); with overlap = 0
  * it runs beside G + 1's candidate building only and ends before G + 1's
  * candidates are scored.
- * Pseudo islands are not screened.  The network must have in_dim >= n + 40
- * and max_batch >= cellular cells x candidates; it is used, not owned;
+ * With screen_pseudo = 0 the pseudo islands run the plain generation.  With
+ * screen_pseudo = 1 a pair that crosses (the plain generation's decision,
+ * draw 0 of its pseudo stream) has `candidates` candidate cut pairs,
+ * candidate t with its cuts from draws 1 and 2 of Philox purpose 32 + t and
+ * the children c1 = OX(a, b), c2 = OX(b, a); the network scores every
+ * candidate child (of every pair, crossing or not), the candidate whose
+ * better child scores lowest wins (the lowest t on ties), its two children
+ * are decoded exactly and replace the pair as in the plain generation
+ * (family best-2, or always); no pseudo pair enters the ring buffer.  The
+ * pseudo islands then step together (at most 64 of them), and the network
+ * must also have max_batch >= pseudo pairs x candidates x 2.  The network
+ * must have in_dim >= n + 40 and max_batch >= cellular cells x candidates;
+ * it is used, not owned;
  * ring_capacity must be at least cells + train_batch.  Generations are
  * replayed from CUDA graphs (captured on first use; four forms: before /
  * after the warm-up, with / without a training round).
@@ -596,12 +607,20 @@ typedef struct {
     int32_t warmup_generations;  /* generations scored 0 while the ring fills (5) */
     float lr;                    /* Adam learning rate (1e-3) */
     int32_t overlap;             /* 1: the training round runs beside the whole screen (1) */
+    int32_t screen_pseudo;       /* 1: the pseudo islands' pairs are screened too (0) */
 } ffs_surrogate_params;
 void ffs_surrogate_params_default(ffs_surrogate_params *p);
 int ffs_islands_attach_surrogate(ffs_islands *isl, ffs_mlp *mlp, const ffs_surrogate_params *sp,
                                  ffs_stream stream);
 int ffs_islands_surrogate_last(const ffs_islands *isl, float *scores, int32_t *chosen, float *loss,
                                int64_t *pairs, int16_t *candidates, int32_t ld_out, ffs_stream stream);
+/* With screen_pseudo: the last generation's pseudo candidate children's
+ * scores [pairs x candidates x 2] (pairs of the pseudo islands in island
+ * order, then candidate, then child), the picks [pairs] (-1: the pair did
+ * not cross) and the candidate children [pairs x candidates x 2][ld_out]
+ * (may be NULL). */
+int ffs_islands_surrogate_last_pseudo(const ffs_islands *isl, float *scores, int32_t *chosen, int16_t *candidates,
+                                      int32_t ld_out, ffs_stream stream);
 
 /* ------------------------------------------------------------------------
  * The checked build (no counterpart in the paper).  The library built with

@@ -111,6 +111,7 @@ _SIGS = [
     ("ffs_surrogate_params_default", None, [_vp]),
     ("ffs_islands_attach_surrogate", _i32, [_vp, _vp, _vp, _vp]),
     ("ffs_islands_surrogate_last", _i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
+    ("ffs_islands_surrogate_last_pseudo", _i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     ("ffs_measure_int_rate", _i32, [_i32, _vp, _vp, _vp]),
     ("ffs_selftest_wait_timeout", _i32, [_i64, _vp, _vp]),
     ("ffs_islands_set_generation", _i32, [_vp, _i64]),
@@ -729,7 +730,7 @@ def ffs_mlp_check(m: MLP, stream=None):
 class ffs_surrogate_params(ctypes.Structure):
     _fields_ = [("candidates", _i32), ("train_every", _i32), ("train_steps", _i32), ("train_batch", _i32),
                 ("ring_capacity", _i32), ("warmup_generations", _i32), ("lr", ctypes.c_float),
-                ("overlap", _i32)]
+                ("overlap", _i32), ("screen_pseudo", _i32)]
 
 
 def ffs_surrogate_params_default() -> ffs_surrogate_params:
@@ -749,6 +750,12 @@ def ffs_islands_surrogate_last(isl: Islands, scores=None, chosen=None, loss=None
     _check(load().ffs_islands_surrogate_last(isl.handle, _ptr(scores), _ptr(chosen), _ptr(loss), ctypes.byref(pairs),
                                              _ptr(candidates), ld_out, _stream(stream)))
     return pairs.value
+
+
+def ffs_islands_surrogate_last_pseudo(isl: Islands, scores=None, chosen=None, candidates=None, ld_out: int = 0,
+                                      stream=None):
+    _check(load().ffs_islands_surrogate_last_pseudo(isl.handle, _ptr(scores), _ptr(chosen), _ptr(candidates), ld_out,
+                                                    _stream(stream)))
 
 
 def ffs_measure_int_rate(kind: int, stream=None) -> dict:

@@ -41,10 +41,11 @@ __device__ __forceinline__ bool ffs_dcheck(bool ok, int code)
 
 // Purpose codes of the Philox counter's fourth word (bits 24..31):
 // surrogate candidate k of a cell uses kPurposeSurrogateBase + k (k < 16),
+// candidate cut pair t of a screened pseudo pair kPurposeSurrogatePseudoBase + t,
 // the surrogate's training-batch sampling kPurposeTrainSample, its weight
 // initialisation kPurposeMlpInit.
 constexpr uint32_t kPurposeInit = 1, kPurposeCellular = 2, kPurposePseudo = 3, kPurposeMlpInit = 14,
-                   kPurposeTrainSample = 15, kPurposeSurrogateBase = 16;
+                   kPurposeTrainSample = 15, kPurposeSurrogateBase = 16, kPurposeSurrogatePseudoBase = 32;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two

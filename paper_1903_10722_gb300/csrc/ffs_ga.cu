@@ -306,6 +306,81 @@ int launch_pseudo(const ffs_instance *inst, const GaScalars &g, const IslandBatc
     return FFS_OK;
 }
 
+// Screened pseudo pairs (after the scoring of their candidates): lane
+// l < kPairsPerWarp of a warp takes one pair.  The crossover decision is the
+// plain generation's (draw 0, purpose kPurposePseudo); a crossing pair takes
+// the candidate whose better child scores lowest, min(scores[2 (q K + t)],
+// scores[2 (q K + t) + 1]) (the lowest t on ties), and its two children go
+// to the compacted child slots that the decode and replacement launches of
+// the plain generation then read.  chosen[q] = the pick, or -1.
+__global__ void k_sur_pseudo_pick(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int ld, int K,
+                                  const int16_t *cand, const float *scores, int32_t *chosen, PseudoScratch s)
+{
+    const int pairs = size / 2;
+    const int total = pairs * batch.count;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw * kPairsPerWarp >= total) return;   // whole warps leave together
+    const int gp = gw * kPairsPerWarp + lane;
+    const bool mine = lane < kPairsPerWarp && gp < total;
+    const int gq = mine ? gp : gw * kPairsPerWarp;
+    const int bi = gq / pairs, k = gq - bi * pairs;
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(batch.ref[bi], pin, msin, pout, msout, gen);
+    bool cross = false;
+    int pick = 0;
+    if (mine) {
+        const U4 d = draw_block(g.seed, kPurposePseudo, batch.ref[bi].island, gen, (uint32_t)k, 0u);
+        cross = fires(d.x, g.pseudo_pc);
+        const float *sc = scores + (int64_t)gq * K * 2;
+        float best = 0.0f;
+        for (int t = 0; t < K; ++t) {
+            const float s1 = sc[2 * t], s2 = sc[2 * t + 1];
+            const float v = s2 < s1 ? s2 : s1;
+            if (t == 0 || v < best) {
+                best = v;
+                pick = t;
+            }
+        }
+        if (!FFS_DCHECK(pick >= 0 && pick < K, kCheckPick)) pick = 0;
+        chosen[gq] = cross ? pick : -1;
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, cross);
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(s.count, 2 * __popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const int slot = base + 2 * __popc(mask & ((1u << lane) - 1u));
+    if (mine) s.pair_slot[gp] = cross ? slot : -1;
+    const int16_t *c1 = cand + ((int64_t)gq * K + pick) * 2 * ld;
+    warp_copy_row_pairs(cross, c1, s.children + (int64_t)slot * ld, c1 + ld, s.children + (int64_t)(slot + 1) * ld,
+                        ld);
+}
+
+// The rest of a screened pseudo generation once its candidates are scored:
+// the picks into the child slots, their exact decode and the plain
+// generation's replacement.
+int launch_pseudo_screened(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size, int ld,
+                           int K, const int16_t *cand, const float *scores, int32_t *chosen, void *scratch, int B_req,
+                           int T_req, unsigned long long *decoded, cudaStream_t st)
+{
+    const int pairs = size / 2 * batch.count;
+    if (pairs <= 0) return FFS_OK;
+    PseudoScratch s = carve(scratch, size, ld, batch.count);
+    FFS_CUDA_TRY(cudaMemsetAsync(s.count, 0, 2 * sizeof(int32_t), st));
+    k_sur_pseudo_pick<<<pair_blocks(pairs, 128), 128, 0, st>>>(g, batch, size, ld, K, cand, scores, chosen, s);
+    FFS_CUDA_TRY(cudaGetLastError());
+    int rc = launch_eval(inst, s.children, 2 * (int64_t)pairs, ld, s.child_ms, s.count, B_req, T_req, decoded, st,
+                         g.variant);
+    if (rc) return rc;
+    k_pseudo_replace<<<pair_blocks(pairs, 128), 128, 0, st>>>(g, batch, size, ld, s);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // One launch for the decoding work of a generation: the children of all
 // cellular islands (bred by k_breed_dual into the output rows; decoded
@@ -775,6 +850,14 @@ struct SurrogateState {
     void *X = nullptr;             // BF16 [cells_total * K][xw]
     float *scores = nullptr;       // [cells_total * K]
     int32_t *chosen = nullptr;     // [cells_total]
+    // screened pseudo pairs (screen_pseudo): every pair's candidate children,
+    // their scoring rows and scores after the cellular ones in X and scores,
+    // the picks
+    int pairs_total = 0;           // pairs of all pseudo islands
+    int pseudo_size = 0;           // rows of each pseudo island
+    int16_t *cand_p = nullptr;     // [pairs_total * K * 2][ld]
+    int32_t *chosen_p = nullptr;   // [pairs_total]
+    std::vector<int> pseudo_islands;
     int16_t *ring_rows = nullptr;  // [ring_cap][ld]
     int32_t *ring_ms = nullptr;
     long long ring_cap = 0, ring_count = 0;
@@ -797,6 +880,7 @@ struct SurrogateState {
     cudaGraphExec_t g_gen[2][2][2] = {};   // [warm][train][migration due]
     cudaStream_t side = nullptr, side2 = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fork2_ev = nullptr, join2_ev = nullptr, fold_ev = nullptr;
+    cudaEvent_t pcand_ev = nullptr, pfwd_ev = nullptr;   // screened pseudo: candidates built, scores written
     void drop_graphs()
     {
         for (auto &plane : g_gen)
@@ -809,7 +893,7 @@ struct SurrogateState {
         drop_graphs();
         if (side) cudaStreamDestroy(side);
         if (side2) cudaStreamDestroy(side2);
-        for (cudaEvent_t e : {fork_ev, join_ev, fork2_ev, join2_ev, fold_ev})
+        for (cudaEvent_t e : {fork_ev, join_ev, fork2_ev, join2_ev, fold_ev, pcand_ev, pfwd_ev})
             if (e) cudaEventDestroy(e);
     }
 };
@@ -858,9 +942,12 @@ static IslandRef device_ref(const ffs_islands *S, int i)
     return r;
 }
 
-template <typename F>
+template <typename F, typename H>
 static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, bool use_copy,
-                                    bool fold_ready, cudaStream_t st, F between);
+                                    bool fold_ready, cudaStream_t st, F between, H after_scores);
+static int screened_pseudo_candidates(ffs_islands *S, bool warm, cudaStream_t st);
+static int screened_pseudo_scores(ffs_islands *S, bool warm, bool use_copy, cudaStream_t st);
+static int screened_pseudo_finish(ffs_islands *S, cudaStream_t st);
 
 // CTAs of the scoring forward's persistent GEMM while a training round runs
 // beside it: the SMs left over take the round's kernels.
@@ -904,7 +991,21 @@ static int islands_generation_launch(ffs_islands *S, const std::vector<int> &ids
             int rc = launch_sur_tick(S->sur->d_ctr, 2, -1, st);
             if (rc) return rc;
             rc = screened_cellular_launch(S, sel, S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations, false,
-                                          false, st, [](cudaStream_t) { return (int)FFS_OK; });
+                                          false, st, [](cudaStream_t) { return (int)FFS_OK; },
+                                          [](cudaStream_t) { return (int)FFS_OK; });
+            if (rc) return rc;
+            continue;
+        }
+        if (kind == 1 && S->sur && S->sur->sp.screen_pseudo && !sel.empty()) {
+            // a screened pseudo generation alone (every pseudo island together)
+            if (sel.size() != S->sur->pseudo_islands.size())
+                return set_error(FFS_EUNSUPPORTED, "screened pseudo islands step together");
+            const bool warm = S->host_gen[sel[0]] + 1 > S->sur->sp.warmup_generations;
+            int rc = screened_pseudo_candidates(S, warm, st);
+            if (!rc && warm)
+                rc = mlp_fold_bias(S->sur->mlp, false, S->sur->P, S->sur->inst_feat, S->sur->nfeat, st);
+            if (!rc) rc = screened_pseudo_scores(S, warm, false, st);
+            if (!rc) rc = screened_pseudo_finish(S, st);
             if (rc) return rc;
             continue;
         }
@@ -989,9 +1090,9 @@ static int record_launch(ffs_islands *S, cudaStream_t st)
 // each cell's best-scored candidate exactly, replaces the cell iff better and
 // appends the pair to the ring (the device ring counter advanced by the
 // cells of each batch).
-template <typename F>
+template <typename F, typename H>
 static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel, bool warm, bool use_copy,
-                                    bool fold_ready, cudaStream_t st, F between)
+                                    bool fold_ready, cudaStream_t st, F between, H after_scores)
 {
     SurrogateState *R = S->sur;
     const GaScalars g = scalars_of(&S->prm);
@@ -1021,10 +1122,11 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
     if (warm && !fold_ready &&
         (rc = mlp_fold_bias(R->mlp, use_copy, R->P, R->inst_feat, R->nfeat, st)))
         return rc;
+    // every batch's scores, then `after_scores` (more scoring on this
+    // stream), then every batch's selection
     offset = 0;
     for (const IslandBatch &batch : batches) {
         const int ncells = batch.count * cells;
-        const int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
         float *scores = R->scores + (int64_t)offset * K;
         if (warm) {
             const void *X = static_cast<const char *>(R->X) + (int64_t)offset * K * R->xw * 2;
@@ -1034,6 +1136,14 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
         } else if ((rc = launch_fill_f32(scores, (int64_t)ncells * K, 0.0f, st))) {
             return rc;
         }
+        offset += ncells;
+    }
+    if ((rc = after_scores(st))) return rc;
+    offset = 0;
+    for (const IslandBatch &batch : batches) {
+        const int ncells = batch.count * cells;
+        const int16_t *cand = R->cand + (int64_t)offset * K * S->ld;
+        const float *scores = R->scores + (int64_t)offset * K;
         if ((rc = launch_sur_select(S->inst, g, batch, S->rows, S->cols, S->ld, K, cand, scores, R->chosen + offset,
                                     R->ring_rows, R->ring_ms, R->ring_cap, R->d_ctr, S->prm.decode_chunk,
                                     S->prm.block_threads, S->d_decoded, st)))
@@ -1042,6 +1152,52 @@ static int screened_cellular_launch(ffs_islands *S, const std::vector<int> &sel,
         offset += ncells;
     }
     return FFS_OK;
+}
+
+// Screened pseudo islands (all of them, one batch): candidates on `st` into
+// cand_p and, warm, their scoring rows after the cellular ones in X.
+static IslandBatch pseudo_batch(const ffs_islands *S)
+{
+    IslandBatch b;
+    memset(&b, 0, sizeof(b));
+    b.count = (int)S->sur->pseudo_islands.size();
+    for (int t = 0; t < b.count; ++t) b.ref[t] = device_ref(S, S->sur->pseudo_islands[t]);
+    return b;
+}
+
+static int screened_pseudo_candidates(ffs_islands *S, bool warm, cudaStream_t st)
+{
+    SurrogateState *R = S->sur;
+    const int K = R->sp.candidates;
+    void *Xp = static_cast<char *>(R->X) + (int64_t)R->cells_total * K * R->xw * 2;
+    return launch_sur_pseudo_candidates(S->inst, scalars_of(&S->prm), pseudo_batch(S), R->pseudo_size, S->ld, K,
+                                        R->cand_p, warm ? Xp : nullptr, R->xw, st);
+}
+
+// Their scores (after the cellular ones): the forward pass over their rows
+// (layer 1's folded bias computed before, in stream order), or zeros during
+// the warm-up.
+static int screened_pseudo_scores(ffs_islands *S, bool warm, bool use_copy, cudaStream_t st)
+{
+    SurrogateState *R = S->sur;
+    const int K = R->sp.candidates;
+    const int64_t rows = (int64_t)R->pairs_total * K * 2;
+    float *sp = R->scores + (int64_t)R->cells_total * K;
+    if (!warm) return launch_fill_f32(sp, rows, 0.0f, st);
+    const void *Xp = static_cast<const char *>(R->X) + (int64_t)R->cells_total * K * R->xw * 2;
+    return mlp_forward_folded(R->mlp, use_copy, Xp, R->xw, S->inst->n, R->P, R->inst_feat, R->nfeat, (int)rows, sp,
+                              use_copy ? kScreenForwardCtas : 0, st);
+}
+
+// The picks, their exact decode and the replacement.
+static int screened_pseudo_finish(ffs_islands *S, cudaStream_t st)
+{
+    SurrogateState *R = S->sur;
+    const int K = R->sp.candidates;
+    const float *sp = R->scores + (int64_t)R->cells_total * K;
+    return launch_pseudo_screened(S->inst, scalars_of(&S->prm), pseudo_batch(S), R->pseudo_size, S->ld, K, R->cand_p,
+                                  sp, R->chosen_p, S->d_scratch, S->prm.decode_chunk, S->prm.block_threads,
+                                  S->d_decoded, st);
 }
 
 // One round of online training of the surrogate on pairs from the ring
@@ -1084,11 +1240,19 @@ static int screened_generation(ffs_islands *S, bool warm, bool train, bool migra
     int rc = launch_sur_tick(R->d_ctr, 2, -1, st);
     if (rc) return rc;
     if (overlap && warm && (rc = mlp_take_copy(R->mlp, st))) return rc;
+    // screened pseudo islands: their candidates on the side stream now,
+    // scored after the cellular candidates, then picked and decoded there
+    const bool screen_pse = R->sp.screen_pseudo && !pse.empty();
     if (!pse.empty()) {
         NvtxRange r("ffs pseudo islands (side stream)");
         FFS_CUDA_TRY(cudaEventRecord(R->fork_ev, st));
         FFS_CUDA_TRY(cudaStreamWaitEvent(R->side, R->fork_ev, 0));
-        if ((rc = islands_generation_launch(S, pse, R->side))) return rc;
+        if (screen_pse) {
+            if ((rc = screened_pseudo_candidates(S, warm, R->side))) return rc;
+            FFS_CUDA_TRY(cudaEventRecord(R->pcand_ev, R->side));
+        } else if ((rc = islands_generation_launch(S, pse, R->side))) {
+            return rc;
+        }
     }
     // with overlap, the training stream first folds the copy's layer-1 bias
     // (beside the candidate building), then runs the round
@@ -1106,11 +1270,24 @@ static int screened_generation(ffs_islands *S, bool warm, bool train, bool migra
     }
     {
         NvtxRange r("ffs screened cellular islands: candidates, scores, select");
-        rc = screened_cellular_launch(S, cel, warm, overlap, fold_side, st, [&](cudaStream_t cs) -> int {
-            if (train && !overlap) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
-            if (fold_side) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->fold_ev, 0));
-            return FFS_OK;
-        });
+        rc = screened_cellular_launch(
+            S, cel, warm, overlap, fold_side, st,
+            [&](cudaStream_t cs) -> int {
+                if (train && !overlap) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->join2_ev, 0));
+                if (fold_side) FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->fold_ev, 0));
+                return FFS_OK;
+            },
+            [&](cudaStream_t cs) -> int {
+                if (!screen_pse) return FFS_OK;
+                // the pseudo candidates' scores on this stream (after the
+                // cellular ones: one forward at a time), the rest on `side`
+                FFS_CUDA_TRY(cudaStreamWaitEvent(cs, R->pcand_ev, 0));
+                int r2 = screened_pseudo_scores(S, warm, overlap, cs);
+                if (r2) return r2;
+                FFS_CUDA_TRY(cudaEventRecord(R->pfwd_ev, cs));
+                FFS_CUDA_TRY(cudaStreamWaitEvent(R->side, R->pfwd_ev, 0));
+                return screened_pseudo_finish(S, R->side);
+            });
         if (rc) return rc;
     }
     if (overlap) FFS_CUDA_TRY(cudaStreamWaitEvent(st, R->join2_ev, 0));
@@ -1447,6 +1624,20 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     if ((long long)sp->ring_capacity < (long long)cells_total + sp->train_batch)
         return set_error(FFS_EINVAL, "ring_capacity must hold one generation's pairs plus a training batch");
     if (sp->overlap != 0 && sp->overlap != 1) return set_error(FFS_EINVAL, "overlap must be 0 or 1");
+    if (sp->screen_pseudo != 0 && sp->screen_pseudo != 1) return set_error(FFS_EINVAL, "screen_pseudo must be 0 or 1");
+    std::vector<int> pseudo_islands;
+    long long pairs_total = 0;
+    for (int i = 0; i < S->I; ++i)
+        if (S->kind[i] == 1) {
+            pseudo_islands.push_back(i);
+            pairs_total += S->size[i] / 2;
+        }
+    if (!sp->screen_pseudo) pairs_total = 0;
+    if (sp->screen_pseudo && (int)pseudo_islands.size() > kMaxBatch)
+        return set_error(FFS_EUNSUPPORTED, "screened pseudo islands: at most %d", kMaxBatch);
+    if (pairs_total * K * 2 > mlp_max_batch(mlp))
+        return set_error(FFS_EINVAL, "network max_batch %d < %lld pseudo candidate children per generation",
+                         mlp_max_batch(mlp), pairs_total * K * 2);
     if (sp->overlap && (long long)sp->ring_capacity < 2LL * cells_total)
         return set_error(FFS_EINVAL, "with overlap, ring_capacity must hold two generations' pairs");
     if (sp->overlap) {
@@ -1468,11 +1659,18 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
         S->allocs.push_back(p);
         return p;
     };
-    const size_t ncand = (size_t)cells_total * K;
+    const size_t ncand = (size_t)cells_total * K, npc = (size_t)pairs_total * K * 2;
     R->cand = (int16_t *)alloc(ncand * S->ld * 2);
     R->xw = round_up(n, 8);
-    R->X = alloc(ncand * R->xw * 2);
-    R->scores = (float *)alloc(ncand * 4);
+    R->X = alloc((ncand + npc) * R->xw * 2);
+    R->scores = (float *)alloc((ncand + npc) * 4);
+    R->pairs_total = (int)pairs_total;
+    R->pseudo_islands = pseudo_islands;
+    R->pseudo_size = pseudo_islands.empty() ? 0 : S->size[pseudo_islands[0]];
+    if (npc) {
+        R->cand_p = (int16_t *)alloc(npc * S->ld * 2);
+        R->chosen_p = (int32_t *)alloc((size_t)pairs_total * 4);
+    }
     R->chosen = (int32_t *)alloc((size_t)cells_total * 4);
     R->ring_rows = (int16_t *)alloc((size_t)R->ring_cap * S->ld * 2);
     R->ring_ms = (int32_t *)alloc((size_t)R->ring_cap * 4);
@@ -1484,7 +1682,7 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
     R->d_ctr = (long long *)alloc(4 * sizeof(long long));
     R->d_norm = (float *)alloc(2 * sizeof(float));
     if (!R->cand || !R->X || !R->scores || !R->chosen || !R->ring_rows || !R->ring_ms || !R->inst_feat ||
-        !R->train_X || !R->train_t || !R->loss || !R->d_ctr || !R->d_norm) {
+        !R->train_X || !R->train_t || !R->loss || !R->d_ctr || !R->d_norm || (npc && (!R->cand_p || !R->chosen_p))) {
         delete R;
         return set_error(FFS_ENOMEM, "surrogate buffers");
     }
@@ -1520,7 +1718,9 @@ int ffs_islands_attach_surrogate(ffs_islands *S, ffs_mlp *mlp, const ffs_surroga
         cudaEventCreateWithFlags(&R->join_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->fork2_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&R->join2_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&R->fold_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&R->fold_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->pcand_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&R->pfwd_ev, cudaEventDisableTiming) != cudaSuccess) {
         (void)cudaGetLastError();
         delete R;
         return set_error(FFS_ECUDA, "surrogate state initialisation");
@@ -1552,6 +1752,27 @@ int ffs_islands_surrogate_last(const ffs_islands *S, float *scores, int32_t *cho
                                        (size_t)R->cells_total * R->sp.candidates, cudaMemcpyDefault, st));
     }
     if (pairs) *pairs = R->ring_count;
+    return FFS_OK;
+}
+
+int ffs_islands_surrogate_last_pseudo(const ffs_islands *S, float *scores, int32_t *chosen, int16_t *candidates,
+                                      int32_t ld_out, ffs_stream stream)
+{
+    clear_error();
+    if (!S || !S->sur) return set_error(FFS_EINVAL, "no surrogate attached");
+    const SurrogateState *R = S->sur;
+    if (!R->sp.screen_pseudo || !R->pairs_total) return set_error(FFS_EINVAL, "no screened pseudo islands");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rows = (size_t)R->pairs_total * R->sp.candidates * 2;
+    if (scores)
+        FFS_CUDA_TRY(cudaMemcpyAsync(scores, R->scores + (size_t)R->cells_total * R->sp.candidates, rows * 4,
+                                     cudaMemcpyDefault, st));
+    if (chosen) FFS_CUDA_TRY(cudaMemcpyAsync(chosen, R->chosen_p, (size_t)R->pairs_total * 4, cudaMemcpyDefault, st));
+    if (candidates) {
+        if (ld_out < S->inst->n) return set_error(FFS_EINVAL, "ld_out %d < n %d", ld_out, S->inst->n);
+        FFS_CUDA_TRY(cudaMemcpy2DAsync(candidates, (size_t)ld_out * 2, R->cand_p, (size_t)S->ld * 2,
+                                       (size_t)S->inst->n * 2, rows, cudaMemcpyDefault, st));
+    }
     return FFS_OK;
 }
 

@@ -284,6 +284,10 @@ int validate_rows(const void *p, int ld, int n);
 // Surrogate screening (ffs_surrogate.cu).
 int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
                           int ld, int K, int16_t *cand, void *X, int xw, cudaStream_t st);
+// Every candidate child of screened pseudo pairs ([pairs][K][2] rows of
+// cand) and, with X non-null, their scoring input rows of xw values.
+int launch_sur_pseudo_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
+                                 int ld, int K, int16_t *cand, void *X, int xw, cudaStream_t st);
 int launch_sur_select(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int rows, int cols,
                       int ld, int K, const int16_t *cand, const float *scores, int32_t *chosen, int16_t *ring_rows,
                       int32_t *ring_ms, long long ring_cap, const long long *ctr, int B_req, int T_req,

@@ -147,6 +147,61 @@ __global__ void k_sur_candidates(GaScalars g, const __grid_constant__ IslandBatc
     }
 }
 
+// Candidate cut pairs of screened pseudo pairs: job jj = (pair q, candidate
+// t, child w) with jj = 2 (q K + t) + w over the batch's pairs; candidate t
+// of pair k takes its cuts from draws 1 and 2 of purpose
+// kPurposeSurrogatePseudoBase + t (l = min, r = max of two uniforms in
+// [0, n)), child 0 = OX(a, b), child 1 = OX(b, a).  Lane l < kCandPerWarp of
+// warp w builds job w * kCandPerWarp + l; with X non-null the warp then
+// writes its jobs' job positions (rows of xw values).
+__global__ void k_sur_pseudo_candidates(GaScalars g, const __grid_constant__ IslandBatch batch, int size, int n,
+                                        int ld, int K, int16_t *cand, __nv_bfloat16 *X, int xw)
+{
+    extern __shared__ uint32_t bits_smem[];
+    const int pairs = size / 2;
+    const int total = batch.count * pairs * K * 2;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (gw * kCandPerWarp >= total) return;   // whole warps leave together
+    const int jj = gw * kCandPerWarp + lane;
+    const bool valid = lane < kCandPerWarp && jj < total;
+    const int tj = valid ? jj : gw * kCandPerWarp;
+    const int q = tj >> 1, w = tj & 1;
+    const int gp = q / K, t = q - gp * K;
+    const int bi = gp / pairs, k = gp - bi * pairs;
+    const IslandRef &ref = batch.ref[bi];
+    const int16_t *pin;
+    const int32_t *msin;
+    int16_t *pout;
+    int32_t *msout;
+    uint32_t gen;
+    resolve(ref, pin, msin, pout, msout, gen);
+    const U4 d = draw_block(g.seed, kPurposeSurrogatePseudoBase + (uint32_t)t, ref.island, gen, (uint32_t)k, 0u);
+    const int u = (int)uniform_below(d.y, (uint32_t)n), v = (int)uniform_below(d.z, (uint32_t)n);
+    const int16_t *a = pin + (int64_t)(2 * k) * ld, *b = a + ld;
+    ChildJob job;
+    job.active = valid;
+    job.cross = true;
+    job.l = min(u, v);
+    job.r = max(u, v);
+    job.p1 = w ? b : a;
+    job.p2 = w ? a : b;
+    job.child = cand + (int64_t)tj * ld;
+    if (pairs_build_fits(n)) {
+        warp_build_children_pairs(job, n, ld, bits_smem + (threadIdx.x >> 5) * 2 * mark_words(n));
+    } else {
+        warp_build_children(job, n, ld, bits_smem + (threadIdx.x >> 5) * mark_words(n));
+    }
+    if (!X) return;
+    __syncwarp();
+    unsigned todo = __ballot_sync(0xFFFFFFFFu, valid);
+    while (todo) {
+        const int j0 = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const int r = gw * kCandPerWarp + j0;
+        warp_write_positions(cand + (int64_t)r * ld, n, xw, X + (int64_t)r * xw);
+    }
+}
+
 // Per cell: the best-scored candidate (lowest score, lowest index on ties)
 // is decoded exactly and replaces the cell iff better; the pair is appended
 // to the ring buffer at slot (ring_base + cell) mod ring_cap, ring_base =
@@ -474,6 +529,21 @@ int launch_sur_candidates(const ffs_instance *inst, const GaScalars &g, const Is
     FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_sur_candidates<<<(warps * 32 + T - 1) / T, T, smem, st>>>(g, batch, rows, cols, inst->n, ld, K, cand,
                                                                 static_cast<__nv_bfloat16 *>(X), xw);
+    FFS_CUDA_TRY(cudaGetLastError());
+    return FFS_OK;
+}
+
+int launch_sur_pseudo_candidates(const ffs_instance *inst, const GaScalars &g, const IslandBatch &batch, int size,
+                                 int ld, int K, int16_t *cand, void *X, int xw, cudaStream_t st)
+{
+    const long long total = (long long)batch.count * (size / 2) * K * 2;
+    if (total <= 0) return FFS_OK;
+    const int T = 128;
+    const long long warps = (total + kCandPerWarp - 1) / kCandPerWarp;
+    const size_t smem = (size_t)(T / 32) * (pairs_build_fits(inst->n) ? 2 : 1) * mark_words(inst->n) * 4;
+    FFS_CUDA_TRY(cudaFuncSetAttribute(k_sur_pseudo_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sur_pseudo_candidates<<<(unsigned)((warps * 32 + T - 1) / T), T, smem, st>>>(
+        g, batch, size, inst->n, ld, K, cand, static_cast<__nv_bfloat16 *>(X), xw);
     FFS_CUDA_TRY(cudaGetLastError());
     return FFS_OK;
 }

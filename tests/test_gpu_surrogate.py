@@ -79,6 +79,66 @@ def test_screened_generations_match_oracle_given_scores(gpu, warmup, variant, n,
             assert np.max(np.abs(scores - want)) <= 2e-2 * scale, gen
 
 
+@pytest.mark.parametrize("warmup,always,n,train", [(0, False, 20, 0), (2, False, 37, 0), (2, True, 130, 0),
+                                                   (1, False, 60, 1)])
+def test_screened_pseudo_generations_match_oracle_given_scores(gpu, warmup, always, n, train):
+    """screen_pseudo = 1: the pseudo island's pairs screened too.  Given the
+    GPU's scores (cellular and pseudo), the oracle's screened generations
+    reproduce both islands, the cellular picks and the pseudo picks (-1 for
+    pairs that did not cross); the pseudo scores match the float64 network
+    on the oracle's own candidate children.  n = 130: whole-warp crossover;
+    train = 1: with the training round beside the screen."""
+    rows, cols, K, psize = 8, 8, 4, 64
+    spec = make_instance(n, 4, 2, 4, seed=n)
+    o = orc.Instance(spec.n, spec.S, spec.M, spec.p)
+    g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    prm = gpu.ffs_params_default()
+    prm.seed = 7
+    prm.pseudo_always = int(always)
+    prm.migration_mode, prm.migration_gap = 0, 0
+    isl = gpu.Islands(g, prm, 1, rows, cols, 1, psize)
+    params = mlp_params(540, 512, 256, seed=11)
+    params["b1"] = np.random.default_rng(1).normal(0, 0.05, 512).astype(np.float32)
+    net = gpu.MLP(540, 512, 256, 1024)
+    net.set_params(params)
+    sp = gpu.ffs_surrogate_params_default()
+    sp.candidates, sp.warmup_generations, sp.train_every = K, warmup, train
+    sp.train_batch, sp.train_steps, sp.ring_capacity = 128, 2, 4096
+    sp.screen_pseudo = 1
+    gpu.ffs_islands_attach_surrogate(isl, net, sp)
+    ga = orc.IslandGA(o, orc.Params(seed=7, pseudo_always=always), 1, rows, cols, 1, psize)
+    inst_feat = omlp.instance_features(spec.n, spec.S, spec.M, spec.p)
+    cells, pairs = rows * cols, psize // 2
+    for gen in range(1, 6):
+        before = net.get()
+        gpu.ffs_island_step(isl, -1, 1)
+        scores = np.zeros(cells * K, np.float32)
+        chosen = np.zeros(cells, np.int32)
+        gpu.ffs_islands_surrogate_last(isl, scores, chosen)
+        pscores = np.zeros(pairs * K * 2, np.float32)
+        pchosen = np.zeros(pairs, np.int32)
+        gpu.ffs_islands_surrogate_last_pseudo(isl, pscores, pchosen)
+        torch.cuda.synchronize()
+        pop, ms, want_chosen, _ = orc.screened_cellular_generation(o, ga.prm, 0, gen, rows, cols, ga.pops[0],
+                                                                   ga.mss[0], scores, K)
+        assert chosen.tolist() == want_chosen.tolist(), gen
+        ga.pops[0], ga.mss[0] = pop, ms
+        pop, ms, want_p, cands, _ = orc.screened_pseudo_generation(o, ga.prm, 1, gen, ga.pops[1], ga.mss[1],
+                                                                   pscores, K)
+        assert pchosen.tolist() == want_p.tolist(), gen
+        ga.pops[1], ga.mss[1] = pop, ms
+        _compare(gpu, isl, ga, spec.n, gen)
+        if gen <= warmup:
+            assert not pscores.any()
+        else:
+            # the screen scores with the weights as they stood when the generation began
+            X = omlp.features(cands, spec.n, 500, inst_feat)
+            want, _ = omlp.forward(before, X, rounded=True)
+            scale = np.mean(np.abs(want)) + 1e-3
+            assert np.max(np.abs(pscores - want)) <= 2e-2 * scale, gen
+        assert (want_p >= 0).any() and (want_p < 0).any()
+
+
 @pytest.mark.parametrize("overlap", [0, 1])
 def test_screened_training_runs_and_keeps_parity(gpu, overlap):
     rows, cols, K = 16, 16, 8
