@@ -66,7 +66,7 @@ def batch():
     assert gpu.ffs_debug_check_error() == 0
 
 
-def screened():
+def screened(screen_pseudo=0):
     spec = make_instance(40, 5, 2, 4, seed=5)
     g = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
     prm = gpu.ffs_params_default()
@@ -76,6 +76,7 @@ def screened():
     net.init(3)
     sp = gpu.ffs_surrogate_params_default()
     sp.ring_capacity, sp.train_batch, sp.warmup_generations = 4096, 128, 2
+    sp.screen_pseudo = screen_pseudo
     gpu.ffs_islands_attach_surrogate(isl, net, sp)
     gpu.ffs_island_step(isl, -1, 8)
     gpu.ffs_mlp_check(net)
@@ -137,6 +138,7 @@ def main():
     islands("penetration")
     batch()
     screened()
+    screened(screen_pseudo=1)
     assign_ga()
     reported_invalid_row()
     print("debug checks ok")

@@ -57,8 +57,8 @@ def test_islands_checkpoint_resume_equals_uninterrupted_run(gpu, mode):
     _assert_same_islands(gpu, a, b)
 
 
-@pytest.mark.parametrize("overlap", [0, 1])
-def test_screened_islands_checkpoint_resume_equals_uninterrupted_run(gpu, overlap):
+@pytest.mark.parametrize("overlap,screen_pseudo", [(0, 0), (1, 0), (1, 1)])
+def test_screened_islands_checkpoint_resume_equals_uninterrupted_run(gpu, overlap, screen_pseudo):
     spec = make_instance(40, 6, 2, 5, seed=41)
     inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
     rows = cols = 8
@@ -74,6 +74,7 @@ def test_screened_islands_checkpoint_resume_equals_uninterrupted_run(gpu, overla
         sp.candidates, sp.warmup_generations, sp.train_every, sp.train_steps = K, 2, 1, 2
         sp.train_batch, sp.ring_capacity = 128, 512      # the ring wraps within the run
         sp.overlap = overlap
+        sp.screen_pseudo = screen_pseudo
         gpu.ffs_islands_attach_surrogate(isl, net, sp)
         return isl, net
 
