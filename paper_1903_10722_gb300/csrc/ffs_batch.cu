@@ -96,7 +96,6 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
     const SmemMap map = smem_map(shape.max_n, shape.max_S, T, 0);   // the crossover ran in k_batch_breed
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * shape.max_S;
-    uint32_t *region = smem + map.region + threadIdx.x;
     int32_t *st = reinterpret_cast<int32_t *>(smem + map.stage);
     const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
     const int cells = rows * cols;
@@ -160,6 +159,7 @@ __global__ void __launch_bounds__(512) k_batch_cellular(const BatchInst *__restr
         __syncthreads();
         if (s_skip) continue;   // block-uniform; the loop head synchronises again
         const DecodeLayout &L = s_L;
+        uint32_t *region = thread_region(smem + map.region, L.thread_words);
         const IslandRef ref = batch_ref(I, cur, gen, un.x);
         const int end = min(un.y + T, cells);
         for (int base = un.y + warp * 32; base < end; base += T) {

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(512) k_eval(DecodeLayout L, const uint32_t *__
     decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
-    uint32_t *region = smem + map.region + threadIdx.x;
+    uint32_t *region = thread_region(smem + map.region, Ls.thread_words);
     if (decoded && blockIdx.x == 0 && threadIdx.x == 0 && N > 0) atomicAdd(decoded, (unsigned long long)N);
     for (int64_t base = (int64_t)blockIdx.x * T + warp * 32; base < N; base += (int64_t)gridDim.x * T) {
         const int64_t c = base + lane;

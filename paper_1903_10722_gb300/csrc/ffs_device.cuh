@@ -137,8 +137,20 @@ struct DecodeLayout {
 // functions below are out of line (one call per stage and round); passing
 // them 32-bit shared addresses instead of generic pointers keeps their
 // arguments few (all in registers) and their loads and stores in the shared
-// space.  One thread's words are T apart (stride = 4T bytes).
+// space.  A warp's 32 threads own a block of 32 x thread_words words of the
+// region, lane-interleaved (word k of lane l at 32 k + l), so one thread's
+// words are kWordStride = 128 bytes apart: a compile-time stride, which the
+// loads and stores of consecutive words take as immediate offsets.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kWordStride = 128u;
+
+// This thread's first word of the decoder's region.
+__device__ __forceinline__ uint32_t *thread_region(uint32_t *region_base, int thread_words)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    return region_base + (size_t)warp * 32u * (uint32_t)thread_words + lane;
+}
+
 __device__ __forceinline__ uint32_t lds32(uint32_t a)
 {
     uint32_t v;
@@ -160,7 +172,8 @@ __device__ __forceinline__ uint32_t lds16(uint32_t a)
 
 // A stage's saved heap as one word: bit 31 set -> TMEM address of the
 // thread's first heap word (consecutive columns of its lane; TMEM addresses
-// never use bit 31), else the shared address of its first word (stride 4T).
+// never use bit 31), else the shared address of its first word (stride
+// kWordStride).
 constexpr uint32_t kHeapInTmem = 0x80000000u;
 
 __device__ __forceinline__ uint32_t heap_handle(const DecodeLayout &L, uint32_t region_sa, int T, int s)
@@ -171,7 +184,8 @@ __device__ __forceinline__ uint32_t heap_handle(const DecodeLayout &L, uint32_t 
         return kHeapInTmem | (L.tmem_addr + ((uint32_t)((warp & 3) * 32) << 16) +
                               (uint32_t)((warp >> 2) * L.tmem_group_cols + off));
     }
-    return region_sa + (uint32_t)((off - L.tmem_split) * T) * 4u;
+    (void)T;
+    return region_sa + (uint32_t)(off - L.tmem_split) * kWordStride;
 }
 
 // Saved heap -> f[0, Mr) (the other slots keep their values).  TMEM loads
@@ -392,7 +406,7 @@ __device__ __noinline__ uint4 stage_round(uint32_t nB, uint32_t SH, uint32_t hea
     uint32_t mulSH;
     asm("mov.b32 %0, %1;" : "=r"(mulSH) : "r"(1u << SH));
     const uint32_t lowmask = mulSH - 1u, idmask = lowmask & ~1u;
-    const uint32_t stride = blockDim.x * 4u;
+    constexpr uint32_t stride = kWordStride;
     const bool single = B >= n;
     const uint32_t rel = (obj & 0xFFFFu) << 2, due = EMIT ? 0u : (obj >> 16) << 2;
     uint32_t tard = 0;
@@ -590,7 +604,7 @@ __device__ __noinline__ uint4 pair_round(uint32_t nB, uint32_t SH, uint32_t heap
     uint32_t mulSH;
     asm("mov.b32 %0, %1;" : "=r"(mulSH) : "r"(1u << SH));
     const uint32_t lowmask = mulSH - 1u, idmask = lowmask & ~1u;
-    const uint32_t stride = blockDim.x * 4u;
+    constexpr uint32_t stride = kWordStride;
     const bool chunked = B < n;
     if constexpr (EMIT_B) due = 0u;
     uint32_t tard = 0;
@@ -763,7 +777,7 @@ __device__ __forceinline__ void genes_to_keys(const int16_t *genes, int cnt, uin
 
 // Decode one chromosome (row of genes in global memory, 16-byte aligned).
 //   L     : the block's layout in shared memory (see decode_tmem_begin).
-//   region: this thread's interleaved shared words (base + tid), stride T.
+//   region: this thread's first shared word (thread_region), stride kWordStride.
 //   ptab  : shared uint16 table, row s at ptab + s * table_row_halves(n).
 //   wst   : this warp's per-stage state, S entries (shared).
 // All lanes of a warp must call this together for the same instance (the
@@ -775,7 +789,7 @@ __device__ __forceinline__ int32_t decode_chromosome(const DecodeLayout &L, cons
                                                      WarpStageState *wst)
 {
     const int n = L.n, S = L.S;
-    const uint32_t stride = (uint32_t)T * 4u;
+    constexpr uint32_t stride = kWordStride;
     const uint32_t region_sa = tc::smem_u32(region);
     const uint32_t buf = region_sa + (uint32_t)L.heap_words * stride;
     const uint32_t tab = tc::smem_u32(ptab);

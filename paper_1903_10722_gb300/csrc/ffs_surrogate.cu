@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(512) k_sur_select(DecodeLayout L, const uint32
     decode_tmem_begin(Ls);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStageState *wst = reinterpret_cast<WarpStageState *>(smem + map.warp) + warp * L.S;
-    uint32_t *region = smem + map.region + threadIdx.x;
+    uint32_t *region = thread_region(smem + map.region, Ls.thread_words);
     const uint16_t *tab = reinterpret_cast<const uint16_t *>(smem + map.tab);
     const int cells = rows * cols;
     const int total = cells * batch.count;
