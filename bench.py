@@ -1164,13 +1164,13 @@ def _paper_instance(ffs, inst, iseed, gens, seeds, sweep):
 # the launch shapes the autotuner picks, (threads, chunk, variant) -> bytes,
 # from ncu captures of the current kernel (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = {(384, 104, 3): 116_367_872 + 7_662_592}
+K_STEP_DECODE_DRAM_BYTES = {(384, 104, 3): 116_588_544 + 7_509_248}
 
 
 # DRAM bytes of one k_batch_cellular (decode) launch of batch_256, per
 # launch shape (threads, chunk, variant), from ncu captures of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum); other shapes null.
-K_BATCH_CELLULAR_DRAM_BYTES = {(384, 128, 3): 143_038_976 + 30_597_632}
+K_BATCH_CELLULAR_DRAM_BYTES = {(384, 128, 3): 142_953_728 + 31_060_992}
 
 
 def launches_per_generation(w) -> int:
