@@ -951,7 +951,7 @@ static int screened_pseudo_finish(ffs_islands *S, cudaStream_t st);
 
 // CTAs of the scoring forward's persistent GEMM while a training round runs
 // beside it: the SMs left over take the round's kernels.
-constexpr int kScreenForwardCtas = 112;
+constexpr int kScreenForwardCtas = 96;
 
 // One generation of the islands in `ids` (all of one kind): cellular islands
 // in launches of up to kMaxBatch, pseudo islands likewise, one decode of all
