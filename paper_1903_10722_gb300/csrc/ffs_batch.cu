@@ -13,6 +13,7 @@
 // better over its cell's copy.  Shared memory is sized for the largest
 // instance.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -705,9 +706,11 @@ struct BatchBlobHeader {
     int32_t count, rows, cols, pad;
     uint64_t fingerprint;
     int64_t generation, decoded;
+    int64_t bytes;       // the blob's length
+    uint64_t checksum;   // blob_checksum of the whole blob, this field taken as zero
     ffs_params prm;
 };
-constexpr uint32_t kBatchBlobMagic = 0x42534646u, kBatchBlobVersion = 1;
+constexpr uint32_t kBatchBlobMagic = 0x42534646u, kBatchBlobVersion = 2;
 
 static int64_t b16(int64_t b) { return (b + 15) / 16 * 16; }
 
@@ -767,6 +770,7 @@ int ffs_batch_checkpoint_save(const ffs_batch *b, void *host, int64_t capacity, 
     hd.cols = b->cols;
     hd.fingerprint = batch_fingerprint(b);
     hd.generation = b->host_gen;
+    hd.bytes = need;
     hd.prm = b->prm;
     unsigned long long dec = 0;
     FFS_CUDA_TRY(cudaMemcpyAsync(&dec, b->d_decoded, 8, cudaMemcpyDeviceToHost, st));
@@ -781,6 +785,8 @@ int ffs_batch_checkpoint_save(const ffs_batch *b, void *host, int64_t capacity, 
         FFS_CUDA_TRY(cudaMemcpyAsync(ms, h.ms[b->host_cur], (size_t)cells * 4, cudaMemcpyDefault, st));
     }
     FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint64_t ck = blob_checksum(static_cast<const char *>(host), need, offsetof(BatchBlobHeader, checksum));
+    memcpy(static_cast<char *>(host) + offsetof(BatchBlobHeader, checksum), &ck, 8);
     return FFS_OK;
 }
 
@@ -796,6 +802,10 @@ int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_
     memcpy(&hd, hp, sizeof(hd));
     if (hd.magic != kBatchBlobMagic || hd.version != kBatchBlobVersion)
         return set_error(FFS_EINVAL, "not a batch checkpoint of this version");
+    if (hd.bytes < (int64_t)sizeof(hd) || hd.bytes > size || hd.bytes % 16)
+        return set_error(FFS_EINVAL, "checkpoint truncated (%lld of %lld bytes)", (long long)size, (long long)hd.bytes);
+    if (blob_checksum(static_cast<const char *>(host), hd.bytes, offsetof(BatchBlobHeader, checksum)) != hd.checksum)
+        return set_error(FFS_EINVAL, "checkpoint corrupted (checksum differs)");
     if (hd.count != b->count || hd.rows != b->rows || hd.cols != b->cols)
         return set_error(FFS_EINVAL, "checkpoint of %d instances on %dx%d tori; this batch: %d on %dx%d", hd.count,
                          hd.rows, hd.cols, b->count, b->rows, b->cols);

@@ -1,5 +1,6 @@
 // ffs_capi.cu -- C ABI entry points: errors, instances, the batched decoder,
 // Philox draws and population initialisation.
+#include <atomic>
 #include <climits>
 #include <cstdlib>
 #include <cstdarg>
@@ -10,6 +11,17 @@
 #include "ffs_lanes.cuh"
 
 namespace fgpu {
+
+bool injected_alloc_failure()
+{
+    static const long long at = [] {
+        const char *e = getenv("FFS_INJECT_ALLOC_FAILURE");
+        return e ? atoll(e) : 0LL;
+    }();
+    static std::atomic<long long> count{0};
+    return at > 0 && ++count == at;
+}
+
 
 static thread_local std::string g_err;
 

@@ -5,6 +5,7 @@
 // (chunked ranking, ring and penetration copies), and the islands handle
 // that replays one generation of every island from a CUDA graph.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -2196,6 +2197,8 @@ struct IslandsBlobHeader {
     int32_t I, ld, n, has_surrogate;
     uint64_t fingerprint;
     int64_t decoded;
+    int64_t bytes;       // the blob's length
+    uint64_t checksum;   // blob_checksum of the whole blob, this field taken as zero
     ffs_params prm;
 };
 struct IslandBlobEntry {
@@ -2208,7 +2211,7 @@ struct SurrogateBlob {
     int32_t candidates, pad;
     int64_t ring_cap, ring_count, train_rounds, valid;
 };
-constexpr uint32_t kIslandsBlobMagic = 0x49534646u, kIslandsBlobVersion = 2;
+constexpr uint32_t kIslandsBlobMagic = 0x49534646u, kIslandsBlobVersion = 3;
 
 static int64_t r16(int64_t b) { return (b + 15) / 16 * 16; }
 
@@ -2248,6 +2251,7 @@ int ffs_checkpoint_save(const ffs_islands *S, void *host, int64_t capacity, ffs_
     h.n = S->inst->n;
     h.has_surrogate = S->sur ? 1 : 0;
     h.fingerprint = instance_fingerprint(S->inst);
+    h.bytes = need;
     h.prm = S->prm;
     unsigned long long dec = 0;
     FFS_CUDA_TRY(cudaMemcpyAsync(&dec, S->d_decoded, 8, cudaMemcpyDeviceToHost, st));
@@ -2299,6 +2303,9 @@ int ffs_checkpoint_save(const ffs_islands *S, void *host, int64_t capacity, ffs_
         if (rc) return rc;
     }
     FFS_CUDA_TRY(cudaStreamSynchronize(st));
+    // the checksum over everything written, its own field taken as zero
+    const uint64_t ck = blob_checksum(static_cast<const char *>(host), need, offsetof(IslandsBlobHeader, checksum));
+    memcpy(static_cast<char *>(host) + offsetof(IslandsBlobHeader, checksum), &ck, 8);
     return FFS_OK;
 }
 
@@ -2315,6 +2322,10 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
     memcpy(&h, hp, sizeof(h));
     if (h.magic != kIslandsBlobMagic || h.version != kIslandsBlobVersion)
         return set_error(FFS_EINVAL, "not an islands checkpoint of this version");
+    if (h.bytes < (int64_t)sizeof(h) || h.bytes > size || h.bytes % 16)
+        return set_error(FFS_EINVAL, "checkpoint truncated (%lld of %lld bytes)", (long long)size, (long long)h.bytes);
+    if (blob_checksum(static_cast<const char *>(host), h.bytes, offsetof(IslandsBlobHeader, checksum)) != h.checksum)
+        return set_error(FFS_EINVAL, "checkpoint corrupted (checksum differs)");
     if (h.I != S->I || h.ld != S->ld || h.n != S->inst->n)
         return set_error(FFS_EINVAL, "checkpoint of %d islands (ld %d, n %d); this handle has %d (ld %d, n %d)", h.I, h.ld,
                          h.n, S->I, S->ld, S->inst->n);

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -134,6 +135,27 @@ inline uint64_t instance_fingerprint(const ffs_instance *I, uint64_t h = 1469598
     mix((int64_t)I->host_D.size());
     for (int32_t v : I->host_D) mix(v);
     mix(I->wt);
+    return h;
+}
+
+// Failure injection for tests (host side, no device fault): with
+// FFS_INJECT_ALLOC_FAILURE=k in the environment, the k-th device allocation
+// of a network's buffers in the process (counting from 1) fails as an
+// out-of-memory allocation would.  Unset: never.
+bool injected_alloc_failure();
+
+// Checksum of a checkpoint blob: FNV-1a over its 64-bit words (blobs are
+// multiples of 16 bytes), the word at byte offset `skip` (the checksum's own
+// field) taken as zero.
+inline uint64_t blob_checksum(const char *p, int64_t bytes, int64_t skip)
+{
+    uint64_t h = 14695981039346656037ull;
+    for (int64_t o = 0; o + 8 <= bytes; o += 8) {
+        uint64_t w = 0;
+        if (o != skip) memcpy(&w, p + o, 8);
+        h ^= w;
+        h *= 1099511628211ull;
+    }
     return h;
 }
 

@@ -1120,9 +1120,14 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->h1 = h1;
     M->h2 = h2;
     M->max_batch = max_batch;
+    bool failed = false;   // an allocation failed (nothing is kept for it)
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+        if (injected_alloc_failure() || cudaMalloc(&p, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            failed = true;
+            return nullptr;
+        }
         M->allocs.push_back(p);
         return p;
     };
@@ -1150,11 +1155,10 @@ int ffs_mlp_create(int32_t in_dim, int32_t h1, int32_t h2, int32_t max_batch, ff
     M->d_adam_t = (long long *)alloc(8);
     M->d_adam_done = (unsigned int *)alloc(4);
     M->fold = (float *)alloc((size_t)h1 * 4);
-    for (void *p : M->allocs)
-        if (!p) {
-            mlp_free(M);
-            return set_error(FFS_ENOMEM, "MLP buffers");
-        }
+    if (failed) {
+        mlp_free(M);
+        return set_error(FFS_ENOMEM, "MLP buffers");
+    }
     for (cudaStream_t &s : M->aux)
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
             (void)cudaGetLastError();

@@ -125,6 +125,79 @@ def test_islands_checkpoint_refuses_other_shapes_and_instances(gpu):
         gpu.ffs_checkpoint_load(c, blob)
 
 
+def test_checkpoints_refuse_corrupted_blobs(gpu):
+    """A checkpoint with one byte altered (in the header, a population row, a
+    makespan or the surrogate's ring and weights) fails its checksum: load
+    returns FFS_EINVAL and writes nothing; the unaltered blob still loads."""
+    spec = make_instance(30, 6, 2, 4, seed=31)
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    a = _dual(gpu, inst)
+    net = gpu.MLP(540, 512, 256, 1024)
+    net.init(3)
+    sp = gpu.ffs_surrogate_params_default()
+    sp.candidates, sp.train_batch, sp.ring_capacity, sp.warmup_generations = 4, 128, 1024, 1
+    gpu.ffs_islands_attach_surrogate(a, net, sp)
+    gpu.ffs_island_step(a, -1, 3)
+    blob = gpu.ffs_checkpoint_save(a)
+    b = _dual(gpu, inst)
+    net_b = gpu.MLP(540, 512, 256, 1024)
+    gpu.ffs_islands_attach_surrogate(b, net_b, sp)
+    before = _islands_state(gpu, b)
+    for at in (40, 300, len(blob) // 3, len(blob) // 2, len(blob) - 5):
+        bad = blob.copy()
+        bad[at] ^= 0x10
+        with pytest.raises(gpu.FFSError) as e:
+            gpu.ffs_checkpoint_load(b, bad)
+        assert e.value.status == gpu.FFS_EINVAL
+    after = _islands_state(gpu, b)
+    assert all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) for x, y in zip(before, after))
+    gpu.ffs_checkpoint_load(b, blob)
+    _assert_same_islands(gpu, a, b)
+    # the batch's checkpoint likewise
+    specs = make_batch(count=3, seed=5, n_range=(5, 40), s_range=(2, 5), m_range=(1, 4))
+    bt = gpu.Batch(specs, gpu.ffs_params_default(), 8, 8)
+    gpu.ffs_batch_step(bt, 2)
+    bblob = gpu.ffs_batch_checkpoint_save(bt)
+    bad = bblob.copy()
+    bad[len(bad) // 2] ^= 0x01
+    bt2 = gpu.Batch(specs, gpu.ffs_params_default(), 8, 8)
+    with pytest.raises(gpu.FFSError) as e:
+        gpu.ffs_batch_checkpoint_load(bt2, bad)
+    assert e.value.status == gpu.FFS_EINVAL
+    gpu.ffs_batch_checkpoint_load(bt2, bblob)
+
+
+_ALLOC_CHILD = """
+import sys
+sys.path.insert(0, {root!r})
+import paper_1903_10722_gb300 as gpu
+try:
+    gpu.MLP(540, 512, 256, 256)
+    print("no failure")
+except gpu.FFSError as e:
+    print("status", e.status)
+m = gpu.MLP(540, 512, 256, 256)   # later allocations succeed
+m.init(1)
+print("after", m.adam_steps())
+"""
+
+
+def test_allocation_failure_is_reported(gpu):
+    """An allocation made to fail on the host (FFS_INJECT_ALLOC_FAILURE=3: the
+    third allocation of a network's buffers, in a child process) is reported
+    as FFS_ENOMEM with everything allocated so far freed; the next network is
+    created and used normally."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FFS_INJECT_ALLOC_FAILURE="3")
+    r = subprocess.run([sys.executable, "-c", _ALLOC_CHILD.format(root=root)], capture_output=True, text=True,
+                       env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "status %d" % gpu.FFS_ENOMEM in r.stdout and "after 0" in r.stdout, r.stdout
+
+
 def test_batch_checkpoint_resume_equals_uninterrupted_run(gpu):
     specs = make_batch(count=7, seed=5, n_range=(5, 120), s_range=(2, 9), m_range=(1, 8))
     prm = gpu.ffs_params_default()
