@@ -457,9 +457,10 @@ int ffs_islands_stats_history(const ffs_islands *isl, int64_t *out, int32_t max_
  * instance's rows and makespans, the generation count, the decode count and
  * the GA parameters) to or from a host blob of ffs_batch_checkpoint_bytes
  * bytes; both synchronise `stream`.  The blob carries its length and a
- * checksum of its contents (FNV-1a over 64-bit words).  Load accepts only a
- * complete, unaltered blob of a batch of the same instances and torus
- * (FFS_EINVAL otherwise, nothing written); the
+ * checksum of its contents (FNV-1a over 64-bit words).  Load reads no byte
+ * past that length (`size` may be larger) and accepts only a complete,
+ * unaltered blob whose sections fill its length exactly, of a batch of the
+ * same instances and torus (FFS_EINVAL otherwise, nothing written); the
  * launch shape in use is kept.  Generations after a load draw the same
  * Philox streams as the uninterrupted run, so the results are identical.
  * ffs_batch_dry_run: kind 0 runs one generation's launches (breeding and
@@ -671,8 +672,11 @@ int ffs_islands_set_generation(ffs_islands *isl, int64_t generation);
  * with a surrogate attached its ring buffer (filled slots and counters),
  * training-round count and the network's parameters, Adam moments and step
  * count.  Save and load synchronise `stream`.  The blob carries its length
- * and a checksum of its contents (FNV-1a over 64-bit words); load refuses a
- * truncated or altered blob (FFS_EINVAL, nothing written) and checks that it
+ * and a checksum of its contents (FNV-1a over 64-bit words); load reads no
+ * byte past that length (`size` may be larger), refuses a truncated or
+ * altered blob, one whose sections do not fill its length exactly, and GA
+ * parameters outside ffs_islands_create's limits (FFS_EINVAL, nothing
+ * written), and checks that it
  * comes from a handle of the same instance (a fingerprint of n, S, M, p and
  * the objective's tables), islands, row stride and surrogate shape (attach
  * the surrogate before loading), else FFS_EINVAL with nothing written; the

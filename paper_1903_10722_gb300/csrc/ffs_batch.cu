@@ -806,6 +806,7 @@ int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_
         return set_error(FFS_EINVAL, "checkpoint truncated (%lld of %lld bytes)", (long long)size, (long long)hd.bytes);
     if (blob_checksum(static_cast<const char *>(host), hd.bytes, offsetof(BatchBlobHeader, checksum)) != hd.checksum)
         return set_error(FFS_EINVAL, "checkpoint corrupted (checksum differs)");
+    r.size = hd.bytes;   // only what the checksum covers is read
     if (hd.count != b->count || hd.rows != b->rows || hd.cols != b->cols)
         return set_error(FFS_EINVAL, "checkpoint of %d instances on %dx%d tori; this batch: %d on %dx%d", hd.count,
                          hd.rows, hd.cols, b->count, b->rows, b->cols);
@@ -819,6 +820,8 @@ int ffs_batch_checkpoint_load(ffs_batch *b, const void *host, int64_t size, ffs_
         mss[i] = r.take(b16(cells * 4));
         if (!rows[i] || !mss[i]) return set_error(FFS_EINVAL, "checkpoint truncated (instance %d)", i);
     }
+    if (r.off != hd.bytes)
+        return set_error(FFS_EINVAL, "checkpoint of %lld bytes, its sections %lld", (long long)hd.bytes, (long long)r.off);
     for (int i = 0; i < b->count; ++i) {
         const BatchInst &h = b->hinst[i];
         FFS_CUDA_TRY(cudaMemcpyAsync(h.pop[b->host_cur], rows[i], (size_t)cells * h.ld * 2, cudaMemcpyDefault, st));

@@ -1446,6 +1446,19 @@ static void drop_generation_graphs(ffs_islands *S)
     if (S->sur) S->sur->drop_graphs();
 }
 
+// The GA parameters' own limits (at creation and when a checkpoint brings
+// them back).
+static int check_ga_params(const ffs_params *prm)
+{
+    if (prm->migration_mode < FFS_MIG_NONE || prm->migration_mode > FFS_MIG_PENETRATION)
+        return set_error(FFS_EINVAL, "migration_mode %d", prm->migration_mode);
+    if (prm->ring_den <= 0 || prm->ring_num < 0 || prm->theta_den <= 0 || prm->theta_num < 0 ||
+        prm->theta_num > prm->theta_den)
+        return set_error(FFS_EINVAL, "migration fractions must be num >= 0, den > 0, theta <= 1");
+    if (prm->migration_gap < 0) return set_error(FFS_EINVAL, "migration_gap %d < 0", prm->migration_gap);
+    return FFS_OK;
+}
+
 int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t n_cellular, int32_t rows,
                        int32_t cols, int32_t n_pseudo, int32_t pseudo_size, ffs_stream stream, ffs_islands **out)
 {
@@ -1458,12 +1471,7 @@ int ffs_islands_create(const ffs_instance *inst, const ffs_params *prm, int32_t 
         return set_error(FFS_EINVAL, "bad torus %dx%d", rows, cols);
     if (n_pseudo > 0 && (pseudo_size < 2 || (pseudo_size & 1)))
         return set_error(FFS_EINVAL, "pseudo island size %d must be even and >= 2", pseudo_size);
-    if (prm->migration_mode < FFS_MIG_NONE || prm->migration_mode > FFS_MIG_PENETRATION)
-        return set_error(FFS_EINVAL, "migration_mode %d", prm->migration_mode);
-    if (prm->ring_den <= 0 || prm->ring_num < 0 || prm->theta_den <= 0 || prm->theta_num < 0 ||
-        prm->theta_num > prm->theta_den)
-        return set_error(FFS_EINVAL, "migration fractions must be num >= 0, den > 0, theta <= 1");
-    if (prm->migration_gap < 0) return set_error(FFS_EINVAL, "migration_gap %d < 0", prm->migration_gap);
+    if (int rc = check_ga_params(prm)) return rc;
     ffs_islands *S = new ffs_islands();
     S->inst = inst;
     S->prm = *prm;
@@ -2326,6 +2334,8 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
         return set_error(FFS_EINVAL, "checkpoint truncated (%lld of %lld bytes)", (long long)size, (long long)h.bytes);
     if (blob_checksum(static_cast<const char *>(host), h.bytes, offsetof(IslandsBlobHeader, checksum)) != h.checksum)
         return set_error(FFS_EINVAL, "checkpoint corrupted (checksum differs)");
+    r.size = h.bytes;   // only what the checksum covers is read
+    if (int rc = check_ga_params(&h.prm)) return rc;
     if (h.I != S->I || h.ld != S->ld || h.n != S->inst->n)
         return set_error(FFS_EINVAL, "checkpoint of %d islands (ld %d, n %d); this handle has %d (ld %d, n %d)", h.I, h.ld,
                          h.n, S->I, S->ld, S->inst->n);
@@ -2372,6 +2382,8 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
         net = r.take(net_bytes);
         if (!ring_rows || !ring_ms || !net) return set_error(FFS_EINVAL, "checkpoint truncated (surrogate state)");
     }
+    if (r.off != h.bytes)
+        return set_error(FFS_EINVAL, "checkpoint of %lld bytes, its sections %lld", (long long)h.bytes, (long long)r.off);
     // everything validated: write the state
     for (int i = 0; i < S->I; ++i) {
         const int c = S->host_cur[i];

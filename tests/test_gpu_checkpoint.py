@@ -167,6 +167,68 @@ def test_checkpoints_refuse_corrupted_blobs(gpu):
     gpu.ffs_batch_checkpoint_load(bt2, bblob)
 
 
+def _reseal(blob, bytes_at, sum_at, length=None):
+    """The blob with its length field (at byte `bytes_at`) set to `length` when
+    given and its checksum (at `sum_at`) recomputed over that length: FNV-1a
+    over the 64-bit words, the checksum's own word taken as zero -- so that
+    only the checks after the checksum can refuse it."""
+    b = blob.copy()
+    if length is not None:
+        b[bytes_at:bytes_at + 8] = np.frombuffer(np.int64(length).tobytes(), np.uint8)
+    n = int(np.frombuffer(b[bytes_at:bytes_at + 8].tobytes(), np.int64)[0])
+    words = np.frombuffer(b[:n].tobytes(), dtype=np.uint64).copy()
+    words[sum_at // 8] = 0
+    h = 14695981039346656037
+    for w in words.tolist():
+        h = ((h ^ w) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    b[sum_at:sum_at + 8] = np.frombuffer(np.uint64(h).tobytes(), np.uint8)
+    return b
+
+
+def test_checkpoints_read_only_their_own_length_and_check_parameters(gpu):
+    """Bytes after a blob's own length are never read (a longer buffer loads);
+    a length field made shorter, with a valid checksum over that length, is
+    refused because the sections no longer fit; GA parameters outside
+    ffs_islands_create's limits are refused under a valid checksum; nothing
+    is written by a refused load."""
+    spec = make_instance(24, 5, 2, 3, seed=32)
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    a = _dual(gpu, inst)
+    gpu.ffs_island_step(a, -1, 4)
+    blob = gpu.ffs_checkpoint_save(a)
+    BYTES, SUM, PRM = 40, 48, 56   # IslandsBlobHeader offsets
+    assert np.array_equal(_reseal(blob, BYTES, SUM), blob)   # the test's checksum is the library's
+    b = _dual(gpu, inst)
+    before = _islands_state(gpu, b)
+    refused = [_reseal(blob, BYTES, SUM, len(blob) - 16)]
+    for field, value in (("migration_mode", 9), ("ring_den", 0), ("theta_num", 1 << 40), ("migration_gap", -1)):
+        bad = blob.copy()
+        f = getattr(gpu.ffs_params, field)
+        bad[PRM + f.offset:PRM + f.offset + f.size] = np.frombuffer(
+            np.array([value], dtype=np.int64 if f.size == 8 else np.int32).tobytes(), np.uint8)
+        refused.append(_reseal(bad, BYTES, SUM))
+    for bad in refused:
+        with pytest.raises(gpu.FFSError) as e:
+            gpu.ffs_checkpoint_load(b, bad)
+        assert e.value.status == gpu.FFS_EINVAL
+    after = _islands_state(gpu, b)
+    assert all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) for x, y in zip(before, after))
+    gpu.ffs_checkpoint_load(b, np.concatenate([blob, np.full(64, 0xA5, np.uint8)]))
+    _assert_same_islands(gpu, a, b)
+    # the batch's blob likewise (BatchBlobHeader: length at 48, checksum at 56)
+    specs = make_batch(count=3, seed=6, n_range=(5, 40), s_range=(2, 5), m_range=(1, 4))
+    bt = gpu.Batch(specs, gpu.ffs_params_default(), 8, 8)
+    gpu.ffs_batch_step(bt, 2)
+    bblob = gpu.ffs_batch_checkpoint_save(bt)
+    assert np.array_equal(_reseal(bblob, 48, 56), bblob)
+    bt2 = gpu.Batch(specs, gpu.ffs_params_default(), 8, 8)
+    with pytest.raises(gpu.FFSError) as e:
+        gpu.ffs_batch_checkpoint_load(bt2, _reseal(bblob, 48, 56, len(bblob) - 16))
+    assert e.value.status == gpu.FFS_EINVAL
+    gpu.ffs_batch_checkpoint_load(bt2, np.concatenate([bblob, np.zeros(32, np.uint8)]))
+    assert gpu.ffs_batch_best(bt2).tolist() == gpu.ffs_batch_best(bt).tolist()
+
+
 _ALLOC_CHILD = """
 import sys
 sys.path.insert(0, {root!r})
