@@ -2381,6 +2381,7 @@ int ffs_checkpoint_load(ffs_islands *S, const void *host, int64_t size, ffs_stre
         net_bytes = r16(mlp_state_bytes(R->mlp));
         net = r.take(net_bytes);
         if (!ring_rows || !ring_ms || !net) return set_error(FFS_EINVAL, "checkpoint truncated (surrogate state)");
+        if (int rc = mlp_check_state(R->mlp, net, net_bytes)) return rc;
     }
     if (r.off != h.bytes)
         return set_error(FFS_EINVAL, "checkpoint of %lld bytes, its sections %lld", (long long)h.bytes, (long long)r.off);

@@ -325,6 +325,7 @@ int mlp_max_batch(const ffs_mlp *m);
 int64_t mlp_state_bytes(const ffs_mlp *m);
 int mlp_save(const ffs_mlp *m, void *host, cudaStream_t st);                   // synchronises
 int mlp_load(ffs_mlp *m, const void *host, int64_t size, cudaStream_t st);     // synchronises
+int mlp_check_state(const ffs_mlp *m, const void *host, int64_t size);        // mlp_load's checks alone
 // The scoring copy: allocate it (idempotent) and take it (stream-ordered);
 // mlp_forward_folded reads it when asked to (with activations of its own;
 // max_ctas > 0 caps the CTAs of its persistent GEMMs).

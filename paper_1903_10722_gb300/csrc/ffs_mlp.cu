@@ -1061,7 +1061,7 @@ int mlp_save(const ffs_mlp *M, void *host, cudaStream_t st)
     return FFS_OK;
 }
 
-int mlp_load(ffs_mlp *M, const void *host, int64_t size, cudaStream_t st)
+int mlp_check_state(const ffs_mlp *M, const void *host, int64_t size)
 {
     if (size < (int64_t)sizeof(MlpBlobHeader)) return set_error(FFS_EINVAL, "network state: %lld bytes", (long long)size);
     MlpBlobHeader h;
@@ -1073,6 +1073,14 @@ int mlp_load(ffs_mlp *M, const void *host, int64_t size, cudaStream_t st)
                          M->in_dim, M->h1, M->h2);
     if (size < mlp_state_bytes(M)) return set_error(FFS_EINVAL, "network state truncated");
     if (h.adam_t < 0) return set_error(FFS_EINVAL, "network state: step count %lld", (long long)h.adam_t);
+    return FFS_OK;
+}
+
+int mlp_load(ffs_mlp *M, const void *host, int64_t size, cudaStream_t st)
+{
+    if (int rc = mlp_check_state(M, host, size)) return rc;
+    MlpBlobHeader h;
+    memcpy(&h, host, sizeof(h));
     const float *p = reinterpret_cast<const float *>(static_cast<const char *>(host) + sizeof(h));
     FFS_CUDA_TRY(cudaMemcpyAsync(M->params, p, M->n_params * 4, cudaMemcpyDefault, st));
     FFS_CUDA_TRY(cudaMemcpyAsync(M->m, p + M->n_params, M->n_params * 4, cudaMemcpyDefault, st));

@@ -229,6 +229,38 @@ def test_checkpoints_read_only_their_own_length_and_check_parameters(gpu):
     assert gpu.ffs_batch_best(bt2).tolist() == gpu.ffs_batch_best(bt).tolist()
 
 
+def test_screened_checkpoint_checks_the_network_before_writing(gpu):
+    """The network's part of a screened blob (its last section) is checked
+    before anything is written: with its magic altered and the checksum
+    resealed, the load is refused and the islands keep their rows."""
+    spec = make_instance(20, 4, 2, 3, seed=33)
+    inst = gpu.Instance(spec.n, spec.S, spec.M, spec.p)
+    sp = gpu.ffs_surrogate_params_default()
+    sp.candidates, sp.train_batch, sp.ring_capacity, sp.warmup_generations = 4, 128, 1024, 1
+    a = _dual(gpu, inst)
+    net = gpu.MLP(540, 512, 256, 1024)
+    net.init(5)
+    gpu.ffs_islands_attach_surrogate(a, net, sp)
+    gpu.ffs_island_step(a, -1, 3)
+    blob = gpu.ffs_checkpoint_save(a)
+    net_bytes = int(gpu.load().ffs_mlp_state_bytes(net.handle))
+    at = len(blob) - (net_bytes + 15) // 16 * 16   # the network's header
+    bad = blob.copy()
+    bad[at] ^= 0x01
+    bad = _reseal(bad, 40, 48)
+    b = _dual(gpu, inst)
+    net_b = gpu.MLP(540, 512, 256, 1024)
+    gpu.ffs_islands_attach_surrogate(b, net_b, sp)
+    before = _islands_state(gpu, b)
+    with pytest.raises(gpu.FFSError) as e:
+        gpu.ffs_checkpoint_load(b, bad)
+    assert e.value.status == gpu.FFS_EINVAL and "network state" in str(e.value)
+    after = _islands_state(gpu, b)
+    assert all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) for x, y in zip(before, after))
+    gpu.ffs_checkpoint_load(b, blob)
+    _assert_same_islands(gpu, a, b)
+
+
 _ALLOC_CHILD = """
 import sys
 sys.path.insert(0, {root!r})
