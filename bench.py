@@ -1164,7 +1164,7 @@ def _paper_instance(ffs, inst, iseed, gens, seeds, sweep):
 # the launch shapes the autotuner picks, (threads, chunk, variant) -> bytes,
 # from ncu captures of the current kernel (--metrics dram__bytes_read.sum,
 # dram__bytes_write.sum); other shapes report null.
-K_STEP_DECODE_DRAM_BYTES = {(384, 104, 3): 116_588_544 + 7_509_248}
+K_STEP_DECODE_DRAM_BYTES = {(384, 104, 3): 116_588_544 + 7_509_248, (384, 128, 3): 117_054_976 + 6_821_376}
 
 
 # DRAM bytes of one k_batch_cellular (decode) launch of batch_256, per
