@@ -403,7 +403,7 @@ def run_ours(args):
     _apply_shape(prm, args)
     stream = torch.cuda.current_stream()
     isl = ffs.Islands(inst, prm, w["n_cellular"], w["rows"], w["cols"], w["n_pseudo"], w["pseudo_size"])
-    tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=4)
+    tuned = None if args.no_autotune else ffs.ffs_islands_autotune(isl, repeats=8)
     if tuned:
         used = ffs.ffs_islands_params(isl)
         prm.decode_chunk, prm.block_threads, prm.decode_variant = used.decode_chunk, used.block_threads, used.decode_variant
