@@ -12,12 +12,18 @@ replayed from the library's CUDA graph.  ``value`` = exact makespan evaluations
 (children decoded) per second, counted by the library.
 
 Other keys: ``roofline`` for the dominant kernel (the decode launch,
-integer-ALU bound, timed with the breeding and replacement launches around
-it; algorithmic ops per launch / their CUDA-event duration vs. SMs x 128
-lanes x max SM clock), ``e2e`` (the same step with the
-populations uploaded from and downloaded to pinned host memory every step),
-``cpu_baseline`` (the CPU oracle on a bounded sample), ``clocks`` (nvidia-smi
-sampled during the timed region).
+integer-ALU bound: algorithmic ops per launch / its CUDA-event duration
+timed alone, against SMs x 128 lanes x max SM clock; ``group`` the same
+with the breeding and pair-replacement launches around it; ``traffic`` its
+DRAM bytes from an ncu capture at the launch shape in use), ``e2e`` (the
+same step with the populations uploaded from and downloaded to pinned host
+memory every step), ``cpu_baseline`` (the CPU oracle on a bounded sample),
+``clocks`` (nvidia-smi sampled during the timed region), and two
+sub-records: ``batch_256`` (256 uneven instances in one persistent launch,
+with its own roofline and clocks) and ``surrogate_100x10`` (plain against
+surrogate-screened GA over GA seeds 7..11: the median best-versus-time
+curves, the time-to-plain-best ratio, rank quality and the per-generation
+cost split); ``--no-subrecords`` leaves both out.
 
 ``--impl reference`` times the CPU oracle on this workload instead.  N > 1
 (torchrun) runs independent replicas, one per GPU (the islands of one run
